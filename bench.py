@@ -1,0 +1,313 @@
+#!/usr/bin/env python
+"""Benchmark of the sketch-based IM hot path (one K-seed selection per step).
+
+A step is one call of im_select_seeds on the mid-size workload: R-MAT scale
+20 (edge factor 16, a/b/c = 0.57/0.19/0.19, duplicates and self-loops
+removed), weighted-cascade IC, J = 256 simulations, K = 50 seeds, rebuild
+threshold e = 0.01 (the paper's Table 3 workload shape at Pokec /
+LiveJournal scale; synthetic because the SNAP graphs are not available).
+Covers every step of the method: draws, fill, propagation to the fixpoint,
+estimate + argmax, cover, count, rebuilds.
+
+Metric: K-seed selections per second (the inverse of time-to-K-seeds),
+whole job: with --gpus N every rank runs an independent replica (the path
+does not shard on one GPU), value = N * steps / max-over-ranks time.
+
+--impl reference times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-K-seeds (K-seed selections/s)"
+UNIT = "selections/s"
+CPU_SAMPLE_J = 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="rmat20")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(wl, g, world):
+    return {"workload": wl.name, "n": g.n, "m": g.m, "J": wl.J, "K": wl.K,
+            "model": wl.model["kind"], "rebuild_eps": wl.rebuild_eps, "seed": wl.seed,
+            "l2": "inputs larger than L2 (n*J register bytes > 129 MB)",
+            "replicas": world, "parallelism": f"replicas x{world}"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def ncu_traffic(workload):
+    """DRAM bytes per sweep launch from the committed ncu summary, if current."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+        return d.get(workload)
+    except Exception:
+        return None
+
+
+def cpu_baseline(wl, g):
+    """The oracle, as it stands, on a bounded sample: J=16 of the workload's J
+    simulations (all K seeds, same graph and model); time scaled by J/16."""
+    import oracle as O
+    thr = O.thresholds(g, wl.model)
+    t = time.perf_counter()
+    O.select_seeds(g, thr, CPU_SAMPLE_J, wl.K, wl.seed, wl.rebuild_eps, "reverse")
+    dt = time.perf_counter() - t
+    scaled = dt * wl.J / CPU_SAMPLE_J
+    return {"value": 1.0 / scaled, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": (f"oracle select_seeds on the same graph with J={CPU_SAMPLE_J} of {wl.J} "
+                       f"simulations, K={wl.K}; measured {dt:.2f} s, scaled x{wl.J // CPU_SAMPLE_J} "
+                       f"to {scaled:.1f} s per selection")}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as O
+    import workloads as W
+    wl = W.workload(args.workload)
+    g = wl.graph()
+    thr = O.thresholds(g, wl.model)
+    for _ in range(args.warmup):
+        O.select_seeds(g, thr, CPU_SAMPLE_J, wl.K, wl.seed, wl.rebuild_eps, "reverse")
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        O.select_seeds(g, thr, CPU_SAMPLE_J, wl.K, wl.seed, wl.rebuild_eps, "reverse")
+        times.append((time.perf_counter() - t) * wl.J / CPU_SAMPLE_J)
+    per = sum(times) / len(times)
+    value = 1.0 / per
+    sample = (f"oracle select_seeds with J={CPU_SAMPLE_J} of {wl.J} simulations per step, "
+              f"K={wl.K}; step times scaled x{wl.J // CPU_SAMPLE_J}")
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+           "data": "synthetic", "config": workload_config(wl, g, 1),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_2410_14047_gb300 as im
+    import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    wl = W.workload(args.workload)
+    g = wl.graph()
+    ctx = im.im_ctx_create(local)
+    G = im.im_graph_load(ctx, g.rowptr, g.col, wl.model)
+    im.im_ctx_set_timing(ctx, True)
+
+    def step():
+        return im.im_select_seeds(G, wl.K, wl.J, seed=wl.seed, rebuild_eps=wl.rebuild_eps)
+
+    ref_seeds = None
+    for _ in range(args.warmup):
+        ref_seeds = step()["seeds"].tolist()
+
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    agg = {"alg_bytes_sweep": 0, "ms_propagate": 0.0, "sweep_launches": 0, "launches": 0,
+           "builds": 0, "sweeps": 0, "ms_pick_kernels": 0.0, "ms_cover_kernels": 0.0,
+           "ms_fill_kernels": 0.0, "cover_levels": 0, "sweep_edges": 0}
+    deterministic = True
+    ev0.record(stream)
+    for _ in range(args.steps):
+        r = step()
+        st = im.im_last_stats(ctx)
+        for k in agg:
+            agg[k] += st[k]
+        deterministic &= (r["seeds"].tolist() == ref_seeds)
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t.item())
+
+    # end-to-end through the public API with host buffers: pinned host CSR,
+    # graph load (H2D copy) + selection + result read-back every step
+    rp_pin = torch.from_numpy(g.rowptr).pin_memory()
+    col_pin = torch.from_numpy(g.col).pin_memory()
+    rp_np, col_np = rp_pin.numpy(), col_pin.numpy()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        G2 = im.im_graph_load(ctx, rp_np, col_np, wl.model)
+        r2 = im.im_select_seeds(G2, wl.K, wl.J, seed=wl.seed, rebuild_eps=wl.rebuild_eps)
+        G2.free()
+        deterministic &= (r2["seeds"].tolist() == ref_seeds)
+    torch.cuda.synchronize()
+    e_el = time.perf_counter() - e0
+    te = torch.tensor([e_el], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e_max = float(te.item())
+
+    if rank == 0:
+        golden = None
+        gp = os.path.join(ROOT, "tests", "golden", f"select_{args.workload}.json")
+        if os.path.exists(gp):
+            golden = json.load(open(gp))["seeds"] == ref_seeds
+        peaks = measured_peaks()
+        peak = peaks["hbm_gbs"] if peaks else 6800.0
+        achieved = (agg["alg_bytes_sweep"] / 1e9) / (agg["ms_propagate"] / 1e3) if agg["ms_propagate"] else 0.0
+        per_launch_bytes = agg["alg_bytes_sweep"] / max(agg["sweep_launches"], 1)
+        tr = ncu_traffic(args.workload)
+        out = {
+            "metric": METRIC, "value": world * args.steps / tmax, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic (seeded R-MAT standing in for the paper's SNAP graphs)",
+            "config": workload_config(wl, g, world),
+            "time_to_k_seeds_s": tmax / args.steps,
+            "register_gteps": agg["sweep_edges"] * wl.J / (agg["ms_propagate"] / 1e3) / 1e9
+            if agg["ms_propagate"] else None,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": tr,
+                         "kernel": "k_frontier<kWC,kPush> (propagation sweep)",
+                         "alg_bytes_per_launch": per_launch_bytes,
+                         "avg_launch_ms": agg["ms_propagate"] / max(agg["sweep_launches"], 1),
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
+            "phase_ms_per_step": {k: agg[k] / args.steps for k in
+                                  ("ms_propagate", "ms_pick_kernels", "ms_cover_kernels", "ms_fill_kernels")},
+            "counts_per_step": {k: agg[k] / args.steps for k in
+                                ("builds", "sweeps", "sweep_launches", "cover_levels", "launches")},
+            "gpu_launches": int(agg["launches"]),
+            "e2e": {"value": world * args.e2e_steps / e_max, "unit": UNIT,
+                    "h2d_bytes_per_step": int(g.rowptr.nbytes + g.col.nbytes),
+                    "d2h_bytes_per_step": int(wl.K * (4 + 8 + 8))},
+            "clocks": clocks,
+            "deterministic": bool(deterministic),
+            "seeds_match_oracle_golden": golden,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(wl, g)
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,208 @@
+/*
+ * difuser_im.h — C ABI of the GB300 (sm_103a) implementation of the
+ * single-GPU hot path of DiFuseR's sketch-based influence maximization
+ * (Gokturk & Kaya, arXiv 2410.14047) under the independent cascade model.
+ *
+ * Everything here is plain C: host or device pointers and sizes, no C++ or
+ * PyTorch types.  Every call returns an im_status; on error the outputs are
+ * left untouched and im_last_error() describes the failure.  All device work
+ * of a context runs on the CUDA stream given at im_ctx_create.  The library
+ * never calls back into the caller except through the optional allocator.
+ *
+ * Conventions shared by every entry point (the paper leaves them open):
+ *   edge hash      hE(u,v) = MurmurHash3_x86_32(LE32(u)||LE32(v), seed 0) & 0x7FFFFFFF   (Sec. 2.2, Eq. hash)
+ *   vertex hash    hV_j(u) = MurmurHash3_x86_32(LE32(u), seed salt_j)                       (Sec. 2.3)
+ *   rank           r0(u,j) = clz32(hV_j(u)) in [0,32]                                       (Eq. sketch-init)
+ *   threshold      thr(u,v) = floor((double)w_fp32(u,v) * 2^31), w = 1 -> 2^31 (always live)
+ *   live test      edge (u,v) live in simulation j iff (X_j XOR hE(u,v)) < thr(u,v)        (Eq. hash_prob)
+ *   simulations    (X_j, salt_j), j < J, from SplitMix64(seed): z = next(), X = z & 0x7FFFFFFF,
+ *                  salt = z >> 32, stable-sorted by X (Sec. 2.2, Sec. 4.1 FASST sort)
+ *   registers      M[u][j] uint8, n x J row-major (a vertex's J registers contiguous, Sec. 3.1);
+ *                  value in [0,32], or 0xFF = u visited in simulation j (Sec. 3.1, Sec. 3.3)
+ *   estimate sum   S_u = sum_j f(M[u][j]), f(r) = 2^(32-r), f(0xFF) = 2^32, exact uint64
+ *                  (harmonic mean of Eq. gpu-sketch-int: H_u = J * 2^32 / S_u)
+ *   estimate       e_u = J * 2^32 / (phi * S_u), phi = 0.77351 (Eq. sketch-estimate)
+ *
+ * Limits: 1 <= n < 2^26, 0 <= m < 2^31, J in {16,32,64,128,256,512,1024}.
+ */
+#ifndef DIFUSER_IM_H
+#define DIFUSER_IM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define IM_API __attribute__((visibility("default")))
+#else
+#define IM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct im_ctx im_ctx;
+typedef struct im_graph im_graph;
+typedef struct im_sketch im_sketch;
+
+typedef enum {
+    IM_OK = 0,
+    IM_E_INVAL = -1,   /* bad argument (NULL pointer, malformed CSR, unsupported J) */
+    IM_E_RANGE = -2,   /* a size or id out of range (K > n, vertex id >= n, n too large) */
+    IM_E_NOMEM = -3,   /* the allocation would exceed the context's HBM budget, or failed */
+    IM_E_CUDA = -4,    /* a CUDA runtime call failed; im_last_error() has the CUDA message */
+    IM_E_TIMEOUT = -5, /* an iteration bound was exceeded (a loop that should have converged) */
+    IM_E_STATE = -6    /* call not valid in the current state (e.g. sketch of another graph) */
+} im_status;
+
+typedef enum {
+    IM_IC_UNIFORM = 0,    /* every edge has probability p (Sec. 5 settings 0.005, 0.01, 0.1) */
+    IM_IC_WC = 1,         /* weighted cascade, w(u,v) = 1 / indeg(v) in fp32 (Sec. 2.1, Fig. 1b) */
+    IM_IC_TRIVALENCY = 2, /* w(u,v) = {0.1, 0.01, 0.001}[MurmurHash3_x86_32(LE32(u)||LE32(v),
+                             (uint32)(seed ^ seed >> 32)) mod 3] */
+    IM_IC_EXPLICIT = 3    /* per-edge probabilities w[e] in out-CSR order (Sec. 5 N/U settings) */
+} im_model_kind;
+
+typedef struct {
+    int32_t kind;     /* im_model_kind */
+    float p;          /* IM_IC_UNIFORM: edge probability in [0, 1] */
+    uint64_t seed;    /* IM_IC_TRIVALENCY: class-hash seed */
+    const float* w;   /* IM_IC_EXPLICIT: m host floats in [0, 1], out-CSR order; copied */
+} im_model;
+
+/* Device memory provider.  alloc returns a device pointer of at least `bytes`
+ * bytes (256-byte aligned) usable on `stream`, or NULL; free releases it.
+ * Passing NULL to im_ctx_create selects cudaMallocAsync / cudaFreeAsync. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* user);
+    void (*free)(void* ptr, size_t bytes, void* stream, void* user);
+    void* user;
+} im_allocator;
+
+/* Per-call counters and phase times of the last im_select_seeds /
+ * im_sketch_build on a context (device-side counters, CUDA-event times). */
+typedef struct {
+    double ms_total;          /* whole call, host wall clock */
+    double ms_build;          /* sims + fill + propagation of the first build, host wall clock */
+    double ms_rebuild;        /* all rebuilds, host wall clock */
+    double ms_pick;           /* all pick + cover + score read-back steps, host wall clock */
+    double ms_propagate;      /* CUDA-event time of all propagation sweep kernels (timing on) */
+    double ms_cover_kernels;  /* CUDA-event time of all cover level kernels (timing on) */
+    double ms_pick_kernels;   /* CUDA-event time of all estimate + argmax kernels (timing on) */
+    double ms_fill_kernels;   /* CUDA-event time of all fill kernels (timing on) */
+    int64_t launches;         /* kernels launched by the call */
+    int64_t sweep_launches;   /* propagation sweep kernels launched (with or without work) */
+    int64_t builds;           /* 1 + number of rebuilds */
+    int64_t sweeps;           /* propagation sweep launches that had work */
+    int64_t cover_levels;     /* cover level launches that had work */
+    uint64_t sweep_vertices;  /* queue entries processed by all sweeps */
+    uint64_t sweep_edges;     /* in-edges examined by all sweeps */
+    uint64_t sweep_chunks;    /* 16-simulation chunks with >= 1 live, non-visited source register */
+    uint64_t sweep_cas;       /* 4-register words written by atomic CAS (improvements) */
+    uint64_t sweep_changed;   /* vertices enqueued as changed */
+    uint64_t cover_edges;     /* out-edges examined by cover levels */
+    uint64_t cover_chunks;    /* 16-simulation chunks examined by cover levels */
+    uint64_t visited;         /* registers visited at the end (Count(M,-1)) */
+    uint64_t alg_bytes_sweep; /* algorithmic bytes of all sweeps (see the design notes) */
+} im_stats;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (NULL = the legacy default stream).  `hbm_budget_bytes` caps the device
+ * memory the context may hold (0 = no cap).  `alloc` may be NULL.
+ * Errors: IM_E_INVAL (out NULL), IM_E_CUDA (no such device). */
+IM_API im_status im_ctx_create(int device, void* cuda_stream, uint64_t hbm_budget_bytes,
+                        const im_allocator* alloc, im_ctx** out);
+IM_API void im_ctx_destroy(im_ctx* ctx);
+/* Bytes currently held / the high-water mark of a context. */
+IM_API uint64_t im_ctx_bytes_in_use(const im_ctx* ctx);
+IM_API uint64_t im_ctx_bytes_peak(const im_ctx* ctx);
+/* Message of the last error on this context ("" if none); valid until the next call. */
+IM_API const char* im_last_error(const im_ctx* ctx);
+IM_API const char* im_status_str(im_status s);
+/* Counters of the last selection / build (see im_stats). */
+IM_API im_status im_last_stats(const im_ctx* ctx, im_stats* out);
+/* enable != 0: bracket every kernel launch with CUDA events on the context's
+ * stream and report per-kind kernel time in im_stats (adds two event records
+ * per launch).  Off by default. */
+IM_API im_status im_ctx_set_timing(im_ctx* ctx, int enable);
+
+/* ---- graph ------------------------------------------------------------- */
+
+/* Copies a directed graph (CSR of out-edges: rowptr[n+1], col[m], host
+ * int32, rows sorted ascending, no duplicate edges, no self-loops: parallel
+ * edges must be merged beforehand, Sec. 2.1) and a diffusion model to the
+ * device, builds the reverse CSR (in-edges) and the edge thresholds
+ * (Sec. 2.1 models, Eq. hash_prob fixed point).  The caller keeps ownership of
+ * every input.  Errors: IM_E_INVAL (malformed CSR or model), IM_E_RANGE
+ * (n or m out of range), IM_E_NOMEM, IM_E_CUDA. */
+IM_API im_status im_graph_load(im_ctx* ctx, int32_t n, int64_t m, const int32_t* rowptr,
+                        const int32_t* col, const im_model* model, im_graph** out);
+IM_API void im_graph_free(im_graph* g);
+/* Device pointers of the loaded out-CSR (for callers that gather on device). */
+IM_API im_status im_graph_info(const im_graph* g, int32_t* n, int64_t* m);
+
+/* ---- sketches (the step-level interface of Alg. 4) ---------------------- */
+
+/* Draws the J simulations (X_j, salt_j) from `seed` (Sec. 2.2, Sec. 4.1),
+ * fills the registers with the vertices' own ranks (Alg. 1) and propagates
+ * them to the fixpoint of Alg. 2: M[u][j] = max rank over the vertices
+ * reachable from u along edges live in simulation j.  Errors: IM_E_INVAL
+ * (unsupported J), IM_E_NOMEM, IM_E_CUDA, IM_E_TIMEOUT. */
+IM_API im_status im_sketch_build(im_graph* g, int32_t J, uint64_t seed, im_sketch** out);
+IM_API void im_sketch_free(im_sketch* sk);
+/* Copies the n x J registers to host memory (n*J bytes, row-major). */
+IM_API im_status im_sketch_registers(const im_sketch* sk, uint8_t* host_out);
+/* Overwrites the registers from host memory (n*J bytes).  For tests: tie and
+ * visited-mark injection.  The visited count is recomputed from the bytes. */
+IM_API im_status im_sketch_set_registers(im_sketch* sk, const uint8_t* host_in);
+/* Copies the sorted simulation parameters X[J], salt[J] to host memory. */
+IM_API im_status im_sketch_sims(const im_sketch* sk, uint32_t* X_out, uint32_t* salt_out);
+/* Sketchwise-Sum of Alg. 4: S_u for every vertex (exact uint64, host n). */
+IM_API im_status im_sketch_sums(const im_sketch* sk, uint64_t* host_out);
+/* Estimate + argmax of Alg. 4: the vertex s not yet picked on this sketch with
+ * the smallest S_s (largest estimate), lowest id on ties; s becomes picked.
+ * *S_out = S_s, *est_out = J * 2^32 / (phi * S_s).  IM_E_RANGE when every
+ * vertex is already picked. */
+IM_API im_status im_sketch_pick(im_sketch* sk, int32_t* s_out, uint64_t* S_out, double* est_out);
+/* Cascade of Alg. 3 / Alg. 4 from vertex s: marks s and every vertex reachable
+ * from s along live edges visited (0xFF) in each simulation.  *count_out =
+ * Count(M,-1) after the cover.  s need not have been picked. */
+IM_API im_status im_sketch_cover(im_sketch* sk, int32_t s, uint64_t* count_out);
+/* Rebuild of Alg. 4: Fill-Sketches + Simulate to the fixpoint on the
+ * non-visited registers; visited registers are kept. */
+IM_API im_status im_sketch_rebuild(im_sketch* sk);
+
+/* ---- the whole method --------------------------------------------------- */
+
+/* Alg. 4 on one device: draws J simulations from `seed`, builds the sketches,
+ * then K times picks the vertex of largest estimate (ties -> lowest id),
+ * covers it and rebuilds when (score - oldscore) / score > rebuild_eps
+ * (score = Count(M,-1)/J, FP64; never after the K-th seed; rebuild_eps < 0
+ * disables rebuilds).  `model` = NULL uses the graph's model.
+ * Outputs (host): seeds_out[K]; score_out[K] (score after each seed, may be
+ * NULL); estimate_out[K] (estimate of each seed when picked, may be NULL);
+ * sketch_out (may be NULL) receives the final sketch, which the caller frees.
+ * Errors: IM_E_RANGE (K < 1 or K > n), IM_E_INVAL, IM_E_NOMEM, IM_E_CUDA,
+ * IM_E_TIMEOUT. */
+IM_API im_status im_select_seeds(im_graph* g, int32_t K, int32_t J, const im_model* model,
+                          uint64_t seed, double rebuild_eps, int32_t* seeds_out,
+                          double* score_out, double* estimate_out, im_sketch** sketch_out);
+
+/* Independent-cascade Monte-Carlo spread of a seed set (the independent
+ * quality oracle of Sec. 5.1, run on the GPU): R simulations; in simulation r
+ * out-edge e (out-CSR index) fires iff (SplitMix64 output number r*m + e of
+ * the stream started at `seed`) >> 33 is below thr[e] — independent coins, each
+ * edge tried once per simulation.  *mean_out = mean reach size, *stderr_out =
+ * sample standard deviation / sqrt(R); sum_out / sumsq_out (may be NULL)
+ * receive the exact sums of reach sizes and squares.  Seeds are host ids.
+ * Errors: IM_E_RANGE (bad id, k < 1, R < 2), IM_E_NOMEM, IM_E_CUDA. */
+IM_API im_status im_spread_mc(im_graph* g, const int32_t* seeds, int32_t k, int64_t R, uint64_t seed,
+                       double* mean_out, double* stderr_out, uint64_t* sum_out,
+                       uint64_t* sumsq_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIFUSER_IM_H */

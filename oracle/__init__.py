@@ -80,6 +80,9 @@ def _load():
                                    P(u64), P(u64)]),
         "orc_spread_ic": (None, [i32, i64, P(i32), P(i32), P(u32), P(i32), i32, i64, u64,
                                  P(u64), P(u64)]),
+        "orc_register_entry": (i32, [i32, i64, P(i32), P(i32), P(u32), u32, u32, ctypes.c_void_p,
+                                     i32]),
+        "orc_reach_mark": (i64, [i32, i64, P(i32), P(i32), P(u32), u32, P(i32), i32, P(u8)]),
         "orc_num_threads": (ctypes.c_int, []),
     }
     for name, (res, args) in sig.items():
@@ -263,6 +266,31 @@ def spread_hash(g, thr, seeds, R: int, seed: int):
 def spread_ic(g, thr, seeds, R: int, seed: int):
     """IC Monte-Carlo spread with independent counter-based coins: (sum, sum of squares)."""
     return _spread("orc_spread_ic", g, thr, seeds, R, seed)
+
+
+def register_entry(g, thr, Xj: int, saltj: int, u: int, vis=None) -> int:
+    """One register by BFS: max rank over R*_j(u) (vis: n bytes, nonzero = visited)."""
+    L = _load()
+    thr = np.ascontiguousarray(thr, dtype=np.uint32)
+    if thr.size == 0:
+        thr = np.zeros(1, np.uint32)
+    vp = None if vis is None else np.ascontiguousarray(vis, dtype=np.uint8).ctypes.data_as(ctypes.c_void_p)
+    return int(L.orc_register_entry(g.n, g.m, _p(g.rowptr, ctypes.c_int32), _p(g.col, ctypes.c_int32),
+                                    _p(thr, ctypes.c_uint32), int(Xj), int(saltj), vp, int(u)))
+
+
+def reach_mark(g, thr, Xj: int, seeds) -> np.ndarray:
+    """Boolean reach set of a seed set in one simulation."""
+    L = _load()
+    thr = np.ascontiguousarray(thr, dtype=np.uint32)
+    if thr.size == 0:
+        thr = np.zeros(1, np.uint32)
+    s = np.ascontiguousarray(seeds, dtype=np.int32)
+    mark = np.empty(max(g.n, 1), dtype=np.uint8)
+    L.orc_reach_mark(g.n, g.m, _p(g.rowptr, ctypes.c_int32), _p(g.col, ctypes.c_int32),
+                     _p(thr, ctypes.c_uint32), int(Xj), _p(s, ctypes.c_int32), s.shape[0],
+                     _p(mark, ctypes.c_uint8))
+    return mark[: g.n].astype(bool)
 
 
 def num_threads() -> int:

@@ -615,6 +615,62 @@ void orc_spread_ic(int32_t n, int64_t m, const int32_t* rowptr, const int32_t* c
     *sumsq_out = sumsq;
 }
 
+/* O1 for one register (full-size spot checks): the largest rank over
+ * R*_j(u), by one BFS from u over edges live in simulation j that avoids
+ * visited vertices (vis[v] != 0; vis may be NULL).  Returns 0xFF if u itself
+ * is visited. */
+int32_t orc_register_entry(int32_t n, int64_t m, const int32_t* rowptr, const int32_t* col,
+                           const uint32_t* thr, uint32_t Xj, uint32_t saltj, const uint8_t* vis,
+                           int32_t u) {
+    (void)m;
+    if (vis && vis[u]) return VISITED;
+    int32_t* queue = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    uint8_t* seen = (uint8_t*)calloc((size_t)n, 1);
+    int32_t head = 0, tail = 0, best = 0;
+    queue[tail++] = u;
+    seen[u] = 1;
+    while (head < tail) {
+        int32_t x = queue[head++];
+        int32_t r = orc_rank(x, saltj);
+        if (r > best) best = r;
+        for (int64_t e = rowptr[x]; e < rowptr[x + 1]; e++) {
+            int32_t y = col[e];
+            if (seen[y] || (vis && vis[y])) continue;
+            if (!live(Xj, orc_edge_hash(x, y), thr[e])) continue;
+            seen[y] = 1;
+            queue[tail++] = y;
+        }
+    }
+    free(queue);
+    free(seen);
+    return best;
+}
+
+/* Reach of a seed set in one simulation (Alg. 3 cascade written as a plain
+ * BFS): mark[v] = 1 for every vertex reachable from the seeds along edges
+ * live in simulation j.  Returns the number of marked vertices. */
+int64_t orc_reach_mark(int32_t n, int64_t m, const int32_t* rowptr, const int32_t* col,
+                       const uint32_t* thr, uint32_t Xj, const int32_t* seeds, int32_t k,
+                       uint8_t* mark) {
+    (void)m;
+    memset(mark, 0, (size_t)n);
+    int32_t* queue = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    int32_t head = 0, tail = 0;
+    for (int32_t i = 0; i < k; i++)
+        if (!mark[seeds[i]]) { mark[seeds[i]] = 1; queue[tail++] = seeds[i]; }
+    while (head < tail) {
+        int32_t x = queue[head++];
+        for (int64_t e = rowptr[x]; e < rowptr[x + 1]; e++) {
+            int32_t y = col[e];
+            if (mark[y] || !live(Xj, orc_edge_hash(x, y), thr[e])) continue;
+            mark[y] = 1;
+            queue[tail++] = y;
+        }
+    }
+    free(queue);
+    return tail;
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

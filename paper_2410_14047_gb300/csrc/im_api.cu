@@ -1,0 +1,968 @@
+// Host implementation of the C ABI declared in include/difuser_im.h.
+//
+// Owns device memory (through the caller's allocator or cudaMallocAsync,
+// charged against the context's HBM budget), validates inputs, and drives
+// the kernels of im_kernels.cu through Alg. 4 of the paper: build
+// (Alg. 1 + Alg. 2 to a fixpoint), then K times pick (Sketchwise-Sum +
+// argmax), cover (Alg. 3 levels) and the error-adaptive rebuild.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/difuser_im.h"
+#include "im_launch.h"
+
+using namespace im;
+
+struct im_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    uint64_t budget = 0;
+    uint64_t in_use = 0;
+    uint64_t peak = 0;
+    bool custom_alloc = false;
+    im_allocator alloc{};
+    std::unordered_map<void*, size_t> sizes;
+    std::string err;
+    im_stats stats{};
+    unsigned long long* pinned = nullptr;  // small pinned staging buffer (64 words)
+    // kernel timing: event pairs recorded around launches, summed at sync points
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_kind;
+    int ev_used = 0;
+};
+
+namespace {
+
+struct DBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+im_status fail(im_ctx* c, im_status s, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+im_status cuda_fail(im_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, IM_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(ctx, call)                                      \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+#define CKS(call)                        \
+    do {                                 \
+        im_status s_ = (call);           \
+        if (s_ != IM_OK) return s_;      \
+    } while (0)
+
+im_status dalloc(im_ctx* c, size_t bytes, DBuf& out) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes == 0) bytes = 256;
+    if (c->budget && c->in_use + bytes > c->budget)
+        return fail(c, IM_E_NOMEM, "HBM budget exceeded: %llu + %llu > %llu bytes",
+                    (unsigned long long)c->in_use, (unsigned long long)bytes,
+                    (unsigned long long)c->budget);
+    void* p = nullptr;
+    if (c->custom_alloc) {
+        p = c->alloc.alloc(bytes, c->stream, c->alloc.user);
+        if (!p) return fail(c, IM_E_NOMEM, "allocator returned NULL for %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMallocAsync(&p, bytes, c->stream);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(c, IM_E_NOMEM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+        }
+    }
+    out.p = p;
+    out.bytes = bytes;
+    c->sizes[p] = bytes;
+    c->in_use += bytes;
+    if (c->in_use > c->peak) c->peak = c->in_use;
+    return IM_OK;
+}
+
+void dfree(im_ctx* c, DBuf& b) {
+    if (!b.p) return;
+    if (c->custom_alloc) c->alloc.free(b.p, b.bytes, c->stream, c->alloc.user);
+    else cudaFreeAsync(b.p, c->stream);
+    c->sizes.erase(b.p);
+    c->in_use -= b.bytes;
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+bool valid_J(int32_t J) {
+    return J >= 16 && J <= kMaxJ && (J & (J - 1)) == 0;
+}
+
+uint32_t prob_threshold_host(float w) {
+    const double t = std::floor((double)w * 2147483648.0);
+    if (!(t > 0.0)) return 0u;
+    if (t >= 2147483648.0) return 2147483648u;
+    return (uint32_t)t;
+}
+
+// Alg. 4 rebuild test in FP64: (score - oldscore) / score > e, score = count/J.
+bool rebuild_due(uint64_t count, uint64_t oldcount, int32_t J, double e) {
+    if (e < 0.0) return false;
+    const double score = (double)count / (double)J;
+    const double oldscore = (double)oldcount / (double)J;
+    return (score - oldscore) / score > e;
+}
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(
+               std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+enum TimeKind { kTPush = 0, kTCover = 1, kTPick = 2, kTFill = 3, kTOther = 4 };
+
+// Adds the durations of the recorded event pairs (all complete: call after a
+// stream synchronize) to the context's statistics.
+void timing_collect(im_ctx* c) {
+    for (int i = 0; i < c->ev_used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]) != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        switch (c->ev_kind[i]) {
+            case kTPush: c->stats.ms_propagate += ms; break;
+            case kTCover: c->stats.ms_cover_kernels += ms; break;
+            case kTPick: c->stats.ms_pick_kernels += ms; break;
+            case kTFill: c->stats.ms_fill_kernels += ms; break;
+            default: break;
+        }
+    }
+    c->ev_used = 0;
+}
+
+// Launch bracket: records a start event (timing on), runs the launch, records
+// the stop event and counts the launch.
+template <class F>
+cudaError_t timed(im_ctx* c, int kind, F&& launch) {
+    int slot = -1;
+    if (c->timing) {
+        if (c->ev_used * 2 + 2 > (int)c->ev.size()) {
+            cudaError_t e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) return e;
+            timing_collect(c);
+        }
+        slot = c->ev_used++;
+        c->ev_kind[slot] = kind;
+        cudaEventRecord(c->ev[2 * slot], c->stream);
+    }
+    cudaError_t e = launch();
+    if (slot >= 0) cudaEventRecord(c->ev[2 * slot + 1], c->stream);
+    c->stats.launches++;
+    if (kind == kTPush) c->stats.sweep_launches++;
+    return e;
+}
+
+// Stream synchronize followed by the collection of finished timings.
+cudaError_t sync_collect(im_ctx* c) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess && c->timing) timing_collect(c);
+    return e;
+}
+
+}  // namespace
+
+struct im_graph {
+    im_ctx* ctx = nullptr;
+    int32_t n = 0;
+    int64_t m = 0;
+    int kind = kUniform;
+    DBuf rp_out, col_out, rp_in, src_in, thr_v, thr_out, thr_in, q_all, ctr_all;
+    GraphDev dev{};
+};
+
+struct im_sketch {
+    im_graph* g = nullptr;
+    int32_t J = 0;
+    DBuf M, X, salt, tab, q[3], ctr, gen, seed_bits, count, part_S, part_u, ticket, stats, err;
+    DBuf out_seed, out_S, out_est;
+    int32_t out_cap = 0;
+    int32_t gen_counter = 0;
+    int32_t picks = 0;
+};
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+extern "C" im_status im_ctx_create(int device, void* cuda_stream, uint64_t hbm_budget_bytes,
+                                   const im_allocator* alloc, im_ctx** out) {
+    if (!out) return IM_E_INVAL;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || device < 0 || device >= ndev) {
+        (void)cudaGetLastError();
+        return IM_E_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return IM_E_CUDA;
+    im_ctx* c = new im_ctx();
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->budget = hbm_budget_bytes;
+    if (alloc && alloc->alloc && alloc->free) {
+        c->custom_alloc = true;
+        c->alloc = *alloc;
+    }
+    if (cudaMallocHost(&c->pinned, 64 * sizeof(unsigned long long)) != cudaSuccess) {
+        delete c;
+        return IM_E_CUDA;
+    }
+    *out = c;
+    return IM_OK;
+}
+
+extern "C" void im_ctx_destroy(im_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    if (c->pinned) cudaFreeHost(c->pinned);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    delete c;
+}
+
+extern "C" im_status im_ctx_set_timing(im_ctx* c, int enable) {
+    if (!c) return IM_E_INVAL;
+    if (enable && c->ev.empty()) {
+        c->ev.resize(256);
+        c->ev_kind.resize(128);
+        for (auto& e : c->ev) CK(c, cudaEventCreate(&e));
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->ev_used = 0;
+    c->timing = enable != 0;
+    return IM_OK;
+}
+
+extern "C" uint64_t im_ctx_bytes_in_use(const im_ctx* c) { return c ? c->in_use : 0; }
+extern "C" uint64_t im_ctx_bytes_peak(const im_ctx* c) { return c ? c->peak : 0; }
+extern "C" const char* im_last_error(const im_ctx* c) { return c ? c->err.c_str() : ""; }
+
+extern "C" const char* im_status_str(im_status s) {
+    switch (s) {
+        case IM_OK: return "IM_OK";
+        case IM_E_INVAL: return "IM_E_INVAL";
+        case IM_E_RANGE: return "IM_E_RANGE";
+        case IM_E_NOMEM: return "IM_E_NOMEM";
+        case IM_E_CUDA: return "IM_E_CUDA";
+        case IM_E_TIMEOUT: return "IM_E_TIMEOUT";
+        case IM_E_STATE: return "IM_E_STATE";
+    }
+    return "IM_E_UNKNOWN";
+}
+
+extern "C" im_status im_last_stats(const im_ctx* c, im_stats* out) {
+    if (!c || !out) return IM_E_INVAL;
+    *out = c->stats;
+    return IM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// graph
+// ---------------------------------------------------------------------------
+static im_status check_model(im_ctx* c, const im_model* mdl, int64_t m) {
+    if (!mdl) return fail(c, IM_E_INVAL, "model is NULL");
+    if (mdl->kind < kUniform || mdl->kind > kExplicit)
+        return fail(c, IM_E_INVAL, "unknown model kind %d", mdl->kind);
+    if (mdl->kind == kUniform && !(mdl->p >= 0.0f && mdl->p <= 1.0f))
+        return fail(c, IM_E_INVAL, "uniform p must be in [0,1]");
+    if (mdl->kind == kExplicit && m > 0 && !mdl->w)
+        return fail(c, IM_E_INVAL, "explicit model needs w[m]");
+    return IM_OK;
+}
+
+static void graph_release(im_graph* g) {
+    im_ctx* c = g->ctx;
+    for (DBuf* b : {&g->rp_out, &g->col_out, &g->rp_in, &g->src_in, &g->thr_v, &g->thr_out,
+                    &g->thr_in, &g->q_all, &g->ctr_all})
+        dfree(c, *b);
+}
+
+// Sets the model part of the device view; allocates per-vertex / per-edge
+// thresholds as the model needs.  thr_out / thr_in of an explicit model are
+// filled by the caller (they need the reverse CSR).
+static im_status set_model(im_graph* g, const im_model* mdl) {
+    im_ctx* c = g->ctx;
+    g->kind = mdl->kind;
+    g->dev.thr_uniform = prob_threshold_host(mdl->p);
+    g->dev.tri_seed = (uint32_t)(mdl->seed ^ (mdl->seed >> 32));
+    g->dev.tri_thr[0] = prob_threshold_host(0.1f);
+    g->dev.tri_thr[1] = prob_threshold_host(0.01f);
+    g->dev.tri_thr[2] = prob_threshold_host(0.001f);
+    if (mdl->kind == kExplicit && g->m > 0) {
+        DBuf w;
+        CKS(dalloc(c, (size_t)g->m * sizeof(float), w));
+        cudaError_t e = cudaMemcpyAsync(w.p, mdl->w, (size_t)g->m * sizeof(float),
+                                        cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) {
+            if (!g->thr_out.p) {
+                im_status s = dalloc(c, (size_t)g->m * 4, g->thr_out);
+                if (s != IM_OK) { dfree(c, w); return s; }
+            }
+            e = launch_thr_explicit(w.as<float>(), g->m, g->thr_out.as<uint32_t>(), c->stream);
+        }
+        dfree(c, w);
+        if (e != cudaSuccess) return cuda_fail(c, e, "explicit thresholds");
+    }
+    return IM_OK;
+}
+
+extern "C" im_status im_graph_load(im_ctx* c, int32_t n, int64_t m, const int32_t* rowptr,
+                                   const int32_t* col, const im_model* model, im_graph** out) {
+    if (!c || !out || !rowptr || (m > 0 && !col)) return fail(c, IM_E_INVAL, "NULL argument");
+    if (n < 1 || n >= (1 << 26)) return fail(c, IM_E_RANGE, "n must be in [1, 2^26)");
+    if (m < 0 || m >= (1ll << 31)) return fail(c, IM_E_RANGE, "m must be in [0, 2^31)");
+    CKS(check_model(c, model, m));
+    if (rowptr[0] != 0 || rowptr[n] != m) return fail(c, IM_E_INVAL, "rowptr[0] != 0 or rowptr[n] != m");
+    for (int32_t u = 0; u < n; ++u) {
+        const int32_t b = rowptr[u], e = rowptr[u + 1];
+        if (e < b) return fail(c, IM_E_INVAL, "rowptr decreases at %d", u);
+        for (int32_t i = b; i < e; ++i) {
+            const int32_t v = col[i];
+            if (v < 0 || v >= n) return fail(c, IM_E_RANGE, "col[%d] = %d out of range", i, v);
+            if (v == u) return fail(c, IM_E_INVAL, "self-loop at vertex %d", u);
+            if (i > b && col[i - 1] >= v)
+                return fail(c, IM_E_INVAL, "row %d not strictly ascending (duplicate edge?)", u);
+        }
+    }
+    CK(c, cudaSetDevice(c->device));
+    im_graph* g = new im_graph();
+    g->ctx = c;
+    g->n = n;
+    g->m = m;
+    auto bail = [&](im_status s) {
+        graph_release(g);
+        delete g;
+        return s;
+    };
+    im_status s;
+    const size_t rp_bytes = ((size_t)n + 1) * 4, e_bytes = (size_t)(m > 0 ? m : 1) * 4;
+    if ((s = dalloc(c, rp_bytes, g->rp_out)) != IM_OK) return bail(s);
+    if ((s = dalloc(c, e_bytes, g->col_out)) != IM_OK) return bail(s);
+    if ((s = dalloc(c, rp_bytes, g->rp_in)) != IM_OK) return bail(s);
+    if ((s = dalloc(c, e_bytes, g->src_in)) != IM_OK) return bail(s);
+    if ((s = dalloc(c, (size_t)n * 4, g->thr_v)) != IM_OK) return bail(s);
+    if ((s = dalloc(c, (size_t)n * sizeof(QEntry), g->q_all)) != IM_OK) return bail(s);
+    if ((s = dalloc(c, 8, g->ctr_all)) != IM_OK) return bail(s);
+    DBuf cnt, tmp, fill;
+    if ((s = dalloc(c, ((size_t)n + 1) * 4, cnt)) != IM_OK) return bail(s);
+    if ((s = dalloc(c, scan_tmp_bytes(n), tmp)) != IM_OK) { dfree(c, cnt); return bail(s); }
+    if ((s = dalloc(c, ((size_t)n + 1) * 4, fill)) != IM_OK) { dfree(c, cnt); dfree(c, tmp); return bail(s); }
+    auto st = c->stream;
+    cudaError_t e = cudaMemcpyAsync(g->rp_out.p, rowptr, rp_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && m > 0)
+        e = cudaMemcpyAsync(g->col_out.p, col, (size_t)m * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt.p, 0, ((size_t)n + 1) * 4, st);
+    if (e == cudaSuccess) e = launch_indegree(g->col_out.as<int32_t>(), m, cnt.as<int32_t>(), st);
+    if (e == cudaSuccess) e = launch_exclusive_scan(cnt.as<int32_t>(), n, g->rp_in.as<int32_t>(), tmp.p, st);
+    if (e == cudaSuccess) e = launch_thr_wc(g->rp_in.as<int32_t>(), n, g->thr_v.as<uint32_t>(), st);
+    if (e != cudaSuccess) { dfree(c, cnt); dfree(c, tmp); dfree(c, fill); return bail(cuda_fail(c, e, "graph load")); }
+    if ((s = set_model(g, model)) != IM_OK) { dfree(c, cnt); dfree(c, tmp); dfree(c, fill); return bail(s); }
+    if (g->kind == kExplicit && m > 0) {
+        if ((s = dalloc(c, (size_t)m * 4, g->thr_in)) != IM_OK) { dfree(c, cnt); dfree(c, tmp); dfree(c, fill); return bail(s); }
+    }
+    e = cudaMemsetAsync(fill.p, 0, ((size_t)n + 1) * 4, st);
+    if (e == cudaSuccess)
+        e = launch_scatter_in(g->rp_out.as<int32_t>(), g->col_out.as<int32_t>(), n, g->rp_in.as<int32_t>(),
+                              fill.as<int32_t>(), g->src_in.as<int32_t>(), g->thr_out.as<uint32_t>(),
+                              g->thr_in.as<uint32_t>(), st);
+    // all-vertex queue: entries for vertices with in-edges, in id order
+    if (e == cudaSuccess) e = launch_flag_nonzero_in(g->rp_in.as<int32_t>(), n, cnt.as<int32_t>(), st);
+    if (e == cudaSuccess) e = launch_exclusive_scan(cnt.as<int32_t>(), n, fill.as<int32_t>(), tmp.p, st);
+    if (e == cudaSuccess)
+        e = launch_all_queue(g->rp_in.as<int32_t>(), n, g->thr_v.as<uint32_t>(), fill.as<int32_t>(),
+                             g->q_all.as<QEntry>(), st);
+    int32_t nq = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nq, fill.as<int32_t>() + n, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) {
+        const unsigned long long ctr = ((unsigned long long)nq << kCountShift) | (unsigned long long)m;
+        e = cudaMemcpyAsync(g->ctr_all.p, &ctr, 8, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    dfree(c, cnt);
+    dfree(c, tmp);
+    dfree(c, fill);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "graph load"));
+    g->dev.n = n;
+    g->dev.m = m;
+    g->dev.rp_out = g->rp_out.as<int32_t>();
+    g->dev.col_out = g->col_out.as<int32_t>();
+    g->dev.rp_in = g->rp_in.as<int32_t>();
+    g->dev.src_in = g->src_in.as<int32_t>();
+    g->dev.thr_v = g->thr_v.as<uint32_t>();
+    g->dev.thr_out = g->thr_out.as<uint32_t>();
+    g->dev.thr_in = g->thr_in.as<uint32_t>();
+    *out = g;
+    return IM_OK;
+}
+
+extern "C" void im_graph_free(im_graph* g) {
+    if (!g) return;
+    graph_release(g);
+    delete g;
+}
+
+extern "C" im_status im_graph_info(const im_graph* g, int32_t* n, int64_t* m) {
+    if (!g) return IM_E_INVAL;
+    if (n) *n = g->n;
+    if (m) *m = g->m;
+    return IM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// sketches
+// ---------------------------------------------------------------------------
+static void sketch_release(im_sketch* sk) {
+    im_ctx* c = sk->g->ctx;
+    for (DBuf* b : {&sk->M, &sk->X, &sk->salt, &sk->tab, &sk->q[0], &sk->q[1], &sk->q[2], &sk->ctr,
+                    &sk->gen, &sk->seed_bits, &sk->count, &sk->part_S, &sk->part_u, &sk->ticket,
+                    &sk->stats, &sk->err, &sk->out_seed, &sk->out_S, &sk->out_est})
+        dfree(c, *b);
+}
+
+static im_status sketch_alloc(im_graph* g, int32_t J, im_sketch** out) {
+    im_ctx* c = g->ctx;
+    if (!valid_J(J)) return fail(c, IM_E_INVAL, "J must be a power of two in [16, 1024], got %d", J);
+    im_sketch* sk = new im_sketch();
+    sk->g = g;
+    sk->J = J;
+    const int32_t n = g->n;
+    const int pg = pick_grid(n, J);
+    im_status s = IM_OK;
+    auto A = [&](DBuf& b, size_t bytes) {
+        if (s == IM_OK) s = dalloc(c, bytes, b);
+    };
+    A(sk->M, (size_t)n * J);
+    A(sk->X, (size_t)J * 4);
+    A(sk->salt, (size_t)J * 4);
+    A(sk->tab, (size_t)kTabSize * 2);
+    for (int i = 0; i < 3; ++i) A(sk->q[i], (size_t)n * sizeof(QEntry));
+    A(sk->ctr, (size_t)(kMaxLevels + 2) * 8);
+    A(sk->gen, (size_t)n * 4);
+    A(sk->seed_bits, (((size_t)n + 31) / 32) * 4);
+    A(sk->count, 8);
+    A(sk->part_S, (size_t)pg * 8);
+    A(sk->part_u, (size_t)pg * 4);
+    A(sk->ticket, 4);
+    A(sk->stats, (size_t)kStCount * 8);
+    A(sk->err, 4);
+    if (s != IM_OK) {
+        sketch_release(sk);
+        delete sk;
+        return s;
+    }
+    auto st = c->stream;
+    cudaError_t e = cudaMemsetAsync(sk->gen.p, 0, sk->gen.bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sk->seed_bits.p, 0, sk->seed_bits.bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sk->count.p, 0, 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sk->ticket.p, 0, 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sk->stats.p, 0, sk->stats.bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sk->err.p, 0, 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sk->M.p, 0, sk->M.bytes, st);
+    if (e != cudaSuccess) {
+        sketch_release(sk);
+        delete sk;
+        return cuda_fail(c, e, "sketch init");
+    }
+    *out = sk;
+    return IM_OK;
+}
+
+static im_status ensure_out_cap(im_sketch* sk, int32_t K) {
+    if (K <= sk->out_cap) return IM_OK;
+    im_ctx* c = sk->g->ctx;
+    const int32_t cap = K < 64 ? 64 : K;
+    DBuf a, b, d;
+    CKS(dalloc(c, (size_t)cap * 4, a));
+    im_status s = dalloc(c, (size_t)cap * 8, b);
+    if (s == IM_OK) s = dalloc(c, (size_t)cap * 8, d);
+    if (s != IM_OK) { dfree(c, a); dfree(c, b); return s; }
+    dfree(c, sk->out_seed);
+    dfree(c, sk->out_S);
+    dfree(c, sk->out_est);
+    sk->out_seed = a;
+    sk->out_S = b;
+    sk->out_est = d;
+    sk->out_cap = cap;
+    return IM_OK;
+}
+
+static FrontierArgs frontier_args(im_sketch* sk) {
+    FrontierArgs a{};
+    a.M = sk->M.as<uint8_t>();
+    a.J = sk->J;
+    a.X = sk->X.as<uint32_t>();
+    a.tab = sk->tab.as<uint16_t>();
+    a.gen = sk->gen.as<int32_t>();
+    a.count = sk->count.as<unsigned long long>();
+    a.stats = sk->stats.as<unsigned long long>();
+    a.err = sk->err.as<uint32_t>();
+    return a;
+}
+
+// Reads the device error word; converts raised bits to a status.
+static im_status check_err(im_sketch* sk) {
+    im_ctx* c = sk->g->ctx;
+    uint32_t err = 0;
+    CK(c, cudaMemcpyAsync(&err, sk->err.p, 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (err & kErrQueue) return fail(c, IM_E_STATE, "frontier queue overflow");
+    if (err & kErrCasLimit) return fail(c, IM_E_TIMEOUT, "register CAS retry limit exceeded");
+    return IM_OK;
+}
+
+
+// Runs frontier levels until the queue is empty.  Level t reads (q_in, ctr_in)
+// and writes queue q[t & 1] and counter ctr[t + 1].  The host reads the newest
+// counter every `check` levels (2, 4, then 8); levels launched after the
+// queue emptied see an empty queue and return at once.
+static im_status run_levels(im_sketch* sk, int mode, const QEntry* q0,
+                            const unsigned long long* c0) {
+    im_graph* g = sk->g;
+    im_ctx* c = g->ctx;
+    auto st = c->stream;
+    unsigned long long* ctr = sk->ctr.as<unsigned long long>();
+    CK(c, cudaMemsetAsync(ctr + 1, 0, (size_t)(kMaxLevels + 1) * 8, st));
+    FrontierArgs a = frontier_args(sk);
+    const int grid = frontier_grid();
+    const QEntry* qin = q0;
+    const unsigned long long* cin = c0;
+    int check = 2;
+    int64_t t = 0;
+    for (;;) {
+        a.q_in = qin;
+        a.ctr_in = cin;
+        a.q_out = sk->q[t & 1].as<QEntry>();
+        a.ctr_out = ctr + t + 1;
+        a.gen_next = ++sk->gen_counter;
+        CK(c, timed(c, mode == kPush ? kTPush : kTCover,
+                    [&] { return launch_frontier(g->kind, mode, g->dev, a, grid, st); }));
+        qin = a.q_out;
+        cin = a.ctr_out;
+        ++t;
+        if (t % check == 0) {
+            CK(c, cudaMemcpyAsync(c->pinned, ctr + t, 8, cudaMemcpyDeviceToHost, st));
+            CK(c, sync_collect(c));
+            if ((c->pinned[0] >> kCountShift) == 0) break;
+            if (t + 8 >= kMaxLevels)
+                return fail(c, IM_E_TIMEOUT, "frontier did not empty within %d levels", kMaxLevels);
+            if (check < 8) check *= 2;
+        }
+    }
+    return check_err(sk);
+}
+
+static im_status propagate(im_sketch* sk) {
+    im_graph* g = sk->g;
+    return run_levels(sk, kPush, g->q_all.as<QEntry>(), g->ctr_all.as<unsigned long long>());
+}
+
+// Fill (Alg. 1) of the non-visited registers, then Simulate to the fixpoint.
+static im_status build_registers(im_sketch* sk) {
+    im_ctx* c = sk->g->ctx;
+    CK(c, timed(c, kTFill, [&] {
+        return launch_fill(sk->M.as<uint8_t>(), sk->g->n, sk->J, sk->salt.as<uint32_t>(), c->stream);
+    }));
+    return propagate(sk);
+}
+
+static void stats_begin(im_ctx* c) {
+    memset(&c->stats, 0, sizeof c->stats);
+    c->ev_used = 0;
+}
+
+static im_status stats_collect(im_sketch* sk) {
+    im_ctx* c = sk->g->ctx;
+    unsigned long long h[kStCount];
+    unsigned long long cnt = 0;
+    CK(c, cudaMemcpyAsync(h, sk->stats.p, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(&cnt, sk->count.p, 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, sync_collect(c));
+    im_stats& s = c->stats;
+    s.sweeps = (int64_t)h[kStSweepLevels];
+    s.cover_levels = (int64_t)h[kStCoverLevels];
+    s.sweep_vertices = h[kStSweepVertices];
+    s.sweep_edges = h[kStSweepEdges];
+    s.sweep_chunks = h[kStSweepChunks];
+    s.sweep_cas = h[kStSweepCas];
+    s.sweep_changed = h[kStSweepChanged];
+    s.cover_edges = h[kStCoverEdges];
+    s.cover_chunks = h[kStCoverChunks];
+    s.visited = cnt;
+    // algorithmic bytes of the sweeps: queue entry (16 B) + the queued vertex's
+    // register row (J B) per queued vertex, source id (4 B, + 4 B threshold for
+    // explicit weights) per in-edge, one 16-byte target chunk read per chunk
+    // with a live non-visited source register, one 4-byte word per CAS write
+    const uint64_t t = sk->g->kind == kExplicit ? 4 : 0;
+    s.alg_bytes_sweep = s.sweep_vertices * (16 + (uint64_t)sk->J) + s.sweep_edges * (4 + t) +
+                        s.sweep_chunks * 16 + s.sweep_cas * 4;
+    return IM_OK;
+}
+
+static im_status sketch_start(im_graph* g, int32_t J, uint64_t seed, im_sketch** out) {
+    im_ctx* c = g->ctx;
+    CK(c, cudaSetDevice(c->device));
+    im_sketch* sk = nullptr;
+    CKS(sketch_alloc(g, J, &sk));
+    cudaError_t e = timed(c, kTOther, [&] {
+        return launch_sims(seed, J, sk->X.as<uint32_t>(), sk->salt.as<uint32_t>(),
+                           sk->tab.as<uint16_t>(), c->stream);
+    });
+    if (e != cudaSuccess) {
+        sketch_release(sk);
+        delete sk;
+        return cuda_fail(c, e, "launch_sims");
+    }
+    *out = sk;
+    return IM_OK;
+}
+
+extern "C" im_status im_sketch_build(im_graph* g, int32_t J, uint64_t seed, im_sketch** out) {
+    if (!g || !out) return IM_E_INVAL;
+    im_ctx* c = g->ctx;
+    stats_begin(c);
+    const double t0 = now_ms();
+    im_sketch* sk = nullptr;
+    CKS(sketch_start(g, J, seed, &sk));
+    im_status s = build_registers(sk);
+    if (s == IM_OK) s = stats_collect(sk);
+    if (s != IM_OK) {
+        sketch_release(sk);
+        delete sk;
+        return s;
+    }
+    c->stats.builds = 1;
+    c->stats.ms_build = c->stats.ms_total = now_ms() - t0;
+    *out = sk;
+    return IM_OK;
+}
+
+extern "C" void im_sketch_free(im_sketch* sk) {
+    if (!sk) return;
+    sketch_release(sk);
+    delete sk;
+}
+
+extern "C" im_status im_sketch_registers(const im_sketch* sk, uint8_t* host_out) {
+    if (!sk || !host_out) return IM_E_INVAL;
+    im_ctx* c = sk->g->ctx;
+    CK(c, cudaMemcpyAsync(host_out, sk->M.p, (size_t)sk->g->n * sk->J, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return IM_OK;
+}
+
+extern "C" im_status im_sketch_set_registers(im_sketch* sk, const uint8_t* host_in) {
+    if (!sk || !host_in) return IM_E_INVAL;
+    im_ctx* c = sk->g->ctx;
+    const size_t bytes = (size_t)sk->g->n * sk->J;
+    for (size_t i = 0; i < bytes; ++i)
+        if (host_in[i] > 32 && host_in[i] != 0xFF)
+            return fail(c, IM_E_INVAL, "register byte %zu = %u is neither a rank nor 0xFF", i, host_in[i]);
+    CK(c, cudaMemcpyAsync(sk->M.p, host_in, bytes, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemsetAsync(sk->count.p, 0, 8, c->stream));
+    CK(c, launch_count_visited(sk->M.as<uint8_t>(), (int64_t)bytes, sk->count.as<unsigned long long>(), c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return IM_OK;
+}
+
+extern "C" im_status im_sketch_sims(const im_sketch* sk, uint32_t* X_out, uint32_t* salt_out) {
+    if (!sk) return IM_E_INVAL;
+    im_ctx* c = sk->g->ctx;
+    if (X_out) CK(c, cudaMemcpyAsync(X_out, sk->X.p, (size_t)sk->J * 4, cudaMemcpyDeviceToHost, c->stream));
+    if (salt_out) CK(c, cudaMemcpyAsync(salt_out, sk->salt.p, (size_t)sk->J * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return IM_OK;
+}
+
+extern "C" im_status im_sketch_sums(const im_sketch* sk, uint64_t* host_out) {
+    if (!sk || !host_out) return IM_E_INVAL;
+    im_ctx* c = sk->g->ctx;
+    DBuf S;
+    CKS(dalloc(c, (size_t)sk->g->n * 8, S));
+    cudaError_t e = launch_sums(sk->M.as<uint8_t>(), sk->g->n, sk->J, S.as<unsigned long long>(), c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host_out, S.p, (size_t)sk->g->n * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dfree(c, S);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sketch sums");
+    return IM_OK;
+}
+
+static PickArgs pick_args(im_sketch* sk, int k) {
+    PickArgs a{};
+    a.M = sk->M.as<uint8_t>();
+    a.J = sk->J;
+    a.n = sk->g->n;
+    a.seed_bits = sk->seed_bits.as<uint32_t>();
+    a.part_S = sk->part_S.as<unsigned long long>();
+    a.part_u = sk->part_u.as<int32_t>();
+    a.ticket = sk->ticket.as<unsigned int>();
+    a.out_seed = sk->out_seed.as<int32_t>();
+    a.out_S = sk->out_S.as<unsigned long long>();
+    a.out_est = sk->out_est.as<double>();
+    a.k = k;
+    a.rp_out = sk->g->rp_out.as<int32_t>();
+    a.q_cover = sk->q[2].as<QEntry>();
+    a.ctr_cover = sk->ctr.as<unsigned long long>();
+    a.count = sk->count.as<unsigned long long>();
+    a.mark = 1;
+    return a;
+}
+
+// Pick (estimate + argmax) followed by the cover of the picked vertex.
+static im_status pick_and_cover(im_sketch* sk, int k) {
+    im_ctx* c = sk->g->ctx;
+    const PickArgs a = pick_args(sk, k);
+    CK(c, timed(c, kTPick, [&] { return launch_pick(a, c->stream); }));
+    return run_levels(sk, kCover, sk->q[2].as<QEntry>(), sk->ctr.as<unsigned long long>());
+}
+
+extern "C" im_status im_sketch_pick(im_sketch* sk, int32_t* s_out, uint64_t* S_out, double* est_out) {
+    if (!sk) return IM_E_INVAL;
+    im_ctx* c = sk->g->ctx;
+    if (sk->picks >= sk->g->n) return fail(c, IM_E_RANGE, "every vertex is already picked");
+    CKS(ensure_out_cap(sk, sk->picks + 1));
+    PickArgs a = pick_args(sk, sk->picks);
+    a.mark = 0;  // record the pick only; the caller covers with im_sketch_cover
+    CK(c, launch_pick(a, c->stream));
+    int32_t s = -1;
+    unsigned long long S = 0;
+    double est = 0;
+    CK(c, cudaMemcpyAsync(&s, a.out_seed + a.k, 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(&S, a.out_S + a.k, 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(&est, a.out_est + a.k, 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (s < 0) return fail(c, IM_E_RANGE, "no vertex left to pick");
+    sk->picks++;
+    if (s_out) *s_out = s;
+    if (S_out) *S_out = S;
+    if (est_out) *est_out = est;
+    return IM_OK;
+}
+
+extern "C" im_status im_sketch_cover(im_sketch* sk, int32_t s, uint64_t* count_out) {
+    if (!sk) return IM_E_INVAL;
+    im_ctx* c = sk->g->ctx;
+    if (s < 0 || s >= sk->g->n) return fail(c, IM_E_RANGE, "vertex %d out of range", s);
+    unsigned long long* ctr = sk->ctr.as<unsigned long long>();
+    CK(c, launch_cover_seed(sk->M.as<uint8_t>(), sk->J, s, sk->g->rp_out.as<int32_t>(),
+                            sk->q[2].as<QEntry>(), ctr, sk->count.as<unsigned long long>(), c->stream));
+    CKS(run_levels(sk, kCover, sk->q[2].as<QEntry>(), ctr));
+    if (count_out) {
+        unsigned long long cnt = 0;
+        CK(c, cudaMemcpyAsync(&cnt, sk->count.p, 8, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        *count_out = cnt;
+    }
+    return IM_OK;
+}
+
+extern "C" im_status im_sketch_rebuild(im_sketch* sk) {
+    if (!sk) return IM_E_INVAL;
+    return build_registers(sk);
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 4
+// ---------------------------------------------------------------------------
+extern "C" im_status im_select_seeds(im_graph* g, int32_t K, int32_t J, const im_model* model,
+                                     uint64_t seed, double rebuild_eps, int32_t* seeds_out,
+                                     double* score_out, double* estimate_out, im_sketch** sketch_out) {
+    if (!g || !seeds_out) return IM_E_INVAL;
+    im_ctx* c = g->ctx;
+    if (K < 1 || K > g->n) return fail(c, IM_E_RANGE, "K must be in [1, n], got %d", K);
+    if (!valid_J(J)) return fail(c, IM_E_INVAL, "J must be a power of two in [16, 1024], got %d", J);
+    // a per-call model override changes the graph's model words for this call only
+    struct ModelGuard {
+        im_graph* g;
+        GraphDev dev;
+        int kind;
+        ~ModelGuard() { g->dev = dev; g->kind = kind; }
+    } guard{g, g->dev, g->kind};
+    if (model) {
+        CKS(check_model(c, model, g->m));
+        if (model->kind == kExplicit || g->kind == kExplicit)
+            return fail(c, IM_E_STATE, "an explicit-weight model must be given at im_graph_load");
+        CKS(set_model(g, model));
+    }
+    stats_begin(c);
+    const double t0 = now_ms();
+    im_sketch* sk = nullptr;
+    CKS(sketch_start(g, J, seed, &sk));
+    auto bail = [&](im_status s) {
+        sketch_release(sk);
+        delete sk;
+        return s;
+    };
+    im_status s = ensure_out_cap(sk, K);
+    if (s != IM_OK) return bail(s);
+    if ((s = build_registers(sk)) != IM_OK) return bail(s);
+    const double t_build = now_ms();
+    c->stats.ms_build = t_build - t0;
+    std::vector<double> score(K);
+    uint64_t oldcount = 0;
+    int64_t rebuilds = 0;
+    double ms_rebuild = 0, ms_pc = 0;
+    for (int32_t k = 0; k < K; ++k) {
+        const double tk = now_ms();
+        if ((s = pick_and_cover(sk, k)) != IM_OK) return bail(s);
+        cudaError_t e = cudaMemcpyAsync(c->pinned, sk->count.p, 8, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = sync_collect(c);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "read count"));
+        const uint64_t count = c->pinned[0];
+        score[k] = (double)count / (double)J;
+        const double tr = now_ms();
+        ms_pc += tr - tk;
+        if (k + 1 < K && rebuild_due(count, oldcount, J, rebuild_eps)) {
+            if ((s = build_registers(sk)) != IM_OK) return bail(s);
+            oldcount = count;
+            ++rebuilds;
+            ms_rebuild += now_ms() - tr;
+        }
+    }
+    sk->picks = K;
+    std::vector<int32_t> seeds(K);
+    std::vector<double> est(K);
+    cudaError_t e = cudaMemcpyAsync(seeds.data(), sk->out_seed.p, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(est.data(), sk->out_est.p, (size_t)K * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "read seeds"));
+    if ((s = stats_collect(sk)) != IM_OK) return bail(s);
+    c->stats.builds = 1 + rebuilds;
+    c->stats.ms_rebuild = ms_rebuild;
+    c->stats.ms_pick = ms_pc;
+    c->stats.ms_total = now_ms() - t0;
+    memcpy(seeds_out, seeds.data(), (size_t)K * 4);
+    if (score_out) memcpy(score_out, score.data(), (size_t)K * 8);
+    if (estimate_out) memcpy(estimate_out, est.data(), (size_t)K * 8);
+    if (sketch_out) *sketch_out = sk;
+    else bail(IM_OK);
+    return IM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Monte-Carlo spread with independent coins (Sec. 5.1 quality oracle)
+// ---------------------------------------------------------------------------
+extern "C" im_status im_spread_mc(im_graph* g, const int32_t* seeds, int32_t k, int64_t R,
+                                  uint64_t seed, double* mean_out, double* stderr_out,
+                                  uint64_t* sum_out, uint64_t* sumsq_out) {
+    if (!g || !seeds) return IM_E_INVAL;
+    im_ctx* c = g->ctx;
+    if (k < 1) return fail(c, IM_E_RANGE, "k must be >= 1");
+    if (R < 2) return fail(c, IM_E_RANGE, "R must be >= 2");
+    for (int32_t i = 0; i < k; ++i)
+        if (seeds[i] < 0 || seeds[i] >= g->n) return fail(c, IM_E_RANGE, "seed %d out of range", seeds[i]);
+    CK(c, cudaSetDevice(c->device));
+    const int32_t n = g->n;
+    int B = 32;
+    while (B < 1024 && B < R) B <<= 1;
+    const int words = B / 32;
+    DBuf vis, F[3], Q[3], ctr, gen, reach, acc, sd;
+    std::vector<DBuf*> all = {&vis, &F[0], &F[1], &F[2], &Q[0], &Q[1], &Q[2], &ctr, &gen, &reach, &acc, &sd};
+    auto release = [&]() {
+        for (DBuf* b : all) dfree(c, *b);
+    };
+    im_status s = IM_OK;
+    const size_t vbytes = (size_t)n * words * 4;
+    for (DBuf* b : {&vis, &F[0], &F[1], &F[2]})
+        if (s == IM_OK) s = dalloc(c, vbytes, *b);
+    for (int i = 0; i < 3 && s == IM_OK; ++i) s = dalloc(c, (size_t)n * sizeof(QEntry), Q[i]);
+    if (s == IM_OK) s = dalloc(c, (size_t)(kMaxLevels + 2) * 8, ctr);
+    if (s == IM_OK) s = dalloc(c, (size_t)n * 4, gen);
+    if (s == IM_OK) s = dalloc(c, (size_t)1024 * 8, reach);
+    if (s == IM_OK) s = dalloc(c, 16, acc);
+    if (s == IM_OK) s = dalloc(c, (size_t)k * 4, sd);
+    if (s != IM_OK) { release(); return s; }
+    auto st = c->stream;
+    cudaError_t e = cudaMemcpyAsync(sd.p, seeds, (size_t)k * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(gen.p, 0, gen.bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(acc.p, 0, 16, st);
+    if (e != cudaSuccess) { release(); return cuda_fail(c, e, "spread init"); }
+    unsigned long long* cp = ctr.as<unsigned long long>();
+    const int grid = frontier_grid();
+    int32_t stamp = 0;
+    for (int64_t r0 = 0; r0 < R; r0 += B) {
+        const int valid = (int)std::min<int64_t>(B, R - r0);
+        for (DBuf* b : {&vis, &F[0], &F[1], &F[2]})
+            if (e == cudaSuccess) e = cudaMemsetAsync(b->p, 0, vbytes, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(reach.p, 0, reach.bytes, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(cp, 0, (size_t)(kMaxLevels + 2) * 8, st);
+        McArgs a{};
+        a.n = n;
+        a.m = g->m;
+        a.seed = seed;
+        a.r0 = r0;
+        a.words = words;
+        a.vis = vis.as<uint32_t>();
+        a.gen = gen.as<int32_t>();
+        a.f_next = F[0].as<uint32_t>();
+        a.q_out = Q[0].as<QEntry>();
+        a.ctr_out = cp;
+        a.gen_next = ++stamp;
+        if (e == cudaSuccess) e = launch_mc_seed(g->dev, a, sd.as<int32_t>(), k, valid, st);
+        int check = 2;
+        for (int64_t l = 0; e == cudaSuccess; ) {
+            a.f_cur = F[l % 3].as<uint32_t>();
+            a.f_next = F[(l + 1) % 3].as<uint32_t>();
+            a.f_prev = F[(l + 2) % 3].as<uint32_t>();
+            a.q_in = Q[l % 3].as<QEntry>();
+            a.ctr_in = cp + l;
+            a.q_prev = l >= 1 ? Q[(l + 2) % 3].as<QEntry>() : nullptr;
+            a.ctr_prev = l >= 1 ? cp + l - 1 : nullptr;
+            a.q_out = Q[(l + 1) % 3].as<QEntry>();
+            a.ctr_out = cp + l + 1;
+            a.gen_next = ++stamp;
+            e = launch_mc_level(g->kind, g->dev, a, grid, st);
+            ++l;
+            if (e == cudaSuccess && l % check == 0) {
+                e = cudaMemcpyAsync(c->pinned, cp + l, 8, cudaMemcpyDeviceToHost, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                if (e != cudaSuccess) break;
+                if ((c->pinned[0] >> kCountShift) == 0) break;
+                if (l + 8 >= kMaxLevels) { release(); return fail(c, IM_E_TIMEOUT, "spread did not converge"); }
+                if (check < 8) check *= 2;
+            }
+        }
+        if (e == cudaSuccess) e = launch_mc_count(vis.as<uint32_t>(), n, words, reach.as<unsigned long long>(), st);
+        if (e == cudaSuccess) e = launch_mc_reduce(reach.as<unsigned long long>(), valid, acc.as<unsigned long long>(), st);
+        if (e != cudaSuccess) break;
+    }
+    unsigned long long h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, acc.p, 16, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    release();
+    if (e != cudaSuccess) return cuda_fail(c, e, "spread");
+    const double mean = (double)h[0] / (double)R;
+    const long double var = ((long double)h[1] - (long double)h[0] * (long double)h[0] / (long double)R) /
+                            (long double)(R - 1);
+    if (mean_out) *mean_out = mean;
+    if (stderr_out) *stderr_out = std::sqrt((double)(var > 0 ? var : 0) / (double)R);
+    if (sum_out) *sum_out = h[0];
+    if (sumsq_out) *sumsq_out = h[1];
+    return IM_OK;
+}

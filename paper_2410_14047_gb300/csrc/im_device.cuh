@@ -1,0 +1,188 @@
+// Device-side building blocks of the sketch-based IM hot path (sm_103a).
+//
+// Hashes (Sec. 2.2 Eq. hash, Sec. 2.3 Eq. sketch-init), the fused-sampling
+// live test (Eq. hash_prob), the per-simulation random draws (Sec. 2.2) and
+// the byte-level register operations (Eq. sketch-merge with the visited
+// marker of Sec. 3.1).  Written for this library from the published
+// definitions of MurmurHash3_x86_32 and SplitMix64.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace im {
+
+constexpr uint32_t kVisited = 0xFFu;
+constexpr int kMaxJ = 1024;
+constexpr int kTabBits = 12;                   // range table resolution (top bits of X)
+constexpr int kTabSize = (1 << kTabBits) + 1;  // 4097 entries
+constexpr int kCountShift = 38;                // packed queue counter: count << 38 | edges
+constexpr uint64_t kEdgeMask = (1ull << kCountShift) - 1;
+constexpr int kMaxLevels = 16384;              // propagation sweeps / cover levels per phase
+constexpr int kCasRetryLimit = 4096;
+
+enum ModelKind : int { kUniform = 0, kWC = 1, kTrivalency = 2, kExplicit = 3 };
+
+// Error bits a kernel may raise (host turns them into IM_E_* codes).
+enum : uint32_t { kErrCasLimit = 1u, kErrQueue = 2u };
+
+// Device view of a loaded graph.
+struct GraphDev {
+    int32_t n;
+    int64_t m;
+    const int32_t* rp_out;   // n+1, out-CSR row pointers
+    const int32_t* col_out;  // m, out-neighbours
+    const int32_t* rp_in;    // n+1, in-CSR row pointers
+    const int32_t* src_in;   // m, in-neighbours (sources of in-edges)
+    const uint32_t* thr_v;   // kWC: threshold of every edge into v
+    const uint32_t* thr_out; // kExplicit: per out-edge threshold
+    const uint32_t* thr_in;  // kExplicit: per in-edge threshold
+    uint32_t thr_uniform;    // kUniform
+    uint32_t tri_seed;       // kTrivalency class-hash seed
+    uint32_t tri_thr[3];     // kTrivalency thresholds of the three classes
+};
+
+// Work-queue entry: a vertex, the start of its edge row in the CSR the phase
+// walks, its offset in the phase's flat edge space, and a model word (the
+// weighted-cascade threshold of its in-edges for propagation sweeps).
+struct __align__(16) QEntry {
+    int32_t v;
+    int32_t rp;
+    int32_t off;
+    uint32_t aux;
+};
+
+// ---------------------------------------------------------------------------
+// MurmurHash3_x86_32 pieces (public-domain algorithm by A. Appleby).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t rotl32(uint32_t x, int r) { return __funnelshift_l(x, x, r); }
+
+__device__ __forceinline__ uint32_t mm3_k(uint32_t k) {
+    k *= 0xcc9e2d51u;
+    k = rotl32(k, 15);
+    return k * 0x1b873593u;
+}
+
+__device__ __forceinline__ uint32_t mm3_h(uint32_t h, uint32_t k) {
+    h ^= k;
+    h = rotl32(h, 13);
+    return h * 5u + 0xe6546b64u;
+}
+
+__device__ __forceinline__ uint32_t mm3_final(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    return h ^ (h >> 16);
+}
+
+// Hash of the 8-byte key LE32(a) || LE32(b) (the GPU is little-endian, so a
+// 4-byte block read of LE32(a) is a itself).
+__device__ __forceinline__ uint32_t hash_pair(uint32_t a, uint32_t b, uint32_t seed) {
+    return mm3_final(mm3_h(mm3_h(seed, mm3_k(a)), mm3_k(b)) ^ 8u);
+}
+
+// Eq. (hash): h(u,v) = Murmur3(u || v) mod 2^31.
+__device__ __forceinline__ uint32_t edge_hash(uint32_t u, uint32_t v) {
+    return hash_pair(u, v, 0u) & 0x7FFFFFFFu;
+}
+
+// Eq. (sketch-init): rank = clz(h_j(u)), h_j = Murmur3 of the 4-byte key u with
+// seed salt_j.  `ku` = mm3_k(u), shared by all simulations of a vertex.
+__device__ __forceinline__ uint32_t rank_of(uint32_t ku, uint32_t salt) {
+    return (uint32_t)__clz((int)mm3_final(mm3_h(salt, ku) ^ 4u));
+}
+
+// SplitMix64 output number k (0-based) of the stream started at `seed`
+// (Steele, Lea, Flood 2014).
+__device__ __forceinline__ uint64_t splitmix_at(uint64_t seed, uint64_t k) {
+    uint64_t z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// ---------------------------------------------------------------------------
+// Edge thresholds of the diffusion models (Sec. 2.1), fixed point of Eq. hash_prob.
+// `e` is the edge's index in the CSR the caller walks (out- or in-CSR).
+// ---------------------------------------------------------------------------
+template <int KIND, bool IN_ORIENTATION>
+__device__ __forceinline__ uint32_t edge_threshold(const GraphDev& g, uint32_t u, uint32_t v,
+                                                   int64_t e, uint32_t aux) {
+    if constexpr (KIND == kUniform) {
+        return g.thr_uniform;
+    } else if constexpr (KIND == kWC) {
+        if constexpr (IN_ORIENTATION) return aux;  // threshold of the queue vertex's in-edges
+        else return __ldg(g.thr_v + v);
+    } else if constexpr (KIND == kTrivalency) {
+        const uint32_t cls = hash_pair(u, v, g.tri_seed) % 3u;
+        return cls == 0u ? g.tri_thr[0] : (cls == 1u ? g.tri_thr[1] : g.tri_thr[2]);
+    } else {
+        if constexpr (IN_ORIENTATION) return __ldg(g.thr_in + e);
+        else return __ldg(g.thr_out + e);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Candidate simulations of an edge.  With X sorted ascending (Sec. 4.1), the
+// simulations in which an edge of hash h and threshold thr can be live form
+// one contiguous index range: (X_j ^ h) < thr < 2^(t+1), t = msb(thr), forces
+// X_j and h to agree on every bit above t, and the X_j with a given prefix
+// are consecutive.  The range is a superset of the live simulations (at
+// least half of it is live in expectation); the live test is still applied
+// to every simulation in it.  sTab[b] = #{j : X_j < b << 19}.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void candidate_range(uint32_t h, uint32_t thr, int J,
+                                                const uint32_t* sX, const uint16_t* sTab,
+                                                int& lo, int& hi) {
+    if (thr == 0u) { lo = hi = 0; return; }
+    if (thr >= 0x40000000u) { lo = 0; hi = J; return; }
+    const int t = 31 - __clz((int)thr);  // 0..29
+    const int L = 30 - t;                // prefix length in bits of a 31-bit value, 1..30
+    const uint32_t p = h >> (t + 1);
+    if (L <= kTabBits) {
+        const int sh = kTabBits - L;
+        lo = sTab[p << sh];
+        hi = sTab[(p + 1u) << sh];
+    } else {
+        const uint32_t b = h >> (31 - kTabBits);
+        int a = sTab[b];
+        const int z = sTab[b + 1];
+        while (a < z && (sX[a] >> (t + 1)) < p) ++a;
+        int e = a;
+        while (e < z && (sX[e] >> (t + 1)) == p) ++e;
+        lo = a;
+        hi = e;
+    }
+}
+
+// Live mask of 4 consecutive simulations as bytes (0xFF = live): Eq. (hash_prob).
+__device__ __forceinline__ uint32_t live4(uint4 x, uint32_t h, uint32_t thr) {
+    return (((x.x ^ h) < thr) ? 0x000000FFu : 0u) | (((x.y ^ h) < thr) ? 0x0000FF00u : 0u) |
+           (((x.z ^ h) < thr) ? 0x00FF0000u : 0u) | (((x.w ^ h) < thr) ? 0xFF000000u : 0u);
+}
+
+// 0xFF in every byte of x that is a visited register.  Register values are
+// <= 32 < 0x80, so bit 7 of a byte marks the visited value 0xFF.
+__device__ __forceinline__ uint32_t visited_bytes(uint32_t x) {
+    return ((x & 0x80808080u) >> 7) * 0xFFu;
+}
+
+// Byte-wise max (Eq. sketch-merge) of a (bytes in [0,32] or 0xFF) and b (bytes
+// in [0,32]); a visited byte of a stays 0xFF.  (a|0x80) - b never borrows
+// across bytes because every byte of b is below 0x80.
+__device__ __forceinline__ uint32_t byte_max(uint32_t a, uint32_t b) {
+    const uint32_t ge = (((a | 0x80808080u) - b) & 0x80808080u) >> 7;
+    const uint32_t m = ge * 0xFFu;
+    return (a & m) | (b & ~m);
+}
+
+// 16-byte load that bypasses L1 (registers are updated in place by other SMs).
+__device__ __forceinline__ uint4 ld_cg16(const uint8_t* p) {
+    return __ldcg(reinterpret_cast<const uint4*>(p));
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+}  // namespace im

@@ -1,0 +1,1038 @@
+// Kernels of the sketch-based IM hot path for GB300 (sm_103a).
+//
+//   k_sims         per-simulation draws X_j, salt_j, FASST sort, range table   (Sec. 2.2, Sec. 4.1)
+//   k_fill         Fill-Sketches: M[u][j] = rank of u in simulation j         (Alg. 1, Eq. sketch-init)
+//   k_frontier     one level of a frontier over a unified queue:
+//                    kPush : Simulate (Alg. 2) as push sweeps from the vertices
+//                            whose registers changed, merged with byte max (Eq. sketch-merge)
+//                    kCover: Cascade (Alg. 3): visited marks spread along live edges
+//   k_pick         Sketchwise-Sum + argmax + seed init of the cover        (Eq. gpu-sketch-int, Alg. 4)
+//   k_mc_*         independent-cascade Monte-Carlo spread (Sec. 5.1 oracle)
+//
+// Schedule: every frontier level walks the flat edge space of its queue
+// (sum of the queued vertices' degrees).  Each warp owns an equal slice of
+// that space, so a hub's edges are spread over many warps (power-law skew)
+// and no warp holds more than its share.  Inside a 32-edge batch every lane
+// resolves one edge (hash, threshold, candidate range); the batch's
+// 16-simulation chunks are then dealt round-robin to the lanes, so lanes work
+// on useful chunks only and consecutive lanes read consecutive 16-byte pieces
+// of a register row.
+#include <cstdio>
+
+#include "im_launch.h"
+
+namespace im {
+
+constexpr int kBlock = 256;
+constexpr int kWarpsPerBlock = kBlock / 32;
+
+// ---------------------------------------------------------------------------
+// a1: simulations.  One block; thread j draws SplitMix64 output j, X_j = low 31
+// bits, salt_j = high 32 bits; rank-sort by (X, j) (stable); sTab[b] = number
+// of X below b << 19.
+// ---------------------------------------------------------------------------
+__global__ void k_sims(uint64_t seed, int J, uint32_t* X, uint32_t* salt, uint16_t* tab) {
+    __shared__ uint32_t sx[kMaxJ];
+    __shared__ uint32_t sorted[kMaxJ];
+    const int j = threadIdx.x;
+    uint32_t x = 0, s = 0;
+    if (j < J) {
+        const uint64_t z = splitmix_at(seed, (uint64_t)j);
+        x = (uint32_t)z & 0x7FFFFFFFu;
+        s = (uint32_t)(z >> 32);
+        sx[j] = x;
+    }
+    __syncthreads();
+    if (j < J) {
+        int r = 0;
+        for (int i = 0; i < J; ++i) {
+            const uint32_t xi = sx[i];
+            r += (xi < x) || (xi == x && i < j);
+        }
+        sorted[r] = x;
+        X[r] = x;
+        salt[r] = s;
+    }
+    __syncthreads();
+    for (int b = j; b < kTabSize; b += blockDim.x) {
+        const uint32_t key = (uint32_t)b << (31 - kTabBits);
+        int lo = 0, hi = J;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (sorted[mid] < key) lo = mid + 1; else hi = mid;
+        }
+        tab[b] = (uint16_t)lo;
+    }
+}
+
+cudaError_t launch_sims(uint64_t seed, int J, uint32_t* X, uint32_t* salt, uint16_t* tab,
+                        cudaStream_t st) {
+    k_sims<<<1, kMaxJ, 0, st>>>(seed, J, X, salt, tab);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// a3: Fill-Sketches (Alg. 1).  Thread per 16-byte chunk of a register row;
+// non-visited bytes get the vertex's rank, visited bytes are kept.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_fill(uint8_t* __restrict__ M, int32_t n, int J,
+                                                 const uint32_t* __restrict__ salt) {
+    const int cpr_log = __ffs(J >> 4) - 1;  // chunks per row = J/16, a power of two
+    const int64_t total = (int64_t)n << cpr_log;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t u = (uint32_t)(c >> cpr_log);
+        const int ch = (int)(c & ((1 << cpr_log) - 1));
+        uint4* p = reinterpret_cast<uint4*>(M + (size_t)u * J + ch * 16);
+        const uint4 cur = *p;
+        const uint32_t ku = mm3_k(u);
+        const uint4* sl = reinterpret_cast<const uint4*>(salt + ch * 16);
+        uint32_t w[4] = {cur.x, cur.y, cur.z, cur.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 s4 = __ldg(sl + q);
+            const uint32_t r = rank_of(ku, s4.x) | (rank_of(ku, s4.y) << 8) |
+                               (rank_of(ku, s4.z) << 16) | (rank_of(ku, s4.w) << 24);
+            const uint32_t vis = visited_bytes(w[q]);
+            w[q] = (w[q] & vis) | (r & ~vis);
+        }
+        *p = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+cudaError_t launch_fill(uint8_t* M, int32_t n, int J, const uint32_t* salt, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int64_t total = (int64_t)n * (J / 16);
+    int64_t grid = (total + kBlock - 1) / kBlock;
+    if (grid > 152 * 16) grid = 152 * 16;
+    k_fill<<<(int)grid, kBlock, 0, st>>>(M, n, J, salt);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Flat-edge-space helpers.
+// ---------------------------------------------------------------------------
+
+// Index of the last queue entry whose offset is <= f (a warp-wide 32-ary search).
+__device__ __forceinline__ int32_t find_covering(const QEntry* __restrict__ q, int32_t count,
+                                                 int64_t f) {
+    int32_t lo = 0, hi = count;
+    const int lane = (int)lane_id();
+    while (hi - lo > 1) {
+        const int32_t step = (hi - lo + 31) >> 5;
+        const int64_t idx = (int64_t)lo + (int64_t)step * (lane + 1);
+        const bool le = idx < hi && (int64_t)__ldcg(&q[idx].off) <= f;
+        const int c = __popc(__ballot_sync(0xFFFFFFFFu, le));
+        const int32_t nlo = lo + step * c;
+        const int32_t nhi = (c < 32) ? (int32_t)min((int64_t)hi, (int64_t)lo + (int64_t)step * (c + 1)) : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    return lo;
+}
+
+// Warp-aggregated append of (vertex, row start, degree, aux) to a queue whose
+// counter packs count << 38 | edges.  Lanes with want == false do not append.
+__device__ __forceinline__ void warp_append(bool want, int32_t v, int32_t rp, int32_t deg,
+                                            uint32_t aux, QEntry* __restrict__ q,
+                                            unsigned long long* ctr, int32_t cap, uint32_t* err) {
+    const unsigned wm = __ballot_sync(0xFFFFFFFFu, want);
+    if (wm == 0u) return;
+    const int lane = (int)lane_id();
+    int d = want ? deg : 0;
+    int incl = d;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, s);
+        if (lane >= s) incl += y;
+    }
+    const int totd = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    const int totc = __popc(wm);
+    unsigned long long base = 0;
+    if (lane == 0)
+        base = atomicAdd(ctr, ((unsigned long long)totc << kCountShift) | (unsigned long long)totd);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (want) {
+        const int32_t slot = (int32_t)(base >> kCountShift) + __popc(wm & ((1u << lane) - 1u));
+        const int32_t off = (int32_t)(base & kEdgeMask) + (incl - d);
+        if (slot < cap) {
+            QEntry e;
+            e.v = v;
+            e.rp = rp;
+            e.off = off;
+            e.aux = aux;
+            q[slot] = e;
+        } else {
+            atomicOr(err, kErrQueue);
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, s);
+    return x;
+}
+
+// ---------------------------------------------------------------------------
+// a4 / a7: one frontier level.
+//   kPush : queue vertex q = v, edge (o, q) from the in-CSR; chunks of M[q]
+//           whose simulations are live and not visited are max-merged into
+//           M[o] with atomic CAS (Alg. 2 as a push: only improvements write).
+//   kCover: queue vertex q = u, edge (q, o) from the out-CSR; simulations in
+//           which q is visited and the edge is live mark o visited (Alg. 3).
+// A vertex o whose registers changed is appended once (stamp gen[o]) to the
+// next queue, with its in-degree (push) or out-degree (cover).
+// ---------------------------------------------------------------------------
+template <int KIND, int MODE>
+__global__ void __launch_bounds__(kBlock) k_frontier(GraphDev g, FrontierArgs a) {
+    __shared__ __align__(16) uint32_t sX[kMaxJ];
+    __shared__ uint16_t sTab[kTabSize];
+    const int J = a.J;
+    for (int i = threadIdx.x; i < J; i += blockDim.x) sX[i] = __ldg(a.X + i);
+    for (int i = threadIdx.x; i < kTabSize; i += blockDim.x) sTab[i] = __ldg(a.tab + i);
+    __syncthreads();
+
+    const unsigned long long c = __ldcg(a.ctr_in);
+    const int32_t count = (int32_t)(c >> kCountShift);
+    const int64_t E = (int64_t)(c & kEdgeMask);
+    if (E == 0) return;
+    const int lane = (int)lane_id();
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    if (warp == 0 && lane == 0) {
+        atomicAdd(a.stats + (MODE == kPush ? kStSweepVertices : kStCoverVertices),
+                  (unsigned long long)count);
+        atomicAdd(a.stats + (MODE == kPush ? kStSweepEdges : kStCoverEdges),
+                  (unsigned long long)E);
+        atomicAdd(a.stats + (MODE == kPush ? kStSweepLevels : kStCoverLevels), 1ull);
+    }
+    const int64_t nb = (E + 31) >> 5;
+    const int64_t per = (nb + nwarps - 1) / nwarps;
+    const int64_t b0 = warp * per;
+    const int64_t b1 = min(nb, b0 + per);
+    if (b0 >= b1) return;
+    const int64_t fend = min(E, b1 << 5);
+    int64_t f0 = b0 << 5;
+    int32_t qi = find_covering(a.q_in, count, f0);
+
+    unsigned long long st_chunks = 0, st_cas = 0, st_changed = 0, st_new = 0;
+    const int32_t cap = g.n;
+
+    for (; f0 < fend; f0 += 32) {
+        // ---- resolve the batch's edges --------------------------------------
+        const int32_t wi = qi + lane;
+        const bool wvalid = wi < count;
+        QEntry ent;
+        if (wvalid) {
+            const int4 raw = __ldcg(reinterpret_cast<const int4*>(a.q_in) + wi);
+            ent.v = raw.x; ent.rp = raw.y; ent.off = raw.z; ent.aux = (uint32_t)raw.w;
+        } else {
+            ent.v = 0; ent.rp = 0; ent.off = 0x7FFFFFFF; ent.aux = 0;
+        }
+        const int64_t rel = (int64_t)ent.off - f0;
+        const int c0 = __popc(__ballot_sync(0xFFFFFFFFu, wvalid && rel <= 0));
+        const unsigned starts =
+            __reduce_or_sync(0xFFFFFFFFu, (wvalid && rel >= 1 && rel <= 31) ? (1u << rel) : 0u);
+        const int myw = c0 - 1 + __popc(starts & ((2u << lane) - 1u));
+        const int32_t qv = __shfl_sync(0xFFFFFFFFu, ent.v, myw);
+        const int32_t qrp = __shfl_sync(0xFFFFFFFFu, ent.rp, myw);
+        const int32_t qoff = __shfl_sync(0xFFFFFFFFu, ent.off, myw);
+        const uint32_t qaux = __shfl_sync(0xFFFFFFFFu, ent.aux, myw);
+        const int64_t f = f0 + lane;
+        const bool act = f < fend;
+
+        int32_t o = 0;
+        uint32_t h = 0, thr = 0;
+        int clo = 0, nch = 0;
+        if (act) {
+            const int64_t e = (int64_t)qrp + (f - qoff);
+            if constexpr (MODE == kPush) {
+                o = __ldg(g.src_in + e);
+                h = edge_hash((uint32_t)o, (uint32_t)qv);
+                thr = edge_threshold<KIND, true>(g, (uint32_t)o, (uint32_t)qv, e, qaux);
+            } else {
+                o = __ldg(g.col_out + e);
+                h = edge_hash((uint32_t)qv, (uint32_t)o);
+                thr = edge_threshold<KIND, false>(g, (uint32_t)qv, (uint32_t)o, e, 0u);
+            }
+            int lo, hi;
+            candidate_range(h, thr, J, sX, sTab, lo, hi);
+            if (hi > lo) {
+                clo = lo >> 4;
+                nch = ((hi + 15) >> 4) - clo;
+            }
+        }
+
+        // ---- deal the batch's 16-simulation chunks to the lanes --------------
+        int incl = nch;
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, incl, s);
+            if (lane >= s) incl += y;
+        }
+        const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        const int excl = incl - nch;
+        for (int base = 0; base < total; base += 32) {
+            const int k = base + lane;
+            int i = 0;
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                const int ic = __shfl_sync(0xFFFFFFFFu, incl, i + s - 1);
+                if (ic <= k) i += s;
+            }
+            if (i > 31) i = 31;
+            const int ex_i = __shfl_sync(0xFFFFFFFFu, excl, i);
+            const int cl_i = __shfl_sync(0xFFFFFFFFu, clo, i);
+            const int32_t o_i = __shfl_sync(0xFFFFFFFFu, o, i);
+            const int32_t q_i = __shfl_sync(0xFFFFFFFFu, qv, i);
+            const uint32_t h_i = __shfl_sync(0xFFFFFFFFu, h, i);
+            const uint32_t t_i = __shfl_sync(0xFFFFFFFFu, thr, i);
+            bool changed = false;
+            if (k < total) {
+                const int chunk = cl_i + (k - ex_i);
+                const uint4* xs = reinterpret_cast<const uint4*>(sX + chunk * 16);
+                const uint4 src = ld_cg16(a.M + (size_t)q_i * J + chunk * 16);
+                uint32_t sw[4] = {src.x, src.y, src.z, src.w};
+                uint32_t cand[4];
+                uint32_t any = 0;
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const uint32_t L = live4(xs[w], h_i, t_i);
+                    if constexpr (MODE == kPush) cand[w] = sw[w] & L & ~visited_bytes(sw[w]);
+                    else cand[w] = L & visited_bytes(sw[w]);
+                    any |= cand[w];
+                }
+                if (any) {
+                    ++st_chunks;
+                    uint8_t* trow = a.M + (size_t)o_i * J + chunk * 16;
+                    const uint4 tg = ld_cg16(trow);
+                    uint32_t tw[4] = {tg.x, tg.y, tg.z, tg.w};
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        unsigned int* addr = reinterpret_cast<unsigned int*>(trow + 4 * w);
+                        if constexpr (MODE == kPush) {
+                            if (cand[w] == 0u) continue;
+                            uint32_t cur = tw[w];
+                            uint32_t nw = byte_max(cur, cand[w]);
+                            int tries = 0;
+                            while (nw != cur) {
+                                const uint32_t prev = atomicCAS(addr, cur, nw);
+                                if (prev == cur) {
+                                    changed = true;
+                                    ++st_cas;
+                                    break;
+                                }
+                                cur = prev;
+                                nw = byte_max(cur, cand[w]);
+                                if (++tries > kCasRetryLimit) {
+                                    atomicOr(a.err, kErrCasLimit);
+                                    break;
+                                }
+                            }
+                        } else {
+                            const uint32_t newly = cand[w] & ~visited_bytes(tw[w]);
+                            if (newly == 0u) continue;
+                            const uint32_t prev = atomicOr(addr, newly);
+                            const uint32_t really = newly & ~visited_bytes(prev);
+                            if (really) {
+                                changed = true;
+                                st_new += (unsigned)(__popc(really) >> 3);
+                            }
+                        }
+                    }
+                }
+            }
+            // ---- enqueue changed vertices for the next level ------------------
+            bool want = false;
+            int32_t rp = 0, deg = 0;
+            uint32_t aux = 0;
+            if (changed) {
+                want = atomicExch(a.gen + o_i, a.gen_next) != a.gen_next;
+                if (want) {
+                    if constexpr (MODE == kPush) {
+                        rp = __ldg(g.rp_in + o_i);
+                        deg = __ldg(g.rp_in + o_i + 1) - rp;
+                        if constexpr (KIND == kWC) aux = __ldg(g.thr_v + o_i);
+                    } else {
+                        rp = __ldg(g.rp_out + o_i);
+                        deg = __ldg(g.rp_out + o_i + 1) - rp;
+                    }
+                    want = deg > 0;
+                    st_changed += want ? 1 : 0;
+                }
+            }
+            warp_append(want, o_i, rp, deg, aux, a.q_out, a.ctr_out, cap, a.err);
+        }
+
+        // ---- advance the window to the entry covering f0 + 32 -----------------
+        const int n32 = __popc(__ballot_sync(0xFFFFFFFFu, wvalid && rel <= 32));
+        int32_t qn = qi + n32 - 1;
+        if (n32 == 32 && qi + 32 < count) {
+            if ((int64_t)__ldcg(&a.q_in[qi + 32].off) <= f0 + 32) qn = qi + 32;
+        }
+        qi = qn;
+    }
+
+    st_chunks = warp_sum(st_chunks);
+    st_cas = warp_sum(st_cas);
+    st_changed = warp_sum(st_changed);
+    st_new = warp_sum(st_new);
+    if (lane == 0) {
+        if constexpr (MODE == kPush) {
+            if (st_chunks) atomicAdd(a.stats + kStSweepChunks, st_chunks);
+            if (st_cas) atomicAdd(a.stats + kStSweepCas, st_cas);
+            if (st_changed) atomicAdd(a.stats + kStSweepChanged, st_changed);
+        } else {
+            if (st_chunks) atomicAdd(a.stats + kStCoverChunks, st_chunks);
+            if (st_new) {
+                atomicAdd(a.stats + kStCoverNew, st_new);
+                atomicAdd(a.count, st_new);
+            }
+        }
+    }
+}
+
+int frontier_grid() {
+    static int grid = 0;
+    if (grid == 0) {
+        int dev = 0, sms = 152, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_frontier<kUniform, kPush>, kBlock, 0);
+        if (per_sm < 1) per_sm = 1;
+        grid = sms * per_sm;
+    }
+    return grid;
+}
+
+template <int MODE>
+static cudaError_t launch_frontier_mode(int kind, const GraphDev& g, const FrontierArgs& a,
+                                        int grid, cudaStream_t st) {
+    switch (kind) {
+        case kUniform: k_frontier<kUniform, MODE><<<grid, kBlock, 0, st>>>(g, a); break;
+        case kWC: k_frontier<kWC, MODE><<<grid, kBlock, 0, st>>>(g, a); break;
+        case kTrivalency: k_frontier<kTrivalency, MODE><<<grid, kBlock, 0, st>>>(g, a); break;
+        default: k_frontier<kExplicit, MODE><<<grid, kBlock, 0, st>>>(g, a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_frontier(int kind, int mode, const GraphDev& g, const FrontierArgs& a, int grid,
+                            cudaStream_t st) {
+    return mode == kPush ? launch_frontier_mode<kPush>(kind, g, a, grid, st)
+                         : launch_frontier_mode<kCover>(kind, g, a, grid, st);
+}
+
+// ---------------------------------------------------------------------------
+// a5 / a6: Sketchwise-Sum + argmax (Alg. 4) + seed init of the cover.
+// S_u = sum_j 2^(32 - M[u][j]) with visited = 2^32 (exact uint64); the pick
+// is the smallest (S_u, u) over vertices not yet picked.  A warp covers
+// 32 / LPR rows at once (LPR = min(J/16, 32) lanes per row, 16 bytes a lane).
+// The last block to finish reduces the per-block minima, records the seed
+// and its estimate J*2^32/(phi*S), marks its row visited and queues it for
+// the cover.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long row_terms16(uint4 q) {
+    unsigned long long s = 0;
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const uint32_t r = (w[i] >> (8 * b)) & 0xFFu;
+            s += (r == kVisited) ? (1ull << 32) : (1ull << (32 - r));
+        }
+    }
+    return s;
+}
+
+// Sum of the row owned by this lane's segment; valid in every lane of the segment.
+__device__ __forceinline__ unsigned long long row_sum(const uint8_t* __restrict__ M, int J,
+                                                      int32_t row, int lpr, int cpl, int seg_lane) {
+    unsigned long long s = 0;
+    const uint8_t* p = M + (size_t)row * J;
+    for (int c = 0; c < cpl; ++c) {
+        const int chunk = seg_lane + c * lpr;
+        s += row_terms16(__ldcg(reinterpret_cast<const uint4*>(p) + chunk));
+    }
+    for (int off = lpr >> 1; off >= 1; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
+    return s;
+}
+
+__device__ __forceinline__ void lex_min(unsigned long long& S, int32_t& u, unsigned long long oS,
+                                        int32_t ou) {
+    if (oS < S || (oS == S && ou < u)) { S = oS; u = ou; }
+}
+
+// Marks row s visited and queues s as level 0 of a cover (one block).
+__device__ void cover_seed_block(uint8_t* M, int J, int32_t s, const int32_t* rp_out, QEntry* q,
+                                 unsigned long long* ctr, unsigned long long* count) {
+    __shared__ unsigned int newly_sh;
+    if (threadIdx.x == 0) newly_sh = 0;
+    __syncthreads();
+    unsigned int newly = 0;
+    uint8_t* row = M + (size_t)s * J;
+    for (int j = threadIdx.x; j < J; j += blockDim.x) {
+        if (row[j] != kVisited) { row[j] = (uint8_t)kVisited; ++newly; }
+    }
+    newly = (unsigned)warp_sum(newly);
+    if (lane_id() == 0 && newly) atomicAdd(&newly_sh, newly);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int nw = newly_sh;
+        if (nw) atomicAdd(count, (unsigned long long)nw);
+        const int32_t rp = rp_out[s];
+        const int32_t deg = rp_out[s + 1] - rp;
+        if (nw && deg > 0) {
+            QEntry e;
+            e.v = s; e.rp = rp; e.off = 0; e.aux = 0;
+            q[0] = e;
+            *ctr = (1ull << kCountShift) | (unsigned long long)deg;
+        } else {
+            *ctr = 0ull;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_pick(PickArgs a) {
+    __shared__ unsigned long long sS[kWarpsPerBlock];
+    __shared__ int32_t sU[kWarpsPerBlock];
+    __shared__ bool is_last;
+    const int J = a.J;
+    const int cpr = J >> 4;
+    const int lpr = cpr < 32 ? cpr : 32;
+    const int cpl = cpr / lpr;
+    const int rpw = 32 / lpr;
+    const int lane = (int)lane_id();
+    const int seg = lane / lpr, seg_lane = lane % lpr;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long bestS = ~0ull;
+    int32_t bestU = 0x7FFFFFFF;
+    for (int64_t r0 = warp * rpw; r0 < a.n; r0 += nwarps * rpw) {
+        const int64_t row = r0 + seg;
+        const bool ok = row < a.n;
+        const unsigned long long s = row_sum(a.M, J, ok ? (int32_t)row : 0, lpr, cpl, seg_lane);
+        if (ok && seg_lane == 0) {
+            const bool picked = (__ldcg(a.seed_bits + (row >> 5)) >> (row & 31)) & 1u;
+            if (!picked) lex_min(bestS, bestU, s, (int32_t)row);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const unsigned long long oS = __shfl_xor_sync(0xFFFFFFFFu, bestS, off);
+        const int32_t ou = __shfl_xor_sync(0xFFFFFFFFu, bestU, off);
+        lex_min(bestS, bestU, oS, ou);
+    }
+    const int wib = threadIdx.x >> 5;
+    if (lane == 0) { sS[wib] = bestS; sU[wib] = bestU; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kWarpsPerBlock; ++w) lex_min(bestS, bestU, sS[w], sU[w]);
+        a.part_S[blockIdx.x] = bestS;
+        a.part_u[blockIdx.x] = bestU;
+        __threadfence();
+        const unsigned t = atomicAdd(a.ticket, 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    // ---- last block: global minimum, seed record, cover seed ----------------
+    __threadfence();
+    unsigned long long gS = ~0ull;
+    int32_t gU = 0x7FFFFFFF;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+        lex_min(gS, gU, __ldcg(a.part_S + b), __ldcg(a.part_u + b));
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const unsigned long long oS = __shfl_xor_sync(0xFFFFFFFFu, gS, off);
+        const int32_t ou = __shfl_xor_sync(0xFFFFFFFFu, gU, off);
+        lex_min(gS, gU, oS, ou);
+    }
+    __shared__ unsigned long long fS;
+    __shared__ int32_t fU;
+    if (lane == 0) { sS[wib] = gS; sU[wib] = gU; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kWarpsPerBlock; ++w) lex_min(gS, gU, sS[w], sU[w]);
+        fS = gS;
+        fU = gU;
+        *a.ticket = 0u;
+        if (gS == ~0ull) {
+            a.out_seed[a.k] = -1;
+            *a.ctr_cover = 0ull;
+        } else {
+            a.out_seed[a.k] = gU;
+            a.out_S[a.k] = gS;
+            a.out_est[a.k] = ((double)J * 4294967296.0) / (0.77351 * (double)gS);
+            a.seed_bits[gU >> 5] |= 1u << (gU & 31);
+        }
+    }
+    __syncthreads();
+    if (fS == ~0ull || !a.mark) return;
+    cover_seed_block(a.M, J, fU, a.rp_out, a.q_cover, a.ctr_cover, a.count);
+}
+
+int pick_grid(int32_t n, int J) {
+    const int cpr = J / 16;
+    const int lpr = cpr < 32 ? cpr : 32;
+    const int rpw = 32 / lpr;
+    const int64_t rows_per_block = (int64_t)rpw * kWarpsPerBlock;
+    int64_t grid = (n + rows_per_block - 1) / rows_per_block;
+    if (grid > 152 * 8) grid = 152 * 8;
+    if (grid < 1) grid = 1;
+    return (int)grid;
+}
+
+cudaError_t launch_pick(const PickArgs& a, cudaStream_t st) {
+    k_pick<<<pick_grid(a.n, a.J), kBlock, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kBlock) k_cover_seed(uint8_t* M, int J, int32_t s,
+                                                       const int32_t* rp_out, QEntry* q,
+                                                       unsigned long long* ctr,
+                                                       unsigned long long* count) {
+    cover_seed_block(M, J, s, rp_out, q, ctr, count);
+}
+
+cudaError_t launch_cover_seed(uint8_t* M, int J, int32_t s, const int32_t* rp_out, QEntry* q,
+                              unsigned long long* ctr, unsigned long long* count, cudaStream_t st) {
+    k_cover_seed<<<1, kBlock, 0, st>>>(M, J, s, rp_out, q, ctr, count);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kBlock) k_sums(const uint8_t* __restrict__ M, int32_t n, int J,
+                                                 unsigned long long* __restrict__ S) {
+    const int cpr = J >> 4;
+    const int lpr = cpr < 32 ? cpr : 32;
+    const int cpl = cpr / lpr;
+    const int rpw = 32 / lpr;
+    const int lane = (int)lane_id();
+    const int seg = lane / lpr, seg_lane = lane % lpr;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r0 = warp * rpw; r0 < n; r0 += nwarps * rpw) {
+        const int64_t row = r0 + seg;
+        const bool ok = row < n;
+        const unsigned long long s = row_sum(M, J, ok ? (int32_t)row : 0, lpr, cpl, seg_lane);
+        if (ok && seg_lane == 0) S[row] = s;
+    }
+}
+
+cudaError_t launch_sums(const uint8_t* M, int32_t n, int J, unsigned long long* S, cudaStream_t st) {
+    k_sums<<<pick_grid(n, J), kBlock, 0, st>>>(M, n, J, S);
+    return cudaGetLastError();
+}
+
+__global__ void k_count_visited(const uint8_t* __restrict__ M, int64_t words16,
+                                unsigned long long* out) {
+    unsigned long long c = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < words16;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(M) + i);
+        c += (__popc(visited_bytes(q.x)) + __popc(visited_bytes(q.y)) + __popc(visited_bytes(q.z)) +
+              __popc(visited_bytes(q.w))) >> 3;
+    }
+    c = warp_sum(c);
+    if (lane_id() == 0 && c) atomicAdd(out, c);
+}
+
+cudaError_t launch_count_visited(const uint8_t* M, int64_t bytes, unsigned long long* out,
+                                 cudaStream_t st) {
+    const int64_t w = bytes / 16;
+    if (w == 0) return cudaSuccess;
+    int64_t grid = (w + kBlock - 1) / kBlock;
+    if (grid > 152 * 8) grid = 152 * 8;
+    k_count_visited<<<(int)grid, kBlock, 0, st>>>(M, w, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Graph load: in-degrees, scan, reverse CSR, thresholds, the all-vertex queue.
+// ---------------------------------------------------------------------------
+__global__ void k_indegree(const int32_t* __restrict__ col, int64_t m, int32_t* cnt) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(cnt + col[e], 1);
+}
+
+cudaError_t launch_indegree(const int32_t* col, int64_t m, int32_t* cnt, cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    k_indegree<<<152 * 8, kBlock, 0, st>>>(col, m, cnt);
+    return cudaGetLastError();
+}
+
+constexpr int kScanTile = 2048;  // elements per block (256 threads x 8)
+
+__global__ void k_scan_tiles(const int32_t* __restrict__ in, int32_t n, int32_t* __restrict__ out,
+                             int64_t* __restrict__ tile_sums) {
+    __shared__ int64_t warp_tot[kWarpsPerBlock];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * 8;
+    int32_t v[8];
+    int64_t local = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        v[i] = (base + i < n) ? in[base + i] : 0;
+        local += v[i];
+    }
+    const int lane = (int)lane_id(), w = threadIdx.x >> 5;
+    int64_t incl = local;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        const int64_t y = __shfl_up_sync(0xFFFFFFFFu, incl, s);
+        if (lane >= s) incl += y;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    int64_t wbase = 0;
+    for (int i = 0; i < w; ++i) wbase += warp_tot[i];
+    int64_t run = wbase + incl - local;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (base + i < n) out[base + i] = (int32_t)run;  // tile-local exclusive prefix
+        run += v[i];
+    }
+    if (threadIdx.x == blockDim.x - 1) tile_sums[blockIdx.x] = wbase + incl;
+}
+
+__global__ void k_scan_sums(int64_t* tile_sums, int ntiles, int32_t* out_total_slot) {
+    // single block: exclusive scan of the tile sums in place; writes the total
+    if (threadIdx.x == 0) {
+        int64_t run = 0;
+        for (int t = 0; t < ntiles; ++t) {
+            const int64_t s = tile_sums[t];
+            tile_sums[t] = run;
+            run += s;
+        }
+        *out_total_slot = (int32_t)run;
+    }
+}
+
+__global__ void k_scan_add(int32_t* __restrict__ out, int32_t n, const int64_t* __restrict__ tile_sums) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += (int32_t)tile_sums[i / kScanTile];
+}
+
+size_t scan_tmp_bytes(int32_t n) {
+    const int64_t tiles = ((int64_t)n + kScanTile - 1) / kScanTile;
+    return (size_t)(tiles + 1) * sizeof(int64_t);
+}
+
+cudaError_t launch_exclusive_scan(const int32_t* cnt, int32_t n, int32_t* out, void* tmp,
+                                  cudaStream_t st) {
+    const int ntiles = (int)(((int64_t)n + kScanTile - 1) / kScanTile);
+    int64_t* sums = static_cast<int64_t*>(tmp);
+    if (ntiles > 0) k_scan_tiles<<<ntiles, kBlock, 0, st>>>(cnt, n, out, sums);
+    k_scan_sums<<<1, 32, 0, st>>>(sums, ntiles, out + n);
+    if (n > 0) k_scan_add<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(out, n, sums);
+    return cudaGetLastError();
+}
+
+__global__ void k_scatter_in(const int32_t* __restrict__ rp_out, const int32_t* __restrict__ col_out,
+                             int32_t n, const int32_t* __restrict__ rp_in, int32_t* fill,
+                             int32_t* __restrict__ src_in, const uint32_t* __restrict__ thr_out,
+                             uint32_t* __restrict__ thr_in) {
+    const int lane = (int)lane_id();
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = warp; u < n; u += nwarps) {
+        const int32_t b = rp_out[u], e = rp_out[u + 1];
+        for (int32_t i = b + lane; i < e; i += 32) {
+            const int32_t v = col_out[i];
+            const int32_t pos = rp_in[v] + atomicAdd(fill + v, 1);
+            src_in[pos] = (int32_t)u;
+            if (thr_in) thr_in[pos] = thr_out[i];
+        }
+    }
+}
+
+cudaError_t launch_scatter_in(const int32_t* rp_out, const int32_t* col_out, int32_t n,
+                              const int32_t* rp_in, int32_t* fill, int32_t* src_in,
+                              const uint32_t* thr_out, uint32_t* thr_in, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_scatter_in<<<152 * 8, kBlock, 0, st>>>(rp_out, col_out, n, rp_in, fill, src_in, thr_out, thr_in);
+    return cudaGetLastError();
+}
+
+// Weighted cascade (Sec. 2.1): w = 1/indeg(v) rounded to fp32 (IEEE division),
+// threshold floor(w * 2^31) computed exactly in fp64.
+__device__ __forceinline__ uint32_t prob_threshold_dev(float w) {
+    const double t = floor((double)w * 2147483648.0);
+    if (!(t > 0.0)) return 0u;
+    if (t >= 2147483648.0) return 2147483648u;
+    return (uint32_t)t;
+}
+
+__global__ void k_thr_wc(const int32_t* __restrict__ rp_in, int32_t n, uint32_t* __restrict__ thr_v) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int32_t d = rp_in[v + 1] - rp_in[v];
+    thr_v[v] = d > 0 ? prob_threshold_dev(__fdiv_rn(1.0f, (float)d)) : 0u;
+}
+
+cudaError_t launch_thr_wc(const int32_t* rp_in, int32_t n, uint32_t* thr_v, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_thr_wc<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(rp_in, n, thr_v);
+    return cudaGetLastError();
+}
+
+__global__ void k_thr_explicit(const float* __restrict__ w, int64_t m, uint32_t* __restrict__ thr) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        thr[e] = prob_threshold_dev(w[e]);
+}
+
+cudaError_t launch_thr_explicit(const float* w, int64_t m, uint32_t* thr, cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    k_thr_explicit<<<152 * 8, kBlock, 0, st>>>(w, m, thr);
+    return cudaGetLastError();
+}
+
+__global__ void k_flag_nonzero_in(const int32_t* __restrict__ rp_in, int32_t n, int32_t* flag) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) flag[v] = rp_in[v + 1] > rp_in[v] ? 1 : 0;
+}
+
+cudaError_t launch_flag_nonzero_in(const int32_t* rp_in, int32_t n, int32_t* flag, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_flag_nonzero_in<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(rp_in, n, flag);
+    return cudaGetLastError();
+}
+
+// Entry k of the all-vertex queue is the k-th vertex with in-edges; its offset
+// in the flat in-edge space is its in-CSR row start.
+__global__ void k_all_queue(const int32_t* __restrict__ rp_in, int32_t n,
+                            const uint32_t* __restrict__ thr_v, const int32_t* __restrict__ pos,
+                            QEntry* __restrict__ q) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int32_t b = rp_in[v], e = rp_in[v + 1];
+    if (e > b) {
+        QEntry x;
+        x.v = (int32_t)v; x.rp = b; x.off = b; x.aux = thr_v ? thr_v[v] : 0u;
+        q[pos[v]] = x;
+    }
+}
+
+cudaError_t launch_all_queue(const int32_t* rp_in, int32_t n, const uint32_t* thr_v,
+                             const int32_t* pos, QEntry* q, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_all_queue<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(rp_in, n, thr_v, pos, q);
+    return cudaGetLastError();
+}
+
+}  // namespace im
+
+namespace im {
+
+// ---------------------------------------------------------------------------
+// Independent-cascade Monte-Carlo spread (the paper's independent quality
+// oracle, Sec. 5.1, on the GPU).  In simulation r, out-edge e fires iff
+// (SplitMix64 output r*m + e of the coin stream) >> 33 < thr[e]; an edge is
+// tried once per simulation, when its source is first reached.  One frontier
+// level walks the out-edges of the vertices newly reached at the previous
+// level; lanes own 32-simulation words and flip coins only for simulations
+// in which the source is new.
+// ---------------------------------------------------------------------------
+__global__ void k_mc_seed(McArgs a, const int32_t* __restrict__ seeds, int k, int valid,
+                          const int32_t* __restrict__ rp_out) {
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const int32_t s = seeds[i];
+        for (int w = 0; w < a.words; ++w) {
+            const int lo = w * 32;
+            uint32_t mask = 0u;
+            if (valid >= lo + 32) mask = 0xFFFFFFFFu;
+            else if (valid > lo) mask = (1u << (valid - lo)) - 1u;
+            a.vis[(size_t)s * a.words + w] = mask;
+            a.f_next[(size_t)s * a.words + w] = mask;  // new bits of level 0
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const int32_t s = seeds[i];
+        if (atomicExch(a.gen + s, a.gen_next) == a.gen_next) continue;
+        const int32_t rp = rp_out[s], deg = rp_out[s + 1] - rp;
+        if (deg <= 0) continue;
+        const unsigned long long base =
+            atomicAdd(a.ctr_out, (1ull << kCountShift) | (unsigned long long)deg);
+        QEntry e;
+        e.v = s; e.rp = rp; e.off = (int32_t)(base & kEdgeMask); e.aux = 0;
+        a.q_out[base >> kCountShift] = e;
+    }
+}
+
+cudaError_t launch_mc_seed(const GraphDev& g, const McArgs& a, const int32_t* seeds, int k,
+                           int valid, cudaStream_t st) {
+    k_mc_seed<<<1, kBlock, 0, st>>>(a, seeds, k, valid, g.rp_out);
+    return cudaGetLastError();
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kBlock) k_mc_level(GraphDev g, McArgs a) {
+    const int lane = (int)lane_id();
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int words = a.words;
+    // clear the new-bits of the level before the previous one (no one reads them now)
+    if (a.q_prev) {
+        const int32_t cp = (int32_t)(__ldcg(a.ctr_prev) >> kCountShift);
+        for (int64_t i = warp; i < cp; i += nwarps) {
+            const int32_t u = __ldcg(&a.q_prev[i].v);
+            if (lane < words) a.f_prev[(size_t)u * words + lane] = 0u;
+        }
+    }
+    const unsigned long long c = __ldcg(a.ctr_in);
+    const int32_t count = (int32_t)(c >> kCountShift);
+    const int64_t E = (int64_t)(c & kEdgeMask);
+    if (E == 0) return;
+    const int64_t nb = (E + 31) >> 5;
+    const int64_t per = (nb + nwarps - 1) / nwarps;
+    const int64_t b0 = warp * per;
+    const int64_t b1 = min(nb, b0 + per);
+    if (b0 >= b1) return;
+    const int64_t fend = min(E, b1 << 5);
+    int64_t f0 = b0 << 5;
+    int32_t qi = find_covering(a.q_in, count, f0);
+    for (; f0 < fend; f0 += 32) {
+        const int32_t wi = qi + lane;
+        const bool wvalid = wi < count;
+        QEntry ent;
+        if (wvalid) {
+            const int4 raw = __ldcg(reinterpret_cast<const int4*>(a.q_in) + wi);
+            ent.v = raw.x; ent.rp = raw.y; ent.off = raw.z; ent.aux = (uint32_t)raw.w;
+        } else {
+            ent.v = 0; ent.rp = 0; ent.off = 0x7FFFFFFF; ent.aux = 0;
+        }
+        const int64_t rel = (int64_t)ent.off - f0;
+        const int c0 = __popc(__ballot_sync(0xFFFFFFFFu, wvalid && rel <= 0));
+        const unsigned starts =
+            __reduce_or_sync(0xFFFFFFFFu, (wvalid && rel >= 1 && rel <= 31) ? (1u << rel) : 0u);
+        const int myw = c0 - 1 + __popc(starts & ((2u << lane) - 1u));
+        const int32_t qv = __shfl_sync(0xFFFFFFFFu, ent.v, myw);
+        const int32_t qrp = __shfl_sync(0xFFFFFFFFu, ent.rp, myw);
+        const int32_t qoff = __shfl_sync(0xFFFFFFFFu, ent.off, myw);
+        const int64_t f = f0 + lane;
+        const int nact = (int)min((int64_t)32, fend - f0);
+        int64_t e = 0;
+        int32_t o = 0;
+        uint32_t thr = 0;
+        if (lane < nact) {
+            e = (int64_t)qrp + (f - qoff);
+            o = __ldg(g.col_out + e);
+            thr = edge_threshold<KIND, false>(g, (uint32_t)qv, (uint32_t)o, e, 0u);
+        }
+        for (int i = 0; i < nact; ++i) {
+            const int32_t u_i = __shfl_sync(0xFFFFFFFFu, qv, i);
+            const int32_t o_i = __shfl_sync(0xFFFFFFFFu, o, i);
+            const int64_t e_i = __shfl_sync(0xFFFFFFFFu, e, i);
+            const uint32_t t_i = __shfl_sync(0xFFFFFFFFu, thr, i);
+            bool changed = false;
+            if (lane < words && t_i > 0u) {
+                uint32_t bits = __ldcg(a.f_cur + (size_t)u_i * words + lane);
+                uint32_t live = 0u;
+                while (bits) {
+                    const int b = __ffs((int)bits) - 1;
+                    bits &= bits - 1u;
+                    const uint64_t r = (uint64_t)a.r0 + (uint64_t)(lane * 32 + b);
+                    const uint32_t coin = (uint32_t)(splitmix_at(a.seed, r * (uint64_t)a.m + (uint64_t)e_i) >> 33);
+                    if (coin < t_i) live |= 1u << b;
+                }
+                if (live) {
+                    uint32_t* vw = a.vis + (size_t)o_i * words + lane;
+                    const uint32_t cand = live & ~__ldcg(vw);
+                    if (cand) {
+                        const uint32_t really = cand & ~atomicOr(vw, cand);
+                        if (really) {
+                            atomicOr(a.f_next + (size_t)o_i * words + lane, really);
+                            changed = true;
+                        }
+                    }
+                }
+            }
+            if (__ballot_sync(0xFFFFFFFFu, changed) && lane == 0) {
+                if (atomicExch(a.gen + o_i, a.gen_next) != a.gen_next) {
+                    const int32_t rp = __ldg(g.rp_out + o_i), deg = __ldg(g.rp_out + o_i + 1) - rp;
+                    if (deg > 0) {
+                        const unsigned long long base =
+                            atomicAdd(a.ctr_out, (1ull << kCountShift) | (unsigned long long)deg);
+                        QEntry x;
+                        x.v = o_i; x.rp = rp; x.off = (int32_t)(base & kEdgeMask); x.aux = 0;
+                        a.q_out[base >> kCountShift] = x;
+                    }
+                }
+            }
+        }
+        const int n32 = __popc(__ballot_sync(0xFFFFFFFFu, wvalid && rel <= 32));
+        int32_t qn = qi + n32 - 1;
+        if (n32 == 32 && qi + 32 < count) {
+            if ((int64_t)__ldcg(&a.q_in[qi + 32].off) <= f0 + 32) qn = qi + 32;
+        }
+        qi = qn;
+    }
+}
+
+cudaError_t launch_mc_level(int kind, const GraphDev& g, const McArgs& a, int grid, cudaStream_t st) {
+    switch (kind) {
+        case kUniform: k_mc_level<kUniform><<<grid, kBlock, 0, st>>>(g, a); break;
+        case kWC: k_mc_level<kWC><<<grid, kBlock, 0, st>>>(g, a); break;
+        case kTrivalency: k_mc_level<kTrivalency><<<grid, kBlock, 0, st>>>(g, a); break;
+        default: k_mc_level<kExplicit><<<grid, kBlock, 0, st>>>(g, a); break;
+    }
+    return cudaGetLastError();
+}
+
+// Per-simulation reach sizes: reach[32 w + b] += number of vertices with bit b of word w set.
+__global__ void __launch_bounds__(kBlock) k_mc_count(const uint32_t* __restrict__ vis, int32_t n,
+                                                     int words, unsigned long long* reach) {
+    __shared__ unsigned int sh[kMaxJ];
+    for (int i = threadIdx.x; i < words * 32; i += blockDim.x) sh[i] = 0u;
+    __syncthreads();
+    const int w = threadIdx.x % words;
+    const int rpb = blockDim.x / words;
+    unsigned int cnt[32];
+#pragma unroll
+    for (int b = 0; b < 32; ++b) cnt[b] = 0u;
+    for (int64_t u = (int64_t)blockIdx.x * rpb + threadIdx.x / words; u < n; u += (int64_t)gridDim.x * rpb) {
+        const uint32_t x = __ldg(vis + (size_t)u * words + w);
+#pragma unroll
+        for (int b = 0; b < 32; ++b) cnt[b] += (x >> b) & 1u;
+    }
+#pragma unroll
+    for (int b = 0; b < 32; ++b)
+        if (cnt[b]) atomicAdd(&sh[w * 32 + b], cnt[b]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < words * 32; i += blockDim.x)
+        if (sh[i]) atomicAdd(reach + i, (unsigned long long)sh[i]);
+}
+
+cudaError_t launch_mc_count(const uint32_t* vis, int32_t n, int words, unsigned long long* reach,
+                            cudaStream_t st) {
+    k_mc_count<<<152 * 4, kBlock, 0, st>>>(vis, n, words, reach);
+    return cudaGetLastError();
+}
+
+__global__ void k_mc_reduce(const unsigned long long* __restrict__ reach, int valid,
+                            unsigned long long* acc) {
+    unsigned long long s = 0, q = 0;
+    for (int r = threadIdx.x; r < valid; r += blockDim.x) {
+        const unsigned long long x = reach[r];
+        s += x;
+        q += x * x;
+    }
+    s = warp_sum(s);
+    q = warp_sum(q);
+    if (lane_id() == 0) {
+        atomicAdd(acc, s);
+        atomicAdd(acc + 1, q);
+    }
+}
+
+cudaError_t launch_mc_reduce(const unsigned long long* reach, int valid, unsigned long long* acc,
+                             cudaStream_t st) {
+    k_mc_reduce<<<1, kBlock, 0, st>>>(reach, valid, acc);
+    return cudaGetLastError();
+}
+
+}  // namespace im

@@ -1,0 +1,289 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer results (registers, visited marks, sums, seeds, counts) must be
+bit-exact; the FP64 spread estimate within rtol 1e-12; Monte-Carlo spreads
+exact against the oracle's identical coin stream and within 3 standard errors
+of the standard-RNG oracle.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from oracle import mc
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def im():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2410_14047_gb300 as lib
+    lib.load_library()
+    return lib
+
+
+@pytest.fixture(scope="module")
+def ctx(im):
+    return im.im_ctx_create(0)
+
+
+def _graphs():
+    return {
+        "er2k": W.erdos_renyi(2000, 16000, seed=3),
+        "rmat12": W.rmat(12, 16, seed=5),
+        "cl5k": W.chung_lu(5000, 12.0, 2.1, seed=9),
+        "path": W.from_edges(40, [(i, i + 1) for i in range(39)]),
+        "star_in": W.from_edges(33, [(i, 0) for i in range(1, 33)]),
+        "cycle": W.from_edges(50, [(i, (i + 1) % 50) for i in range(50)]),
+        "single": W.from_edges(1, []),
+        "isolated": W.from_edges(100, [(3, 4), (4, 5), (90, 3)]),
+    }
+
+
+GRAPHS = _graphs()
+MODELS = {
+    "p01": {"kind": "uniform", "p": 0.01},
+    "p30": {"kind": "uniform", "p": 0.3},
+    "p1": {"kind": "uniform", "p": 1.0},
+    "p0": {"kind": "uniform", "p": 0.0},
+    "wc": {"kind": "wc"},
+    "tri": {"kind": "trivalency", "seed": 2410},
+}
+
+
+def _explicit(g, seed=1):
+    return {"kind": "explicit", "w": W.edge_weights(g.m, "normal", 0.05, 0.025, seed=seed)}
+
+
+# --- a1: simulations --------------------------------------------------------------
+
+@pytest.mark.parametrize("J", [16, 32, 64, 128, 256, 512, 1024])
+def test_sims_match_oracle(im, ctx, J):
+    g = GRAPHS["path"]
+    G = im.im_graph_load(ctx, g.rowptr, g.col, MODELS["p30"])
+    for seed in (0, 2410, 2**63 + 5):
+        sk = im.im_sketch_build(G, J, seed)
+        X, s = sk.sims()
+        Xo, so = O.draw_sims(seed, J)
+        assert np.array_equal(X, Xo) and np.array_equal(s, so)
+
+
+# --- a2-a4: thresholds, fill, propagation ------------------------------------------
+
+BUILD_CASES = [
+    ("er2k", "p01", 64), ("er2k", "p30", 256), ("er2k", "p1", 16), ("er2k", "p0", 32),
+    ("rmat12", "wc", 256), ("rmat12", "tri", 512), ("rmat12", "p30", 1024), ("rmat12", "wc", 16),
+    ("cl5k", "wc", 128), ("cl5k", "p01", 64), ("path", "p1", 64), ("star_in", "p1", 32),
+    ("cycle", "p1", 16), ("cycle", "p30", 128), ("single", "p30", 16), ("isolated", "p1", 64),
+]
+
+
+@pytest.mark.parametrize("gname,mname,J", BUILD_CASES)
+def test_build_matches_oracle(im, ctx, gname, mname, J):
+    g = GRAPHS[gname]
+    model = MODELS[mname]
+    G = im.im_graph_load(ctx, g.rowptr, g.col, model)
+    sk = im.im_sketch_build(G, J, 77)
+    M = sk.registers()
+    X, salt = O.draw_sims(77, J)
+    ref = O.build_reverse(g, O.thresholds(g, model), J, X, salt)
+    assert np.array_equal(M, ref)
+    assert np.array_equal(sk.sums(), O.sums(ref))
+
+
+def test_build_explicit_weights(im, ctx):
+    g = GRAPHS["rmat12"]
+    model = _explicit(g)
+    G = im.im_graph_load(ctx, g.rowptr, g.col, model)
+    sk = im.im_sketch_build(G, 128, 5)
+    X, salt = O.draw_sims(5, 128)
+    assert np.array_equal(sk.registers(), O.build_reverse(g, O.thresholds(g, model), 128, X, salt))
+
+
+# --- a5-a9 step by step --------------------------------------------------------------
+
+@pytest.mark.parametrize("gname,mname,J", [("er2k", "p30", 64), ("rmat12", "wc", 256),
+                                           ("cl5k", "tri", 128)])
+def test_steps_cover_rebuild_pick(im, ctx, gname, mname, J):
+    g = GRAPHS[gname]
+    model = MODELS[mname]
+    thr = O.thresholds(g, model)
+    G = im.im_graph_load(ctx, g.rowptr, g.col, model)
+    sk = im.im_sketch_build(G, J, 31)
+    X, salt = O.draw_sims(31, J)
+    M = O.build_reverse(g, thr, J, X, salt)
+    is_seed = np.zeros(g.n, np.uint8)
+    count = 0
+    for step in range(4):
+        s, S, est = sk.pick()
+        S_ref = O.sums(M)
+        s_ref = O.pick(S_ref, is_seed)
+        assert (s, S) == (s_ref, int(S_ref[s_ref]))
+        assert est == pytest.approx(O.estimate(J, S), rel=1e-12)
+        is_seed[s] = 1
+        c = sk.cover(s)
+        count += O.cover(g, thr, J, X, M, s)
+        assert c == count
+        assert np.array_equal(sk.registers(), M)
+        if step % 2 == 1:
+            sk.rebuild()
+            O.fill(g, J, salt, M)
+            M = O.build_reverse(g, thr, J, X, salt, M)
+            assert np.array_equal(sk.registers(), M)
+
+
+def test_pick_ties_lowest_id_and_exclusion(im, ctx):
+    g = GRAPHS["isolated"]
+    G = im.im_graph_load(ctx, g.rowptr, g.col, MODELS["p30"])
+    J = 64
+    sk = im.im_sketch_build(G, J, 1)
+    M = np.zeros((g.n, J), np.uint8)
+    M[[7, 3, 50], :] = 5   # three-way tie at the best estimate: 3 < 7 < 50
+    M[60, :] = 4
+    M[61, : J // 2] = 0xFF  # visited registers count like rank 0
+    sk.set_registers(M)
+    assert [sk.pick()[0] for _ in range(4)] == [3, 7, 50, 60]
+    # everything else ties at S = J * 2^32 (all zero or visited): lowest id not yet picked
+    assert sk.pick()[0] == 0 and sk.pick()[0] == 1 and sk.pick()[0] == 2 and sk.pick()[0] == 4
+
+
+def test_sums_extremes(im, ctx):
+    g = GRAPHS["isolated"]
+    G = im.im_graph_load(ctx, g.rowptr, g.col, MODELS["p30"])
+    J = 1024
+    sk = im.im_sketch_build(G, J, 1)
+    M = np.zeros((g.n, J), np.uint8)
+    M[1] = 32
+    M[2] = 0xFF
+    M[3, ::2] = 31
+    sk.set_registers(M)
+    S = sk.sums()
+    assert S[0] == J * 2**32 and S[1] == J and S[2] == J * 2**32
+    assert S[3] == (J // 2) * 2 + (J // 2) * 2**32
+    assert np.array_equal(S, O.sums(M))
+
+
+# --- the whole method (Alg. 4) -------------------------------------------------------
+
+SELECT_CASES = [
+    ("er2k", "p30", 64, 8, 0.01), ("er2k", "p01", 128, 6, 0.0), ("rmat12", "wc", 256, 12, 0.01),
+    ("rmat12", "tri", 512, 6, 0.01), ("cl5k", "wc", 64, 10, -1.0), ("cl5k", "p30", 1024, 5, 0.01),
+    ("isolated", "p1", 16, 100, 0.01), ("single", "p30", 32, 1, 0.01), ("path", "p30", 32, 40, 0.01),
+]
+
+
+@pytest.mark.parametrize("gname,mname,J,K,eps", SELECT_CASES)
+def test_select_seeds_matches_oracle(im, ctx, gname, mname, J, K, eps):
+    g = GRAPHS[gname]
+    model = MODELS[mname]
+    G = im.im_graph_load(ctx, g.rowptr, g.col, model)
+    r = im.im_select_seeds(G, K, J, seed=123, rebuild_eps=eps, return_sketch=True)
+    ref = O.select_seeds(g, O.thresholds(g, model), J, K, 123, eps, "reverse")
+    assert r["seeds"].tolist() == ref["seeds"].tolist()
+    assert np.array_equal(r["score"], ref["score"])
+    np.testing.assert_allclose(r["est"], ref["est"], rtol=1e-12, atol=0)
+    assert np.array_equal(r["sketch"].registers(), ref["M"])
+    st = im.im_last_stats(ctx)
+    assert st["builds"] == 1 + ref["rebuilds"]
+    assert st["visited"] == int((ref["M"] == 0xFF).sum())
+
+
+def test_select_seeds_model_override(im, ctx):
+    g = GRAPHS["rmat12"]
+    G = im.im_graph_load(ctx, g.rowptr, g.col, MODELS["wc"])
+    r = im.im_select_seeds(G, 5, 64, model=MODELS["p30"], seed=9)
+    ref = O.select_seeds(g, O.thresholds(g, MODELS["p30"]), 64, 5, 9, 0.01, "reverse")
+    assert r["seeds"].tolist() == ref["seeds"].tolist()
+    # the override lasts for that call only
+    r2 = im.im_select_seeds(G, 5, 64, seed=9)
+    ref2 = O.select_seeds(g, O.thresholds(g, MODELS["wc"]), 64, 5, 9, 0.01, "reverse")
+    assert r2["seeds"].tolist() == ref2["seeds"].tolist()
+
+
+def test_select_seeds_explicit(im, ctx):
+    g = GRAPHS["cl5k"]
+    model = {"kind": "explicit", "w": W.edge_weights(g.m, "uniform", 0.0, 0.1, seed=4)}
+    G = im.im_graph_load(ctx, g.rowptr, g.col, model)
+    r = im.im_select_seeds(G, 8, 256, seed=4)
+    ref = O.select_seeds(g, O.thresholds(g, model), 256, 8, 4, 0.01, "reverse")
+    assert r["seeds"].tolist() == ref["seeds"].tolist()
+    assert np.array_equal(r["score"], ref["score"])
+
+
+def test_tiny_workload_golden(im, ctx):
+    gold = json.load(open(os.path.join(GOLDEN, "select_er10k.json")))
+    wl = W.workload("er10k")
+    g = wl.graph()
+    G = im.im_graph_load(ctx, g.rowptr, g.col, wl.model)
+    r = im.im_select_seeds(G, wl.K, wl.J, seed=wl.seed, rebuild_eps=wl.rebuild_eps)
+    assert r["seeds"].tolist() == gold["seeds"]
+    assert r["score"].tolist() == gold["score"]
+    np.testing.assert_allclose(r["est"], [float.fromhex(x) for x in gold["est"]], rtol=1e-12)
+
+
+# --- Monte-Carlo spread ----------------------------------------------------------------
+
+@pytest.mark.parametrize("gname,mname,R", [("er2k", "p30", 1000), ("rmat12", "wc", 333),
+                                           ("cl5k", "tri", 2048), ("path", "p30", 40)])
+def test_spread_mc_matches_oracle_coins(im, ctx, gname, mname, R):
+    g = GRAPHS[gname]
+    model = MODELS[mname]
+    G = im.im_graph_load(ctx, g.rowptr, g.col, model)
+    seeds = [0, 1, 2, 2]
+    r = im.im_spread_mc(G, seeds, R, seed=17)
+    s, sq = O.spread_ic(g, O.thresholds(g, model), seeds, R, seed=17)
+    assert (r["sum"], r["sumsq"]) == (s, sq)
+
+
+def test_spread_mc_vs_standard_rng(im, ctx):
+    g = GRAPHS["er2k"]
+    model = MODELS["p30"]
+    G = im.im_graph_load(ctx, g.rowptr, g.col, {"kind": "uniform", "p": 0.05})
+    seeds = [10, 20, 30]
+    r = im.im_spread_mc(G, seeds, 4096, seed=3)
+    src = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    m2, se2 = mc.spread(g.n, src, g.col, np.full(g.m, np.float32(0.05)), seeds, 2000, seed=8)
+    assert abs(r["mean"] - m2) < 3 * np.sqrt(r["stderr"] ** 2 + se2**2)
+    del model
+
+
+def test_spread_mc_closed_forms(im, ctx):
+    g = W.from_edges(2, [(0, 1)])
+    for p in (0.01, 0.3):
+        G = im.im_graph_load(ctx, g.rowptr, g.col, {"kind": "uniform", "p": p})
+        r = im.im_spread_mc(G, [0], 100_000, seed=5)
+        assert abs(r["mean"] - (1 + p)) < 4 * r["stderr"]
+    G = im.im_graph_load(ctx, g.rowptr, g.col, {"kind": "explicit", "w": np.array([0.19], np.float32)})
+    r = im.im_spread_mc(G, [0], 100_000, seed=6)
+    assert abs(r["mean"] - 1.19) < 4 * r["stderr"]  # the merged-edge example of Sec. 2.1
+
+
+# --- errors ------------------------------------------------------------------------------
+
+def test_errors(im, ctx):
+    g = GRAPHS["er2k"]
+    G = im.im_graph_load(ctx, g.rowptr, g.col, MODELS["p30"])
+    with pytest.raises(im.IMError) as e:
+        im.im_select_seeds(G, g.n + 1, 64)
+    assert e.value.status == -2
+    with pytest.raises(im.IMError) as e:
+        im.im_sketch_build(G, 48, 1)
+    assert e.value.status == -1
+    bad = g.col.copy()
+    bad[5] = bad[4]  # duplicate edge
+    with pytest.raises(im.IMError) as e:
+        im.im_graph_load(ctx, g.rowptr, bad, MODELS["p30"])
+    assert e.value.status == -1
+    small = im.im_ctx_create(0, hbm_budget_bytes=1 << 16)
+    with pytest.raises(im.IMError) as e:
+        im.im_graph_load(small, g.rowptr, g.col, MODELS["p30"])
+    assert e.value.status == -3
+    assert im.im_ctx_bytes_in_use(small) == 0
