@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--workload", default="rmat20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--mode", default="select", choices=["select", "build"],
+                    help="select: the benchmark; build: time im_sketch_build only (profiling)")
+    ap.add_argument("--quick", action="store_true",
+                    help="profiling runs: no clock sampling, end-to-end pass or CPU baseline")
     return ap.parse_args()
 
 
@@ -198,19 +202,38 @@ def run_gpu(args):
     G = im.im_graph_load(ctx, g.rowptr, g.col, wl.model)
     im.im_ctx_set_timing(ctx, True)
 
+    if args.mode == "build":
+        # profiling mode: sketch builds only (fill + propagation to the fixpoint)
+        for _ in range(args.warmup):
+            im.im_sketch_build(G, wl.J, wl.seed).free()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            im.im_sketch_build(G, wl.J, wl.seed).free()
+        torch.cuda.synchronize()
+        if rank == 0:
+            st = im.im_last_stats(ctx)
+            print(json.dumps({"mode": "build", "workload": wl.name, "steps": args.steps,
+                              "ms_per_build": (time.perf_counter() - t0) / max(args.steps, 1) * 1e3,
+                              "sweeps": st["sweeps"], "ms_propagate": st["ms_propagate"]}), flush=True)
+        return 0
+
     def step():
         return im.im_select_seeds(G, wl.K, wl.J, seed=wl.seed, rebuild_eps=wl.rebuild_eps)
 
     ref_seeds = None
     for _ in range(args.warmup):
         ref_seeds = step()["seeds"].tolist()
+    if ref_seeds is None:
+        ref_seeds = step()["seeds"].tolist()
 
     stream = torch.cuda.current_stream()
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(local) if not args.quick else None
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    sampler.start()
+    if sampler:
+        sampler.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     agg = {"alg_bytes_sweep": 0, "ms_propagate": 0.0, "sweep_launches": 0, "launches": 0,
            "builds": 0, "sweeps": 0, "ms_pick_kernels": 0.0, "ms_cover_kernels": 0.0,
@@ -228,7 +251,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clocks = sampler.stop()
+    clocks = sampler.stop() if sampler else None
     elapsed = ev0.elapsed_time(ev1) / 1e3
     t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
     if dist:
@@ -244,7 +267,7 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     e0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    for _ in range(0 if args.quick else args.e2e_steps):
         G2 = im.im_graph_load(ctx, rp_np, col_np, wl.model)
         r2 = im.im_select_seeds(G2, wl.K, wl.J, seed=wl.seed, rebuild_eps=wl.rebuild_eps)
         G2.free()
@@ -286,14 +309,14 @@ def run_gpu(args):
             "counts_per_step": {k: agg[k] / args.steps for k in
                                 ("builds", "sweeps", "sweep_launches", "cover_levels", "launches")},
             "gpu_launches": int(agg["launches"]),
-            "e2e": {"value": world * args.e2e_steps / e_max, "unit": UNIT,
+            "e2e": {"value": (world * args.e2e_steps / e_max) if not args.quick else None, "unit": UNIT,
                     "h2d_bytes_per_step": int(g.rowptr.nbytes + g.col.nbytes),
                     "d2h_bytes_per_step": int(wl.K * (4 + 8 + 8))},
             "clocks": clocks,
             "deterministic": bool(deterministic),
             "seeds_match_oracle_golden": golden,
         }
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and not args.quick:
             out["cpu_baseline"] = cpu_baseline(wl, g)
         print(json.dumps(out), flush=True)
     if dist:

@@ -104,7 +104,32 @@ typedef struct {
     uint64_t cover_chunks;    /* 16-simulation chunks examined by cover levels */
     uint64_t visited;         /* registers visited at the end (Count(M,-1)) */
     uint64_t alg_bytes_sweep; /* algorithmic bytes of all sweeps (see the design notes) */
+    uint64_t sweep_heavy;     /* hub vertices pushed by per-simulation hash search */
+    uint64_t sweep_heavy_sims;/* (hub, changed simulation) searches */
 } im_stats;
+
+/* Schedule knobs of the frontier kernels (chosen by the autotuner; results
+ * do not depend on them).  heavy_indeg: in-degree above which a vertex whose
+ * in-edges share one threshold below 2^26 (weighted cascade, small uniform p)
+ * is pushed by per-simulation hash search instead of an in-edge scan;
+ * light_batches: 32-edge batches a warp claims at once; grid_blocks: blocks
+ * per frontier launch (0 = SM count x occupancy); check_every: frontier
+ * launches between the host's first two emptiness checks (then doubling to 8). */
+typedef struct {
+    int32_t heavy_indeg;
+    int32_t light_batches;
+    int32_t grid_blocks;
+    int32_t check_every;
+} im_tuning;
+
+/* One frontier launch of the last selection / build (tracing on). */
+typedef struct {
+    int32_t kind;    /* 0 = propagation sweep (Alg. 2), 1 = cover level (Alg. 3) */
+    int32_t level;   /* level index within its phase */
+    int64_t count;   /* queued vertices the launch processed */
+    int64_t edges;   /* edges of those vertices (in-edges for sweeps, out-edges for covers) */
+    double ms;       /* kernel time, CUDA events on the context's stream */
+} im_trace_rec;
 
 /* ---- context ----------------------------------------------------------- */
 
@@ -127,6 +152,14 @@ IM_API im_status im_last_stats(const im_ctx* ctx, im_stats* out);
  * stream and report per-kind kernel time in im_stats (adds two event records
  * per launch).  Off by default. */
 IM_API im_status im_ctx_set_timing(im_ctx* ctx, int enable);
+/* Sets (NULL = defaults {64, 4, 0, 2}) or reads the schedule knobs. */
+IM_API im_status im_ctx_set_tuning(im_ctx* ctx, const im_tuning* tuning);
+IM_API im_status im_ctx_get_tuning(const im_ctx* ctx, im_tuning* tuning);
+/* enable != 0: also keep one im_trace_rec per frontier launch (implies timing). */
+IM_API im_status im_ctx_set_trace(im_ctx* ctx, int enable);
+/* Copies up to `cap` trace records of the last selection / build into `out`
+ * (may be NULL to query); returns the number of records available. */
+IM_API int64_t im_last_trace(const im_ctx* ctx, im_trace_rec* out, int64_t cap);
 
 /* ---- graph ------------------------------------------------------------- */
 

@@ -24,7 +24,9 @@ STATUS = {0: "IM_OK", -1: "IM_E_INVAL", -2: "IM_E_RANGE", -3: "IM_E_NOMEM", -4: 
 
 # Every symbol the C header declares, for the load check.
 EXPORTS = ["im_ctx_create", "im_ctx_destroy", "im_ctx_bytes_in_use", "im_ctx_bytes_peak",
-           "im_last_error", "im_status_str", "im_last_stats", "im_ctx_set_timing", "im_graph_load", "im_graph_free",
+           "im_last_error", "im_status_str", "im_last_stats", "im_ctx_set_timing",
+           "im_ctx_set_trace", "im_last_trace", "im_ctx_set_tuning", "im_ctx_get_tuning",
+           "im_graph_load", "im_graph_free",
            "im_graph_info", "im_sketch_build", "im_sketch_free", "im_sketch_registers",
            "im_sketch_set_registers", "im_sketch_sims", "im_sketch_sums", "im_sketch_pick",
            "im_sketch_cover", "im_sketch_rebuild", "im_select_seeds", "im_spread_mc"]
@@ -57,7 +59,18 @@ class im_stats(ctypes.Structure):
                                               "cover_levels")] + \
                [(k, ctypes.c_uint64) for k in ("sweep_vertices", "sweep_edges", "sweep_chunks",
                                                "sweep_cas", "sweep_changed", "cover_edges",
-                                               "cover_chunks", "visited", "alg_bytes_sweep")]
+                                               "cover_chunks", "visited", "alg_bytes_sweep",
+                                               "sweep_heavy", "sweep_heavy_sims")]
+
+
+class im_tuning(ctypes.Structure):
+    _fields_ = [("heavy_indeg", ctypes.c_int32), ("light_batches", ctypes.c_int32),
+                ("grid_blocks", ctypes.c_int32), ("check_every", ctypes.c_int32)]
+
+
+class im_trace_rec(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("count", ctypes.c_int64),
+                ("edges", ctypes.c_int64), ("ms", ctypes.c_double)]
 
 
 _lib = None
@@ -82,6 +95,10 @@ def load_library(path: str = LIB_PATH):
         "im_status_str": (ctypes.c_char_p, [ctypes.c_int]),
         "im_last_stats": (ctypes.c_int, [vp, P(im_stats)]),
         "im_ctx_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
+        "im_ctx_set_trace": (ctypes.c_int, [vp, ctypes.c_int]),
+        "im_last_trace": (i64, [vp, P(im_trace_rec), i64]),
+        "im_ctx_set_tuning": (ctypes.c_int, [vp, P(im_tuning)]),
+        "im_ctx_get_tuning": (ctypes.c_int, [vp, P(im_tuning)]),
         "im_graph_load": (ctypes.c_int, [vp, i32, i64, P(i32), P(i32), P(im_model), P(vp)]),
         "im_graph_free": (None, [vp]),
         "im_graph_info": (ctypes.c_int, [vp, P(i32), P(i64)]),
@@ -325,6 +342,39 @@ def im_last_stats(ctx: Context) -> dict:
 
 def im_ctx_set_timing(ctx: Context, enable: bool = True):
     ctx.check(ctx.lib.im_ctx_set_timing(ctx.handle, 1 if enable else 0))
+
+
+def im_ctx_set_tuning(ctx: Context, tuning: dict | None = None):
+    """Schedule knobs (heavy_indeg, light_batches, grid_blocks, check_every); None = defaults."""
+    if tuning is None:
+        ctx.check(ctx.lib.im_ctx_set_tuning(ctx.handle, None))
+        return
+    t = im_tuning()
+    cur = im_ctx_get_tuning(ctx)
+    cur.update(tuning)
+    for k, _ in im_tuning._fields_:
+        setattr(t, k, int(cur[k]))
+    ctx.check(ctx.lib.im_ctx_set_tuning(ctx.handle, ctypes.byref(t)))
+
+
+def im_ctx_get_tuning(ctx: Context) -> dict:
+    t = im_tuning()
+    ctx.check(ctx.lib.im_ctx_get_tuning(ctx.handle, ctypes.byref(t)))
+    return {k: getattr(t, k) for k, _ in im_tuning._fields_}
+
+
+def im_ctx_set_trace(ctx: Context, enable: bool = True):
+    ctx.check(ctx.lib.im_ctx_set_trace(ctx.handle, 1 if enable else 0))
+
+
+def im_last_trace(ctx: Context) -> np.ndarray:
+    """Per-launch records of the last call: structured array (kind, level, count, edges, ms)."""
+    n = int(ctx.lib.im_last_trace(ctx.handle, None, 0))
+    buf = (im_trace_rec * max(n, 1))()
+    ctx.lib.im_last_trace(ctx.handle, buf, n)
+    dt = np.dtype([("kind", np.int32), ("level", np.int32), ("count", np.int64),
+                   ("edges", np.int64), ("ms", np.float64)])
+    return np.frombuffer(bytes(buf), dtype=dt, count=n).copy()
 
 
 def im_ctx_bytes_in_use(ctx: Context) -> int:

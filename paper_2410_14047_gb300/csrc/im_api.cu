@@ -5,6 +5,7 @@
 // the kernels of im_kernels.cu through Alg. 4 of the paper: build
 // (Alg. 1 + Alg. 2 to a fixpoint), then K times pick (Sketchwise-Sum +
 // argmax), cover (Alg. 3 levels) and the error-adaptive rebuild.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -35,7 +36,13 @@ struct im_ctx {
     bool timing = false;
     std::vector<cudaEvent_t> ev;
     std::vector<int> ev_kind;
+    std::vector<int64_t> ev_seq;     // launch sequence number of each recorded pair
     int ev_used = 0;
+    int64_t seq = 0;                 // launches since the start of the call
+    bool trace = false;
+    std::vector<float> launch_ms;    // kernel time per launch sequence number (tracing)
+    std::vector<im_trace_rec> recs;  // frontier launches of the last call
+    im_tuning tuning{64, 4, 0, 2};
 };
 
 namespace {
@@ -146,6 +153,11 @@ void timing_collect(im_ctx* c) {
             (void)cudaGetLastError();
             continue;
         }
+        if (c->trace) {
+            const int64_t q = c->ev_seq[i];
+            if ((int64_t)c->launch_ms.size() <= q) c->launch_ms.resize(q + 1024, 0.f);
+            c->launch_ms[q] = ms;
+        }
         switch (c->ev_kind[i]) {
             case kTPush: c->stats.ms_propagate += ms; break;
             case kTCover: c->stats.ms_cover_kernels += ms; break;
@@ -170,11 +182,13 @@ cudaError_t timed(im_ctx* c, int kind, F&& launch) {
         }
         slot = c->ev_used++;
         c->ev_kind[slot] = kind;
+        c->ev_seq[slot] = c->seq;
         cudaEventRecord(c->ev[2 * slot], c->stream);
     }
     cudaError_t e = launch();
     if (slot >= 0) cudaEventRecord(c->ev[2 * slot + 1], c->stream);
     c->stats.launches++;
+    c->seq++;
     if (kind == kTPush) c->stats.sweep_launches++;
     return e;
 }
@@ -193,14 +207,15 @@ struct im_graph {
     int32_t n = 0;
     int64_t m = 0;
     int kind = kUniform;
-    DBuf rp_out, col_out, rp_in, src_in, thr_v, thr_out, thr_in, q_all, ctr_all;
+    DBuf rp_out, col_out, rp_in, src_in, h_in, thr_v, thr_out, thr_in, cls_split;
     GraphDev dev{};
 };
 
 struct im_sketch {
     im_graph* g = nullptr;
     int32_t J = 0;
-    DBuf M, X, salt, tab, q[3], ctr, gen, seed_bits, count, part_S, part_u, ticket, stats, err;
+    DBuf M, X, salt, tab, ql[3], qh[3], ctr, claim, chg[3], gen, seed_bits, count, part_S, part_u,
+        ticket, stats, err;
     DBuf out_seed, out_S, out_est;
     int32_t out_cap = 0;
     int32_t gen_counter = 0;
@@ -249,12 +264,46 @@ extern "C" im_status im_ctx_set_timing(im_ctx* c, int enable) {
     if (enable && c->ev.empty()) {
         c->ev.resize(256);
         c->ev_kind.resize(128);
+        c->ev_seq.resize(128);
         for (auto& e : c->ev) CK(c, cudaEventCreate(&e));
     }
     CK(c, cudaStreamSynchronize(c->stream));
     c->ev_used = 0;
-    c->timing = enable != 0;
+    c->timing = enable != 0 || c->trace;
     return IM_OK;
+}
+
+extern "C" im_status im_ctx_set_tuning(im_ctx* c, const im_tuning* t) {
+    if (!c) return IM_E_INVAL;
+    if (!t) {
+        c->tuning = im_tuning{64, 4, 0, 2};
+        return IM_OK;
+    }
+    if (t->heavy_indeg < 0 || t->light_batches < 1 || t->light_batches > 4096 || t->grid_blocks < 0 ||
+        t->check_every < 1 || t->check_every > 64)
+        return fail(c, IM_E_INVAL, "tuning out of range");
+    c->tuning = *t;
+    return IM_OK;
+}
+
+extern "C" im_status im_ctx_get_tuning(const im_ctx* c, im_tuning* t) {
+    if (!c || !t) return IM_E_INVAL;
+    *t = c->tuning;
+    return IM_OK;
+}
+
+extern "C" im_status im_ctx_set_trace(im_ctx* c, int enable) {
+    if (!c) return IM_E_INVAL;
+    c->trace = enable != 0;
+    return im_ctx_set_timing(c, c->timing || c->trace);
+}
+
+extern "C" int64_t im_last_trace(const im_ctx* c, im_trace_rec* out, int64_t cap) {
+    if (!c) return 0;
+    const int64_t n = (int64_t)c->recs.size();
+    if (out)
+        for (int64_t i = 0; i < n && i < cap; ++i) out[i] = c->recs[i];
+    return n;
 }
 
 extern "C" uint64_t im_ctx_bytes_in_use(const im_ctx* c) { return c ? c->in_use : 0; }
@@ -296,8 +345,8 @@ static im_status check_model(im_ctx* c, const im_model* mdl, int64_t m) {
 
 static void graph_release(im_graph* g) {
     im_ctx* c = g->ctx;
-    for (DBuf* b : {&g->rp_out, &g->col_out, &g->rp_in, &g->src_in, &g->thr_v, &g->thr_out,
-                    &g->thr_in, &g->q_all, &g->ctr_all})
+    for (DBuf* b : {&g->rp_out, &g->col_out, &g->rp_in, &g->src_in, &g->h_in, &g->thr_v,
+                    &g->thr_out, &g->thr_in, &g->cls_split})
         dfree(c, *b);
 }
 
@@ -364,13 +413,14 @@ extern "C" im_status im_graph_load(im_ctx* c, int32_t n, int64_t m, const int32_
     if ((s = dalloc(c, e_bytes, g->col_out)) != IM_OK) return bail(s);
     if ((s = dalloc(c, rp_bytes, g->rp_in)) != IM_OK) return bail(s);
     if ((s = dalloc(c, e_bytes, g->src_in)) != IM_OK) return bail(s);
+    if ((s = dalloc(c, e_bytes, g->h_in)) != IM_OK) return bail(s);
     if ((s = dalloc(c, (size_t)n * 4, g->thr_v)) != IM_OK) return bail(s);
-    if ((s = dalloc(c, (size_t)n * sizeof(QEntry), g->q_all)) != IM_OK) return bail(s);
-    if ((s = dalloc(c, 8, g->ctr_all)) != IM_OK) return bail(s);
-    DBuf cnt, tmp, fill;
+    if (model->kind == kTrivalency && (s = dalloc(c, (size_t)n * 8, g->cls_split)) != IM_OK) return bail(s);
+    DBuf cnt, tmp;
     if ((s = dalloc(c, ((size_t)n + 1) * 4, cnt)) != IM_OK) return bail(s);
-    if ((s = dalloc(c, scan_tmp_bytes(n), tmp)) != IM_OK) { dfree(c, cnt); return bail(s); }
-    if ((s = dalloc(c, ((size_t)n + 1) * 4, fill)) != IM_OK) { dfree(c, cnt); dfree(c, tmp); return bail(s); }
+    const size_t tmp_bytes = std::max(scan_tmp_bytes(n), build_in_csr_tmp_bytes(m));
+    if ((s = dalloc(c, tmp_bytes, tmp)) != IM_OK) { dfree(c, cnt); return bail(s); }
+    auto release_tmp = [&]() { dfree(c, cnt); dfree(c, tmp); };
     auto st = c->stream;
     cudaError_t e = cudaMemcpyAsync(g->rp_out.p, rowptr, rp_bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && m > 0)
@@ -379,33 +429,18 @@ extern "C" im_status im_graph_load(im_ctx* c, int32_t n, int64_t m, const int32_
     if (e == cudaSuccess) e = launch_indegree(g->col_out.as<int32_t>(), m, cnt.as<int32_t>(), st);
     if (e == cudaSuccess) e = launch_exclusive_scan(cnt.as<int32_t>(), n, g->rp_in.as<int32_t>(), tmp.p, st);
     if (e == cudaSuccess) e = launch_thr_wc(g->rp_in.as<int32_t>(), n, g->thr_v.as<uint32_t>(), st);
-    if (e != cudaSuccess) { dfree(c, cnt); dfree(c, tmp); dfree(c, fill); return bail(cuda_fail(c, e, "graph load")); }
-    if ((s = set_model(g, model)) != IM_OK) { dfree(c, cnt); dfree(c, tmp); dfree(c, fill); return bail(s); }
+    if (e != cudaSuccess) { release_tmp(); return bail(cuda_fail(c, e, "graph load")); }
+    if ((s = set_model(g, model)) != IM_OK) { release_tmp(); return bail(s); }
     if (g->kind == kExplicit && m > 0) {
-        if ((s = dalloc(c, (size_t)m * 4, g->thr_in)) != IM_OK) { dfree(c, cnt); dfree(c, tmp); dfree(c, fill); return bail(s); }
+        if ((s = dalloc(c, (size_t)m * 4, g->thr_in)) != IM_OK) { release_tmp(); return bail(s); }
     }
-    e = cudaMemsetAsync(fill.p, 0, ((size_t)n + 1) * 4, st);
-    if (e == cudaSuccess)
-        e = launch_scatter_in(g->rp_out.as<int32_t>(), g->col_out.as<int32_t>(), n, g->rp_in.as<int32_t>(),
-                              fill.as<int32_t>(), g->src_in.as<int32_t>(), g->thr_out.as<uint32_t>(),
-                              g->thr_in.as<uint32_t>(), st);
-    // all-vertex queue: entries for vertices with in-edges, in id order
-    if (e == cudaSuccess) e = launch_flag_nonzero_in(g->rp_in.as<int32_t>(), n, cnt.as<int32_t>(), st);
-    if (e == cudaSuccess) e = launch_exclusive_scan(cnt.as<int32_t>(), n, fill.as<int32_t>(), tmp.p, st);
-    if (e == cudaSuccess)
-        e = launch_all_queue(g->rp_in.as<int32_t>(), n, g->thr_v.as<uint32_t>(), fill.as<int32_t>(),
-                             g->q_all.as<QEntry>(), st);
-    int32_t nq = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&nq, fill.as<int32_t>() + n, 4, cudaMemcpyDeviceToHost, st);
+    // in-CSR sorted by (target, class, edge hash): rows of equal-threshold in-edges in hash order
+    e = launch_build_in_csr(g->rp_out.as<int32_t>(), g->col_out.as<int32_t>(), n, m, g->kind,
+                            g->dev.tri_seed, g->thr_out.as<uint32_t>(), g->rp_in.as<int32_t>(),
+                            g->src_in.as<int32_t>(), g->h_in.as<uint32_t>(), g->thr_in.as<uint32_t>(),
+                            g->cls_split.as<int2>(), tmp.p, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess) {
-        const unsigned long long ctr = ((unsigned long long)nq << kCountShift) | (unsigned long long)m;
-        e = cudaMemcpyAsync(g->ctr_all.p, &ctr, 8, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    }
-    dfree(c, cnt);
-    dfree(c, tmp);
-    dfree(c, fill);
+    release_tmp();
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "graph load"));
     g->dev.n = n;
     g->dev.m = m;
@@ -413,6 +448,7 @@ extern "C" im_status im_graph_load(im_ctx* c, int32_t n, int64_t m, const int32_
     g->dev.col_out = g->col_out.as<int32_t>();
     g->dev.rp_in = g->rp_in.as<int32_t>();
     g->dev.src_in = g->src_in.as<int32_t>();
+    g->dev.h_in = g->h_in.as<uint32_t>();
     g->dev.thr_v = g->thr_v.as<uint32_t>();
     g->dev.thr_out = g->thr_out.as<uint32_t>();
     g->dev.thr_in = g->thr_in.as<uint32_t>();
@@ -438,9 +474,11 @@ extern "C" im_status im_graph_info(const im_graph* g, int32_t* n, int64_t* m) {
 // ---------------------------------------------------------------------------
 static void sketch_release(im_sketch* sk) {
     im_ctx* c = sk->g->ctx;
-    for (DBuf* b : {&sk->M, &sk->X, &sk->salt, &sk->tab, &sk->q[0], &sk->q[1], &sk->q[2], &sk->ctr,
-                    &sk->gen, &sk->seed_bits, &sk->count, &sk->part_S, &sk->part_u, &sk->ticket,
-                    &sk->stats, &sk->err, &sk->out_seed, &sk->out_S, &sk->out_est})
+    for (DBuf* b : {&sk->M, &sk->X, &sk->salt, &sk->tab, &sk->ql[0], &sk->ql[1], &sk->ql[2],
+                    &sk->qh[0], &sk->qh[1], &sk->qh[2], &sk->ctr, &sk->claim, &sk->chg[0],
+                    &sk->chg[1], &sk->chg[2], &sk->gen, &sk->seed_bits, &sk->count, &sk->part_S,
+                    &sk->part_u, &sk->ticket, &sk->stats, &sk->err, &sk->out_seed, &sk->out_S,
+                    &sk->out_est})
         dfree(c, *b);
 }
 
@@ -460,8 +498,11 @@ static im_status sketch_alloc(im_graph* g, int32_t J, im_sketch** out) {
     A(sk->X, (size_t)J * 4);
     A(sk->salt, (size_t)J * 4);
     A(sk->tab, (size_t)kTabSize * 2);
-    for (int i = 0; i < 3; ++i) A(sk->q[i], (size_t)n * sizeof(QEntry));
-    A(sk->ctr, (size_t)(kMaxLevels + 2) * 8);
+    for (int i = 0; i < 3; ++i) A(sk->ql[i], (size_t)n * sizeof(QEntry));
+    for (int i = 0; i < 3; ++i) A(sk->qh[i], (size_t)n * sizeof(QEntry));
+    A(sk->ctr, (size_t)(kMaxLevels + 2) * 16);
+    A(sk->claim, (size_t)(kMaxLevels + 2) * 4);
+    for (int i = 0; i < 3; ++i) A(sk->chg[i], (size_t)n * ((J + 31) / 32) * 4);
     A(sk->gen, (size_t)n * 4);
     A(sk->seed_bits, (((size_t)n + 31) / 32) * 4);
     A(sk->count, 8);
@@ -511,16 +552,21 @@ static im_status ensure_out_cap(im_sketch* sk, int32_t K) {
     return IM_OK;
 }
 
-static FrontierArgs frontier_args(im_sketch* sk) {
-    FrontierArgs a{};
+static LevelArgs level_args(im_sketch* sk) {
+    LevelArgs a{};
     a.M = sk->M.as<uint8_t>();
     a.J = sk->J;
+    a.words = (sk->J + 31) / 32;
     a.X = sk->X.as<uint32_t>();
     a.tab = sk->tab.as<uint16_t>();
     a.gen = sk->gen.as<int32_t>();
     a.count = sk->count.as<unsigned long long>();
     a.stats = sk->stats.as<unsigned long long>();
     a.err = sk->err.as<uint32_t>();
+    const im_tuning& t = sk->g->ctx->tuning;
+    // the heavy path reads 32 register bytes per lane: J >= 32 only
+    a.heavy_indeg = sk->J >= 32 ? t.heavy_indeg : 0x7FFFFFFF;
+    a.light_batches = t.light_batches > 0 ? t.light_batches : 4;
     return a;
 }
 
@@ -529,48 +575,89 @@ static im_status check_err(im_sketch* sk) {
     im_ctx* c = sk->g->ctx;
     uint32_t err = 0;
     CK(c, cudaMemcpyAsync(&err, sk->err.p, 4, cudaMemcpyDeviceToHost, c->stream));
-    CK(c, cudaStreamSynchronize(c->stream));
+    CK(c, sync_collect(c));
     if (err & kErrQueue) return fail(c, IM_E_STATE, "frontier queue overflow");
     if (err & kErrCasLimit) return fail(c, IM_E_TIMEOUT, "register CAS retry limit exceeded");
     return IM_OK;
 }
 
+// Start of a propagation or cover phase: level counters, work counters and
+// change masks back to zero.
+static im_status phase_begin(im_sketch* sk) {
+    im_ctx* c = sk->g->ctx;
+    auto st = c->stream;
+    CK(c, cudaMemsetAsync(sk->ctr.p, 0, sk->ctr.bytes, st));
+    CK(c, cudaMemsetAsync(sk->claim.p, 0, sk->claim.bytes, st));
+    for (int i = 0; i < 3; ++i) CK(c, cudaMemsetAsync(sk->chg[i].p, 0, sk->chg[i].bytes, st));
+    return IM_OK;
+}
 
-// Runs frontier levels until the queue is empty.  Level t reads (q_in, ctr_in)
-// and writes queue q[t & 1] and counter ctr[t + 1].  The host reads the newest
-// counter every `check` levels (2, 4, then 8); levels launched after the
-// queue emptied see an empty queue and return at once.
-static im_status run_levels(im_sketch* sk, int mode, const QEntry* q0,
-                            const unsigned long long* c0) {
+// Runs frontier levels until both queues are empty.  Level t reads queue
+// t % 3 with counters ctr[t], writes queue (t+1) % 3 with counters ctr[t+1],
+// and clears the change bits of queue (t+2) % 3 (read by level t-1).  The host
+// reads the newest counters every `check` levels; levels launched after the
+// queues emptied see empty queues and return at once.
+static im_status run_levels(im_sketch* sk, int mode, bool all_first) {
     im_graph* g = sk->g;
     im_ctx* c = g->ctx;
     auto st = c->stream;
-    unsigned long long* ctr = sk->ctr.as<unsigned long long>();
-    CK(c, cudaMemsetAsync(ctr + 1, 0, (size_t)(kMaxLevels + 1) * 8, st));
-    FrontierArgs a = frontier_args(sk);
-    const int grid = frontier_grid();
-    const QEntry* qin = q0;
-    const unsigned long long* cin = c0;
-    int check = 2;
+    ulonglong2* ctr = sk->ctr.as<ulonglong2>();
+    unsigned int* claim = sk->claim.as<unsigned int>();
+    LevelArgs a = level_args(sk);
+    const int grid = c->tuning.grid_blocks > 0 ? c->tuning.grid_blocks : level_grid();
+    int check = c->tuning.check_every > 0 ? c->tuning.check_every : 2;
     int64_t t = 0;
+    const int64_t seq0 = c->seq;
     for (;;) {
-        a.q_in = qin;
-        a.ctr_in = cin;
-        a.q_out = sk->q[t & 1].as<QEntry>();
-        a.ctr_out = ctr + t + 1;
+        const int bi = (int)(t % 3), bo = (int)((t + 1) % 3), bp = (int)((t + 2) % 3);
+        a.ql_in = sk->ql[bi].as<QEntry>();
+        a.cl_in = &ctr[t].x;
+        a.qh_in = sk->qh[bi].as<QEntry>();
+        a.ch_in = mode == kPush ? &ctr[t].y : nullptr;
+        a.ql_out = sk->ql[bo].as<QEntry>();
+        a.cl_out = &ctr[t + 1].x;
+        a.qh_out = sk->qh[bo].as<QEntry>();
+        a.ch_out = &ctr[t + 1].y;
+        if (t >= 1) {
+            a.ql_prev = sk->ql[bp].as<QEntry>();
+            a.cl_prev = &ctr[t - 1].x;
+            a.qh_prev = sk->qh[bp].as<QEntry>();
+            a.ch_prev = mode == kPush ? &ctr[t - 1].y : nullptr;
+            a.chg_prev = sk->chg[bp].as<uint32_t>();
+        } else {
+            a.ql_prev = nullptr; a.cl_prev = nullptr; a.qh_prev = nullptr; a.ch_prev = nullptr;
+            a.chg_prev = nullptr;
+        }
+        a.chg_cur = sk->chg[bi].as<uint32_t>();
+        a.chg_next = sk->chg[bo].as<uint32_t>();
+        a.all_changed = (t == 0 && all_first) ? 1 : 0;
+        a.claim = claim + t;
         a.gen_next = ++sk->gen_counter;
         CK(c, timed(c, mode == kPush ? kTPush : kTCover,
-                    [&] { return launch_frontier(g->kind, mode, g->dev, a, grid, st); }));
-        qin = a.q_out;
-        cin = a.ctr_out;
+                    [&] { return launch_level(g->kind, mode, g->dev, a, grid, st); }));
         ++t;
         if (t % check == 0) {
-            CK(c, cudaMemcpyAsync(c->pinned, ctr + t, 8, cudaMemcpyDeviceToHost, st));
+            CK(c, cudaMemcpyAsync(c->pinned, &ctr[t], 16, cudaMemcpyDeviceToHost, st));
             CK(c, sync_collect(c));
-            if ((c->pinned[0] >> kCountShift) == 0) break;
-            if (t + 8 >= kMaxLevels)
+            if ((c->pinned[0] >> kCountShift) == 0 && (c->pinned[1] >> kCountShift) == 0) break;
+            if (t + 16 >= kMaxLevels)
                 return fail(c, IM_E_TIMEOUT, "frontier did not empty within %d levels", kMaxLevels);
             if (check < 8) check *= 2;
+        }
+    }
+    if (c->trace) {
+        std::vector<ulonglong2> h((size_t)t);
+        CK(c, cudaMemcpyAsync(h.data(), ctr, (size_t)t * 16, cudaMemcpyDeviceToHost, st));
+        CK(c, sync_collect(c));
+        for (int64_t l = 0; l < t; ++l) {
+            im_trace_rec r{};
+            r.kind = mode;
+            r.level = (int32_t)l;
+            r.count = (int64_t)(h[l].x >> kCountShift) + (int64_t)(h[l].y >> kCountShift);
+            r.edges = (int64_t)(h[l].x & kEdgeMask) + (int64_t)(h[l].y & kEdgeMask);
+            const int64_t q = seq0 + l;
+            r.ms = q < (int64_t)c->launch_ms.size() ? c->launch_ms[q] : 0.0;
+            c->recs.push_back(r);
         }
     }
     return check_err(sk);
@@ -578,7 +665,16 @@ static im_status run_levels(im_sketch* sk, int mode, const QEntry* q0,
 
 static im_status propagate(im_sketch* sk) {
     im_graph* g = sk->g;
-    return run_levels(sk, kPush, g->q_all.as<QEntry>(), g->ctr_all.as<unsigned long long>());
+    im_ctx* c = g->ctx;
+    CKS(phase_begin(sk));
+    LevelArgs a = level_args(sk);
+    ulonglong2* ctr = sk->ctr.as<ulonglong2>();
+    a.ql_out = sk->ql[0].as<QEntry>();
+    a.cl_out = &ctr[0].x;
+    a.qh_out = sk->qh[0].as<QEntry>();
+    a.ch_out = &ctr[0].y;
+    CK(c, timed(c, kTOther, [&] { return launch_init_queues(g->kind, g->dev, a, c->stream); }));
+    return run_levels(sk, kPush, true);
 }
 
 // Fill (Alg. 1) of the non-visited registers, then Simulate to the fixpoint.
@@ -593,6 +689,9 @@ static im_status build_registers(im_sketch* sk) {
 static void stats_begin(im_ctx* c) {
     memset(&c->stats, 0, sizeof c->stats);
     c->ev_used = 0;
+    c->seq = 0;
+    c->recs.clear();
+    c->launch_ms.clear();
 }
 
 static im_status stats_collect(im_sketch* sk) {
@@ -613,6 +712,8 @@ static im_status stats_collect(im_sketch* sk) {
     s.cover_edges = h[kStCoverEdges];
     s.cover_chunks = h[kStCoverChunks];
     s.visited = cnt;
+    s.sweep_heavy = h[kStSweepHeavy];
+    s.sweep_heavy_sims = h[kStSweepHeavySims];
     // algorithmic bytes of the sweeps: queue entry (16 B) + the queued vertex's
     // register row (J B) per queued vertex, source id (4 B, + 4 B threshold for
     // explicit weights) per in-edge, one 16-byte target chunk read per chunk
@@ -726,8 +827,9 @@ static PickArgs pick_args(im_sketch* sk, int k) {
     a.out_est = sk->out_est.as<double>();
     a.k = k;
     a.rp_out = sk->g->rp_out.as<int32_t>();
-    a.q_cover = sk->q[2].as<QEntry>();
-    a.ctr_cover = sk->ctr.as<unsigned long long>();
+    a.q_cover = sk->ql[0].as<QEntry>();
+    a.ctr_cover = &sk->ctr.as<ulonglong2>()[0].x;
+    a.chg0 = sk->chg[0].as<uint32_t>();
     a.count = sk->count.as<unsigned long long>();
     a.mark = 1;
     return a;
@@ -736,9 +838,10 @@ static PickArgs pick_args(im_sketch* sk, int k) {
 // Pick (estimate + argmax) followed by the cover of the picked vertex.
 static im_status pick_and_cover(im_sketch* sk, int k) {
     im_ctx* c = sk->g->ctx;
+    CKS(phase_begin(sk));
     const PickArgs a = pick_args(sk, k);
     CK(c, timed(c, kTPick, [&] { return launch_pick(a, c->stream); }));
-    return run_levels(sk, kCover, sk->q[2].as<QEntry>(), sk->ctr.as<unsigned long long>());
+    return run_levels(sk, kCover, false);
 }
 
 extern "C" im_status im_sketch_pick(im_sketch* sk, int32_t* s_out, uint64_t* S_out, double* est_out) {
@@ -768,10 +871,11 @@ extern "C" im_status im_sketch_cover(im_sketch* sk, int32_t s, uint64_t* count_o
     if (!sk) return IM_E_INVAL;
     im_ctx* c = sk->g->ctx;
     if (s < 0 || s >= sk->g->n) return fail(c, IM_E_RANGE, "vertex %d out of range", s);
-    unsigned long long* ctr = sk->ctr.as<unsigned long long>();
+    CKS(phase_begin(sk));
     CK(c, launch_cover_seed(sk->M.as<uint8_t>(), sk->J, s, sk->g->rp_out.as<int32_t>(),
-                            sk->q[2].as<QEntry>(), ctr, sk->count.as<unsigned long long>(), c->stream));
-    CKS(run_levels(sk, kCover, sk->q[2].as<QEntry>(), ctr));
+                            sk->ql[0].as<QEntry>(), &sk->ctr.as<ulonglong2>()[0].x,
+                            sk->chg[0].as<uint32_t>(), sk->count.as<unsigned long long>(), c->stream));
+    CKS(run_levels(sk, kCover, false));
     if (count_out) {
         unsigned long long cnt = 0;
         CK(c, cudaMemcpyAsync(&cnt, sk->count.p, 8, cudaMemcpyDeviceToHost, c->stream));
@@ -904,7 +1008,7 @@ extern "C" im_status im_spread_mc(im_graph* g, const int32_t* seeds, int32_t k, 
     if (e == cudaSuccess) e = cudaMemsetAsync(acc.p, 0, 16, st);
     if (e != cudaSuccess) { release(); return cuda_fail(c, e, "spread init"); }
     unsigned long long* cp = ctr.as<unsigned long long>();
-    const int grid = frontier_grid();
+    const int grid = level_grid();
     int32_t stamp = 0;
     for (int64_t r0 = 0; r0 < R; r0 += B) {
         const int valid = (int)std::min<int64_t>(B, R - r0);

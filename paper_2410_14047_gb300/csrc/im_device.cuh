@@ -33,7 +33,8 @@ struct GraphDev {
     const int32_t* rp_out;   // n+1, out-CSR row pointers
     const int32_t* col_out;  // m, out-neighbours
     const int32_t* rp_in;    // n+1, in-CSR row pointers
-    const int32_t* src_in;   // m, in-neighbours (sources of in-edges)
+    const int32_t* src_in;   // m, in-neighbours (sources of in-edges), rows sorted by (class, hash)
+    const uint32_t* h_in;    // m, edge hash hE(source, target) of every in-edge
     const uint32_t* thr_v;   // kWC: threshold of every edge into v
     const uint32_t* thr_out; // kExplicit: per out-edge threshold
     const uint32_t* thr_in;  // kExplicit: per in-edge threshold

@@ -1,0 +1,552 @@
+// Frontier kernels of the hot path (sm_103a): propagation sweeps (Alg. 2 as a
+// push from changed vertices) and cover levels (Alg. 3).
+//
+// Work of a level = a "light" queue, walked as a flat edge space (sum of the
+// queued vertices' degrees), plus, for propagation, a "heavy" queue of
+// in-degree hubs.  Warps claim units dynamically from one counter: first the
+// heavy vertices (longest first), then slices of `light_batches` 32-edge
+// batches.  Each queued vertex carries a change mask (one bit per
+// simulation): only simulations that changed at the previous level are pushed
+// (propagation) or expanded (cover).
+//
+// Light vertex, per in-edge (propagation) or out-edge (cover): lanes resolve
+// 32 edges (stored edge hash, threshold, candidate range of Eq. hash_prob over
+// the sorted X), then the batch's 16-simulation chunks that hold a changed
+// simulation are dealt to the lanes; a chunk moves 16 register bytes with one
+// 16-byte load and merges them with a byte-wise max (Eq. sketch-merge) through
+// CAS on 4-byte words, only where a register improves.
+//
+// Heavy vertex v (weighted-cascade or uniform model, threshold below 2^26):
+// every in-edge of v has the same threshold, and in-rows are sorted by edge
+// hash, so the in-edges live in simulation j are inside one hash interval
+// (the edge hash must agree with X_j above the threshold's top bit).  Each
+// changed simulation costs two binary searches in v's row plus the live
+// candidates, instead of a scan of all in-edges.
+#include "im_launch.h"
+
+namespace im {
+
+constexpr int kFBlock = 256;
+
+__device__ __forceinline__ unsigned long long wsum(unsigned long long x) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, s);
+    return x;
+}
+
+// Last queue entry whose offset is <= f (warp-wide 32-ary search).
+__device__ __forceinline__ int32_t covering_entry(const QEntry* __restrict__ q, int32_t count, int64_t f) {
+    int32_t lo = 0, hi = count;
+    const int lane = (int)lane_id();
+    while (hi - lo > 1) {
+        const int32_t step = (hi - lo + 31) >> 5;
+        const int64_t idx = (int64_t)lo + (int64_t)step * (lane + 1);
+        const bool le = idx < hi && (int64_t)__ldcg(&q[idx].off) <= f;
+        const int c = __popc(__ballot_sync(0xFFFFFFFFu, le));
+        const int32_t nlo = lo + step * c;
+        const int32_t nhi = (c < 32) ? (int32_t)min((int64_t)hi, (int64_t)lo + (int64_t)step * (c + 1)) : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    return lo;
+}
+
+// Warp-aggregated append to a queue with a packed (count << 38 | edges) counter.
+__device__ __forceinline__ void append(bool want, int32_t v, int32_t rp, int32_t deg, uint32_t aux,
+                                       QEntry* __restrict__ q, unsigned long long* ctr, int32_t cap,
+                                       uint32_t* err) {
+    const unsigned wm = __ballot_sync(0xFFFFFFFFu, want);
+    if (wm == 0u) return;
+    const int lane = (int)lane_id();
+    const int d = want ? deg : 0;
+    int incl = d;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, s);
+        if (lane >= s) incl += y;
+    }
+    const int totd = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 0)
+        base = atomicAdd(ctr, ((unsigned long long)__popc(wm) << kCountShift) | (unsigned long long)totd);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (want) {
+        const int32_t slot = (int32_t)(base >> kCountShift) + __popc(wm & ((1u << lane) - 1u));
+        if (slot < cap) {
+            QEntry e;
+            e.v = v;
+            e.rp = rp;
+            e.off = (int32_t)(base & kEdgeMask) + (incl - d);
+            e.aux = aux;
+            q[slot] = e;
+        } else {
+            atomicOr(err, kErrQueue);
+        }
+    }
+}
+
+// 16 change bits -> 4 words of byte masks (0xFF where the bit is set).
+__device__ __forceinline__ uint32_t bits_to_bytes(uint32_t b4) {
+    return ((b4 * 0x00204081u) & 0x01010101u) * 0xFFu;
+}
+
+// Non-zero bytes of a word -> 4 bits.
+__device__ __forceinline__ uint32_t bytes_to_bits(uint32_t d) {
+    const uint32_t t = (((d & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | d) & 0x80808080u;
+    return ((t >> 7) * 0x10204080u) >> 28;
+}
+
+// Where a vertex whose registers changed goes for the next propagation
+// level: the heavy queue when it is an in-degree hub whose in-edges share one
+// small threshold, else the light queue.
+template <int KIND>
+__device__ __forceinline__ bool is_heavy(int32_t deg, uint32_t thr, int32_t heavy_indeg) {
+    if constexpr (KIND == kWC || KIND == kUniform)
+        return deg > heavy_indeg && thr > 0u && thr < (1u << 26);
+    else
+        return false;
+}
+
+// Byte-wise max of cand into the 16 register bytes at trow through CAS on
+// 4-byte words.  Returns the changed registers as 16 bits.
+__device__ __forceinline__ uint32_t merge_chunk(uint8_t* trow, const uint32_t cand[4], uint4 tg,
+                                               unsigned long long& n_cas, uint32_t* err) {
+    uint32_t tw[4] = {tg.x, tg.y, tg.z, tg.w};
+    uint32_t bits = 0u;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        if (cand[w] == 0u) continue;
+        unsigned int* addr = reinterpret_cast<unsigned int*>(trow + 4 * w);
+        uint32_t cur = tw[w];
+        uint32_t nw = byte_max(cur, cand[w]);
+        int tries = 0;
+        while (nw != cur) {
+            const uint32_t prev = atomicCAS(addr, cur, nw);
+            if (prev == cur) {
+                bits |= bytes_to_bits(nw ^ cur) << (4 * w);
+                ++n_cas;
+                break;
+            }
+            cur = prev;
+            nw = byte_max(cur, cand[w]);
+            if (++tries > kCasRetryLimit) {
+                atomicOr(err, kErrCasLimit);
+                break;
+            }
+        }
+    }
+    return bits;
+}
+
+// ---------------------------------------------------------------------------
+// Light units: a slice of 32-edge batches of the flat edge space.
+// ---------------------------------------------------------------------------
+template <int KIND, int MODE>
+__device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& a, const uint32_t* sX,
+                                            const uint16_t* sTab, int64_t b0, int64_t b1, int32_t nl,
+                                            int64_t El, unsigned long long& st_chunks,
+                                            unsigned long long& st_cas, unsigned long long& st_new) {
+    const int lane = (int)lane_id();
+    const int J = a.J, words = a.words;
+    const int64_t fend = min(El, b1 << 5);
+    int64_t f0 = b0 << 5;
+    int32_t qi = covering_entry(a.ql_in, nl, f0);
+    for (; f0 < fend; f0 += 32) {
+        const int32_t wi = qi + lane;
+        const bool wvalid = wi < nl;
+        int4 raw = make_int4(0, 0, 0x7FFFFFFF, 0);
+        if (wvalid) raw = __ldcg(reinterpret_cast<const int4*>(a.ql_in) + wi);
+        const int64_t rel = (int64_t)raw.z - f0;
+        const int c0 = __popc(__ballot_sync(0xFFFFFFFFu, wvalid && rel <= 0));
+        const unsigned starts =
+            __reduce_or_sync(0xFFFFFFFFu, (wvalid && rel >= 1 && rel <= 31) ? (1u << rel) : 0u);
+        const int myw = c0 - 1 + __popc(starts & ((2u << lane) - 1u));
+        const int32_t qv = __shfl_sync(0xFFFFFFFFu, raw.x, myw);
+        const int32_t qrp = __shfl_sync(0xFFFFFFFFu, raw.y, myw);
+        const int32_t qoff = __shfl_sync(0xFFFFFFFFu, raw.z, myw);
+        const uint32_t qaux = (uint32_t)__shfl_sync(0xFFFFFFFFu, raw.w, myw);
+        const int64_t f = f0 + lane;
+        int32_t o = 0;
+        uint32_t h = 0, thr = 0;
+        int clo = 0, nch = 0;
+        if (f < fend) {
+            const int64_t e = (int64_t)qrp + (f - qoff);
+            if constexpr (MODE == kPush) {
+                o = __ldg(g.src_in + e);
+                h = __ldg(g.h_in + e);
+                thr = edge_threshold<KIND, true>(g, (uint32_t)o, (uint32_t)qv, e, qaux);
+            } else {
+                o = __ldg(g.col_out + e);
+                h = edge_hash((uint32_t)qv, (uint32_t)o);
+                thr = edge_threshold<KIND, false>(g, (uint32_t)qv, (uint32_t)o, e, 0u);
+            }
+            int lo, hi;
+            candidate_range(h, thr, J, sX, sTab, lo, hi);
+            if (hi > lo) {
+                clo = lo >> 4;
+                nch = ((hi + 15) >> 4) - clo;
+            }
+        }
+        int incl = nch;
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, incl, s);
+            if (lane >= s) incl += y;
+        }
+        const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        const int excl = incl - nch;
+        for (int base = 0; base < total; base += 32) {
+            const int k = base + lane;
+            int i = 0;
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                const int ic = __shfl_sync(0xFFFFFFFFu, incl, i + s - 1);
+                if (ic <= k) i += s;
+            }
+            if (i > 31) i = 31;
+            const int ex_i = __shfl_sync(0xFFFFFFFFu, excl, i);
+            const int cl_i = __shfl_sync(0xFFFFFFFFu, clo, i);
+            const int32_t o_i = __shfl_sync(0xFFFFFFFFu, o, i);
+            const int32_t q_i = __shfl_sync(0xFFFFFFFFu, qv, i);
+            const uint32_t h_i = __shfl_sync(0xFFFFFFFFu, h, i);
+            const uint32_t t_i = __shfl_sync(0xFFFFFFFFu, thr, i);
+            uint32_t nbits = 0u;
+            int chunk = 0;
+            if (k < total) {
+                chunk = cl_i + (k - ex_i);
+                uint32_t chb = 0xFFFFu;
+                if (!a.all_changed)
+                    chb = (__ldcg(a.chg_cur + (size_t)q_i * words + (chunk >> 1)) >> ((chunk & 1) * 16)) & 0xFFFFu;
+                if (chb) {
+                    const uint4* xs = reinterpret_cast<const uint4*>(sX + chunk * 16);
+                    const uint8_t* srow = a.M + (size_t)q_i * J + chunk * 16;
+                    uint8_t* trow = a.M + (size_t)o_i * J + chunk * 16;
+                    const uint4 src = ld_cg16(srow);
+                    const uint4 tg = ld_cg16(trow);
+                    const uint32_t sw[4] = {src.x, src.y, src.z, src.w};
+                    const uint32_t tw[4] = {tg.x, tg.y, tg.z, tg.w};
+                    uint32_t cand[4];
+                    uint32_t any = 0u;
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        const uint32_t L = live4(xs[w], h_i, t_i) & bits_to_bytes((chb >> (4 * w)) & 0xFu);
+                        if constexpr (MODE == kPush) cand[w] = sw[w] & L & ~visited_bytes(sw[w]);
+                        else cand[w] = L & visited_bytes(sw[w]) & ~visited_bytes(tw[w]);
+                        any |= cand[w];
+                    }
+                    if (any) {
+                        ++st_chunks;
+                        if constexpr (MODE == kPush) {
+                            nbits = merge_chunk(trow, cand, tg, st_cas, a.err);
+                        } else {
+#pragma unroll
+                            for (int w = 0; w < 4; ++w) {
+                                if (cand[w] == 0u) continue;
+                                const uint32_t prev = atomicOr(reinterpret_cast<unsigned int*>(trow + 4 * w), cand[w]);
+                                const uint32_t really = cand[w] & ~visited_bytes(prev);
+                                if (really) {
+                                    nbits |= bytes_to_bits(really) << (4 * w);
+                                    st_new += (unsigned)(__popc(really) >> 3);
+                                }
+                            }
+                        }
+                        if (nbits)
+                            atomicOr(a.chg_next + (size_t)o_i * words + (chunk >> 1), nbits << ((chunk & 1) * 16));
+                    }
+                }
+            }
+            // enqueue vertices whose registers changed
+            bool want = false;
+            int32_t rp = 0, deg = 0;
+            uint32_t aux = 0u;
+            bool heavy = false;
+            if (nbits) {
+                want = atomicExch(a.gen + o_i, a.gen_next) != a.gen_next;
+                if (want) {
+                    if constexpr (MODE == kPush) {
+                        rp = __ldg(g.rp_in + o_i);
+                        deg = __ldg(g.rp_in + o_i + 1) - rp;
+                        if constexpr (KIND == kWC) aux = __ldg(g.thr_v + o_i);
+                        heavy = is_heavy<KIND>(deg, KIND == kWC ? aux : g.thr_uniform, a.heavy_indeg);
+                    } else {
+                        rp = __ldg(g.rp_out + o_i);
+                        deg = __ldg(g.rp_out + o_i + 1) - rp;
+                    }
+                    want = deg > 0;
+                }
+            }
+            append(want && !heavy, o_i, rp, deg, aux, a.ql_out, a.cl_out, g.n, a.err);
+            if constexpr (MODE == kPush) append(want && heavy, o_i, rp, deg, aux, a.qh_out, a.ch_out, g.n, a.err);
+        }
+        const int n32 = __popc(__ballot_sync(0xFFFFFFFFu, wvalid && rel <= 32));
+        int32_t qn = qi + n32 - 1;
+        if (n32 == 32 && qi + 32 < nl) {
+            if ((int64_t)__ldcg(&a.ql_in[qi + 32].off) <= f0 + 32) qn = qi + 32;
+        }
+        qi = qn;
+    }
+}
+
+// First index in [lo, hi) with h_in[index] >= key.
+__device__ __forceinline__ int32_t lower_bound_h(const uint32_t* __restrict__ h, int32_t lo, int32_t hi,
+                                                 uint32_t key) {
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (__ldg(h + mid) < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Heavy unit: one in-degree hub, its changed simulations dealt to the lanes.
+// ---------------------------------------------------------------------------
+template <int KIND>
+__device__ __forceinline__ void heavy_vertex(const GraphDev& g, const LevelArgs& a, const uint32_t* sX,
+                                             QEntry ent, unsigned long long& st_chunks,
+                                             unsigned long long& st_cas) {
+    const int lane = (int)lane_id();
+    const int J = a.J, words = a.words;
+    const int32_t v = ent.v;
+    const int32_t rb = ent.rp;
+    const int32_t re = __ldg(g.rp_in + v + 1);
+    const uint32_t thr = KIND == kWC ? ent.aux : g.thr_uniform;
+    const int t1 = 32 - __clz((int)thr);  // t + 1, thr in (0, 2^26)
+    // changed simulations of v whose source register can still raise a target
+    uint32_t cw = 0u;
+    if (lane < words) {
+        cw = a.all_changed ? 0xFFFFFFFFu : __ldcg(a.chg_cur + (size_t)v * words + lane);
+        if (cw) {
+            const uint8_t* srow = a.M + (size_t)v * J + lane * 32;
+            const uint4 s0 = ld_cg16(srow), s1 = ld_cg16(srow + 16);
+            const uint32_t sw[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+            uint32_t useful = 0u;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                // a register is useful when it is neither visited nor 0
+                const uint32_t nz = bytes_to_bits(sw[q]);
+                const uint32_t vis = bytes_to_bits(visited_bytes(sw[q]));
+                useful |= (nz & ~vis) << (4 * q);
+            }
+            cw &= useful;
+        }
+    }
+    const int cnt = __popc(cw);
+    int incl = cnt;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, s);
+        if (lane >= s) incl += y;
+    }
+    const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    const int excl = incl - cnt;
+    for (int base = 0; base < total; base += 32) {
+        const int k = base + lane;
+        int i = 0;
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) {
+            const int ic = __shfl_sync(0xFFFFFFFFu, incl, i + s - 1);
+            if (ic <= k) i += s;
+        }
+        if (i > 31) i = 31;
+        const uint32_t word = __shfl_sync(0xFFFFFFFFu, cw, i);
+        const int ex_i = __shfl_sync(0xFFFFFFFFu, excl, i);
+        int32_t a0 = 0, a1 = 0;
+        int j = 0;
+        uint32_t val = 0u, Xj = 0u;
+        if (k < total) {
+            const int bit = (int)__fns(word, 0u, k - ex_i + 1);
+            j = i * 32 + bit;
+            val = a.M[(size_t)v * J + j];
+            Xj = sX[j];
+            const uint32_t lo_key = (Xj >> t1) << t1;
+            const uint32_t hi_key = lo_key + (1u << t1);
+            a0 = lower_bound_h(g.h_in, rb, re, lo_key);
+            a1 = lower_bound_h(g.h_in, a0, re, hi_key);
+            ++st_chunks;
+        }
+        int ncand = a1 - a0;
+        int maxc = ncand;
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) maxc = max(maxc, __shfl_xor_sync(0xFFFFFFFFu, maxc, s));
+        for (int c = 0; c < maxc; ++c) {
+            bool changed = false;
+            int32_t u = 0;
+            if (c < ncand) {
+                const int32_t e = a0 + c;
+                const uint32_t h = __ldg(g.h_in + e);
+                if ((Xj ^ h) < thr) {
+                    u = __ldg(g.src_in + e);
+                    unsigned int* addr = reinterpret_cast<unsigned int*>(a.M + (((size_t)u * J + j) & ~(size_t)3));
+                    const uint32_t b = val << (8 * (j & 3));
+                    uint32_t cur = __ldcg(addr);
+                    uint32_t nw = byte_max(cur, b);
+                    int tries = 0;
+                    while (nw != cur) {
+                        const uint32_t prev = atomicCAS(addr, cur, nw);
+                        if (prev == cur) { changed = true; ++st_cas; break; }
+                        cur = prev;
+                        nw = byte_max(cur, b);
+                        if (++tries > kCasRetryLimit) { atomicOr(a.err, kErrCasLimit); break; }
+                    }
+                    if (changed) atomicOr(a.chg_next + (size_t)u * words + (j >> 5), 1u << (j & 31));
+                }
+            }
+            bool want = false, heavy = false;
+            int32_t rp = 0, deg = 0;
+            uint32_t aux = 0u;
+            if (changed) {
+                want = atomicExch(a.gen + u, a.gen_next) != a.gen_next;
+                if (want) {
+                    rp = __ldg(g.rp_in + u);
+                    deg = __ldg(g.rp_in + u + 1) - rp;
+                    if constexpr (KIND == kWC) aux = __ldg(g.thr_v + u);
+                    heavy = is_heavy<KIND>(deg, KIND == kWC ? aux : g.thr_uniform, a.heavy_indeg);
+                    want = deg > 0;
+                }
+            }
+            append(want && !heavy, u, rp, deg, aux, a.ql_out, a.cl_out, g.n, a.err);
+            append(want && heavy, u, rp, deg, aux, a.qh_out, a.ch_out, g.n, a.err);
+        }
+    }
+}
+
+template <int KIND, int MODE>
+__global__ void __launch_bounds__(kFBlock) k_level(GraphDev g, LevelArgs a) {
+    __shared__ __align__(16) uint32_t sX[kMaxJ];
+    __shared__ uint16_t sTab[kTabSize];
+    const int lane = (int)lane_id();
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // clear the change bits read by the level before the previous one
+    if (a.chg_prev) {
+        const int32_t nlp = a.cl_prev ? (int32_t)(__ldcg(a.cl_prev) >> kCountShift) : 0;
+        const int32_t nhp = a.ch_prev ? (int32_t)(__ldcg(a.ch_prev) >> kCountShift) : 0;
+        for (int64_t i = warp; i < (int64_t)nlp + nhp; i += nwarps) {
+            const int32_t v = i < nlp ? __ldcg(&a.ql_prev[i].v) : __ldcg(&a.qh_prev[i - nlp].v);
+            if (lane < a.words) a.chg_prev[(size_t)v * a.words + lane] = 0u;
+        }
+    }
+    const unsigned long long cl = __ldcg(a.cl_in);
+    const unsigned long long ch = a.ch_in ? __ldcg(a.ch_in) : 0ull;
+    const int32_t nl = (int32_t)(cl >> kCountShift);
+    const int64_t El = (int64_t)(cl & kEdgeMask);
+    const int32_t nh = (int32_t)(ch >> kCountShift);
+    const int64_t nbl = (El + 31) >> 5;
+    const int64_t lunits = (nbl + a.light_batches - 1) / a.light_batches;
+    const int64_t total = (int64_t)nh + lunits;
+    if (total == 0) return;
+    for (int i = threadIdx.x; i < a.J; i += blockDim.x) sX[i] = __ldg(a.X + i);
+    for (int i = threadIdx.x; i < kTabSize; i += blockDim.x) sTab[i] = __ldg(a.tab + i);
+    __syncthreads();
+    if (warp == 0 && lane == 0) {
+        atomicAdd(a.stats + (MODE == kPush ? kStSweepVertices : kStCoverVertices),
+                  (unsigned long long)(nl + nh));
+        atomicAdd(a.stats + (MODE == kPush ? kStSweepEdges : kStCoverEdges), (unsigned long long)El);
+        atomicAdd(a.stats + (MODE == kPush ? kStSweepLevels : kStCoverLevels), 1ull);
+        if (MODE == kPush) atomicAdd(a.stats + kStSweepHeavy, (unsigned long long)nh);
+    }
+    unsigned long long st_chunks = 0, st_cas = 0, st_new = 0, st_hsims = 0;
+    for (;;) {
+        unsigned int unit = 0;
+        if (lane == 0) unit = atomicAdd(a.claim, 1u);
+        unit = __shfl_sync(0xFFFFFFFFu, unit, 0);
+        if ((int64_t)unit >= total) break;
+        if ((int64_t)unit < nh) {
+            if constexpr (MODE == kPush && (KIND == kWC || KIND == kUniform)) {
+                const int4 raw = __ldcg(reinterpret_cast<const int4*>(a.qh_in) + unit);
+                QEntry ent;
+                ent.v = raw.x; ent.rp = raw.y; ent.off = raw.z; ent.aux = (uint32_t)raw.w;
+                heavy_vertex<KIND>(g, a, sX, ent, st_hsims, st_cas);
+            }
+        } else {
+            const int64_t lu = (int64_t)unit - nh;
+            const int64_t b0 = lu * a.light_batches;
+            const int64_t b1 = min(nbl, b0 + a.light_batches);
+            light_slice<KIND, MODE>(g, a, sX, sTab, b0, b1, nl, El, st_chunks, st_cas, st_new);
+        }
+    }
+    st_chunks = wsum(st_chunks);
+    st_cas = wsum(st_cas);
+    st_new = wsum(st_new);
+    st_hsims = wsum(st_hsims);
+    if (lane == 0) {
+        if constexpr (MODE == kPush) {
+            if (st_chunks) atomicAdd(a.stats + kStSweepChunks, st_chunks);
+            if (st_cas) atomicAdd(a.stats + kStSweepCas, st_cas);
+            if (st_hsims) atomicAdd(a.stats + kStSweepHeavySims, st_hsims);
+        } else {
+            if (st_chunks) atomicAdd(a.stats + kStCoverChunks, st_chunks);
+            if (st_new) {
+                atomicAdd(a.stats + kStCoverNew, st_new);
+                atomicAdd(a.count, st_new);
+            }
+        }
+    }
+}
+
+int level_grid() {
+    static int grid = 0;
+    if (grid == 0) {
+        int dev = 0, sms = 152, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level<kWC, kPush>, kFBlock, 0);
+        if (per_sm < 1) per_sm = 1;
+        grid = sms * per_sm;
+    }
+    return grid;
+}
+
+template <int MODE>
+static cudaError_t launch_level_mode(int kind, const GraphDev& g, const LevelArgs& a, int grid,
+                                     cudaStream_t st) {
+    switch (kind) {
+        case kUniform: k_level<kUniform, MODE><<<grid, kFBlock, 0, st>>>(g, a); break;
+        case kWC: k_level<kWC, MODE><<<grid, kFBlock, 0, st>>>(g, a); break;
+        case kTrivalency: k_level<kTrivalency, MODE><<<grid, kFBlock, 0, st>>>(g, a); break;
+        default: k_level<kExplicit, MODE><<<grid, kFBlock, 0, st>>>(g, a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level(int kind, int mode, const GraphDev& g, const LevelArgs& a, int grid,
+                         cudaStream_t st) {
+    return mode == kPush ? launch_level_mode<kPush>(kind, g, a, grid, st)
+                         : launch_level_mode<kCover>(kind, g, a, grid, st);
+}
+
+// ---------------------------------------------------------------------------
+// Level-0 queues of a build: every vertex with in-edges, hubs to the heavy queue.
+// ---------------------------------------------------------------------------
+template <int KIND>
+__global__ void __launch_bounds__(kFBlock) k_init_queues(GraphDev g, LevelArgs a) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x; v0 < g.n; v0 += stride) {
+        const int64_t v = v0 + threadIdx.x;
+        bool want = false, heavy = false;
+        int32_t rp = 0, deg = 0;
+        uint32_t aux = 0u;
+        if (v < g.n) {
+            rp = g.rp_in[v];
+            deg = g.rp_in[v + 1] - rp;
+            if constexpr (KIND == kWC) aux = g.thr_v[v];
+            heavy = is_heavy<KIND>(deg, KIND == kWC ? aux : g.thr_uniform, a.heavy_indeg);
+            want = deg > 0;
+        }
+        append(want && !heavy, (int32_t)v, rp, deg, aux, a.ql_out, a.cl_out, g.n, a.err);
+        append(want && heavy, (int32_t)v, rp, deg, aux, a.qh_out, a.ch_out, g.n, a.err);
+    }
+}
+
+cudaError_t launch_init_queues(int kind, const GraphDev& g, const LevelArgs& a, cudaStream_t st) {
+    const int grid = 152 * 8;
+    switch (kind) {
+        case kUniform: k_init_queues<kUniform><<<grid, kFBlock, 0, st>>>(g, a); break;
+        case kWC: k_init_queues<kWC><<<grid, kFBlock, 0, st>>>(g, a); break;
+        case kTrivalency: k_init_queues<kTrivalency><<<grid, kFBlock, 0, st>>>(g, a); break;
+        default: k_init_queues<kExplicit><<<grid, kFBlock, 0, st>>>(g, a); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace im

@@ -2,21 +2,13 @@
 //
 //   k_sims         per-simulation draws X_j, salt_j, FASST sort, range table   (Sec. 2.2, Sec. 4.1)
 //   k_fill         Fill-Sketches: M[u][j] = rank of u in simulation j         (Alg. 1, Eq. sketch-init)
-//   k_frontier     one level of a frontier over a unified queue:
-//                    kPush : Simulate (Alg. 2) as push sweeps from the vertices
-//                            whose registers changed, merged with byte max (Eq. sketch-merge)
-//                    kCover: Cascade (Alg. 3): visited marks spread along live edges
+//   (im_frontier.cu holds the propagation sweeps and cover levels)
 //   k_pick         Sketchwise-Sum + argmax + seed init of the cover        (Eq. gpu-sketch-int, Alg. 4)
 //   k_mc_*         independent-cascade Monte-Carlo spread (Sec. 5.1 oracle)
 //
-// Schedule: every frontier level walks the flat edge space of its queue
-// (sum of the queued vertices' degrees).  Each warp owns an equal slice of
-// that space, so a hub's edges are spread over many warps (power-law skew)
-// and no warp holds more than its share.  Inside a 32-edge batch every lane
-// resolves one edge (hash, threshold, candidate range); the batch's
-// 16-simulation chunks are then dealt round-robin to the lanes, so lanes work
-// on useful chunks only and consecutive lanes read consecutive 16-byte pieces
-// of a register row.
+// The Monte-Carlo levels walk the flat out-edge space of their queue (sum of
+// the queued vertices' out-degrees); each warp owns an equal slice of it, so a
+// hub's edges are spread over many warps.
 #include <cstdio>
 
 #include "im_launch.h"
@@ -131,297 +123,10 @@ __device__ __forceinline__ int32_t find_covering(const QEntry* __restrict__ q, i
     return lo;
 }
 
-// Warp-aggregated append of (vertex, row start, degree, aux) to a queue whose
-// counter packs count << 38 | edges.  Lanes with want == false do not append.
-__device__ __forceinline__ void warp_append(bool want, int32_t v, int32_t rp, int32_t deg,
-                                            uint32_t aux, QEntry* __restrict__ q,
-                                            unsigned long long* ctr, int32_t cap, uint32_t* err) {
-    const unsigned wm = __ballot_sync(0xFFFFFFFFu, want);
-    if (wm == 0u) return;
-    const int lane = (int)lane_id();
-    int d = want ? deg : 0;
-    int incl = d;
-#pragma unroll
-    for (int s = 1; s < 32; s <<= 1) {
-        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, s);
-        if (lane >= s) incl += y;
-    }
-    const int totd = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    const int totc = __popc(wm);
-    unsigned long long base = 0;
-    if (lane == 0)
-        base = atomicAdd(ctr, ((unsigned long long)totc << kCountShift) | (unsigned long long)totd);
-    base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    if (want) {
-        const int32_t slot = (int32_t)(base >> kCountShift) + __popc(wm & ((1u << lane) - 1u));
-        const int32_t off = (int32_t)(base & kEdgeMask) + (incl - d);
-        if (slot < cap) {
-            QEntry e;
-            e.v = v;
-            e.rp = rp;
-            e.off = off;
-            e.aux = aux;
-            q[slot] = e;
-        } else {
-            atomicOr(err, kErrQueue);
-        }
-    }
-}
-
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
 #pragma unroll
     for (int s = 16; s >= 1; s >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, s);
     return x;
-}
-
-// ---------------------------------------------------------------------------
-// a4 / a7: one frontier level.
-//   kPush : queue vertex q = v, edge (o, q) from the in-CSR; chunks of M[q]
-//           whose simulations are live and not visited are max-merged into
-//           M[o] with atomic CAS (Alg. 2 as a push: only improvements write).
-//   kCover: queue vertex q = u, edge (q, o) from the out-CSR; simulations in
-//           which q is visited and the edge is live mark o visited (Alg. 3).
-// A vertex o whose registers changed is appended once (stamp gen[o]) to the
-// next queue, with its in-degree (push) or out-degree (cover).
-// ---------------------------------------------------------------------------
-template <int KIND, int MODE>
-__global__ void __launch_bounds__(kBlock) k_frontier(GraphDev g, FrontierArgs a) {
-    __shared__ __align__(16) uint32_t sX[kMaxJ];
-    __shared__ uint16_t sTab[kTabSize];
-    const int J = a.J;
-    for (int i = threadIdx.x; i < J; i += blockDim.x) sX[i] = __ldg(a.X + i);
-    for (int i = threadIdx.x; i < kTabSize; i += blockDim.x) sTab[i] = __ldg(a.tab + i);
-    __syncthreads();
-
-    const unsigned long long c = __ldcg(a.ctr_in);
-    const int32_t count = (int32_t)(c >> kCountShift);
-    const int64_t E = (int64_t)(c & kEdgeMask);
-    if (E == 0) return;
-    const int lane = (int)lane_id();
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    if (warp == 0 && lane == 0) {
-        atomicAdd(a.stats + (MODE == kPush ? kStSweepVertices : kStCoverVertices),
-                  (unsigned long long)count);
-        atomicAdd(a.stats + (MODE == kPush ? kStSweepEdges : kStCoverEdges),
-                  (unsigned long long)E);
-        atomicAdd(a.stats + (MODE == kPush ? kStSweepLevels : kStCoverLevels), 1ull);
-    }
-    const int64_t nb = (E + 31) >> 5;
-    const int64_t per = (nb + nwarps - 1) / nwarps;
-    const int64_t b0 = warp * per;
-    const int64_t b1 = min(nb, b0 + per);
-    if (b0 >= b1) return;
-    const int64_t fend = min(E, b1 << 5);
-    int64_t f0 = b0 << 5;
-    int32_t qi = find_covering(a.q_in, count, f0);
-
-    unsigned long long st_chunks = 0, st_cas = 0, st_changed = 0, st_new = 0;
-    const int32_t cap = g.n;
-
-    for (; f0 < fend; f0 += 32) {
-        // ---- resolve the batch's edges --------------------------------------
-        const int32_t wi = qi + lane;
-        const bool wvalid = wi < count;
-        QEntry ent;
-        if (wvalid) {
-            const int4 raw = __ldcg(reinterpret_cast<const int4*>(a.q_in) + wi);
-            ent.v = raw.x; ent.rp = raw.y; ent.off = raw.z; ent.aux = (uint32_t)raw.w;
-        } else {
-            ent.v = 0; ent.rp = 0; ent.off = 0x7FFFFFFF; ent.aux = 0;
-        }
-        const int64_t rel = (int64_t)ent.off - f0;
-        const int c0 = __popc(__ballot_sync(0xFFFFFFFFu, wvalid && rel <= 0));
-        const unsigned starts =
-            __reduce_or_sync(0xFFFFFFFFu, (wvalid && rel >= 1 && rel <= 31) ? (1u << rel) : 0u);
-        const int myw = c0 - 1 + __popc(starts & ((2u << lane) - 1u));
-        const int32_t qv = __shfl_sync(0xFFFFFFFFu, ent.v, myw);
-        const int32_t qrp = __shfl_sync(0xFFFFFFFFu, ent.rp, myw);
-        const int32_t qoff = __shfl_sync(0xFFFFFFFFu, ent.off, myw);
-        const uint32_t qaux = __shfl_sync(0xFFFFFFFFu, ent.aux, myw);
-        const int64_t f = f0 + lane;
-        const bool act = f < fend;
-
-        int32_t o = 0;
-        uint32_t h = 0, thr = 0;
-        int clo = 0, nch = 0;
-        if (act) {
-            const int64_t e = (int64_t)qrp + (f - qoff);
-            if constexpr (MODE == kPush) {
-                o = __ldg(g.src_in + e);
-                h = edge_hash((uint32_t)o, (uint32_t)qv);
-                thr = edge_threshold<KIND, true>(g, (uint32_t)o, (uint32_t)qv, e, qaux);
-            } else {
-                o = __ldg(g.col_out + e);
-                h = edge_hash((uint32_t)qv, (uint32_t)o);
-                thr = edge_threshold<KIND, false>(g, (uint32_t)qv, (uint32_t)o, e, 0u);
-            }
-            int lo, hi;
-            candidate_range(h, thr, J, sX, sTab, lo, hi);
-            if (hi > lo) {
-                clo = lo >> 4;
-                nch = ((hi + 15) >> 4) - clo;
-            }
-        }
-
-        // ---- deal the batch's 16-simulation chunks to the lanes --------------
-        int incl = nch;
-#pragma unroll
-        for (int s = 1; s < 32; s <<= 1) {
-            const int y = __shfl_up_sync(0xFFFFFFFFu, incl, s);
-            if (lane >= s) incl += y;
-        }
-        const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        const int excl = incl - nch;
-        for (int base = 0; base < total; base += 32) {
-            const int k = base + lane;
-            int i = 0;
-#pragma unroll
-            for (int s = 16; s >= 1; s >>= 1) {
-                const int ic = __shfl_sync(0xFFFFFFFFu, incl, i + s - 1);
-                if (ic <= k) i += s;
-            }
-            if (i > 31) i = 31;
-            const int ex_i = __shfl_sync(0xFFFFFFFFu, excl, i);
-            const int cl_i = __shfl_sync(0xFFFFFFFFu, clo, i);
-            const int32_t o_i = __shfl_sync(0xFFFFFFFFu, o, i);
-            const int32_t q_i = __shfl_sync(0xFFFFFFFFu, qv, i);
-            const uint32_t h_i = __shfl_sync(0xFFFFFFFFu, h, i);
-            const uint32_t t_i = __shfl_sync(0xFFFFFFFFu, thr, i);
-            bool changed = false;
-            if (k < total) {
-                const int chunk = cl_i + (k - ex_i);
-                const uint4* xs = reinterpret_cast<const uint4*>(sX + chunk * 16);
-                const uint4 src = ld_cg16(a.M + (size_t)q_i * J + chunk * 16);
-                uint32_t sw[4] = {src.x, src.y, src.z, src.w};
-                uint32_t cand[4];
-                uint32_t any = 0;
-#pragma unroll
-                for (int w = 0; w < 4; ++w) {
-                    const uint32_t L = live4(xs[w], h_i, t_i);
-                    if constexpr (MODE == kPush) cand[w] = sw[w] & L & ~visited_bytes(sw[w]);
-                    else cand[w] = L & visited_bytes(sw[w]);
-                    any |= cand[w];
-                }
-                if (any) {
-                    ++st_chunks;
-                    uint8_t* trow = a.M + (size_t)o_i * J + chunk * 16;
-                    const uint4 tg = ld_cg16(trow);
-                    uint32_t tw[4] = {tg.x, tg.y, tg.z, tg.w};
-#pragma unroll
-                    for (int w = 0; w < 4; ++w) {
-                        unsigned int* addr = reinterpret_cast<unsigned int*>(trow + 4 * w);
-                        if constexpr (MODE == kPush) {
-                            if (cand[w] == 0u) continue;
-                            uint32_t cur = tw[w];
-                            uint32_t nw = byte_max(cur, cand[w]);
-                            int tries = 0;
-                            while (nw != cur) {
-                                const uint32_t prev = atomicCAS(addr, cur, nw);
-                                if (prev == cur) {
-                                    changed = true;
-                                    ++st_cas;
-                                    break;
-                                }
-                                cur = prev;
-                                nw = byte_max(cur, cand[w]);
-                                if (++tries > kCasRetryLimit) {
-                                    atomicOr(a.err, kErrCasLimit);
-                                    break;
-                                }
-                            }
-                        } else {
-                            const uint32_t newly = cand[w] & ~visited_bytes(tw[w]);
-                            if (newly == 0u) continue;
-                            const uint32_t prev = atomicOr(addr, newly);
-                            const uint32_t really = newly & ~visited_bytes(prev);
-                            if (really) {
-                                changed = true;
-                                st_new += (unsigned)(__popc(really) >> 3);
-                            }
-                        }
-                    }
-                }
-            }
-            // ---- enqueue changed vertices for the next level ------------------
-            bool want = false;
-            int32_t rp = 0, deg = 0;
-            uint32_t aux = 0;
-            if (changed) {
-                want = atomicExch(a.gen + o_i, a.gen_next) != a.gen_next;
-                if (want) {
-                    if constexpr (MODE == kPush) {
-                        rp = __ldg(g.rp_in + o_i);
-                        deg = __ldg(g.rp_in + o_i + 1) - rp;
-                        if constexpr (KIND == kWC) aux = __ldg(g.thr_v + o_i);
-                    } else {
-                        rp = __ldg(g.rp_out + o_i);
-                        deg = __ldg(g.rp_out + o_i + 1) - rp;
-                    }
-                    want = deg > 0;
-                    st_changed += want ? 1 : 0;
-                }
-            }
-            warp_append(want, o_i, rp, deg, aux, a.q_out, a.ctr_out, cap, a.err);
-        }
-
-        // ---- advance the window to the entry covering f0 + 32 -----------------
-        const int n32 = __popc(__ballot_sync(0xFFFFFFFFu, wvalid && rel <= 32));
-        int32_t qn = qi + n32 - 1;
-        if (n32 == 32 && qi + 32 < count) {
-            if ((int64_t)__ldcg(&a.q_in[qi + 32].off) <= f0 + 32) qn = qi + 32;
-        }
-        qi = qn;
-    }
-
-    st_chunks = warp_sum(st_chunks);
-    st_cas = warp_sum(st_cas);
-    st_changed = warp_sum(st_changed);
-    st_new = warp_sum(st_new);
-    if (lane == 0) {
-        if constexpr (MODE == kPush) {
-            if (st_chunks) atomicAdd(a.stats + kStSweepChunks, st_chunks);
-            if (st_cas) atomicAdd(a.stats + kStSweepCas, st_cas);
-            if (st_changed) atomicAdd(a.stats + kStSweepChanged, st_changed);
-        } else {
-            if (st_chunks) atomicAdd(a.stats + kStCoverChunks, st_chunks);
-            if (st_new) {
-                atomicAdd(a.stats + kStCoverNew, st_new);
-                atomicAdd(a.count, st_new);
-            }
-        }
-    }
-}
-
-int frontier_grid() {
-    static int grid = 0;
-    if (grid == 0) {
-        int dev = 0, sms = 152, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_frontier<kUniform, kPush>, kBlock, 0);
-        if (per_sm < 1) per_sm = 1;
-        grid = sms * per_sm;
-    }
-    return grid;
-}
-
-template <int MODE>
-static cudaError_t launch_frontier_mode(int kind, const GraphDev& g, const FrontierArgs& a,
-                                        int grid, cudaStream_t st) {
-    switch (kind) {
-        case kUniform: k_frontier<kUniform, MODE><<<grid, kBlock, 0, st>>>(g, a); break;
-        case kWC: k_frontier<kWC, MODE><<<grid, kBlock, 0, st>>>(g, a); break;
-        case kTrivalency: k_frontier<kTrivalency, MODE><<<grid, kBlock, 0, st>>>(g, a); break;
-        default: k_frontier<kExplicit, MODE><<<grid, kBlock, 0, st>>>(g, a); break;
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_frontier(int kind, int mode, const GraphDev& g, const FrontierArgs& a, int grid,
-                            cudaStream_t st) {
-    return mode == kPush ? launch_frontier_mode<kPush>(kind, g, a, grid, st)
-                         : launch_frontier_mode<kCover>(kind, g, a, grid, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -467,14 +172,20 @@ __device__ __forceinline__ void lex_min(unsigned long long& S, int32_t& u, unsig
 
 // Marks row s visited and queues s as level 0 of a cover (one block).
 __device__ void cover_seed_block(uint8_t* M, int J, int32_t s, const int32_t* rp_out, QEntry* q,
-                                 unsigned long long* ctr, unsigned long long* count) {
+                                 unsigned long long* ctr, uint32_t* chg0, unsigned long long* count) {
     __shared__ unsigned int newly_sh;
     if (threadIdx.x == 0) newly_sh = 0;
     __syncthreads();
     unsigned int newly = 0;
     uint8_t* row = M + (size_t)s * J;
-    for (int j = threadIdx.x; j < J; j += blockDim.x) {
-        if (row[j] != kVisited) { row[j] = (uint8_t)kVisited; ++newly; }
+    const int Jr = (J + 31) & ~31;
+    const int words = Jr >> 5;
+    for (int j = threadIdx.x; j < Jr; j += blockDim.x) {
+        const bool fresh = j < J && row[j] != kVisited;
+        if (fresh) { row[j] = (uint8_t)kVisited; ++newly; }
+        // change mask of the seed at cover level 0: its newly visited simulations
+        const unsigned bits = __ballot_sync(0xFFFFFFFFu, fresh);
+        if ((j & 31) == 0) chg0[(size_t)s * words + (j >> 5)] = bits;
     }
     newly = (unsigned)warp_sum(newly);
     if (lane_id() == 0 && newly) atomicAdd(&newly_sh, newly);
@@ -571,7 +282,7 @@ __global__ void __launch_bounds__(kBlock) k_pick(PickArgs a) {
     }
     __syncthreads();
     if (fS == ~0ull || !a.mark) return;
-    cover_seed_block(a.M, J, fU, a.rp_out, a.q_cover, a.ctr_cover, a.count);
+    cover_seed_block(a.M, J, fU, a.rp_out, a.q_cover, a.ctr_cover, a.chg0, a.count);
 }
 
 int pick_grid(int32_t n, int J) {
@@ -592,14 +303,15 @@ cudaError_t launch_pick(const PickArgs& a, cudaStream_t st) {
 
 __global__ void __launch_bounds__(kBlock) k_cover_seed(uint8_t* M, int J, int32_t s,
                                                        const int32_t* rp_out, QEntry* q,
-                                                       unsigned long long* ctr,
+                                                       unsigned long long* ctr, uint32_t* chg0,
                                                        unsigned long long* count) {
-    cover_seed_block(M, J, s, rp_out, q, ctr, count);
+    cover_seed_block(M, J, s, rp_out, q, ctr, chg0, count);
 }
 
 cudaError_t launch_cover_seed(uint8_t* M, int J, int32_t s, const int32_t* rp_out, QEntry* q,
-                              unsigned long long* ctr, unsigned long long* count, cudaStream_t st) {
-    k_cover_seed<<<1, kBlock, 0, st>>>(M, J, s, rp_out, q, ctr, count);
+                              unsigned long long* ctr, uint32_t* chg0, unsigned long long* count,
+                              cudaStream_t st) {
+    k_cover_seed<<<1, kBlock, 0, st>>>(M, J, s, rp_out, q, ctr, chg0, count);
     return cudaGetLastError();
 }
 
@@ -730,32 +442,6 @@ cudaError_t launch_exclusive_scan(const int32_t* cnt, int32_t n, int32_t* out, v
     return cudaGetLastError();
 }
 
-__global__ void k_scatter_in(const int32_t* __restrict__ rp_out, const int32_t* __restrict__ col_out,
-                             int32_t n, const int32_t* __restrict__ rp_in, int32_t* fill,
-                             int32_t* __restrict__ src_in, const uint32_t* __restrict__ thr_out,
-                             uint32_t* __restrict__ thr_in) {
-    const int lane = (int)lane_id();
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = warp; u < n; u += nwarps) {
-        const int32_t b = rp_out[u], e = rp_out[u + 1];
-        for (int32_t i = b + lane; i < e; i += 32) {
-            const int32_t v = col_out[i];
-            const int32_t pos = rp_in[v] + atomicAdd(fill + v, 1);
-            src_in[pos] = (int32_t)u;
-            if (thr_in) thr_in[pos] = thr_out[i];
-        }
-    }
-}
-
-cudaError_t launch_scatter_in(const int32_t* rp_out, const int32_t* col_out, int32_t n,
-                              const int32_t* rp_in, int32_t* fill, int32_t* src_in,
-                              const uint32_t* thr_out, uint32_t* thr_in, cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
-    k_scatter_in<<<152 * 8, kBlock, 0, st>>>(rp_out, col_out, n, rp_in, fill, src_in, thr_out, thr_in);
-    return cudaGetLastError();
-}
-
 // Weighted cascade (Sec. 2.1): w = 1/indeg(v) rounded to fp32 (IEEE division),
 // threshold floor(w * 2^31) computed exactly in fp64.
 __device__ __forceinline__ uint32_t prob_threshold_dev(float w) {
@@ -787,39 +473,6 @@ __global__ void k_thr_explicit(const float* __restrict__ w, int64_t m, uint32_t*
 cudaError_t launch_thr_explicit(const float* w, int64_t m, uint32_t* thr, cudaStream_t st) {
     if (m == 0) return cudaSuccess;
     k_thr_explicit<<<152 * 8, kBlock, 0, st>>>(w, m, thr);
-    return cudaGetLastError();
-}
-
-__global__ void k_flag_nonzero_in(const int32_t* __restrict__ rp_in, int32_t n, int32_t* flag) {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v < n) flag[v] = rp_in[v + 1] > rp_in[v] ? 1 : 0;
-}
-
-cudaError_t launch_flag_nonzero_in(const int32_t* rp_in, int32_t n, int32_t* flag, cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
-    k_flag_nonzero_in<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(rp_in, n, flag);
-    return cudaGetLastError();
-}
-
-// Entry k of the all-vertex queue is the k-th vertex with in-edges; its offset
-// in the flat in-edge space is its in-CSR row start.
-__global__ void k_all_queue(const int32_t* __restrict__ rp_in, int32_t n,
-                            const uint32_t* __restrict__ thr_v, const int32_t* __restrict__ pos,
-                            QEntry* __restrict__ q) {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n) return;
-    const int32_t b = rp_in[v], e = rp_in[v + 1];
-    if (e > b) {
-        QEntry x;
-        x.v = (int32_t)v; x.rp = b; x.off = b; x.aux = thr_v ? thr_v[v] : 0u;
-        q[pos[v]] = x;
-    }
-}
-
-cudaError_t launch_all_queue(const int32_t* rp_in, int32_t n, const uint32_t* thr_v,
-                             const int32_t* pos, QEntry* q, cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
-    k_all_queue<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(rp_in, n, thr_v, pos, q);
     return cudaGetLastError();
 }
 
@@ -1032,6 +685,202 @@ __global__ void k_mc_reduce(const unsigned long long* __restrict__ reach, int va
 cudaError_t launch_mc_reduce(const unsigned long long* reach, int valid, unsigned long long* acc,
                              cudaStream_t st) {
     k_mc_reduce<<<1, kBlock, 0, st>>>(reach, valid, acc);
+    return cudaGetLastError();
+}
+
+}  // namespace im
+
+namespace im {
+
+// ---------------------------------------------------------------------------
+// Graph load: LSD radix sort (8-bit digits, stable) of 64-bit keys carrying a
+// 32-bit payload.  Used once per graph to build the in-CSR sorted by
+// (target, class, edge hash).
+// ---------------------------------------------------------------------------
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kBlock * kSortItems;  // 4096 keys per block
+
+__global__ void __launch_bounds__(kBlock) k_sort_hist(const unsigned long long* __restrict__ keys,
+                                                      int64_t n, int shift, int nblocks,
+                                                      int32_t* __restrict__ hist) {
+    __shared__ unsigned int h[256];
+    h[threadIdx.x] = 0u;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortItems; ++r) {
+        const int64_t i = base + (int64_t)r * kBlock + threadIdx.x;
+        if (i < n) atomicAdd(&h[(unsigned)(keys[i] >> shift) & 0xFFu], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = (int32_t)h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kBlock) k_sort_scatter(
+    const unsigned long long* __restrict__ keys, const int32_t* __restrict__ vals, int64_t n, int shift,
+    int nblocks, const int32_t* __restrict__ offs, unsigned long long* __restrict__ keys_out,
+    int32_t* __restrict__ vals_out) {
+    __shared__ unsigned int wcount[kWarpsPerBlock][256];
+    __shared__ unsigned int run[256];
+    const int lane = (int)lane_id(), w = threadIdx.x >> 5;
+    run[threadIdx.x] = (unsigned)offs[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortItems; ++r) {
+        for (int d = lane; d < 256; d += 32) wcount[w][d] = 0u;
+        __syncthreads();
+        const int64_t i = base + (int64_t)r * kBlock + threadIdx.x;
+        const bool ok = i < n;
+        unsigned long long k = 0;
+        int32_t v = 0;
+        unsigned d = 256u + (unsigned)lane;  // distinct dummy digits for missing keys
+        if (ok) {
+            k = keys[i];
+            v = vals[i];
+            d = (unsigned)(k >> shift) & 0xFFu;
+        }
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+        const unsigned rank_w = __popc(peers & ((1u << lane) - 1u));
+        if (ok && rank_w == 0) wcount[w][d] = __popc(peers);
+        __syncthreads();
+        if (ok) {
+            unsigned before = 0;
+            for (int ww = 0; ww < w; ++ww) before += wcount[ww][d];
+            const unsigned pos = run[d] + before + rank_w;
+            keys_out[pos] = k;
+            vals_out[pos] = v;
+        }
+        __syncthreads();
+        {
+            unsigned tot = 0;
+            for (int ww = 0; ww < kWarpsPerBlock; ++ww) tot += wcount[ww][threadIdx.x];
+            run[threadIdx.x] += tot;
+        }
+        __syncthreads();
+    }
+}
+
+size_t sort_tmp_bytes(int64_t n) {
+    const int64_t nb = (n + kSortTile - 1) / kSortTile;
+    const int64_t cnt = 256 * (nb > 0 ? nb : 1);
+    return 2 * ((size_t)(cnt + 1) * 4 + 256) + scan_tmp_bytes((int32_t)cnt) + 256 +
+           ((size_t)n * 8 + 256) + (size_t)n * 4 + 256;
+}
+
+// Sort keys of the in-CSR: (target << 33) | (class << 31) | hE(source, target),
+// payload = out-edge index.  class = trivalency class (0 for other models).
+__global__ void k_in_keys(const int32_t* __restrict__ rp_out, const int32_t* __restrict__ col_out,
+                          int32_t n, int kind, uint32_t tri_seed, unsigned long long* __restrict__ keys,
+                          int32_t* __restrict__ perm, int32_t* __restrict__ src_out) {
+    const int lane = (int)lane_id();
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = warp; u < n; u += nwarps) {
+        const int32_t b = rp_out[u], e = rp_out[u + 1];
+        for (int32_t i = b + lane; i < e; i += 32) {
+            const uint32_t v = (uint32_t)col_out[i];
+            const uint32_t cls = kind == kTrivalency ? hash_pair((uint32_t)u, v, tri_seed) % 3u : 0u;
+            keys[i] = ((unsigned long long)v << 33) | ((unsigned long long)cls << 31) |
+                      edge_hash((uint32_t)u, v);
+            perm[i] = i;
+            src_out[i] = (int32_t)u;
+        }
+    }
+}
+
+__global__ void k_in_gather(const unsigned long long* __restrict__ keys, const int32_t* __restrict__ perm,
+                            int64_t m, const int32_t* __restrict__ src_out,
+                            const uint32_t* __restrict__ thr_out, int32_t* __restrict__ src_in,
+                            uint32_t* __restrict__ h_in, uint32_t* __restrict__ thr_in) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = perm[i];
+        src_in[i] = src_out[e];
+        h_in[i] = (uint32_t)keys[i] & 0x7FFFFFFFu;
+        if (thr_in) thr_in[i] = thr_out[e];
+    }
+}
+
+// For trivalency: first in-edge of class >= 1 and of class >= 2 in each in-row.
+__global__ void k_cls_split(const int32_t* __restrict__ rp_in, const unsigned long long* __restrict__ keys,
+                            int32_t n, int2* __restrict__ split) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int32_t b = rp_in[v], e = rp_in[v + 1];
+    int2 r;
+    int32_t lo = b, hi = e;  // first index with class >= 1
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (((keys[mid] >> 31) & 3ull) >= 1ull) hi = mid; else lo = mid + 1;
+    }
+    r.x = lo;
+    hi = e;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (((keys[mid] >> 31) & 3ull) >= 2ull) hi = mid; else lo = mid + 1;
+    }
+    r.y = lo;
+    split[v] = r;
+}
+
+cudaError_t launch_build_in_csr(const int32_t* rp_out, const int32_t* col_out, int32_t n, int64_t m,
+                                int kind, uint32_t tri_seed, const uint32_t* thr_out,
+                                const int32_t* rp_in, int32_t* src_in, uint32_t* h_in,
+                                uint32_t* thr_in, int2* cls_split, void* tmp, cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    char* p = static_cast<char*>(tmp);
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(p);
+    p += ((size_t)m * 8 + 255) & ~(size_t)255;
+    int32_t* perm = reinterpret_cast<int32_t*>(p);
+    p += ((size_t)m * 4 + 255) & ~(size_t)255;
+    int32_t* src_out = reinterpret_cast<int32_t*>(p);
+    p += ((size_t)m * 4 + 255) & ~(size_t)255;
+    k_in_keys<<<152 * 8, kBlock, 0, st>>>(rp_out, col_out, n, kind, tri_seed, keys, perm, src_out);
+    int bits = 33;
+    while ((1ll << (bits - 33)) < n) ++bits;
+    cudaError_t e = launch_radix_sort(keys, perm, m, bits, p, st);
+    if (e != cudaSuccess) return e;
+    k_in_gather<<<152 * 8, kBlock, 0, st>>>(keys, perm, m, src_out, thr_out, src_in, h_in, thr_in);
+    if (cls_split) k_cls_split<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(rp_in, keys, n, cls_split);
+    return cudaGetLastError();
+}
+
+size_t build_in_csr_tmp_bytes(int64_t m) {
+    return ((size_t)m * 8 + 256) + 2 * ((size_t)m * 4 + 256) + sort_tmp_bytes(m);
+}
+
+// Sorts (keys, vals) in place by the key bits [0, bits); tmp >= sort_tmp_bytes(n).
+cudaError_t launch_radix_sort(unsigned long long* keys, int32_t* vals, int64_t n, int bits,
+                              void* tmp, cudaStream_t st) {
+    if (n <= 1) return cudaSuccess;
+    const int nb = (int)((n + kSortTile - 1) / kSortTile);
+    const int cnt = 256 * nb;
+    char* p = static_cast<char*>(tmp);
+    int32_t* hist = reinterpret_cast<int32_t*>(p);
+    p += ((size_t)(cnt + 1) * 4 + 255) & ~(size_t)255;
+    int32_t* offs = reinterpret_cast<int32_t*>(p);
+    p += ((size_t)(cnt + 1) * 4 + 255) & ~(size_t)255;
+    void* scan_tmp = p;
+    p += (scan_tmp_bytes(cnt) + 255) & ~(size_t)255;
+    unsigned long long* k2 = reinterpret_cast<unsigned long long*>(p);
+    p += ((size_t)n * 8 + 255) & ~(size_t)255;
+    int32_t* v2 = reinterpret_cast<int32_t*>(p);
+    unsigned long long* ka = keys;
+    unsigned long long* kb = k2;
+    int32_t* va = vals;
+    int32_t* vb = v2;
+    int passes = 0;
+    for (int shift = 0; shift < bits; shift += 8, ++passes) {
+        k_sort_hist<<<nb, kBlock, 0, st>>>(ka, n, shift, nb, hist);
+        cudaError_t e = launch_exclusive_scan(hist, cnt, offs, scan_tmp, st);
+        if (e != cudaSuccess) return e;
+        k_sort_scatter<<<nb, kBlock, 0, st>>>(ka, va, n, shift, nb, offs, kb, vb);
+        unsigned long long* tk = ka; ka = kb; kb = tk;
+        int32_t* tv = va; va = vb; vb = tv;
+    }
+    if (passes & 1) {
+        cudaError_t e = cudaMemcpyAsync(keys, ka, (size_t)n * 8, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(vals, va, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
     return cudaGetLastError();
 }
 

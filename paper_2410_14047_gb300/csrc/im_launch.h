@@ -22,26 +22,52 @@ enum StatIndex : int {
     kStCoverNew,
     kStSweepLevels,
     kStCoverLevels,
+    kStSweepHeavy,
+    kStSweepHeavySims,
     kStCount
 };
 
 enum FrontierMode : int { kPush = 0, kCover = 1 };
 
-struct FrontierArgs {
+
+// One frontier level (propagation sweep or cover level).  Queue t of a phase
+// lives in buffer t % 3; counters pack count << 38 | edges.
+struct LevelArgs {
     uint8_t* M;
     int J;
-    const uint32_t* X;     // J sorted draws
-    const uint16_t* tab;   // kTabSize range table
-    const QEntry* q_in;
-    const unsigned long long* ctr_in;
-    QEntry* q_out;
-    unsigned long long* ctr_out;
-    int32_t* gen;          // per-vertex enqueue stamps
+    int words;                           // J / 32 change-mask words per vertex
+    const uint32_t* X;
+    const uint16_t* tab;
+    const QEntry* ql_in;                 // light queue (flat edge space)
+    const unsigned long long* cl_in;
+    const QEntry* qh_in;                 // heavy queue (propagation only; may be NULL)
+    const unsigned long long* ch_in;
+    QEntry* ql_out;
+    unsigned long long* cl_out;
+    QEntry* qh_out;
+    unsigned long long* ch_out;
+    const QEntry* ql_prev;               // queues of the previous level (change-bit clearing)
+    const unsigned long long* cl_prev;
+    const QEntry* qh_prev;
+    const unsigned long long* ch_prev;
+    const uint32_t* chg_cur;             // n * words: simulations changed at the previous level
+    uint32_t* chg_next;
+    uint32_t* chg_prev;                  // cleared for the previous level's queues (may be NULL)
+    int all_changed;                     // level 0 of a build: every simulation counts as changed
+    int32_t heavy_indeg;
+    int light_batches;                   // 32-edge batches per claimed unit
+    unsigned int* claim;                 // dynamic work counter of this level
+    int32_t* gen;
     int32_t gen_next;
-    unsigned long long* count;  // visited-register counter (cover)
-    unsigned long long* stats;  // kStCount counters
+    unsigned long long* count;           // visited-register counter (cover)
+    unsigned long long* stats;
     uint32_t* err;
 };
+
+int level_grid();
+cudaError_t launch_level(int kind, int mode, const GraphDev& g, const LevelArgs& a, int grid,
+                         cudaStream_t st);
+cudaError_t launch_init_queues(int kind, const GraphDev& g, const LevelArgs& a, cudaStream_t st);
 
 struct PickArgs {
     uint8_t* M;
@@ -58,6 +84,7 @@ struct PickArgs {
     const int32_t* rp_out;
     QEntry* q_cover;              // cover queue, level 0
     unsigned long long* ctr_cover;
+    uint32_t* chg0;               // change mask of cover level 0 (n * J/32 words)
     unsigned long long* count;
     int mark;                     // 1: mark the seed's row visited and queue it for the cover
 };
@@ -67,14 +94,12 @@ int pick_grid(int32_t n, int J);
 cudaError_t launch_sims(uint64_t seed, int J, uint32_t* X, uint32_t* salt, uint16_t* tab,
                         cudaStream_t st);
 cudaError_t launch_fill(uint8_t* M, int32_t n, int J, const uint32_t* salt, cudaStream_t st);
-cudaError_t launch_frontier(int kind, int mode, const GraphDev& g, const FrontierArgs& a,
-                            int grid, cudaStream_t st);
-int frontier_grid();
 cudaError_t launch_pick(const PickArgs& a, cudaStream_t st);
 // Marks row s visited (adding the newly visited registers to *count) and
 // queues s as level 0 of a cover.
 cudaError_t launch_cover_seed(uint8_t* M, int J, int32_t s, const int32_t* rp_out, QEntry* q,
-                              unsigned long long* ctr, unsigned long long* count, cudaStream_t st);
+                              unsigned long long* ctr, uint32_t* chg0, unsigned long long* count,
+                              cudaStream_t st);
 cudaError_t launch_sums(const uint8_t* M, int32_t n, int J, unsigned long long* S, cudaStream_t st);
 cudaError_t launch_count_visited(const uint8_t* M, int64_t bytes, unsigned long long* out,
                                  cudaStream_t st);
@@ -85,16 +110,19 @@ cudaError_t launch_indegree(const int32_t* col, int64_t m, int32_t* cnt, cudaStr
 size_t scan_tmp_bytes(int32_t n);
 cudaError_t launch_exclusive_scan(const int32_t* cnt, int32_t n, int32_t* out, void* tmp,
                                   cudaStream_t st);
-cudaError_t launch_scatter_in(const int32_t* rp_out, const int32_t* col_out, int32_t n,
-                              const int32_t* rp_in, int32_t* fill, int32_t* src_in,
-                              const uint32_t* thr_out, uint32_t* thr_in, cudaStream_t st);
+// In-CSR sorted by (target, trivalency class, edge hash): src_in, h_in (edge
+// hashes), thr_in (explicit models, may be NULL), cls_split (trivalency, may
+// be NULL).  rp_in must already hold the in-CSR row pointers.
+size_t build_in_csr_tmp_bytes(int64_t m);
+cudaError_t launch_build_in_csr(const int32_t* rp_out, const int32_t* col_out, int32_t n, int64_t m,
+                                int kind, uint32_t tri_seed, const uint32_t* thr_out,
+                                const int32_t* rp_in, int32_t* src_in, uint32_t* h_in,
+                                uint32_t* thr_in, int2* cls_split, void* tmp, cudaStream_t st);
+cudaError_t launch_radix_sort(unsigned long long* keys, int32_t* vals, int64_t n, int bits,
+                              void* tmp, cudaStream_t st);
+size_t sort_tmp_bytes(int64_t n);
 cudaError_t launch_thr_wc(const int32_t* rp_in, int32_t n, uint32_t* thr_v, cudaStream_t st);
 cudaError_t launch_thr_explicit(const float* w, int64_t m, uint32_t* thr, cudaStream_t st);
-// queue of every vertex with in-degree > 0 (offsets = rp_in), count returned in *count_dev
-cudaError_t launch_all_queue(const int32_t* rp_in, int32_t n, const uint32_t* thr_v,
-                             const int32_t* pos, QEntry* q, cudaStream_t st);
-cudaError_t launch_flag_nonzero_in(const int32_t* rp_in, int32_t n, int32_t* flag,
-                                   cudaStream_t st);
 
 // Monte-Carlo spread (independent coins): simulations of a batch are bits of
 // `words` 32-bit words per vertex.

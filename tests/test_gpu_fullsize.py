@@ -1,0 +1,67 @@
+"""Parity at the full mid-size workload (R-MAT scale 20, WC, J=256, K=50) in
+the configuration bench.py times: seeds, scores and estimates against the
+oracle's stored run (tests/golden/make_golden.py), plus sampled registers
+(one oracle BFS each) and whole visited columns (oracle reach sets)."""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def setup():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2410_14047_gb300 as im
+    wl = W.workload("rmat20")
+    g = wl.graph()
+    gold = json.load(open(os.path.join(GOLDEN, "select_rmat20.json")))
+    h = hashlib.sha256()
+    h.update(g.rowptr.tobytes())
+    h.update(g.col.tobytes())
+    assert h.hexdigest() == gold["graph_sha256"], "generator output differs from the golden run"
+    ctx = im.im_ctx_create(0)
+    G = im.im_graph_load(ctx, g.rowptr, g.col, wl.model)
+    return im, ctx, G, g, wl, gold
+
+
+def test_mid_workload_selection_matches_oracle(setup):
+    im, ctx, G, g, wl, gold = setup
+    r = im.im_select_seeds(G, wl.K, wl.J, seed=wl.seed, rebuild_eps=wl.rebuild_eps, return_sketch=True)
+    assert r["seeds"].tolist() == gold["seeds"]
+    assert r["score"].tolist() == gold["score"]
+    np.testing.assert_allclose(r["est"], [float.fromhex(x) for x in gold["est"]], rtol=1e-12, atol=0)
+    M = r["sketch"].registers()
+    assert hashlib.sha256(M.tobytes()).hexdigest() == gold["registers_sha256"]
+    assert im.im_last_stats(ctx)["builds"] == 1 + gold["rebuilds"]
+    # visited columns equal the oracle's reach sets of the seed set
+    X, _ = r["sketch"].sims()
+    thr = O.thresholds(g, wl.model)
+    for j in (0, 77, 255):
+        assert np.array_equal(M[:, j] == 0xFF, O.reach_mark(g, thr, X[j], gold["seeds"]))
+
+
+def test_mid_workload_build_sampled_registers(setup):
+    im, ctx, G, g, wl, gold = setup
+    sk = im.im_sketch_build(G, wl.J, wl.seed)
+    M = sk.registers()
+    X, salt = sk.sims()
+    Xo, so = O.draw_sims(wl.seed, wl.J)
+    assert np.array_equal(X, Xo) and np.array_equal(salt, so)
+    thr = O.thresholds(g, wl.model)
+    rng = np.random.default_rng(5)
+    deg = np.diff(g.rowptr)
+    hubs = np.argsort(deg)[-20:]
+    us = np.concatenate([rng.integers(0, g.n, 60), hubs])
+    for u in us:
+        for j in rng.integers(0, wl.J, 3):
+            assert M[u, j] == O.register_entry(g, thr, X[j], salt[j], int(u)), (u, j)

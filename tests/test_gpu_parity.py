@@ -287,3 +287,25 @@ def test_errors(im, ctx):
         im.im_graph_load(small, g.rowptr, g.col, MODELS["p30"])
     assert e.value.status == -3
     assert im.im_ctx_bytes_in_use(small) == 0
+
+
+# --- schedule knobs change the work split, never the result ---------------------------------
+
+@pytest.mark.parametrize("tuning", [{"heavy_indeg": 0}, {"heavy_indeg": 8, "light_batches": 1},
+                                    {"heavy_indeg": 1 << 30, "light_batches": 16},
+                                    {"heavy_indeg": 32, "grid_blocks": 7, "check_every": 1}])
+@pytest.mark.parametrize("gname,mname,J", [("rmat12", "wc", 256), ("cl5k", "p01", 64),
+                                           ("er2k", "wc", 1024), ("rmat12", "tri", 32)])
+def test_tuning_does_not_change_results(im, ctx, tuning, gname, mname, J):
+    g = GRAPHS[gname]
+    model = MODELS[mname]
+    c2 = im.im_ctx_create(0)
+    im.im_ctx_set_tuning(c2, tuning)
+    G = im.im_graph_load(c2, g.rowptr, g.col, model)
+    r = im.im_select_seeds(G, 6, J, seed=55, return_sketch=True)
+    ref = O.select_seeds(g, O.thresholds(g, model), J, 6, 55, 0.01, "reverse")
+    assert r["seeds"].tolist() == ref["seeds"].tolist()
+    assert np.array_equal(r["score"], ref["score"])
+    assert np.array_equal(r["sketch"].registers(), ref["M"])
+    if tuning.get("heavy_indeg") == 0 and mname in ("wc", "p01") and J >= 32:
+        assert im.im_last_stats(c2)["sweep_vertices"] > 0
