@@ -114,12 +114,15 @@ typedef struct {
  * is pushed by per-simulation hash search instead of an in-edge scan;
  * light_batches: 32-edge batches a warp claims at once; grid_blocks: blocks
  * per frontier launch (0 = SM count x occupancy); check_every: frontier
- * launches between the host's first two emptiness checks (then doubling to 8). */
+ * launches between the host's first two emptiness checks (then doubling to 8);
+ * persistent: 1 = all levels of a phase in one cooperative launch with grid
+ * barriers between levels (per-level launches when tracing). */
 typedef struct {
     int32_t heavy_indeg;
     int32_t light_batches;
     int32_t grid_blocks;
     int32_t check_every;
+    int32_t persistent;
 } im_tuning;
 
 /* One frontier launch of the last selection / build (tracing on). */
@@ -152,7 +155,7 @@ IM_API im_status im_last_stats(const im_ctx* ctx, im_stats* out);
  * stream and report per-kind kernel time in im_stats (adds two event records
  * per launch).  Off by default. */
 IM_API im_status im_ctx_set_timing(im_ctx* ctx, int enable);
-/* Sets (NULL = defaults {64, 4, 0, 2}) or reads the schedule knobs. */
+/* Sets (NULL = defaults {64, 4, 0, 2, 1}) or reads the schedule knobs. */
 IM_API im_status im_ctx_set_tuning(im_ctx* ctx, const im_tuning* tuning);
 IM_API im_status im_ctx_get_tuning(const im_ctx* ctx, im_tuning* tuning);
 /* enable != 0: also keep one im_trace_rec per frontier launch (implies timing). */

@@ -42,7 +42,7 @@ struct im_ctx {
     bool trace = false;
     std::vector<float> launch_ms;    // kernel time per launch sequence number (tracing)
     std::vector<im_trace_rec> recs;  // frontier launches of the last call
-    im_tuning tuning{64, 4, 0, 2};
+    im_tuning tuning{64, 4, 0, 2, 1};
 };
 
 namespace {
@@ -215,7 +215,7 @@ struct im_sketch {
     im_graph* g = nullptr;
     int32_t J = 0;
     DBuf M, X, salt, tab, ql[3], qh[3], ctr, claim, chg[3], gen, seed_bits, count, part_S, part_u,
-        ticket, stats, err;
+        ticket, stats, err, bar;
     DBuf out_seed, out_S, out_est;
     int32_t out_cap = 0;
     int32_t gen_counter = 0;
@@ -276,11 +276,11 @@ extern "C" im_status im_ctx_set_timing(im_ctx* c, int enable) {
 extern "C" im_status im_ctx_set_tuning(im_ctx* c, const im_tuning* t) {
     if (!c) return IM_E_INVAL;
     if (!t) {
-        c->tuning = im_tuning{64, 4, 0, 2};
+        c->tuning = im_tuning{64, 4, 0, 2, 1};
         return IM_OK;
     }
     if (t->heavy_indeg < 0 || t->light_batches < 1 || t->light_batches > 4096 || t->grid_blocks < 0 ||
-        t->check_every < 1 || t->check_every > 64)
+        t->check_every < 1 || t->check_every > 64 || t->persistent < 0 || t->persistent > 1)
         return fail(c, IM_E_INVAL, "tuning out of range");
     c->tuning = *t;
     return IM_OK;
@@ -478,7 +478,7 @@ static void sketch_release(im_sketch* sk) {
                     &sk->qh[0], &sk->qh[1], &sk->qh[2], &sk->ctr, &sk->claim, &sk->chg[0],
                     &sk->chg[1], &sk->chg[2], &sk->gen, &sk->seed_bits, &sk->count, &sk->part_S,
                     &sk->part_u, &sk->ticket, &sk->stats, &sk->err, &sk->out_seed, &sk->out_S,
-                    &sk->out_est})
+                    &sk->out_est, &sk->bar})
         dfree(c, *b);
 }
 
@@ -511,6 +511,7 @@ static im_status sketch_alloc(im_graph* g, int32_t J, im_sketch** out) {
     A(sk->ticket, 4);
     A(sk->stats, (size_t)kStCount * 8);
     A(sk->err, 4);
+    A(sk->bar, 16);
     if (s != IM_OK) {
         sketch_release(sk);
         delete sk;
@@ -578,6 +579,7 @@ static im_status check_err(im_sketch* sk) {
     CK(c, sync_collect(c));
     if (err & kErrQueue) return fail(c, IM_E_STATE, "frontier queue overflow");
     if (err & kErrCasLimit) return fail(c, IM_E_TIMEOUT, "register CAS retry limit exceeded");
+    if (err & kErrBarrier) return fail(c, IM_E_TIMEOUT, "grid barrier wait exceeded its time limit");
     return IM_OK;
 }
 
@@ -589,7 +591,43 @@ static im_status phase_begin(im_sketch* sk) {
     CK(c, cudaMemsetAsync(sk->ctr.p, 0, sk->ctr.bytes, st));
     CK(c, cudaMemsetAsync(sk->claim.p, 0, sk->claim.bytes, st));
     for (int i = 0; i < 3; ++i) CK(c, cudaMemsetAsync(sk->chg[i].p, 0, sk->chg[i].bytes, st));
+    CK(c, cudaMemsetAsync(sk->bar.p, 0, sk->bar.bytes, st));
     return IM_OK;
+}
+
+// All levels of a phase in one cooperative launch; one host synchronisation.
+static im_status run_phase_persistent(im_sketch* sk, int mode, bool all_first, int grid) {
+    im_graph* g = sk->g;
+    im_ctx* c = g->ctx;
+    auto st = c->stream;
+    PhaseArgs p{};
+    p.base = level_args(sk);
+    for (int i = 0; i < 3; ++i) {
+        p.ql[i] = sk->ql[i].as<QEntry>();
+        p.qh[i] = sk->qh[i].as<QEntry>();
+        p.chg[i] = sk->chg[i].as<uint32_t>();
+    }
+    p.ctr = sk->ctr.as<ulonglong2>();
+    p.claim = sk->claim.as<unsigned int>();
+    p.all_first = all_first ? 1 : 0;
+    p.max_levels = kMaxLevels - 2;
+    p.gen_base = sk->gen_counter + 1;
+    unsigned int* bar = sk->bar.as<unsigned int>();
+    p.bar_arrive = bar;
+    p.bar_gen = bar + 1;
+    p.abort_flag = bar + 2;
+    p.levels_out = reinterpret_cast<int*>(bar + 3);
+    p.limit_ns = 20ull * 1000 * 1000 * 1000;
+    CK(c, timed(c, mode == kPush ? kTPush : kTCover,
+                [&] { return launch_phase(g->kind, mode, g->dev, p, grid, st); }));
+    CK(c, cudaMemcpyAsync(c->pinned, bar, 16, cudaMemcpyDeviceToHost, st));
+    CK(c, sync_collect(c));
+    const unsigned int* hb = reinterpret_cast<const unsigned int*>(c->pinned);
+    const int levels = (int)hb[3];
+    sk->gen_counter += levels + 1;
+    if (levels >= p.max_levels)
+        return fail(c, IM_E_TIMEOUT, "frontier did not empty within %d levels", p.max_levels);
+    return check_err(sk);
 }
 
 // Runs frontier levels until both queues are empty.  Level t reads queue
@@ -601,6 +639,10 @@ static im_status run_levels(im_sketch* sk, int mode, bool all_first) {
     im_graph* g = sk->g;
     im_ctx* c = g->ctx;
     auto st = c->stream;
+    if (c->tuning.persistent && !c->trace) {
+        const int pgrid = phase_grid();
+        if (pgrid > 0) return run_phase_persistent(sk, mode, all_first, pgrid);
+    }
     ulonglong2* ctr = sk->ctr.as<ulonglong2>();
     unsigned int* claim = sk->claim.as<unsigned int>();
     LevelArgs a = level_args(sk);

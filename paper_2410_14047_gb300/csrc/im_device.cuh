@@ -24,7 +24,7 @@ constexpr int kCasRetryLimit = 4096;
 enum ModelKind : int { kUniform = 0, kWC = 1, kTrivalency = 2, kExplicit = 3 };
 
 // Error bits a kernel may raise (host turns them into IM_E_* codes).
-enum : uint32_t { kErrCasLimit = 1u, kErrQueue = 2u };
+enum : uint32_t { kErrCasLimit = 1u, kErrQueue = 2u, kErrBarrier = 4u };
 
 // Device view of a loaded graph.
 struct GraphDev {

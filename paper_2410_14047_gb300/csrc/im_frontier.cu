@@ -410,22 +410,28 @@ __device__ __forceinline__ void heavy_vertex(const GraphDev& g, const LevelArgs&
     }
 }
 
-template <int KIND, int MODE>
-__global__ void __launch_bounds__(kFBlock) k_level(GraphDev g, LevelArgs a) {
-    __shared__ __align__(16) uint32_t sX[kMaxJ];
-    __shared__ uint16_t sTab[kTabSize];
+struct LevelStats {
+    unsigned long long chunks = 0, cas = 0, fresh = 0, hsims = 0;
+};
+
+// Clears the change bits read by the level before the previous one.
+__device__ __forceinline__ void clear_prev_bits(const LevelArgs& a, int64_t warp, int64_t nwarps) {
+    if (!a.chg_prev) return;
     const int lane = (int)lane_id();
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    // clear the change bits read by the level before the previous one
-    if (a.chg_prev) {
-        const int32_t nlp = a.cl_prev ? (int32_t)(__ldcg(a.cl_prev) >> kCountShift) : 0;
-        const int32_t nhp = a.ch_prev ? (int32_t)(__ldcg(a.ch_prev) >> kCountShift) : 0;
-        for (int64_t i = warp; i < (int64_t)nlp + nhp; i += nwarps) {
-            const int32_t v = i < nlp ? __ldcg(&a.ql_prev[i].v) : __ldcg(&a.qh_prev[i - nlp].v);
-            if (lane < a.words) a.chg_prev[(size_t)v * a.words + lane] = 0u;
-        }
+    const int32_t nlp = a.cl_prev ? (int32_t)(__ldcg(a.cl_prev) >> kCountShift) : 0;
+    const int32_t nhp = a.ch_prev ? (int32_t)(__ldcg(a.ch_prev) >> kCountShift) : 0;
+    for (int64_t i = warp; i < (int64_t)nlp + nhp; i += nwarps) {
+        const int32_t v = i < nlp ? __ldcg(&a.ql_prev[i].v) : __ldcg(&a.qh_prev[i - nlp].v);
+        if (lane < a.words) a.chg_prev[(size_t)v * a.words + lane] = 0u;
     }
+}
+
+// Work of one level: heavy vertices first, then slices of light batches, all
+// claimed from the level's counter.
+template <int KIND, int MODE>
+__device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a, const uint32_t* sX,
+                                           const uint16_t* sTab, int64_t warp, LevelStats& ls) {
+    const int lane = (int)lane_id();
     const unsigned long long cl = __ldcg(a.cl_in);
     const unsigned long long ch = a.ch_in ? __ldcg(a.ch_in) : 0ull;
     const int32_t nl = (int32_t)(cl >> kCountShift);
@@ -435,9 +441,6 @@ __global__ void __launch_bounds__(kFBlock) k_level(GraphDev g, LevelArgs a) {
     const int64_t lunits = (nbl + a.light_batches - 1) / a.light_batches;
     const int64_t total = (int64_t)nh + lunits;
     if (total == 0) return;
-    for (int i = threadIdx.x; i < a.J; i += blockDim.x) sX[i] = __ldg(a.X + i);
-    for (int i = threadIdx.x; i < kTabSize; i += blockDim.x) sTab[i] = __ldg(a.tab + i);
-    __syncthreads();
     if (warp == 0 && lane == 0) {
         atomicAdd(a.stats + (MODE == kPush ? kStSweepVertices : kStCoverVertices),
                   (unsigned long long)(nl + nh));
@@ -445,7 +448,6 @@ __global__ void __launch_bounds__(kFBlock) k_level(GraphDev g, LevelArgs a) {
         atomicAdd(a.stats + (MODE == kPush ? kStSweepLevels : kStCoverLevels), 1ull);
         if (MODE == kPush) atomicAdd(a.stats + kStSweepHeavy, (unsigned long long)nh);
     }
-    unsigned long long st_chunks = 0, st_cas = 0, st_new = 0, st_hsims = 0;
     for (;;) {
         unsigned int unit = 0;
         if (lane == 0) unit = atomicAdd(a.claim, 1u);
@@ -456,31 +458,199 @@ __global__ void __launch_bounds__(kFBlock) k_level(GraphDev g, LevelArgs a) {
                 const int4 raw = __ldcg(reinterpret_cast<const int4*>(a.qh_in) + unit);
                 QEntry ent;
                 ent.v = raw.x; ent.rp = raw.y; ent.off = raw.z; ent.aux = (uint32_t)raw.w;
-                heavy_vertex<KIND>(g, a, sX, ent, st_hsims, st_cas);
+                heavy_vertex<KIND>(g, a, sX, ent, ls.hsims, ls.cas);
             }
         } else {
             const int64_t lu = (int64_t)unit - nh;
             const int64_t b0 = lu * a.light_batches;
             const int64_t b1 = min(nbl, b0 + a.light_batches);
-            light_slice<KIND, MODE>(g, a, sX, sTab, b0, b1, nl, El, st_chunks, st_cas, st_new);
+            light_slice<KIND, MODE>(g, a, sX, sTab, b0, b1, nl, El, ls.chunks, ls.cas, ls.fresh);
         }
     }
-    st_chunks = wsum(st_chunks);
-    st_cas = wsum(st_cas);
-    st_new = wsum(st_new);
-    st_hsims = wsum(st_hsims);
-    if (lane == 0) {
+}
+
+template <int MODE>
+__device__ __forceinline__ void flush_stats(const LevelArgs& a, LevelStats& ls) {
+    ls.chunks = wsum(ls.chunks);
+    ls.cas = wsum(ls.cas);
+    ls.fresh = wsum(ls.fresh);
+    ls.hsims = wsum(ls.hsims);
+    if (lane_id() == 0) {
         if constexpr (MODE == kPush) {
-            if (st_chunks) atomicAdd(a.stats + kStSweepChunks, st_chunks);
-            if (st_cas) atomicAdd(a.stats + kStSweepCas, st_cas);
-            if (st_hsims) atomicAdd(a.stats + kStSweepHeavySims, st_hsims);
+            if (ls.chunks) atomicAdd(a.stats + kStSweepChunks, ls.chunks);
+            if (ls.cas) atomicAdd(a.stats + kStSweepCas, ls.cas);
+            if (ls.hsims) atomicAdd(a.stats + kStSweepHeavySims, ls.hsims);
         } else {
-            if (st_chunks) atomicAdd(a.stats + kStCoverChunks, st_chunks);
-            if (st_new) {
-                atomicAdd(a.stats + kStCoverNew, st_new);
-                atomicAdd(a.count, st_new);
+            if (ls.chunks) atomicAdd(a.stats + kStCoverChunks, ls.chunks);
+            if (ls.fresh) {
+                atomicAdd(a.stats + kStCoverNew, ls.fresh);
+                atomicAdd(a.count, ls.fresh);
             }
         }
+    }
+    ls = LevelStats();
+}
+
+__device__ __forceinline__ void load_tables(const LevelArgs& a, uint32_t* sX, uint16_t* sTab) {
+    for (int i = threadIdx.x; i < a.J; i += blockDim.x) sX[i] = __ldg(a.X + i);
+    for (int i = threadIdx.x; i < kTabSize; i += blockDim.x) sTab[i] = __ldg(a.tab + i);
+    __syncthreads();
+}
+
+// One level per launch (used when the host traces every level).
+template <int KIND, int MODE>
+__global__ void __launch_bounds__(kFBlock) k_level(GraphDev g, LevelArgs a) {
+    __shared__ __align__(16) uint32_t sX[kMaxJ];
+    __shared__ uint16_t sTab[kTabSize];
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    clear_prev_bits(a, warp, nwarps);
+    const unsigned long long cl = __ldcg(a.cl_in);
+    const unsigned long long ch = a.ch_in ? __ldcg(a.ch_in) : 0ull;
+    if ((cl >> kCountShift) == 0 && (ch >> kCountShift) == 0) return;
+    load_tables(a, sX, sTab);
+    LevelStats ls;
+    level_work<KIND, MODE>(g, a, sX, sTab, warp, ls);
+    flush_stats<MODE>(a, ls);
+}
+
+// Grid-wide barrier of a cooperative launch: arrival counter + generation
+// word.  Every wait is bounded by `limit_ns` of global time; a block that
+// gives up raises kErrBarrier and the abort word, and all blocks leave the
+// phase at their next barrier.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ bool grid_barrier(unsigned int* arrive, volatile unsigned int* gen, volatile unsigned int* abort_flag,
+                             uint32_t* err, unsigned long long limit_ns) {
+    __syncthreads();
+    __shared__ bool ok;
+    if (threadIdx.x == 0) {
+        ok = true;
+        const unsigned int g0 = *gen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(arrive, 1u);
+        if (arrived == gridDim.x - 1) {
+            *arrive = 0u;
+            __threadfence();
+            atomicAdd((unsigned int*)gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*gen == g0) {
+                if (*abort_flag) { ok = false; break; }
+                if (global_ns() - t0 > limit_ns) {
+                    atomicOr(err, kErrBarrier);
+                    *abort_flag = 1u;
+                    ok = false;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*abort_flag) ok = false;
+    }
+    __syncthreads();
+    return ok;
+}
+
+// All levels of one phase in one cooperative launch: level t uses queue
+// buffers t % 3 as in k_level; a grid barrier separates levels; the phase
+// ends when both queues of the next level are empty.
+template <int KIND, int MODE>
+__global__ void __launch_bounds__(kFBlock) k_phase(GraphDev g, PhaseArgs p) {
+    __shared__ __align__(16) uint32_t sX[kMaxJ];
+    __shared__ uint16_t sTab[kTabSize];
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    LevelArgs a = p.base;
+    load_tables(a, sX, sTab);
+    LevelStats ls;
+    int t = 0;
+    for (; t < p.max_levels; ++t) {
+        const int bi = t % 3, bo = (t + 1) % 3, bp = (t + 2) % 3;
+        a.ql_in = p.ql[bi];
+        a.cl_in = &p.ctr[t].x;
+        a.qh_in = p.qh[bi];
+        a.ch_in = MODE == kPush ? &p.ctr[t].y : nullptr;
+        a.ql_out = p.ql[bo];
+        a.cl_out = &p.ctr[t + 1].x;
+        a.qh_out = p.qh[bo];
+        a.ch_out = &p.ctr[t + 1].y;
+        if (t >= 1) {
+            a.ql_prev = p.ql[bp];
+            a.cl_prev = &p.ctr[t - 1].x;
+            a.qh_prev = p.qh[bp];
+            a.ch_prev = MODE == kPush ? &p.ctr[t - 1].y : nullptr;
+            a.chg_prev = p.chg[bp];
+        } else {
+            a.ql_prev = nullptr; a.cl_prev = nullptr; a.qh_prev = nullptr; a.ch_prev = nullptr;
+            a.chg_prev = nullptr;
+        }
+        a.chg_cur = p.chg[bi];
+        a.chg_next = p.chg[bo];
+        a.all_changed = (t == 0 && p.all_first) ? 1 : 0;
+        a.claim = p.claim + t;
+        a.gen_next = p.gen_base + t;
+        clear_prev_bits(a, warp, nwarps);
+        level_work<KIND, MODE>(g, a, sX, sTab, warp, ls);
+        if (!grid_barrier(p.bar_arrive, p.bar_gen, p.abort_flag, a.err, p.limit_ns)) break;
+        const unsigned long long c2l = __ldcg(&p.ctr[t + 1].x);
+        const unsigned long long c2h = __ldcg(&p.ctr[t + 1].y);
+        if ((c2l >> kCountShift) == 0 && (c2h >> kCountShift) == 0) { ++t; break; }
+    }
+    flush_stats<MODE>(a, ls);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *p.levels_out = t;
+}
+
+int phase_grid() {
+    static int grid = 0;
+    if (grid == 0) {
+        int dev = 0, sms = 152, per_sm = 0, coop = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phase<kWC, kPush>, kFBlock, 0);
+        int pc = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, k_phase<kWC, kCover>, kFBlock, 0);
+        if (pc < per_sm) per_sm = pc;
+        for (int kd : {0, 2, 3}) {
+            int q = 0;
+            if (kd == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_phase<kUniform, kPush>, kFBlock, 0);
+            if (kd == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_phase<kTrivalency, kPush>, kFBlock, 0);
+            if (kd == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_phase<kExplicit, kPush>, kFBlock, 0);
+            if (q < per_sm) per_sm = q;
+        }
+        if (per_sm < 1 || !coop) per_sm = 0;
+        grid = sms * per_sm;
+    }
+    return grid;
+}
+
+template <int KIND, int MODE>
+static cudaError_t coop_launch(const GraphDev& g, const PhaseArgs& p, int grid, cudaStream_t st) {
+    void* args[] = {(void*)&g, (void*)&p};
+    return cudaLaunchCooperativeKernel((const void*)k_phase<KIND, MODE>, dim3(grid), dim3(kFBlock), args, 0, st);
+}
+
+cudaError_t launch_phase(int kind, int mode, const GraphDev& g, const PhaseArgs& p, int grid,
+                         cudaStream_t st) {
+    if (mode == kPush) {
+        switch (kind) {
+            case kUniform: return coop_launch<kUniform, kPush>(g, p, grid, st);
+            case kWC: return coop_launch<kWC, kPush>(g, p, grid, st);
+            case kTrivalency: return coop_launch<kTrivalency, kPush>(g, p, grid, st);
+            default: return coop_launch<kExplicit, kPush>(g, p, grid, st);
+        }
+    }
+    switch (kind) {
+        case kUniform: return coop_launch<kUniform, kCover>(g, p, grid, st);
+        case kWC: return coop_launch<kWC, kCover>(g, p, grid, st);
+        case kTrivalency: return coop_launch<kTrivalency, kCover>(g, p, grid, st);
+        default: return coop_launch<kExplicit, kCover>(g, p, grid, st);
     }
 }
 

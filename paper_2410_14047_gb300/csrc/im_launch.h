@@ -64,7 +64,28 @@ struct LevelArgs {
     uint32_t* err;
 };
 
+// All levels of a phase in one cooperative launch (grid barrier between levels).
+struct PhaseArgs {
+    LevelArgs base;                      // fields that do not depend on the level
+    QEntry* ql[3];
+    QEntry* qh[3];
+    ulonglong2* ctr;                     // per level: (light, heavy) packed counters
+    unsigned int* claim;                 // per level work counters
+    uint32_t* chg[3];
+    int all_first;
+    int max_levels;
+    int32_t gen_base;                    // enqueue stamp of level t = gen_base + t
+    unsigned int* bar_arrive;
+    unsigned int* bar_gen;
+    unsigned int* abort_flag;
+    unsigned long long limit_ns;         // bound on every barrier wait
+    int* levels_out;                     // levels the phase ran
+};
+
 int level_grid();
+int phase_grid();  // 0 when cooperative launch is unavailable
+cudaError_t launch_phase(int kind, int mode, const GraphDev& g, const PhaseArgs& p, int grid,
+                         cudaStream_t st);
 cudaError_t launch_level(int kind, int mode, const GraphDev& g, const LevelArgs& a, int grid,
                          cudaStream_t st);
 cudaError_t launch_init_queues(int kind, const GraphDev& g, const LevelArgs& a, cudaStream_t st);
