@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--mode", default="select", choices=["select", "build"],
                     help="select: the benchmark; build: time im_sketch_build only (profiling)")
+    ap.add_argument("--tuning", default="",
+                    help="JSON schedule knobs passed to im_ctx_set_tuning (profiling and sweeps)")
     ap.add_argument("--quick", action="store_true",
                     help="profiling runs: no clock sampling, end-to-end pass or CPU baseline")
     return ap.parse_args()
@@ -199,6 +201,8 @@ def run_gpu(args):
     wl = W.workload(args.workload)
     g = wl.graph()
     ctx = im.im_ctx_create(local)
+    if args.tuning:
+        im.im_ctx_set_tuning(ctx, json.loads(args.tuning))
     G = im.im_graph_load(ctx, g.rowptr, g.col, wl.model)
     im.im_ctx_set_timing(ctx, True)
 

@@ -106,6 +106,8 @@ typedef struct {
     uint64_t alg_bytes_sweep; /* algorithmic bytes of all sweeps (see the design notes) */
     uint64_t sweep_heavy;     /* hub vertices pushed by per-simulation hash search */
     uint64_t sweep_heavy_sims;/* (hub, changed simulation) searches */
+    uint64_t sweep_batches;   /* 32-edge batches resolved by propagation levels */
+    uint64_t sweep_dealt;     /* 16-simulation chunk items dealt (before the live test) */
 } im_stats;
 
 /* Schedule knobs of the frontier kernels (chosen by the autotuner; results
@@ -116,13 +118,17 @@ typedef struct {
  * per frontier launch (0 = SM count x occupancy); check_every: frontier
  * launches between the host's first two emptiness checks (then doubling to 8);
  * persistent: 1 = all levels of a phase in one cooperative launch with grid
- * barriers between levels (per-level launches when tracing). */
+ * barriers between levels (per-level launches when tracing); dense_div: a
+ * propagation level whose frontier exceeds (vertices with in-edges) /
+ * dense_div walks every such vertex in vertex order (0 = never; the first
+ * level of a build always does when dense_div > 0). */
 typedef struct {
     int32_t heavy_indeg;
     int32_t light_batches;
     int32_t grid_blocks;
     int32_t check_every;
     int32_t persistent;
+    int32_t dense_div;
 } im_tuning;
 
 /* One frontier launch of the last selection / build (tracing on). */
@@ -155,7 +161,7 @@ IM_API im_status im_last_stats(const im_ctx* ctx, im_stats* out);
  * stream and report per-kind kernel time in im_stats (adds two event records
  * per launch).  Off by default. */
 IM_API im_status im_ctx_set_timing(im_ctx* ctx, int enable);
-/* Sets (NULL = defaults {64, 4, 0, 2, 1}) or reads the schedule knobs. */
+/* Sets (NULL = defaults {64, 4, 0, 2, 1, 8}) or reads the schedule knobs. */
 IM_API im_status im_ctx_set_tuning(im_ctx* ctx, const im_tuning* tuning);
 IM_API im_status im_ctx_get_tuning(const im_ctx* ctx, im_tuning* tuning);
 /* enable != 0: also keep one im_trace_rec per frontier launch (implies timing). */

@@ -60,13 +60,14 @@ class im_stats(ctypes.Structure):
                [(k, ctypes.c_uint64) for k in ("sweep_vertices", "sweep_edges", "sweep_chunks",
                                                "sweep_cas", "sweep_changed", "cover_edges",
                                                "cover_chunks", "visited", "alg_bytes_sweep",
-                                               "sweep_heavy", "sweep_heavy_sims")]
+                                               "sweep_heavy", "sweep_heavy_sims", "sweep_batches",
+                                               "sweep_dealt")]
 
 
 class im_tuning(ctypes.Structure):
     _fields_ = [("heavy_indeg", ctypes.c_int32), ("light_batches", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("persistent", ctypes.c_int32)]
+                ("persistent", ctypes.c_int32), ("dense_div", ctypes.c_int32)]
 
 
 class im_trace_rec(ctypes.Structure):

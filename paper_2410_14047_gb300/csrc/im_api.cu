@@ -42,7 +42,7 @@ struct im_ctx {
     bool trace = false;
     std::vector<float> launch_ms;    // kernel time per launch sequence number (tracing)
     std::vector<im_trace_rec> recs;  // frontier launches of the last call
-    im_tuning tuning{64, 4, 0, 2, 1};
+    im_tuning tuning{64, 4, 0, 2, 1, 8};
 };
 
 namespace {
@@ -207,7 +207,8 @@ struct im_graph {
     int32_t n = 0;
     int64_t m = 0;
     int kind = kUniform;
-    DBuf rp_out, col_out, rp_in, src_in, h_in, thr_v, thr_out, thr_in, cls_split;
+    DBuf rp_out, col_out, rp_in, src_in, h_in, h_out, thrw_out, thr_v, thr_out, thr_in, cls_split, q_dense;
+    int32_t n_dense = 0;
     GraphDev dev{};
 };
 
@@ -276,11 +277,12 @@ extern "C" im_status im_ctx_set_timing(im_ctx* c, int enable) {
 extern "C" im_status im_ctx_set_tuning(im_ctx* c, const im_tuning* t) {
     if (!c) return IM_E_INVAL;
     if (!t) {
-        c->tuning = im_tuning{64, 4, 0, 2, 1};
+        c->tuning = im_tuning{64, 4, 0, 2, 1, 8};
         return IM_OK;
     }
     if (t->heavy_indeg < 0 || t->light_batches < 1 || t->light_batches > 4096 || t->grid_blocks < 0 ||
-        t->check_every < 1 || t->check_every > 64 || t->persistent < 0 || t->persistent > 1)
+        t->check_every < 1 || t->check_every > 64 || t->persistent < 0 || t->persistent > 1 ||
+        t->dense_div < 0)
         return fail(c, IM_E_INVAL, "tuning out of range");
     c->tuning = *t;
     return IM_OK;
@@ -345,8 +347,8 @@ static im_status check_model(im_ctx* c, const im_model* mdl, int64_t m) {
 
 static void graph_release(im_graph* g) {
     im_ctx* c = g->ctx;
-    for (DBuf* b : {&g->rp_out, &g->col_out, &g->rp_in, &g->src_in, &g->h_in, &g->thr_v,
-                    &g->thr_out, &g->thr_in, &g->cls_split})
+    for (DBuf* b : {&g->rp_out, &g->col_out, &g->rp_in, &g->src_in, &g->h_in, &g->h_out,
+                    &g->thrw_out, &g->thr_v, &g->thr_out, &g->thr_in, &g->cls_split, &g->q_dense})
         dfree(c, *b);
 }
 
@@ -414,7 +416,10 @@ extern "C" im_status im_graph_load(im_ctx* c, int32_t n, int64_t m, const int32_
     if ((s = dalloc(c, rp_bytes, g->rp_in)) != IM_OK) return bail(s);
     if ((s = dalloc(c, e_bytes, g->src_in)) != IM_OK) return bail(s);
     if ((s = dalloc(c, e_bytes, g->h_in)) != IM_OK) return bail(s);
+    if ((s = dalloc(c, e_bytes, g->h_out)) != IM_OK) return bail(s);
+    if ((s = dalloc(c, e_bytes, g->thrw_out)) != IM_OK) return bail(s);
     if ((s = dalloc(c, (size_t)n * 4, g->thr_v)) != IM_OK) return bail(s);
+    if ((s = dalloc(c, (size_t)n * sizeof(QEntry), g->q_dense)) != IM_OK) return bail(s);
     if (model->kind == kTrivalency && (s = dalloc(c, (size_t)n * 8, g->cls_split)) != IM_OK) return bail(s);
     DBuf cnt, tmp;
     if ((s = dalloc(c, ((size_t)n + 1) * 4, cnt)) != IM_OK) return bail(s);
@@ -429,6 +434,10 @@ extern "C" im_status im_graph_load(im_ctx* c, int32_t n, int64_t m, const int32_
     if (e == cudaSuccess) e = launch_indegree(g->col_out.as<int32_t>(), m, cnt.as<int32_t>(), st);
     if (e == cudaSuccess) e = launch_exclusive_scan(cnt.as<int32_t>(), n, g->rp_in.as<int32_t>(), tmp.p, st);
     if (e == cudaSuccess) e = launch_thr_wc(g->rp_in.as<int32_t>(), n, g->thr_v.as<uint32_t>(), st);
+    if (e == cudaSuccess)
+        e = launch_out_edge_words(g->rp_out.as<int32_t>(), g->col_out.as<int32_t>(), n, m,
+                                  g->thr_v.as<uint32_t>(), g->h_out.as<uint32_t>(),
+                                  g->thrw_out.as<uint32_t>(), st);
     if (e != cudaSuccess) { release_tmp(); return bail(cuda_fail(c, e, "graph load")); }
     if ((s = set_model(g, model)) != IM_OK) { release_tmp(); return bail(s); }
     if (g->kind == kExplicit && m > 0) {
@@ -439,9 +448,19 @@ extern "C" im_status im_graph_load(im_ctx* c, int32_t n, int64_t m, const int32_
                             g->dev.tri_seed, g->thr_out.as<uint32_t>(), g->rp_in.as<int32_t>(),
                             g->src_in.as<int32_t>(), g->h_in.as<uint32_t>(), g->thr_in.as<uint32_t>(),
                             g->cls_split.as<int2>(), tmp.p, st);
+    // static vertex-ordered queue for dense levels (cnt and tmp reused as scratch)
+    DBuf pos;
+    if (e == cudaSuccess && (s = dalloc(c, ((size_t)n + 1) * 4, pos)) != IM_OK) { release_tmp(); return bail(s); }
+    if (e == cudaSuccess)
+        e = launch_dense_queue(g->rp_in.as<int32_t>(), n, g->thr_v.as<uint32_t>(), cnt.as<int32_t>(),
+                               pos.as<int32_t>(), tmp.p, g->q_dense.as<QEntry>(), st);
+    int32_t nd = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nd, pos.as<int32_t>() + n, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dfree(c, pos);
     release_tmp();
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "graph load"));
+    g->n_dense = nd;
     g->dev.n = n;
     g->dev.m = m;
     g->dev.rp_out = g->rp_out.as<int32_t>();
@@ -449,6 +468,8 @@ extern "C" im_status im_graph_load(im_ctx* c, int32_t n, int64_t m, const int32_
     g->dev.rp_in = g->rp_in.as<int32_t>();
     g->dev.src_in = g->src_in.as<int32_t>();
     g->dev.h_in = g->h_in.as<uint32_t>();
+    g->dev.h_out = g->h_out.as<uint32_t>();
+    g->dev.thrw_out = g->thrw_out.as<uint32_t>();
     g->dev.thr_v = g->thr_v.as<uint32_t>();
     g->dev.thr_out = g->thr_out.as<uint32_t>();
     g->dev.thr_in = g->thr_in.as<uint32_t>();
@@ -568,6 +589,10 @@ static LevelArgs level_args(im_sketch* sk) {
     // the heavy path reads 32 register bytes per lane: J >= 32 only
     a.heavy_indeg = sk->J >= 32 ? t.heavy_indeg : 0x7FFFFFFF;
     a.light_batches = t.light_batches > 0 ? t.light_batches : 4;
+    a.q_dense = sk->g->q_dense.as<QEntry>();
+    a.n_dense = sk->g->n_dense;
+    a.e_dense = sk->g->m;
+    a.dense_div = t.dense_div;
     return a;
 }
 
@@ -756,6 +781,8 @@ static im_status stats_collect(im_sketch* sk) {
     s.visited = cnt;
     s.sweep_heavy = h[kStSweepHeavy];
     s.sweep_heavy_sims = h[kStSweepHeavySims];
+    s.sweep_batches = h[kStSweepBatches];
+    s.sweep_dealt = h[kStSweepDealt];
     // algorithmic bytes of the sweeps: queue entry (16 B) + the queued vertex's
     // register row (J B) per queued vertex, source id (4 B, + 4 B threshold for
     // explicit weights) per in-edge, one 16-byte target chunk read per chunk

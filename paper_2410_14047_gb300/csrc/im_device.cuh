@@ -35,6 +35,8 @@ struct GraphDev {
     const int32_t* rp_in;    // n+1, in-CSR row pointers
     const int32_t* src_in;   // m, in-neighbours (sources of in-edges), rows sorted by (class, hash)
     const uint32_t* h_in;    // m, edge hash hE(source, target) of every in-edge
+    const uint32_t* h_out;   // m, edge hash of every out-edge (out-CSR order)
+    const uint32_t* thrw_out;// m, weighted-cascade threshold of every out-edge
     const uint32_t* thr_v;   // kWC: threshold of every edge into v
     const uint32_t* thr_out; // kExplicit: per out-edge threshold
     const uint32_t* thr_in;  // kExplicit: per in-edge threshold
@@ -115,7 +117,7 @@ __device__ __forceinline__ uint32_t edge_threshold(const GraphDev& g, uint32_t u
         return g.thr_uniform;
     } else if constexpr (KIND == kWC) {
         if constexpr (IN_ORIENTATION) return aux;  // threshold of the queue vertex's in-edges
-        else return __ldg(g.thr_v + v);
+        else return __ldg(g.thrw_out + e);
     } else if constexpr (KIND == kTrivalency) {
         const uint32_t cls = hash_pair(u, v, g.tri_seed) % 3u;
         return cls == 0u ? g.tri_thr[0] : (cls == 1u ? g.tri_thr[1] : g.tri_thr[2]);

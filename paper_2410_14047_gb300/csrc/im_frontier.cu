@@ -108,27 +108,44 @@ __device__ __forceinline__ bool is_heavy(int32_t deg, uint32_t thr, int32_t heav
 }
 
 // Byte-wise max of cand into the 16 register bytes at trow through CAS on
-// 4-byte words.  Returns the changed registers as 16 bits.
+// 4-byte words: the four first attempts are issued together, retries (a word
+// changed by another thread meanwhile) one word at a time.  Returns the
+// changed registers as 16 bits.
 __device__ __forceinline__ uint32_t merge_chunk(uint8_t* trow, const uint32_t cand[4], uint4 tg,
                                                unsigned long long& n_cas, uint32_t* err) {
-    uint32_t tw[4] = {tg.x, tg.y, tg.z, tg.w};
+    uint32_t cur[4] = {tg.x, tg.y, tg.z, tg.w};
+    uint32_t nw[4], prev[4];
+    bool pend[4];
     uint32_t bits = 0u;
+    unsigned int* addr = reinterpret_cast<unsigned int*>(trow);
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-        if (cand[w] == 0u) continue;
-        unsigned int* addr = reinterpret_cast<unsigned int*>(trow + 4 * w);
-        uint32_t cur = tw[w];
-        uint32_t nw = byte_max(cur, cand[w]);
+        nw[w] = byte_max(cur[w], cand[w]);
+        pend[w] = cand[w] != 0u && nw[w] != cur[w];
+    }
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+        if (pend[w]) prev[w] = atomicCAS(addr + w, cur[w], nw[w]);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        if (!pend[w]) continue;
+        if (prev[w] == cur[w]) {
+            bits |= bytes_to_bits(nw[w] ^ cur[w]) << (4 * w);
+            ++n_cas;
+            continue;
+        }
+        uint32_t c = prev[w];
+        uint32_t n = byte_max(c, cand[w]);
         int tries = 0;
-        while (nw != cur) {
-            const uint32_t prev = atomicCAS(addr, cur, nw);
-            if (prev == cur) {
-                bits |= bytes_to_bits(nw ^ cur) << (4 * w);
+        while (n != c) {
+            const uint32_t pv = atomicCAS(addr + w, c, n);
+            if (pv == c) {
+                bits |= bytes_to_bits(n ^ c) << (4 * w);
                 ++n_cas;
                 break;
             }
-            cur = prev;
-            nw = byte_max(cur, cand[w]);
+            c = pv;
+            n = byte_max(c, cand[w]);
             if (++tries > kCasRetryLimit) {
                 atomicOr(err, kErrCasLimit);
                 break;
@@ -142,20 +159,23 @@ __device__ __forceinline__ uint32_t merge_chunk(uint8_t* trow, const uint32_t ca
 // Light units: a slice of 32-edge batches of the flat edge space.
 // ---------------------------------------------------------------------------
 template <int KIND, int MODE>
-__device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& a, const uint32_t* sX,
+__device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& a, const QEntry* __restrict__ qlin,
+                                            const uint32_t* sX,
                                             const uint16_t* sTab, int64_t b0, int64_t b1, int32_t nl,
                                             int64_t El, unsigned long long& st_chunks,
-                                            unsigned long long& st_cas, unsigned long long& st_new) {
+                                            unsigned long long& st_cas, unsigned long long& st_new,
+                                            unsigned long long& st_batches, unsigned long long& st_dealt) {
     const int lane = (int)lane_id();
     const int J = a.J, words = a.words;
     const int64_t fend = min(El, b1 << 5);
     int64_t f0 = b0 << 5;
-    int32_t qi = covering_entry(a.ql_in, nl, f0);
+    int32_t qi = covering_entry(qlin, nl, f0);
+    // queue window of the first batch; later windows are prefetched one batch ahead
+    int4 raw = make_int4(0, 0, 0x7FFFFFFF, 0);
+    if (qi + lane < nl) raw = __ldcg(reinterpret_cast<const int4*>(qlin) + qi + lane);
     for (; f0 < fend; f0 += 32) {
         const int32_t wi = qi + lane;
         const bool wvalid = wi < nl;
-        int4 raw = make_int4(0, 0, 0x7FFFFFFF, 0);
-        if (wvalid) raw = __ldcg(reinterpret_cast<const int4*>(a.ql_in) + wi);
         const int64_t rel = (int64_t)raw.z - f0;
         const int c0 = __popc(__ballot_sync(0xFFFFFFFFu, wvalid && rel <= 0));
         const unsigned starts =
@@ -165,6 +185,14 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
         const int32_t qrp = __shfl_sync(0xFFFFFFFFu, raw.y, myw);
         const int32_t qoff = __shfl_sync(0xFFFFFFFFu, raw.z, myw);
         const uint32_t qaux = (uint32_t)__shfl_sync(0xFFFFFFFFu, raw.w, myw);
+        // the window of the next batch: the entry covering f0 + 32
+        const int n32 = __popc(__ballot_sync(0xFFFFFFFFu, wvalid && rel <= 32));
+        int32_t qn = qi + n32 - 1;
+        if (n32 == 32 && qi + 32 < nl) {
+            if ((int64_t)__ldcg(&qlin[qi + 32].off) <= f0 + 32) qn = qi + 32;
+        }
+        int4 rawn = make_int4(0, 0, 0x7FFFFFFF, 0);
+        if (f0 + 32 < fend && qn + lane < nl) rawn = __ldcg(reinterpret_cast<const int4*>(qlin) + qn + lane);
         const int64_t f = f0 + lane;
         int32_t o = 0;
         uint32_t h = 0, thr = 0;
@@ -177,7 +205,7 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                 thr = edge_threshold<KIND, true>(g, (uint32_t)o, (uint32_t)qv, e, qaux);
             } else {
                 o = __ldg(g.col_out + e);
-                h = edge_hash((uint32_t)qv, (uint32_t)o);
+                h = __ldg(g.h_out + e);
                 thr = edge_threshold<KIND, false>(g, (uint32_t)qv, (uint32_t)o, e, 0u);
             }
             int lo, hi;
@@ -185,6 +213,13 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
             if (hi > lo) {
                 clo = lo >> 4;
                 nch = ((hi + 15) >> 4) - clo;
+                if (!a.all_changed) {
+                    // no chunk item unless a candidate simulation of qv changed
+                    uint32_t any = 0u;
+                    const uint32_t* cw = a.chg_cur + (size_t)qv * words;
+                    for (int w = lo >> 5; w <= (hi - 1) >> 5 && !any; ++w) any |= __ldcg(cw + w);
+                    if (!any) nch = 0;
+                }
             }
         }
         int incl = nch;
@@ -195,6 +230,7 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
         }
         const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
         const int excl = incl - nch;
+        if (lane == 0) { ++st_batches; st_dealt += (unsigned)total; }
         for (int base = 0; base < total; base += 32) {
             const int k = base + lane;
             int i = 0;
@@ -261,35 +297,41 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
             uint32_t aux = 0u;
             bool heavy = false;
             if (nbits) {
+                // the enqueue stamp and the row words are fetched together
+                const int32_t* rpp = MODE == kPush ? g.rp_in : g.rp_out;
+                rp = __ldg(rpp + o_i);
+                deg = __ldg(rpp + o_i + 1);
+                if constexpr (MODE == kPush && KIND == kWC) aux = __ldg(g.thr_v + o_i);
                 want = atomicExch(a.gen + o_i, a.gen_next) != a.gen_next;
-                if (want) {
-                    if constexpr (MODE == kPush) {
-                        rp = __ldg(g.rp_in + o_i);
-                        deg = __ldg(g.rp_in + o_i + 1) - rp;
-                        if constexpr (KIND == kWC) aux = __ldg(g.thr_v + o_i);
-                        heavy = is_heavy<KIND>(deg, KIND == kWC ? aux : g.thr_uniform, a.heavy_indeg);
-                    } else {
-                        rp = __ldg(g.rp_out + o_i);
-                        deg = __ldg(g.rp_out + o_i + 1) - rp;
-                    }
-                    want = deg > 0;
-                }
+                deg -= rp;
+                if constexpr (MODE == kPush)
+                    heavy = is_heavy<KIND>(deg, KIND == kWC ? aux : g.thr_uniform, a.heavy_indeg);
+                want = want && deg > 0;
             }
             append(want && !heavy, o_i, rp, deg, aux, a.ql_out, a.cl_out, g.n, a.err);
             if constexpr (MODE == kPush) append(want && heavy, o_i, rp, deg, aux, a.qh_out, a.ch_out, g.n, a.err);
         }
-        const int n32 = __popc(__ballot_sync(0xFFFFFFFFu, wvalid && rel <= 32));
-        int32_t qn = qi + n32 - 1;
-        if (n32 == 32 && qi + 32 < nl) {
-            if ((int64_t)__ldcg(&a.ql_in[qi + 32].off) <= f0 + 32) qn = qi + 32;
-        }
         qi = qn;
+        raw = rawn;
     }
 }
 
-// First index in [lo, hi) with h_in[index] >= key.
+// First index in [lo, hi) with h[index] >= key.  h is sorted ascending and
+// holds edge hashes, spread uniformly over [0, 2^31): a few interpolation
+// probes (each keeping every value of [lo, hi) inside [vlo, vhi]) shrink the
+// range to a handful of entries, then bisection finishes (and bounds the
+// worst case).
 __device__ __forceinline__ int32_t lower_bound_h(const uint32_t* __restrict__ h, int32_t lo, int32_t hi,
                                                  uint32_t key) {
+    uint32_t vlo = 0u, vhi = 0x7FFFFFFFu;
+    for (int it = 0; it < 4 && hi - lo > 8; ++it) {
+        const uint64_t span = (uint64_t)(vhi - vlo) + 1u;
+        int64_t g = lo + (int64_t)(((uint64_t)(key - vlo) * (uint64_t)(hi - lo)) / span);
+        if (g >= hi) g = hi - 1;
+        const uint32_t x = __ldg(h + g);
+        if (x < key) { lo = (int32_t)g + 1; vlo = x; }
+        else { hi = (int32_t)g; vhi = x; }
+    }
     while (lo < hi) {
         const int32_t mid = (lo + hi) >> 1;
         if (__ldg(h + mid) < key) lo = mid + 1; else hi = mid;
@@ -411,7 +453,7 @@ __device__ __forceinline__ void heavy_vertex(const GraphDev& g, const LevelArgs&
 }
 
 struct LevelStats {
-    unsigned long long chunks = 0, cas = 0, fresh = 0, hsims = 0;
+    unsigned long long chunks = 0, cas = 0, fresh = 0, hsims = 0, batches = 0, dealt = 0;
 };
 
 // Clears the change bits read by the level before the previous one.
@@ -434,11 +476,25 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
     const int lane = (int)lane_id();
     const unsigned long long cl = __ldcg(a.cl_in);
     const unsigned long long ch = a.ch_in ? __ldcg(a.ch_in) : 0ull;
-    const int32_t nl = (int32_t)(cl >> kCountShift);
-    const int64_t El = (int64_t)(cl & kEdgeMask);
-    const int32_t nh = (int32_t)(ch >> kCountShift);
+    int32_t nl = (int32_t)(cl >> kCountShift);
+    int64_t El = (int64_t)(cl & kEdgeMask);
+    int32_t nh = (int32_t)(ch >> kCountShift);
+    const QEntry* ql = a.ql_in;
+    // dense level: walk every vertex with in-edges in vertex order (contiguous
+    // in-CSR reads); vertices without changed simulations produce no chunks
+    if (MODE == kPush && a.q_dense && a.dense_div > 0 && (nl + nh) > 0 &&
+        ((int64_t)(nl + nh) * a.dense_div > (int64_t)a.n_dense || a.all_changed)) {
+        ql = a.q_dense;
+        nl = a.n_dense;
+        El = a.e_dense;
+        nh = 0;
+    }
     const int64_t nbl = (El + 31) >> 5;
-    const int64_t lunits = (nbl + a.light_batches - 1) / a.light_batches;
+    // batches per claim: the tuned value, fewer when the level has fewer
+    // batches than warps (shorter chains on small levels)
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t lb = max((int64_t)1, min((int64_t)a.light_batches, nbl / nwarps));
+    const int64_t lunits = (nbl + lb - 1) / lb;
     const int64_t total = (int64_t)nh + lunits;
     if (total == 0) return;
     if (warp == 0 && lane == 0) {
@@ -462,9 +518,10 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
             }
         } else {
             const int64_t lu = (int64_t)unit - nh;
-            const int64_t b0 = lu * a.light_batches;
-            const int64_t b1 = min(nbl, b0 + a.light_batches);
-            light_slice<KIND, MODE>(g, a, sX, sTab, b0, b1, nl, El, ls.chunks, ls.cas, ls.fresh);
+            const int64_t b0 = lu * lb;
+            const int64_t b1 = min(nbl, b0 + lb);
+            light_slice<KIND, MODE>(g, a, ql, sX, sTab, b0, b1, nl, El, ls.chunks, ls.cas, ls.fresh,
+                                    ls.batches, ls.dealt);
         }
     }
 }
@@ -475,8 +532,12 @@ __device__ __forceinline__ void flush_stats(const LevelArgs& a, LevelStats& ls) 
     ls.cas = wsum(ls.cas);
     ls.fresh = wsum(ls.fresh);
     ls.hsims = wsum(ls.hsims);
+    ls.batches = wsum(ls.batches);
+    ls.dealt = wsum(ls.dealt);
     if (lane_id() == 0) {
         if constexpr (MODE == kPush) {
+            if (ls.batches) atomicAdd(a.stats + kStSweepBatches, ls.batches);
+            if (ls.dealt) atomicAdd(a.stats + kStSweepDealt, ls.dealt);
             if (ls.chunks) atomicAdd(a.stats + kStSweepChunks, ls.chunks);
             if (ls.cas) atomicAdd(a.stats + kStSweepCas, ls.cas);
             if (ls.hsims) atomicAdd(a.stats + kStSweepHeavySims, ls.hsims);

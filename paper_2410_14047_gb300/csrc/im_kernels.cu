@@ -442,6 +442,35 @@ cudaError_t launch_exclusive_scan(const int32_t* cnt, int32_t n, int32_t* out, v
     return cudaGetLastError();
 }
 
+// Static queue of every vertex with in-edges, in vertex order (dense levels):
+// entry k is the k-th such vertex, its flat-space offset is its in-row start.
+__global__ void k_flag_in(const int32_t* __restrict__ rp_in, int32_t n, int32_t* flag) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) flag[v] = rp_in[v + 1] > rp_in[v] ? 1 : 0;
+}
+
+__global__ void k_dense_queue(const int32_t* __restrict__ rp_in, int32_t n, const uint32_t* __restrict__ thr_v,
+                              const int32_t* __restrict__ pos, QEntry* __restrict__ q) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int32_t b = rp_in[v], e = rp_in[v + 1];
+    if (e > b) {
+        QEntry x;
+        x.v = (int32_t)v; x.rp = b; x.off = b; x.aux = thr_v[v];
+        q[pos[v]] = x;
+    }
+}
+
+cudaError_t launch_dense_queue(const int32_t* rp_in, int32_t n, const uint32_t* thr_v, int32_t* flag,
+                               int32_t* pos, void* scan_tmp, QEntry* q, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_flag_in<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(rp_in, n, flag);
+    cudaError_t e = launch_exclusive_scan(flag, n, pos, scan_tmp, st);
+    if (e != cudaSuccess) return e;
+    k_dense_queue<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(rp_in, n, thr_v, pos, q);
+    return cudaGetLastError();
+}
+
 // Weighted cascade (Sec. 2.1): w = 1/indeg(v) rounded to fp32 (IEEE division),
 // threshold floor(w * 2^31) computed exactly in fp64.
 __device__ __forceinline__ uint32_t prob_threshold_dev(float w) {
@@ -784,6 +813,31 @@ __global__ void k_in_keys(const int32_t* __restrict__ rp_out, const int32_t* __r
             src_out[i] = (int32_t)u;
         }
     }
+}
+
+// Out-edge hash and weighted-cascade threshold of every out-edge (out-CSR order).
+__global__ void k_out_edge_words(const int32_t* __restrict__ rp_out, const int32_t* __restrict__ col_out,
+                                 int32_t n, const uint32_t* __restrict__ thr_v, uint32_t* __restrict__ h_out,
+                                 uint32_t* __restrict__ thrw_out) {
+    const int lane = (int)lane_id();
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = warp; u < n; u += nwarps) {
+        const int32_t b = rp_out[u], e = rp_out[u + 1];
+        for (int32_t i = b + lane; i < e; i += 32) {
+            const uint32_t v = (uint32_t)col_out[i];
+            h_out[i] = edge_hash((uint32_t)u, v);
+            thrw_out[i] = thr_v[v];
+        }
+    }
+}
+
+cudaError_t launch_out_edge_words(const int32_t* rp_out, const int32_t* col_out, int32_t n, int64_t m,
+                                  const uint32_t* thr_v, uint32_t* h_out, uint32_t* thrw_out,
+                                  cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    k_out_edge_words<<<152 * 8, kBlock, 0, st>>>(rp_out, col_out, n, thr_v, h_out, thrw_out);
+    return cudaGetLastError();
 }
 
 __global__ void k_in_gather(const unsigned long long* __restrict__ keys, const int32_t* __restrict__ perm,

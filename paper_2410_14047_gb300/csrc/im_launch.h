@@ -24,6 +24,8 @@ enum StatIndex : int {
     kStCoverLevels,
     kStSweepHeavy,
     kStSweepHeavySims,
+    kStSweepBatches,
+    kStSweepDealt,
     kStCount
 };
 
@@ -54,6 +56,10 @@ struct LevelArgs {
     uint32_t* chg_next;
     uint32_t* chg_prev;                  // cleared for the previous level's queues (may be NULL)
     int all_changed;                     // level 0 of a build: every simulation counts as changed
+    const QEntry* q_dense;               // every vertex with in-edges, vertex order (propagation)
+    int32_t n_dense;
+    int64_t e_dense;
+    int32_t dense_div;                   // dense level when frontier > n_dense / dense_div (0: never)
     int32_t heavy_indeg;
     int light_batches;                   // 32-edge batches per claimed unit
     unsigned int* claim;                 // dynamic work counter of this level
@@ -139,9 +145,15 @@ cudaError_t launch_build_in_csr(const int32_t* rp_out, const int32_t* col_out, i
                                 int kind, uint32_t tri_seed, const uint32_t* thr_out,
                                 const int32_t* rp_in, int32_t* src_in, uint32_t* h_in,
                                 uint32_t* thr_in, int2* cls_split, void* tmp, cudaStream_t st);
+cudaError_t launch_out_edge_words(const int32_t* rp_out, const int32_t* col_out, int32_t n, int64_t m,
+                                  const uint32_t* thr_v, uint32_t* h_out, uint32_t* thrw_out,
+                                  cudaStream_t st);
 cudaError_t launch_radix_sort(unsigned long long* keys, int32_t* vals, int64_t n, int bits,
                               void* tmp, cudaStream_t st);
 size_t sort_tmp_bytes(int64_t n);
+// Static queue of the vertices with in-edges in vertex order; pos[n] = count.
+cudaError_t launch_dense_queue(const int32_t* rp_in, int32_t n, const uint32_t* thr_v, int32_t* flag,
+                               int32_t* pos, void* scan_tmp, QEntry* q, cudaStream_t st);
 cudaError_t launch_thr_wc(const int32_t* rp_in, int32_t n, uint32_t* thr_v, cudaStream_t st);
 cudaError_t launch_thr_explicit(const float* w, int64_t m, uint32_t* thr, cudaStream_t st);
 
