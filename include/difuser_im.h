@@ -232,6 +232,30 @@ IM_API im_status im_select_seeds(im_graph* g, int32_t K, int32_t J, const im_mod
                           uint64_t seed, double rebuild_eps, int32_t* seeds_out,
                           double* score_out, double* estimate_out, im_sketch** sketch_out);
 
+/* Estimate + argmax without allocating (the paper has no counterpart: this is
+ * a library entry point for callers that cannot allocate device memory, such
+ * as code running inside a memory arena it does not own or a process whose
+ * device memory is fully reserved up front, where a cudaMalloc would fail or
+ * stall the device).  Same result as im_sketch_pick on the same registers:
+ * the vertex s not marked in `picked` with the smallest S_s (largest
+ * estimate), lowest id on ties; its bit in `picked` is set.
+ *   M       device, n*J register bytes (row-major, as im_sketch_registers)
+ *   picked  device, ceil(n/32) uint32 words: bit v set = v excluded; in/out
+ *   s_out   device int32: the pick, -1 if every vertex is excluded
+ *   S_out   device uint64: S_s;  est_out: device double, J*2^32/(phi*S_s)
+ * Work runs on `cuda_stream` (NULL = legacy default stream); results are
+ * ready when the stream reaches them.  Scratch lives in one static device
+ * array (at most 1216 blocks of partials, about 15 KB, held by every GPU that
+ * loads the library until exit) shared by all calls: calls that overlap on
+ * the GPU race and must be serialised by the caller.  The first call on each
+ * device looks up the array's address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  Calls no cudaMalloc/cudaFree.
+ * Errors: IM_E_INVAL (NULL pointer, unsupported J), IM_E_RANGE (n outside
+ * [1, 2^26)), IM_E_CUDA. */
+IM_API im_status im_argmax_noalloc(const uint8_t* M, int32_t n, int32_t J, uint32_t* picked,
+                                   void* cuda_stream, int32_t* s_out, uint64_t* S_out,
+                                   double* est_out);
+
 /* Independent-cascade Monte-Carlo spread of a seed set (the independent
  * quality oracle of Sec. 5.1, run on the GPU): R simulations; in simulation r
  * out-edge e (out-CSR index) fires iff (SplitMix64 output number r*m + e of

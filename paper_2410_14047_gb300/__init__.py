@@ -29,7 +29,8 @@ EXPORTS = ["im_ctx_create", "im_ctx_destroy", "im_ctx_bytes_in_use", "im_ctx_byt
            "im_graph_load", "im_graph_free",
            "im_graph_info", "im_sketch_build", "im_sketch_free", "im_sketch_registers",
            "im_sketch_set_registers", "im_sketch_sims", "im_sketch_sums", "im_sketch_pick",
-           "im_sketch_cover", "im_sketch_rebuild", "im_select_seeds", "im_spread_mc"]
+           "im_sketch_cover", "im_sketch_rebuild", "im_select_seeds", "im_spread_mc",
+           "im_argmax_noalloc"]
 
 
 class IMError(RuntimeError):
@@ -116,6 +117,7 @@ def load_library(path: str = LIB_PATH):
         "im_select_seeds": (ctypes.c_int, [vp, i32, i32, P(im_model), u64, f64, P(i32), P(f64),
                                            P(f64), P(vp)]),
         "im_spread_mc": (ctypes.c_int, [vp, P(i32), i32, i64, u64, P(f64), P(f64), P(u64), P(u64)]),
+        "im_argmax_noalloc": (ctypes.c_int, [vp, i32, i32, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

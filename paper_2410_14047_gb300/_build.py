@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "_libdifuser_im.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["im_kernels.cu", "im_frontier.cu", "im_api.cu"]
+SOURCES = ["im_kernels.cu", "im_frontier.cu", "im_api.cu", "im_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, h) for h in ("im_device.cuh", "im_launch.h")] + [
     os.path.join(ROOT, "include", "difuser_im.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kBlock) k_pick(PickArgs a) {
         *a.ticket = 0u;
         if (gS == ~0ull) {
             a.out_seed[a.k] = -1;
-            *a.ctr_cover = 0ull;
+            if (a.ctr_cover) *a.ctr_cover = 0ull;
         } else {
             a.out_seed[a.k] = gU;
             a.out_S[a.k] = gS;
