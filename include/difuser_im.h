@@ -60,14 +60,17 @@ typedef enum {
     IM_IC_WC = 1,         /* weighted cascade, w(u,v) = 1 / indeg(v) in fp32 (Sec. 2.1, Fig. 1b) */
     IM_IC_TRIVALENCY = 2, /* w(u,v) = {0.1, 0.01, 0.001}[MurmurHash3_x86_32(LE32(u)||LE32(v),
                              (uint32)(seed ^ seed >> 32)) mod 3] */
-    IM_IC_EXPLICIT = 3    /* per-edge probabilities w[e] in out-CSR order (Sec. 5 N/U settings) */
+    IM_IC_EXPLICIT = 3,   /* per-edge probabilities w[e] in out-CSR order (Sec. 5 N/U settings) */
+    IM_IC_TARGET = 4      /* per-target-vertex probabilities w[v], n floats: every edge into v
+                             fires with w[v] (weighted cascade is the case w[v] = 1/indeg(v)) */
 } im_model_kind;
 
 typedef struct {
     int32_t kind;     /* im_model_kind */
     float p;          /* IM_IC_UNIFORM: edge probability in [0, 1] */
     uint64_t seed;    /* IM_IC_TRIVALENCY: class-hash seed */
-    const float* w;   /* IM_IC_EXPLICIT: m host floats in [0, 1], out-CSR order; copied */
+    const float* w;   /* IM_IC_EXPLICIT: m host floats in [0, 1], out-CSR order;
+                         IM_IC_TARGET: n host floats in [0, 1]; copied */
 } im_model;
 
 /* Device memory provider.  alloc returns a device pointer of at least `bytes`
@@ -231,6 +234,31 @@ IM_API im_status im_sketch_rebuild(im_sketch* sk);
 IM_API im_status im_select_seeds(im_graph* g, int32_t K, int32_t J, const im_model* model,
                           uint64_t seed, double rebuild_eps, int32_t* seeds_out,
                           double* score_out, double* estimate_out, im_sketch** sketch_out);
+
+/* ---- batches: many graphs in one device union ---------------------------- */
+
+typedef struct im_batch im_batch;
+
+/* Loads G graphs (host CSRs, same rules as im_graph_load) as one device batch:
+ * a disjoint union with vertex ids offset per graph, graph g under uniform IC
+ * with probability p[g].  Errors: IM_E_INVAL, IM_E_RANGE (total vertices must
+ * be < 2^26, total edges < 2^31), IM_E_NOMEM, IM_E_CUDA. */
+IM_API im_status im_batch_load(im_ctx* ctx, int32_t G, const int32_t* n, const int64_t* m,
+                               const int32_t* const* rowptr, const int32_t* const* col,
+                               const float* p, im_batch** out);
+IM_API void im_batch_free(im_batch* b);
+/* Alg. 4 on every graph of the batch at once: graph g gets K[g] seeds with
+ * J[g] simulations drawn from `seed` (all graphs share the draws of their J,
+ * so each graph's result equals im_select_seeds on that graph alone with the
+ * same seed, J, K and rebuild_eps).  Rounds pick one seed in every graph that
+ * still needs one; covers of all graphs run as one frontier; rebuilds cover
+ * the graphs whose rule fired.  Outputs concatenated in graph order (local
+ * vertex ids): seeds_out[sum K], score_out[sum K] (may be NULL),
+ * estimate_out[sum K] (may be NULL).  Errors: IM_E_RANGE (K[g] outside
+ * [1, n_g]), IM_E_INVAL, IM_E_NOMEM, IM_E_CUDA, IM_E_TIMEOUT. */
+IM_API im_status im_batch_select_seeds(im_batch* b, const int32_t* J, const int32_t* K, uint64_t seed,
+                                       double rebuild_eps, int32_t* seeds_out, double* score_out,
+                                       double* estimate_out);
 
 /* Estimate + argmax without allocating (the paper has no counterpart: this is
  * a library entry point for callers that cannot allocate device memory, such

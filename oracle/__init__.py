@@ -25,7 +25,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_liboracle.so")
 _lib = None
 
-MODEL_KINDS = {"uniform": 0, "wc": 1, "trivalency": 2, "explicit": 3}
+MODEL_KINDS = {"uniform": 0, "wc": 1, "trivalency": 2, "explicit": 3, "target": 4}
 PHI = 0.77351
 VISITED = 0xFF
 

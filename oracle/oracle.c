@@ -140,7 +140,8 @@ uint32_t orc_prob_threshold(float w) {
  * kind 0: uniform IC with probability p;
  * kind 1: weighted cascade, w(u,v) = 1/indeg(v) (fp32 division);
  * kind 2: trivalency, w(u,v) = {0.1, 0.01, 0.001}[Murmur3(u||v, seed32) mod 3];
- * kind 3: explicit per-edge probabilities w[e].
+ * kind 3: explicit per-edge probabilities w[e];
+ * kind 4: per-target probabilities, w[v] for every edge into v.
  * Returns 0, or -1 on a bad kind. */
 int orc_thresholds(int32_t n, int64_t m, const int32_t* rowptr, const int32_t* col, int32_t kind,
                    float p, uint64_t model_seed, const float* w, uint32_t* thr) {
@@ -170,6 +171,10 @@ int orc_thresholds(int32_t n, int64_t m, const int32_t* rowptr, const int32_t* c
     }
     if (kind == 3) {
         for (int64_t e = 0; e < m; e++) thr[e] = orc_prob_threshold(w[e]);
+        return 0;
+    }
+    if (kind == 4) {
+        for (int64_t e = 0; e < m; e++) thr[e] = orc_prob_threshold(w[col[e]]);
         return 0;
     }
     return -1;

@@ -18,7 +18,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_libdifuser_im.so")
 
-MODEL_KINDS = {"uniform": 0, "wc": 1, "trivalency": 2, "explicit": 3}
+MODEL_KINDS = {"uniform": 0, "wc": 1, "trivalency": 2, "explicit": 3, "target": 4}
 STATUS = {0: "IM_OK", -1: "IM_E_INVAL", -2: "IM_E_RANGE", -3: "IM_E_NOMEM", -4: "IM_E_CUDA",
           -5: "IM_E_TIMEOUT", -6: "IM_E_STATE"}
 
@@ -30,7 +30,7 @@ EXPORTS = ["im_ctx_create", "im_ctx_destroy", "im_ctx_bytes_in_use", "im_ctx_byt
            "im_graph_info", "im_sketch_build", "im_sketch_free", "im_sketch_registers",
            "im_sketch_set_registers", "im_sketch_sims", "im_sketch_sums", "im_sketch_pick",
            "im_sketch_cover", "im_sketch_rebuild", "im_select_seeds", "im_spread_mc",
-           "im_argmax_noalloc"]
+           "im_argmax_noalloc", "im_batch_load", "im_batch_free", "im_batch_select_seeds"]
 
 
 class IMError(RuntimeError):
@@ -118,6 +118,10 @@ def load_library(path: str = LIB_PATH):
                                            P(f64), P(vp)]),
         "im_spread_mc": (ctypes.c_int, [vp, P(i32), i32, i64, u64, P(f64), P(f64), P(u64), P(u64)]),
         "im_argmax_noalloc": (ctypes.c_int, [vp, i32, i32, vp, vp, vp, vp, vp]),
+        "im_batch_load": (ctypes.c_int, [vp, i32, P(i32), P(i64), P(P(i32)), P(P(i32)), P(ctypes.c_float),
+                                         P(vp)]),
+        "im_batch_free": (None, [vp]),
+        "im_batch_select_seeds": (ctypes.c_int, [vp, P(i32), P(i32), u64, f64, P(i32), P(f64), P(f64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -142,7 +146,7 @@ def _model(model: dict | None, keep: list):
     m.kind = MODEL_KINDS[model["kind"]]
     m.p = float(model.get("p", 0.0))
     m.seed = _u64(model.get("seed", 0))
-    if model["kind"] == "explicit":
+    if model["kind"] in ("explicit", "target"):
         w = np.ascontiguousarray(model["w"], dtype=np.float32)
         keep.append(w)
         m.w = _p(w, ctypes.c_float)
@@ -336,6 +340,57 @@ def im_spread_mc(graph: Graph, seeds, R: int, seed: int = 1):
                                                _u64(seed), ctypes.byref(mean), ctypes.byref(se),
                                                ctypes.byref(a), ctypes.byref(b)))
     return {"mean": mean.value, "stderr": se.value, "sum": int(a.value), "sumsq": int(b.value)}
+
+
+class Batch:
+    def __init__(self, ctx: Context, handle, ns):
+        self.ctx, self.handle, self.ns = ctx, handle, list(ns)
+
+    def free(self):
+        if self.handle:
+            self.ctx.lib.im_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def im_batch_load(ctx: Context, graphs, p) -> Batch:
+    """graphs: objects with rowptr / col arrays (int32); p: uniform IC probability per graph."""
+    G = len(graphs)
+    rps = [np.ascontiguousarray(g.rowptr, dtype=np.int32) for g in graphs]
+    cols = [np.ascontiguousarray(g.col if len(g.col) else np.zeros(1), dtype=np.int32) for g in graphs]
+    n = np.array([r.shape[0] - 1 for r in rps], dtype=np.int32)
+    m = np.array([len(g.col) for g in graphs], dtype=np.int64)
+    P32 = ctypes.POINTER(ctypes.c_int32)
+    rp_arr = (P32 * G)(*[_p(r, ctypes.c_int32) for r in rps])
+    col_arr = (P32 * G)(*[_p(c, ctypes.c_int32) for c in cols])
+    pf = np.ascontiguousarray(p, dtype=np.float32)
+    h = ctypes.c_void_p()
+    ctx.check(ctx.lib.im_batch_load(ctx.handle, G, _p(n, ctypes.c_int32), _p(m, ctypes.c_int64),
+                                    rp_arr, col_arr, _p(pf, ctypes.c_float), ctypes.byref(h)))
+    return Batch(ctx, h, n.tolist())
+
+
+def im_batch_select_seeds(batch: Batch, J, K, seed: int = 2410, rebuild_eps: float = 0.01) -> list:
+    """Alg. 4 on every graph of the batch; returns one dict(seeds, score, est) per graph."""
+    J = np.ascontiguousarray(J, dtype=np.int32)
+    K = np.ascontiguousarray(K, dtype=np.int32)
+    tot = int(K.sum())
+    seeds = np.empty(tot, dtype=np.int32)
+    score = np.empty(tot, dtype=np.float64)
+    est = np.empty(tot, dtype=np.float64)
+    batch.ctx.check(batch.ctx.lib.im_batch_select_seeds(
+        batch.handle, _p(J, ctypes.c_int32), _p(K, ctypes.c_int32), _u64(seed), float(rebuild_eps),
+        _p(seeds, ctypes.c_int32), _p(score, ctypes.c_double), _p(est, ctypes.c_double)))
+    out, o = [], 0
+    for k in K.tolist():
+        out.append({"seeds": seeds[o:o + k].copy(), "score": score[o:o + k].copy(), "est": est[o:o + k].copy()})
+        o += k
+    return out
 
 
 def im_last_stats(ctx: Context) -> dict:

@@ -206,8 +206,10 @@ struct im_graph {
     im_ctx* ctx = nullptr;
     int32_t n = 0;
     int64_t m = 0;
-    int kind = kUniform;
-    DBuf rp_out, col_out, rp_in, src_in, h_in, h_out, thrw_out, thr_v, thr_out, thr_in, cls_split, q_dense;
+    int kind = kUniform;       // kernel family (a per-target model runs as kWC)
+    int load_kind = kUniform;  // model kind given at load
+    DBuf rp_out, col_out, rp_in, src_in, h_in, h_out, thrw_out, thr_v, thr_out, thr_in, cls_split, q_dense,
+        hkey;
     int32_t n_dense = 0;
     GraphDev dev{};
 };
@@ -221,6 +223,11 @@ struct im_sketch {
     int32_t out_cap = 0;
     int32_t gen_counter = 0;
     int32_t picks = 0;
+    // batches (several graphs in one union): graph of every vertex, visited
+    // counter per graph, graphs whose rows a build covers
+    const int32_t* gid = nullptr;
+    unsigned long long* gcount = nullptr;
+    const uint8_t* gflag = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -336,8 +343,10 @@ extern "C" im_status im_last_stats(const im_ctx* c, im_stats* out) {
 // ---------------------------------------------------------------------------
 static im_status check_model(im_ctx* c, const im_model* mdl, int64_t m) {
     if (!mdl) return fail(c, IM_E_INVAL, "model is NULL");
-    if (mdl->kind < kUniform || mdl->kind > kExplicit)
+    if (mdl->kind < kUniform || mdl->kind > kTargetModel)
         return fail(c, IM_E_INVAL, "unknown model kind %d", mdl->kind);
+    if (mdl->kind == kTargetModel && !mdl->w)
+        return fail(c, IM_E_INVAL, "per-target model needs w[n]");
     if (mdl->kind == kUniform && !(mdl->p >= 0.0f && mdl->p <= 1.0f))
         return fail(c, IM_E_INVAL, "uniform p must be in [0,1]");
     if (mdl->kind == kExplicit && m > 0 && !mdl->w)
@@ -348,7 +357,8 @@ static im_status check_model(im_ctx* c, const im_model* mdl, int64_t m) {
 static void graph_release(im_graph* g) {
     im_ctx* c = g->ctx;
     for (DBuf* b : {&g->rp_out, &g->col_out, &g->rp_in, &g->src_in, &g->h_in, &g->h_out,
-                    &g->thrw_out, &g->thr_v, &g->thr_out, &g->thr_in, &g->cls_split, &g->q_dense})
+                    &g->thrw_out, &g->thr_v, &g->thr_out, &g->thr_in, &g->cls_split, &g->q_dense,
+                    &g->hkey})
         dfree(c, *b);
 }
 
@@ -357,7 +367,9 @@ static void graph_release(im_graph* g) {
 // filled by the caller (they need the reverse CSR).
 static im_status set_model(im_graph* g, const im_model* mdl) {
     im_ctx* c = g->ctx;
-    g->kind = mdl->kind;
+    // a per-target-vertex model runs the weighted-cascade kernels (every
+    // in-edge of v has v's threshold); its thresholds are set at load
+    g->kind = mdl->kind == kTargetModel ? kWC : mdl->kind;
     g->dev.thr_uniform = prob_threshold_host(mdl->p);
     g->dev.tri_seed = (uint32_t)(mdl->seed ^ (mdl->seed >> 32));
     g->dev.tri_thr[0] = prob_threshold_host(0.1f);
@@ -381,8 +393,9 @@ static im_status set_model(im_graph* g, const im_model* mdl) {
     return IM_OK;
 }
 
-extern "C" im_status im_graph_load(im_ctx* c, int32_t n, int64_t m, const int32_t* rowptr,
-                                   const int32_t* col, const im_model* model, im_graph** out) {
+static im_status graph_load_impl(im_ctx* c, int32_t n, int64_t m, const int32_t* rowptr,
+                                 const int32_t* col, const im_model* model, const int32_t* hkey_host,
+                                 im_graph** out) {
     if (!c || !out || !rowptr || (m > 0 && !col)) return fail(c, IM_E_INVAL, "NULL argument");
     if (n < 1 || n >= (1 << 26)) return fail(c, IM_E_RANGE, "n must be in [1, 2^26)");
     if (m < 0 || m >= (1ll << 31)) return fail(c, IM_E_RANGE, "m must be in [0, 2^31)");
@@ -434,18 +447,33 @@ extern "C" im_status im_graph_load(im_ctx* c, int32_t n, int64_t m, const int32_
     if (e == cudaSuccess) e = launch_indegree(g->col_out.as<int32_t>(), m, cnt.as<int32_t>(), st);
     if (e == cudaSuccess) e = launch_exclusive_scan(cnt.as<int32_t>(), n, g->rp_in.as<int32_t>(), tmp.p, st);
     if (e == cudaSuccess) e = launch_thr_wc(g->rp_in.as<int32_t>(), n, g->thr_v.as<uint32_t>(), st);
+    if (e == cudaSuccess && model->kind == kTargetModel) {
+        // per-target probabilities replace the weighted-cascade thresholds
+        DBuf w;
+        if ((s = dalloc(c, (size_t)n * sizeof(float), w)) != IM_OK) { release_tmp(); return bail(s); }
+        e = cudaMemcpyAsync(w.p, model->w, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = launch_thr_explicit(w.as<float>(), n, g->thr_v.as<uint32_t>(), st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        dfree(c, w);
+    }
+    if (e == cudaSuccess && hkey_host) {
+        if ((s = dalloc(c, (size_t)n * 4, g->hkey)) != IM_OK) { release_tmp(); return bail(s); }
+        e = cudaMemcpyAsync(g->hkey.p, hkey_host, (size_t)n * 4, cudaMemcpyHostToDevice, st);
+    }
     if (e == cudaSuccess)
         e = launch_out_edge_words(g->rp_out.as<int32_t>(), g->col_out.as<int32_t>(), n, m,
-                                  g->thr_v.as<uint32_t>(), g->h_out.as<uint32_t>(),
+                                  g->thr_v.as<uint32_t>(), g->hkey.as<int32_t>(), g->h_out.as<uint32_t>(),
                                   g->thrw_out.as<uint32_t>(), st);
     if (e != cudaSuccess) { release_tmp(); return bail(cuda_fail(c, e, "graph load")); }
     if ((s = set_model(g, model)) != IM_OK) { release_tmp(); return bail(s); }
+    g->load_kind = model->kind;
     if (g->kind == kExplicit && m > 0) {
         if ((s = dalloc(c, (size_t)m * 4, g->thr_in)) != IM_OK) { release_tmp(); return bail(s); }
     }
     // in-CSR sorted by (target, class, edge hash): rows of equal-threshold in-edges in hash order
     e = launch_build_in_csr(g->rp_out.as<int32_t>(), g->col_out.as<int32_t>(), n, m, g->kind,
-                            g->dev.tri_seed, g->thr_out.as<uint32_t>(), g->rp_in.as<int32_t>(),
+                            g->dev.tri_seed, g->hkey.as<int32_t>(), g->thr_out.as<uint32_t>(),
+                            g->rp_in.as<int32_t>(),
                             g->src_in.as<int32_t>(), g->h_in.as<uint32_t>(), g->thr_in.as<uint32_t>(),
                             g->cls_split.as<int2>(), tmp.p, st);
     // static vertex-ordered queue for dense levels (cnt and tmp reused as scratch)
@@ -475,6 +503,11 @@ extern "C" im_status im_graph_load(im_ctx* c, int32_t n, int64_t m, const int32_
     g->dev.thr_in = g->thr_in.as<uint32_t>();
     *out = g;
     return IM_OK;
+}
+
+extern "C" im_status im_graph_load(im_ctx* c, int32_t n, int64_t m, const int32_t* rowptr,
+                                   const int32_t* col, const im_model* model, im_graph** out) {
+    return graph_load_impl(c, n, m, rowptr, col, model, nullptr, out);
 }
 
 extern "C" void im_graph_free(im_graph* g) {
@@ -592,7 +625,10 @@ static LevelArgs level_args(im_sketch* sk) {
     a.q_dense = sk->g->q_dense.as<QEntry>();
     a.n_dense = sk->g->n_dense;
     a.e_dense = sk->g->m;
-    a.dense_div = t.dense_div;
+    a.dense_div = sk->gflag ? 0 : t.dense_div;  // a batch build covers only some graphs
+    a.gid = sk->gid;
+    a.gcount = sk->gcount;
+    a.gflag = sk->gflag;
     return a;
 }
 
@@ -978,8 +1014,9 @@ extern "C" im_status im_select_seeds(im_graph* g, int32_t K, int32_t J, const im
     } guard{g, g->dev, g->kind};
     if (model) {
         CKS(check_model(c, model, g->m));
-        if (model->kind == kExplicit || g->kind == kExplicit)
-            return fail(c, IM_E_STATE, "an explicit-weight model must be given at im_graph_load");
+        if (model->kind == kExplicit || model->kind == kTargetModel || g->load_kind == kExplicit ||
+            g->load_kind == kTargetModel)
+            return fail(c, IM_E_STATE, "explicit and per-target models are fixed at im_graph_load");
         CKS(set_model(g, model));
     }
     stats_begin(c);
@@ -1137,5 +1174,247 @@ extern "C" im_status im_spread_mc(im_graph* g, const int32_t* seeds, int32_t k, 
     if (stderr_out) *stderr_out = std::sqrt((double)(var > 0 ? var : 0) / (double)R);
     if (sum_out) *sum_out = h[0];
     if (sumsq_out) *sumsq_out = h[1];
+    return IM_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Batches: many graphs as one disjoint union (vertex ids offset per graph),
+// uniform IC probability per graph as a per-target model.  A selection runs
+// Alg. 4 on every graph at once, one seed per graph per round; the graphs of
+// one J share the simulation draws of the seed.
+// ---------------------------------------------------------------------------
+struct im_batch {
+    im_ctx* ctx = nullptr;
+    im_graph* g = nullptr;
+    int32_t G = 0;
+    std::vector<int32_t> voff;  // G + 1 vertex offsets
+    DBuf gid;
+};
+
+extern "C" im_status im_batch_load(im_ctx* c, int32_t G, const int32_t* n, const int64_t* m,
+                                   const int32_t* const* rowptr, const int32_t* const* col,
+                                   const float* p, im_batch** out) {
+    if (!c || !out || !n || !m || !rowptr || !col || !p) return fail(c, IM_E_INVAL, "NULL argument");
+    if (G < 1) return fail(c, IM_E_RANGE, "G must be >= 1");
+    int64_t N = 0, Mt = 0;
+    for (int32_t g = 0; g < G; ++g) {
+        if (n[g] < 1 || m[g] < 0 || !rowptr[g] || (m[g] > 0 && !col[g]))
+            return fail(c, IM_E_INVAL, "graph %d: bad sizes or NULL arrays", g);
+        if (!(p[g] >= 0.0f && p[g] <= 1.0f)) return fail(c, IM_E_INVAL, "graph %d: p outside [0,1]", g);
+        if (rowptr[g][0] != 0 || rowptr[g][n[g]] != m[g]) return fail(c, IM_E_INVAL, "graph %d: bad rowptr", g);
+        N += n[g];
+        Mt += m[g];
+    }
+    if (N >= (1 << 26)) return fail(c, IM_E_RANGE, "total vertices must be < 2^26");
+    if (Mt >= (1ll << 31)) return fail(c, IM_E_RANGE, "total edges must be < 2^31");
+    std::vector<int32_t> rp((size_t)N + 1);
+    std::vector<int32_t> cl((size_t)(Mt > 0 ? Mt : 1));
+    std::vector<float> w((size_t)N);
+    im_batch* b = new im_batch();
+    b->ctx = c;
+    b->G = G;
+    b->voff.resize((size_t)G + 1);
+    std::vector<int32_t> gid_h((size_t)N), key_h((size_t)N);
+    int64_t vo = 0, eo = 0;
+    for (int32_t g = 0; g < G; ++g) {
+        b->voff[g] = (int32_t)vo;
+        for (int32_t u = 0; u < n[g]; ++u) {
+            rp[vo + u] = (int32_t)(eo + rowptr[g][u]);
+            w[vo + u] = p[g];
+            gid_h[vo + u] = g;
+            key_h[vo + u] = u;  // hashes use the vertex id inside its own graph
+        }
+        for (int64_t e = 0; e < m[g]; ++e) cl[eo + e] = col[g][e] + (int32_t)vo;
+        vo += n[g];
+        eo += m[g];
+    }
+    b->voff[G] = (int32_t)vo;
+    rp[N] = (int32_t)Mt;
+    im_model md{};
+    md.kind = kTargetModel;
+    md.w = w.data();
+    im_status s = graph_load_impl(c, (int32_t)N, Mt, rp.data(), cl.data(), &md, key_h.data(), &b->g);
+    if (s != IM_OK) {
+        delete b;
+        return s;
+    }
+    if ((s = dalloc(c, (size_t)N * 4, b->gid)) != IM_OK) {
+        im_graph_free(b->g);
+        delete b;
+        return s;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->gid.p, gid_h.data(), (size_t)N * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        dfree(c, b->gid);
+        im_graph_free(b->g);
+        delete b;
+        return cuda_fail(c, e, "batch load");
+    }
+    *out = b;
+    return IM_OK;
+}
+
+extern "C" void im_batch_free(im_batch* b) {
+    if (!b) return;
+    dfree(b->ctx, b->gid);
+    im_graph_free(b->g);
+    delete b;
+}
+
+// Fill of the flagged graphs' rows, then propagation from their vertices.
+static im_status batch_build(im_sketch* sk) {
+    im_ctx* c = sk->g->ctx;
+    CK(c, timed(c, kTFill, [&] {
+        return launch_fill_flagged(sk->M.as<uint8_t>(), sk->g->n, sk->J, sk->salt.as<uint32_t>(),
+                                   sk->gid, sk->gflag, sk->g->hkey.as<int32_t>(), c->stream);
+    }));
+    return propagate(sk);
+}
+
+extern "C" im_status im_batch_select_seeds(im_batch* b, const int32_t* J, const int32_t* K,
+                                           uint64_t seed, double rebuild_eps, int32_t* seeds_out,
+                                           double* score_out, double* estimate_out) {
+    if (!b || !J || !K || !seeds_out) return IM_E_INVAL;
+    im_ctx* c = b->ctx;
+    const int32_t G = b->G;
+    std::vector<int64_t> koff((size_t)G + 1, 0);
+    for (int32_t g = 0; g < G; ++g) {
+        const int32_t ng = b->voff[g + 1] - b->voff[g];
+        if (K[g] < 1 || K[g] > ng) return fail(c, IM_E_RANGE, "graph %d: K must be in [1, n]", g);
+        if (!valid_J(J[g])) return fail(c, IM_E_INVAL, "graph %d: unsupported J %d", g, J[g]);
+        koff[g + 1] = koff[g] + K[g];
+    }
+    stats_begin(c);
+    const double t0 = now_ms();
+    auto st = c->stream;
+    std::vector<int32_t> Js(J, J + G);
+    std::sort(Js.begin(), Js.end());
+    Js.erase(std::unique(Js.begin(), Js.end()), Js.end());
+    int64_t builds = 0;
+    for (int32_t Jg : Js) {
+        std::vector<int32_t> members;
+        int32_t maxK = 0;
+        for (int32_t g = 0; g < G; ++g)
+            if (J[g] == Jg) { members.push_back(g); maxK = std::max(maxK, K[g]); }
+        // tiles: row ranges of at most 4096 rows inside one member graph
+        std::vector<int4> tiles;
+        std::vector<int32_t> tb((size_t)G, 0), te((size_t)G, 0);
+        for (int32_t g : members) {
+            tb[g] = (int32_t)tiles.size();
+            for (int32_t r = b->voff[g]; r < b->voff[g + 1]; r += 4096)
+                tiles.push_back(make_int4(g, r, std::min(r + 4096, b->voff[g + 1]), 0));
+            te[g] = (int32_t)tiles.size();
+        }
+        im_sketch* sk = nullptr;
+        CKS(sketch_start(b->g, Jg, seed, &sk));
+        DBuf tiles_d, tb_d, te_d, active_d, flag_d, gcount_d, pS, pU, oseed, oS, oest;
+        std::vector<DBuf*> tmp = {&tiles_d, &tb_d, &te_d, &active_d, &flag_d, &gcount_d, &pS, &pU, &oseed, &oS, &oest};
+        auto cleanup = [&]() {
+            for (DBuf* x : tmp) dfree(c, *x);
+            sketch_release(sk);
+            delete sk;
+        };
+        im_status s = IM_OK;
+        auto A = [&](DBuf& x, size_t bytes) { if (s == IM_OK) s = dalloc(c, bytes, x); };
+        A(tiles_d, tiles.size() * sizeof(int4) + 16);
+        A(tb_d, (size_t)G * 4);
+        A(te_d, (size_t)G * 4);
+        A(active_d, (size_t)G);
+        A(flag_d, (size_t)G);
+        A(gcount_d, (size_t)G * 8);
+        A(pS, tiles.size() * 8 + 8);
+        A(pU, tiles.size() * 4 + 4);
+        A(oseed, (size_t)G * maxK * 4);
+        A(oS, (size_t)G * maxK * 8);
+        A(oest, (size_t)G * maxK * 8);
+        if (s != IM_OK) { cleanup(); return s; }
+        std::vector<uint8_t> active((size_t)G, 0), flag((size_t)G, 0);
+        for (int32_t g : members) flag[g] = 1;
+        cudaError_t e = cudaMemcpyAsync(tiles_d.p, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tb_d.p, tb.data(), (size_t)G * 4, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(te_d.p, te.data(), (size_t)G * 4, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(flag_d.p, flag.data(), (size_t)G, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(gcount_d.p, 0, (size_t)G * 8, st);
+        if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "batch setup"); }
+        sk->gid = b->gid.as<int32_t>();
+        sk->gcount = gcount_d.as<unsigned long long>();
+        sk->gflag = flag_d.as<uint8_t>();
+        if ((s = batch_build(sk)) != IM_OK) { cleanup(); return s; }
+        ++builds;
+        std::vector<unsigned long long> count((size_t)G, 0), oldcount((size_t)G, 0);
+        std::vector<std::vector<double>> score((size_t)G);
+        for (int32_t r = 0; r < maxK; ++r) {
+            for (int32_t g : members) active[g] = r < K[g] ? 1 : 0;
+            e = cudaMemcpyAsync(active_d.p, active.data(), (size_t)G, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "batch round"); }
+            if ((s = phase_begin(sk)) != IM_OK) { cleanup(); return s; }
+            BatchPickArgs pa{};
+            pa.M = sk->M.as<uint8_t>();
+            pa.J = Jg;
+            pa.tiles = tiles_d.as<int4>();
+            pa.ntiles = (int)tiles.size();
+            pa.active = active_d.as<uint8_t>();
+            pa.picked = sk->seed_bits.as<uint32_t>();
+            pa.part_S = pS.as<unsigned long long>();
+            pa.part_u = pU.as<int32_t>();
+            pa.tile_begin = tb_d.as<int32_t>();
+            pa.tile_end = te_d.as<int32_t>();
+            pa.G = G;
+            pa.round = r;
+            pa.maxK = maxK;
+            pa.out_seed = oseed.as<int32_t>();
+            pa.out_S = oS.as<unsigned long long>();
+            pa.out_est = oest.as<double>();
+            pa.rp_out = b->g->rp_out.as<int32_t>();
+            pa.q_cover = sk->ql[0].as<QEntry>();
+            pa.ctr_cover = &sk->ctr.as<ulonglong2>()[0].x;
+            pa.chg0 = sk->chg[0].as<uint32_t>();
+            pa.gcount = sk->gcount;
+            pa.err = sk->err.as<uint32_t>();
+            e = timed(c, kTPick, [&] { return launch_batch_pick(pa, st); });
+            if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "batch pick"); }
+            if ((s = run_levels(sk, kCover, false)) != IM_OK) { cleanup(); return s; }
+            e = cudaMemcpyAsync(count.data(), gcount_d.p, (size_t)G * 8, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = sync_collect(c);
+            if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "batch counts"); }
+            bool any = false;
+            for (int32_t g : members) {
+                flag[g] = 0;
+                if (!active[g]) continue;
+                score[g].push_back((double)count[g] / (double)Jg);
+                if (r + 1 < K[g] && rebuild_due(count[g], oldcount[g], Jg, rebuild_eps)) {
+                    flag[g] = 1;
+                    oldcount[g] = count[g];
+                    any = true;
+                }
+            }
+            if (any) {
+                e = cudaMemcpyAsync(flag_d.p, flag.data(), (size_t)G, cudaMemcpyHostToDevice, st);
+                if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "batch flags"); }
+                if ((s = batch_build(sk)) != IM_OK) { cleanup(); return s; }
+                ++builds;
+            }
+        }
+        std::vector<int32_t> hseed((size_t)G * maxK);
+        std::vector<double> hest((size_t)G * maxK);
+        e = cudaMemcpyAsync(hseed.data(), oseed.p, hseed.size() * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hest.data(), oest.p, hest.size() * 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = sync_collect(c);
+        if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "batch results"); }
+        for (int32_t g : members) {
+            for (int32_t k = 0; k < K[g]; ++k) {
+                const int32_t sg = hseed[(size_t)g * maxK + k];
+                seeds_out[koff[g] + k] = sg >= 0 ? sg - b->voff[g] : -1;
+                if (score_out) score_out[koff[g] + k] = score[g][k];
+                if (estimate_out) estimate_out[koff[g] + k] = hest[(size_t)g * maxK + k];
+            }
+        }
+        if ((s = stats_collect(sk)) != IM_OK) { cleanup(); return s; }
+        cleanup();
+    }
+    c->stats.builds = builds;
+    c->stats.ms_total = now_ms() - t0;
     return IM_OK;
 }

@@ -21,7 +21,8 @@ constexpr uint64_t kEdgeMask = (1ull << kCountShift) - 1;
 constexpr int kMaxLevels = 16384;              // propagation sweeps / cover levels per phase
 constexpr int kCasRetryLimit = 4096;
 
-enum ModelKind : int { kUniform = 0, kWC = 1, kTrivalency = 2, kExplicit = 3 };
+enum ModelKind : int { kUniform = 0, kWC = 1, kTrivalency = 2, kExplicit = 3,
+                       kTargetModel = 4 /* per-target-vertex probability; runs as kWC */ };
 
 // Error bits a kernel may raise (host turns them into IM_E_* codes).
 enum : uint32_t { kErrCasLimit = 1u, kErrQueue = 2u, kErrBarrier = 4u };

@@ -283,6 +283,9 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                                 if (really) {
                                     nbits |= bytes_to_bits(really) << (4 * w);
                                     st_new += (unsigned)(__popc(really) >> 3);
+                                    if (a.gcount)
+                                        atomicAdd(a.gcount + __ldg(a.gid + o_i),
+                                                  (unsigned long long)(__popc(really) >> 3));
                                 }
                             }
                         }
@@ -762,7 +765,7 @@ __global__ void __launch_bounds__(kFBlock) k_init_queues(GraphDev g, LevelArgs a
             deg = g.rp_in[v + 1] - rp;
             if constexpr (KIND == kWC) aux = g.thr_v[v];
             heavy = is_heavy<KIND>(deg, KIND == kWC ? aux : g.thr_uniform, a.heavy_indeg);
-            want = deg > 0;
+            want = deg > 0 && (!a.gflag || a.gflag[a.gid[v]]);
         }
         append(want && !heavy, (int32_t)v, rp, deg, aux, a.ql_out, a.cl_out, g.n, a.err);
         append(want && heavy, (int32_t)v, rp, deg, aux, a.qh_out, a.ch_out, g.n, a.err);

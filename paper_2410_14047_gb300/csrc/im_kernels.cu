@@ -92,6 +92,45 @@ __global__ void __launch_bounds__(kBlock) k_fill(uint8_t* __restrict__ M, int32_
     }
 }
 
+__global__ void __launch_bounds__(kBlock) k_fill_flagged(uint8_t* __restrict__ M, int32_t n, int J,
+                                                         const uint32_t* __restrict__ salt,
+                                                         const int32_t* __restrict__ gid,
+                                                         const uint8_t* __restrict__ gflag,
+                                                         const int32_t* __restrict__ hkey) {
+    const int cpr_log = __ffs(J >> 4) - 1;
+    const int64_t total = (int64_t)n << cpr_log;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t u = (uint32_t)(c >> cpr_log);
+        if (!gflag[gid[u]]) continue;
+        const int ch = (int)(c & ((1 << cpr_log) - 1));
+        uint4* p = reinterpret_cast<uint4*>(M + (size_t)u * J + ch * 16);
+        const uint4 cur = *p;
+        const uint32_t ku = mm3_k((uint32_t)hkey[u]);  // rank of the graph's own vertex id
+        const uint4* sl = reinterpret_cast<const uint4*>(salt + ch * 16);
+        uint32_t w[4] = {cur.x, cur.y, cur.z, cur.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 s4 = __ldg(sl + q);
+            const uint32_t r = rank_of(ku, s4.x) | (rank_of(ku, s4.y) << 8) |
+                               (rank_of(ku, s4.z) << 16) | (rank_of(ku, s4.w) << 24);
+            const uint32_t vis = visited_bytes(w[q]);
+            w[q] = (w[q] & vis) | (r & ~vis);
+        }
+        *p = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+cudaError_t launch_fill_flagged(uint8_t* M, int32_t n, int J, const uint32_t* salt, const int32_t* gid,
+                                const uint8_t* gflag, const int32_t* hkey, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int64_t total = (int64_t)n * (J / 16);
+    int64_t grid = (total + kBlock - 1) / kBlock;
+    if (grid > 152 * 16) grid = 152 * 16;
+    k_fill_flagged<<<(int)grid, kBlock, 0, st>>>(M, n, J, salt, gid, gflag, hkey);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fill(uint8_t* M, int32_t n, int J, const uint32_t* salt, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     const int64_t total = (int64_t)n * (J / 16);
@@ -797,8 +836,9 @@ size_t sort_tmp_bytes(int64_t n) {
 // Sort keys of the in-CSR: (target << 33) | (class << 31) | hE(source, target),
 // payload = out-edge index.  class = trivalency class (0 for other models).
 __global__ void k_in_keys(const int32_t* __restrict__ rp_out, const int32_t* __restrict__ col_out,
-                          int32_t n, int kind, uint32_t tri_seed, unsigned long long* __restrict__ keys,
-                          int32_t* __restrict__ perm, int32_t* __restrict__ src_out) {
+                          int32_t n, int kind, uint32_t tri_seed, const int32_t* __restrict__ hkey,
+                          unsigned long long* __restrict__ keys, int32_t* __restrict__ perm,
+                          int32_t* __restrict__ src_out) {
     const int lane = (int)lane_id();
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -806,9 +846,11 @@ __global__ void k_in_keys(const int32_t* __restrict__ rp_out, const int32_t* __r
         const int32_t b = rp_out[u], e = rp_out[u + 1];
         for (int32_t i = b + lane; i < e; i += 32) {
             const uint32_t v = (uint32_t)col_out[i];
-            const uint32_t cls = kind == kTrivalency ? hash_pair((uint32_t)u, v, tri_seed) % 3u : 0u;
-            keys[i] = ((unsigned long long)v << 33) | ((unsigned long long)cls << 31) |
-                      edge_hash((uint32_t)u, v);
+            // hash keys: the vertex ids of the graph the edge belongs to
+            const uint32_t ku = hkey ? (uint32_t)hkey[u] : (uint32_t)u;
+            const uint32_t kv = hkey ? (uint32_t)hkey[v] : v;
+            const uint32_t cls = kind == kTrivalency ? hash_pair(ku, kv, tri_seed) % 3u : 0u;
+            keys[i] = ((unsigned long long)v << 33) | ((unsigned long long)cls << 31) | edge_hash(ku, kv);
             perm[i] = i;
             src_out[i] = (int32_t)u;
         }
@@ -817,8 +859,8 @@ __global__ void k_in_keys(const int32_t* __restrict__ rp_out, const int32_t* __r
 
 // Out-edge hash and weighted-cascade threshold of every out-edge (out-CSR order).
 __global__ void k_out_edge_words(const int32_t* __restrict__ rp_out, const int32_t* __restrict__ col_out,
-                                 int32_t n, const uint32_t* __restrict__ thr_v, uint32_t* __restrict__ h_out,
-                                 uint32_t* __restrict__ thrw_out) {
+                                 int32_t n, const uint32_t* __restrict__ thr_v, const int32_t* __restrict__ hkey,
+                                 uint32_t* __restrict__ h_out, uint32_t* __restrict__ thrw_out) {
     const int lane = (int)lane_id();
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -826,17 +868,17 @@ __global__ void k_out_edge_words(const int32_t* __restrict__ rp_out, const int32
         const int32_t b = rp_out[u], e = rp_out[u + 1];
         for (int32_t i = b + lane; i < e; i += 32) {
             const uint32_t v = (uint32_t)col_out[i];
-            h_out[i] = edge_hash((uint32_t)u, v);
+            h_out[i] = hkey ? edge_hash((uint32_t)hkey[u], (uint32_t)hkey[v]) : edge_hash((uint32_t)u, v);
             thrw_out[i] = thr_v[v];
         }
     }
 }
 
 cudaError_t launch_out_edge_words(const int32_t* rp_out, const int32_t* col_out, int32_t n, int64_t m,
-                                  const uint32_t* thr_v, uint32_t* h_out, uint32_t* thrw_out,
-                                  cudaStream_t st) {
+                                  const uint32_t* thr_v, const int32_t* hkey, uint32_t* h_out,
+                                  uint32_t* thrw_out, cudaStream_t st) {
     if (m == 0) return cudaSuccess;
-    k_out_edge_words<<<152 * 8, kBlock, 0, st>>>(rp_out, col_out, n, thr_v, h_out, thrw_out);
+    k_out_edge_words<<<152 * 8, kBlock, 0, st>>>(rp_out, col_out, n, thr_v, hkey, h_out, thrw_out);
     return cudaGetLastError();
 }
 
@@ -876,7 +918,7 @@ __global__ void k_cls_split(const int32_t* __restrict__ rp_in, const unsigned lo
 }
 
 cudaError_t launch_build_in_csr(const int32_t* rp_out, const int32_t* col_out, int32_t n, int64_t m,
-                                int kind, uint32_t tri_seed, const uint32_t* thr_out,
+                                int kind, uint32_t tri_seed, const int32_t* hkey, const uint32_t* thr_out,
                                 const int32_t* rp_in, int32_t* src_in, uint32_t* h_in,
                                 uint32_t* thr_in, int2* cls_split, void* tmp, cudaStream_t st) {
     if (m == 0) return cudaSuccess;
@@ -887,7 +929,7 @@ cudaError_t launch_build_in_csr(const int32_t* rp_out, const int32_t* col_out, i
     p += ((size_t)m * 4 + 255) & ~(size_t)255;
     int32_t* src_out = reinterpret_cast<int32_t*>(p);
     p += ((size_t)m * 4 + 255) & ~(size_t)255;
-    k_in_keys<<<152 * 8, kBlock, 0, st>>>(rp_out, col_out, n, kind, tri_seed, keys, perm, src_out);
+    k_in_keys<<<152 * 8, kBlock, 0, st>>>(rp_out, col_out, n, kind, tri_seed, hkey, keys, perm, src_out);
     int bits = 33;
     while ((1ll << (bits - 33)) < n) ++bits;
     cudaError_t e = launch_radix_sort(keys, perm, m, bits, p, st);
@@ -935,6 +977,138 @@ cudaError_t launch_radix_sort(unsigned long long* keys, int32_t* vals, int64_t n
         if (e == cudaSuccess) e = cudaMemcpyAsync(vals, va, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;
     }
+    return cudaGetLastError();
+}
+
+}  // namespace im
+
+namespace im {
+
+// ---------------------------------------------------------------------------
+// Batches: estimate + argmax of every active graph (Alg. 4 per graph).
+// k_batch_tiles: per tile (row range inside one graph) the smallest (S_u, u)
+// over rows not picked.  k_batch_graphs: one block per active graph reduces
+// its tiles, records the seed and its estimate, marks its row visited (the
+// graph's visited counter), and appends it to the cover's level-0 queue.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_batch_tiles(BatchPickArgs a) {
+    __shared__ unsigned long long sS[kWarpsPerBlock];
+    __shared__ int32_t sU[kWarpsPerBlock];
+    const int J = a.J;
+    const int cpr = J >> 4;
+    const int lpr = cpr < 32 ? cpr : 32;
+    const int cpl = cpr / lpr;
+    const int rpw = 32 / lpr;
+    const int lane = (int)lane_id();
+    const int seg = lane / lpr, seg_lane = lane % lpr;
+    const int wib = threadIdx.x >> 5;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const int4 T = a.tiles[t];
+        unsigned long long bestS = ~0ull;
+        int32_t bestU = 0x7FFFFFFF;
+        if (a.active[T.x]) {
+            for (int64_t r0 = (int64_t)T.y + (int64_t)wib * rpw; r0 < T.z; r0 += (int64_t)kWarpsPerBlock * rpw) {
+                const int64_t row = r0 + seg;
+                const bool ok = row < T.z;
+                const unsigned long long s = row_sum(a.M, J, ok ? (int32_t)row : T.y, lpr, cpl, seg_lane);
+                if (ok && seg_lane == 0) {
+                    const bool picked = (__ldcg(a.picked + (row >> 5)) >> (row & 31)) & 1u;
+                    if (!picked) lex_min(bestS, bestU, s, (int32_t)row);
+                }
+            }
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            const unsigned long long oS = __shfl_xor_sync(0xFFFFFFFFu, bestS, off);
+            const int32_t ou = __shfl_xor_sync(0xFFFFFFFFu, bestU, off);
+            lex_min(bestS, bestU, oS, ou);
+        }
+        if (lane == 0) { sS[wib] = bestS; sU[wib] = bestU; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < kWarpsPerBlock; ++w) lex_min(bestS, bestU, sS[w], sU[w]);
+            a.part_S[t] = bestS;
+            a.part_u[t] = bestU;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_batch_graphs(BatchPickArgs a) {
+    __shared__ unsigned long long sS[kWarpsPerBlock];
+    __shared__ int32_t sU[kWarpsPerBlock];
+    __shared__ unsigned long long fS;
+    __shared__ int32_t fU;
+    __shared__ unsigned int newly_sh;
+    const int g = blockIdx.x;
+    if (g >= a.G || !a.active[g]) return;
+    const int lane = (int)lane_id(), wib = threadIdx.x >> 5;
+    unsigned long long bS = ~0ull;
+    int32_t bU = 0x7FFFFFFF;
+    for (int t = a.tile_begin[g] + threadIdx.x; t < a.tile_end[g]; t += blockDim.x)
+        lex_min(bS, bU, __ldcg(a.part_S + t), __ldcg(a.part_u + t));
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const unsigned long long oS = __shfl_xor_sync(0xFFFFFFFFu, bS, off);
+        const int32_t ou = __shfl_xor_sync(0xFFFFFFFFu, bU, off);
+        lex_min(bS, bU, oS, ou);
+    }
+    if (lane == 0) { sS[wib] = bS; sU[wib] = bU; }
+    __syncthreads();
+    const int slot = g * a.maxK + a.round;
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kWarpsPerBlock; ++w) lex_min(bS, bU, sS[w], sU[w]);
+        fS = bS;
+        fU = bU;
+        newly_sh = 0u;
+        if (bS == ~0ull) {
+            a.out_seed[slot] = -1;
+        } else {
+            a.out_seed[slot] = bU;
+            a.out_S[slot] = bS;
+            a.out_est[slot] = ((double)a.J * 4294967296.0) / (0.77351 * (double)bS);
+            atomicOr(a.picked + (bU >> 5), 1u << (bU & 31));
+        }
+    }
+    __syncthreads();
+    if (fS == ~0ull) return;
+    // the cover's level 0: the seed's row becomes visited
+    const int32_t s = fU;
+    const int J = a.J;
+    uint8_t* row = a.M + (size_t)s * J;
+    const int Jr = (J + 31) & ~31;
+    const int words = Jr >> 5;
+    unsigned int newly = 0;
+    for (int j = threadIdx.x; j < Jr; j += blockDim.x) {
+        const bool fresh = j < J && row[j] != kVisited;
+        if (fresh) { row[j] = (uint8_t)kVisited; ++newly; }
+        const unsigned bits = __ballot_sync(0xFFFFFFFFu, fresh);
+        if ((j & 31) == 0) a.chg0[(size_t)s * words + (j >> 5)] = bits;
+    }
+    newly = (unsigned)warp_sum(newly);
+    if (lane == 0 && newly) atomicAdd(&newly_sh, newly);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int nw = newly_sh;
+        if (nw) atomicAdd(a.gcount + g, (unsigned long long)nw);
+        const int32_t rp = a.rp_out[s];
+        const int32_t deg = a.rp_out[s + 1] - rp;
+        if (nw && deg > 0) {
+            const unsigned long long base =
+                atomicAdd(a.ctr_cover, (1ull << kCountShift) | (unsigned long long)deg);
+            QEntry e;
+            e.v = s; e.rp = rp; e.off = (int32_t)(base & kEdgeMask); e.aux = 0;
+            a.q_cover[base >> kCountShift] = e;
+        }
+    }
+}
+
+cudaError_t launch_batch_pick(const BatchPickArgs& a, cudaStream_t st) {
+    if (a.ntiles > 0) {
+        const int grid = a.ntiles < 152 * 8 ? a.ntiles : 152 * 8;
+        k_batch_tiles<<<grid, kBlock, 0, st>>>(a);
+    }
+    k_batch_graphs<<<a.G, kBlock, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -68,6 +68,9 @@ struct LevelArgs {
     unsigned long long* count;           // visited-register counter (cover)
     unsigned long long* stats;
     uint32_t* err;
+    const int32_t* gid;                  // batches: graph of every vertex (NULL for one graph)
+    unsigned long long* gcount;          // batches: visited-register counter per graph (cover)
+    const uint8_t* gflag;                // batches: graphs whose vertices enter level 0 (build)
 };
 
 // All levels of a phase in one cooperative launch (grid barrier between levels).
@@ -121,6 +124,37 @@ int pick_grid(int32_t n, int J);
 cudaError_t launch_sims(uint64_t seed, int J, uint32_t* X, uint32_t* salt, uint16_t* tab,
                         cudaStream_t st);
 cudaError_t launch_fill(uint8_t* M, int32_t n, int J, const uint32_t* salt, cudaStream_t st);
+// Fill of the rows whose graph has gflag[gid[u]] != 0 (batches).
+cudaError_t launch_fill_flagged(uint8_t* M, int32_t n, int J, const uint32_t* salt, const int32_t* gid,
+                                const uint8_t* gflag, const int32_t* hkey, cudaStream_t st);
+
+// Batches: estimate + argmax per graph.  Tiles are row ranges inside one
+// graph: (graph, row begin, row end).
+struct BatchPickArgs {
+    uint8_t* M;
+    int J;
+    const int4* tiles;            // x = graph, y = row begin, z = row end
+    int ntiles;
+    const uint8_t* active;        // graph picks this round
+    uint32_t* picked;             // picked bitmap over the union
+    unsigned long long* part_S;   // per tile
+    int32_t* part_u;
+    const int32_t* tile_begin;    // per graph: first tile (tiles of a graph are consecutive)
+    const int32_t* tile_end;
+    int G;
+    int round;
+    int maxK;
+    int32_t* out_seed;            // [G * maxK]: global vertex ids
+    unsigned long long* out_S;
+    double* out_est;
+    const int32_t* rp_out;
+    QEntry* q_cover;              // cover level-0 queue
+    unsigned long long* ctr_cover;
+    uint32_t* chg0;
+    unsigned long long* gcount;
+    uint32_t* err;
+};
+cudaError_t launch_batch_pick(const BatchPickArgs& a, cudaStream_t st);
 cudaError_t launch_pick(const PickArgs& a, cudaStream_t st);
 // Marks row s visited (adding the newly visited registers to *count) and
 // queues s as level 0 of a cover.
@@ -139,15 +173,17 @@ cudaError_t launch_exclusive_scan(const int32_t* cnt, int32_t n, int32_t* out, v
                                   cudaStream_t st);
 // In-CSR sorted by (target, trivalency class, edge hash): src_in, h_in (edge
 // hashes), thr_in (explicit models, may be NULL), cls_split (trivalency, may
-// be NULL).  rp_in must already hold the in-CSR row pointers.
+// be NULL).  rp_in must already hold the in-CSR row pointers.  hkey (may be
+// NULL = the vertex id itself) is the id each vertex hashes with (batches:
+// its id inside its own graph).
 size_t build_in_csr_tmp_bytes(int64_t m);
 cudaError_t launch_build_in_csr(const int32_t* rp_out, const int32_t* col_out, int32_t n, int64_t m,
-                                int kind, uint32_t tri_seed, const uint32_t* thr_out,
+                                int kind, uint32_t tri_seed, const int32_t* hkey, const uint32_t* thr_out,
                                 const int32_t* rp_in, int32_t* src_in, uint32_t* h_in,
                                 uint32_t* thr_in, int2* cls_split, void* tmp, cudaStream_t st);
 cudaError_t launch_out_edge_words(const int32_t* rp_out, const int32_t* col_out, int32_t n, int64_t m,
-                                  const uint32_t* thr_v, uint32_t* h_out, uint32_t* thrw_out,
-                                  cudaStream_t st);
+                                  const uint32_t* thr_v, const int32_t* hkey, uint32_t* h_out,
+                                  uint32_t* thrw_out, cudaStream_t st);
 cudaError_t launch_radix_sort(unsigned long long* keys, int32_t* vals, int64_t n, int bits,
                               void* tmp, cudaStream_t st);
 size_t sort_tmp_bytes(int64_t n);
