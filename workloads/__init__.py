@@ -183,3 +183,20 @@ def workload(name: str) -> Workload:
                         lambda: rmat(24, 16, seed=2410), {"kind": "trivalency", "seed": 2410},
                         J=512, K=50)
     raise KeyError(name)
+
+
+def batched_workload(G: int = 512, seed: int = 2410):
+    """The batched form: G directed Chung-Lu graphs (gamma 2.1), n uniform in
+    [1000, 200000], average degree uniform in [8, 32]; per graph K uniform in
+    [5, 50], J in {64, 128}, uniform IC p in [0.005, 0.05].  Returns
+    (graphs, p, J, K)."""
+    rng = np.random.default_rng(seed)
+    graphs, p, J, K = [], [], [], []
+    for i in range(G):
+        n = int(rng.integers(1000, 200001))
+        d = float(rng.uniform(8, 32))
+        graphs.append(chung_lu(n, d, 2.1, seed=seed * 1000 + i))
+        p.append(float(np.float32(rng.uniform(0.005, 0.05))))
+        J.append(int(rng.choice([64, 128])))
+        K.append(int(rng.integers(5, 51)))
+    return graphs, p, J, K

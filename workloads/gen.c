@@ -179,8 +179,9 @@ int64_t wl_erdos_renyi(int32_t n, int64_t m, uint64_t seed, int32_t* rowptr, int
 
 /*
  * Directed Chung-Lu graph with power-law expected degrees: vertex i has
- * weight w_i = C (i + i0)^(-1/(gamma-1)), with i0 and C fixed so that
- * sum_i w_i = n * avg_deg and w_0 = sqrt(sum_i w_i) (so w_u w_v / sum w <= 1).
+ * weight w_i = C (i + i0)^(-1/(gamma-1)), with C fixed so that
+ * sum_i w_i = n * avg_deg and i0 chosen (with the power sum approximated by
+ * its integral) so that w_0 is about sqrt(sum_i w_i).
  * Edge (u, v), u != v, appears independently with probability
  * min(1, w_u w_v / sum w).  Edges of a row are generated by geometric
  * skipping (Miller, Hagberg, "Efficient generation of networks with given
@@ -225,11 +226,14 @@ int64_t wl_chung_lu(int32_t n, double avg_deg, double gamma, uint64_t seed, int3
     if (n < 2 || avg_deg <= 0.0 || gamma <= 1.0) return -2;
     double alpha = 1.0 / (gamma - 1.0);
     double target = (double)n * avg_deg;
-    /* bisection on i0: f(i0) = w_0^2 - sum w, with C chosen so that sum w = target */
+    /* bisection on i0 with sum_i (i+i0)^-alpha approximated by its integral
+     * over [i0 - 1/2, n + i0 - 1/2]; C then comes from the exact sum */
     double lo = 1e-3, hi = (double)n * 4.0;
-    for (int it = 0; it < 200; it++) {
+    for (int it = 0; it < 100; it++) {
         double mid = 0.5 * (lo + hi);
-        double C = target / cl_weight_sum(n, alpha, mid);
+        double a0 = mid - 0.5 > 1e-9 ? mid - 0.5 : 1e-9;
+        double sum = (pow((double)n + a0, 1.0 - alpha) - pow(a0, 1.0 - alpha)) / (1.0 - alpha);
+        double C = target / sum;
         double w0 = C * pow(mid, -alpha);
         if (w0 * w0 > target) lo = mid; else hi = mid;
     }
