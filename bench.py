@@ -49,6 +49,12 @@ def parse():
                     help="graphs of the batched workload (--workload batched)")
     ap.add_argument("--tuning", default="",
                     help="JSON schedule knobs passed to im_ctx_set_tuning (profiling and sweeps)")
+    ap.add_argument("--queries", type=int, default=400,
+                    help="queries of the served workload (--workload served)")
+    ap.add_argument("--rate", type=float, default=200.0,
+                    help="mean Poisson arrival rate of the served workload, queries/s")
+    ap.add_argument("--slots", type=int, default=8,
+                    help="concurrent queries of the server (--workload served)")
     ap.add_argument("--quick", action="store_true",
                     help="profiling runs: no clock sampling, end-to-end pass or CPU baseline")
     return ap.parse_args()
@@ -262,6 +268,103 @@ def run_batched(args):
     return 0
 
 
+def run_served(args):
+    """Served form: Poisson arrivals of queries against 16 resident R-MAT
+    graphs, run by the query server (concurrent slots, HBM-budget admission)
+    and, on the same arrival sequence, by the plain path one query at a time.
+    Latency = completion - arrival; queries/s = queries / (last completion -
+    first arrival)."""
+    import numpy as np
+    import torch
+
+    import paper_2410_14047_gb300 as im
+    import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    t0 = time.perf_counter()
+    graphs = W.served_graphs(seed=2410)
+    gen_s = time.perf_counter() - t0
+    ctx = im.im_ctx_create(local)
+    loaded = [im.im_graph_load(ctx, g.rowptr, g.col, {"kind": "wc"}) for g in graphs]
+    torch.cuda.synchronize()
+    qs = W.served_queries(args.queries, rate=args.rate, n_graphs=len(graphs), seed=2410)
+    budget = 150 * 10**9
+    srv = im.Server(local, slots=args.slots, hbm_budget_bytes=budget, max_bypass=2 * args.slots)
+    for G in loaded:
+        srv.add_graph(G)
+    warm = W.served_queries(max(args.warmup, 1) * 4, rate=1e6, n_graphs=len(graphs), seed=99)
+    for q in warm:  # module load, pool growth, first launches of each path
+        srv.wait(srv.submit(**{k: q[k] for k in ("graph", "K", "J", "model", "seed", "rebuild_eps")}))
+        im.im_select_seeds(loaded[q["graph"]], q["K"], q["J"], model=q["model"], seed=q["seed"])
+    torch.cuda.synchronize()
+
+    def args_of(q):
+        return {k: q[k] for k in ("graph", "K", "J", "model", "seed", "rebuild_eps")}
+
+    clocks = None if args.quick else ClockSampler(local)
+    if clocks:
+        clocks.start()
+    # served: submit at the arrival times, collect completions
+    t_base = srv.clock_ms() + 50.0
+    tickets = []
+    for q in qs:
+        due = t_base + q["arrival_s"] * 1e3
+        while True:
+            now = srv.clock_ms()
+            if now >= due:
+                break
+            time.sleep(min(0.002, (due - now) / 1e3))
+        tickets.append(srv.submit(**args_of(q)))
+    served = [srv.wait(t) for t in tickets]
+    sstats = srv.stats()
+    s_done = np.array([r["t_done_ms"] for r in served])
+    s_arr = np.array([t_base + q["arrival_s"] * 1e3 for q in qs])
+    s_lat = (s_done - s_arr) / 1e3
+    served_s = (s_done.max() - s_arr.min()) / 1e3
+    srv.close()
+    # plain: one query at a time in arrival order on the same resident graphs
+    t_base = srv.clock_ms() + 50.0
+    p_done = []
+    plain_res = []
+    for q in qs:
+        due = t_base + q["arrival_s"] * 1e3
+        while srv.clock_ms() < due:
+            time.sleep(0.001)
+        plain_res.append(im.im_select_seeds(loaded[q["graph"]], q["K"], q["J"], model=q["model"],
+                                            seed=q["seed"], rebuild_eps=q["rebuild_eps"]))
+        p_done.append(srv.clock_ms())
+    p_done = np.array(p_done)
+    p_arr = np.array([t_base + q["arrival_s"] * 1e3 for q in qs])
+    p_lat = (p_done - p_arr) / 1e3
+    plain_s = (p_done.max() - p_arr.min()) / 1e3
+    clk = clocks.stop() if clocks else None
+    identical = all(r["status"] == 0 and r["seeds"].tolist() == pr["seeds"].tolist()
+                    and np.array_equal(r["score"], pr["score"]) for r, pr in zip(served, plain_res))
+    N = len(qs)
+    out = {"metric": "served IM queries/s (p50/p99 latency, arrival to result)", "value": N / served_s,
+           "unit": "queries/s", "impl": "gb300-served", "n_gpus": 1, "higher_is_better": True,
+           "dtype": "u8", "data": "synthetic (seeded R-MAT graphs, Poisson arrivals)",
+           "config": {"workload": f"served: 16 resident R-MAT graphs scales 14-22 ef 16, {N} queries, "
+                                  f"Poisson {args.rate:g}/s, K {{10,25,50}}, J {{64,256,1024}}, "
+                                  "model p=0.01 or WC, 150 GB budget",
+                      "queries": N, "rate": args.rate, "slots": args.slots, "budget_bytes": budget,
+                      "sum_n": int(sum(g.n for g in graphs)), "sum_m": int(sum(g.m for g in graphs))},
+           "served": {"value": N / served_s, "total_s": served_s,
+                      "p50_s": float(np.percentile(s_lat, 50)), "p99_s": float(np.percentile(s_lat, 99)),
+                      "running_peak": sstats["running_peak"], "reserved_peak_bytes": sstats["reserved_peak"],
+                      "graph_bytes": sstats["graph_bytes"], "bypassed": sstats["bypassed"]},
+           "plain": {"value": N / plain_s, "unit": "queries/s", "total_s": plain_s,
+                     "p50_s": float(np.percentile(p_lat, 50)), "p99_s": float(np.percentile(p_lat, 99))},
+           "speedup_vs_plain": plain_s / served_s,
+           "identical_to_plain": bool(identical),
+           "generation_s": gen_s}
+    if clk:
+        out["clocks"] = clk
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -412,6 +515,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
     return run_gpu(args)
 
 

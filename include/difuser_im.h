@@ -296,6 +296,89 @@ IM_API im_status im_spread_mc(im_graph* g, const int32_t* seeds, int32_t k, int6
                        double* mean_out, double* stderr_out, uint64_t* sum_out,
                        uint64_t* sumsq_out);
 
+/* ---- served form: concurrent queries on resident graphs ----------------- */
+
+/* A query server (the paper has none: it serves one query per run).  It keeps
+ * graphs resident and runs im_select_seeds queries that arrive at any time:
+ * `slots` worker threads, each with its own CUDA stream and stream-ordered
+ * memory pool, so the kernels of up to `slots` queries overlap on the device
+ * (continuous batching: a query starts as soon as a slot and its device memory
+ * are free, while others are running).  Admission control: the resident graphs
+ * plus the device bytes reserved by running queries (im_server_query_bytes,
+ * an exact upper bound of what a query allocates) never exceed the budget.
+ * Pending queries start in arrival order; one that fits may start ahead of an
+ * older one that does not, at most `max_bypass` times in a row for that older
+ * query.  Each query's result is the one im_select_seeds gives for the same
+ * graph and arguments: queries share only the read-only graph. */
+typedef struct im_server im_server;
+
+typedef struct {
+    int32_t device;             /* CUDA device of the server and its graphs */
+    int32_t slots;              /* concurrent queries, 1..64 */
+    uint64_t hbm_budget_bytes;  /* resident graphs + running queries; 0 = no limit */
+    int32_t max_bypass;         /* >= 0; see above */
+} im_server_config;
+
+typedef struct {
+    int32_t graph;       /* id from im_server_add_graph */
+    int32_t K;           /* seeds to select, 1..n */
+    int32_t J;           /* simulations (registers per vertex) */
+    im_model model;      /* uniform / weighted cascade / trivalency (w unused);
+                            kind -1: the model the graph was loaded with */
+    uint64_t seed;       /* simulation seed, as im_select_seeds */
+    double rebuild_eps;  /* as im_select_seeds */
+} im_query;
+
+typedef struct {
+    int64_t ticket;
+    int32_t status;      /* im_status of the query */
+    int32_t slot;        /* worker that ran it */
+    double t_submit_ms;  /* im_server_clock_ms() at submission */
+    double t_start_ms;   /* ... when a slot took it */
+    double t_done_ms;    /* ... when its seeds were on the host */
+    double ms_select;    /* host time of the selection itself */
+    uint64_t bytes;      /* device bytes reserved for it */
+    char error[160];     /* message when status != IM_OK */
+} im_query_result;
+
+typedef struct {
+    int64_t submitted, completed, failed, bypassed;
+    int32_t slots, running, running_peak, pending;
+    uint64_t budget, graph_bytes, reserved, reserved_peak;
+} im_server_stats;
+
+/* Starts the worker threads.  Errors: IM_E_INVAL (NULL, slots outside
+ * [1, 64], max_bypass < 0), IM_E_CUDA. */
+IM_API im_status im_server_create(const im_server_config* cfg, im_server** out);
+/* Runs every pending query to completion, then stops the workers and frees
+ * the server (not the graphs). */
+IM_API void im_server_destroy(im_server* srv);
+/* Registers a loaded graph (any context on the server's device); the graph
+ * must outlive the server and is only read.  Its device bytes count against
+ * the budget.  Errors: IM_E_INVAL, IM_E_STATE (other device), IM_E_NOMEM
+ * (graphs alone exceed the budget). */
+IM_API im_status im_server_add_graph(im_server* srv, im_graph* g, int32_t* id_out);
+/* Device bytes a query of J simulations and K seeds on graph `graph` reserves. */
+IM_API im_status im_server_query_bytes(im_server* srv, int32_t graph, int32_t J, int32_t K,
+                                       uint64_t* bytes_out);
+/* Queues a query and returns at once.  seeds_out (K int32), score_out and
+ * estimate_out (K doubles each, may be NULL) are host buffers the caller owns
+ * and keeps valid until im_server_wait returns for this ticket; they are
+ * written by the worker.  Errors (nothing queued): IM_E_INVAL, IM_E_RANGE
+ * (graph id, K), IM_E_STATE (model fixed at load), IM_E_NOMEM (the query alone
+ * exceeds what the budget leaves beside the graphs). */
+IM_API im_status im_server_submit(im_server* srv, const im_query* q, int32_t* seeds_out,
+                                  double* score_out, double* estimate_out, int64_t* ticket_out);
+/* Waits up to timeout_ms (< 0: no limit) for the query to finish and fills
+ * *out; the ticket is then released.  Returns IM_E_TIMEOUT if it is still
+ * pending or running, IM_E_RANGE for an unknown ticket; otherwise IM_OK (the
+ * query's own status is out->status). */
+IM_API im_status im_server_wait(im_server* srv, int64_t ticket, double timeout_ms,
+                                im_query_result* out);
+IM_API im_status im_server_get_stats(im_server* srv, im_server_stats* out);
+/* Monotonic clock of the result timestamps, in milliseconds. */
+IM_API double im_server_clock_ms(void);
+
 #ifdef __cplusplus
 }
 #endif

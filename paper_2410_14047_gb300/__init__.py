@@ -30,7 +30,9 @@ EXPORTS = ["im_ctx_create", "im_ctx_destroy", "im_ctx_bytes_in_use", "im_ctx_byt
            "im_graph_info", "im_sketch_build", "im_sketch_free", "im_sketch_registers",
            "im_sketch_set_registers", "im_sketch_sims", "im_sketch_sums", "im_sketch_pick",
            "im_sketch_cover", "im_sketch_rebuild", "im_select_seeds", "im_spread_mc",
-           "im_argmax_noalloc", "im_batch_load", "im_batch_free", "im_batch_select_seeds"]
+           "im_argmax_noalloc", "im_batch_load", "im_batch_free", "im_batch_select_seeds",
+           "im_server_create", "im_server_destroy", "im_server_add_graph", "im_server_query_bytes",
+           "im_server_submit", "im_server_wait", "im_server_get_stats", "im_server_clock_ms"]
 
 
 class IMError(RuntimeError):
@@ -74,6 +76,29 @@ class im_tuning(ctypes.Structure):
 class im_trace_rec(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("count", ctypes.c_int64),
                 ("edges", ctypes.c_int64), ("ms", ctypes.c_double)]
+
+
+class im_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("slots", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_uint64), ("max_bypass", ctypes.c_int32)]
+
+
+class im_query(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_int32), ("K", ctypes.c_int32), ("J", ctypes.c_int32),
+                ("model", im_model), ("seed", ctypes.c_uint64), ("rebuild_eps", ctypes.c_double)]
+
+
+class im_query_result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_int64), ("status", ctypes.c_int32), ("slot", ctypes.c_int32),
+                ("t_submit_ms", ctypes.c_double), ("t_start_ms", ctypes.c_double),
+                ("t_done_ms", ctypes.c_double), ("ms_select", ctypes.c_double),
+                ("bytes", ctypes.c_uint64), ("error", ctypes.c_char * 160)]
+
+
+class im_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "failed", "bypassed")] + \
+               [(k, ctypes.c_int32) for k in ("slots", "running", "running_peak", "pending")] + \
+               [(k, ctypes.c_uint64) for k in ("budget", "graph_bytes", "reserved", "reserved_peak")]
 
 
 _lib = None
@@ -122,6 +147,14 @@ def load_library(path: str = LIB_PATH):
                                          P(vp)]),
         "im_batch_free": (None, [vp]),
         "im_batch_select_seeds": (ctypes.c_int, [vp, P(i32), P(i32), u64, f64, P(i32), P(f64), P(f64)]),
+        "im_server_create": (ctypes.c_int, [P(im_server_config), P(vp)]),
+        "im_server_destroy": (None, [vp]),
+        "im_server_add_graph": (ctypes.c_int, [vp, vp, P(i32)]),
+        "im_server_query_bytes": (ctypes.c_int, [vp, i32, i32, i32, P(u64)]),
+        "im_server_submit": (ctypes.c_int, [vp, P(im_query), P(i32), P(f64), P(f64), P(i64)]),
+        "im_server_wait": (ctypes.c_int, [vp, i64, f64, P(im_query_result)]),
+        "im_server_get_stats": (ctypes.c_int, [vp, P(im_server_stats)]),
+        "im_server_clock_ms": (f64, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -442,3 +475,88 @@ def im_ctx_bytes_in_use(ctx: Context) -> int:
 
 def im_ctx_bytes_peak(ctx: Context) -> int:
     return int(ctx.lib.im_ctx_bytes_peak(ctx.handle))
+
+
+class Server:
+    """Query server over resident graphs (im_server_*): concurrent selections,
+    each on its own worker stream, admitted under a device-memory budget."""
+
+    def __init__(self, device: int = 0, slots: int = 8, hbm_budget_bytes: int = 0, max_bypass: int = 4):
+        self.lib = load_library()
+        cfg = im_server_config(int(device), int(slots), int(hbm_budget_bytes), int(max_bypass))
+        h = ctypes.c_void_p()
+        st = self.lib.im_server_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != 0:
+            raise IMError(st, "im_server_create")
+        self.handle = h
+        self.graphs: list = []
+        self._live: dict = {}
+
+    def _check(self, st: int, what: str):
+        if st != 0:
+            raise IMError(st, what)
+
+    def add_graph(self, graph: Graph) -> int:
+        gid = ctypes.c_int32()
+        self._check(self.lib.im_server_add_graph(self.handle, graph.handle, ctypes.byref(gid)),
+                    "im_server_add_graph")
+        self.graphs.append(graph)  # the graph must outlive the server
+        return gid.value
+
+    def query_bytes(self, graph: int, J: int, K: int) -> int:
+        b = ctypes.c_uint64()
+        self._check(self.lib.im_server_query_bytes(self.handle, int(graph), int(J), int(K), ctypes.byref(b)),
+                    "im_server_query_bytes")
+        return int(b.value)
+
+    def submit(self, graph: int, K: int, J: int, model: dict | None = None, seed: int = 2410,
+               rebuild_eps: float = 0.01) -> int:
+        q = im_query()
+        q.graph, q.K, q.J = int(graph), int(K), int(J)
+        mdl = _model(model, [])
+        if mdl is None:
+            q.model.kind = -1
+        else:
+            q.model = mdl
+        q.seed = _u64(seed)
+        q.rebuild_eps = float(rebuild_eps)
+        seeds = np.empty(K, dtype=np.int32)
+        score = np.empty(K, dtype=np.float64)
+        est = np.empty(K, dtype=np.float64)
+        t = ctypes.c_int64()
+        self._check(self.lib.im_server_submit(self.handle, ctypes.byref(q), _p(seeds, ctypes.c_int32),
+                                              _p(score, ctypes.c_double), _p(est, ctypes.c_double),
+                                              ctypes.byref(t)), "im_server_submit")
+        self._live[t.value] = (seeds, score, est)  # the worker writes these until wait returns
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: float = -1.0) -> dict:
+        r = im_query_result()
+        self._check(self.lib.im_server_wait(self.handle, int(ticket), float(timeout_ms), ctypes.byref(r)),
+                    "im_server_wait")
+        seeds, score, est = self._live.pop(ticket)
+        out = {k: getattr(r, k) for k in ("ticket", "status", "slot", "t_submit_ms", "t_start_ms",
+                                          "t_done_ms", "ms_select", "bytes")}
+        out["error"] = r.error.decode(errors="replace")
+        out.update(seeds=seeds, score=score, est=est)
+        return out
+
+    def stats(self) -> dict:
+        s = im_server_stats()
+        self._check(self.lib.im_server_get_stats(self.handle, ctypes.byref(s)), "im_server_get_stats")
+        return {k: getattr(s, k) for k, _ in im_server_stats._fields_}
+
+    def clock_ms(self) -> float:
+        return float(self.lib.im_server_clock_ms())
+
+    def close(self):
+        if self.handle:
+            self.lib.im_server_destroy(self.handle)
+            self.handle = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -10,12 +10,12 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "_libdifuser_im.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["im_kernels.cu", "im_frontier.cu", "im_api.cu", "im_noalloc.cu"]
-HEADERS = [os.path.join(CSRC, h) for h in ("im_device.cuh", "im_launch.h")] + [
+SOURCES = ["im_kernels.cu", "im_frontier.cu", "im_api.cu", "im_noalloc.cu", "im_server.cu"]
+HEADERS = [os.path.join(CSRC, h) for h in ("im_device.cuh", "im_launch.h", "im_internal.h")] + [
     os.path.join(ROOT, "include", "difuser_im.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-         "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
+         "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "-Xcompiler", "-pthread"]
 
 
 def _stale() -> bool:
@@ -45,7 +45,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if p.returncode != 0:
             raise RuntimeError(f"nvcc failed: {' '.join(cmd)}\n{out.decode(errors='replace')}")
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [NVCC, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp, *objs]
+    cmd = [NVCC, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-Xcompiler", "-pthread", "-o", tmp,
+           *objs]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout.decode(errors='replace')}")

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/difuser_im.h"
+#include "im_internal.h"
 #include "im_launch.h"
 
 using namespace im;
@@ -28,6 +29,7 @@ struct im_ctx {
     uint64_t peak = 0;
     bool custom_alloc = false;
     im_allocator alloc{};
+    cudaMemPool_t pool = nullptr;  // stream-ordered pool of a server worker (else the device default)
     std::unordered_map<void*, size_t> sizes;
     std::string err;
     im_stats stats{};
@@ -82,9 +84,13 @@ im_status cuda_fail(im_ctx* c, cudaError_t e, const char* what) {
         if (s_ != IM_OK) return s_;      \
     } while (0)
 
-im_status dalloc(im_ctx* c, size_t bytes, DBuf& out) {
+size_t round_bytes(size_t bytes) {
     bytes = (bytes + 255) & ~(size_t)255;
-    if (bytes == 0) bytes = 256;
+    return bytes == 0 ? 256 : bytes;
+}
+
+im_status dalloc(im_ctx* c, size_t bytes, DBuf& out) {
+    bytes = round_bytes(bytes);
     if (c->budget && c->in_use + bytes > c->budget)
         return fail(c, IM_E_NOMEM, "HBM budget exceeded: %llu + %llu > %llu bytes",
                     (unsigned long long)c->in_use, (unsigned long long)bytes,
@@ -94,7 +100,8 @@ im_status dalloc(im_ctx* c, size_t bytes, DBuf& out) {
         p = c->alloc.alloc(bytes, c->stream, c->alloc.user);
         if (!p) return fail(c, IM_E_NOMEM, "allocator returned NULL for %zu bytes", bytes);
     } else {
-        cudaError_t e = cudaMallocAsync(&p, bytes, c->stream);
+        cudaError_t e = c->pool ? cudaMallocFromPoolAsync(&p, bytes, c->pool, c->stream)
+                                : cudaMallocAsync(&p, bytes, c->stream);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
             return fail(c, IM_E_NOMEM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
@@ -216,6 +223,7 @@ struct im_graph {
 
 struct im_sketch {
     im_graph* g = nullptr;
+    im_ctx* ctx = nullptr;  // execution context: allocator, stream, statistics
     int32_t J = 0;
     DBuf M, X, salt, tab, ql[3], qh[3], ctr, claim, chg[3], gen, seed_bits, count, part_S, part_u,
         ticket, stats, err, bar;
@@ -223,6 +231,10 @@ struct im_sketch {
     int32_t out_cap = 0;
     int32_t gen_counter = 0;
     int32_t picks = 0;
+    // the graph's device view with this sketch's model words (a per-call model
+    // override changes the copy, never the shared graph)
+    GraphDev dev{};
+    int kind = kUniform;
     // batches (several graphs in one union): graph of every vertex, visited
     // counter per graph, graphs whose rows a build covers
     const int32_t* gid = nullptr;
@@ -362,6 +374,17 @@ static void graph_release(im_graph* g) {
         dfree(c, *b);
 }
 
+// Model words of a device view (uniform, weighted-cascade, trivalency: no
+// per-edge data beyond what every graph holds).
+static void model_words(GraphDev& dev, int& kind, const im_model* mdl) {
+    kind = mdl->kind == kTargetModel ? kWC : mdl->kind;
+    dev.thr_uniform = prob_threshold_host(mdl->p);
+    dev.tri_seed = (uint32_t)(mdl->seed ^ (mdl->seed >> 32));
+    dev.tri_thr[0] = prob_threshold_host(0.1f);
+    dev.tri_thr[1] = prob_threshold_host(0.01f);
+    dev.tri_thr[2] = prob_threshold_host(0.001f);
+}
+
 // Sets the model part of the device view; allocates per-vertex / per-edge
 // thresholds as the model needs.  thr_out / thr_in of an explicit model are
 // filled by the caller (they need the reverse CSR).
@@ -369,12 +392,7 @@ static im_status set_model(im_graph* g, const im_model* mdl) {
     im_ctx* c = g->ctx;
     // a per-target-vertex model runs the weighted-cascade kernels (every
     // in-edge of v has v's threshold); its thresholds are set at load
-    g->kind = mdl->kind == kTargetModel ? kWC : mdl->kind;
-    g->dev.thr_uniform = prob_threshold_host(mdl->p);
-    g->dev.tri_seed = (uint32_t)(mdl->seed ^ (mdl->seed >> 32));
-    g->dev.tri_thr[0] = prob_threshold_host(0.1f);
-    g->dev.tri_thr[1] = prob_threshold_host(0.01f);
-    g->dev.tri_thr[2] = prob_threshold_host(0.001f);
+    model_words(g->dev, g->kind, mdl);
     if (mdl->kind == kExplicit && g->m > 0) {
         DBuf w;
         CKS(dalloc(c, (size_t)g->m * sizeof(float), w));
@@ -527,7 +545,7 @@ extern "C" im_status im_graph_info(const im_graph* g, int32_t* n, int64_t* m) {
 // sketches
 // ---------------------------------------------------------------------------
 static void sketch_release(im_sketch* sk) {
-    im_ctx* c = sk->g->ctx;
+    im_ctx* c = sk->ctx;
     for (DBuf* b : {&sk->M, &sk->X, &sk->salt, &sk->tab, &sk->ql[0], &sk->ql[1], &sk->ql[2],
                     &sk->qh[0], &sk->qh[1], &sk->qh[2], &sk->ctr, &sk->claim, &sk->chg[0],
                     &sk->chg[1], &sk->chg[2], &sk->gen, &sk->seed_bits, &sk->count, &sk->part_S,
@@ -536,18 +554,12 @@ static void sketch_release(im_sketch* sk) {
         dfree(c, *b);
 }
 
-static im_status sketch_alloc(im_graph* g, int32_t J, im_sketch** out) {
-    im_ctx* c = g->ctx;
-    if (!valid_J(J)) return fail(c, IM_E_INVAL, "J must be a power of two in [16, 1024], got %d", J);
-    im_sketch* sk = new im_sketch();
-    sk->g = g;
-    sk->J = J;
-    const int32_t n = g->n;
+// Device buffers of a sketch of J simulations over n vertices, with their
+// sizes; sketch_alloc allocates exactly this list and query_bytes sums it.
+using BufPlan = std::vector<std::pair<DBuf*, size_t>>;
+static void sketch_plan(im_sketch* sk, int32_t n, int32_t J, BufPlan& plan) {
     const int pg = pick_grid(n, J);
-    im_status s = IM_OK;
-    auto A = [&](DBuf& b, size_t bytes) {
-        if (s == IM_OK) s = dalloc(c, bytes, b);
-    };
+    auto A = [&](DBuf& b, size_t bytes) { plan.emplace_back(&b, bytes); };
     A(sk->M, (size_t)n * J);
     A(sk->X, (size_t)J * 4);
     A(sk->salt, (size_t)J * 4);
@@ -566,6 +578,22 @@ static im_status sketch_alloc(im_graph* g, int32_t J, im_sketch** out) {
     A(sk->stats, (size_t)kStCount * 8);
     A(sk->err, 4);
     A(sk->bar, 16);
+}
+
+// Output buffers for K seeds (ensure_out_cap): seed ids, S and estimates.
+static int32_t out_cap_for(int32_t K) { return K < 64 ? 64 : K; }
+
+static im_status sketch_alloc(im_ctx* c, im_graph* g, int32_t J, im_sketch** out) {
+    if (!valid_J(J)) return fail(c, IM_E_INVAL, "J must be a power of two in [16, 1024], got %d", J);
+    im_sketch* sk = new im_sketch();
+    sk->g = g;
+    sk->ctx = c;
+    sk->J = J;
+    BufPlan plan;
+    sketch_plan(sk, g->n, J, plan);
+    im_status s = IM_OK;
+    for (auto& [b, bytes] : plan)
+        if (s == IM_OK) s = dalloc(c, bytes, *b);
     if (s != IM_OK) {
         sketch_release(sk);
         delete sk;
@@ -590,8 +618,8 @@ static im_status sketch_alloc(im_graph* g, int32_t J, im_sketch** out) {
 
 static im_status ensure_out_cap(im_sketch* sk, int32_t K) {
     if (K <= sk->out_cap) return IM_OK;
-    im_ctx* c = sk->g->ctx;
-    const int32_t cap = K < 64 ? 64 : K;
+    im_ctx* c = sk->ctx;
+    const int32_t cap = out_cap_for(K);
     DBuf a, b, d;
     CKS(dalloc(c, (size_t)cap * 4, a));
     im_status s = dalloc(c, (size_t)cap * 8, b);
@@ -618,7 +646,7 @@ static LevelArgs level_args(im_sketch* sk) {
     a.count = sk->count.as<unsigned long long>();
     a.stats = sk->stats.as<unsigned long long>();
     a.err = sk->err.as<uint32_t>();
-    const im_tuning& t = sk->g->ctx->tuning;
+    const im_tuning& t = sk->ctx->tuning;
     // the heavy path reads 32 register bytes per lane: J >= 32 only
     a.heavy_indeg = sk->J >= 32 ? t.heavy_indeg : 0x7FFFFFFF;
     a.light_batches = t.light_batches > 0 ? t.light_batches : 4;
@@ -634,7 +662,7 @@ static LevelArgs level_args(im_sketch* sk) {
 
 // Reads the device error word; converts raised bits to a status.
 static im_status check_err(im_sketch* sk) {
-    im_ctx* c = sk->g->ctx;
+    im_ctx* c = sk->ctx;
     uint32_t err = 0;
     CK(c, cudaMemcpyAsync(&err, sk->err.p, 4, cudaMemcpyDeviceToHost, c->stream));
     CK(c, sync_collect(c));
@@ -647,7 +675,7 @@ static im_status check_err(im_sketch* sk) {
 // Start of a propagation or cover phase: level counters, work counters and
 // change masks back to zero.
 static im_status phase_begin(im_sketch* sk) {
-    im_ctx* c = sk->g->ctx;
+    im_ctx* c = sk->ctx;
     auto st = c->stream;
     CK(c, cudaMemsetAsync(sk->ctr.p, 0, sk->ctr.bytes, st));
     CK(c, cudaMemsetAsync(sk->claim.p, 0, sk->claim.bytes, st));
@@ -659,7 +687,7 @@ static im_status phase_begin(im_sketch* sk) {
 // All levels of a phase in one cooperative launch; one host synchronisation.
 static im_status run_phase_persistent(im_sketch* sk, int mode, bool all_first, int grid) {
     im_graph* g = sk->g;
-    im_ctx* c = g->ctx;
+    im_ctx* c = sk->ctx;
     auto st = c->stream;
     PhaseArgs p{};
     p.base = level_args(sk);
@@ -680,7 +708,7 @@ static im_status run_phase_persistent(im_sketch* sk, int mode, bool all_first, i
     p.levels_out = reinterpret_cast<int*>(bar + 3);
     p.limit_ns = 20ull * 1000 * 1000 * 1000;
     CK(c, timed(c, mode == kPush ? kTPush : kTCover,
-                [&] { return launch_phase(g->kind, mode, g->dev, p, grid, st); }));
+                [&] { return launch_phase(sk->kind, mode, sk->dev, p, grid, st); }));
     CK(c, cudaMemcpyAsync(c->pinned, bar, 16, cudaMemcpyDeviceToHost, st));
     CK(c, sync_collect(c));
     const unsigned int* hb = reinterpret_cast<const unsigned int*>(c->pinned);
@@ -698,7 +726,7 @@ static im_status run_phase_persistent(im_sketch* sk, int mode, bool all_first, i
 // queues emptied see empty queues and return at once.
 static im_status run_levels(im_sketch* sk, int mode, bool all_first) {
     im_graph* g = sk->g;
-    im_ctx* c = g->ctx;
+    im_ctx* c = sk->ctx;
     auto st = c->stream;
     if (c->tuning.persistent && !c->trace) {
         const int pgrid = phase_grid();
@@ -737,7 +765,7 @@ static im_status run_levels(im_sketch* sk, int mode, bool all_first) {
         a.claim = claim + t;
         a.gen_next = ++sk->gen_counter;
         CK(c, timed(c, mode == kPush ? kTPush : kTCover,
-                    [&] { return launch_level(g->kind, mode, g->dev, a, grid, st); }));
+                    [&] { return launch_level(sk->kind, mode, sk->dev, a, grid, st); }));
         ++t;
         if (t % check == 0) {
             CK(c, cudaMemcpyAsync(c->pinned, &ctr[t], 16, cudaMemcpyDeviceToHost, st));
@@ -768,7 +796,7 @@ static im_status run_levels(im_sketch* sk, int mode, bool all_first) {
 
 static im_status propagate(im_sketch* sk) {
     im_graph* g = sk->g;
-    im_ctx* c = g->ctx;
+    im_ctx* c = sk->ctx;
     CKS(phase_begin(sk));
     LevelArgs a = level_args(sk);
     ulonglong2* ctr = sk->ctr.as<ulonglong2>();
@@ -776,13 +804,13 @@ static im_status propagate(im_sketch* sk) {
     a.cl_out = &ctr[0].x;
     a.qh_out = sk->qh[0].as<QEntry>();
     a.ch_out = &ctr[0].y;
-    CK(c, timed(c, kTOther, [&] { return launch_init_queues(g->kind, g->dev, a, c->stream); }));
+    CK(c, timed(c, kTOther, [&] { return launch_init_queues(sk->kind, sk->dev, a, c->stream); }));
     return run_levels(sk, kPush, true);
 }
 
 // Fill (Alg. 1) of the non-visited registers, then Simulate to the fixpoint.
 static im_status build_registers(im_sketch* sk) {
-    im_ctx* c = sk->g->ctx;
+    im_ctx* c = sk->ctx;
     CK(c, timed(c, kTFill, [&] {
         return launch_fill(sk->M.as<uint8_t>(), sk->g->n, sk->J, sk->salt.as<uint32_t>(), c->stream);
     }));
@@ -798,7 +826,7 @@ static void stats_begin(im_ctx* c) {
 }
 
 static im_status stats_collect(im_sketch* sk) {
-    im_ctx* c = sk->g->ctx;
+    im_ctx* c = sk->ctx;
     unsigned long long h[kStCount];
     unsigned long long cnt = 0;
     CK(c, cudaMemcpyAsync(h, sk->stats.p, sizeof h, cudaMemcpyDeviceToHost, c->stream));
@@ -823,17 +851,18 @@ static im_status stats_collect(im_sketch* sk) {
     // register row (J B) per queued vertex, source id (4 B, + 4 B threshold for
     // explicit weights) per in-edge, one 16-byte target chunk read per chunk
     // with a live non-visited source register, one 4-byte word per CAS write
-    const uint64_t t = sk->g->kind == kExplicit ? 4 : 0;
+    const uint64_t t = sk->kind == kExplicit ? 4 : 0;
     s.alg_bytes_sweep = s.sweep_vertices * (16 + (uint64_t)sk->J) + s.sweep_edges * (4 + t) +
                         s.sweep_chunks * 16 + s.sweep_cas * 4;
     return IM_OK;
 }
 
-static im_status sketch_start(im_graph* g, int32_t J, uint64_t seed, im_sketch** out) {
-    im_ctx* c = g->ctx;
+static im_status sketch_start(im_ctx* c, im_graph* g, int32_t J, uint64_t seed, im_sketch** out) {
     CK(c, cudaSetDevice(c->device));
     im_sketch* sk = nullptr;
-    CKS(sketch_alloc(g, J, &sk));
+    CKS(sketch_alloc(c, g, J, &sk));
+    sk->dev = g->dev;
+    sk->kind = g->kind;
     cudaError_t e = timed(c, kTOther, [&] {
         return launch_sims(seed, J, sk->X.as<uint32_t>(), sk->salt.as<uint32_t>(),
                            sk->tab.as<uint16_t>(), c->stream);
@@ -853,7 +882,7 @@ extern "C" im_status im_sketch_build(im_graph* g, int32_t J, uint64_t seed, im_s
     stats_begin(c);
     const double t0 = now_ms();
     im_sketch* sk = nullptr;
-    CKS(sketch_start(g, J, seed, &sk));
+    CKS(sketch_start(c, g, J, seed, &sk));
     im_status s = build_registers(sk);
     if (s == IM_OK) s = stats_collect(sk);
     if (s != IM_OK) {
@@ -875,7 +904,7 @@ extern "C" void im_sketch_free(im_sketch* sk) {
 
 extern "C" im_status im_sketch_registers(const im_sketch* sk, uint8_t* host_out) {
     if (!sk || !host_out) return IM_E_INVAL;
-    im_ctx* c = sk->g->ctx;
+    im_ctx* c = sk->ctx;
     CK(c, cudaMemcpyAsync(host_out, sk->M.p, (size_t)sk->g->n * sk->J, cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     return IM_OK;
@@ -883,7 +912,7 @@ extern "C" im_status im_sketch_registers(const im_sketch* sk, uint8_t* host_out)
 
 extern "C" im_status im_sketch_set_registers(im_sketch* sk, const uint8_t* host_in) {
     if (!sk || !host_in) return IM_E_INVAL;
-    im_ctx* c = sk->g->ctx;
+    im_ctx* c = sk->ctx;
     const size_t bytes = (size_t)sk->g->n * sk->J;
     for (size_t i = 0; i < bytes; ++i)
         if (host_in[i] > 32 && host_in[i] != 0xFF)
@@ -897,7 +926,7 @@ extern "C" im_status im_sketch_set_registers(im_sketch* sk, const uint8_t* host_
 
 extern "C" im_status im_sketch_sims(const im_sketch* sk, uint32_t* X_out, uint32_t* salt_out) {
     if (!sk) return IM_E_INVAL;
-    im_ctx* c = sk->g->ctx;
+    im_ctx* c = sk->ctx;
     if (X_out) CK(c, cudaMemcpyAsync(X_out, sk->X.p, (size_t)sk->J * 4, cudaMemcpyDeviceToHost, c->stream));
     if (salt_out) CK(c, cudaMemcpyAsync(salt_out, sk->salt.p, (size_t)sk->J * 4, cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
@@ -906,7 +935,7 @@ extern "C" im_status im_sketch_sims(const im_sketch* sk, uint32_t* X_out, uint32
 
 extern "C" im_status im_sketch_sums(const im_sketch* sk, uint64_t* host_out) {
     if (!sk || !host_out) return IM_E_INVAL;
-    im_ctx* c = sk->g->ctx;
+    im_ctx* c = sk->ctx;
     DBuf S;
     CKS(dalloc(c, (size_t)sk->g->n * 8, S));
     cudaError_t e = launch_sums(sk->M.as<uint8_t>(), sk->g->n, sk->J, S.as<unsigned long long>(), c->stream);
@@ -942,7 +971,7 @@ static PickArgs pick_args(im_sketch* sk, int k) {
 
 // Pick (estimate + argmax) followed by the cover of the picked vertex.
 static im_status pick_and_cover(im_sketch* sk, int k) {
-    im_ctx* c = sk->g->ctx;
+    im_ctx* c = sk->ctx;
     CKS(phase_begin(sk));
     const PickArgs a = pick_args(sk, k);
     CK(c, timed(c, kTPick, [&] { return launch_pick(a, c->stream); }));
@@ -951,7 +980,7 @@ static im_status pick_and_cover(im_sketch* sk, int k) {
 
 extern "C" im_status im_sketch_pick(im_sketch* sk, int32_t* s_out, uint64_t* S_out, double* est_out) {
     if (!sk) return IM_E_INVAL;
-    im_ctx* c = sk->g->ctx;
+    im_ctx* c = sk->ctx;
     if (sk->picks >= sk->g->n) return fail(c, IM_E_RANGE, "every vertex is already picked");
     CKS(ensure_out_cap(sk, sk->picks + 1));
     PickArgs a = pick_args(sk, sk->picks);
@@ -974,7 +1003,7 @@ extern "C" im_status im_sketch_pick(im_sketch* sk, int32_t* s_out, uint64_t* S_o
 
 extern "C" im_status im_sketch_cover(im_sketch* sk, int32_t s, uint64_t* count_out) {
     if (!sk) return IM_E_INVAL;
-    im_ctx* c = sk->g->ctx;
+    im_ctx* c = sk->ctx;
     if (s < 0 || s >= sk->g->n) return fail(c, IM_E_RANGE, "vertex %d out of range", s);
     CKS(phase_begin(sk));
     CK(c, launch_cover_seed(sk->M.as<uint8_t>(), sk->J, s, sk->g->rp_out.as<int32_t>(),
@@ -998,31 +1027,25 @@ extern "C" im_status im_sketch_rebuild(im_sketch* sk) {
 // ---------------------------------------------------------------------------
 // Alg. 4
 // ---------------------------------------------------------------------------
-extern "C" im_status im_select_seeds(im_graph* g, int32_t K, int32_t J, const im_model* model,
-                                     uint64_t seed, double rebuild_eps, int32_t* seeds_out,
-                                     double* score_out, double* estimate_out, im_sketch** sketch_out) {
-    if (!g || !seeds_out) return IM_E_INVAL;
-    im_ctx* c = g->ctx;
+// Alg. 4 of one query, executed on context c (its allocator and stream); the
+// graph is only read.
+static im_status select_seeds_impl(im_ctx* c, im_graph* g, int32_t K, int32_t J, const im_model* model,
+                                   uint64_t seed, double rebuild_eps, int32_t* seeds_out,
+                                   double* score_out, double* estimate_out, im_sketch** sketch_out) {
+    if (!c || !g || !seeds_out) return IM_E_INVAL;
     if (K < 1 || K > g->n) return fail(c, IM_E_RANGE, "K must be in [1, n], got %d", K);
     if (!valid_J(J)) return fail(c, IM_E_INVAL, "J must be a power of two in [16, 1024], got %d", J);
-    // a per-call model override changes the graph's model words for this call only
-    struct ModelGuard {
-        im_graph* g;
-        GraphDev dev;
-        int kind;
-        ~ModelGuard() { g->dev = dev; g->kind = kind; }
-    } guard{g, g->dev, g->kind};
     if (model) {
         CKS(check_model(c, model, g->m));
         if (model->kind == kExplicit || model->kind == kTargetModel || g->load_kind == kExplicit ||
             g->load_kind == kTargetModel)
             return fail(c, IM_E_STATE, "explicit and per-target models are fixed at im_graph_load");
-        CKS(set_model(g, model));
     }
     stats_begin(c);
     const double t0 = now_ms();
     im_sketch* sk = nullptr;
-    CKS(sketch_start(g, J, seed, &sk));
+    CKS(sketch_start(c, g, J, seed, &sk));
+    if (model) model_words(sk->dev, sk->kind, model);  // this call's model, on the sketch's copy
     auto bail = [&](im_status s) {
         sketch_release(sk);
         delete sk;
@@ -1074,6 +1097,81 @@ extern "C" im_status im_select_seeds(im_graph* g, int32_t K, int32_t J, const im
     else bail(IM_OK);
     return IM_OK;
 }
+
+extern "C" im_status im_select_seeds(im_graph* g, int32_t K, int32_t J, const im_model* model,
+                                     uint64_t seed, double rebuild_eps, int32_t* seeds_out,
+                                     double* score_out, double* estimate_out, im_sketch** sketch_out) {
+    if (!g) return IM_E_INVAL;
+    return select_seeds_impl(g->ctx, g, K, J, model, seed, rebuild_eps, seeds_out, score_out,
+                             estimate_out, sketch_out);
+}
+
+// ---------------------------------------------------------------------------
+// internal entry points of the query server
+// ---------------------------------------------------------------------------
+namespace imi {
+
+im_status ctx_create_worker(int device, cudaStream_t stream, cudaMemPool_t pool, im_ctx** out) {
+    im_ctx* c = nullptr;
+    CKS(im_ctx_create(device, stream, 0, nullptr, &c));
+    c->pool = pool;
+    c->tuning.persistent = 0;
+    *out = c;
+    return IM_OK;
+}
+
+void ctx_set_budget(im_ctx* c, uint64_t bytes) { c->budget = bytes; }
+const char* ctx_error(const im_ctx* c) { return c->err.c_str(); }
+
+im_status select_seeds_on(im_ctx* c, im_graph* g, int32_t K, int32_t J, const im_model* model,
+                          uint64_t seed, double rebuild_eps, int32_t* seeds_out, double* score_out,
+                          double* estimate_out) {
+    return select_seeds_impl(c, g, K, J, model, seed, rebuild_eps, seeds_out, score_out,
+                             estimate_out, nullptr);
+}
+
+uint64_t query_bytes(const im_graph* g, int32_t J, int32_t K) {
+    im_sketch probe;
+    BufPlan plan;
+    sketch_plan(&probe, g->n, J, plan);
+    uint64_t total = 0;
+    for (auto& pb : plan) total += round_bytes(pb.second);
+    const size_t cap = (size_t)out_cap_for(K);
+    total += round_bytes(cap * 4) + 2 * round_bytes(cap * 8);
+    return total;
+}
+
+uint64_t graph_bytes(const im_graph* g) {
+    uint64_t total = 0;
+    for (const DBuf* b : {&g->rp_out, &g->col_out, &g->rp_in, &g->src_in, &g->h_in, &g->h_out,
+                          &g->thrw_out, &g->thr_v, &g->thr_out, &g->thr_in, &g->cls_split,
+                          &g->q_dense, &g->hkey})
+        total += b->bytes;
+    return total;
+}
+
+int32_t graph_n(const im_graph* g) { return g->n; }
+int graph_device(const im_graph* g) { return g->ctx->device; }
+
+im_status check_query_model(const im_graph* g, const im_model* model, char* msg, size_t cap) {
+    if (!model) return IM_OK;
+    if (model->kind == kExplicit || model->kind == kTargetModel || g->load_kind == kExplicit ||
+        g->load_kind == kTargetModel) {
+        snprintf(msg, cap, "explicit and per-target models are fixed at im_graph_load");
+        return IM_E_STATE;
+    }
+    if (model->kind < kUniform || model->kind > kTrivalency) {
+        snprintf(msg, cap, "unknown model kind %d", model->kind);
+        return IM_E_INVAL;
+    }
+    if (model->kind == kUniform && !(model->p >= 0.0f && model->p <= 1.0f)) {
+        snprintf(msg, cap, "uniform p must be in [0,1]");
+        return IM_E_INVAL;
+    }
+    return IM_OK;
+}
+
+}  // namespace imi
 
 // ---------------------------------------------------------------------------
 // Monte-Carlo spread with independent coins (Sec. 5.1 quality oracle)
@@ -1265,7 +1363,7 @@ extern "C" void im_batch_free(im_batch* b) {
 
 // Fill of the flagged graphs' rows, then propagation from their vertices.
 static im_status batch_build(im_sketch* sk) {
-    im_ctx* c = sk->g->ctx;
+    im_ctx* c = sk->ctx;
     CK(c, timed(c, kTFill, [&] {
         return launch_fill_flagged(sk->M.as<uint8_t>(), sk->g->n, sk->J, sk->salt.as<uint32_t>(),
                                    sk->gid, sk->gflag, sk->g->hkey.as<int32_t>(), c->stream);
@@ -1308,7 +1406,7 @@ extern "C" im_status im_batch_select_seeds(im_batch* b, const int32_t* J, const 
             te[g] = (int32_t)tiles.size();
         }
         im_sketch* sk = nullptr;
-        CKS(sketch_start(b->g, Jg, seed, &sk));
+        CKS(sketch_start(c, b->g, Jg, seed, &sk));
         DBuf tiles_d, tb_d, te_d, active_d, flag_d, gcount_d, pS, pU, oseed, oS, oest;
         std::vector<DBuf*> tmp = {&tiles_d, &tb_d, &te_d, &active_d, &flag_d, &gcount_d, &pS, &pU, &oseed, &oS, &oest};
         auto cleanup = [&]() {

@@ -200,3 +200,31 @@ def batched_workload(G: int = 512, seed: int = 2410):
         J.append(int(rng.choice([64, 128])))
         K.append(int(rng.integers(5, 51)))
     return graphs, p, J, K
+
+
+# Served form: 16 resident R-MAT graphs (edge factor 16), scales 14..22 spread
+# evenly with the lower scales repeated.
+SERVED_SCALES = (14, 15, 16, 17, 18, 19, 20, 21, 22, 14, 15, 16, 17, 18, 19, 20)
+
+
+def served_graphs(seed: int = 2410, scales=SERVED_SCALES) -> list:
+    return [rmat(s, 16, seed=seed + 17 * i) for i, s in enumerate(scales)]
+
+
+def served_queries(count: int, rate: float = 200.0, n_graphs: int = len(SERVED_SCALES),
+                   seed: int = 2410) -> list:
+    """Poisson arrivals (mean `rate` per second, first at t = 0) of queries:
+    graph uniform over the resident graphs, K in {10, 25, 50}, J in
+    {64, 256, 1024}, model uniform p = 0.01 or weighted cascade, rebuild
+    threshold 0.01, simulation seed drawn per query."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, count)
+    gaps[0] = 0.0
+    arrival = np.cumsum(gaps)
+    out = []
+    for i in range(count):
+        model = {"kind": "uniform", "p": 0.01} if rng.integers(2) == 0 else {"kind": "wc"}
+        out.append({"arrival_s": float(arrival[i]), "graph": int(rng.integers(n_graphs)),
+                    "K": int(rng.choice([10, 25, 50])), "J": int(rng.choice([64, 256, 1024])),
+                    "model": model, "seed": int(rng.integers(1 << 40)), "rebuild_eps": 0.01})
+    return out
