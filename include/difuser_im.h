@@ -124,7 +124,10 @@ typedef struct {
  * barriers between levels (per-level launches when tracing); dense_div: a
  * propagation level whose frontier exceeds (vertices with in-edges) /
  * dense_div walks every such vertex in vertex order (0 = never; the first
- * level of a build always does when dense_div > 0). */
+ * level of a build always does when dense_div > 0); lazy_pick: 1 = in
+ * im_select_seeds, picks after the first recompute S_u only for the vertices
+ * whose stored S_u (a lower bound: S_u never decreases during a selection)
+ * could still beat the best candidate, 0 = every pick reads every row. */
 typedef struct {
     int32_t heavy_indeg;
     int32_t light_batches;
@@ -132,6 +135,7 @@ typedef struct {
     int32_t check_every;
     int32_t persistent;
     int32_t dense_div;
+    int32_t lazy_pick;
 } im_tuning;
 
 /* One frontier launch of the last selection / build (tracing on). */

@@ -44,7 +44,7 @@ struct im_ctx {
     bool trace = false;
     std::vector<float> launch_ms;    // kernel time per launch sequence number (tracing)
     std::vector<im_trace_rec> recs;  // frontier launches of the last call
-    im_tuning tuning{64, 4, 0, 2, 1, 8};
+    im_tuning tuning{64, 4, 0, 2, 1, 8, 1};
 };
 
 namespace {
@@ -226,7 +226,9 @@ struct im_sketch {
     im_ctx* ctx = nullptr;  // execution context: allocator, stream, statistics
     int32_t J = 0;
     DBuf M, X, salt, tab, ql[3], qh[3], ctr, claim, chg[3], gen, seed_bits, count, part_S, part_u,
-        ticket, stats, err, bar;
+        ticket, stats, err, bar, lb, cand, part_S2, part_u2;
+    bool lazy = false;      // picks after the first refresh stored sums only (im_select_seeds)
+    bool lb_ready = false;  // lb holds the sums of the last full pick or later refreshes
     DBuf out_seed, out_S, out_est;
     int32_t out_cap = 0;
     int32_t gen_counter = 0;
@@ -296,12 +298,12 @@ extern "C" im_status im_ctx_set_timing(im_ctx* c, int enable) {
 extern "C" im_status im_ctx_set_tuning(im_ctx* c, const im_tuning* t) {
     if (!c) return IM_E_INVAL;
     if (!t) {
-        c->tuning = im_tuning{64, 4, 0, 2, 1, 8};
+        c->tuning = im_tuning{64, 4, 0, 2, 1, 8, 1};
         return IM_OK;
     }
     if (t->heavy_indeg < 0 || t->light_batches < 1 || t->light_batches > 4096 || t->grid_blocks < 0 ||
         t->check_every < 1 || t->check_every > 64 || t->persistent < 0 || t->persistent > 1 ||
-        t->dense_div < 0)
+        t->dense_div < 0 || t->lazy_pick < 0 || t->lazy_pick > 1)
         return fail(c, IM_E_INVAL, "tuning out of range");
     c->tuning = *t;
     return IM_OK;
@@ -544,21 +546,11 @@ extern "C" im_status im_graph_info(const im_graph* g, int32_t* n, int64_t* m) {
 // ---------------------------------------------------------------------------
 // sketches
 // ---------------------------------------------------------------------------
-static void sketch_release(im_sketch* sk) {
-    im_ctx* c = sk->ctx;
-    for (DBuf* b : {&sk->M, &sk->X, &sk->salt, &sk->tab, &sk->ql[0], &sk->ql[1], &sk->ql[2],
-                    &sk->qh[0], &sk->qh[1], &sk->qh[2], &sk->ctr, &sk->claim, &sk->chg[0],
-                    &sk->chg[1], &sk->chg[2], &sk->gen, &sk->seed_bits, &sk->count, &sk->part_S,
-                    &sk->part_u, &sk->ticket, &sk->stats, &sk->err, &sk->out_seed, &sk->out_S,
-                    &sk->out_est, &sk->bar})
-        dfree(c, *b);
-}
-
 // Device buffers of a sketch of J simulations over n vertices, with their
 // sizes; sketch_alloc allocates exactly this list and query_bytes sums it.
 using BufPlan = std::vector<std::pair<DBuf*, size_t>>;
 static void sketch_plan(im_sketch* sk, int32_t n, int32_t J, BufPlan& plan) {
-    const int pg = pick_grid(n, J);
+    const int pg = std::max(pick_grid(n, J), pick_lazy_grid(n));
     auto A = [&](DBuf& b, size_t bytes) { plan.emplace_back(&b, bytes); };
     A(sk->M, (size_t)n * J);
     A(sk->X, (size_t)J * 4);
@@ -578,6 +570,19 @@ static void sketch_plan(im_sketch* sk, int32_t n, int32_t J, BufPlan& plan) {
     A(sk->stats, (size_t)kStCount * 8);
     A(sk->err, 4);
     A(sk->bar, 16);
+    A(sk->lb, (size_t)n * 8);
+    A(sk->cand, 4);
+    A(sk->part_S2, (size_t)pg * 8);
+    A(sk->part_u2, (size_t)pg * 4);
+}
+
+// Frees every buffer of the plan and the output buffers (null ones are skipped).
+static void sketch_release(im_sketch* sk) {
+    im_ctx* c = sk->ctx;
+    BufPlan plan;
+    sketch_plan(sk, sk->g->n, sk->J, plan);
+    for (auto& pb : plan) dfree(c, *pb.first);
+    for (DBuf* b : {&sk->out_seed, &sk->out_S, &sk->out_est}) dfree(c, *b);
 }
 
 // Output buffers for K seeds (ensure_out_cap): seed ids, S and estimates.
@@ -969,12 +974,22 @@ static PickArgs pick_args(im_sketch* sk, int k) {
     return a;
 }
 
-// Pick (estimate + argmax) followed by the cover of the picked vertex.
+// Pick (estimate + argmax) followed by the cover of the picked vertex.  In
+// a lazy sketch the first pick stores every S_u and later picks refresh only
+// the stored sums that could beat the candidate.
 static im_status pick_and_cover(im_sketch* sk, int k) {
     im_ctx* c = sk->ctx;
     CKS(phase_begin(sk));
-    const PickArgs a = pick_args(sk, k);
-    CK(c, timed(c, kTPick, [&] { return launch_pick(a, c->stream); }));
+    PickArgs a = pick_args(sk, k);
+    if (sk->lazy) {
+        a.lb = sk->lb.as<unsigned long long>();
+        a.cand = sk->cand.as<int32_t>();
+        a.part_S2 = sk->part_S2.as<unsigned long long>();
+        a.part_u2 = sk->part_u2.as<int32_t>();
+    }
+    const bool lazy_now = sk->lazy && sk->lb_ready;
+    CK(c, timed(c, kTPick, [&] { return lazy_now ? launch_pick_lazy(a, c->stream) : launch_pick(a, c->stream); }));
+    if (sk->lazy) sk->lb_ready = true;
     return run_levels(sk, kCover, false);
 }
 
@@ -1046,6 +1061,7 @@ static im_status select_seeds_impl(im_ctx* c, im_graph* g, int32_t K, int32_t J,
     im_sketch* sk = nullptr;
     CKS(sketch_start(c, g, J, seed, &sk));
     if (model) model_words(sk->dev, sk->kind, model);  // this call's model, on the sketch's copy
+    sk->lazy = c->tuning.lazy_pick != 0;
     auto bail = [&](im_status s) {
         sketch_release(sk);
         delete sk;

@@ -245,10 +245,93 @@ __device__ void cover_seed_block(uint8_t* M, int J, int32_t s, const int32_t* rp
     }
 }
 
-__global__ void __launch_bounds__(kBlock) k_pick(PickArgs a) {
-    __shared__ unsigned long long sS[kWarpsPerBlock];
-    __shared__ int32_t sU[kWarpsPerBlock];
+// Least and second-least (S, u) pairs in lexicographic order.
+struct Top2 {
+    unsigned long long s1 = ~0ull, s2 = ~0ull;
+    int32_t u1 = 0x7FFFFFFF, u2 = 0x7FFFFFFF;
+    __device__ __forceinline__ void insert(unsigned long long s, int32_t u) {
+        if (s < s1 || (s == s1 && u < u1)) {
+            s2 = s1; u2 = u1; s1 = s; u1 = u;
+        } else if (s < s2 || (s == s2 && u < u2)) {
+            s2 = s; u2 = u;
+        }
+    }
+    __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            const unsigned long long a1 = __shfl_xor_sync(0xFFFFFFFFu, s1, off);
+            const unsigned long long a2 = __shfl_xor_sync(0xFFFFFFFFu, s2, off);
+            const int32_t b1 = __shfl_xor_sync(0xFFFFFFFFu, u1, off);
+            const int32_t b2 = __shfl_xor_sync(0xFFFFFFFFu, u2, off);
+            insert(a1, b1);
+            insert(a2, b2);
+        }
+    }
+};
+
+// Block + grid reduction of the per-thread Top2 (last block by ticket), then
+// the seed record: out_seed / out_S / out_est[k], the seed bit, the next
+// lazy candidate, and (mark) the seed row visited + queued for the cover.
+__device__ void pick_finish(const PickArgs& a, Top2 t) {
+    __shared__ unsigned long long sS1[kWarpsPerBlock], sS2[kWarpsPerBlock];
+    __shared__ int32_t sU1[kWarpsPerBlock], sU2[kWarpsPerBlock];
     __shared__ bool is_last;
+    __shared__ unsigned long long fS;
+    __shared__ int32_t fU;
+    const int lane = (int)lane_id();
+    const int wib = threadIdx.x >> 5;
+    t.warp_reduce();
+    if (lane == 0) { sS1[wib] = t.s1; sU1[wib] = t.u1; sS2[wib] = t.s2; sU2[wib] = t.u2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kWarpsPerBlock; ++w) { t.insert(sS1[w], sU1[w]); t.insert(sS2[w], sU2[w]); }
+        a.part_S[blockIdx.x] = t.s1;
+        a.part_u[blockIdx.x] = t.u1;
+        if (a.part_S2) { a.part_S2[blockIdx.x] = t.s2; a.part_u2[blockIdx.x] = t.u2; }
+        __threadfence();
+        const unsigned tk = atomicAdd(a.ticket, 1u);
+        is_last = (tk == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    // ---- last block: global top-2, seed record, cover seed ------------------
+    __threadfence();
+    Top2 g;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        g.insert(__ldcg(a.part_S + b), __ldcg(a.part_u + b));
+        if (a.part_S2) g.insert(__ldcg(a.part_S2 + b), __ldcg(a.part_u2 + b));
+    }
+    g.warp_reduce();
+    __syncthreads();  // the shared arrays are reused
+    if (lane == 0) { sS1[wib] = g.s1; sU1[wib] = g.u1; sS2[wib] = g.s2; sU2[wib] = g.u2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kWarpsPerBlock; ++w) { g.insert(sS1[w], sU1[w]); g.insert(sS2[w], sU2[w]); }
+        fS = g.s1;
+        fU = g.u1;
+        *a.ticket = 0u;
+        if (a.cand) *a.cand = g.s2 == ~0ull ? -1 : g.u2;
+        if (g.s1 == ~0ull) {
+            a.out_seed[a.k] = -1;
+            if (a.ctr_cover) *a.ctr_cover = 0ull;
+        } else {
+            a.out_seed[a.k] = g.u1;
+            a.out_S[a.k] = g.s1;
+            a.out_est[a.k] = ((double)a.J * 4294967296.0) / (0.77351 * (double)g.s1);
+            a.seed_bits[g.u1 >> 5] |= 1u << (g.u1 & 31);
+        }
+    }
+    __syncthreads();
+    if (fS == ~0ull || !a.mark) return;
+    cover_seed_block(a.M, a.J, fU, a.rp_out, a.q_cover, a.ctr_cover, a.chg0, a.count);
+}
+
+__device__ __forceinline__ bool is_picked(const uint32_t* seed_bits, int64_t v) {
+    return (__ldcg(seed_bits + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+// Full pick: S_u of every row (stored in lb when lazy picks follow).
+__global__ void __launch_bounds__(kBlock) k_pick(PickArgs a) {
     const int J = a.J;
     const int cpr = J >> 4;
     const int lpr = cpr < 32 ? cpr : 32;
@@ -258,70 +341,65 @@ __global__ void __launch_bounds__(kBlock) k_pick(PickArgs a) {
     const int seg = lane / lpr, seg_lane = lane % lpr;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned long long bestS = ~0ull;
-    int32_t bestU = 0x7FFFFFFF;
+    Top2 t;
     for (int64_t r0 = warp * rpw; r0 < a.n; r0 += nwarps * rpw) {
         const int64_t row = r0 + seg;
         const bool ok = row < a.n;
         const unsigned long long s = row_sum(a.M, J, ok ? (int32_t)row : 0, lpr, cpl, seg_lane);
         if (ok && seg_lane == 0) {
-            const bool picked = (__ldcg(a.seed_bits + (row >> 5)) >> (row & 31)) & 1u;
-            if (!picked) lex_min(bestS, bestU, s, (int32_t)row);
+            if (a.lb) a.lb[row] = s;
+            if (!is_picked(a.seed_bits, row)) t.insert(s, (int32_t)row);
         }
     }
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-        const unsigned long long oS = __shfl_xor_sync(0xFFFFFFFFu, bestS, off);
-        const int32_t ou = __shfl_xor_sync(0xFFFFFFFFu, bestU, off);
-        lex_min(bestS, bestU, oS, ou);
+    pick_finish(a, t);
+}
+
+// S of one row by a whole warp (every lane gets the sum).
+__device__ __forceinline__ unsigned long long warp_row_sum(const uint8_t* __restrict__ M, int J,
+                                                           int32_t row) {
+    const int cpr = J >> 4;
+    const uint4* p = reinterpret_cast<const uint4*>(M + (size_t)row * J);
+    unsigned long long s = 0;
+    for (int c = (int)lane_id(); c < cpr; c += 32) s += row_terms16(__ldcg(p + c));
+    return warp_sum(s);
+}
+
+// Lazy pick (CELF-style, exact): S_u only grows during a selection (covers
+// turn registers into visited = 2^32, rebuilds lower the ranks of what stays
+// unvisited), so lb[v] <= S_v.  With S_c fresh for the candidate c, every
+// unpicked v with (lb[v], v) < (S_c, c) is refreshed; then the least stored
+// pair is the least current pair, the same vertex a full pick chooses.
+__global__ void __launch_bounds__(kBlock) k_pick_lazy(PickArgs a) {
+    const int J = a.J;
+    const int lane = (int)lane_id();
+    const int32_t c = __ldcg(a.cand);
+    unsigned long long Sc = 0;
+    int32_t uc = -1;  // no candidate: nothing is refreshed
+    if (c >= 0) {
+        Sc = warp_row_sum(a.M, J, c);
+        uc = c;
     }
-    const int wib = threadIdx.x >> 5;
-    if (lane == 0) { sS[wib] = bestS; sU[wib] = bestU; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < kWarpsPerBlock; ++w) lex_min(bestS, bestU, sS[w], sU[w]);
-        a.part_S[blockIdx.x] = bestS;
-        a.part_u[blockIdx.x] = bestU;
-        __threadfence();
-        const unsigned t = atomicAdd(a.ticket, 1u);
-        is_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!is_last) return;
-    // ---- last block: global minimum, seed record, cover seed ----------------
-    __threadfence();
-    unsigned long long gS = ~0ull;
-    int32_t gU = 0x7FFFFFFF;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-        lex_min(gS, gU, __ldcg(a.part_S + b), __ldcg(a.part_u + b));
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-        const unsigned long long oS = __shfl_xor_sync(0xFFFFFFFFu, gS, off);
-        const int32_t ou = __shfl_xor_sync(0xFFFFFFFFu, gU, off);
-        lex_min(gS, gU, oS, ou);
-    }
-    __shared__ unsigned long long fS;
-    __shared__ int32_t fU;
-    if (lane == 0) { sS[wib] = gS; sU[wib] = gU; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < kWarpsPerBlock; ++w) lex_min(gS, gU, sS[w], sU[w]);
-        fS = gS;
-        fU = gU;
-        *a.ticket = 0u;
-        if (gS == ~0ull) {
-            a.out_seed[a.k] = -1;
-            if (a.ctr_cover) *a.ctr_cover = 0ull;
-        } else {
-            a.out_seed[a.k] = gU;
-            a.out_S[a.k] = gS;
-            a.out_est[a.k] = ((double)J * 4294967296.0) / (0.77351 * (double)gS);
-            a.seed_bits[gU >> 5] |= 1u << (gU & 31);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    Top2 t;
+    for (int64_t base = warp * 32; base < a.n; base += nwarps * 32) {
+        const int64_t v = base + lane;
+        const bool ok = v < a.n && !is_picked(a.seed_bits, v);
+        unsigned long long lv = ok ? __ldcg(a.lb + v) : ~0ull;
+        const bool stale = ok && (lv < Sc || (lv == Sc && (int32_t)v < uc));
+        unsigned int m = __ballot_sync(0xFFFFFFFFu, stale);
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            const unsigned long long s = warp_row_sum(a.M, J, (int32_t)(base + b));
+            if (lane == b) {
+                lv = s;
+                a.lb[v] = s;
+            }
         }
+        if (ok) t.insert(lv, (int32_t)v);
     }
-    __syncthreads();
-    if (fS == ~0ull || !a.mark) return;
-    cover_seed_block(a.M, J, fU, a.rp_out, a.q_cover, a.ctr_cover, a.chg0, a.count);
+    pick_finish(a, t);
 }
 
 int pick_grid(int32_t n, int J) {
@@ -337,6 +415,19 @@ int pick_grid(int32_t n, int J) {
 
 cudaError_t launch_pick(const PickArgs& a, cudaStream_t st) {
     k_pick<<<pick_grid(a.n, a.J), kBlock, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+int pick_lazy_grid(int32_t n) {
+    const int64_t per_block = (int64_t)kWarpsPerBlock * 32 * 4;
+    int64_t grid = (n + per_block - 1) / per_block;
+    if (grid > 152 * 8) grid = 152 * 8;
+    if (grid < 1) grid = 1;
+    return (int)grid;
+}
+
+cudaError_t launch_pick_lazy(const PickArgs& a, cudaStream_t st) {
+    k_pick_lazy<<<pick_lazy_grid(a.n), kBlock, 0, st>>>(a);
     return cudaGetLastError();
 }
 

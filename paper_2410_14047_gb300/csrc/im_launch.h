@@ -117,9 +117,18 @@ struct PickArgs {
     uint32_t* chg0;               // change mask of cover level 0 (n * J/32 words)
     unsigned long long* count;
     int mark;                     // 1: mark the seed's row visited and queue it for the cover
+    // lazy picks (S_u never decreases during a selection, so a stored S_u is
+    // a lower bound of the current one): lb[n] stored sums, cand = the vertex
+    // of least stored (S, u) besides the pick, part_S2 / part_u2 = per-block
+    // runner-up.  All null: plain full pick.
+    unsigned long long* lb;
+    int32_t* cand;
+    unsigned long long* part_S2;
+    int32_t* part_u2;
 };
 
 int pick_grid(int32_t n, int J);
+int pick_lazy_grid(int32_t n);
 
 cudaError_t launch_sims(uint64_t seed, int J, uint32_t* X, uint32_t* salt, uint16_t* tab,
                         cudaStream_t st);
@@ -156,6 +165,9 @@ struct BatchPickArgs {
 };
 cudaError_t launch_batch_pick(const BatchPickArgs& a, cudaStream_t st);
 cudaError_t launch_pick(const PickArgs& a, cudaStream_t st);
+// Lazy pick: refreshes S_v of every unpicked v whose stored (lb[v], v) is
+// below (S_cand, cand) with S_cand fresh, then takes the least stored pair.
+cudaError_t launch_pick_lazy(const PickArgs& a, cudaStream_t st);
 // Marks row s visited (adding the newly visited registers to *count) and
 // queues s as level 0 of a cover.
 cudaError_t launch_cover_seed(uint8_t* M, int J, int32_t s, const int32_t* rp_out, QEntry* q,

@@ -296,7 +296,8 @@ def test_errors(im, ctx):
                                     {"heavy_indeg": 32, "grid_blocks": 7, "check_every": 1,
                                      "persistent": 0},
                                     {"persistent": 0, "light_batches": 2},
-                                    {"dense_div": 0}, {"dense_div": 1000000, "heavy_indeg": 16}])
+                                    {"dense_div": 0}, {"dense_div": 1000000, "heavy_indeg": 16},
+                                    {"lazy_pick": 0}])
 @pytest.mark.parametrize("gname,mname,J", [("rmat12", "wc", 256), ("cl5k", "p01", 64),
                                            ("er2k", "wc", 1024), ("rmat12", "tri", 32)])
 def test_tuning_does_not_change_results(im, ctx, tuning, gname, mname, J):
@@ -312,3 +313,27 @@ def test_tuning_does_not_change_results(im, ctx, tuning, gname, mname, J):
     assert np.array_equal(r["sketch"].registers(), ref["M"])
     if tuning.get("heavy_indeg") == 0 and mname in ("wc", "p01") and J >= 32:
         assert im.im_last_stats(c2)["sweep_vertices"] > 0
+
+
+# --- lazy picks: stored sums are lower bounds, the pick stays exact -------------------------
+
+@pytest.mark.parametrize("gname,mname,J,K,eps", [("isolated", "p30", 64, 40, 0.01),
+                                                 ("er2k", "wc", 64, 300, 0.01),
+                                                 ("er2k", "p01", 128, 200, -1.0),
+                                                 ("rmat12", "tri", 32, 120, 0.2)])
+def test_lazy_pick_equals_full_pick(im, gname, mname, J, K, eps):
+    g = GRAPHS[gname]
+    model = MODELS[mname]
+    out = []
+    for lazy in (1, 0):
+        c2 = im.im_ctx_create(0)
+        im.im_ctx_set_tuning(c2, {"lazy_pick": lazy})
+        G = im.im_graph_load(c2, g.rowptr, g.col, model)
+        before = im.im_ctx_bytes_in_use(c2)
+        out.append(im.im_select_seeds(G, K, J, seed=8, rebuild_eps=eps))
+        assert im.im_ctx_bytes_in_use(c2) == before  # the selection frees what it allocated
+    assert out[0]["seeds"].tolist() == out[1]["seeds"].tolist()
+    assert np.array_equal(out[0]["score"], out[1]["score"])
+    assert np.array_equal(out[0]["est"], out[1]["est"])
+    ref = O.select_seeds(g, O.thresholds(g, model), J, K, 8, eps, "reverse")
+    assert out[0]["seeds"].tolist() == ref["seeds"].tolist()
