@@ -491,7 +491,9 @@ def run_gpu(args):
             if agg["ms_propagate"] else None,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": tr,
-                         "kernel": "k_frontier<kWC,kPush> (propagation sweep)",
+                         "kernel": "k_phase<%s,kPush> (persistent propagation phase, one launch per build)"
+                                   % {"wc": "kWC", "uniform": "kUniform", "trivalency": "kTrivalency",
+                                      "explicit": "kExplicit"}[wl.model["kind"]],
                          "alg_bytes_per_launch": per_launch_bytes,
                          "avg_launch_ms": agg["ms_propagate"] / max(agg["sweep_launches"], 1),
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
