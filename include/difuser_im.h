@@ -106,11 +106,15 @@ typedef struct {
     uint64_t cover_edges;     /* out-edges examined by cover levels */
     uint64_t cover_chunks;    /* 16-simulation chunks examined by cover levels */
     uint64_t visited;         /* registers visited at the end (Count(M,-1)) */
-    uint64_t alg_bytes_sweep; /* algorithmic bytes of all sweeps (see the design notes) */
+    uint64_t alg_bytes_sweep; /* bytes the sweeps must move: per queued vertex 16 + J, per
+                                 examined in-edge 4 (8 when J = 1024), per in-edge live in a
+                                 changed chunk 8 (+4 explicit weights), per live chunk 32,
+                                 per CAS 4 */
     uint64_t sweep_heavy;     /* hub vertices pushed by per-simulation hash search */
     uint64_t sweep_heavy_sims;/* (hub, changed simulation) searches */
     uint64_t sweep_batches;   /* 32-edge batches resolved by propagation levels */
     uint64_t sweep_dealt;     /* 16-simulation chunk items dealt (before the live test) */
+    uint64_t sweep_edges_live;/* examined in-edges live in a chunk where the source changed */
 } im_stats;
 
 /* Schedule knobs of the frontier kernels (chosen by the autotuner; results

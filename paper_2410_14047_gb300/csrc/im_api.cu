@@ -226,8 +226,9 @@ struct im_sketch {
     im_ctx* ctx = nullptr;  // execution context: allocator, stream, statistics
     int32_t J = 0;
     DBuf M, X, salt, tab, ql[3], qh[3], ctr, claim, chg[3], gen, seed_bits, count, part_S, part_u,
-        ticket, stats, err, bar, lb, cand, part_S2, part_u2;
+        ticket, stats, err, bar, lb, cand, part_S2, part_u2, lcm_in_lo, lcm_in_hi, lcm_out_lo, lcm_out_hi;
     bool lazy = false;      // picks after the first refresh stored sums only (im_select_seeds)
+    bool chg_dirty = true;  // change masks may hold bits (new sketch, or a phase that failed)
     bool lb_ready = false;  // lb holds the sums of the last full pick or later refreshes
     DBuf out_seed, out_S, out_est;
     int32_t out_cap = 0;
@@ -549,7 +550,7 @@ extern "C" im_status im_graph_info(const im_graph* g, int32_t* n, int64_t* m) {
 // Device buffers of a sketch of J simulations over n vertices, with their
 // sizes; sketch_alloc allocates exactly this list and query_bytes sums it.
 using BufPlan = std::vector<std::pair<DBuf*, size_t>>;
-static void sketch_plan(im_sketch* sk, int32_t n, int32_t J, BufPlan& plan) {
+static void sketch_plan(im_sketch* sk, int32_t n, int64_t m_edges, int32_t J, BufPlan& plan) {
     const int pg = std::max(pick_grid(n, J), pick_lazy_grid(n));
     auto A = [&](DBuf& b, size_t bytes) { plan.emplace_back(&b, bytes); };
     A(sk->M, (size_t)n * J);
@@ -574,13 +575,21 @@ static void sketch_plan(im_sketch* sk, int32_t n, int32_t J, BufPlan& plan) {
     A(sk->cand, 4);
     A(sk->part_S2, (size_t)pg * 8);
     A(sk->part_u2, (size_t)pg * 4);
+    // live chunk masks of every in-edge and out-edge (chunks 32..63: J = 1024)
+    const size_t m = (size_t)m_edges;
+    A(sk->lcm_in_lo, m * 4);
+    A(sk->lcm_out_lo, m * 4);
+    if (J > 512) {
+        A(sk->lcm_in_hi, m * 4);
+        A(sk->lcm_out_hi, m * 4);
+    }
 }
 
 // Frees every buffer of the plan and the output buffers (null ones are skipped).
 static void sketch_release(im_sketch* sk) {
     im_ctx* c = sk->ctx;
     BufPlan plan;
-    sketch_plan(sk, sk->g->n, sk->J, plan);
+    sketch_plan(sk, sk->g->n, sk->g->m, sk->J, plan);
     for (auto& pb : plan) dfree(c, *pb.first);
     for (DBuf* b : {&sk->out_seed, &sk->out_S, &sk->out_est}) dfree(c, *b);
 }
@@ -595,7 +604,7 @@ static im_status sketch_alloc(im_ctx* c, im_graph* g, int32_t J, im_sketch** out
     sk->ctx = c;
     sk->J = J;
     BufPlan plan;
-    sketch_plan(sk, g->n, J, plan);
+    sketch_plan(sk, g->n, g->m, J, plan);
     im_status s = IM_OK;
     for (auto& [b, bytes] : plan)
         if (s == IM_OK) s = dalloc(c, bytes, *b);
@@ -665,6 +674,13 @@ static LevelArgs level_args(im_sketch* sk) {
     return a;
 }
 
+// Live chunk masks of the phase's edge orientation.
+static void set_lcm(LevelArgs& a, const im_sketch* sk, int mode) {
+    const bool in = mode == kPush;
+    a.lcm_lo = (in ? sk->lcm_in_lo : sk->lcm_out_lo).as<uint32_t>();
+    a.lcm_hi = sk->J > 512 ? (in ? sk->lcm_in_hi : sk->lcm_out_hi).as<uint32_t>() : nullptr;
+}
+
 // Reads the device error word; converts raised bits to a status.
 static im_status check_err(im_sketch* sk) {
     im_ctx* c = sk->ctx;
@@ -677,14 +693,19 @@ static im_status check_err(im_sketch* sk) {
     return IM_OK;
 }
 
-// Start of a propagation or cover phase: level counters, work counters and
-// change masks back to zero.
+// Start of a propagation or cover phase: level counters and work counters
+// back to zero.  A phase that completes leaves its change masks zero (the
+// last level's bits are cleared by the phase itself); after a new sketch or a
+// failed phase they are cleared here.
 static im_status phase_begin(im_sketch* sk) {
     im_ctx* c = sk->ctx;
     auto st = c->stream;
     CK(c, cudaMemsetAsync(sk->ctr.p, 0, sk->ctr.bytes, st));
     CK(c, cudaMemsetAsync(sk->claim.p, 0, sk->claim.bytes, st));
-    for (int i = 0; i < 3; ++i) CK(c, cudaMemsetAsync(sk->chg[i].p, 0, sk->chg[i].bytes, st));
+    if (sk->chg_dirty) {
+        for (int i = 0; i < 3; ++i) CK(c, cudaMemsetAsync(sk->chg[i].p, 0, sk->chg[i].bytes, st));
+        sk->chg_dirty = false;
+    }
     CK(c, cudaMemsetAsync(sk->bar.p, 0, sk->bar.bytes, st));
     return IM_OK;
 }
@@ -696,6 +717,7 @@ static im_status run_phase_persistent(im_sketch* sk, int mode, bool all_first, i
     auto st = c->stream;
     PhaseArgs p{};
     p.base = level_args(sk);
+    set_lcm(p.base, sk, mode);
     for (int i = 0; i < 3; ++i) {
         p.ql[i] = sk->ql[i].as<QEntry>();
         p.qh[i] = sk->qh[i].as<QEntry>();
@@ -719,9 +741,12 @@ static im_status run_phase_persistent(im_sketch* sk, int mode, bool all_first, i
     const unsigned int* hb = reinterpret_cast<const unsigned int*>(c->pinned);
     const int levels = (int)hb[3];
     sk->gen_counter += levels + 1;
+    sk->chg_dirty = true;
     if (levels >= p.max_levels)
         return fail(c, IM_E_TIMEOUT, "frontier did not empty within %d levels", p.max_levels);
-    return check_err(sk);
+    CKS(check_err(sk));
+    sk->chg_dirty = false;
+    return IM_OK;
 }
 
 // Runs frontier levels until both queues are empty.  Level t reads queue
@@ -740,6 +765,7 @@ static im_status run_levels(im_sketch* sk, int mode, bool all_first) {
     ulonglong2* ctr = sk->ctr.as<ulonglong2>();
     unsigned int* claim = sk->claim.as<unsigned int>();
     LevelArgs a = level_args(sk);
+    set_lcm(a, sk, mode);
     const int grid = c->tuning.grid_blocks > 0 ? c->tuning.grid_blocks : level_grid();
     int check = c->tuning.check_every > 0 ? c->tuning.check_every : 2;
     int64_t t = 0;
@@ -776,10 +802,33 @@ static im_status run_levels(im_sketch* sk, int mode, bool all_first) {
             CK(c, cudaMemcpyAsync(c->pinned, &ctr[t], 16, cudaMemcpyDeviceToHost, st));
             CK(c, sync_collect(c));
             if ((c->pinned[0] >> kCountShift) == 0 && (c->pinned[1] >> kCountShift) == 0) break;
-            if (t + 16 >= kMaxLevels)
+            if (t + 16 >= kMaxLevels) {
+                sk->chg_dirty = true;
                 return fail(c, IM_E_TIMEOUT, "frontier did not empty within %d levels", kMaxLevels);
+            }
             if (check < 8) check *= 2;
         }
+    }
+    {
+        // one more level on the empty queue t: it only clears the change bits
+        // of queue t - 1, so the phase leaves every change mask zero
+        const int bi = (int)(t % 3), bo = (int)((t + 1) % 3), bp = (int)((t + 2) % 3);
+        a.ql_in = sk->ql[bi].as<QEntry>();
+        a.cl_in = &ctr[t].x;
+        a.qh_in = sk->qh[bi].as<QEntry>();
+        a.ch_in = mode == kPush ? &ctr[t].y : nullptr;
+        a.ql_prev = sk->ql[bp].as<QEntry>();
+        a.cl_prev = &ctr[t - 1].x;
+        a.qh_prev = sk->qh[bp].as<QEntry>();
+        a.ch_prev = mode == kPush ? &ctr[t - 1].y : nullptr;
+        a.chg_prev = sk->chg[bp].as<uint32_t>();
+        a.chg_cur = sk->chg[bi].as<uint32_t>();
+        a.chg_next = sk->chg[bo].as<uint32_t>();
+        a.all_changed = 0;
+        a.claim = claim + t;
+        a.gen_next = ++sk->gen_counter;
+        CK(c, timed(c, mode == kPush ? kTPush : kTCover,
+                    [&] { return launch_level(sk->kind, mode, sk->dev, a, grid, st); }));
     }
     if (c->trace) {
         std::vector<ulonglong2> h((size_t)t);
@@ -796,7 +845,10 @@ static im_status run_levels(im_sketch* sk, int mode, bool all_first) {
             c->recs.push_back(r);
         }
     }
-    return check_err(sk);
+    sk->chg_dirty = true;
+    CKS(check_err(sk));
+    sk->chg_dirty = false;
+    return IM_OK;
 }
 
 static im_status propagate(im_sketch* sk) {
@@ -852,30 +904,48 @@ static im_status stats_collect(im_sketch* sk) {
     s.sweep_heavy_sims = h[kStSweepHeavySims];
     s.sweep_batches = h[kStSweepBatches];
     s.sweep_dealt = h[kStSweepDealt];
+    s.sweep_edges_live = h[kStSweepLiveEdges];
     // algorithmic bytes of the sweeps: queue entry (16 B) + the queued vertex's
-    // register row (J B) per queued vertex, source id (4 B, + 4 B threshold for
-    // explicit weights) per in-edge, one 16-byte target chunk read per chunk
-    // with a live non-visited source register, one 4-byte word per CAS write
+    // register row (J B) per queued vertex; live chunk mask (4 B, 8 B when
+    // J = 1024) per in-edge; source id + edge hash (8 B, + 4 B threshold for
+    // explicit weights) per in-edge live in a changed chunk; source + target
+    // 16-byte pieces per chunk with a live non-visited source register; one
+    // 4-byte word per CAS write
     const uint64_t t = sk->kind == kExplicit ? 4 : 0;
-    s.alg_bytes_sweep = s.sweep_vertices * (16 + (uint64_t)sk->J) + s.sweep_edges * (4 + t) +
-                        s.sweep_chunks * 16 + s.sweep_cas * 4;
+    const uint64_t lw = sk->J > 512 ? 8 : 4;
+    s.alg_bytes_sweep = s.sweep_vertices * (16 + (uint64_t)sk->J) + s.sweep_edges * lw +
+                        s.sweep_edges_live * (8 + t) + s.sweep_chunks * 32 + s.sweep_cas * 4;
     return IM_OK;
 }
 
-static im_status sketch_start(im_ctx* c, im_graph* g, int32_t J, uint64_t seed, im_sketch** out) {
+// New sketch: buffers, the J simulations, the model words (the graph's, or
+// `model` for this call) and the live chunk masks of every edge.
+static im_status sketch_start(im_ctx* c, im_graph* g, int32_t J, uint64_t seed, const im_model* model,
+                              im_sketch** out) {
     CK(c, cudaSetDevice(c->device));
     im_sketch* sk = nullptr;
     CKS(sketch_alloc(c, g, J, &sk));
     sk->dev = g->dev;
     sk->kind = g->kind;
+    if (model) model_words(sk->dev, sk->kind, model);  // this call's model, on the sketch's copy
     cudaError_t e = timed(c, kTOther, [&] {
         return launch_sims(seed, J, sk->X.as<uint32_t>(), sk->salt.as<uint32_t>(),
                            sk->tab.as<uint16_t>(), c->stream);
     });
+    for (int mode : {kPush, kCover}) {
+        if (e != cudaSuccess) break;
+        const bool in = mode == kPush;
+        e = timed(c, kTOther, [&] {
+            return launch_live_chunks(sk->kind, mode, sk->dev, sk->X.as<uint32_t>(), sk->tab.as<uint16_t>(), J,
+                                      (in ? sk->lcm_in_lo : sk->lcm_out_lo).as<uint32_t>(),
+                                      J > 512 ? (in ? sk->lcm_in_hi : sk->lcm_out_hi).as<uint32_t>() : nullptr,
+                                      c->stream);
+        });
+    }
     if (e != cudaSuccess) {
         sketch_release(sk);
         delete sk;
-        return cuda_fail(c, e, "launch_sims");
+        return cuda_fail(c, e, "sketch setup");
     }
     *out = sk;
     return IM_OK;
@@ -887,7 +957,7 @@ extern "C" im_status im_sketch_build(im_graph* g, int32_t J, uint64_t seed, im_s
     stats_begin(c);
     const double t0 = now_ms();
     im_sketch* sk = nullptr;
-    CKS(sketch_start(c, g, J, seed, &sk));
+    CKS(sketch_start(c, g, J, seed, nullptr, &sk));
     im_status s = build_registers(sk);
     if (s == IM_OK) s = stats_collect(sk);
     if (s != IM_OK) {
@@ -1059,8 +1129,7 @@ static im_status select_seeds_impl(im_ctx* c, im_graph* g, int32_t K, int32_t J,
     stats_begin(c);
     const double t0 = now_ms();
     im_sketch* sk = nullptr;
-    CKS(sketch_start(c, g, J, seed, &sk));
-    if (model) model_words(sk->dev, sk->kind, model);  // this call's model, on the sketch's copy
+    CKS(sketch_start(c, g, J, seed, model, &sk));
     sk->lazy = c->tuning.lazy_pick != 0;
     auto bail = [&](im_status s) {
         sketch_release(sk);
@@ -1149,7 +1218,7 @@ im_status select_seeds_on(im_ctx* c, im_graph* g, int32_t K, int32_t J, const im
 uint64_t query_bytes(const im_graph* g, int32_t J, int32_t K) {
     im_sketch probe;
     BufPlan plan;
-    sketch_plan(&probe, g->n, J, plan);
+    sketch_plan(&probe, g->n, g->m, J, plan);
     uint64_t total = 0;
     for (auto& pb : plan) total += round_bytes(pb.second);
     const size_t cap = (size_t)out_cap_for(K);
@@ -1422,7 +1491,7 @@ extern "C" im_status im_batch_select_seeds(im_batch* b, const int32_t* J, const 
             te[g] = (int32_t)tiles.size();
         }
         im_sketch* sk = nullptr;
-        CKS(sketch_start(c, b->g, Jg, seed, &sk));
+        CKS(sketch_start(c, b->g, Jg, seed, nullptr, &sk));
         DBuf tiles_d, tb_d, te_d, active_d, flag_d, gcount_d, pS, pU, oseed, oS, oest;
         std::vector<DBuf*> tmp = {&tiles_d, &tb_d, &te_d, &active_d, &flag_d, &gcount_d, &pS, &pU, &oseed, &oS, &oest};
         auto cleanup = [&]() {

@@ -155,6 +155,37 @@ __device__ __forceinline__ uint32_t merge_chunk(uint8_t* trow, const uint32_t ca
     return bits;
 }
 
+// Two bits per change word: bit 0 = a simulation of its low 16 changed, bit 1
+// = of its high 16 (one bit per 16-simulation chunk).
+__device__ __forceinline__ uint32_t halves_nonzero(uint32_t w) {
+    return ((w & 0xFFFFu) != 0u ? 1u : 0u) | ((w >> 16) != 0u ? 2u : 0u);
+}
+
+// Chunks of vertex v with a changed simulation: bits 0..31 in lo, 32..63 in hi.
+__device__ __forceinline__ void chunk_change_mask(const uint32_t* __restrict__ chg, int32_t v, int words,
+                                                  uint32_t& lo, uint32_t& hi) {
+    lo = 0u;
+    hi = 0u;
+    const uint32_t* row = chg + (size_t)v * words;
+    if (words >= 4) {
+        for (int q = 0; q < (words >> 2); ++q) {
+            const uint4 w4 = __ldcg(reinterpret_cast<const uint4*>(row) + q);
+            const uint32_t b = halves_nonzero(w4.x) | (halves_nonzero(w4.y) << 2) | (halves_nonzero(w4.z) << 4) |
+                               (halves_nonzero(w4.w) << 6);
+            if (q < 4) lo |= b << (8 * q);
+            else hi |= b << (8 * (q - 4));
+        }
+    } else {
+        for (int w = 0; w < words; ++w) lo |= halves_nonzero(__ldcg(row + w)) << (2 * w);
+    }
+}
+
+// Position of the r-th (0-based) set bit of the 64-bit mask (lo, hi).
+__device__ __forceinline__ int nth_chunk(uint32_t lo, uint32_t hi, int r) {
+    const int cl = __popc(lo);
+    return r < cl ? (int)__fns(lo, 0u, r + 1) : 32 + (int)__fns(hi, 0u, r - cl + 1);
+}
+
 // ---------------------------------------------------------------------------
 // Light units: a slice of 32-edge batches of the flat edge space.
 // ---------------------------------------------------------------------------
@@ -164,7 +195,8 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                                             const uint16_t* sTab, int64_t b0, int64_t b1, int32_t nl,
                                             int64_t El, unsigned long long& st_chunks,
                                             unsigned long long& st_cas, unsigned long long& st_new,
-                                            unsigned long long& st_batches, unsigned long long& st_dealt) {
+                                            unsigned long long& st_batches, unsigned long long& st_dealt,
+                                            unsigned long long& st_live) {
     const int lane = (int)lane_id();
     const int J = a.J, words = a.words;
     const int64_t fend = min(El, b1 << 5);
@@ -193,35 +225,36 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
         }
         int4 rawn = make_int4(0, 0, 0x7FFFFFFF, 0);
         if (f0 + 32 < fend && qn + lane < nl) rawn = __ldcg(reinterpret_cast<const int4*>(qlin) + qn + lane);
+        // chunks with a changed simulation of each queue entry this batch uses
+        uint32_t cm_lo = 0xFFFFFFFFu, cm_hi = 0xFFFFFFFFu;
+        if (!a.all_changed && wvalid && rel <= 31 && lane >= c0 - 1)
+            chunk_change_mask(a.chg_cur, raw.x, words, cm_lo, cm_hi);
+        const uint32_t qcm_lo = __shfl_sync(0xFFFFFFFFu, cm_lo, myw);
+        const uint32_t qcm_hi = __shfl_sync(0xFFFFFFFFu, cm_hi, myw);
         const int64_t f = f0 + lane;
         int32_t o = 0;
         uint32_t h = 0, thr = 0;
-        int clo = 0, nch = 0;
-        if (f < fend) {
+        uint32_t m_lo = 0u, m_hi = 0u;
+        int nch = 0;
+        if (f < fend && (qcm_lo | qcm_hi)) {
+            // chunks in which this edge is live and its source changed
             const int64_t e = (int64_t)qrp + (f - qoff);
-            if constexpr (MODE == kPush) {
-                o = __ldg(g.src_in + e);
-                h = __ldg(g.h_in + e);
-                thr = edge_threshold<KIND, true>(g, (uint32_t)o, (uint32_t)qv, e, qaux);
-            } else {
-                o = __ldg(g.col_out + e);
-                h = __ldg(g.h_out + e);
-                thr = edge_threshold<KIND, false>(g, (uint32_t)qv, (uint32_t)o, e, 0u);
-            }
-            int lo, hi;
-            candidate_range(h, thr, J, sX, sTab, lo, hi);
-            if (hi > lo) {
-                clo = lo >> 4;
-                nch = ((hi + 15) >> 4) - clo;
-                if (!a.all_changed) {
-                    // no chunk item unless a candidate simulation of qv changed
-                    uint32_t any = 0u;
-                    const uint32_t* cw = a.chg_cur + (size_t)qv * words;
-                    for (int w = lo >> 5; w <= (hi - 1) >> 5 && !any; ++w) any |= __ldcg(cw + w);
-                    if (!any) nch = 0;
+            m_lo = __ldg(a.lcm_lo + e) & qcm_lo;
+            if (a.lcm_hi) m_hi = __ldg(a.lcm_hi + e) & qcm_hi;
+            nch = __popc(m_lo) + __popc(m_hi);
+            if (nch) {
+                if constexpr (MODE == kPush) {
+                    o = __ldg(g.src_in + e);
+                    h = __ldg(g.h_in + e);
+                    thr = edge_threshold<KIND, true>(g, (uint32_t)o, (uint32_t)qv, e, qaux);
+                } else {
+                    o = __ldg(g.col_out + e);
+                    h = __ldg(g.h_out + e);
+                    thr = edge_threshold<KIND, false>(g, (uint32_t)qv, (uint32_t)o, e, 0u);
                 }
             }
         }
+        if (nch) ++st_live;
         int incl = nch;
 #pragma unroll
         for (int s = 1; s < 32; s <<= 1) {
@@ -241,7 +274,8 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
             }
             if (i > 31) i = 31;
             const int ex_i = __shfl_sync(0xFFFFFFFFu, excl, i);
-            const int cl_i = __shfl_sync(0xFFFFFFFFu, clo, i);
+            const uint32_t ml_i = __shfl_sync(0xFFFFFFFFu, m_lo, i);
+            const uint32_t mh_i = __shfl_sync(0xFFFFFFFFu, m_hi, i);
             const int32_t o_i = __shfl_sync(0xFFFFFFFFu, o, i);
             const int32_t q_i = __shfl_sync(0xFFFFFFFFu, qv, i);
             const uint32_t h_i = __shfl_sync(0xFFFFFFFFu, h, i);
@@ -249,7 +283,7 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
             uint32_t nbits = 0u;
             int chunk = 0;
             if (k < total) {
-                chunk = cl_i + (k - ex_i);
+                chunk = nth_chunk(ml_i, mh_i, k - ex_i);
                 uint32_t chb = 0xFFFFu;
                 if (!a.all_changed)
                     chb = (__ldcg(a.chg_cur + (size_t)q_i * words + (chunk >> 1)) >> ((chunk & 1) * 16)) & 0xFFFFu;
@@ -456,7 +490,7 @@ __device__ __forceinline__ void heavy_vertex(const GraphDev& g, const LevelArgs&
 }
 
 struct LevelStats {
-    unsigned long long chunks = 0, cas = 0, fresh = 0, hsims = 0, batches = 0, dealt = 0;
+    unsigned long long chunks = 0, cas = 0, fresh = 0, hsims = 0, batches = 0, dealt = 0, live = 0;
 };
 
 // Clears the change bits read by the level before the previous one.
@@ -524,7 +558,7 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
             const int64_t b0 = lu * lb;
             const int64_t b1 = min(nbl, b0 + lb);
             light_slice<KIND, MODE>(g, a, ql, sX, sTab, b0, b1, nl, El, ls.chunks, ls.cas, ls.fresh,
-                                    ls.batches, ls.dealt);
+                                    ls.batches, ls.dealt, ls.live);
         }
     }
 }
@@ -537,8 +571,10 @@ __device__ __forceinline__ void flush_stats(const LevelArgs& a, LevelStats& ls) 
     ls.hsims = wsum(ls.hsims);
     ls.batches = wsum(ls.batches);
     ls.dealt = wsum(ls.dealt);
+    ls.live = wsum(ls.live);
     if (lane_id() == 0) {
         if constexpr (MODE == kPush) {
+            if (ls.live) atomicAdd(a.stats + kStSweepLiveEdges, ls.live);
             if (ls.batches) atomicAdd(a.stats + kStSweepBatches, ls.batches);
             if (ls.dealt) atomicAdd(a.stats + kStSweepDealt, ls.dealt);
             if (ls.chunks) atomicAdd(a.stats + kStSweepChunks, ls.chunks);
@@ -667,6 +703,17 @@ __global__ void __launch_bounds__(kFBlock) k_phase(GraphDev g, PhaseArgs p) {
         if ((c2l >> kCountShift) == 0 && (c2h >> kCountShift) == 0) { ++t; break; }
     }
     flush_stats<MODE>(a, ls);
+    // the last queue read (t - 1) still has its change bits; clearing them
+    // leaves every change mask zero for the next phase
+    if (t >= 1 && t < p.max_levels && !*(volatile unsigned int*)p.abort_flag) {
+        const int bl = (t - 1) % 3;
+        a.ql_prev = p.ql[bl];
+        a.cl_prev = &p.ctr[t - 1].x;
+        a.qh_prev = p.qh[bl];
+        a.ch_prev = MODE == kPush ? &p.ctr[t - 1].y : nullptr;
+        a.chg_prev = p.chg[bl];
+        clear_prev_bits(a, warp, nwarps);
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) *p.levels_out = t;
 }
 
@@ -747,6 +794,144 @@ cudaError_t launch_level(int kind, int mode, const GraphDev& g, const LevelArgs&
                          cudaStream_t st) {
     return mode == kPush ? launch_level_mode<kPush>(kind, g, a, grid, st)
                          : launch_level_mode<kCover>(kind, g, a, grid, st);
+}
+
+// ---------------------------------------------------------------------------
+// Live chunk masks (once per sketch: the simulations and thresholds are fixed
+// for its lifetime).  Bit c of edge e is set iff the edge is live (Eq.
+// hash_prob) in at least one simulation of chunk c (sorted simulations 16c ..
+// 16c+15).  A level then reads 4 bytes of an edge to learn which of its
+// source's changed chunks can move registers; the edge's id, hash and
+// threshold are read only for those.
+//
+// Work split by edges, not rows (a hub's edges spread over many warps): a
+// warp takes 512 consecutive edges, finds the row of the first by a 32-ary
+// search of the row starts, then for each 32 edges loads the starts of the
+// next 32 rows and every lane picks its row among them (a lane whose edge
+// lies past those rows, after a run of empty rows, searches on its own).
+// ---------------------------------------------------------------------------
+constexpr int kLcmEdgesPerWarp = 512;
+
+// Last row r in [lo, hi) with rp[r] <= e (rp non-decreasing, rp[lo] <= e), warp-wide.
+__device__ __forceinline__ int32_t row_of_warp(const int32_t* __restrict__ rp, int32_t lo, int32_t hi, int64_t e) {
+    const int lane = (int)lane_id();
+    while (hi - lo > 1) {
+        const int32_t step = (hi - lo + 31) >> 5;
+        const int64_t idx = (int64_t)lo + (int64_t)step * (lane + 1);
+        const bool le = idx < hi && (int64_t)__ldg(rp + idx) <= e;
+        const int c = __popc(__ballot_sync(0xFFFFFFFFu, le));
+        const int32_t nlo = lo + step * c;
+        const int32_t nhi = (c < 32) ? (int32_t)min((int64_t)hi, (int64_t)lo + (int64_t)step * (c + 1)) : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    return lo;
+}
+
+// Same search by one thread (binary).
+__device__ __forceinline__ int32_t row_of_thread(const int32_t* __restrict__ rp, int32_t lo, int32_t hi, int64_t e) {
+    while (hi - lo > 1) {
+        const int32_t mid = lo + ((hi - lo) >> 1);
+        if ((int64_t)__ldg(rp + mid) <= e) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <int KIND, int MODE>
+__global__ void __launch_bounds__(kFBlock) k_live_chunks(GraphDev g, const uint32_t* __restrict__ X,
+                                                         const uint16_t* __restrict__ tab, int J,
+                                                         uint32_t* __restrict__ lo_out,
+                                                         uint32_t* __restrict__ hi_out) {
+    __shared__ __align__(16) uint32_t sX[kMaxJ];
+    __shared__ uint16_t sTab[kTabSize];
+    for (int i = threadIdx.x; i < J; i += blockDim.x) sX[i] = __ldg(X + i);
+    for (int i = threadIdx.x; i < kTabSize; i += blockDim.x) sTab[i] = __ldg(tab + i);
+    __syncthreads();
+    const int lane = (int)lane_id();
+    const int32_t* rp = MODE == kPush ? g.rp_in : g.rp_out;
+    const int64_t m = g.m;
+    const int32_t n = g.n;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nchunks = J >> 4;
+    const uint32_t all_lo = nchunks >= 32 ? 0xFFFFFFFFu : ((1u << nchunks) - 1u);
+    const uint32_t all_hi = nchunks > 32 ? 0xFFFFFFFFu : 0u;
+    for (int64_t s0 = warp * kLcmEdgesPerWarp; s0 < m; s0 += nwarps * kLcmEdgesPerWarp) {
+        const int64_t s1 = min(m, s0 + kLcmEdgesPerWarp);
+        int32_t r0 = row_of_warp(rp, 0, n, s0);
+        for (int64_t f0 = s0; f0 < s1; f0 += 32) {
+            const int64_t e = f0 + lane;
+            // starts of rows r0 .. r0+31 (rows past n start after every edge)
+            const int64_t r = (int64_t)r0 + lane;
+            const int32_t beg = r <= n ? __ldg(rp + r) : 0x7FFFFFFF;
+            int i = 0;
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                const int32_t b = __shfl_sync(0xFFFFFFFFu, beg, (i + s) & 31);
+                if (i + s <= 31 && (int64_t)b <= e) i += s;
+            }
+            int32_t v = r0 + i;
+            // past the 32 rows (a run of empty rows): own search
+            if (e < s1 && i == 31 && r0 + 32 <= n && (int64_t)__ldg(rp + r0 + 32) <= e)
+                v = row_of_thread(rp, r0 + 31, n, e);
+            // the next batch starts in the row of this batch's last edge
+            r0 = __shfl_sync(0xFFFFFFFFu, v, 31);
+            if (e >= s1) continue;
+            uint32_t h, thr;
+            if constexpr (MODE == kPush) {
+                const int32_t u = __ldg(g.src_in + e);
+                h = __ldg(g.h_in + e);
+                const uint32_t aux = KIND == kWC ? __ldg(g.thr_v + v) : 0u;
+                thr = edge_threshold<KIND, true>(g, (uint32_t)u, (uint32_t)v, e, aux);
+            } else {
+                const int32_t w = __ldg(g.col_out + e);
+                h = __ldg(g.h_out + e);
+                thr = edge_threshold<KIND, false>(g, (uint32_t)v, (uint32_t)w, e, 0u);
+            }
+            uint32_t mlo = 0u, mhi = 0u;
+            if (thr >= 0x80000000u) {
+                mlo = all_lo;
+                mhi = all_hi;
+            } else if (thr > 0u) {
+                int lo, hi;
+                candidate_range(h, thr, J, sX, sTab, lo, hi);
+                for (int c = lo >> 4; hi > lo && c <= ((hi - 1) >> 4); ++c) {
+                    const int j1 = min(hi, 16 * c + 16);
+                    for (int j = max(lo, 16 * c); j < j1; ++j) {
+                        if ((sX[j] ^ h) < thr) {
+                            if (c < 32) mlo |= 1u << c;
+                            else mhi |= 1u << (c - 32);
+                            break;
+                        }
+                    }
+                }
+            }
+            lo_out[e] = mlo;
+            if (hi_out) hi_out[e] = mhi;
+        }
+    }
+}
+
+template <int MODE>
+static cudaError_t live_chunks_mode(int kind, const GraphDev& g, const uint32_t* X, const uint16_t* tab, int J,
+                                    uint32_t* lo, uint32_t* hi, int grid, cudaStream_t st) {
+    switch (kind) {
+        case kUniform: k_live_chunks<kUniform, MODE><<<grid, kFBlock, 0, st>>>(g, X, tab, J, lo, hi); break;
+        case kWC: k_live_chunks<kWC, MODE><<<grid, kFBlock, 0, st>>>(g, X, tab, J, lo, hi); break;
+        case kTrivalency: k_live_chunks<kTrivalency, MODE><<<grid, kFBlock, 0, st>>>(g, X, tab, J, lo, hi); break;
+        default: k_live_chunks<kExplicit, MODE><<<grid, kFBlock, 0, st>>>(g, X, tab, J, lo, hi); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_live_chunks(int kind, int mode, const GraphDev& g, const uint32_t* X, const uint16_t* tab,
+                               int J, uint32_t* lo, uint32_t* hi, cudaStream_t st) {
+    if (g.m == 0) return cudaSuccess;
+    const int64_t groups = (g.m + kLcmEdgesPerWarp - 1) / kLcmEdgesPerWarp;
+    const int64_t want = (groups + (kFBlock / 32) - 1) / (kFBlock / 32);
+    const int grid = (int)max((int64_t)1, min(want, (int64_t)level_grid()));
+    return mode == kPush ? live_chunks_mode<kPush>(kind, g, X, tab, J, lo, hi, grid, st)
+                         : live_chunks_mode<kCover>(kind, g, X, tab, J, lo, hi, grid, st);
 }
 
 // ---------------------------------------------------------------------------

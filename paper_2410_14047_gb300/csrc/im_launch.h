@@ -26,6 +26,7 @@ enum StatIndex : int {
     kStSweepHeavySims,
     kStSweepBatches,
     kStSweepDealt,
+    kStSweepLiveEdges,  // examined in-edges live in a changed chunk (their ids and hashes are read)
     kStCount
 };
 
@@ -71,6 +72,12 @@ struct LevelArgs {
     const int32_t* gid;                  // batches: graph of every vertex (NULL for one graph)
     unsigned long long* gcount;          // batches: visited-register counter per graph (cover)
     const uint8_t* gflag;                // batches: graphs whose vertices enter level 0 (build)
+    // live chunk masks of the level's edge orientation (in-edges for
+    // propagation, out-edges for covers): bit c of edge e = the edge is live
+    // in a simulation of chunk c (16c .. 16c+15); chunks 32..63 in lcm_hi
+    // (J = 1024, else NULL)
+    const uint32_t* lcm_lo;
+    const uint32_t* lcm_hi;
 };
 
 // All levels of a phase in one cooperative launch (grid barrier between levels).
@@ -165,6 +172,10 @@ struct BatchPickArgs {
 };
 cudaError_t launch_batch_pick(const BatchPickArgs& a, cudaStream_t st);
 cudaError_t launch_pick(const PickArgs& a, cudaStream_t st);
+// Live chunk masks of every in-edge (mode kPush) or out-edge (kCover) for the
+// simulations X (sorted) of one sketch.
+cudaError_t launch_live_chunks(int kind, int mode, const GraphDev& g, const uint32_t* X, const uint16_t* tab,
+                               int J, uint32_t* lo, uint32_t* hi, cudaStream_t st);
 // Lazy pick: refreshes S_v of every unpicked v whose stored (lb[v], v) is
 // below (S_cand, cand) with S_cand fresh, then takes the least stored pair.
 cudaError_t launch_pick_lazy(const PickArgs& a, cudaStream_t st);
