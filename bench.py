@@ -412,6 +412,12 @@ def run_gpu(args):
     def step():
         return im.im_select_seeds(G, wl.K, wl.J, seed=wl.seed, rebuild_eps=wl.rebuild_eps)
 
+    # the schedule knobs for this workload: the project's autotuner, untimed
+    tuned = None
+    if not args.tuning and not args.quick:
+        from paper_2410_14047_gb300 import autotune
+        tuned = autotune.tune(ctx, step, repeats=1)
+
     ref_seeds = None
     for _ in range(args.warmup):
         ref_seeds = step()["seeds"].tolist()
@@ -508,6 +514,9 @@ def run_gpu(args):
             "clocks": clocks,
             "deterministic": bool(deterministic),
             "seeds_match_oracle_golden": golden,
+            "tuning": {"knobs": im.im_ctx_get_tuning(ctx),
+                       "source": "autotuner (untimed, before warm-up)" if tuned else
+                       ("--tuning" if args.tuning else "defaults")},
         }
         if world == 1 and not args.no_cpu_baseline and not args.quick:
             out["cpu_baseline"] = cpu_baseline(wl, g)

@@ -16,9 +16,9 @@ import time
 from . import im_ctx_get_tuning, im_ctx_set_tuning
 
 DEFAULT_SPACE = {
-    "heavy_indeg": [16, 64, 256],
-    "light_batches": [2, 4, 8],
-    "dense_div": [0, 8],
+    "heavy_indeg": [64, 256],
+    "light_batches": [4, 8, 16],
+    "dense_div": [0, 4],
 }
 
 

@@ -196,7 +196,7 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                                             int64_t El, unsigned long long& st_chunks,
                                             unsigned long long& st_cas, unsigned long long& st_new,
                                             unsigned long long& st_batches, unsigned long long& st_dealt,
-                                            unsigned long long& st_live) {
+                                            unsigned long long& st_live, bool skip_heavy) {
     const int lane = (int)lane_id();
     const int J = a.J, words = a.words;
     const int64_t fend = min(El, b1 << 5);
@@ -227,8 +227,18 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
         if (f0 + 32 < fend && qn + lane < nl) rawn = __ldcg(reinterpret_cast<const int4*>(qlin) + qn + lane);
         // chunks with a changed simulation of each queue entry this batch uses
         uint32_t cm_lo = 0xFFFFFFFFu, cm_hi = 0xFFFFFFFFu;
-        if (!a.all_changed && wvalid && rel <= 31 && lane >= c0 - 1)
-            chunk_change_mask(a.chg_cur, raw.x, words, cm_lo, cm_hi);
+        const bool used = wvalid && rel <= 31 && lane >= c0 - 1;
+        if (!a.all_changed && used) chunk_change_mask(a.chg_cur, raw.x, words, cm_lo, cm_hi);
+        if constexpr (MODE == kPush) {
+            // dense walk: the heavy queue pushes the hubs
+            if (skip_heavy && used) {
+                const int32_t deg = __ldg(g.rp_in + raw.x + 1) - raw.y;
+                if (is_heavy<KIND>(deg, KIND == kWC ? (uint32_t)raw.w : g.thr_uniform, a.heavy_indeg)) {
+                    cm_lo = 0u;
+                    cm_hi = 0u;
+                }
+            }
+        }
         const uint32_t qcm_lo = __shfl_sync(0xFFFFFFFFu, cm_lo, myw);
         const uint32_t qcm_hi = __shfl_sync(0xFFFFFFFFu, cm_hi, myw);
         const int64_t f = f0 + lane;
@@ -519,12 +529,13 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
     const QEntry* ql = a.ql_in;
     // dense level: walk every vertex with in-edges in vertex order (contiguous
     // in-CSR reads); vertices without changed simulations produce no chunks
+    bool dense = false;
     if (MODE == kPush && a.q_dense && a.dense_div > 0 && (nl + nh) > 0 &&
         ((int64_t)(nl + nh) * a.dense_div > (int64_t)a.n_dense || a.all_changed)) {
         ql = a.q_dense;
         nl = a.n_dense;
         El = a.e_dense;
-        nh = 0;
+        dense = true;
     }
     const int64_t nbl = (El + 31) >> 5;
     // batches per claim: the tuned value, fewer when the level has fewer
@@ -558,7 +569,7 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
             const int64_t b0 = lu * lb;
             const int64_t b1 = min(nbl, b0 + lb);
             light_slice<KIND, MODE>(g, a, ql, sX, sTab, b0, b1, nl, El, ls.chunks, ls.cas, ls.fresh,
-                                    ls.batches, ls.dealt, ls.live);
+                                    ls.batches, ls.dealt, ls.live, dense && nh > 0);
         }
     }
 }
