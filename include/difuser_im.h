@@ -148,7 +148,7 @@ typedef struct {
     int32_t level;   /* level index within its phase */
     int64_t count;   /* queued vertices the launch processed */
     int64_t edges;   /* edges of those vertices (in-edges for sweeps, out-edges for covers) */
-    double ms;       /* kernel time, CUDA events on the context's stream */
+    double ms;       /* duration of the level (see im_ctx_set_trace) */
 } im_trace_rec;
 
 /* ---- context ----------------------------------------------------------- */
@@ -175,7 +175,10 @@ IM_API im_status im_ctx_set_timing(im_ctx* ctx, int enable);
 /* Sets (NULL = defaults {256, 4, 0, 2, 1, 0, 1}) or reads the schedule knobs. */
 IM_API im_status im_ctx_set_tuning(im_ctx* ctx, const im_tuning* tuning);
 IM_API im_status im_ctx_get_tuning(const im_ctx* ctx, im_tuning* tuning);
-/* enable != 0: also keep one im_trace_rec per frontier launch (implies timing). */
+/* enable != 0: also keep one im_trace_rec per frontier level (implies timing):
+ * its duration comes from CUDA events around the level's launch, or, when a
+ * phase runs all its levels in one launch, from the device's global timer
+ * read at every level boundary. */
 IM_API im_status im_ctx_set_trace(im_ctx* ctx, int enable);
 /* Copies up to `cap` trace records of the last selection / build into `out`
  * (may be NULL to query); returns the number of records available. */

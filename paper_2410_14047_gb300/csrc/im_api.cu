@@ -226,7 +226,8 @@ struct im_sketch {
     im_ctx* ctx = nullptr;  // execution context: allocator, stream, statistics
     int32_t J = 0;
     DBuf M, X, salt, tab, ql[3], qh[3], ctr, claim, chg[3], gen, seed_bits, count, part_S, part_u,
-        ticket, stats, err, bar, lb, cand, part_S2, part_u2, lcm_in_lo, lcm_in_hi, lcm_out_lo, lcm_out_hi;
+        ticket, stats, err, bar, lb, cand, part_S2, part_u2, lcm_in_lo, lcm_in_hi, lcm_out_lo, lcm_out_hi,
+        level_ns;
     bool lazy = false;      // picks after the first refresh stored sums only (im_select_seeds)
     bool chg_dirty = true;  // change masks may hold bits (new sketch, or a phase that failed)
     bool lb_ready = false;  // lb holds the sums of the last full pick or later refreshes
@@ -571,6 +572,7 @@ static void sketch_plan(im_sketch* sk, int32_t n, int64_t m_edges, int32_t J, Bu
     A(sk->stats, (size_t)kStCount * 8);
     A(sk->err, 4);
     A(sk->bar, 16);
+    A(sk->level_ns, (size_t)(kMaxLevels + 2) * 8);
     A(sk->lb, (size_t)n * 8);
     A(sk->cand, 4);
     A(sk->part_S2, (size_t)pg * 8);
@@ -712,7 +714,6 @@ static im_status phase_begin(im_sketch* sk) {
 
 // All levels of a phase in one cooperative launch; one host synchronisation.
 static im_status run_phase_persistent(im_sketch* sk, int mode, bool all_first, int grid) {
-    im_graph* g = sk->g;
     im_ctx* c = sk->ctx;
     auto st = c->stream;
     PhaseArgs p{};
@@ -734,6 +735,7 @@ static im_status run_phase_persistent(im_sketch* sk, int mode, bool all_first, i
     p.abort_flag = bar + 2;
     p.levels_out = reinterpret_cast<int*>(bar + 3);
     p.limit_ns = 20ull * 1000 * 1000 * 1000;
+    p.level_ns = c->trace ? sk->level_ns.as<unsigned long long>() : nullptr;
     CK(c, timed(c, mode == kPush ? kTPush : kTCover,
                 [&] { return launch_phase(sk->kind, mode, sk->dev, p, grid, st); }));
     CK(c, cudaMemcpyAsync(c->pinned, bar, 16, cudaMemcpyDeviceToHost, st));
@@ -742,6 +744,23 @@ static im_status run_phase_persistent(im_sketch* sk, int mode, bool all_first, i
     const int levels = (int)hb[3];
     sk->gen_counter += levels + 1;
     sk->chg_dirty = true;
+    if (c->trace && levels > 0 && levels < p.max_levels) {
+        // per-level records from the in-kernel clock (one launch for all levels)
+        std::vector<ulonglong2> h((size_t)levels);
+        std::vector<unsigned long long> ns((size_t)levels + 1);
+        CK(c, cudaMemcpyAsync(h.data(), sk->ctr.p, (size_t)levels * 16, cudaMemcpyDeviceToHost, st));
+        CK(c, cudaMemcpyAsync(ns.data(), sk->level_ns.p, ((size_t)levels + 1) * 8, cudaMemcpyDeviceToHost, st));
+        CK(c, sync_collect(c));
+        for (int l = 0; l < levels; ++l) {
+            im_trace_rec r{};
+            r.kind = mode;
+            r.level = l;
+            r.count = (int64_t)(h[l].x >> kCountShift) + (int64_t)(h[l].y >> kCountShift);
+            r.edges = (int64_t)(h[l].x & kEdgeMask) + (int64_t)(h[l].y & kEdgeMask);
+            r.ms = (double)(ns[l + 1] - ns[l]) * 1e-6;
+            c->recs.push_back(r);
+        }
+    }
     if (levels >= p.max_levels)
         return fail(c, IM_E_TIMEOUT, "frontier did not empty within %d levels", p.max_levels);
     CKS(check_err(sk));
@@ -755,10 +774,9 @@ static im_status run_phase_persistent(im_sketch* sk, int mode, bool all_first, i
 // reads the newest counters every `check` levels; levels launched after the
 // queues emptied see empty queues and return at once.
 static im_status run_levels(im_sketch* sk, int mode, bool all_first) {
-    im_graph* g = sk->g;
     im_ctx* c = sk->ctx;
     auto st = c->stream;
-    if (c->tuning.persistent && !c->trace) {
+    if (c->tuning.persistent) {
         const int pgrid = phase_grid();
         if (pgrid > 0) return run_phase_persistent(sk, mode, all_first, pgrid);
     }
@@ -852,7 +870,6 @@ static im_status run_levels(im_sketch* sk, int mode, bool all_first) {
 }
 
 static im_status propagate(im_sketch* sk) {
-    im_graph* g = sk->g;
     im_ctx* c = sk->ctx;
     CKS(phase_begin(sk));
     LevelArgs a = level_args(sk);

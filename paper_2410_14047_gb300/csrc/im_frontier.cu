@@ -27,6 +27,16 @@
 namespace im {
 
 constexpr int kFBlock = 256;
+// resident blocks per SM the frontier kernels are compiled for (register cap);
+// the work is latency-bound, so more resident warps hide more of it
+#ifndef IM_PHASE_MIN_BLOCKS
+#define IM_PHASE_MIN_BLOCKS 4
+#endif
+#ifndef IM_LEVEL_MIN_BLOCKS
+#define IM_LEVEL_MIN_BLOCKS 4
+#endif
+constexpr int kPhaseMinBlocks = IM_PHASE_MIN_BLOCKS;
+constexpr int kLevelMinBlocks = IM_LEVEL_MIN_BLOCKS;
 
 __device__ __forceinline__ unsigned long long wsum(unsigned long long x) {
 #pragma unroll
@@ -161,22 +171,31 @@ __device__ __forceinline__ uint32_t halves_nonzero(uint32_t w) {
     return ((w & 0xFFFFu) != 0u ? 1u : 0u) | ((w >> 16) != 0u ? 2u : 0u);
 }
 
-// Chunks of vertex v with a changed simulation: bits 0..31 in lo, 32..63 in hi.
+// Chunks of vertex v with a changed simulation: bits 0..31 in lo, 32..63 in
+// hi.  The change words are also kept in `keep` (words <= kKeepWords).
+constexpr int kKeepWords = 8;
 __device__ __forceinline__ void chunk_change_mask(const uint32_t* __restrict__ chg, int32_t v, int words,
-                                                  uint32_t& lo, uint32_t& hi) {
+                                                  uint32_t& lo, uint32_t& hi, uint32_t* keep) {
     lo = 0u;
     hi = 0u;
     const uint32_t* row = chg + (size_t)v * words;
     if (words >= 4) {
         for (int q = 0; q < (words >> 2); ++q) {
             const uint4 w4 = __ldcg(reinterpret_cast<const uint4*>(row) + q);
+            if (words <= kKeepWords) {
+                keep[4 * q] = w4.x; keep[4 * q + 1] = w4.y; keep[4 * q + 2] = w4.z; keep[4 * q + 3] = w4.w;
+            }
             const uint32_t b = halves_nonzero(w4.x) | (halves_nonzero(w4.y) << 2) | (halves_nonzero(w4.z) << 4) |
                                (halves_nonzero(w4.w) << 6);
             if (q < 4) lo |= b << (8 * q);
             else hi |= b << (8 * (q - 4));
         }
     } else {
-        for (int w = 0; w < words; ++w) lo |= halves_nonzero(__ldcg(row + w)) << (2 * w);
+        for (int w = 0; w < words; ++w) {
+            const uint32_t x = __ldcg(row + w);
+            keep[w] = x;
+            lo |= halves_nonzero(x) << (2 * w);
+        }
     }
 }
 
@@ -196,7 +215,8 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                                             int64_t El, unsigned long long& st_chunks,
                                             unsigned long long& st_cas, unsigned long long& st_new,
                                             unsigned long long& st_batches, unsigned long long& st_dealt,
-                                            unsigned long long& st_live, bool skip_heavy) {
+                                            unsigned long long& st_live, bool skip_heavy,
+                                            uint32_t (*sKeep)[kKeepWords]) {
     const int lane = (int)lane_id();
     const int J = a.J, words = a.words;
     const int64_t fend = min(El, b1 << 5);
@@ -225,10 +245,31 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
         }
         int4 rawn = make_int4(0, 0, 0x7FFFFFFF, 0);
         if (f0 + 32 < fend && qn + lane < nl) rawn = __ldcg(reinterpret_cast<const int4*>(qlin) + qn + lane);
+        // this lane's edge: live chunk mask, source and hash are fetched at
+        // once (one round trip with the change words below)
+        const int64_t f = f0 + lane;
+        const int64_t e = (int64_t)qrp + (f - qoff);
+        int32_t o = 0;
+        uint32_t h = 0, thr = 0;
+        uint32_t m_lo = 0u, m_hi = 0u;
+        if (f < fend) {
+            m_lo = __ldg(a.lcm_lo + e);
+            if (a.lcm_hi) m_hi = __ldg(a.lcm_hi + e);
+            if constexpr (MODE == kPush) {
+                o = __ldg(g.src_in + e);
+                h = __ldg(g.h_in + e);
+                if constexpr (KIND == kExplicit) thr = __ldg(g.thr_in + e);
+            } else {
+                o = __ldg(g.col_out + e);
+                h = __ldg(g.h_out + e);
+                if constexpr (KIND == kExplicit || KIND == kWC) thr = edge_threshold<KIND, false>(g, 0u, 0u, e, 0u);
+            }
+        }
         // chunks with a changed simulation of each queue entry this batch uses
         uint32_t cm_lo = 0xFFFFFFFFu, cm_hi = 0xFFFFFFFFu;
         const bool used = wvalid && rel <= 31 && lane >= c0 - 1;
-        if (!a.all_changed && used) chunk_change_mask(a.chg_cur, raw.x, words, cm_lo, cm_hi);
+        __syncwarp();
+        if (!a.all_changed && used) chunk_change_mask(a.chg_cur, raw.x, words, cm_lo, cm_hi, sKeep[lane]);
         if constexpr (MODE == kPush) {
             // dense walk: the heavy queue pushes the hubs
             if (skip_heavy && used) {
@@ -239,29 +280,16 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                 }
             }
         }
-        const uint32_t qcm_lo = __shfl_sync(0xFFFFFFFFu, cm_lo, myw);
-        const uint32_t qcm_hi = __shfl_sync(0xFFFFFFFFu, cm_hi, myw);
-        const int64_t f = f0 + lane;
-        int32_t o = 0;
-        uint32_t h = 0, thr = 0;
-        uint32_t m_lo = 0u, m_hi = 0u;
-        int nch = 0;
-        if (f < fend && (qcm_lo | qcm_hi)) {
-            // chunks in which this edge is live and its source changed
-            const int64_t e = (int64_t)qrp + (f - qoff);
-            m_lo = __ldg(a.lcm_lo + e) & qcm_lo;
-            if (a.lcm_hi) m_hi = __ldg(a.lcm_hi + e) & qcm_hi;
-            nch = __popc(m_lo) + __popc(m_hi);
-            if (nch) {
-                if constexpr (MODE == kPush) {
-                    o = __ldg(g.src_in + e);
-                    h = __ldg(g.h_in + e);
-                    thr = edge_threshold<KIND, true>(g, (uint32_t)o, (uint32_t)qv, e, qaux);
-                } else {
-                    o = __ldg(g.col_out + e);
-                    h = __ldg(g.h_out + e);
+        __syncwarp();
+        m_lo &= __shfl_sync(0xFFFFFFFFu, cm_lo, myw);
+        m_hi &= __shfl_sync(0xFFFFFFFFu, cm_hi, myw);
+        const int nch = __popc(m_lo) + __popc(m_hi);
+        if (nch) {
+            if constexpr (MODE == kPush) {
+                if constexpr (KIND != kExplicit) thr = edge_threshold<KIND, true>(g, (uint32_t)o, (uint32_t)qv, e, qaux);
+            } else {
+                if constexpr (KIND != kExplicit && KIND != kWC)
                     thr = edge_threshold<KIND, false>(g, (uint32_t)qv, (uint32_t)o, e, 0u);
-                }
             }
         }
         if (nch) ++st_live;
@@ -284,6 +312,7 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
             }
             if (i > 31) i = 31;
             const int ex_i = __shfl_sync(0xFFFFFFFFu, excl, i);
+            const int w_i = __shfl_sync(0xFFFFFFFFu, myw, i);
             const uint32_t ml_i = __shfl_sync(0xFFFFFFFFu, m_lo, i);
             const uint32_t mh_i = __shfl_sync(0xFFFFFFFFu, m_hi, i);
             const int32_t o_i = __shfl_sync(0xFFFFFFFFu, o, i);
@@ -295,8 +324,11 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
             if (k < total) {
                 chunk = nth_chunk(ml_i, mh_i, k - ex_i);
                 uint32_t chb = 0xFFFFu;
-                if (!a.all_changed)
-                    chb = (__ldcg(a.chg_cur + (size_t)q_i * words + (chunk >> 1)) >> ((chunk & 1) * 16)) & 0xFFFFu;
+                if (!a.all_changed) {
+                    const uint32_t cw = words <= kKeepWords ? sKeep[w_i][chunk >> 1]
+                                                            : __ldcg(a.chg_cur + (size_t)q_i * words + (chunk >> 1));
+                    chb = (cw >> ((chunk & 1) * 16)) & 0xFFFFu;
+                }
                 if (chb) {
                     const uint4* xs = reinterpret_cast<const uint4*>(sX + chunk * 16);
                     const uint8_t* srow = a.M + (size_t)q_i * J + chunk * 16;
@@ -519,7 +551,8 @@ __device__ __forceinline__ void clear_prev_bits(const LevelArgs& a, int64_t warp
 // claimed from the level's counter.
 template <int KIND, int MODE>
 __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a, const uint32_t* sX,
-                                           const uint16_t* sTab, int64_t warp, LevelStats& ls) {
+                                           const uint16_t* sTab, int64_t warp, LevelStats& ls,
+                                           uint32_t (*sKeep)[kKeepWords]) {
     const int lane = (int)lane_id();
     const unsigned long long cl = __ldcg(a.cl_in);
     const unsigned long long ch = a.ch_in ? __ldcg(a.ch_in) : 0ull;
@@ -537,39 +570,53 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
         El = a.e_dense;
         dense = true;
     }
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // a small level scans the hubs' in-edges as a second flat edge space
+    // (split over many warps) instead of searching per changed simulation:
+    // the searches' chains of dependent loads would set the level's latency
+    const int64_t Eh = (int64_t)(ch & kEdgeMask);
+    const bool hscan = MODE == kPush && nh > 0 && El + Eh <= nwarps * 32 * 4;
     const int64_t nbl = (El + 31) >> 5;
+    const int64_t nbh = hscan ? (Eh + 31) >> 5 : 0;
     // batches per claim: the tuned value, fewer when the level has fewer
     // batches than warps (shorter chains on small levels)
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t lb = max((int64_t)1, min((int64_t)a.light_batches, nbl / nwarps));
+    const int64_t lb = max((int64_t)1, min((int64_t)a.light_batches, (nbl + nbh) / nwarps));
     const int64_t lunits = (nbl + lb - 1) / lb;
-    const int64_t total = (int64_t)nh + lunits;
+    const int64_t hunits = (nbh + lb - 1) / lb;
+    const int64_t nhv = hscan ? 0 : (int64_t)nh;  // hubs searched per changed simulation
+    const int64_t total = nhv + lunits + hunits;
     if (total == 0) return;
     if (warp == 0 && lane == 0) {
         atomicAdd(a.stats + (MODE == kPush ? kStSweepVertices : kStCoverVertices),
                   (unsigned long long)(nl + nh));
-        atomicAdd(a.stats + (MODE == kPush ? kStSweepEdges : kStCoverEdges), (unsigned long long)El);
+        atomicAdd(a.stats + (MODE == kPush ? kStSweepEdges : kStCoverEdges), (unsigned long long)(El + (hscan ? Eh : 0)));
         atomicAdd(a.stats + (MODE == kPush ? kStSweepLevels : kStCoverLevels), 1ull);
-        if (MODE == kPush) atomicAdd(a.stats + kStSweepHeavy, (unsigned long long)nh);
+        if (MODE == kPush) atomicAdd(a.stats + kStSweepHeavy, (unsigned long long)nhv);
     }
     for (;;) {
         unsigned int unit = 0;
         if (lane == 0) unit = atomicAdd(a.claim, 1u);
         unit = __shfl_sync(0xFFFFFFFFu, unit, 0);
         if ((int64_t)unit >= total) break;
-        if ((int64_t)unit < nh) {
+        if ((int64_t)unit < nhv) {
             if constexpr (MODE == kPush && (KIND == kWC || KIND == kUniform)) {
                 const int4 raw = __ldcg(reinterpret_cast<const int4*>(a.qh_in) + unit);
                 QEntry ent;
                 ent.v = raw.x; ent.rp = raw.y; ent.off = raw.z; ent.aux = (uint32_t)raw.w;
                 heavy_vertex<KIND>(g, a, sX, ent, ls.hsims, ls.cas);
             }
-        } else {
-            const int64_t lu = (int64_t)unit - nh;
+        } else if ((int64_t)unit < nhv + lunits) {
+            const int64_t lu = (int64_t)unit - nhv;
             const int64_t b0 = lu * lb;
             const int64_t b1 = min(nbl, b0 + lb);
             light_slice<KIND, MODE>(g, a, ql, sX, sTab, b0, b1, nl, El, ls.chunks, ls.cas, ls.fresh,
-                                    ls.batches, ls.dealt, ls.live, dense && nh > 0);
+                                    ls.batches, ls.dealt, ls.live, dense && nh > 0, sKeep);
+        } else {
+            const int64_t hu = (int64_t)unit - nhv - lunits;
+            const int64_t b0 = hu * lb;
+            const int64_t b1 = min(nbh, b0 + lb);
+            light_slice<KIND, MODE>(g, a, a.qh_in, sX, sTab, b0, b1, nh, Eh, ls.chunks, ls.cas, ls.fresh,
+                                    ls.batches, ls.dealt, ls.live, false, sKeep);
         }
     }
 }
@@ -610,9 +657,10 @@ __device__ __forceinline__ void load_tables(const LevelArgs& a, uint32_t* sX, ui
 
 // One level per launch (used when the host traces every level).
 template <int KIND, int MODE>
-__global__ void __launch_bounds__(kFBlock) k_level(GraphDev g, LevelArgs a) {
+__global__ void __launch_bounds__(kFBlock, kLevelMinBlocks) k_level(GraphDev g, LevelArgs a) {
     __shared__ __align__(16) uint32_t sX[kMaxJ];
     __shared__ uint16_t sTab[kTabSize];
+    __shared__ uint32_t sKeep[kFBlock / 32][32][kKeepWords];
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     clear_prev_bits(a, warp, nwarps);
@@ -621,7 +669,7 @@ __global__ void __launch_bounds__(kFBlock) k_level(GraphDev g, LevelArgs a) {
     if ((cl >> kCountShift) == 0 && (ch >> kCountShift) == 0) return;
     load_tables(a, sX, sTab);
     LevelStats ls;
-    level_work<KIND, MODE>(g, a, sX, sTab, warp, ls);
+    level_work<KIND, MODE>(g, a, sX, sTab, warp, ls, sKeep[threadIdx.x >> 5]);
     flush_stats<MODE>(a, ls);
 }
 
@@ -672,15 +720,17 @@ __device__ bool grid_barrier(unsigned int* arrive, volatile unsigned int* gen, v
 // buffers t % 3 as in k_level; a grid barrier separates levels; the phase
 // ends when both queues of the next level are empty.
 template <int KIND, int MODE>
-__global__ void __launch_bounds__(kFBlock) k_phase(GraphDev g, PhaseArgs p) {
+__global__ void __launch_bounds__(kFBlock, kPhaseMinBlocks) k_phase(GraphDev g, PhaseArgs p) {
     __shared__ __align__(16) uint32_t sX[kMaxJ];
     __shared__ uint16_t sTab[kTabSize];
+    __shared__ uint32_t sKeep[kFBlock / 32][32][kKeepWords];
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     LevelArgs a = p.base;
     load_tables(a, sX, sTab);
     LevelStats ls;
     int t = 0;
+    if (p.level_ns && blockIdx.x == 0 && threadIdx.x == 0) p.level_ns[0] = global_ns();
     for (; t < p.max_levels; ++t) {
         const int bi = t % 3, bo = (t + 1) % 3, bp = (t + 2) % 3;
         a.ql_in = p.ql[bi];
@@ -707,8 +757,9 @@ __global__ void __launch_bounds__(kFBlock) k_phase(GraphDev g, PhaseArgs p) {
         a.claim = p.claim + t;
         a.gen_next = p.gen_base + t;
         clear_prev_bits(a, warp, nwarps);
-        level_work<KIND, MODE>(g, a, sX, sTab, warp, ls);
+        level_work<KIND, MODE>(g, a, sX, sTab, warp, ls, sKeep[threadIdx.x >> 5]);
         if (!grid_barrier(p.bar_arrive, p.bar_gen, p.abort_flag, a.err, p.limit_ns)) break;
+        if (p.level_ns && blockIdx.x == 0 && threadIdx.x == 0) p.level_ns[t + 1] = global_ns();
         const unsigned long long c2l = __ldcg(&p.ctr[t + 1].x);
         const unsigned long long c2h = __ldcg(&p.ctr[t + 1].y);
         if ((c2l >> kCountShift) == 0 && (c2h >> kCountShift) == 0) { ++t; break; }

@@ -96,6 +96,7 @@ struct PhaseArgs {
     unsigned int* abort_flag;
     unsigned long long limit_ns;         // bound on every barrier wait
     int* levels_out;                     // levels the phase ran
+    unsigned long long* level_ns;        // tracing: global time at the start of level t (may be NULL)
 };
 
 int level_grid();
