@@ -131,7 +131,11 @@ typedef struct {
  * level of a build always does when dense_div > 0); lazy_pick: 1 = in
  * im_select_seeds, picks after the first recompute S_u only for the vertices
  * whose stored S_u (a lower bound: S_u never decreases during a selection)
- * could still beat the best candidate, 0 = every pick reads every row. */
+ * could still beat the best candidate, 0 = every pick reads every row;
+ * buckets: 1 = each sketch groups the live (edge, 16-simulation chunk) pairs
+ * of every vertex by chunk with their live masks, and a level visits only the
+ * groups whose chunk changed (falls back to edge scans when the groups would
+ * exceed 4 entries per edge), 0 = edge scans with live chunk masks. */
 typedef struct {
     int32_t heavy_indeg;
     int32_t light_batches;
@@ -140,6 +144,7 @@ typedef struct {
     int32_t persistent;
     int32_t dense_div;
     int32_t lazy_pick;
+    int32_t buckets;
 } im_tuning;
 
 /* One frontier launch of the last selection / build (tracing on). */
@@ -172,7 +177,7 @@ IM_API im_status im_last_stats(const im_ctx* ctx, im_stats* out);
  * stream and report per-kind kernel time in im_stats (adds two event records
  * per launch).  Off by default. */
 IM_API im_status im_ctx_set_timing(im_ctx* ctx, int enable);
-/* Sets (NULL = defaults {256, 4, 0, 2, 1, 0, 1}) or reads the schedule knobs. */
+/* Sets (NULL = defaults {256, 4, 0, 2, 1, 0, 1, 1}) or reads the schedule knobs. */
 IM_API im_status im_ctx_set_tuning(im_ctx* ctx, const im_tuning* tuning);
 IM_API im_status im_ctx_get_tuning(const im_ctx* ctx, im_tuning* tuning);
 /* enable != 0: also keep one im_trace_rec per frontier level (implies timing):

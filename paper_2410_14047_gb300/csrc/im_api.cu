@@ -44,7 +44,7 @@ struct im_ctx {
     bool trace = false;
     std::vector<float> launch_ms;    // kernel time per launch sequence number (tracing)
     std::vector<im_trace_rec> recs;  // frontier launches of the last call
-    im_tuning tuning{256, 4, 0, 2, 1, 0, 1};
+    im_tuning tuning{256, 4, 0, 2, 1, 0, 1, 1};
 };
 
 namespace {
@@ -228,6 +228,15 @@ struct im_sketch {
     DBuf M, X, salt, tab, ql[3], qh[3], ctr, claim, chg[3], gen, seed_bits, count, part_S, part_u,
         ticket, stats, err, bar, lb, cand, part_S2, part_u2, lcm_in_lo, lcm_in_hi, lcm_out_lo, lcm_out_hi,
         level_ns;
+    // bucket mode: bucketed live lists per orientation (0: in-edges, 1:
+    // out-edges); the light queues then hold buckets, bq_cap entries each
+    DBuf bk_end[2], bk_other[2], bk_mask[2];
+    // bucket mode keeps the cover's change masks apart from the
+    // propagation's: a bucket that is empty in one orientation may keep stale
+    // bits there (never read), which must not reach the other orientation
+    DBuf chg_cov[3];
+    bool buckets = false;
+    int32_t bq_cap = 0;
     bool lazy = false;      // picks after the first refresh stored sums only (im_select_seeds)
     bool chg_dirty = true;  // change masks may hold bits (new sketch, or a phase that failed)
     bool lb_ready = false;  // lb holds the sums of the last full pick or later refreshes
@@ -300,12 +309,12 @@ extern "C" im_status im_ctx_set_timing(im_ctx* c, int enable) {
 extern "C" im_status im_ctx_set_tuning(im_ctx* c, const im_tuning* t) {
     if (!c) return IM_E_INVAL;
     if (!t) {
-        c->tuning = im_tuning{256, 4, 0, 2, 1, 0, 1};
+        c->tuning = im_tuning{256, 4, 0, 2, 1, 0, 1, 1};
         return IM_OK;
     }
     if (t->heavy_indeg < 0 || t->light_batches < 1 || t->light_batches > 4096 || t->grid_blocks < 0 ||
         t->check_every < 1 || t->check_every > 64 || t->persistent < 0 || t->persistent > 1 ||
-        t->dense_div < 0 || t->lazy_pick < 0 || t->lazy_pick > 1)
+        t->dense_div < 0 || t->lazy_pick < 0 || t->lazy_pick > 1 || t->buckets < 0 || t->buckets > 1)
         return fail(c, IM_E_INVAL, "tuning out of range");
     c->tuning = *t;
     return IM_OK;
@@ -558,8 +567,6 @@ static void sketch_plan(im_sketch* sk, int32_t n, int64_t m_edges, int32_t J, Bu
     A(sk->X, (size_t)J * 4);
     A(sk->salt, (size_t)J * 4);
     A(sk->tab, (size_t)kTabSize * 2);
-    for (int i = 0; i < 3; ++i) A(sk->ql[i], (size_t)n * sizeof(QEntry));
-    for (int i = 0; i < 3; ++i) A(sk->qh[i], (size_t)n * sizeof(QEntry));
     A(sk->ctr, (size_t)(kMaxLevels + 2) * 16);
     A(sk->claim, (size_t)(kMaxLevels + 2) * 4);
     for (int i = 0; i < 3; ++i) A(sk->chg[i], (size_t)n * ((J + 31) / 32) * 4);
@@ -577,7 +584,15 @@ static void sketch_plan(im_sketch* sk, int32_t n, int64_t m_edges, int32_t J, Bu
     A(sk->cand, 4);
     A(sk->part_S2, (size_t)pg * 8);
     A(sk->part_u2, (size_t)pg * 4);
-    // live chunk masks of every in-edge and out-edge (chunks 32..63: J = 1024)
+    (void)m_edges;
+}
+
+// Edge-scan mode buffers: vertex queues (light and heavy, n entries each) and
+// the live chunk masks of every in-edge and out-edge (chunks 32..63: J = 1024).
+static void scan_plan(im_sketch* sk, int32_t n, int64_t m_edges, int32_t J, BufPlan& plan) {
+    auto A = [&](DBuf& b, size_t bytes) { plan.emplace_back(&b, bytes); };
+    for (int i = 0; i < 3; ++i) A(sk->ql[i], (size_t)n * sizeof(QEntry));
+    for (int i = 0; i < 3; ++i) A(sk->qh[i], (size_t)n * sizeof(QEntry));
     const size_t m = (size_t)m_edges;
     A(sk->lcm_in_lo, m * 4);
     A(sk->lcm_out_lo, m * 4);
@@ -587,12 +602,40 @@ static void sketch_plan(im_sketch* sk, int32_t n, int64_t m_edges, int32_t J, Bu
     }
 }
 
-// Frees every buffer of the plan and the output buffers (null ones are skipped).
+// Bucket mode limits: at most kBucketEntriesPerEdge entries per edge on
+// average in each orientation (else the sketch uses edge scans), and the
+// bucket queues hold bucket_queue_cap entries.
+constexpr int64_t kBucketEntriesPerEdge = 4;
+static int64_t bucket_queue_cap(int32_t n) {
+    const int64_t cap = std::max<int64_t>(8 * (int64_t)n, 1 << 20);
+    return std::min<int64_t>(cap, 1 << 25);
+}
+// Device bytes bucket mode may take beyond the fixed plan (upper bound).
+static uint64_t bucket_reserve_bytes(int32_t n, int64_t m, int32_t J) {
+    const uint64_t nb = (uint64_t)n * (uint64_t)(J / 16);
+    const uint64_t ents = (uint64_t)(kBucketEntriesPerEdge * m);
+    uint64_t r = 0;
+    for (int o = 0; o < 2; ++o)
+        r += round_bytes((nb + 1) * 4) + round_bytes(std::max<uint64_t>(ents, 1) * 4) +
+             round_bytes(std::max<uint64_t>(ents, 1) * 2);
+    r += 3 * round_bytes((uint64_t)std::min<int64_t>(bucket_queue_cap(n), (int64_t)std::max<uint64_t>(nb, 1)) *
+                         sizeof(QEntry));
+    r += round_bytes(scan_tmp_bytes((int32_t)std::min<uint64_t>(nb, 0x7FFFFFFF))) + 256;
+    r += 3 * round_bytes((size_t)n * ((J + 31) / 32) * 4);  // the cover's change masks
+    return r;
+}
+
+// Frees every buffer of the plans, the bucket lists and the output buffers
+// (null ones are skipped).
 static void sketch_release(im_sketch* sk) {
     im_ctx* c = sk->ctx;
     BufPlan plan;
     sketch_plan(sk, sk->g->n, sk->g->m, sk->J, plan);
+    scan_plan(sk, sk->g->n, sk->g->m, sk->J, plan);
     for (auto& pb : plan) dfree(c, *pb.first);
+    for (int o = 0; o < 2; ++o)
+        for (DBuf* b : {&sk->bk_end[o], &sk->bk_other[o], &sk->bk_mask[o]}) dfree(c, *b);
+    for (int i = 0; i < 3; ++i) dfree(c, sk->chg_cov[i]);
     for (DBuf* b : {&sk->out_seed, &sk->out_S, &sk->out_est}) dfree(c, *b);
 }
 
@@ -676,11 +719,29 @@ static LevelArgs level_args(im_sketch* sk) {
     return a;
 }
 
+// Change-mask buffer i of a phase of this mode.
+static DBuf& chg_buf(im_sketch* sk, int mode, int i) {
+    return (sk->buckets && mode == kCover) ? sk->chg_cov[i] : sk->chg[i];
+}
+
 // Live chunk masks of the phase's edge orientation.
 static void set_lcm(LevelArgs& a, const im_sketch* sk, int mode) {
     const bool in = mode == kPush;
     a.lcm_lo = (in ? sk->lcm_in_lo : sk->lcm_out_lo).as<uint32_t>();
     a.lcm_hi = sk->J > 512 ? (in ? sk->lcm_in_hi : sk->lcm_out_hi).as<uint32_t>() : nullptr;
+    a.chunks = sk->J / 16;
+    a.nbuckets = (int64_t)sk->g->n * (sk->J / 16);
+    a.bq_cap = sk->bq_cap;
+    if (sk->buckets) {
+        const int o = in ? 0 : 1;
+        a.bk_end = sk->bk_end[o].as<uint32_t>();
+        a.bk_other = sk->bk_other[o].as<int32_t>();
+        a.bk_mask = sk->bk_mask[o].as<uint16_t>();
+    } else {
+        a.bk_end = nullptr;
+        a.bk_other = nullptr;
+        a.bk_mask = nullptr;
+    }
 }
 
 // Reads the device error word; converts raised bits to a status.
@@ -706,6 +767,8 @@ static im_status phase_begin(im_sketch* sk) {
     CK(c, cudaMemsetAsync(sk->claim.p, 0, sk->claim.bytes, st));
     if (sk->chg_dirty) {
         for (int i = 0; i < 3; ++i) CK(c, cudaMemsetAsync(sk->chg[i].p, 0, sk->chg[i].bytes, st));
+        for (int i = 0; i < 3; ++i)
+            if (sk->chg_cov[i].p) CK(c, cudaMemsetAsync(sk->chg_cov[i].p, 0, sk->chg_cov[i].bytes, st));
         sk->chg_dirty = false;
     }
     CK(c, cudaMemsetAsync(sk->bar.p, 0, sk->bar.bytes, st));
@@ -722,7 +785,7 @@ static im_status run_phase_persistent(im_sketch* sk, int mode, bool all_first, i
     for (int i = 0; i < 3; ++i) {
         p.ql[i] = sk->ql[i].as<QEntry>();
         p.qh[i] = sk->qh[i].as<QEntry>();
-        p.chg[i] = sk->chg[i].as<uint32_t>();
+        p.chg[i] = chg_buf(sk, mode, i).as<uint32_t>();
     }
     p.ctr = sk->ctr.as<ulonglong2>();
     p.claim = sk->claim.as<unsigned int>();
@@ -793,7 +856,7 @@ static im_status run_levels(im_sketch* sk, int mode, bool all_first) {
         a.ql_in = sk->ql[bi].as<QEntry>();
         a.cl_in = &ctr[t].x;
         a.qh_in = sk->qh[bi].as<QEntry>();
-        a.ch_in = mode == kPush ? &ctr[t].y : nullptr;
+        a.ch_in = &ctr[t].y;
         a.ql_out = sk->ql[bo].as<QEntry>();
         a.cl_out = &ctr[t + 1].x;
         a.qh_out = sk->qh[bo].as<QEntry>();
@@ -802,14 +865,14 @@ static im_status run_levels(im_sketch* sk, int mode, bool all_first) {
             a.ql_prev = sk->ql[bp].as<QEntry>();
             a.cl_prev = &ctr[t - 1].x;
             a.qh_prev = sk->qh[bp].as<QEntry>();
-            a.ch_prev = mode == kPush ? &ctr[t - 1].y : nullptr;
-            a.chg_prev = sk->chg[bp].as<uint32_t>();
+            a.ch_prev = &ctr[t - 1].y;
+            a.chg_prev = chg_buf(sk, mode, bp).as<uint32_t>();
         } else {
             a.ql_prev = nullptr; a.cl_prev = nullptr; a.qh_prev = nullptr; a.ch_prev = nullptr;
             a.chg_prev = nullptr;
         }
-        a.chg_cur = sk->chg[bi].as<uint32_t>();
-        a.chg_next = sk->chg[bo].as<uint32_t>();
+        a.chg_cur = chg_buf(sk, mode, bi).as<uint32_t>();
+        a.chg_next = chg_buf(sk, mode, bo).as<uint32_t>();
         a.all_changed = (t == 0 && all_first) ? 1 : 0;
         a.claim = claim + t;
         a.gen_next = ++sk->gen_counter;
@@ -834,14 +897,14 @@ static im_status run_levels(im_sketch* sk, int mode, bool all_first) {
         a.ql_in = sk->ql[bi].as<QEntry>();
         a.cl_in = &ctr[t].x;
         a.qh_in = sk->qh[bi].as<QEntry>();
-        a.ch_in = mode == kPush ? &ctr[t].y : nullptr;
+        a.ch_in = &ctr[t].y;
         a.ql_prev = sk->ql[bp].as<QEntry>();
         a.cl_prev = &ctr[t - 1].x;
         a.qh_prev = sk->qh[bp].as<QEntry>();
-        a.ch_prev = mode == kPush ? &ctr[t - 1].y : nullptr;
-        a.chg_prev = sk->chg[bp].as<uint32_t>();
-        a.chg_cur = sk->chg[bi].as<uint32_t>();
-        a.chg_next = sk->chg[bo].as<uint32_t>();
+        a.ch_prev = &ctr[t - 1].y;
+        a.chg_prev = chg_buf(sk, mode, bp).as<uint32_t>();
+        a.chg_cur = chg_buf(sk, mode, bi).as<uint32_t>();
+        a.chg_next = chg_buf(sk, mode, bo).as<uint32_t>();
         a.all_changed = 0;
         a.claim = claim + t;
         a.gen_next = ++sk->gen_counter;
@@ -878,7 +941,9 @@ static im_status propagate(im_sketch* sk) {
     a.cl_out = &ctr[0].x;
     a.qh_out = sk->qh[0].as<QEntry>();
     a.ch_out = &ctr[0].y;
-    CK(c, timed(c, kTOther, [&] { return launch_init_queues(sk->kind, sk->dev, a, c->stream); }));
+    // bucket mode: level 0 walks every bucket, no queue
+    if (!sk->buckets)
+        CK(c, timed(c, kTOther, [&] { return launch_init_queues(sk->kind, sk->dev, a, c->stream); }));
     return run_levels(sk, kPush, true);
 }
 
@@ -930,8 +995,112 @@ static im_status stats_collect(im_sketch* sk) {
     // 4-byte word per CAS write
     const uint64_t t = sk->kind == kExplicit ? 4 : 0;
     const uint64_t lw = sk->J > 512 ? 8 : 4;
-    s.alg_bytes_sweep = s.sweep_vertices * (16 + (uint64_t)sk->J) + s.sweep_edges * lw +
-                        s.sweep_edges_live * (8 + t) + s.sweep_chunks * 32 + s.sweep_cas * 4;
+    if (sk->buckets)
+        // bucket mode: per queued bucket its 16-byte entry; per processed
+        // list entry its endpoint and live mask (6 B), the source and target
+        // 16-byte register pieces and the target bucket's bounds (8 B); per
+        // CAS 4 B
+        s.alg_bytes_sweep = s.sweep_vertices * 16 + s.sweep_dealt * (6 + 32 + 8) + s.sweep_cas * 4;
+    else
+        s.alg_bytes_sweep = s.sweep_vertices * (16 + (uint64_t)sk->J) + s.sweep_edges * lw +
+                            s.sweep_edges_live * (8 + t) + s.sweep_chunks * 32 + s.sweep_cas * 4;
+    return IM_OK;
+}
+
+// Edge-scan mode: vertex queues and the live chunk masks of every edge.
+static im_status build_scan_mode(im_sketch* sk) {
+    im_ctx* c = sk->ctx;
+    const int32_t J = sk->J;
+    BufPlan plan;
+    scan_plan(sk, sk->g->n, sk->g->m, J, plan);
+    for (auto& [b, bytes] : plan) CKS(dalloc(c, bytes, *b));
+    for (int mode : {kPush, kCover}) {
+        const bool in = mode == kPush;
+        CK(c, timed(c, kTOther, [&] {
+            return launch_live_chunks(sk->kind, mode, sk->dev, sk->X.as<uint32_t>(), sk->tab.as<uint16_t>(), J,
+                                      (in ? sk->lcm_in_lo : sk->lcm_out_lo).as<uint32_t>(),
+                                      J > 512 ? (in ? sk->lcm_in_hi : sk->lcm_out_hi).as<uint32_t>() : nullptr,
+                                      c->stream);
+        }));
+    }
+    return IM_OK;
+}
+
+// Bucket mode: count bucket sizes, scan, place every live (edge, chunk)
+// entry; bucket queues of bq_cap entries.  Leaves sk->buckets false (and
+// nothing allocated) when the lists would exceed their memory bound.
+static im_status build_buckets(im_sketch* sk) {
+    im_ctx* c = sk->ctx;
+    auto st = c->stream;
+    const int32_t n = sk->g->n, J = sk->J, C = J / 16;
+    const int64_t m = sk->g->m;
+    const int64_t nb = (int64_t)n * C;
+    if (nb + 1 > 0x7FFFFFFF || m == 0) return IM_OK;
+    DBuf tmp, ne;
+    auto drop = [&]() {
+        dfree(c, tmp);
+        dfree(c, ne);
+        for (int o = 0; o < 2; ++o)
+            for (DBuf* b : {&sk->bk_end[o], &sk->bk_other[o], &sk->bk_mask[o]}) dfree(c, *b);
+        (void)cudaGetLastError();
+    };
+    im_status s = IM_OK;
+    for (int o = 0; o < 2 && s == IM_OK; ++o) s = dalloc(c, (size_t)(nb + 1) * 4, sk->bk_end[o]);
+    if (s == IM_OK) s = dalloc(c, scan_tmp_bytes((int32_t)nb), tmp);
+    if (s == IM_OK) s = dalloc(c, 16, ne);
+    if (s != IM_OK) { drop(); return IM_OK; }  // no room: edge scans
+    cudaError_t e = cudaMemsetAsync(ne.p, 0, 16, st);
+    for (int o = 0; o < 2 && e == cudaSuccess; ++o) {
+        e = cudaMemsetAsync(sk->bk_end[o].p, 0, sk->bk_end[o].bytes, st);
+        if (e == cudaSuccess)
+            e = timed(c, kTOther, [&] {
+                return launch_buckets(0, sk->kind, o == 0 ? kPush : kCover, sk->dev, sk->X.as<uint32_t>(),
+                                      sk->tab.as<uint16_t>(), J, sk->bk_end[o].as<uint32_t>(),
+                                      ne.as<unsigned long long>() + o, nullptr, nullptr, st);
+            });
+    }
+    int64_t total[2] = {0, 0};
+    unsigned long long nonempty[2] = {0, 0};
+    for (int o = 0; o < 2 && e == cudaSuccess; ++o) {
+        int32_t* cnt = reinterpret_cast<int32_t*>(sk->bk_end[o].p);
+        e = launch_exclusive_scan(cnt, (int32_t)nb, cnt, tmp.p, st);
+        // the scan's 64-bit total is the last tile-sum slot
+        const size_t slots = scan_tmp_bytes((int32_t)nb) / 8;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&total[o], tmp.as<int64_t>() + slots - 1, 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(nonempty, ne.p, 16, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { drop(); return cuda_fail(c, e, "bucket count"); }
+    for (int o = 0; o < 2; ++o)
+        if (total[o] > kBucketEntriesPerEdge * m || total[o] >= 0x7FFFFFFF) { drop(); return IM_OK; }
+    for (int o = 0; o < 2 && s == IM_OK; ++o) {
+        s = dalloc(c, (size_t)std::max<int64_t>(total[o], 1) * 4, sk->bk_other[o]);
+        if (s == IM_OK) s = dalloc(c, (size_t)std::max<int64_t>(total[o], 1) * 2, sk->bk_mask[o]);
+    }
+    if (s != IM_OK) { drop(); return IM_OK; }
+    for (int o = 0; o < 2 && e == cudaSuccess; ++o)
+        e = timed(c, kTOther, [&] {
+            return launch_buckets(1, sk->kind, o == 0 ? kPush : kCover, sk->dev, sk->X.as<uint32_t>(),
+                                  sk->tab.as<uint16_t>(), J, sk->bk_end[o].as<uint32_t>(), nullptr,
+                                  sk->bk_other[o].as<int32_t>(), sk->bk_mask[o].as<uint16_t>(), st);
+        });
+    if (e != cudaSuccess) { drop(); return cuda_fail(c, e, "bucket fill"); }
+    dfree(c, tmp);
+    dfree(c, ne);
+    const int64_t most = (int64_t)std::max(nonempty[0], nonempty[1]);
+    const int64_t cap = std::max<int64_t>(1, std::min(bucket_queue_cap(n), most));
+    for (int i = 0; i < 3 && s == IM_OK; ++i) s = dalloc(c, (size_t)cap * sizeof(QEntry), sk->ql[i]);
+    for (int i = 0; i < 3 && s == IM_OK; ++i) s = dalloc(c, sk->chg[i].bytes, sk->chg_cov[i]);
+    if (s != IM_OK) {
+        for (int i = 0; i < 3; ++i) { dfree(c, sk->ql[i]); dfree(c, sk->chg_cov[i]); }
+        drop();
+        return IM_OK;
+    }
+    sk->chg_dirty = true;  // the new buffers start zeroed by the next phase
+    sk->bq_cap = (int32_t)cap;
+    sk->buckets = true;
     return IM_OK;
 }
 
@@ -949,20 +1118,18 @@ static im_status sketch_start(im_ctx* c, im_graph* g, int32_t J, uint64_t seed, 
         return launch_sims(seed, J, sk->X.as<uint32_t>(), sk->salt.as<uint32_t>(),
                            sk->tab.as<uint16_t>(), c->stream);
     });
-    for (int mode : {kPush, kCover}) {
-        if (e != cudaSuccess) break;
-        const bool in = mode == kPush;
-        e = timed(c, kTOther, [&] {
-            return launch_live_chunks(sk->kind, mode, sk->dev, sk->X.as<uint32_t>(), sk->tab.as<uint16_t>(), J,
-                                      (in ? sk->lcm_in_lo : sk->lcm_out_lo).as<uint32_t>(),
-                                      J > 512 ? (in ? sk->lcm_in_hi : sk->lcm_out_hi).as<uint32_t>() : nullptr,
-                                      c->stream);
-        });
-    }
     if (e != cudaSuccess) {
         sketch_release(sk);
         delete sk;
         return cuda_fail(c, e, "sketch setup");
+    }
+    im_status s = IM_OK;
+    if (c->tuning.buckets) s = build_buckets(sk);
+    if (s == IM_OK && !sk->buckets) s = build_scan_mode(sk);
+    if (s != IM_OK) {
+        sketch_release(sk);
+        delete sk;
+        return s;
     }
     *out = sk;
     return IM_OK;
@@ -1055,9 +1222,11 @@ static PickArgs pick_args(im_sketch* sk, int k) {
     a.rp_out = sk->g->rp_out.as<int32_t>();
     a.q_cover = sk->ql[0].as<QEntry>();
     a.ctr_cover = &sk->ctr.as<ulonglong2>()[0].x;
-    a.chg0 = sk->chg[0].as<uint32_t>();
+    a.chg0 = chg_buf(sk, kCover, 0).as<uint32_t>();
     a.count = sk->count.as<unsigned long long>();
     a.mark = 1;
+    a.bk_end_out = sk->buckets ? sk->bk_end[1].as<uint32_t>() : nullptr;
+    a.chunks = sk->J / 16;
     return a;
 }
 
@@ -1110,7 +1279,8 @@ extern "C" im_status im_sketch_cover(im_sketch* sk, int32_t s, uint64_t* count_o
     CKS(phase_begin(sk));
     CK(c, launch_cover_seed(sk->M.as<uint8_t>(), sk->J, s, sk->g->rp_out.as<int32_t>(),
                             sk->ql[0].as<QEntry>(), &sk->ctr.as<ulonglong2>()[0].x,
-                            sk->chg[0].as<uint32_t>(), sk->count.as<unsigned long long>(), c->stream));
+                            chg_buf(sk, kCover, 0).as<uint32_t>(), sk->count.as<unsigned long long>(),
+                            sk->buckets ? sk->bk_end[1].as<uint32_t>() : nullptr, sk->J / 16, c->stream));
     CKS(run_levels(sk, kCover, false));
     if (count_out) {
         unsigned long long cnt = 0;
@@ -1238,6 +1408,11 @@ uint64_t query_bytes(const im_graph* g, int32_t J, int32_t K) {
     sketch_plan(&probe, g->n, g->m, J, plan);
     uint64_t total = 0;
     for (auto& pb : plan) total += round_bytes(pb.second);
+    BufPlan scan;
+    scan_plan(&probe, g->n, g->m, J, scan);
+    uint64_t scan_bytes = 0;
+    for (auto& pb : scan) scan_bytes += round_bytes(pb.second);
+    total += std::max(scan_bytes, bucket_reserve_bytes(g->n, g->m, J));
     const size_t cap = (size_t)out_cap_for(K);
     total += round_bytes(cap * 4) + 2 * round_bytes(cap * 8);
     return total;
@@ -1570,9 +1745,11 @@ extern "C" im_status im_batch_select_seeds(im_batch* b, const int32_t* J, const 
             pa.rp_out = b->g->rp_out.as<int32_t>();
             pa.q_cover = sk->ql[0].as<QEntry>();
             pa.ctr_cover = &sk->ctr.as<ulonglong2>()[0].x;
-            pa.chg0 = sk->chg[0].as<uint32_t>();
+            pa.chg0 = chg_buf(sk, kCover, 0).as<uint32_t>();
             pa.gcount = sk->gcount;
             pa.err = sk->err.as<uint32_t>();
+            pa.bk_end_out = sk->buckets ? sk->bk_end[1].as<uint32_t>() : nullptr;
+            pa.chunks = Jg / 16;
             e = timed(c, kTPick, [&] { return launch_batch_pick(pa, st); });
             if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "batch pick"); }
             if ((s = run_levels(sk, kCover, false)) != IM_OK) { cleanup(); return s; }

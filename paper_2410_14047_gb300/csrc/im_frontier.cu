@@ -531,6 +531,239 @@ __device__ __forceinline__ void heavy_vertex(const GraphDev& g, const LevelArgs&
     }
 }
 
+// ---------------------------------------------------------------------------
+// Bucket mode.  A level's work is a set of buckets (v, chunk c) whose 16
+// change bits are set; a bucket's entries are exactly the edges of v live in
+// a simulation of c, with their live masks, so no edge is visited for a chunk
+// that did not change and no live test runs.  Flat positions walk the queue's
+// buckets (offsets from the packed counter), or, on a level that walks every
+// bucket (level 0 of a build, or a queue that overflowed), the entry array
+// itself.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t bucket_start(const uint32_t* __restrict__ end, int64_t b) {
+    return b > 0 ? __ldcg(end + b - 1) : 0u;
+}
+
+// Last bucket r in [lo, hi) with start(r) <= f (start(lo) <= f), warp-wide.
+__device__ __forceinline__ int64_t bucket_of_warp(const uint32_t* __restrict__ end, int64_t lo, int64_t hi,
+                                                  int64_t f) {
+    const int lane = (int)lane_id();
+    while (hi - lo > 1) {
+        const int64_t step = (hi - lo + 31) >> 5;
+        const int64_t idx = lo + step * (lane + 1);
+        const bool le = idx < hi && (int64_t)bucket_start(end, idx) <= f;
+        const int c = __popc(__ballot_sync(0xFFFFFFFFu, le));
+        const int64_t nlo = lo + step * c;
+        const int64_t nhi = (c < 32) ? min(hi, lo + step * (c + 1)) : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int64_t bucket_of_thread(const uint32_t* __restrict__ end, int64_t lo, int64_t hi,
+                                                    int64_t f) {
+    while (hi - lo > 1) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if ((int64_t)bucket_start(end, mid) <= f) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Warp-aggregated append of buckets; a full queue raises its level's
+// overflow word instead (the next level then walks every bucket).
+__device__ __forceinline__ void bucket_append(bool want, uint32_t b, uint32_t start, uint32_t len,
+                                              QEntry* __restrict__ q, unsigned long long* ctr,
+                                              unsigned long long* overflow, int32_t cap) {
+    const unsigned wm = __ballot_sync(0xFFFFFFFFu, want);
+    if (wm == 0u) return;
+    const int lane = (int)lane_id();
+    const int d = want ? (int)len : 0;
+    int incl = d;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, s);
+        if (lane >= s) incl += y;
+    }
+    const int totd = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    unsigned long long base = ~0ull;
+    if (lane == 0) {
+        // a queue already at capacity is not grown further (its count field
+        // stays far from overflowing)
+        if ((int32_t)(__ldcg(ctr) >> kCountShift) < cap)
+            base = atomicAdd(ctr, ((unsigned long long)__popc(wm) << kCountShift) | (unsigned long long)totd);
+        else
+            atomicOr(overflow, 1ull);
+    }
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (base == ~0ull || !want) return;
+    const int32_t slot = (int32_t)(base >> kCountShift) + __popc(wm & ((1u << lane) - 1u));
+    if (slot < cap) {
+        QEntry e;
+        e.v = (int32_t)b;
+        e.rp = (int32_t)start;
+        e.off = (int32_t)(base & kEdgeMask) + (incl - d);
+        e.aux = len;
+        q[slot] = e;
+    } else {
+        atomicOr(overflow, 1ull);
+    }
+}
+
+// One bucket-mode unit: flat positions [b0*32, b1*32) of the level's walk.
+template <int KIND, int MODE>
+__device__ __forceinline__ void bucket_slice(const GraphDev& g, const LevelArgs& a, const QEntry* __restrict__ qlin,
+                                             int64_t b0, int64_t b1, int32_t nq, int64_t E, bool dense,
+                                             unsigned long long& st_chunks, unsigned long long& st_cas,
+                                             unsigned long long& st_new, unsigned long long& st_batches,
+                                             unsigned long long& st_dealt) {
+    const int lane = (int)lane_id();
+    const int J = a.J, words = a.words;
+    const uint32_t C = (uint32_t)a.chunks;
+    const int64_t nb = a.nbuckets;
+    const uint16_t* chg16 = reinterpret_cast<const uint16_t*>(a.chg_cur);
+    const int64_t fend = min(E, b1 << 5);
+    int64_t f0 = b0 << 5;
+    int32_t qi = 0;
+    int4 raw = make_int4(0, 0, 0x7FFFFFFF, 0);
+    int64_t bk0 = 0;
+    if (!dense) {
+        qi = covering_entry(qlin, nq, f0);
+        if (qi + lane < nq) raw = __ldcg(reinterpret_cast<const int4*>(qlin) + qi + lane);
+    } else {
+        bk0 = bucket_of_warp(a.bk_end, 0, nb, f0);
+    }
+    for (; f0 < fend; f0 += 32) {
+        const int64_t f = f0 + lane;
+        uint32_t bkt = 0u;
+        int64_t e = f;
+        uint32_t chb = 0u;
+        if (!dense) {
+            const int32_t wi = qi + lane;
+            const bool wvalid = wi < nq;
+            const int64_t rel = (int64_t)raw.z - f0;
+            const int c0 = __popc(__ballot_sync(0xFFFFFFFFu, wvalid && rel <= 0));
+            const unsigned starts =
+                __reduce_or_sync(0xFFFFFFFFu, (wvalid && rel >= 1 && rel <= 31) ? (1u << rel) : 0u);
+            const int myw = c0 - 1 + __popc(starts & ((2u << lane) - 1u));
+            // change bits of each window entry's chunk
+            uint32_t cwl = 0u;
+            if (wvalid && rel <= 31 && lane >= c0 - 1) {
+                const uint32_t bw = (uint32_t)raw.x;
+                cwl = chg16[(size_t)(bw / C) * words * 2 + (bw % C)];
+            }
+            bkt = (uint32_t)__shfl_sync(0xFFFFFFFFu, raw.x, myw);
+            const int32_t qrp = __shfl_sync(0xFFFFFFFFu, raw.y, myw);
+            const int32_t qoff = __shfl_sync(0xFFFFFFFFu, raw.z, myw);
+            chb = __shfl_sync(0xFFFFFFFFu, cwl, myw);
+            e = (int64_t)(uint32_t)qrp + (f - qoff);
+            // the window of the next batch: the entry covering f0 + 32
+            const int n32 = __popc(__ballot_sync(0xFFFFFFFFu, wvalid && rel <= 32));
+            int32_t qn = qi + n32 - 1;
+            if (n32 == 32 && qi + 32 < nq) {
+                if ((int64_t)__ldcg(&qlin[qi + 32].off) <= f0 + 32) qn = qi + 32;
+            }
+            int4 rawn = make_int4(0, 0, 0x7FFFFFFF, 0);
+            if (f0 + 32 < fend && qn + lane < nq) rawn = __ldcg(reinterpret_cast<const int4*>(qlin) + qn + lane);
+            qi = qn;
+            raw = rawn;
+        } else {
+            // windows of 32 bucket starts from bk0: a position takes the last
+            // bucket starting at or before it once a later start is known to
+            // exceed it; unresolved positions (a run of empty buckets) move
+            // on with the next window, 31 buckets further
+            int64_t base = bk0;
+            int64_t bf = bk0;
+            bool done = f >= fend;
+            for (;;) {
+                const int64_t bl = base + lane;
+                const uint32_t beg = bl < nb ? bucket_start(a.bk_end, bl) : 0xFFFFFFFFu;
+                const uint32_t b31 = __shfl_sync(0xFFFFFFFFu, beg, 31);
+                int i = 0;
+#pragma unroll
+                for (int s = 16; s >= 1; s >>= 1) {
+                    const uint32_t bb = __shfl_sync(0xFFFFFFFFu, beg, (i + s) & 31);
+                    if (i + s <= 31 && (int64_t)bb <= f) i += s;
+                }
+                uint32_t cwl = 0xFFFFu;
+                if (!a.all_changed && bl < nb) cwl = chg16[(size_t)(bl / C) * words * 2 + (bl % C)];
+                const uint32_t cw_i = __shfl_sync(0xFFFFFFFFu, cwl, i);
+                if (!done && (i < 31 || (int64_t)b31 > f || base + 32 >= nb)) {
+                    bf = base + i;
+                    chb = cw_i;
+                    done = true;
+                }
+                if (__all_sync(0xFFFFFFFFu, done)) break;
+                base += 31;
+            }
+            bkt = (uint32_t)bf;
+            bk0 = __shfl_sync(0xFFFFFFFFu, bf, 31);
+            if (a.gflag && chb) {
+                // a batch rebuild walks only the graphs whose rule fired
+                if (!__ldg(a.gflag + __ldg(a.gid + bkt / C))) chb = 0u;
+            }
+        }
+        if (lane == 0) ++st_batches;
+        const uint32_t u = bkt / C, c = bkt % C;
+        uint32_t nbits = 0u;
+        int32_t o = 0;
+        uint32_t ob = 0u, ostart = 0u, oend = 0u;
+        if (f < fend && chb) {
+            ++st_dealt;
+            o = __ldg(a.bk_other + e);
+            const uint32_t m16 = __ldg(a.bk_mask + e) & chb;
+            const uint8_t* srow = a.M + (size_t)u * J + c * 16;
+            uint8_t* trow = a.M + (size_t)o * J + c * 16;
+            const uint4 src = ld_cg16(srow);
+            const uint4 tg = ld_cg16(trow);
+            ob = (uint32_t)o * C + c;
+            const uint32_t sw[4] = {src.x, src.y, src.z, src.w};
+            const uint32_t tw[4] = {tg.x, tg.y, tg.z, tg.w};
+            uint32_t cand[4];
+            uint32_t any = 0u;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const uint32_t L = bits_to_bytes((m16 >> (4 * w)) & 0xFu);
+                if constexpr (MODE == kPush) cand[w] = sw[w] & L & ~visited_bytes(sw[w]);
+                else cand[w] = L & visited_bytes(sw[w]) & ~visited_bytes(tw[w]);
+                any |= cand[w];
+            }
+            if (any) {
+                ++st_chunks;
+                if constexpr (MODE == kPush) {
+                    nbits = merge_chunk(trow, cand, tg, st_cas, a.err);
+                } else {
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        if (cand[w] == 0u) continue;
+                        const uint32_t prev = atomicOr(reinterpret_cast<unsigned int*>(trow + 4 * w), cand[w]);
+                        const uint32_t really = cand[w] & ~visited_bytes(prev);
+                        if (really) {
+                            nbits |= bytes_to_bits(really) << (4 * w);
+                            st_new += (unsigned)(__popc(really) >> 3);
+                            if (a.gcount)
+                                atomicAdd(a.gcount + __ldg(a.gid + o), (unsigned long long)(__popc(really) >> 3));
+                        }
+                    }
+                }
+            }
+        }
+        // enqueue the target's bucket on the first change of its chunk this
+        // level (the returned change bits tell; the bucket's bounds are read
+        // meanwhile).  An empty bucket is never queued: its change bits are
+        // never read, and a later level only needs them for non-empty ones.
+        bool want = false;
+        if (nbits) {
+            const uint32_t sh = (c & 1u) * 16u;
+            oend = __ldcg(a.bk_end + ob);
+            ostart = bucket_start(a.bk_end, ob);
+            const uint32_t old = atomicOr(a.chg_next + (size_t)o * words + (c >> 1), nbits << sh);
+            want = ((old >> sh) & 0xFFFFu) == 0u && oend > ostart;
+        }
+        bucket_append(want, ob, ostart, oend - ostart, a.ql_out, a.cl_out, a.ch_out, a.bq_cap);
+    }
+}
+
 struct LevelStats {
     unsigned long long chunks = 0, cas = 0, fresh = 0, hsims = 0, batches = 0, dealt = 0, live = 0;
 };
@@ -540,6 +773,23 @@ __device__ __forceinline__ void clear_prev_bits(const LevelArgs& a, int64_t warp
     if (!a.chg_prev) return;
     const int lane = (int)lane_id();
     const int32_t nlp = a.cl_prev ? (int32_t)(__ldcg(a.cl_prev) >> kCountShift) : 0;
+    if (a.bk_end) {
+        // bucket queue: each entry owns the 16 change bits of its chunk; a
+        // queue that overflowed (its level walked every bucket) clears all
+        const bool overflow = nlp > a.bq_cap || (a.ch_prev && __ldcg(a.ch_prev) != 0ull);
+        if (overflow) {
+            const int64_t nw = (int64_t)a.nbuckets / a.chunks * a.words;
+            for (int64_t i = warp * 32 + lane; i < nw; i += nwarps * 32) a.chg_prev[i] = 0u;
+            return;
+        }
+        uint16_t* h16 = reinterpret_cast<uint16_t*>(a.chg_prev);
+        for (int64_t i = warp * 32 + lane; i < nlp; i += nwarps * 32) {
+            const uint32_t b = (uint32_t)__ldcg(&a.ql_prev[i].v);
+            const uint32_t u = b / (uint32_t)a.chunks, c = b % (uint32_t)a.chunks;
+            h16[(size_t)u * a.words * 2 + c] = 0;
+        }
+        return;
+    }
     const int32_t nhp = a.ch_prev ? (int32_t)(__ldcg(a.ch_prev) >> kCountShift) : 0;
     for (int64_t i = warp; i < (int64_t)nlp + nhp; i += nwarps) {
         const int32_t v = i < nlp ? __ldcg(&a.ql_prev[i].v) : __ldcg(&a.qh_prev[i - nlp].v);
@@ -556,6 +806,34 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
     const int lane = (int)lane_id();
     const unsigned long long cl = __ldcg(a.cl_in);
     const unsigned long long ch = a.ch_in ? __ldcg(a.ch_in) : 0ull;
+    if (a.bk_end) {
+        // bucket mode: the queue's buckets, or every bucket when the level is
+        // level 0 of a build or its queue overflowed (ch = overflow word)
+        const int32_t nq = (int32_t)(cl >> kCountShift);
+        const bool dense = a.all_changed || nq > a.bq_cap || ch != 0ull;
+        const int64_t E = dense ? (int64_t)__ldcg(a.bk_end + a.nbuckets - 1) : (int64_t)(cl & kEdgeMask);
+        const int64_t nbl = (E + 31) >> 5;
+        const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        const int64_t lb = max((int64_t)1, min((int64_t)a.light_batches, nbl / nwarps));
+        const int64_t units = (nbl + lb - 1) / lb;
+        if (units == 0) return;
+        if (warp == 0 && lane == 0) {
+            atomicAdd(a.stats + (MODE == kPush ? kStSweepVertices : kStCoverVertices), (unsigned long long)nq);
+            atomicAdd(a.stats + (MODE == kPush ? kStSweepEdges : kStCoverEdges), (unsigned long long)E);
+            atomicAdd(a.stats + (MODE == kPush ? kStSweepLevels : kStCoverLevels), 1ull);
+        }
+        for (;;) {
+            unsigned int unit = 0;
+            if (lane == 0) unit = atomicAdd(a.claim, 1u);
+            unit = __shfl_sync(0xFFFFFFFFu, unit, 0);
+            if ((int64_t)unit >= units) break;
+            const int64_t b0 = (int64_t)unit * lb;
+            const int64_t b1 = min(nbl, b0 + lb);
+            bucket_slice<KIND, MODE>(g, a, a.ql_in, b0, b1, nq, E, dense, ls.chunks, ls.cas, ls.fresh,
+                                     ls.batches, ls.dealt);
+        }
+        return;
+    }
     int32_t nl = (int32_t)(cl >> kCountShift);
     int64_t El = (int64_t)(cl & kEdgeMask);
     int32_t nh = (int32_t)(ch >> kCountShift);
@@ -666,7 +944,7 @@ __global__ void __launch_bounds__(kFBlock, kLevelMinBlocks) k_level(GraphDev g, 
     clear_prev_bits(a, warp, nwarps);
     const unsigned long long cl = __ldcg(a.cl_in);
     const unsigned long long ch = a.ch_in ? __ldcg(a.ch_in) : 0ull;
-    if ((cl >> kCountShift) == 0 && (ch >> kCountShift) == 0) return;
+    if ((cl >> kCountShift) == 0 && (ch >> kCountShift) == 0 && !a.all_changed) return;
     load_tables(a, sX, sTab);
     LevelStats ls;
     level_work<KIND, MODE>(g, a, sX, sTab, warp, ls, sKeep[threadIdx.x >> 5]);
@@ -736,7 +1014,7 @@ __global__ void __launch_bounds__(kFBlock, kPhaseMinBlocks) k_phase(GraphDev g, 
         a.ql_in = p.ql[bi];
         a.cl_in = &p.ctr[t].x;
         a.qh_in = p.qh[bi];
-        a.ch_in = MODE == kPush ? &p.ctr[t].y : nullptr;
+        a.ch_in = &p.ctr[t].y;
         a.ql_out = p.ql[bo];
         a.cl_out = &p.ctr[t + 1].x;
         a.qh_out = p.qh[bo];
@@ -745,7 +1023,7 @@ __global__ void __launch_bounds__(kFBlock, kPhaseMinBlocks) k_phase(GraphDev g, 
             a.ql_prev = p.ql[bp];
             a.cl_prev = &p.ctr[t - 1].x;
             a.qh_prev = p.qh[bp];
-            a.ch_prev = MODE == kPush ? &p.ctr[t - 1].y : nullptr;
+            a.ch_prev = &p.ctr[t - 1].y;
             a.chg_prev = p.chg[bp];
         } else {
             a.ql_prev = nullptr; a.cl_prev = nullptr; a.qh_prev = nullptr; a.ch_prev = nullptr;
@@ -772,7 +1050,7 @@ __global__ void __launch_bounds__(kFBlock, kPhaseMinBlocks) k_phase(GraphDev g, 
         a.ql_prev = p.ql[bl];
         a.cl_prev = &p.ctr[t - 1].x;
         a.qh_prev = p.qh[bl];
-        a.ch_prev = MODE == kPush ? &p.ctr[t - 1].y : nullptr;
+        a.ch_prev = &p.ctr[t - 1].y;
         a.chg_prev = p.chg[bl];
         clear_prev_bits(a, warp, nwarps);
     }
@@ -899,25 +1177,38 @@ __device__ __forceinline__ int32_t row_of_thread(const int32_t* __restrict__ rp,
     return lo;
 }
 
-template <int KIND, int MODE>
-__global__ void __launch_bounds__(kFBlock) k_live_chunks(GraphDev g, const uint32_t* __restrict__ X,
-                                                         const uint16_t* __restrict__ tab, int J,
-                                                         uint32_t* __restrict__ lo_out,
-                                                         uint32_t* __restrict__ hi_out) {
-    __shared__ __align__(16) uint32_t sX[kMaxJ];
-    __shared__ uint16_t sTab[kTabSize];
-    for (int i = threadIdx.x; i < J; i += blockDim.x) sX[i] = __ldg(X + i);
-    for (int i = threadIdx.x; i < kTabSize; i += blockDim.x) sTab[i] = __ldg(tab + i);
-    __syncthreads();
+// Live masks of one edge over every chunk that holds a candidate simulation:
+// fn(c, m16) for each chunk c with m16 != 0 (bit i: simulation 16c + i live).
+template <class F>
+__device__ __forceinline__ void edge_chunk_masks(uint32_t h, uint32_t thr, int J, const uint32_t* sX,
+                                                 const uint16_t* sTab, F&& fn) {
+    if (thr >= 0x80000000u) {
+        for (int c = 0; c < (J >> 4); ++c) fn(c, 0xFFFFu);
+        return;
+    }
+    if (thr == 0u) return;
+    int lo, hi;
+    candidate_range(h, thr, J, sX, sTab, lo, hi);
+    for (int c = lo >> 4; hi > lo && c <= ((hi - 1) >> 4); ++c) {
+        uint32_t m16 = 0u;
+        const int j1 = min(hi, 16 * c + 16);
+        for (int j = max(lo, 16 * c); j < j1; ++j)
+            if ((sX[j] ^ h) < thr) m16 |= 1u << (j - 16 * c);
+        if (m16) fn(c, m16);
+    }
+}
+
+// Every edge of one CSR orientation with its row (the owner vertex), the
+// other endpoint, hash and threshold, edge-balanced over warps:
+// fn(e, row, other, h, thr) once per edge.
+template <int KIND, int MODE, class F>
+__device__ __forceinline__ void for_each_edge(const GraphDev& g, F&& fn) {
     const int lane = (int)lane_id();
     const int32_t* rp = MODE == kPush ? g.rp_in : g.rp_out;
     const int64_t m = g.m;
     const int32_t n = g.n;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int nchunks = J >> 4;
-    const uint32_t all_lo = nchunks >= 32 ? 0xFFFFFFFFu : ((1u << nchunks) - 1u);
-    const uint32_t all_hi = nchunks > 32 ? 0xFFFFFFFFu : 0u;
     for (int64_t s0 = warp * kLcmEdgesPerWarp; s0 < m; s0 += nwarps * kLcmEdgesPerWarp) {
         const int64_t s1 = min(m, s0 + kLcmEdgesPerWarp);
         int32_t r0 = row_of_warp(rp, 0, n, s0);
@@ -940,38 +1231,72 @@ __global__ void __launch_bounds__(kFBlock) k_live_chunks(GraphDev g, const uint3
             r0 = __shfl_sync(0xFFFFFFFFu, v, 31);
             if (e >= s1) continue;
             uint32_t h, thr;
+            int32_t other;
             if constexpr (MODE == kPush) {
-                const int32_t u = __ldg(g.src_in + e);
+                other = __ldg(g.src_in + e);
                 h = __ldg(g.h_in + e);
                 const uint32_t aux = KIND == kWC ? __ldg(g.thr_v + v) : 0u;
-                thr = edge_threshold<KIND, true>(g, (uint32_t)u, (uint32_t)v, e, aux);
+                thr = edge_threshold<KIND, true>(g, (uint32_t)other, (uint32_t)v, e, aux);
             } else {
-                const int32_t w = __ldg(g.col_out + e);
+                other = __ldg(g.col_out + e);
                 h = __ldg(g.h_out + e);
-                thr = edge_threshold<KIND, false>(g, (uint32_t)v, (uint32_t)w, e, 0u);
+                thr = edge_threshold<KIND, false>(g, (uint32_t)v, (uint32_t)other, e, 0u);
             }
-            uint32_t mlo = 0u, mhi = 0u;
-            if (thr >= 0x80000000u) {
-                mlo = all_lo;
-                mhi = all_hi;
-            } else if (thr > 0u) {
-                int lo, hi;
-                candidate_range(h, thr, J, sX, sTab, lo, hi);
-                for (int c = lo >> 4; hi > lo && c <= ((hi - 1) >> 4); ++c) {
-                    const int j1 = min(hi, 16 * c + 16);
-                    for (int j = max(lo, 16 * c); j < j1; ++j) {
-                        if ((sX[j] ^ h) < thr) {
-                            if (c < 32) mlo |= 1u << c;
-                            else mhi |= 1u << (c - 32);
-                            break;
-                        }
-                    }
-                }
-            }
-            lo_out[e] = mlo;
-            if (hi_out) hi_out[e] = mhi;
+            fn(e, v, other, h, thr);
         }
     }
+}
+
+__device__ __forceinline__ void load_sims(const uint32_t* X, const uint16_t* tab, int J, uint32_t* sX,
+                                          uint16_t* sTab) {
+    for (int i = threadIdx.x; i < J; i += blockDim.x) sX[i] = __ldg(X + i);
+    for (int i = threadIdx.x; i < kTabSize; i += blockDim.x) sTab[i] = __ldg(tab + i);
+    __syncthreads();
+}
+
+template <int KIND, int MODE>
+__global__ void __launch_bounds__(kFBlock) k_live_chunks(GraphDev g, const uint32_t* __restrict__ X,
+                                                         const uint16_t* __restrict__ tab, int J,
+                                                         uint32_t* __restrict__ lo_out,
+                                                         uint32_t* __restrict__ hi_out) {
+    __shared__ __align__(16) uint32_t sX[kMaxJ];
+    __shared__ uint16_t sTab[kTabSize];
+    load_sims(X, tab, J, sX, sTab);
+    for_each_edge<KIND, MODE>(g, [&](int64_t e, int32_t, int32_t, uint32_t h, uint32_t thr) {
+        uint32_t mlo = 0u, mhi = 0u;
+        edge_chunk_masks(h, thr, J, sX, sTab, [&](int c, uint32_t) {
+            if (c < 32) mlo |= 1u << c;
+            else mhi |= 1u << (c - 32);
+        });
+        lo_out[e] = mlo;
+        if (hi_out) hi_out[e] = mhi;
+    });
+}
+
+// Bucketed live lists: pass 0 counts, pass 1 places (see launch_buckets).
+template <int KIND, int MODE, int PASS>
+__global__ void __launch_bounds__(kFBlock) k_buckets(GraphDev g, const uint32_t* __restrict__ X,
+                                                     const uint16_t* __restrict__ tab, int J,
+                                                     uint32_t* __restrict__ cnt_or_end,
+                                                     unsigned long long* __restrict__ nonempty,
+                                                     int32_t* __restrict__ other_out,
+                                                     uint16_t* __restrict__ mask_out) {
+    __shared__ __align__(16) uint32_t sX[kMaxJ];
+    __shared__ uint16_t sTab[kTabSize];
+    load_sims(X, tab, J, sX, sTab);
+    const int C = J >> 4;
+    for_each_edge<KIND, MODE>(g, [&](int64_t, int32_t v, int32_t other, uint32_t h, uint32_t thr) {
+        edge_chunk_masks(h, thr, J, sX, sTab, [&](int c, uint32_t m16) {
+            const int64_t b = (int64_t)v * C + c;
+            if constexpr (PASS == 0) {
+                if (atomicAdd(cnt_or_end + b, 1u) == 0u) atomicAdd(nonempty, 1ull);
+            } else {
+                const uint32_t pos = atomicAdd(cnt_or_end + b, 1u);
+                other_out[pos] = other;
+                mask_out[pos] = (uint16_t)m16;
+            }
+        });
+    });
 }
 
 template <int MODE>
@@ -986,12 +1311,41 @@ static cudaError_t live_chunks_mode(int kind, const GraphDev& g, const uint32_t*
     return cudaGetLastError();
 }
 
+template <int MODE, int PASS>
+static cudaError_t buckets_mode(int kind, const GraphDev& g, const uint32_t* X, const uint16_t* tab, int J,
+                                uint32_t* ce, unsigned long long* ne, int32_t* other, uint16_t* mask, int grid,
+                                cudaStream_t st) {
+    switch (kind) {
+        case kUniform: k_buckets<kUniform, MODE, PASS><<<grid, kFBlock, 0, st>>>(g, X, tab, J, ce, ne, other, mask); break;
+        case kWC: k_buckets<kWC, MODE, PASS><<<grid, kFBlock, 0, st>>>(g, X, tab, J, ce, ne, other, mask); break;
+        case kTrivalency: k_buckets<kTrivalency, MODE, PASS><<<grid, kFBlock, 0, st>>>(g, X, tab, J, ce, ne, other, mask); break;
+        default: k_buckets<kExplicit, MODE, PASS><<<grid, kFBlock, 0, st>>>(g, X, tab, J, ce, ne, other, mask); break;
+    }
+    return cudaGetLastError();
+}
+
+static int edge_walk_grid(const GraphDev& g) {
+    const int64_t groups = (g.m + kLcmEdgesPerWarp - 1) / kLcmEdgesPerWarp;
+    const int64_t want = (groups + (kFBlock / 32) - 1) / (kFBlock / 32);
+    return (int)max((int64_t)1, min(want, (int64_t)level_grid()));
+}
+
+cudaError_t launch_buckets(int pass, int kind, int mode, const GraphDev& g, const uint32_t* X,
+                           const uint16_t* tab, int J, uint32_t* cnt_or_end, unsigned long long* nonempty,
+                           int32_t* other, uint16_t* mask, cudaStream_t st) {
+    if (g.m == 0) return cudaSuccess;
+    const int grid = edge_walk_grid(g);
+    if (mode == kPush)
+        return pass == 0 ? buckets_mode<kPush, 0>(kind, g, X, tab, J, cnt_or_end, nonempty, other, mask, grid, st)
+                         : buckets_mode<kPush, 1>(kind, g, X, tab, J, cnt_or_end, nonempty, other, mask, grid, st);
+    return pass == 0 ? buckets_mode<kCover, 0>(kind, g, X, tab, J, cnt_or_end, nonempty, other, mask, grid, st)
+                     : buckets_mode<kCover, 1>(kind, g, X, tab, J, cnt_or_end, nonempty, other, mask, grid, st);
+}
+
 cudaError_t launch_live_chunks(int kind, int mode, const GraphDev& g, const uint32_t* X, const uint16_t* tab,
                                int J, uint32_t* lo, uint32_t* hi, cudaStream_t st) {
     if (g.m == 0) return cudaSuccess;
-    const int64_t groups = (g.m + kLcmEdgesPerWarp - 1) / kLcmEdgesPerWarp;
-    const int64_t want = (groups + (kFBlock / 32) - 1) / (kFBlock / 32);
-    const int grid = (int)max((int64_t)1, min(want, (int64_t)level_grid()));
+    const int grid = edge_walk_grid(g);
     return mode == kPush ? live_chunks_mode<kPush>(kind, g, X, tab, J, lo, hi, grid, st)
                          : live_chunks_mode<kCover>(kind, g, X, tab, J, lo, hi, grid, st);
 }

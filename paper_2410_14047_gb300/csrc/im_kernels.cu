@@ -209,9 +209,38 @@ __device__ __forceinline__ void lex_min(unsigned long long& S, int32_t& u, unsig
     if (oS < S || (oS == S && ou < u)) { S = oS; u = ou; }
 }
 
+// Bucket mode: queues the seed's out-buckets whose chunk has newly visited
+// simulations (level 0 of its cover); a chunk without live out-edges keeps
+// no change bits.  One thread; chg_row = the seed's change words.
+__device__ void cover_seed_buckets(int32_t s, uint32_t* chg_row, int C, const uint32_t* bk_end, QEntry* q,
+                                   unsigned long long* ctr) {
+    uint16_t* h16 = reinterpret_cast<uint16_t*>(chg_row);
+    uint32_t k = 0, len_sum = 0;
+    for (int c = 0; c < C; ++c) {
+        if (!h16[c]) continue;
+        const int64_t b = (int64_t)s * C + c;
+        const uint32_t st = b > 0 ? bk_end[b - 1] : 0u, en = bk_end[b];
+        if (en > st) { ++k; len_sum += en - st; }
+        else h16[c] = 0;
+    }
+    if (k == 0) return;
+    const unsigned long long base = atomicAdd(ctr, ((unsigned long long)k << kCountShift) | len_sum);
+    uint32_t slot = (uint32_t)(base >> kCountShift), off = (uint32_t)(base & kEdgeMask);
+    for (int c = 0; c < C; ++c) {
+        if (!h16[c]) continue;
+        const int64_t b = (int64_t)s * C + c;
+        const uint32_t st = b > 0 ? bk_end[b - 1] : 0u, en = bk_end[b];
+        QEntry e;
+        e.v = (int32_t)(uint32_t)b; e.rp = (int32_t)st; e.off = (int32_t)off; e.aux = en - st;
+        q[slot++] = e;
+        off += en - st;
+    }
+}
+
 // Marks row s visited and queues s as level 0 of a cover (one block).
 __device__ void cover_seed_block(uint8_t* M, int J, int32_t s, const int32_t* rp_out, QEntry* q,
-                                 unsigned long long* ctr, uint32_t* chg0, unsigned long long* count) {
+                                 unsigned long long* ctr, uint32_t* chg0, unsigned long long* count,
+                                 const uint32_t* bk_end = nullptr, int C = 0) {
     __shared__ unsigned int newly_sh;
     if (threadIdx.x == 0) newly_sh = 0;
     __syncthreads();
@@ -229,7 +258,12 @@ __device__ void cover_seed_block(uint8_t* M, int J, int32_t s, const int32_t* rp
     newly = (unsigned)warp_sum(newly);
     if (lane_id() == 0 && newly) atomicAdd(&newly_sh, newly);
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && bk_end) {
+        const unsigned int nw = newly_sh;
+        if (nw) atomicAdd(count, (unsigned long long)nw);
+        *ctr = 0ull;
+        if (nw) cover_seed_buckets(s, chg0 + (size_t)s * words, C, bk_end, q, ctr);
+    } else if (threadIdx.x == 0) {
         const unsigned int nw = newly_sh;
         if (nw) atomicAdd(count, (unsigned long long)nw);
         const int32_t rp = rp_out[s];
@@ -323,7 +357,7 @@ __device__ void pick_finish(const PickArgs& a, Top2 t) {
     }
     __syncthreads();
     if (fS == ~0ull || !a.mark) return;
-    cover_seed_block(a.M, a.J, fU, a.rp_out, a.q_cover, a.ctr_cover, a.chg0, a.count);
+    cover_seed_block(a.M, a.J, fU, a.rp_out, a.q_cover, a.ctr_cover, a.chg0, a.count, a.bk_end_out, a.chunks);
 }
 
 __device__ __forceinline__ bool is_picked(const uint32_t* seed_bits, int64_t v) {
@@ -434,14 +468,15 @@ cudaError_t launch_pick_lazy(const PickArgs& a, cudaStream_t st) {
 __global__ void __launch_bounds__(kBlock) k_cover_seed(uint8_t* M, int J, int32_t s,
                                                        const int32_t* rp_out, QEntry* q,
                                                        unsigned long long* ctr, uint32_t* chg0,
-                                                       unsigned long long* count) {
-    cover_seed_block(M, J, s, rp_out, q, ctr, chg0, count);
+                                                       unsigned long long* count, const uint32_t* bk_end,
+                                                       int C) {
+    cover_seed_block(M, J, s, rp_out, q, ctr, chg0, count, bk_end, C);
 }
 
 cudaError_t launch_cover_seed(uint8_t* M, int J, int32_t s, const int32_t* rp_out, QEntry* q,
                               unsigned long long* ctr, uint32_t* chg0, unsigned long long* count,
-                              cudaStream_t st) {
-    k_cover_seed<<<1, kBlock, 0, st>>>(M, J, s, rp_out, q, ctr, chg0, count);
+                              const uint32_t* bk_end, int C, cudaStream_t st) {
+    k_cover_seed<<<1, kBlock, 0, st>>>(M, J, s, rp_out, q, ctr, chg0, count, bk_end, C);
     return cudaGetLastError();
 }
 
@@ -549,6 +584,7 @@ __global__ void k_scan_sums(int64_t* tile_sums, int ntiles, int32_t* out_total_s
             run += s;
         }
         *out_total_slot = (int32_t)run;
+        tile_sums[ntiles] = run;  // the exact 64-bit total
     }
 }
 
@@ -1179,7 +1215,11 @@ __global__ void __launch_bounds__(kBlock) k_batch_graphs(BatchPickArgs a) {
     newly = (unsigned)warp_sum(newly);
     if (lane == 0 && newly) atomicAdd(&newly_sh, newly);
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && a.bk_end_out) {
+        const unsigned int nw = newly_sh;
+        if (nw) atomicAdd(a.gcount + g, (unsigned long long)nw);
+        if (nw) cover_seed_buckets(s, a.chg0 + (size_t)s * words, a.chunks, a.bk_end_out, a.q_cover, a.ctr_cover);
+    } else if (threadIdx.x == 0) {
         const unsigned int nw = newly_sh;
         if (nw) atomicAdd(a.gcount + g, (unsigned long long)nw);
         const int32_t rp = a.rp_out[s];

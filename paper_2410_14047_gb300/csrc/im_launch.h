@@ -78,6 +78,17 @@ struct LevelArgs {
     // (J = 1024, else NULL)
     const uint32_t* lcm_lo;
     const uint32_t* lcm_hi;
+    // bucketed live lists of the level's orientation (NULL bk_end: edge scan).
+    // Bucket b = v * chunks + c holds entries [start(b), end(b)), end(b) =
+    // bk_end[b], start(b) = b ? bk_end[b - 1] : 0: the other endpoint of
+    // every edge of v live in a simulation of chunk c, and its live mask over
+    // the chunk's 16 simulations.  Queue entries are buckets (v = b).
+    const uint32_t* bk_end;
+    const int32_t* bk_other;
+    const uint16_t* bk_mask;
+    int32_t chunks;
+    int64_t nbuckets;
+    int32_t bq_cap;                      // bucket queue capacity; a fuller level walks every bucket
 };
 
 // All levels of a phase in one cooperative launch (grid barrier between levels).
@@ -133,6 +144,10 @@ struct PickArgs {
     int32_t* cand;
     unsigned long long* part_S2;
     int32_t* part_u2;
+    // bucket mode: the cover's level-0 queue holds the seed's out-buckets
+    // (chunks with newly visited simulations and live out-edges)
+    const uint32_t* bk_end_out;
+    int32_t chunks;
 };
 
 int pick_grid(int32_t n, int J);
@@ -170,6 +185,8 @@ struct BatchPickArgs {
     uint32_t* chg0;
     unsigned long long* gcount;
     uint32_t* err;
+    const uint32_t* bk_end_out;   // bucket mode (see PickArgs)
+    int32_t chunks;
 };
 cudaError_t launch_batch_pick(const BatchPickArgs& a, cudaStream_t st);
 cudaError_t launch_pick(const PickArgs& a, cudaStream_t st);
@@ -177,6 +194,14 @@ cudaError_t launch_pick(const PickArgs& a, cudaStream_t st);
 // simulations X (sorted) of one sketch.
 cudaError_t launch_live_chunks(int kind, int mode, const GraphDev& g, const uint32_t* X, const uint16_t* tab,
                                int J, uint32_t* lo, uint32_t* hi, cudaStream_t st);
+// Bucketed live lists of one orientation (mode kPush: in-edges grouped by
+// target, kCover: out-edges grouped by source).  Pass 0 counts bucket sizes
+// into cnt[n * J/16] (zeroed by the caller) and non-empty buckets into
+// *nonempty; after an exclusive scan of cnt into end[] (end[nb] = total),
+// pass 1 fills other / mask and leaves end[b] = end of bucket b.
+cudaError_t launch_buckets(int pass, int kind, int mode, const GraphDev& g, const uint32_t* X,
+                           const uint16_t* tab, int J, uint32_t* cnt_or_end, unsigned long long* nonempty,
+                           int32_t* other, uint16_t* mask, cudaStream_t st);
 // Lazy pick: refreshes S_v of every unpicked v whose stored (lb[v], v) is
 // below (S_cand, cand) with S_cand fresh, then takes the least stored pair.
 cudaError_t launch_pick_lazy(const PickArgs& a, cudaStream_t st);
@@ -184,7 +209,7 @@ cudaError_t launch_pick_lazy(const PickArgs& a, cudaStream_t st);
 // queues s as level 0 of a cover.
 cudaError_t launch_cover_seed(uint8_t* M, int J, int32_t s, const int32_t* rp_out, QEntry* q,
                               unsigned long long* ctr, uint32_t* chg0, unsigned long long* count,
-                              cudaStream_t st);
+                              const uint32_t* bk_end, int C, cudaStream_t st);
 cudaError_t launch_sums(const uint8_t* M, int32_t n, int J, unsigned long long* S, cudaStream_t st);
 cudaError_t launch_count_visited(const uint8_t* M, int64_t bytes, unsigned long long* out,
                                  cudaStream_t st);
