@@ -115,6 +115,8 @@ typedef struct {
     uint64_t sweep_batches;   /* 32-edge batches resolved by propagation levels */
     uint64_t sweep_dealt;     /* 16-simulation chunk items dealt (before the live test) */
     uint64_t sweep_edges_live;/* examined in-edges live in a chunk where the source changed */
+    uint64_t sweep_buckets;   /* (vertex, chunk) buckets queued for propagation levels */
+    uint64_t sweep_bucket_entries; /* bucket list entries processed by propagation levels */
 } im_stats;
 
 /* Schedule knobs of the frontier kernels (chosen by the autotuner; results
@@ -132,10 +134,12 @@ typedef struct {
  * im_select_seeds, picks after the first recompute S_u only for the vertices
  * whose stored S_u (a lower bound: S_u never decreases during a selection)
  * could still beat the best candidate, 0 = every pick reads every row;
- * buckets: 1 = each sketch groups the live (edge, 16-simulation chunk) pairs
- * of every vertex by chunk with their live masks, and a level visits only the
- * groups whose chunk changed (falls back to edge scans when the groups would
- * exceed 4 entries per edge), 0 = edge scans with live chunk masks. */
+ * buckets: b > 0 = each sketch also groups the live (edge, 16-simulation
+ * chunk) pairs of every vertex by chunk, with their live masks (at most 4
+ * entries per edge, else edge scans only), and a level whose input work (edges
+ * or entries) times b is below m queues the changed (vertex, chunk) groups, so
+ * that the next level visits only the edges of changed chunks; 0 = edge scans
+ * with live chunk masks throughout. */
 typedef struct {
     int32_t heavy_indeg;
     int32_t light_batches;
@@ -177,7 +181,7 @@ IM_API im_status im_last_stats(const im_ctx* ctx, im_stats* out);
  * stream and report per-kind kernel time in im_stats (adds two event records
  * per launch).  Off by default. */
 IM_API im_status im_ctx_set_timing(im_ctx* ctx, int enable);
-/* Sets (NULL = defaults {256, 4, 0, 2, 1, 0, 1, 1}) or reads the schedule knobs. */
+/* Sets (NULL = defaults {256, 4, 0, 2, 1, 0, 1, 2}) or reads the schedule knobs. */
 IM_API im_status im_ctx_set_tuning(im_ctx* ctx, const im_tuning* tuning);
 IM_API im_status im_ctx_get_tuning(const im_ctx* ctx, im_tuning* tuning);
 /* enable != 0: also keep one im_trace_rec per frontier level (implies timing):

@@ -64,7 +64,8 @@ class im_stats(ctypes.Structure):
                                                "sweep_cas", "sweep_changed", "cover_edges",
                                                "cover_chunks", "visited", "alg_bytes_sweep",
                                                "sweep_heavy", "sweep_heavy_sims", "sweep_batches",
-                                               "sweep_dealt", "sweep_edges_live")]
+                                               "sweep_dealt", "sweep_edges_live", "sweep_buckets",
+                                               "sweep_bucket_entries")]
 
 
 class im_tuning(ctypes.Structure):

@@ -2,9 +2,11 @@
 
 Chooses the im_tuning knobs (vertex-to-warp mapping: the in-degree above which
 a hub is pushed by per-simulation hash search instead of an in-edge scan;
-work granularity: 32-edge batches per claimed unit; frontier threshold: when a
-propagation level walks every vertex in vertex order) by timing short runs of
-the caller's workload.  The knobs change how work is split, never a result.
+work granularity: 32-edge batches per claimed unit; frontier thresholds: when a
+propagation level walks every vertex in vertex order, and below which level
+size queues switch from vertices to (vertex, chunk) buckets) by timing short
+runs of the caller's workload.  The knobs change how work is split, never a
+result.
 """
 from __future__ import annotations
 
@@ -17,8 +19,9 @@ from . import im_ctx_get_tuning, im_ctx_set_tuning
 
 DEFAULT_SPACE = {
     "heavy_indeg": [64, 256],
-    "light_batches": [4, 8, 16],
+    "light_batches": [4, 16],
     "dense_div": [0, 4],
+    "buckets": [0, 2],
 }
 
 

@@ -44,7 +44,7 @@ struct im_ctx {
     bool trace = false;
     std::vector<float> launch_ms;    // kernel time per launch sequence number (tracing)
     std::vector<im_trace_rec> recs;  // frontier launches of the last call
-    im_tuning tuning{256, 4, 0, 2, 1, 0, 1, 1};
+    im_tuning tuning{256, 4, 0, 2, 1, 0, 1, 2};
 };
 
 namespace {
@@ -227,7 +227,7 @@ struct im_sketch {
     int32_t J = 0;
     DBuf M, X, salt, tab, ql[3], qh[3], ctr, claim, chg[3], gen, seed_bits, count, part_S, part_u,
         ticket, stats, err, bar, lb, cand, part_S2, part_u2, lcm_in_lo, lcm_in_hi, lcm_out_lo, lcm_out_hi,
-        level_ns;
+        level_ns, fmt;
     // bucket mode: bucketed live lists per orientation (0: in-edges, 1:
     // out-edges); the light queues then hold buckets, bq_cap entries each
     DBuf bk_end[2], bk_other[2], bk_mask[2];
@@ -309,12 +309,12 @@ extern "C" im_status im_ctx_set_timing(im_ctx* c, int enable) {
 extern "C" im_status im_ctx_set_tuning(im_ctx* c, const im_tuning* t) {
     if (!c) return IM_E_INVAL;
     if (!t) {
-        c->tuning = im_tuning{256, 4, 0, 2, 1, 0, 1, 1};
+        c->tuning = im_tuning{256, 4, 0, 2, 1, 0, 1, 2};
         return IM_OK;
     }
     if (t->heavy_indeg < 0 || t->light_batches < 1 || t->light_batches > 4096 || t->grid_blocks < 0 ||
         t->check_every < 1 || t->check_every > 64 || t->persistent < 0 || t->persistent > 1 ||
-        t->dense_div < 0 || t->lazy_pick < 0 || t->lazy_pick > 1 || t->buckets < 0 || t->buckets > 1)
+        t->dense_div < 0 || t->lazy_pick < 0 || t->lazy_pick > 1 || t->buckets < 0 || t->buckets > 1024)
         return fail(c, IM_E_INVAL, "tuning out of range");
     c->tuning = *t;
     return IM_OK;
@@ -580,6 +580,7 @@ static void sketch_plan(im_sketch* sk, int32_t n, int64_t m_edges, int32_t J, Bu
     A(sk->err, 4);
     A(sk->bar, 16);
     A(sk->level_ns, (size_t)(kMaxLevels + 2) * 8);
+    A(sk->fmt, (size_t)(kMaxLevels + 2));
     A(sk->lb, (size_t)n * 8);
     A(sk->cand, 4);
     A(sk->part_S2, (size_t)pg * 8);
@@ -732,6 +733,8 @@ static void set_lcm(LevelArgs& a, const im_sketch* sk, int mode) {
     a.chunks = sk->J / 16;
     a.nbuckets = (int64_t)sk->g->n * (sk->J / 16);
     a.bq_cap = sk->bq_cap;
+    a.vq_cap = sk->g->n;
+    a.bucket_div = sk->buckets ? sk->ctx->tuning.buckets : 0;
     if (sk->buckets) {
         const int o = in ? 0 : 1;
         a.bk_end = sk->bk_end[o].as<uint32_t>();
@@ -760,10 +763,13 @@ static im_status check_err(im_sketch* sk) {
 // back to zero.  A phase that completes leaves its change masks zero (the
 // last level's bits are cleared by the phase itself); after a new sketch or a
 // failed phase they are cleared here.
-static im_status phase_begin(im_sketch* sk) {
+static im_status phase_begin(im_sketch* sk, int mode) {
     im_ctx* c = sk->ctx;
     auto st = c->stream;
     CK(c, cudaMemsetAsync(sk->ctr.p, 0, sk->ctr.bytes, st));
+    // the level-0 queue: bucket entries for a cover in bucket mode (the seed
+    // kernel writes them), vertex entries otherwise
+    CK(c, cudaMemsetAsync(sk->fmt.p, (mode == kCover && sk->buckets) ? 1 : 0, 1, st));
     CK(c, cudaMemsetAsync(sk->claim.p, 0, sk->claim.bytes, st));
     if (sk->chg_dirty) {
         for (int i = 0; i < 3; ++i) CK(c, cudaMemsetAsync(sk->chg[i].p, 0, sk->chg[i].bytes, st));
@@ -799,6 +805,7 @@ static im_status run_phase_persistent(im_sketch* sk, int mode, bool all_first, i
     p.levels_out = reinterpret_cast<int*>(bar + 3);
     p.limit_ns = 20ull * 1000 * 1000 * 1000;
     p.level_ns = c->trace ? sk->level_ns.as<unsigned long long>() : nullptr;
+    p.fmt = sk->fmt.as<uint8_t>();
     CK(c, timed(c, mode == kPush ? kTPush : kTCover,
                 [&] { return launch_phase(sk->kind, mode, sk->dev, p, grid, st); }));
     CK(c, cudaMemcpyAsync(c->pinned, bar, 16, cudaMemcpyDeviceToHost, st));
@@ -876,6 +883,9 @@ static im_status run_levels(im_sketch* sk, int mode, bool all_first) {
         a.all_changed = (t == 0 && all_first) ? 1 : 0;
         a.claim = claim + t;
         a.gen_next = ++sk->gen_counter;
+        a.fmt_in = sk->fmt.as<uint8_t>() + t;
+        a.fmt_out = sk->fmt.as<uint8_t>() + t + 1;
+        a.fmt_prev = t >= 1 ? sk->fmt.as<uint8_t>() + t - 1 : nullptr;
         CK(c, timed(c, mode == kPush ? kTPush : kTCover,
                     [&] { return launch_level(sk->kind, mode, sk->dev, a, grid, st); }));
         ++t;
@@ -908,6 +918,9 @@ static im_status run_levels(im_sketch* sk, int mode, bool all_first) {
         a.all_changed = 0;
         a.claim = claim + t;
         a.gen_next = ++sk->gen_counter;
+        a.fmt_in = sk->fmt.as<uint8_t>() + t;
+        a.fmt_out = sk->fmt.as<uint8_t>() + t + 1;
+        a.fmt_prev = sk->fmt.as<uint8_t>() + t - 1;
         CK(c, timed(c, mode == kPush ? kTPush : kTCover,
                     [&] { return launch_level(sk->kind, mode, sk->dev, a, grid, st); }));
     }
@@ -934,16 +947,14 @@ static im_status run_levels(im_sketch* sk, int mode, bool all_first) {
 
 static im_status propagate(im_sketch* sk) {
     im_ctx* c = sk->ctx;
-    CKS(phase_begin(sk));
+    CKS(phase_begin(sk, kPush));
     LevelArgs a = level_args(sk);
     ulonglong2* ctr = sk->ctr.as<ulonglong2>();
     a.ql_out = sk->ql[0].as<QEntry>();
     a.cl_out = &ctr[0].x;
     a.qh_out = sk->qh[0].as<QEntry>();
     a.ch_out = &ctr[0].y;
-    // bucket mode: level 0 walks every bucket, no queue
-    if (!sk->buckets)
-        CK(c, timed(c, kTOther, [&] { return launch_init_queues(sk->kind, sk->dev, a, c->stream); }));
+    CK(c, timed(c, kTOther, [&] { return launch_init_queues(sk->kind, sk->dev, a, c->stream); }));
     return run_levels(sk, kPush, true);
 }
 
@@ -987,6 +998,8 @@ static im_status stats_collect(im_sketch* sk) {
     s.sweep_batches = h[kStSweepBatches];
     s.sweep_dealt = h[kStSweepDealt];
     s.sweep_edges_live = h[kStSweepLiveEdges];
+    s.sweep_buckets = h[kStSweepBuckets];
+    s.sweep_bucket_entries = h[kStSweepBucketEntries];
     // algorithmic bytes of the sweeps: queue entry (16 B) + the queued vertex's
     // register row (J B) per queued vertex; live chunk mask (4 B, 8 B when
     // J = 1024) per in-edge; source id + edge hash (8 B, + 4 B threshold for
@@ -995,15 +1008,12 @@ static im_status stats_collect(im_sketch* sk) {
     // 4-byte word per CAS write
     const uint64_t t = sk->kind == kExplicit ? 4 : 0;
     const uint64_t lw = sk->J > 512 ? 8 : 4;
-    if (sk->buckets)
-        // bucket mode: per queued bucket its 16-byte entry; per processed
-        // list entry its endpoint and live mask (6 B), the source and target
-        // 16-byte register pieces and the target bucket's bounds (8 B); per
-        // CAS 4 B
-        s.alg_bytes_sweep = s.sweep_vertices * 16 + s.sweep_dealt * (6 + 32 + 8) + s.sweep_cas * 4;
-    else
-        s.alg_bytes_sweep = s.sweep_vertices * (16 + (uint64_t)sk->J) + s.sweep_edges * lw +
-                            s.sweep_edges_live * (8 + t) + s.sweep_chunks * 32 + s.sweep_cas * 4;
+    // levels on vertex queues, plus levels on bucket queues: per queued
+    // bucket its 16-byte entry; per processed list entry its endpoint and
+    // live mask (6 B) and the source and target 16-byte register pieces
+    s.alg_bytes_sweep = s.sweep_vertices * (16 + (uint64_t)sk->J) + s.sweep_edges * lw +
+                        s.sweep_edges_live * (8 + t) + s.sweep_chunks * 32 + s.sweep_cas * 4 +
+                        s.sweep_buckets * 16 + s.sweep_bucket_entries * (6 + 32);
     return IM_OK;
 }
 
@@ -1091,13 +1101,21 @@ static im_status build_buckets(im_sketch* sk) {
     dfree(c, ne);
     const int64_t most = (int64_t)std::max(nonempty[0], nonempty[1]);
     const int64_t cap = std::max<int64_t>(1, std::min(bucket_queue_cap(n), most));
-    for (int i = 0; i < 3 && s == IM_OK; ++i) s = dalloc(c, (size_t)cap * sizeof(QEntry), sk->ql[i]);
+    // the light queues hold vertex entries (n at most) or bucket entries
+    DBuf nq[3];
+    if (cap > n)
+        for (int i = 0; i < 3 && s == IM_OK; ++i) s = dalloc(c, (size_t)cap * sizeof(QEntry), nq[i]);
     for (int i = 0; i < 3 && s == IM_OK; ++i) s = dalloc(c, sk->chg[i].bytes, sk->chg_cov[i]);
     if (s != IM_OK) {
-        for (int i = 0; i < 3; ++i) { dfree(c, sk->ql[i]); dfree(c, sk->chg_cov[i]); }
+        for (int i = 0; i < 3; ++i) { dfree(c, nq[i]); dfree(c, sk->chg_cov[i]); }
         drop();
         return IM_OK;
     }
+    if (cap > n)
+        for (int i = 0; i < 3; ++i) {
+            dfree(c, sk->ql[i]);
+            sk->ql[i] = nq[i];
+        }
     sk->chg_dirty = true;  // the new buffers start zeroed by the next phase
     sk->bq_cap = (int32_t)cap;
     sk->buckets = true;
@@ -1123,9 +1141,8 @@ static im_status sketch_start(im_ctx* c, im_graph* g, int32_t J, uint64_t seed, 
         delete sk;
         return cuda_fail(c, e, "sketch setup");
     }
-    im_status s = IM_OK;
-    if (c->tuning.buckets) s = build_buckets(sk);
-    if (s == IM_OK && !sk->buckets) s = build_scan_mode(sk);
+    im_status s = build_scan_mode(sk);
+    if (s == IM_OK && c->tuning.buckets) s = build_buckets(sk);
     if (s != IM_OK) {
         sketch_release(sk);
         delete sk;
@@ -1235,7 +1252,7 @@ static PickArgs pick_args(im_sketch* sk, int k) {
 // the stored sums that could beat the candidate.
 static im_status pick_and_cover(im_sketch* sk, int k) {
     im_ctx* c = sk->ctx;
-    CKS(phase_begin(sk));
+    CKS(phase_begin(sk, kCover));
     PickArgs a = pick_args(sk, k);
     if (sk->lazy) {
         a.lb = sk->lb.as<unsigned long long>();
@@ -1276,7 +1293,7 @@ extern "C" im_status im_sketch_cover(im_sketch* sk, int32_t s, uint64_t* count_o
     if (!sk) return IM_E_INVAL;
     im_ctx* c = sk->ctx;
     if (s < 0 || s >= sk->g->n) return fail(c, IM_E_RANGE, "vertex %d out of range", s);
-    CKS(phase_begin(sk));
+    CKS(phase_begin(sk, kCover));
     CK(c, launch_cover_seed(sk->M.as<uint8_t>(), sk->J, s, sk->g->rp_out.as<int32_t>(),
                             sk->ql[0].as<QEntry>(), &sk->ctr.as<ulonglong2>()[0].x,
                             chg_buf(sk, kCover, 0).as<uint32_t>(), sk->count.as<unsigned long long>(),
@@ -1412,7 +1429,7 @@ uint64_t query_bytes(const im_graph* g, int32_t J, int32_t K) {
     scan_plan(&probe, g->n, g->m, J, scan);
     uint64_t scan_bytes = 0;
     for (auto& pb : scan) scan_bytes += round_bytes(pb.second);
-    total += std::max(scan_bytes, bucket_reserve_bytes(g->n, g->m, J));
+    total += scan_bytes + bucket_reserve_bytes(g->n, g->m, J);
     const size_t cap = (size_t)out_cap_for(K);
     total += round_bytes(cap * 4) + 2 * round_bytes(cap * 8);
     return total;
@@ -1724,7 +1741,7 @@ extern "C" im_status im_batch_select_seeds(im_batch* b, const int32_t* J, const 
             for (int32_t g : members) active[g] = r < K[g] ? 1 : 0;
             e = cudaMemcpyAsync(active_d.p, active.data(), (size_t)G, cudaMemcpyHostToDevice, st);
             if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "batch round"); }
-            if ((s = phase_begin(sk)) != IM_OK) { cleanup(); return s; }
+            if ((s = phase_begin(sk, kCover)) != IM_OK) { cleanup(); return s; }
             BatchPickArgs pa{};
             pa.M = sk->M.as<uint8_t>();
             pa.J = Jg;

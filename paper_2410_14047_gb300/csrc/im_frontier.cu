@@ -205,6 +205,56 @@ __device__ __forceinline__ int nth_chunk(uint32_t lo, uint32_t hi, int r) {
     return r < cl ? (int)__fns(lo, 0u, r + 1) : 32 + (int)__fns(hi, 0u, r - cl + 1);
 }
 
+// Vertex-format enqueue (warp-collective): vertex o, whose registers changed
+// this level, joins the next level's queue once (enqueue stamp), hubs of the
+// propagation in the heavy queue.
+template <int KIND, int MODE>
+__device__ __forceinline__ void vertex_enqueue(const GraphDev& g, const LevelArgs& a, bool changed, int32_t o) {
+    bool want = false;
+    int32_t rp = 0, deg = 0;
+    uint32_t aux = 0u;
+    bool heavy = false;
+    if (changed) {
+        // the enqueue stamp and the row words are fetched together
+        const int32_t* rpp = MODE == kPush ? g.rp_in : g.rp_out;
+        rp = __ldg(rpp + o);
+        deg = __ldg(rpp + o + 1);
+        if constexpr (MODE == kPush && KIND == kWC) aux = __ldg(g.thr_v + o);
+        want = atomicExch(a.gen + o, a.gen_next) != a.gen_next;
+        deg -= rp;
+        if constexpr (MODE == kPush)
+            heavy = is_heavy<KIND>(deg, KIND == kWC ? aux : g.thr_uniform, a.heavy_indeg);
+        want = want && deg > 0;
+    }
+    append(want && !heavy, o, rp, deg, aux, a.ql_out, a.cl_out, a.vq_cap, a.err);
+    if constexpr (MODE == kPush) append(want && heavy, o, rp, deg, aux, a.qh_out, a.ch_out, a.vq_cap, a.err);
+}
+
+// Forward declarations (bucket mode, below).
+__device__ __forceinline__ uint32_t bucket_start(const uint32_t* __restrict__ end, int64_t b);
+__device__ __forceinline__ void bucket_append(bool want, uint32_t b, uint32_t start, uint32_t len,
+                                              QEntry* __restrict__ q, unsigned long long* ctr,
+                                              unsigned long long* overflow, int32_t cap);
+
+// Bucket-format enqueue (warp-collective): the change bits nbits (16, of
+// chunk c) of vertex o are set; the first change of that chunk this level
+// (the returned bits tell) queues the bucket (o, c) unless it is empty (an
+// empty bucket's bits are never read).
+__device__ __forceinline__ void bucket_enqueue(const LevelArgs& a, bool changed, int32_t o, uint32_t c,
+                                               uint32_t nbits) {
+    bool want = false;
+    uint32_t ob = 0u, os = 0u, oe = 0u;
+    if (changed) {
+        const uint32_t sh = (c & 1u) * 16u;
+        ob = (uint32_t)o * (uint32_t)a.chunks + c;
+        oe = __ldcg(a.bk_end + ob);
+        os = bucket_start(a.bk_end, ob);
+        const uint32_t old = atomicOr(a.chg_next + (size_t)o * a.words + (c >> 1), nbits << sh);
+        want = ((old >> sh) & 0xFFFFu) == 0u && oe > os;
+    }
+    bucket_append(want, ob, os, oe - os, a.ql_out, a.cl_out, a.ch_out, a.bq_cap);
+}
+
 // ---------------------------------------------------------------------------
 // Light units: a slice of 32-edge batches of the flat edge space.
 // ---------------------------------------------------------------------------
@@ -216,7 +266,7 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                                             unsigned long long& st_cas, unsigned long long& st_new,
                                             unsigned long long& st_batches, unsigned long long& st_dealt,
                                             unsigned long long& st_live, bool skip_heavy,
-                                            uint32_t (*sKeep)[kKeepWords]) {
+                                            uint32_t (*sKeep)[kKeepWords], bool out_b) {
     const int lane = (int)lane_id();
     const int J = a.J, words = a.words;
     const int64_t fend = min(El, b1 << 5);
@@ -365,30 +415,14 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                                 }
                             }
                         }
-                        if (nbits)
+                        if (nbits && !out_b)
                             atomicOr(a.chg_next + (size_t)o_i * words + (chunk >> 1), nbits << ((chunk & 1) * 16));
                     }
                 }
             }
-            // enqueue vertices whose registers changed
-            bool want = false;
-            int32_t rp = 0, deg = 0;
-            uint32_t aux = 0u;
-            bool heavy = false;
-            if (nbits) {
-                // the enqueue stamp and the row words are fetched together
-                const int32_t* rpp = MODE == kPush ? g.rp_in : g.rp_out;
-                rp = __ldg(rpp + o_i);
-                deg = __ldg(rpp + o_i + 1);
-                if constexpr (MODE == kPush && KIND == kWC) aux = __ldg(g.thr_v + o_i);
-                want = atomicExch(a.gen + o_i, a.gen_next) != a.gen_next;
-                deg -= rp;
-                if constexpr (MODE == kPush)
-                    heavy = is_heavy<KIND>(deg, KIND == kWC ? aux : g.thr_uniform, a.heavy_indeg);
-                want = want && deg > 0;
-            }
-            append(want && !heavy, o_i, rp, deg, aux, a.ql_out, a.cl_out, g.n, a.err);
-            if constexpr (MODE == kPush) append(want && heavy, o_i, rp, deg, aux, a.qh_out, a.ch_out, g.n, a.err);
+            // enqueue what changed: the vertex, or its chunk's bucket
+            if (out_b) bucket_enqueue(a, nbits != 0u, o_i, (uint32_t)chunk, nbits);
+            else vertex_enqueue<KIND, MODE>(g, a, nbits != 0u, o_i);
         }
         qi = qn;
         raw = rawn;
@@ -424,7 +458,7 @@ __device__ __forceinline__ int32_t lower_bound_h(const uint32_t* __restrict__ h,
 template <int KIND>
 __device__ __forceinline__ void heavy_vertex(const GraphDev& g, const LevelArgs& a, const uint32_t* sX,
                                              QEntry ent, unsigned long long& st_chunks,
-                                             unsigned long long& st_cas) {
+                                             unsigned long long& st_cas, bool out_b) {
     const int lane = (int)lane_id();
     const int J = a.J, words = a.words;
     const int32_t v = ent.v;
@@ -509,24 +543,11 @@ __device__ __forceinline__ void heavy_vertex(const GraphDev& g, const LevelArgs&
                         nw = byte_max(cur, b);
                         if (++tries > kCasRetryLimit) { atomicOr(a.err, kErrCasLimit); break; }
                     }
-                    if (changed) atomicOr(a.chg_next + (size_t)u * words + (j >> 5), 1u << (j & 31));
+                    if (changed && !out_b) atomicOr(a.chg_next + (size_t)u * words + (j >> 5), 1u << (j & 31));
                 }
             }
-            bool want = false, heavy = false;
-            int32_t rp = 0, deg = 0;
-            uint32_t aux = 0u;
-            if (changed) {
-                want = atomicExch(a.gen + u, a.gen_next) != a.gen_next;
-                if (want) {
-                    rp = __ldg(g.rp_in + u);
-                    deg = __ldg(g.rp_in + u + 1) - rp;
-                    if constexpr (KIND == kWC) aux = __ldg(g.thr_v + u);
-                    heavy = is_heavy<KIND>(deg, KIND == kWC ? aux : g.thr_uniform, a.heavy_indeg);
-                    want = deg > 0;
-                }
-            }
-            append(want && !heavy, u, rp, deg, aux, a.ql_out, a.cl_out, g.n, a.err);
-            append(want && heavy, u, rp, deg, aux, a.qh_out, a.ch_out, g.n, a.err);
+            if (out_b) bucket_enqueue(a, changed, u, (uint32_t)(j >> 4), 1u << (j & 15));
+            else vertex_enqueue<KIND, kPush>(g, a, changed, u);
         }
     }
 }
@@ -616,7 +637,7 @@ __device__ __forceinline__ void bucket_slice(const GraphDev& g, const LevelArgs&
                                              int64_t b0, int64_t b1, int32_t nq, int64_t E, bool dense,
                                              unsigned long long& st_chunks, unsigned long long& st_cas,
                                              unsigned long long& st_new, unsigned long long& st_batches,
-                                             unsigned long long& st_dealt) {
+                                             unsigned long long& st_dealt, bool out_b) {
     const int lane = (int)lane_id();
     const int J = a.J, words = a.words;
     const uint32_t C = (uint32_t)a.chunks;
@@ -707,7 +728,6 @@ __device__ __forceinline__ void bucket_slice(const GraphDev& g, const LevelArgs&
         const uint32_t u = bkt / C, c = bkt % C;
         uint32_t nbits = 0u;
         int32_t o = 0;
-        uint32_t ob = 0u, ostart = 0u, oend = 0u;
         if (f < fend && chb) {
             ++st_dealt;
             o = __ldg(a.bk_other + e);
@@ -716,7 +736,6 @@ __device__ __forceinline__ void bucket_slice(const GraphDev& g, const LevelArgs&
             uint8_t* trow = a.M + (size_t)o * J + c * 16;
             const uint4 src = ld_cg16(srow);
             const uint4 tg = ld_cg16(trow);
-            ob = (uint32_t)o * C + c;
             const uint32_t sw[4] = {src.x, src.y, src.z, src.w};
             const uint32_t tw[4] = {tg.x, tg.y, tg.z, tg.w};
             uint32_t cand[4];
@@ -748,24 +767,20 @@ __device__ __forceinline__ void bucket_slice(const GraphDev& g, const LevelArgs&
                 }
             }
         }
-        // enqueue the target's bucket on the first change of its chunk this
-        // level (the returned change bits tell; the bucket's bounds are read
-        // meanwhile).  An empty bucket is never queued: its change bits are
-        // never read, and a later level only needs them for non-empty ones.
-        bool want = false;
-        if (nbits) {
-            const uint32_t sh = (c & 1u) * 16u;
-            oend = __ldcg(a.bk_end + ob);
-            ostart = bucket_start(a.bk_end, ob);
-            const uint32_t old = atomicOr(a.chg_next + (size_t)o * words + (c >> 1), nbits << sh);
-            want = ((old >> sh) & 0xFFFFu) == 0u && oend > ostart;
+        // enqueue what changed: the target's bucket of this chunk, or the
+        // target vertex
+        if (out_b) {
+            bucket_enqueue(a, nbits != 0u, o, c, nbits);
+        } else {
+            if (nbits) atomicOr(a.chg_next + (size_t)o * words + (c >> 1), nbits << ((c & 1u) * 16u));
+            vertex_enqueue<KIND, MODE>(g, a, nbits != 0u, o);
         }
-        bucket_append(want, ob, ostart, oend - ostart, a.ql_out, a.cl_out, a.ch_out, a.bq_cap);
     }
 }
 
 struct LevelStats {
-    unsigned long long chunks = 0, cas = 0, fresh = 0, hsims = 0, batches = 0, dealt = 0, live = 0;
+    unsigned long long chunks = 0, cas = 0, fresh = 0, hsims = 0, batches = 0, dealt = 0, live = 0,
+        bentries = 0;
 };
 
 // Clears the change bits read by the level before the previous one.
@@ -773,7 +788,7 @@ __device__ __forceinline__ void clear_prev_bits(const LevelArgs& a, int64_t warp
     if (!a.chg_prev) return;
     const int lane = (int)lane_id();
     const int32_t nlp = a.cl_prev ? (int32_t)(__ldcg(a.cl_prev) >> kCountShift) : 0;
-    if (a.bk_end) {
+    if (a.fmt_prev && __ldcg(a.fmt_prev) != 0) {
         // bucket queue: each entry owns the 16 change bits of its chunk; a
         // queue that overflowed (its level walked every bucket) clears all
         const bool overflow = nlp > a.bq_cap || (a.ch_prev && __ldcg(a.ch_prev) != 0ull);
@@ -806,20 +821,29 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
     const int lane = (int)lane_id();
     const unsigned long long cl = __ldcg(a.cl_in);
     const unsigned long long ch = a.ch_in ? __ldcg(a.ch_in) : 0ull;
-    if (a.bk_end) {
-        // bucket mode: the queue's buckets, or every bucket when the level is
-        // level 0 of a build or its queue overflowed (ch = overflow word)
+    // output format: bucket entries once the level's input work is small
+    // against the graph (the bucketed lists then skip the edges of unchanged
+    // chunks), vertex entries otherwise
+    auto out_bucket = [&](int64_t work) {
+        return a.bk_end != nullptr && a.bucket_div > 0 && work * a.bucket_div < g.m;
+    };
+    const bool in_b = a.fmt_in != nullptr && __ldcg(a.fmt_in) != 0;
+    if (in_b) {
+        // the queue's buckets, or every bucket when the queue overflowed
+        // (ch = overflow word)
         const int32_t nq = (int32_t)(cl >> kCountShift);
         const bool dense = a.all_changed || nq > a.bq_cap || ch != 0ull;
         const int64_t E = dense ? (int64_t)__ldcg(a.bk_end + a.nbuckets - 1) : (int64_t)(cl & kEdgeMask);
+        const bool out_b = out_bucket(E);
+        if (a.fmt_out && blockIdx.x == 0 && threadIdx.x == 0) *a.fmt_out = out_b ? 1 : 0;
         const int64_t nbl = (E + 31) >> 5;
         const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
         const int64_t lb = max((int64_t)1, min((int64_t)a.light_batches, nbl / nwarps));
         const int64_t units = (nbl + lb - 1) / lb;
         if (units == 0) return;
         if (warp == 0 && lane == 0) {
-            atomicAdd(a.stats + (MODE == kPush ? kStSweepVertices : kStCoverVertices), (unsigned long long)nq);
-            atomicAdd(a.stats + (MODE == kPush ? kStSweepEdges : kStCoverEdges), (unsigned long long)E);
+            atomicAdd(a.stats + (MODE == kPush ? kStSweepBuckets : kStCoverVertices), (unsigned long long)nq);
+            if (MODE == kCover) atomicAdd(a.stats + kStCoverEdges, (unsigned long long)E);
             atomicAdd(a.stats + (MODE == kPush ? kStSweepLevels : kStCoverLevels), 1ull);
         }
         for (;;) {
@@ -830,7 +854,7 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
             const int64_t b0 = (int64_t)unit * lb;
             const int64_t b1 = min(nbl, b0 + lb);
             bucket_slice<KIND, MODE>(g, a, a.ql_in, b0, b1, nq, E, dense, ls.chunks, ls.cas, ls.fresh,
-                                     ls.batches, ls.dealt);
+                                     ls.batches, ls.bentries, out_b);
         }
         return;
     }
@@ -863,6 +887,8 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
     const int64_t hunits = (nbh + lb - 1) / lb;
     const int64_t nhv = hscan ? 0 : (int64_t)nh;  // hubs searched per changed simulation
     const int64_t total = nhv + lunits + hunits;
+    const bool out_b = out_bucket(El + Eh);
+    if (a.fmt_out && blockIdx.x == 0 && threadIdx.x == 0) *a.fmt_out = out_b ? 1 : 0;
     if (total == 0) return;
     if (warp == 0 && lane == 0) {
         atomicAdd(a.stats + (MODE == kPush ? kStSweepVertices : kStCoverVertices),
@@ -881,20 +907,20 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
                 const int4 raw = __ldcg(reinterpret_cast<const int4*>(a.qh_in) + unit);
                 QEntry ent;
                 ent.v = raw.x; ent.rp = raw.y; ent.off = raw.z; ent.aux = (uint32_t)raw.w;
-                heavy_vertex<KIND>(g, a, sX, ent, ls.hsims, ls.cas);
+                heavy_vertex<KIND>(g, a, sX, ent, ls.hsims, ls.cas, out_b);
             }
         } else if ((int64_t)unit < nhv + lunits) {
             const int64_t lu = (int64_t)unit - nhv;
             const int64_t b0 = lu * lb;
             const int64_t b1 = min(nbl, b0 + lb);
             light_slice<KIND, MODE>(g, a, ql, sX, sTab, b0, b1, nl, El, ls.chunks, ls.cas, ls.fresh,
-                                    ls.batches, ls.dealt, ls.live, dense && nh > 0, sKeep);
+                                    ls.batches, ls.dealt, ls.live, dense && nh > 0, sKeep, out_b);
         } else {
             const int64_t hu = (int64_t)unit - nhv - lunits;
             const int64_t b0 = hu * lb;
             const int64_t b1 = min(nbh, b0 + lb);
             light_slice<KIND, MODE>(g, a, a.qh_in, sX, sTab, b0, b1, nh, Eh, ls.chunks, ls.cas, ls.fresh,
-                                    ls.batches, ls.dealt, ls.live, false, sKeep);
+                                    ls.batches, ls.dealt, ls.live, false, sKeep, out_b);
         }
     }
 }
@@ -908,8 +934,10 @@ __device__ __forceinline__ void flush_stats(const LevelArgs& a, LevelStats& ls) 
     ls.batches = wsum(ls.batches);
     ls.dealt = wsum(ls.dealt);
     ls.live = wsum(ls.live);
+    ls.bentries = wsum(ls.bentries);
     if (lane_id() == 0) {
         if constexpr (MODE == kPush) {
+            if (ls.bentries) atomicAdd(a.stats + kStSweepBucketEntries, ls.bentries);
             if (ls.live) atomicAdd(a.stats + kStSweepLiveEdges, ls.live);
             if (ls.batches) atomicAdd(a.stats + kStSweepBatches, ls.batches);
             if (ls.dealt) atomicAdd(a.stats + kStSweepDealt, ls.dealt);
@@ -1034,6 +1062,9 @@ __global__ void __launch_bounds__(kFBlock, kPhaseMinBlocks) k_phase(GraphDev g, 
         a.all_changed = (t == 0 && p.all_first) ? 1 : 0;
         a.claim = p.claim + t;
         a.gen_next = p.gen_base + t;
+        a.fmt_in = p.fmt ? p.fmt + t : nullptr;
+        a.fmt_out = p.fmt ? p.fmt + t + 1 : nullptr;
+        a.fmt_prev = (p.fmt && t >= 1) ? p.fmt + t - 1 : nullptr;
         clear_prev_bits(a, warp, nwarps);
         level_work<KIND, MODE>(g, a, sX, sTab, warp, ls, sKeep[threadIdx.x >> 5]);
         if (!grid_barrier(p.bar_arrive, p.bar_gen, p.abort_flag, a.err, p.limit_ns)) break;
@@ -1052,6 +1083,7 @@ __global__ void __launch_bounds__(kFBlock, kPhaseMinBlocks) k_phase(GraphDev g, 
         a.qh_prev = p.qh[bl];
         a.ch_prev = &p.ctr[t - 1].y;
         a.chg_prev = p.chg[bl];
+        a.fmt_prev = p.fmt ? p.fmt + t - 1 : nullptr;
         clear_prev_bits(a, warp, nwarps);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *p.levels_out = t;

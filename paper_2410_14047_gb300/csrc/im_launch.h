@@ -27,6 +27,8 @@ enum StatIndex : int {
     kStSweepBatches,
     kStSweepDealt,
     kStSweepLiveEdges,  // examined in-edges live in a changed chunk (their ids and hashes are read)
+    kStSweepBuckets,        // queued buckets walked by propagation levels
+    kStSweepBucketEntries,  // bucket list entries processed (source chunk changed)
     kStCount
 };
 
@@ -89,6 +91,15 @@ struct LevelArgs {
     int32_t chunks;
     int64_t nbuckets;
     int32_t bq_cap;                      // bucket queue capacity; a fuller level walks every bucket
+    // queue formats (hybrid mode): 0 = vertex entries, 1 = bucket entries.
+    // fmt_in: format of this level's input queue; fmt_out: written by the
+    // level with the format of its output queue; fmt_prev: the previous
+    // level's input (change-bit clearing).  NULL: vertex format throughout.
+    const uint8_t* fmt_in;
+    uint8_t* fmt_out;
+    const uint8_t* fmt_prev;
+    int32_t bucket_div;                  // output in bucket format when input work * bucket_div < m
+    int32_t vq_cap;                      // vertex queue capacity (n)
 };
 
 // All levels of a phase in one cooperative launch (grid barrier between levels).
@@ -108,6 +119,7 @@ struct PhaseArgs {
     unsigned long long limit_ns;         // bound on every barrier wait
     int* levels_out;                     // levels the phase ran
     unsigned long long* level_ns;        // tracing: global time at the start of level t (may be NULL)
+    uint8_t* fmt;                        // per level queue format (hybrid mode; NULL otherwise)
 };
 
 int level_grid();
