@@ -574,17 +574,35 @@ __global__ void k_scan_tiles(const int32_t* __restrict__ in, int32_t n, int32_t*
     if (threadIdx.x == blockDim.x - 1) tile_sums[blockIdx.x] = wbase + incl;
 }
 
-__global__ void k_scan_sums(int64_t* tile_sums, int ntiles, int32_t* out_total_slot) {
-    // single block: exclusive scan of the tile sums in place; writes the total
-    if (threadIdx.x == 0) {
-        int64_t run = 0;
-        for (int t = 0; t < ntiles; ++t) {
-            const int64_t s = tile_sums[t];
-            tile_sums[t] = run;
-            run += s;
-        }
-        *out_total_slot = (int32_t)run;
-        tile_sums[ntiles] = run;  // the exact 64-bit total
+// Exclusive scan of the tile sums in place (one block of kScanSumThreads:
+// each thread scans a contiguous run of tiles), the 32-bit total into
+// *out_total_slot and the exact 64-bit total into tile_sums[ntiles].
+constexpr int kScanSumThreads = 1024;
+__global__ void __launch_bounds__(kScanSumThreads) k_scan_sums(int64_t* tile_sums, int ntiles, int32_t* out_total_slot) {
+    __shared__ int64_t part[kScanSumThreads];
+    const int t = threadIdx.x;
+    const int per = (ntiles + kScanSumThreads - 1) / kScanSumThreads;
+    const int b = min(ntiles, t * per), e = min(ntiles, b + per);
+    int64_t run = 0;
+    for (int i = b; i < e; ++i) run += tile_sums[i];
+    part[t] = run;
+    __syncthreads();
+    // Hillis-Steele inclusive scan of the per-thread totals
+    for (int off = 1; off < kScanSumThreads; off <<= 1) {
+        const int64_t v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int64_t acc = part[t] - run;  // exclusive prefix of this thread's run
+    for (int i = b; i < e; ++i) {
+        const int64_t x = tile_sums[i];
+        tile_sums[i] = acc;
+        acc += x;
+    }
+    if (t == kScanSumThreads - 1) {
+        *out_total_slot = (int32_t)part[t];
+        tile_sums[ntiles] = part[t];  // the exact 64-bit total
     }
 }
 
@@ -603,7 +621,7 @@ cudaError_t launch_exclusive_scan(const int32_t* cnt, int32_t n, int32_t* out, v
     const int ntiles = (int)(((int64_t)n + kScanTile - 1) / kScanTile);
     int64_t* sums = static_cast<int64_t*>(tmp);
     if (ntiles > 0) k_scan_tiles<<<ntiles, kBlock, 0, st>>>(cnt, n, out, sums);
-    k_scan_sums<<<1, 32, 0, st>>>(sums, ntiles, out + n);
+    k_scan_sums<<<1, kScanSumThreads, 0, st>>>(sums, ntiles, out + n);
     if (n > 0) k_scan_add<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(out, n, sums);
     return cudaGetLastError();
 }
