@@ -18,6 +18,7 @@ does not shard on one GPU), value = N * steps / max-over-ranks time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -139,10 +140,15 @@ def measured_peaks():
 
 
 def ncu_traffic(workload):
-    """DRAM bytes per sweep launch from the committed ncu summary, if current."""
+    """DRAM bytes (read + write) per propagation-phase launch from the
+    committed ncu capture, or None when there is none for this workload or
+    the frontier kernels' source changed since it was taken."""
     try:
-        d = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
-        return d.get(workload)
+        d = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json"))).get(workload)
+        src = open(os.path.join(ROOT, "paper_2410_14047_gb300", "csrc", "im_frontier.cu"), "rb").read()
+        if not d or hashlib.sha256(src).hexdigest() != d["frontier_source_sha256"]:
+            return None
+        return d["traffic_bytes_per_launch"]
     except Exception:
         return None
 
