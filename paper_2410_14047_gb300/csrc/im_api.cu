@@ -734,6 +734,9 @@ static void set_lcm(LevelArgs& a, const im_sketch* sk, int mode) {
     a.nbuckets = (int64_t)sk->g->n * (sk->J / 16);
     a.bq_cap = sk->bq_cap;
     a.vq_cap = sk->g->n;
+    // a level appends at most one bucket per processed entry (fewer than m):
+    // below 2^26 - 2^22 edges the packed counter's count field cannot overflow
+    a.bq_guard = sk->g->m >= (int64_t)((1 << 26) - (1 << 22)) ? 1 : 0;
     a.bucket_div = sk->buckets ? sk->ctx->tuning.buckets : 0;
     if (sk->buckets) {
         const int o = in ? 0 : 1;

@@ -234,7 +234,7 @@ __device__ __forceinline__ void vertex_enqueue(const GraphDev& g, const LevelArg
 __device__ __forceinline__ uint32_t bucket_start(const uint32_t* __restrict__ end, int64_t b);
 __device__ __forceinline__ void bucket_append(bool want, uint32_t b, uint32_t start, uint32_t len,
                                               QEntry* __restrict__ q, unsigned long long* ctr,
-                                              unsigned long long* overflow, int32_t cap);
+                                              unsigned long long* overflow, int32_t cap, bool guard);
 
 // Bucket-format enqueue (warp-collective): the change bits nbits (16, of
 // chunk c) of vertex o are set; the first change of that chunk this level
@@ -252,7 +252,7 @@ __device__ __forceinline__ void bucket_enqueue(const LevelArgs& a, bool changed,
         const uint32_t old = atomicOr(a.chg_next + (size_t)o * a.words + (c >> 1), nbits << sh);
         want = ((old >> sh) & 0xFFFFu) == 0u && oe > os;
     }
-    bucket_append(want, ob, os, oe - os, a.ql_out, a.cl_out, a.ch_out, a.bq_cap);
+    bucket_append(want, ob, os, oe - os, a.ql_out, a.cl_out, a.ch_out, a.bq_cap, a.bq_guard != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -271,7 +271,7 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
     const int J = a.J, words = a.words;
     const int64_t fend = min(El, b1 << 5);
     int64_t f0 = b0 << 5;
-    int32_t qi = covering_entry(qlin, nl, f0);
+    int32_t qi = f0 == 0 ? 0 : covering_entry(qlin, nl, f0);
     // queue window of the first batch; later windows are prefetched one batch ahead
     int4 raw = make_int4(0, 0, 0x7FFFFFFF, 0);
     if (qi + lane < nl) raw = __ldcg(reinterpret_cast<const int4*>(qlin) + qi + lane);
@@ -595,7 +595,7 @@ __device__ __forceinline__ int64_t bucket_of_thread(const uint32_t* __restrict__
 // overflow word instead (the next level then walks every bucket).
 __device__ __forceinline__ void bucket_append(bool want, uint32_t b, uint32_t start, uint32_t len,
                                               QEntry* __restrict__ q, unsigned long long* ctr,
-                                              unsigned long long* overflow, int32_t cap) {
+                                              unsigned long long* overflow, int32_t cap, bool guard) {
     const unsigned wm = __ballot_sync(0xFFFFFFFFu, want);
     if (wm == 0u) return;
     const int lane = (int)lane_id();
@@ -609,9 +609,9 @@ __device__ __forceinline__ void bucket_append(bool want, uint32_t b, uint32_t st
     const int totd = __shfl_sync(0xFFFFFFFFu, incl, 31);
     unsigned long long base = ~0ull;
     if (lane == 0) {
-        // a queue already at capacity is not grown further (its count field
-        // stays far from overflowing)
-        if ((int32_t)(__ldcg(ctr) >> kCountShift) < cap)
+        // on graphs whose level could append 2^26 buckets (the count field's
+        // width), a queue already at capacity is not grown further
+        if (!guard || (int32_t)(__ldcg(ctr) >> kCountShift) < cap)
             base = atomicAdd(ctr, ((unsigned long long)__popc(wm) << kCountShift) | (unsigned long long)totd);
         else
             atomicOr(overflow, 1ull);
@@ -649,7 +649,7 @@ __device__ __forceinline__ void bucket_slice(const GraphDev& g, const LevelArgs&
     int4 raw = make_int4(0, 0, 0x7FFFFFFF, 0);
     int64_t bk0 = 0;
     if (!dense) {
-        qi = covering_entry(qlin, nq, f0);
+        qi = f0 == 0 ? 0 : covering_entry(qlin, nq, f0);
         if (qi + lane < nq) raw = __ldcg(reinterpret_cast<const int4*>(qlin) + qi + lane);
     } else {
         bk0 = bucket_of_warp(a.bk_end, 0, nb, f0);
@@ -728,13 +728,18 @@ __device__ __forceinline__ void bucket_slice(const GraphDev& g, const LevelArgs&
         const uint32_t u = bkt / C, c = bkt % C;
         uint32_t nbits = 0u;
         int32_t o = 0;
+        // the entry and the source piece are fetched with the change bits
+        uint32_t m16 = 0u;
+        uint4 src = make_uint4(0u, 0u, 0u, 0u);
+        if (f < fend) {
+            o = __ldg(a.bk_other + e);
+            m16 = __ldg(a.bk_mask + e);
+            src = ld_cg16(a.M + (size_t)u * J + c * 16);
+        }
         if (f < fend && chb) {
             ++st_dealt;
-            o = __ldg(a.bk_other + e);
-            const uint32_t m16 = __ldg(a.bk_mask + e) & chb;
-            const uint8_t* srow = a.M + (size_t)u * J + c * 16;
+            m16 &= chb;
             uint8_t* trow = a.M + (size_t)o * J + c * 16;
-            const uint4 src = ld_cg16(srow);
             const uint4 tg = ld_cg16(trow);
             const uint32_t sw[4] = {src.x, src.y, src.z, src.w};
             const uint32_t tw[4] = {tg.x, tg.y, tg.z, tg.w};
@@ -817,17 +822,15 @@ __device__ __forceinline__ void clear_prev_bits(const LevelArgs& a, int64_t warp
 template <int KIND, int MODE>
 __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a, const uint32_t* sX,
                                            const uint16_t* sTab, int64_t warp, LevelStats& ls,
-                                           uint32_t (*sKeep)[kKeepWords]) {
+                                           uint32_t (*sKeep)[kKeepWords], unsigned long long cl,
+                                           unsigned long long ch, bool in_b) {
     const int lane = (int)lane_id();
-    const unsigned long long cl = __ldcg(a.cl_in);
-    const unsigned long long ch = a.ch_in ? __ldcg(a.ch_in) : 0ull;
     // output format: bucket entries once the level's input work is small
     // against the graph (the bucketed lists then skip the edges of unchanged
     // chunks), vertex entries otherwise
     auto out_bucket = [&](int64_t work) {
         return a.bk_end != nullptr && a.bucket_div > 0 && work * a.bucket_div < g.m;
     };
-    const bool in_b = a.fmt_in != nullptr && __ldcg(a.fmt_in) != 0;
     if (in_b) {
         // the queue's buckets, or every bucket when the queue overflowed
         // (ch = overflow word)
@@ -969,13 +972,19 @@ __global__ void __launch_bounds__(kFBlock, kLevelMinBlocks) k_level(GraphDev g, 
     __shared__ uint32_t sKeep[kFBlock / 32][32][kKeepWords];
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    clear_prev_bits(a, warp, nwarps);
     const unsigned long long cl = __ldcg(a.cl_in);
     const unsigned long long ch = a.ch_in ? __ldcg(a.ch_in) : 0ull;
-    if ((cl >> kCountShift) == 0 && (ch >> kCountShift) == 0 && !a.all_changed) return;
+    const bool in_b = a.fmt_in != nullptr && __ldcg(a.fmt_in) != 0;
+    if ((cl >> kCountShift) == 0 && (ch >> kCountShift) == 0 && !a.all_changed) {
+        clear_prev_bits(a, warp, nwarps);
+        return;
+    }
     load_tables(a, sX, sTab);
     LevelStats ls;
-    level_work<KIND, MODE>(g, a, sX, sTab, warp, ls, sKeep[threadIdx.x >> 5]);
+    level_work<KIND, MODE>(g, a, sX, sTab, warp, ls, sKeep[threadIdx.x >> 5], cl, ch, in_b);
+    // the previous level's change bits (read by no one any more) are cleared
+    // after this level's work, off its critical path
+    clear_prev_bits(a, warp, nwarps);
     flush_stats<MODE>(a, ls);
 }
 
@@ -1037,6 +1046,10 @@ __global__ void __launch_bounds__(kFBlock, kPhaseMinBlocks) k_phase(GraphDev g, 
     LevelStats ls;
     int t = 0;
     if (p.level_ns && blockIdx.x == 0 && threadIdx.x == 0) p.level_ns[0] = global_ns();
+    // counters and format of the level's input queue, read once after the
+    // barrier that precedes it
+    unsigned long long pre_l = __ldcg(&p.ctr[0].x), pre_h = __ldcg(&p.ctr[0].y);
+    bool pre_b = p.fmt != nullptr && __ldcg(p.fmt) != 0;
     for (; t < p.max_levels; ++t) {
         const int bi = t % 3, bo = (t + 1) % 3, bp = (t + 2) % 3;
         a.ql_in = p.ql[bi];
@@ -1065,13 +1078,16 @@ __global__ void __launch_bounds__(kFBlock, kPhaseMinBlocks) k_phase(GraphDev g, 
         a.fmt_in = p.fmt ? p.fmt + t : nullptr;
         a.fmt_out = p.fmt ? p.fmt + t + 1 : nullptr;
         a.fmt_prev = (p.fmt && t >= 1) ? p.fmt + t - 1 : nullptr;
+        level_work<KIND, MODE>(g, a, sX, sTab, warp, ls, sKeep[threadIdx.x >> 5], pre_l, pre_h, pre_b);
+        // the previous level's change bits are cleared after this level's
+        // work (off its critical path), before the barrier
         clear_prev_bits(a, warp, nwarps);
-        level_work<KIND, MODE>(g, a, sX, sTab, warp, ls, sKeep[threadIdx.x >> 5]);
         if (!grid_barrier(p.bar_arrive, p.bar_gen, p.abort_flag, a.err, p.limit_ns)) break;
         if (p.level_ns && blockIdx.x == 0 && threadIdx.x == 0) p.level_ns[t + 1] = global_ns();
-        const unsigned long long c2l = __ldcg(&p.ctr[t + 1].x);
-        const unsigned long long c2h = __ldcg(&p.ctr[t + 1].y);
-        if ((c2l >> kCountShift) == 0 && (c2h >> kCountShift) == 0) { ++t; break; }
+        pre_l = __ldcg(&p.ctr[t + 1].x);
+        pre_h = __ldcg(&p.ctr[t + 1].y);
+        pre_b = p.fmt != nullptr && __ldcg(p.fmt + t + 1) != 0;
+        if ((pre_l >> kCountShift) == 0 && (pre_h >> kCountShift) == 0) { ++t; break; }
     }
     flush_stats<MODE>(a, ls);
     // the last queue read (t - 1) still has its change bits; clearing them

@@ -99,6 +99,7 @@ struct LevelArgs {
     uint8_t* fmt_out;
     const uint8_t* fmt_prev;
     int32_t bucket_div;                  // output in bucket format when input work * bucket_div < m
+    int32_t bq_guard;                    // check the bucket queue's fill before each append (huge graphs)
     int32_t vq_cap;                      // vertex queue capacity (n)
 };
 
