@@ -44,8 +44,9 @@ def parse():
     ap.add_argument("--workload", default="rmat20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--mode", default="select", choices=["select", "build"],
-                    help="select: the benchmark; build: time im_sketch_build only (profiling)")
+    ap.add_argument("--mode", default="select", choices=["select", "build", "fillrate"],
+                    help="select: the benchmark; build: time im_sketch_build only (profiling); "
+                         "fillrate: warp fill rate of the live tests, draw order vs sorted X (Table 6 analogue)")
     ap.add_argument("--batch-graphs", type=int, default=512,
                     help="graphs of the batched workload (--workload batched)")
     ap.add_argument("--tuning", default="",
@@ -66,6 +67,22 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of every rank's x (replicas: the slowest rank sets the
+    whole job's time); x itself when not distributed."""
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_value(steps: int, world: int, tmax: float) -> float:
+    """Whole-job throughput of `world` independent replicas that each ran
+    `steps` steps, the slowest in tmax seconds."""
+    return world * steps / tmax
 
 
 def workload_config(wl, g, world):
@@ -397,6 +414,16 @@ def run_gpu(args):
     G = im.im_graph_load(ctx, g.rowptr, g.col, wl.model)
     im.im_ctx_set_timing(ctx, True)
 
+    if args.mode == "fillrate":
+        # the paper's Table 6 setting: J = 1024, uniform w = 0.01 and 0.1; plus weighted cascade
+        rows = []
+        for model in ({"kind": "uniform", "p": 0.01}, {"kind": "uniform", "p": 0.1}, {"kind": "wc"}):
+            r = im.im_fill_rate(G, 1024, seed=wl.seed, model=model)
+            rows.append({"model": model, "J": 1024, **r})
+        if rank == 0:
+            print(json.dumps({"mode": "fillrate", "workload": wl.name, "rows": rows}), flush=True)
+        return 0
+
     if args.mode == "build":
         # profiling mode: sketch builds only (fill + propagation to the fixpoint)
         for _ in range(args.warmup):
@@ -454,10 +481,7 @@ def run_gpu(args):
         dist.barrier()
     clocks = sampler.stop() if sampler else None
     elapsed = ev0.elapsed_time(ev1) / 1e3
-    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tmax = float(t.item())
+    tmax = max_over_ranks(elapsed, dist, "cuda")
 
     # end-to-end through the public API with host buffers: pinned host CSR,
     # graph load (H2D copy) + selection + result read-back every step
@@ -475,10 +499,7 @@ def run_gpu(args):
         deterministic &= (r2["seeds"].tolist() == ref_seeds)
     torch.cuda.synchronize()
     e_el = time.perf_counter() - e0
-    te = torch.tensor([e_el], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e_max = float(te.item())
+    e_max = max_over_ranks(e_el, dist, "cuda")
 
     if rank == 0:
         golden = None
@@ -491,7 +512,7 @@ def run_gpu(args):
         per_launch_bytes = agg["alg_bytes_sweep"] / max(agg["sweep_launches"], 1)
         tr = ncu_traffic(args.workload)
         out = {
-            "metric": METRIC, "value": world * args.steps / tmax, "unit": UNIT, "n_gpus": world,
+            "metric": METRIC, "value": replicas_value(args.steps, world, tmax), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic (seeded R-MAT standing in for the paper's SNAP graphs)",
@@ -512,7 +533,7 @@ def run_gpu(args):
             "counts_per_step": {k: agg[k] / args.steps for k in
                                 ("builds", "sweeps", "sweep_launches", "cover_levels", "launches")},
             "gpu_launches": int(agg["launches"]),
-            "e2e": {"value": (world * args.e2e_steps / e_max) if not args.quick else None, "unit": UNIT,
+            "e2e": {"value": replicas_value(args.e2e_steps, world, e_max) if not args.quick else None, "unit": UNIT,
                     "h2d_bytes_per_step": int(g.rowptr.nbytes + g.col.nbytes),
                     "d2h_bytes_per_step": int(wl.K * (4 + 8 + 8))},
             "clocks": clocks,

@@ -316,6 +316,23 @@ IM_API im_status im_spread_mc(im_graph* g, const int32_t* seeds, int32_t k, int6
                        double* mean_out, double* stderr_out, uint64_t* sum_out,
                        uint64_t* sumsq_out);
 
+/* ---- diagnostics ------------------------------------------------------- */
+
+/* Warp fill rate of the live tests (Sec. 4.1, Table 6 analogue): with the J
+ * simulations drawn from `seed` and the model (the graph's, or `model`: uniform
+ * / weighted cascade / trivalency), over every in-edge:
+ *   counts_out[0] = edges
+ *   counts_out[1] = live (edge, simulation) pairs (Eq. hash_prob)
+ *   counts_out[2] = 32-simulation warps, in draw order, holding a live pair:
+ *                   what a kernel testing every simulation of an edge runs
+ *   counts_out[3] = aligned 32-simulation warps, in sorted-X order, holding a
+ *                   live pair: what a kernel over the candidate range runs
+ *   counts_out[4] = candidate simulations (width of the sorted range)
+ * Fill rate = live / (32 * warps).  Errors: IM_E_INVAL, IM_E_STATE (model fixed
+ * at load), IM_E_NOMEM, IM_E_CUDA. */
+IM_API im_status im_fill_rate(im_graph* g, int32_t J, uint64_t seed, const im_model* model,
+                              uint64_t* counts_out);
+
 /* ---- served form: concurrent queries on resident graphs ----------------- */
 
 /* A query server (the paper has none: it serves one query per run).  It keeps

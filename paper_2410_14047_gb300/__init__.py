@@ -32,7 +32,8 @@ EXPORTS = ["im_ctx_create", "im_ctx_destroy", "im_ctx_bytes_in_use", "im_ctx_byt
            "im_sketch_cover", "im_sketch_rebuild", "im_select_seeds", "im_spread_mc",
            "im_argmax_noalloc", "im_batch_load", "im_batch_free", "im_batch_select_seeds",
            "im_server_create", "im_server_destroy", "im_server_add_graph", "im_server_query_bytes",
-           "im_server_submit", "im_server_wait", "im_server_get_stats", "im_server_clock_ms"]
+           "im_server_submit", "im_server_wait", "im_server_get_stats", "im_server_clock_ms",
+           "im_fill_rate"]
 
 
 class IMError(RuntimeError):
@@ -157,6 +158,7 @@ def load_library(path: str = LIB_PATH):
         "im_server_wait": (ctypes.c_int, [vp, i64, f64, P(im_query_result)]),
         "im_server_get_stats": (ctypes.c_int, [vp, P(im_server_stats)]),
         "im_server_clock_ms": (f64, []),
+        "im_fill_rate": (ctypes.c_int, [vp, i32, u64, P(im_model), P(u64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -365,6 +367,20 @@ def im_select_seeds(graph: Graph, K: int, J: int, model: dict | None = None, see
     if return_sketch:
         out["sketch"] = Sketch(graph, h, J)
     return out
+
+
+def im_fill_rate(graph: Graph, J: int, seed: int = 2410, model: dict | None = None) -> dict:
+    """Warp fill rate of the live tests, draw order vs sorted X (Table 6 analogue)."""
+    keep = []
+    mdl = _model(model, keep)
+    out = np.zeros(5, dtype=np.uint64)
+    graph.ctx.check(graph.ctx.lib.im_fill_rate(graph.handle, int(J), _u64(seed),
+                                               ctypes.byref(mdl) if mdl is not None else None,
+                                               _p(out, ctypes.c_uint64)))
+    edges, live, wdraw, wsort, cands = (int(x) for x in out)
+    return {"edges": edges, "live": live, "warps_draw": wdraw, "warps_sorted": wsort, "candidates": cands,
+            "fill_draw": live / (32 * wdraw) if wdraw else 0.0,
+            "fill_sorted": live / (32 * wsort) if wsort else 0.0}
 
 
 def im_spread_mc(graph: Graph, seeds, R: int, seed: int = 1):

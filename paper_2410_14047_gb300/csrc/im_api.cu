@@ -1399,6 +1399,46 @@ extern "C" im_status im_select_seeds(im_graph* g, int32_t K, int32_t J, const im
 }
 
 // ---------------------------------------------------------------------------
+// warp fill-rate diagnostic (Table 6 analogue)
+// ---------------------------------------------------------------------------
+extern "C" im_status im_fill_rate(im_graph* g, int32_t J, uint64_t seed, const im_model* model,
+                                  uint64_t* counts_out) {
+    if (!g || !counts_out) return IM_E_INVAL;
+    im_ctx* c = g->ctx;
+    if (!valid_J(J)) return fail(c, IM_E_INVAL, "J must be a power of two in [16, 1024], got %d", J);
+    if (model) {
+        CKS(check_model(c, model, g->m));
+        if (model->kind == kExplicit || model->kind == kTargetModel || g->load_kind == kExplicit ||
+            g->load_kind == kTargetModel)
+            return fail(c, IM_E_STATE, "explicit and per-target models are fixed at im_graph_load");
+    }
+    CK(c, cudaSetDevice(c->device));
+    GraphDev dev = g->dev;
+    int kind = g->kind;
+    if (model) model_words(dev, kind, model);
+    DBuf X, salt, tab, cnt;
+    im_status s = dalloc(c, (size_t)J * 4, X);
+    if (s == IM_OK) s = dalloc(c, (size_t)J * 4, salt);
+    if (s == IM_OK) s = dalloc(c, (size_t)kTabSize * 2, tab);
+    if (s == IM_OK) s = dalloc(c, 5 * 8, cnt);
+    auto release = [&]() { dfree(c, X); dfree(c, salt); dfree(c, tab); dfree(c, cnt); };
+    if (s != IM_OK) { release(); return s; }
+    auto st = c->stream;
+    unsigned long long h[5] = {0, 0, 0, 0, 0};
+    cudaError_t e = cudaMemsetAsync(cnt.p, 0, 5 * 8, st);
+    if (e == cudaSuccess) e = launch_sims(seed, J, X.as<uint32_t>(), salt.as<uint32_t>(), tab.as<uint16_t>(), st);
+    if (e == cudaSuccess)
+        e = launch_fill_rate(kind, dev, seed, X.as<uint32_t>(), tab.as<uint16_t>(), J,
+                             cnt.as<unsigned long long>(), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, cnt.p, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    release();
+    if (e != cudaSuccess) return cuda_fail(c, e, "fill rate");
+    for (int i = 0; i < 5; ++i) counts_out[i] = h[i];
+    return IM_OK;
+}
+
+// ---------------------------------------------------------------------------
 // internal entry points of the query server
 // ---------------------------------------------------------------------------
 namespace imi {

@@ -1347,6 +1347,78 @@ __global__ void __launch_bounds__(kFBlock) k_buckets(GraphDev g, const uint32_t*
     });
 }
 
+// Warp fill rate of the live tests (Table 6 analogue).  For every in-edge:
+// the simulations where it is live, counted once; the 32-simulation warps
+// (draw order) that hold one of them — a kernel testing every simulation in
+// draw order runs those warps; and the 32-simulation warps (sorted order,
+// aligned) that hold one of them — a kernel over the sorted candidate range
+// runs those.  out[0] += edges, out[1] += live (edge, simulation) pairs,
+// out[2] += active draw-order warps, out[3] += active sorted-order warps,
+// out[4] += candidate simulations (the sorted range's width).
+template <int KIND>
+__global__ void __launch_bounds__(kFBlock) k_fill_rate(GraphDev g, uint64_t seed, const uint32_t* __restrict__ X,
+                                                       const uint16_t* __restrict__ tab, int J,
+                                                       unsigned long long* __restrict__ out) {
+    __shared__ __align__(16) uint32_t sX[kMaxJ];
+    __shared__ uint16_t sTab[kTabSize];
+    __shared__ uint16_t sDraw[kMaxJ];  // draw index of the simulation at each sorted position
+    __shared__ uint32_t sRaw[kMaxJ];
+    load_sims(X, tab, J, sX, sTab);
+    for (int d = threadIdx.x; d < J; d += blockDim.x)
+        sRaw[d] = (uint32_t)splitmix_at(seed, (uint64_t)d) & 0x7FFFFFFFu;
+    __syncthreads();
+    for (int d = threadIdx.x; d < J; d += blockDim.x) {
+        // the stable sort position of draw d (the order the sketch uses)
+        const uint32_t x = sRaw[d];
+        int r = 0;
+        for (int i = 0; i < J; ++i) r += (sRaw[i] < x) || (sRaw[i] == x && i < d);
+        sDraw[r] = (uint16_t)d;
+    }
+    __syncthreads();
+    unsigned long long edges = 0, live = 0, wdraw = 0, wsort = 0, cands = 0;
+    for_each_edge<KIND, kPush>(g, [&](int64_t, int32_t, int32_t, uint32_t h, uint32_t thr) {
+        ++edges;
+        int lo = 0, hi = 0;
+        if (thr >= 0x80000000u) { lo = 0; hi = J; }
+        else if (thr > 0u) candidate_range(h, thr, J, sX, sTab, lo, hi);
+        cands += (unsigned long long)(hi - lo);
+        uint32_t draw_warps = 0u;   // bit w: draw-order warp w has a live simulation
+        uint32_t sort_warps = 0u;   // bit w: sorted-order warp w has one
+        for (int j = lo; j < hi; ++j) {
+            if ((sX[j] ^ h) < thr) {
+                ++live;
+                sort_warps |= 1u << (j >> 5);
+                draw_warps |= 1u << (sDraw[j] >> 5);
+            }
+        }
+        wdraw += (unsigned long long)__popc(draw_warps);
+        wsort += (unsigned long long)__popc(sort_warps);
+    });
+    edges = wsum(edges); live = wsum(live); wdraw = wsum(wdraw); wsort = wsum(wsort); cands = wsum(cands);
+    if (lane_id() == 0) {
+        atomicAdd(out + 0, edges);
+        atomicAdd(out + 1, live);
+        atomicAdd(out + 2, wdraw);
+        atomicAdd(out + 3, wsort);
+        atomicAdd(out + 4, cands);
+    }
+}
+
+cudaError_t launch_fill_rate(int kind, const GraphDev& g, uint64_t seed, const uint32_t* X, const uint16_t* tab,
+                             int J, unsigned long long* out, cudaStream_t st) {
+    if (g.m == 0) return cudaSuccess;
+    const int64_t groups = (g.m + kLcmEdgesPerWarp - 1) / kLcmEdgesPerWarp;
+    const int64_t want = (groups + (kFBlock / 32) - 1) / (kFBlock / 32);
+    const int grid = (int)max((int64_t)1, min(want, (int64_t)level_grid()));
+    switch (kind) {
+        case kUniform: k_fill_rate<kUniform><<<grid, kFBlock, 0, st>>>(g, seed, X, tab, J, out); break;
+        case kWC: k_fill_rate<kWC><<<grid, kFBlock, 0, st>>>(g, seed, X, tab, J, out); break;
+        case kTrivalency: k_fill_rate<kTrivalency><<<grid, kFBlock, 0, st>>>(g, seed, X, tab, J, out); break;
+        default: k_fill_rate<kExplicit><<<grid, kFBlock, 0, st>>>(g, seed, X, tab, J, out); break;
+    }
+    return cudaGetLastError();
+}
+
 template <int MODE>
 static cudaError_t live_chunks_mode(int kind, const GraphDev& g, const uint32_t* X, const uint16_t* tab, int J,
                                     uint32_t* lo, uint32_t* hi, int grid, cudaStream_t st) {

@@ -205,6 +205,9 @@ cudaError_t launch_batch_pick(const BatchPickArgs& a, cudaStream_t st);
 cudaError_t launch_pick(const PickArgs& a, cudaStream_t st);
 // Live chunk masks of every in-edge (mode kPush) or out-edge (kCover) for the
 // simulations X (sorted) of one sketch.
+// Warp fill-rate counts of the live tests (see k_fill_rate); out[5] accumulates.
+cudaError_t launch_fill_rate(int kind, const GraphDev& g, uint64_t seed, const uint32_t* X, const uint16_t* tab,
+                             int J, unsigned long long* out, cudaStream_t st);
 cudaError_t launch_live_chunks(int kind, int mode, const GraphDev& g, const uint32_t* X, const uint16_t* tab,
                                int J, uint32_t* lo, uint32_t* hi, cudaStream_t st);
 // Bucketed live lists of one orientation (mode kPush: in-edges grouped by
