@@ -578,7 +578,7 @@ static void sketch_plan(im_sketch* sk, int32_t n, int64_t m_edges, int32_t J, Bu
     A(sk->ticket, 4);
     A(sk->stats, (size_t)kStCount * 8);
     A(sk->err, 4);
-    A(sk->bar, 16);
+    A(sk->bar, 512);  // barrier words (16 B) + 64 group counters from byte 256
     A(sk->level_ns, (size_t)(kMaxLevels + 2) * 8);
     A(sk->fmt, (size_t)(kMaxLevels + 2));
     A(sk->lb, (size_t)n * 8);
@@ -803,6 +803,7 @@ static im_status run_phase_persistent(im_sketch* sk, int mode, bool all_first, i
     p.gen_base = sk->gen_counter + 1;
     unsigned int* bar = sk->bar.as<unsigned int>();
     p.bar_arrive = bar;
+    p.bar_groups = bar + 64;
     p.bar_gen = bar + 1;
     p.abort_flag = bar + 2;
     p.levels_out = reinterpret_cast<int*>(bar + 3);
@@ -850,7 +851,8 @@ static im_status run_levels(im_sketch* sk, int mode, bool all_first) {
     im_ctx* c = sk->ctx;
     auto st = c->stream;
     if (c->tuning.persistent) {
-        const int pgrid = phase_grid();
+        // the grid barrier counts arrivals in 64 groups of 32 blocks
+        const int pgrid = std::min(phase_grid(), 64 * 32);
         if (pgrid > 0) return run_phase_persistent(sk, mode, all_first, pgrid);
     }
     ulonglong2* ctr = sk->ctr.as<ulonglong2>();

@@ -230,6 +230,44 @@ __device__ __forceinline__ void vertex_enqueue(const GraphDev& g, const LevelArg
     if constexpr (MODE == kPush) append(want && heavy, o, rp, deg, aux, a.qh_out, a.ch_out, a.vq_cap, a.err);
 }
 
+// Enqueue in two steps around the register update, so that its round trips
+// overlap the update's: `issue` starts the loads and atomics for target o
+// whose 16 registers of chunk c the item raises (imp, predicted from the
+// target piece it loaded: a register another thread raises first changed this
+// level all the same), `finish` appends (warp-collective).
+struct EnqueueState {
+    int32_t rp = 0, deg = 0;
+    uint32_t aux = 0u, old = 0u, os = 0u, oe = 0u;
+    bool fresh = false;
+};
+
+template <int KIND, int MODE>
+__device__ __forceinline__ EnqueueState vertex_enqueue_issue(const GraphDev& g, const LevelArgs& a, int32_t o,
+                                                             uint32_t c, uint32_t imp) {
+    EnqueueState q;
+    if (imp) {
+        atomicOr(a.chg_next + (size_t)o * a.words + (c >> 1), imp << ((c & 1u) * 16u));
+        const int32_t* rpp = MODE == kPush ? g.rp_in : g.rp_out;
+        q.rp = __ldg(rpp + o);
+        q.deg = __ldg(rpp + o + 1);
+        if constexpr (MODE == kPush && KIND == kWC) q.aux = __ldg(g.thr_v + o);
+        q.fresh = atomicExch(a.gen + o, a.gen_next) != a.gen_next;
+    }
+    return q;
+}
+
+template <int KIND, int MODE>
+__device__ __forceinline__ void vertex_enqueue_finish(const GraphDev& g, const LevelArgs& a, bool changed,
+                                                      int32_t o, const EnqueueState& q) {
+    const int32_t deg = q.deg - q.rp;
+    bool heavy = false;
+    if constexpr (MODE == kPush)
+        heavy = changed && is_heavy<KIND>(deg, KIND == kWC ? q.aux : g.thr_uniform, a.heavy_indeg);
+    const bool want = changed && q.fresh && deg > 0;
+    append(want && !heavy, o, q.rp, deg, q.aux, a.ql_out, a.cl_out, a.vq_cap, a.err);
+    if constexpr (MODE == kPush) append(want && heavy, o, q.rp, deg, q.aux, a.qh_out, a.ch_out, a.vq_cap, a.err);
+}
+
 // Forward declarations (bucket mode, below).
 __device__ __forceinline__ uint32_t bucket_start(const uint32_t* __restrict__ end, int64_t b);
 __device__ __forceinline__ void bucket_append(bool want, uint32_t b, uint32_t start, uint32_t len,
@@ -253,6 +291,26 @@ __device__ __forceinline__ void bucket_enqueue(const LevelArgs& a, bool changed,
         want = ((old >> sh) & 0xFFFFu) == 0u && oe > os;
     }
     bucket_append(want, ob, os, oe - os, a.ql_out, a.cl_out, a.ch_out, a.bq_cap, a.bq_guard != 0);
+}
+
+__device__ __forceinline__ EnqueueState bucket_enqueue_issue(const LevelArgs& a, int32_t o, uint32_t c,
+                                                             uint32_t imp) {
+    EnqueueState q;
+    if (imp) {
+        const uint32_t ob = (uint32_t)o * (uint32_t)a.chunks + c;
+        q.oe = __ldcg(a.bk_end + ob);
+        q.os = bucket_start(a.bk_end, ob);
+        q.old = atomicOr(a.chg_next + (size_t)o * a.words + (c >> 1), imp << ((c & 1u) * 16u));
+    }
+    return q;
+}
+
+__device__ __forceinline__ void bucket_enqueue_finish(const LevelArgs& a, bool changed, int32_t o, uint32_t c,
+                                                      const EnqueueState& q) {
+    const uint32_t sh = (c & 1u) * 16u;
+    const bool want = changed && ((q.old >> sh) & 0xFFFFu) == 0u && q.oe > q.os;
+    bucket_append(want, (uint32_t)o * (uint32_t)a.chunks + c, q.os, q.oe - q.os, a.ql_out, a.cl_out, a.ch_out,
+                  a.bq_cap, a.bq_guard != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -369,8 +427,9 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
             const int32_t q_i = __shfl_sync(0xFFFFFFFFu, qv, i);
             const uint32_t h_i = __shfl_sync(0xFFFFFFFFu, h, i);
             const uint32_t t_i = __shfl_sync(0xFFFFFFFFu, thr, i);
-            uint32_t nbits = 0u;
+            uint32_t nbits = 0u, imp = 0u;
             int chunk = 0;
+            EnqueueState eq;
             if (k < total) {
                 chunk = nth_chunk(ml_i, mh_i, k - ex_i);
                 uint32_t chb = 0xFFFFu;
@@ -395,7 +454,13 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                         if constexpr (MODE == kPush) cand[w] = sw[w] & L & ~visited_bytes(sw[w]);
                         else cand[w] = L & visited_bytes(sw[w]) & ~visited_bytes(tw[w]);
                         any |= cand[w];
+                        // registers this item raises, as the loaded target piece shows
+                        if constexpr (MODE == kPush) imp |= bytes_to_bits(byte_max(tw[w], cand[w]) ^ tw[w]) << (4 * w);
+                        else imp |= bytes_to_bits(cand[w]) << (4 * w);
                     }
+                    // the enqueue's loads and atomics go out before the register update
+                    eq = out_b ? bucket_enqueue_issue(a, o_i, (uint32_t)chunk, imp)
+                               : vertex_enqueue_issue<KIND, MODE>(g, a, o_i, (uint32_t)chunk, imp);
                     if (any) {
                         ++st_chunks;
                         if constexpr (MODE == kPush) {
@@ -415,14 +480,13 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                                 }
                             }
                         }
-                        if (nbits && !out_b)
-                            atomicOr(a.chg_next + (size_t)o_i * words + (chunk >> 1), nbits << ((chunk & 1) * 16));
                     }
                 }
             }
+            (void)nbits;
             // enqueue what changed: the vertex, or its chunk's bucket
-            if (out_b) bucket_enqueue(a, nbits != 0u, o_i, (uint32_t)chunk, nbits);
-            else vertex_enqueue<KIND, MODE>(g, a, nbits != 0u, o_i);
+            if (out_b) bucket_enqueue_finish(a, imp != 0u, o_i, (uint32_t)chunk, eq);
+            else vertex_enqueue_finish<KIND, MODE>(g, a, imp != 0u, o_i, eq);
         }
         qi = qn;
         raw = rawn;
@@ -736,22 +800,32 @@ __device__ __forceinline__ void bucket_slice(const GraphDev& g, const LevelArgs&
             m16 = __ldg(a.bk_mask + e);
             src = ld_cg16(a.M + (size_t)u * J + c * 16);
         }
+        uint32_t imp = 0u;
+        uint4 tg = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t cand[4] = {0u, 0u, 0u, 0u};
+        uint32_t any = 0u;
+        uint8_t* trow = a.M + (size_t)o * J + c * 16;
         if (f < fend && chb) {
             ++st_dealt;
             m16 &= chb;
-            uint8_t* trow = a.M + (size_t)o * J + c * 16;
-            const uint4 tg = ld_cg16(trow);
+            tg = ld_cg16(trow);
             const uint32_t sw[4] = {src.x, src.y, src.z, src.w};
             const uint32_t tw[4] = {tg.x, tg.y, tg.z, tg.w};
-            uint32_t cand[4];
-            uint32_t any = 0u;
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
                 const uint32_t L = bits_to_bytes((m16 >> (4 * w)) & 0xFu);
                 if constexpr (MODE == kPush) cand[w] = sw[w] & L & ~visited_bytes(sw[w]);
                 else cand[w] = L & visited_bytes(sw[w]) & ~visited_bytes(tw[w]);
                 any |= cand[w];
+                // registers this item raises, as the loaded target piece shows
+                if constexpr (MODE == kPush) imp |= bytes_to_bits(byte_max(tw[w], cand[w]) ^ tw[w]) << (4 * w);
+                else imp |= bytes_to_bits(cand[w]) << (4 * w);
             }
+        }
+        // the enqueue's loads and atomics go out before the register update
+        const EnqueueState eq = out_b ? bucket_enqueue_issue(a, o, c, imp)
+                                      : vertex_enqueue_issue<KIND, MODE>(g, a, o, c, imp);
+        {
             if (any) {
                 ++st_chunks;
                 if constexpr (MODE == kPush) {
@@ -772,14 +846,11 @@ __device__ __forceinline__ void bucket_slice(const GraphDev& g, const LevelArgs&
                 }
             }
         }
+        (void)nbits;
         // enqueue what changed: the target's bucket of this chunk, or the
         // target vertex
-        if (out_b) {
-            bucket_enqueue(a, nbits != 0u, o, c, nbits);
-        } else {
-            if (nbits) atomicOr(a.chg_next + (size_t)o * words + (c >> 1), nbits << ((c & 1u) * 16u));
-            vertex_enqueue<KIND, MODE>(g, a, nbits != 0u, o);
-        }
+        if (out_b) bucket_enqueue_finish(a, imp != 0u, o, c, eq);
+        else vertex_enqueue_finish<KIND, MODE>(g, a, imp != 0u, o, eq);
     }
 }
 
@@ -817,13 +888,66 @@ __device__ __forceinline__ void clear_prev_bits(const LevelArgs& a, int64_t warp
     }
 }
 
+// Clearing the previous level's change bits as claimable units (taken by the
+// warps that find no work, off the critical path of the ones that do): mode 1
+// vertex entries (all words of each), 2 bucket entries (their 16 bits), 3 the
+// whole buffer (an overflowed bucket queue); 32 entries or 1024 words a unit.
+struct ClearPlan {
+    int mode = 0;
+    int64_t n = 0, units = 0, nl = 0;
+};
+
+__device__ __forceinline__ ClearPlan clear_plan(const LevelArgs& a, unsigned long long pl, unsigned long long ph,
+                                                bool pb) {
+    ClearPlan c;
+    if (!a.chg_prev) return c;
+    const int32_t nlp = (int32_t)(pl >> kCountShift);
+    if (pb) {
+        if (nlp > a.bq_cap || ph != 0ull) {
+            c.mode = 3;
+            c.n = (int64_t)a.nbuckets / a.chunks * a.words;
+            c.units = (c.n + 1023) >> 10;
+        } else {
+            c.mode = 2;
+            c.n = nlp;
+            c.units = (c.n + 31) >> 5;
+        }
+    } else {
+        c.mode = 1;
+        c.nl = nlp;
+        c.n = (int64_t)nlp + (int64_t)(ph >> kCountShift);
+        c.units = (c.n + 31) >> 5;
+    }
+    return c;
+}
+
+__device__ __forceinline__ void clear_unit(const LevelArgs& a, const ClearPlan& c, int64_t u) {
+    const int lane = (int)lane_id();
+    if (c.mode == 3) {
+        for (int64_t i = (u << 10) + lane; i < min(c.n, (u + 1) << 10); i += 32) a.chg_prev[i] = 0u;
+    } else if (c.mode == 2) {
+        const int64_t i = (u << 5) + lane;
+        if (i < c.n) {
+            const uint32_t b = (uint32_t)__ldcg(&a.ql_prev[i].v);
+            const uint32_t v = b / (uint32_t)a.chunks, ch = b % (uint32_t)a.chunks;
+            reinterpret_cast<uint16_t*>(a.chg_prev)[(size_t)v * a.words * 2 + ch] = 0;
+        }
+    } else if (c.mode == 1) {
+        const int64_t i = (u << 5) + lane;
+        if (i < c.n) {
+            const int32_t v = i < c.nl ? __ldcg(&a.ql_prev[i].v) : __ldcg(&a.qh_prev[i - c.nl].v);
+            for (int w = 0; w < a.words; ++w) a.chg_prev[(size_t)v * a.words + w] = 0u;
+        }
+    }
+}
+
 // Work of one level: heavy vertices first, then slices of light batches, all
 // claimed from the level's counter.
 template <int KIND, int MODE>
 __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a, const uint32_t* sX,
                                            const uint16_t* sTab, int64_t warp, LevelStats& ls,
                                            uint32_t (*sKeep)[kKeepWords], unsigned long long cl,
-                                           unsigned long long ch, bool in_b) {
+                                           unsigned long long ch, bool in_b, const ClearPlan& cp) {
     const int lane = (int)lane_id();
     // output format: bucket entries once the level's input work is small
     // against the graph (the bucketed lists then skip the edges of unchanged
@@ -843,7 +967,7 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
         const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
         const int64_t lb = max((int64_t)1, min((int64_t)a.light_batches, nbl / nwarps));
         const int64_t units = (nbl + lb - 1) / lb;
-        if (units == 0) return;
+        if (units + cp.units == 0) return;
         if (warp == 0 && lane == 0) {
             atomicAdd(a.stats + (MODE == kPush ? kStSweepBuckets : kStCoverVertices), (unsigned long long)nq);
             if (MODE == kCover) atomicAdd(a.stats + kStCoverEdges, (unsigned long long)E);
@@ -853,7 +977,11 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
             unsigned int unit = 0;
             if (lane == 0) unit = atomicAdd(a.claim, 1u);
             unit = __shfl_sync(0xFFFFFFFFu, unit, 0);
-            if ((int64_t)unit >= units) break;
+            if ((int64_t)unit >= units + cp.units) break;
+            if ((int64_t)unit >= units) {
+                clear_unit(a, cp, (int64_t)unit - units);
+                continue;
+            }
             const int64_t b0 = (int64_t)unit * lb;
             const int64_t b1 = min(nbl, b0 + lb);
             bucket_slice<KIND, MODE>(g, a, a.ql_in, b0, b1, nq, E, dense, ls.chunks, ls.cas, ls.fresh,
@@ -892,7 +1020,7 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
     const int64_t total = nhv + lunits + hunits;
     const bool out_b = out_bucket(El + Eh);
     if (a.fmt_out && blockIdx.x == 0 && threadIdx.x == 0) *a.fmt_out = out_b ? 1 : 0;
-    if (total == 0) return;
+    if (total + cp.units == 0) return;
     if (warp == 0 && lane == 0) {
         atomicAdd(a.stats + (MODE == kPush ? kStSweepVertices : kStCoverVertices),
                   (unsigned long long)(nl + nh));
@@ -904,8 +1032,10 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
         unsigned int unit = 0;
         if (lane == 0) unit = atomicAdd(a.claim, 1u);
         unit = __shfl_sync(0xFFFFFFFFu, unit, 0);
-        if ((int64_t)unit >= total) break;
-        if ((int64_t)unit < nhv) {
+        if ((int64_t)unit >= total + cp.units) break;
+        if ((int64_t)unit >= total) {
+            clear_unit(a, cp, (int64_t)unit - total);
+        } else if ((int64_t)unit < nhv) {
             if constexpr (MODE == kPush && (KIND == kWC || KIND == kUniform)) {
                 const int4 raw = __ldcg(reinterpret_cast<const int4*>(a.qh_in) + unit);
                 QEntry ent;
@@ -981,10 +1111,11 @@ __global__ void __launch_bounds__(kFBlock, kLevelMinBlocks) k_level(GraphDev g, 
     }
     load_tables(a, sX, sTab);
     LevelStats ls;
-    level_work<KIND, MODE>(g, a, sX, sTab, warp, ls, sKeep[threadIdx.x >> 5], cl, ch, in_b);
     // the previous level's change bits (read by no one any more) are cleared
-    // after this level's work, off its critical path
-    clear_prev_bits(a, warp, nwarps);
+    // by the warps that find no work
+    const ClearPlan cp = clear_plan(a, a.cl_prev ? __ldcg(a.cl_prev) : 0ull, a.ch_prev ? __ldcg(a.ch_prev) : 0ull,
+                                    a.fmt_prev != nullptr && __ldcg(a.fmt_prev) != 0);
+    level_work<KIND, MODE>(g, a, sX, sTab, warp, ls, sKeep[threadIdx.x >> 5], cl, ch, in_b, cp);
     flush_stats<MODE>(a, ls);
 }
 
@@ -998,34 +1129,50 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-__device__ bool grid_barrier(unsigned int* arrive, volatile unsigned int* gen, volatile unsigned int* abort_flag,
-                             uint32_t* err, unsigned long long limit_ns) {
+__device__ bool grid_barrier(unsigned int* groups, unsigned int* arrive, volatile unsigned int* gen,
+                             volatile unsigned int* abort_flag, uint32_t* err, unsigned long long limit_ns,
+                             unsigned int g0) {
+    // two-level arrival (groups of 32 blocks, then the groups) keeps the
+    // atomics on any one word to 32 at most; the waits poll only the
+    // generation word, with the abort word and the clock every 32 polls
     __syncthreads();
     __shared__ bool ok;
     if (threadIdx.x == 0) {
         ok = true;
-        const unsigned int g0 = *gen;
+        // g0: the generation word's value before this barrier (it counts the
+        // barriers passed, so the caller knows it without a read)
         __threadfence();
-        const unsigned int arrived = atomicAdd(arrive, 1u);
-        if (arrived == gridDim.x - 1) {
-            *arrive = 0u;
+        const unsigned int grp = blockIdx.x >> 5;
+        const unsigned int gsize = min(32u, gridDim.x - grp * 32u);
+        const unsigned int ngroups = (gridDim.x + 31u) >> 5;
+        bool last = false;
+        if (atomicAdd(groups + grp, 1u) == gsize - 1u) {
+            groups[grp] = 0u;
             __threadfence();
-            atomicAdd((unsigned int*)gen, 1u);
-        } else {
+            if (atomicAdd(arrive, 1u) == ngroups - 1u) {
+                *arrive = 0u;
+                __threadfence();
+                atomicAdd((unsigned int*)gen, 1u);
+                last = true;
+            }
+        }
+        if (!last) {
             const unsigned long long t0 = global_ns();
+            unsigned int it = 0;
             while (*gen == g0) {
-                if (*abort_flag) { ok = false; break; }
-                if (global_ns() - t0 > limit_ns) {
-                    atomicOr(err, kErrBarrier);
-                    *abort_flag = 1u;
-                    ok = false;
-                    break;
+                if ((++it & 31u) == 0u) {
+                    if (*abort_flag) { ok = false; break; }
+                    if (global_ns() - t0 > limit_ns) {
+                        atomicOr(err, kErrBarrier);
+                        *abort_flag = 1u;
+                        ok = false;
+                        break;
+                    }
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
         __threadfence();
-        if (*abort_flag) ok = false;
     }
     __syncthreads();
     return ok;
@@ -1050,6 +1197,9 @@ __global__ void __launch_bounds__(kFBlock, kPhaseMinBlocks) k_phase(GraphDev g, 
     // barrier that precedes it
     unsigned long long pre_l = __ldcg(&p.ctr[0].x), pre_h = __ldcg(&p.ctr[0].y);
     bool pre_b = p.fmt != nullptr && __ldcg(p.fmt) != 0;
+    // the previous level's input counters and format (its bits are cleared now)
+    unsigned long long prev_l = 0ull, prev_h = 0ull;
+    bool prev_b = false;
     for (; t < p.max_levels; ++t) {
         const int bi = t % 3, bo = (t + 1) % 3, bp = (t + 2) % 3;
         a.ql_in = p.ql[bi];
@@ -1078,11 +1228,15 @@ __global__ void __launch_bounds__(kFBlock, kPhaseMinBlocks) k_phase(GraphDev g, 
         a.fmt_in = p.fmt ? p.fmt + t : nullptr;
         a.fmt_out = p.fmt ? p.fmt + t + 1 : nullptr;
         a.fmt_prev = (p.fmt && t >= 1) ? p.fmt + t - 1 : nullptr;
-        level_work<KIND, MODE>(g, a, sX, sTab, warp, ls, sKeep[threadIdx.x >> 5], pre_l, pre_h, pre_b);
-        // the previous level's change bits are cleared after this level's
-        // work (off its critical path), before the barrier
-        clear_prev_bits(a, warp, nwarps);
-        if (!grid_barrier(p.bar_arrive, p.bar_gen, p.abort_flag, a.err, p.limit_ns)) break;
+        // the previous level's change bits are cleared by the warps that find
+        // no work this level
+        const ClearPlan cp = clear_plan(a, prev_l, prev_h, prev_b);
+        level_work<KIND, MODE>(g, a, sX, sTab, warp, ls, sKeep[threadIdx.x >> 5], pre_l, pre_h, pre_b, cp);
+        prev_l = pre_l;
+        prev_h = pre_h;
+        prev_b = pre_b;
+        if (!grid_barrier(p.bar_groups, p.bar_arrive, p.bar_gen, p.abort_flag, a.err, p.limit_ns, (unsigned int)t))
+            break;
         if (p.level_ns && blockIdx.x == 0 && threadIdx.x == 0) p.level_ns[t + 1] = global_ns();
         pre_l = __ldcg(&p.ctr[t + 1].x);
         pre_h = __ldcg(&p.ctr[t + 1].y);

@@ -114,7 +114,8 @@ struct PhaseArgs {
     int all_first;
     int max_levels;
     int32_t gen_base;                    // enqueue stamp of level t = gen_base + t
-    unsigned int* bar_arrive;
+    unsigned int* bar_groups;            // per group of 32 blocks: arrivals at the current barrier
+    unsigned int* bar_arrive;            // groups arrived
     unsigned int* bar_gen;
     unsigned int* abort_flag;
     unsigned long long limit_ns;         // bound on every barrier wait
