@@ -117,6 +117,9 @@ typedef struct {
     uint64_t sweep_edges_live;/* examined in-edges live in a chunk where the source changed */
     uint64_t sweep_buckets;   /* (vertex, chunk) buckets queued for propagation levels */
     uint64_t sweep_bucket_entries; /* bucket list entries processed by propagation levels */
+    uint64_t affected;        /* registers recomputed by incremental rebuilds */
+    uint64_t pull_buckets;    /* out-buckets queued by the pulls of incremental rebuilds */
+    uint64_t pull_entries;    /* out-bucket entries walked by those pulls */
 } im_stats;
 
 /* Schedule knobs of the frontier kernels (chosen by the autotuner; results
@@ -139,7 +142,10 @@ typedef struct {
  * entries per edge, else edge scans only), and a level whose input work (edges
  * or entries) times b is below m queues the changed (vertex, chunk) groups, so
  * that the next level visits only the edges of changed chunks; 0 = edge scans
- * with live chunk masks throughout. */
+ * with live chunk masks throughout; incremental: 1 = im_select_seeds rebuilds
+ * only the registers a rebuild can change (those of vertices that reach a
+ * register visited since the last build) when the sketch has the bucketed
+ * lists, 2 = also over edge scans, 0 = full rebuilds. */
 typedef struct {
     int32_t heavy_indeg;
     int32_t light_batches;
@@ -149,6 +155,7 @@ typedef struct {
     int32_t dense_div;
     int32_t lazy_pick;
     int32_t buckets;
+    int32_t incremental;
 } im_tuning;
 
 /* One frontier launch of the last selection / build (tracing on). */
@@ -181,7 +188,7 @@ IM_API im_status im_last_stats(const im_ctx* ctx, im_stats* out);
  * stream and report per-kind kernel time in im_stats (adds two event records
  * per launch).  Off by default. */
 IM_API im_status im_ctx_set_timing(im_ctx* ctx, int enable);
-/* Sets (NULL = defaults {256, 4, 0, 2, 1, 0, 1, 2}) or reads the schedule knobs. */
+/* Sets (NULL = defaults {256, 4, 0, 2, 1, 0, 1, 2, 1}) or reads the schedule knobs. */
 IM_API im_status im_ctx_set_tuning(im_ctx* ctx, const im_tuning* tuning);
 IM_API im_status im_ctx_get_tuning(const im_ctx* ctx, im_tuning* tuning);
 /* enable != 0: also keep one im_trace_rec per frontier level (implies timing):

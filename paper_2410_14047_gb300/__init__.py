@@ -66,14 +66,15 @@ class im_stats(ctypes.Structure):
                                                "cover_chunks", "visited", "alg_bytes_sweep",
                                                "sweep_heavy", "sweep_heavy_sims", "sweep_batches",
                                                "sweep_dealt", "sweep_edges_live", "sweep_buckets",
-                                               "sweep_bucket_entries")]
+                                               "sweep_bucket_entries", "affected",
+                                               "pull_buckets", "pull_entries")]
 
 
 class im_tuning(ctypes.Structure):
     _fields_ = [("heavy_indeg", ctypes.c_int32), ("light_batches", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("persistent", ctypes.c_int32), ("dense_div", ctypes.c_int32),
-                ("lazy_pick", ctypes.c_int32), ("buckets", ctypes.c_int32)]
+                ("lazy_pick", ctypes.c_int32), ("buckets", ctypes.c_int32), ("incremental", ctypes.c_int32)]
 
 
 class im_trace_rec(ctypes.Structure):

@@ -44,7 +44,7 @@ struct im_ctx {
     bool trace = false;
     std::vector<float> launch_ms;    // kernel time per launch sequence number (tracing)
     std::vector<im_trace_rec> recs;  // frontier launches of the last call
-    im_tuning tuning{256, 4, 0, 2, 1, 0, 1, 2};
+    im_tuning tuning{256, 4, 0, 2, 1, 0, 1, 2, 1};
 };
 
 namespace {
@@ -227,7 +227,8 @@ struct im_sketch {
     int32_t J = 0;
     DBuf M, X, salt, tab, ql[3], qh[3], ctr, claim, chg[3], gen, seed_bits, count, part_S, part_u,
         ticket, stats, err, bar, lb, cand, part_S2, part_u2, lcm_in_lo, lcm_in_hi, lcm_out_lo, lcm_out_hi,
-        level_ns, fmt;
+        level_ns, fmt, nv, aff, alist, acount, aldeg, aloff, almask, ascan, apctr;
+    bool incr = false;      // covers record newly visited registers; rebuilds are incremental
     // bucket mode: bucketed live lists per orientation (0: in-edges, 1:
     // out-edges); the light queues then hold buckets, bq_cap entries each
     DBuf bk_end[2], bk_other[2], bk_mask[2];
@@ -309,12 +310,12 @@ extern "C" im_status im_ctx_set_timing(im_ctx* c, int enable) {
 extern "C" im_status im_ctx_set_tuning(im_ctx* c, const im_tuning* t) {
     if (!c) return IM_E_INVAL;
     if (!t) {
-        c->tuning = im_tuning{256, 4, 0, 2, 1, 0, 1, 2};
+        c->tuning = im_tuning{256, 4, 0, 2, 1, 0, 1, 2, 1};
         return IM_OK;
     }
     if (t->heavy_indeg < 0 || t->light_batches < 1 || t->light_batches > 4096 || t->grid_blocks < 0 ||
         t->check_every < 1 || t->check_every > 64 || t->persistent < 0 || t->persistent > 1 ||
-        t->dense_div < 0 || t->lazy_pick < 0 || t->lazy_pick > 1 || t->buckets < 0 || t->buckets > 1024)
+        t->dense_div < 0 || t->lazy_pick < 0 || t->lazy_pick > 1 || t->buckets < 0 || t->buckets > 1024 || t->incremental < 0 || t->incremental > 2)
         return fail(c, IM_E_INVAL, "tuning out of range");
     c->tuning = *t;
     return IM_OK;
@@ -581,6 +582,17 @@ static void sketch_plan(im_sketch* sk, int32_t n, int64_t m_edges, int32_t J, Bu
     A(sk->bar, 512);  // barrier words (16 B) + 64 group counters from byte 256
     A(sk->level_ns, (size_t)(kMaxLevels + 2) * 8);
     A(sk->fmt, (size_t)(kMaxLevels + 2));
+    // incremental rebuilds: newly visited and affected register bits, the
+    // affected vertices
+    A(sk->nv, (size_t)n * ((J + 31) / 32) * 4);
+    A(sk->aff, (size_t)n * ((J + 31) / 32) * 4);
+    A(sk->alist, (size_t)n * 4);
+    A(sk->aldeg, (size_t)n * 4);
+    A(sk->aloff, ((size_t)n + 1) * 4);
+    A(sk->almask, (size_t)n * 8);
+    A(sk->ascan, scan_tmp_bytes(n));
+    A(sk->acount, 4);
+    A(sk->apctr, 16);
     A(sk->lb, (size_t)n * 8);
     A(sk->cand, 4);
     A(sk->part_S2, (size_t)pg * 8);
@@ -667,6 +679,8 @@ static im_status sketch_alloc(im_ctx* c, im_graph* g, int32_t J, im_sketch** out
     if (e == cudaSuccess) e = cudaMemsetAsync(sk->stats.p, 0, sk->stats.bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(sk->err.p, 0, 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(sk->M.p, 0, sk->M.bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sk->nv.p, 0, sk->nv.bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sk->aff.p, 0, sk->aff.bytes, st);
     if (e != cudaSuccess) {
         sketch_release(sk);
         delete sk;
@@ -727,7 +741,9 @@ static DBuf& chg_buf(im_sketch* sk, int mode, int i) {
 
 // Live chunk masks of the phase's edge orientation.
 static void set_lcm(LevelArgs& a, const im_sketch* sk, int mode) {
-    const bool in = mode == kPush;
+    const bool in = mode != kCover;
+    a.aff = sk->aff.as<uint32_t>();
+    a.nv = (mode == kCover && sk->incr) ? sk->nv.as<uint32_t>() : nullptr;
     a.lcm_lo = (in ? sk->lcm_in_lo : sk->lcm_out_lo).as<uint32_t>();
     a.lcm_hi = sk->J > 512 ? (in ? sk->lcm_in_hi : sk->lcm_out_hi).as<uint32_t>() : nullptr;
     a.chunks = sk->J / 16;
@@ -766,13 +782,14 @@ static im_status check_err(im_sketch* sk) {
 // back to zero.  A phase that completes leaves its change masks zero (the
 // last level's bits are cleared by the phase itself); after a new sketch or a
 // failed phase they are cleared here.
-static im_status phase_begin(im_sketch* sk, int mode) {
+static im_status phase_begin(im_sketch* sk, int mode, int fmt0 = -1) {
     im_ctx* c = sk->ctx;
     auto st = c->stream;
     CK(c, cudaMemsetAsync(sk->ctr.p, 0, sk->ctr.bytes, st));
-    // the level-0 queue: bucket entries for a cover in bucket mode (the seed
-    // kernel writes them), vertex entries otherwise
-    CK(c, cudaMemsetAsync(sk->fmt.p, (mode == kCover && sk->buckets) ? 1 : 0, 1, st));
+    // the level-0 queue: bucket entries (fmt0 = 1, or by default for a cover
+    // in bucket mode: the seed kernel writes them), vertex entries otherwise
+    if (fmt0 < 0) fmt0 = (mode == kCover && sk->buckets) ? 1 : 0;
+    CK(c, cudaMemsetAsync(sk->fmt.p, fmt0, 1, st));
     CK(c, cudaMemsetAsync(sk->claim.p, 0, sk->claim.bytes, st));
     if (sk->chg_dirty) {
         for (int i = 0; i < 3; ++i) CK(c, cudaMemsetAsync(sk->chg[i].p, 0, sk->chg[i].bytes, st));
@@ -963,6 +980,81 @@ static im_status propagate(im_sketch* sk) {
     return run_levels(sk, kPush, true);
 }
 
+// Incremental rebuild (same registers as build_registers after covers):
+// affected-set search from the registers visited since the last build, reset
+// and pull of the affected registers, propagation from them.
+static im_status incremental_rebuild(im_sketch* sk) {
+    im_ctx* c = sk->ctx;
+    auto st = c->stream;
+    ulonglong2* ctr = sk->ctr.as<ulonglong2>();
+    IncrArgs x{};
+    x.nv = sk->nv.as<uint32_t>();
+    x.salt = sk->salt.as<uint32_t>();
+    x.hkey = sk->g->hkey.as<int32_t>();
+    x.list = sk->alist.as<int32_t>();
+    x.ldeg = sk->aldeg.as<int32_t>();
+    x.loff = sk->aloff.as<int32_t>();
+    x.lmask = sk->almask.as<uint2>();
+    x.list_count = sk->acount.as<unsigned int>();
+    x.buckets = sk->buckets ? 1 : 0;
+    // the pull queue: the third light queue, free between phases
+    x.pq = sk->ql[2].as<QEntry>();
+    x.pctr = sk->apctr.as<unsigned long long>();
+    // 1. the affected registers (level 0 in bucket format where the sketch
+    // has bucketed lists)
+    CKS(phase_begin(sk, kAffect, x.buckets));
+    LevelArgs a = level_args(sk);
+    set_lcm(a, sk, kAffect);
+    a.ql_out = sk->ql[0].as<QEntry>();
+    a.cl_out = &ctr[0].x;
+    a.qh_out = sk->qh[0].as<QEntry>();
+    a.ch_out = &ctr[0].y;
+    a.chg_next = chg_buf(sk, kAffect, 0).as<uint32_t>();
+    CK(c, timed(c, kTOther, [&] { return launch_incremental(0, sk->kind, sk->dev, a, x, st); }));
+    CKS(run_levels(sk, kAffect, false));
+    // 2. reset to the own ranks, list of affected vertices (and their
+    // affected chunks' out-buckets); 3. pull over their out-edges
+    LevelArgs b = level_args(sk);
+    set_lcm(b, sk, kCover);
+    CK(c, cudaMemsetAsync(x.list_count, 0, 4, st));
+    CK(c, cudaMemsetAsync(x.pctr, 0, 16, st));
+    CK(c, timed(c, kTFill, [&] { return launch_incremental(1, sk->kind, sk->dev, b, x, st); }));
+    CK(c, cudaMemcpyAsync(c->pinned, x.list_count, 4, cudaMemcpyDeviceToHost, st));
+    CK(c, cudaMemcpyAsync(c->pinned + 1, x.pctr, 16, cudaMemcpyDeviceToHost, st));
+    CK(c, sync_collect(c));
+    x.count = (int32_t)(uint32_t)c->pinned[0];
+    const int64_t npull = (int64_t)(c->pinned[1] >> kCountShift);
+    x.pull_buckets = sk->buckets && c->pinned[2] == 0 && npull <= sk->bq_cap ? 1 : 0;
+    if (x.pull_buckets) {
+        c->stats.pull_buckets += (uint64_t)npull;
+        c->stats.pull_entries += c->pinned[1] & kEdgeMask;
+    }
+    if (x.count > 0) {
+        CK(c, timed(c, kTPush, [&] {
+            if (!x.pull_buckets) {
+                cudaError_t e = launch_exclusive_scan(x.ldeg, x.count, sk->aloff.as<int32_t>(), sk->ascan.p, st);
+                if (e != cudaSuccess) return e;
+            }
+            return launch_incremental(2, sk->kind, sk->dev, b, x, st);
+        }));
+    }
+    // 4. propagation from the affected registers
+    CKS(phase_begin(sk, kPush, x.buckets));
+    LevelArgs p = level_args(sk);
+    set_lcm(p, sk, kPush);
+    p.ql_out = sk->ql[0].as<QEntry>();
+    p.cl_out = &ctr[0].x;
+    p.qh_out = sk->qh[0].as<QEntry>();
+    p.ch_out = &ctr[0].y;
+    p.chg_next = chg_buf(sk, kPush, 0).as<uint32_t>();
+    CK(c, timed(c, kTOther, [&] { return launch_incremental(3, sk->kind, sk->dev, p, x, st); }));
+    CKS(run_levels(sk, kPush, false));
+    // 5. the next rebuild starts from what covers visit after this one
+    CK(c, cudaMemsetAsync(sk->nv.p, 0, sk->nv.bytes, st));
+    CK(c, cudaMemsetAsync(sk->aff.p, 0, sk->aff.bytes, st));
+    return IM_OK;
+}
+
 // Fill (Alg. 1) of the non-visited registers, then Simulate to the fixpoint.
 static im_status build_registers(im_sketch* sk) {
     im_ctx* c = sk->ctx;
@@ -1005,6 +1097,7 @@ static im_status stats_collect(im_sketch* sk) {
     s.sweep_edges_live = h[kStSweepLiveEdges];
     s.sweep_buckets = h[kStSweepBuckets];
     s.sweep_bucket_entries = h[kStSweepBucketEntries];
+    s.affected = h[kStAffected];
     // algorithmic bytes of the sweeps: queue entry (16 B) + the queued vertex's
     // register row (J B) per queued vertex; live chunk mask (4 B, 8 B when
     // J = 1024) per in-edge; source id + edge hash (8 B, + 4 B threshold for
@@ -1249,6 +1342,7 @@ static PickArgs pick_args(im_sketch* sk, int k) {
     a.mark = 1;
     a.bk_end_out = sk->buckets ? sk->bk_end[1].as<uint32_t>() : nullptr;
     a.chunks = sk->J / 16;
+    a.nv = sk->incr ? sk->nv.as<uint32_t>() : nullptr;
     return a;
 }
 
@@ -1340,6 +1434,9 @@ static im_status select_seeds_impl(im_ctx* c, im_graph* g, int32_t K, int32_t J,
     im_sketch* sk = nullptr;
     CKS(sketch_start(c, g, J, seed, model, &sk));
     sk->lazy = c->tuning.lazy_pick != 0;
+    // incremental rebuilds pay off with bucketed lists (sparse affected-set
+    // searches); over edge scans a full rebuild is faster unless asked for (2)
+    sk->incr = c->tuning.incremental == 2 || (c->tuning.incremental == 1 && sk->buckets);
     auto bail = [&](im_status s) {
         sketch_release(sk);
         delete sk;
@@ -1365,7 +1462,7 @@ static im_status select_seeds_impl(im_ctx* c, im_graph* g, int32_t K, int32_t J,
         const double tr = now_ms();
         ms_pc += tr - tk;
         if (k + 1 < K && rebuild_due(count, oldcount, J, rebuild_eps)) {
-            if ((s = build_registers(sk)) != IM_OK) return bail(s);
+            if ((s = sk->incr ? incremental_rebuild(sk) : build_registers(sk)) != IM_OK) return bail(s);
             oldcount = count;
             ++rebuilds;
             ms_rebuild += now_ms() - tr;

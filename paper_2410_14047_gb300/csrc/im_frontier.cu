@@ -216,10 +216,10 @@ __device__ __forceinline__ void vertex_enqueue(const GraphDev& g, const LevelArg
     bool heavy = false;
     if (changed) {
         // the enqueue stamp and the row words are fetched together
-        const int32_t* rpp = MODE == kPush ? g.rp_in : g.rp_out;
+        const int32_t* rpp = MODE != kCover ? g.rp_in : g.rp_out;
         rp = __ldg(rpp + o);
         deg = __ldg(rpp + o + 1);
-        if constexpr (MODE == kPush && KIND == kWC) aux = __ldg(g.thr_v + o);
+        if constexpr (MODE != kCover && KIND == kWC) aux = __ldg(g.thr_v + o);
         want = atomicExch(a.gen + o, a.gen_next) != a.gen_next;
         deg -= rp;
         if constexpr (MODE == kPush)
@@ -247,10 +247,10 @@ __device__ __forceinline__ EnqueueState vertex_enqueue_issue(const GraphDev& g, 
     EnqueueState q;
     if (imp) {
         atomicOr(a.chg_next + (size_t)o * a.words + (c >> 1), imp << ((c & 1u) * 16u));
-        const int32_t* rpp = MODE == kPush ? g.rp_in : g.rp_out;
+        const int32_t* rpp = MODE != kCover ? g.rp_in : g.rp_out;
         q.rp = __ldg(rpp + o);
         q.deg = __ldg(rpp + o + 1);
-        if constexpr (MODE == kPush && KIND == kWC) q.aux = __ldg(g.thr_v + o);
+        if constexpr (MODE != kCover && KIND == kWC) q.aux = __ldg(g.thr_v + o);
         q.fresh = atomicExch(a.gen + o, a.gen_next) != a.gen_next;
     }
     return q;
@@ -266,6 +266,29 @@ __device__ __forceinline__ void vertex_enqueue_finish(const GraphDev& g, const L
     const bool want = changed && q.fresh && deg > 0;
     append(want && !heavy, o, q.rp, deg, q.aux, a.ql_out, a.cl_out, a.vq_cap, a.err);
     if constexpr (MODE == kPush) append(want && heavy, o, q.rp, deg, q.aux, a.qh_out, a.ch_out, a.vq_cap, a.err);
+}
+
+// Affected-set search (incremental rebuild): marks the simulations of
+// chunk c in which target o becomes affected (cand: 0xFF bytes where o is
+// reached along a live edge and its register is not visited); returns the
+// 16 bits that were not marked before.
+__device__ __forceinline__ uint32_t mark_affected(const LevelArgs& a, const uint32_t cand[4], int32_t o, uint32_t c,
+                                                  unsigned long long& st_new) {
+    uint32_t b16 = 0u;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) b16 |= bytes_to_bits(cand[w]) << (4 * w);
+    if (!b16) return 0u;
+    const uint32_t sh = (c & 1u) * 16u;
+    const uint32_t old = atomicOr(a.aff + (size_t)o * a.words + (c >> 1), b16 << sh);
+    const uint32_t fresh = b16 & ~(old >> sh) & 0xFFFFu;
+    st_new += (unsigned)__popc(fresh);
+    return fresh;
+}
+
+// Cover: registers newly visited since the last build (the next incremental
+// rebuild starts from them).
+__device__ __forceinline__ void note_newly_visited(const LevelArgs& a, int32_t o, uint32_t c, uint32_t nbits) {
+    if (a.nv && nbits) atomicOr(a.nv + (size_t)o * a.words + (c >> 1), nbits << ((c & 1u) * 16u));
 }
 
 // Forward declarations (bucket mode, below).
@@ -363,7 +386,7 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
         if (f < fend) {
             m_lo = __ldg(a.lcm_lo + e);
             if (a.lcm_hi) m_hi = __ldg(a.lcm_hi + e);
-            if constexpr (MODE == kPush) {
+            if constexpr (MODE != kCover) {
                 o = __ldg(g.src_in + e);
                 h = __ldg(g.h_in + e);
                 if constexpr (KIND == kExplicit) thr = __ldg(g.thr_in + e);
@@ -393,7 +416,7 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
         m_hi &= __shfl_sync(0xFFFFFFFFu, cm_hi, myw);
         const int nch = __popc(m_lo) + __popc(m_hi);
         if (nch) {
-            if constexpr (MODE == kPush) {
+            if constexpr (MODE != kCover) {
                 if constexpr (KIND != kExplicit) thr = edge_threshold<KIND, true>(g, (uint32_t)o, (uint32_t)qv, e, qaux);
             } else {
                 if constexpr (KIND != kExplicit && KIND != kWC)
@@ -452,16 +475,18 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                     for (int w = 0; w < 4; ++w) {
                         const uint32_t L = live4(xs[w], h_i, t_i) & bits_to_bytes((chb >> (4 * w)) & 0xFu);
                         if constexpr (MODE == kPush) cand[w] = sw[w] & L & ~visited_bytes(sw[w]);
-                        else cand[w] = L & visited_bytes(sw[w]) & ~visited_bytes(tw[w]);
+                        else if constexpr (MODE == kCover) cand[w] = L & visited_bytes(sw[w]) & ~visited_bytes(tw[w]);
+                        else cand[w] = L & ~visited_bytes(tw[w]);
                         any |= cand[w];
                         // registers this item raises, as the loaded target piece shows
                         if constexpr (MODE == kPush) imp |= bytes_to_bits(byte_max(tw[w], cand[w]) ^ tw[w]) << (4 * w);
-                        else imp |= bytes_to_bits(cand[w]) << (4 * w);
+                        else if constexpr (MODE == kCover) imp |= bytes_to_bits(cand[w]) << (4 * w);
                     }
+                    if constexpr (MODE == kAffect) imp = mark_affected(a, cand, o_i, (uint32_t)chunk, st_new);
                     // the enqueue's loads and atomics go out before the register update
                     eq = out_b ? bucket_enqueue_issue(a, o_i, (uint32_t)chunk, imp)
                                : vertex_enqueue_issue<KIND, MODE>(g, a, o_i, (uint32_t)chunk, imp);
-                    if (any) {
+                    if (MODE != kAffect && any) {
                         ++st_chunks;
                         if constexpr (MODE == kPush) {
                             nbits = merge_chunk(trow, cand, tg, st_cas, a.err);
@@ -479,6 +504,7 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                                                   (unsigned long long)(__popc(really) >> 3));
                                 }
                             }
+                            note_newly_visited(a, o_i, (uint32_t)chunk, nbits);
                         }
                     }
                 }
@@ -815,17 +841,19 @@ __device__ __forceinline__ void bucket_slice(const GraphDev& g, const LevelArgs&
             for (int w = 0; w < 4; ++w) {
                 const uint32_t L = bits_to_bytes((m16 >> (4 * w)) & 0xFu);
                 if constexpr (MODE == kPush) cand[w] = sw[w] & L & ~visited_bytes(sw[w]);
-                else cand[w] = L & visited_bytes(sw[w]) & ~visited_bytes(tw[w]);
+                else if constexpr (MODE == kCover) cand[w] = L & visited_bytes(sw[w]) & ~visited_bytes(tw[w]);
+                else cand[w] = L & ~visited_bytes(tw[w]);
                 any |= cand[w];
                 // registers this item raises, as the loaded target piece shows
                 if constexpr (MODE == kPush) imp |= bytes_to_bits(byte_max(tw[w], cand[w]) ^ tw[w]) << (4 * w);
-                else imp |= bytes_to_bits(cand[w]) << (4 * w);
+                else if constexpr (MODE == kCover) imp |= bytes_to_bits(cand[w]) << (4 * w);
             }
+            if constexpr (MODE == kAffect) imp = mark_affected(a, cand, o, c, st_new);
         }
         // the enqueue's loads and atomics go out before the register update
         const EnqueueState eq = out_b ? bucket_enqueue_issue(a, o, c, imp)
                                       : vertex_enqueue_issue<KIND, MODE>(g, a, o, c, imp);
-        {
+        if (MODE != kAffect) {
             if (any) {
                 ++st_chunks;
                 if constexpr (MODE == kPush) {
@@ -843,6 +871,7 @@ __device__ __forceinline__ void bucket_slice(const GraphDev& g, const LevelArgs&
                                 atomicAdd(a.gcount + __ldg(a.gid + o), (unsigned long long)(__popc(really) >> 3));
                         }
                     }
+                    note_newly_visited(a, o, c, nbits);
                 }
             }
         }
@@ -953,6 +982,9 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
     // against the graph (the bucketed lists then skip the edges of unchanged
     // chunks), vertex entries otherwise
     auto out_bucket = [&](int64_t work) {
+        // the affected-set search is sparse in simulations: bucket queues
+        // whenever the sketch has the lists
+        if (MODE == kAffect) return a.bk_end != nullptr;
         return a.bk_end != nullptr && a.bucket_div > 0 && work * a.bucket_div < g.m;
     };
     if (in_b) {
@@ -1077,12 +1109,14 @@ __device__ __forceinline__ void flush_stats(const LevelArgs& a, LevelStats& ls) 
             if (ls.chunks) atomicAdd(a.stats + kStSweepChunks, ls.chunks);
             if (ls.cas) atomicAdd(a.stats + kStSweepCas, ls.cas);
             if (ls.hsims) atomicAdd(a.stats + kStSweepHeavySims, ls.hsims);
-        } else {
+        } else if constexpr (MODE == kCover) {
             if (ls.chunks) atomicAdd(a.stats + kStCoverChunks, ls.chunks);
             if (ls.fresh) {
                 atomicAdd(a.stats + kStCoverNew, ls.fresh);
                 atomicAdd(a.count, ls.fresh);
             }
+        } else {
+            if (ls.fresh) atomicAdd(a.stats + kStAffected, ls.fresh);
         }
     }
     ls = LevelStats();
@@ -1270,6 +1304,8 @@ int phase_grid() {
         int pc = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, k_phase<kWC, kCover>, kFBlock, 0);
         if (pc < per_sm) per_sm = pc;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, k_phase<kWC, kAffect>, kFBlock, 0);
+        if (pc < per_sm) per_sm = pc;
         for (int kd : {0, 2, 3}) {
             int q = 0;
             if (kd == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_phase<kUniform, kPush>, kFBlock, 0);
@@ -1297,6 +1333,14 @@ cudaError_t launch_phase(int kind, int mode, const GraphDev& g, const PhaseArgs&
             case kWC: return coop_launch<kWC, kPush>(g, p, grid, st);
             case kTrivalency: return coop_launch<kTrivalency, kPush>(g, p, grid, st);
             default: return coop_launch<kExplicit, kPush>(g, p, grid, st);
+        }
+    }
+    if (mode == kAffect) {
+        switch (kind) {
+            case kUniform: return coop_launch<kUniform, kAffect>(g, p, grid, st);
+            case kWC: return coop_launch<kWC, kAffect>(g, p, grid, st);
+            case kTrivalency: return coop_launch<kTrivalency, kAffect>(g, p, grid, st);
+            default: return coop_launch<kExplicit, kAffect>(g, p, grid, st);
         }
     }
     switch (kind) {
@@ -1334,6 +1378,7 @@ static cudaError_t launch_level_mode(int kind, const GraphDev& g, const LevelArg
 
 cudaError_t launch_level(int kind, int mode, const GraphDev& g, const LevelArgs& a, int grid,
                          cudaStream_t st) {
+    if (mode == kAffect) return launch_level_mode<kAffect>(kind, g, a, grid, st);
     return mode == kPush ? launch_level_mode<kPush>(kind, g, a, grid, st)
                          : launch_level_mode<kCover>(kind, g, a, grid, st);
 }
@@ -1354,13 +1399,14 @@ cudaError_t launch_level(int kind, int mode, const GraphDev& g, const LevelArgs&
 // ---------------------------------------------------------------------------
 constexpr int kLcmEdgesPerWarp = 512;
 
-// Last row r in [lo, hi) with rp[r] <= e (rp non-decreasing, rp[lo] <= e), warp-wide.
-__device__ __forceinline__ int32_t row_of_warp(const int32_t* __restrict__ rp, int32_t lo, int32_t hi, int64_t e) {
+// Last row r in [lo, hi) with start(r) <= e (starts non-decreasing, start(lo) <= e), warp-wide.
+template <class S>
+__device__ __forceinline__ int32_t row_of_warp(S&& start, int32_t lo, int32_t hi, int64_t e) {
     const int lane = (int)lane_id();
     while (hi - lo > 1) {
         const int32_t step = (hi - lo + 31) >> 5;
         const int64_t idx = (int64_t)lo + (int64_t)step * (lane + 1);
-        const bool le = idx < hi && (int64_t)__ldg(rp + idx) <= e;
+        const bool le = idx < hi && start((int32_t)idx) <= e;
         const int c = __popc(__ballot_sync(0xFFFFFFFFu, le));
         const int32_t nlo = lo + step * c;
         const int32_t nhi = (c < 32) ? (int32_t)min((int64_t)hi, (int64_t)lo + (int64_t)step * (c + 1)) : hi;
@@ -1371,10 +1417,11 @@ __device__ __forceinline__ int32_t row_of_warp(const int32_t* __restrict__ rp, i
 }
 
 // Same search by one thread (binary).
-__device__ __forceinline__ int32_t row_of_thread(const int32_t* __restrict__ rp, int32_t lo, int32_t hi, int64_t e) {
+template <class S>
+__device__ __forceinline__ int32_t row_of_thread(S&& start, int32_t lo, int32_t hi, int64_t e) {
     while (hi - lo > 1) {
         const int32_t mid = lo + ((hi - lo) >> 1);
-        if ((int64_t)__ldg(rp + mid) <= e) lo = mid; else hi = mid;
+        if (start(mid) <= e) lo = mid; else hi = mid;
     }
     return lo;
 }
@@ -1400,53 +1447,82 @@ __device__ __forceinline__ void edge_chunk_masks(uint32_t h, uint32_t thr, int J
     }
 }
 
+// Edge-balanced walk of a flat space [0, m) split into rows by the
+// non-decreasing starts start(0..nrows) (start(0) = 0, start(nrows) = m), a
+// warp taking kLcmEdgesPerWarp consecutive positions; ALL: every lane calls
+// fn(f, row, valid) together, else fn(f, row) once per position.
+template <bool ALL, class S, class F>
+__device__ __forceinline__ void walk_rows_by(S&& start, int32_t nrows, int64_t m, F&& fn) {
+    const int lane = (int)lane_id();
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s0 = warp * kLcmEdgesPerWarp; s0 < m; s0 += nwarps * kLcmEdgesPerWarp) {
+        const int64_t s1 = min(m, s0 + kLcmEdgesPerWarp);
+        int32_t r0 = row_of_warp(start, 0, nrows, s0);
+        for (int64_t f0 = s0; f0 < s1; f0 += 32) {
+            const int64_t e = f0 + lane;
+            // starts of rows r0 .. r0+31 (rows past nrows start after every position)
+            const int64_t r = (int64_t)r0 + lane;
+            const int64_t beg = r <= nrows ? start((int32_t)r) : INT64_MAX;
+            int i = 0;
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                const int64_t b = __shfl_sync(0xFFFFFFFFu, beg, (i + s) & 31);
+                if (i + s <= 31 && b <= e) i += s;
+            }
+            int32_t v = r0 + i;
+            // past the 32 rows (a run of empty rows): own search
+            if (e < s1 && i == 31 && r0 + 32 <= nrows && start(r0 + 32) <= e)
+                v = row_of_thread(start, r0 + 31, nrows, e);
+            // the next batch starts in the row of this batch's last position
+            r0 = __shfl_sync(0xFFFFFFFFu, v, 31);
+            if constexpr (ALL) {
+                fn(e, v, e < s1);
+            } else {
+                if (e >= s1) continue;
+                fn(e, v);
+            }
+        }
+    }
+}
+
+// Edge-balanced walk of a flat space [0, m) split into rows by the
+// non-decreasing starts rp[0..nrows] (rp[0] = 0, rp[nrows] = m): fn(f, row)
+// once per position, a warp taking kLcmEdgesPerWarp consecutive positions.
+template <class F>
+__device__ __forceinline__ void walk_rows(const int32_t* __restrict__ rp, int32_t nrows, int64_t m, F&& fn) {
+    walk_rows_by<false>([rp](int32_t r) -> int64_t { return (int64_t)__ldg(rp + r); }, nrows, m, fn);
+}
+
+// The same walk with the row starts given by start(r) (start(nrows) = m),
+// fn(f, row, valid) called by every lane of the warp together (valid false
+// past the end), so fn may use warp-wide operations.
+template <class S, class F>
+__device__ __forceinline__ void walk_rows_all(S&& start, int32_t nrows, int64_t m, F&& fn) {
+    walk_rows_by<true>(start, nrows, m, fn);
+}
+
 // Every edge of one CSR orientation with its row (the owner vertex), the
 // other endpoint, hash and threshold, edge-balanced over warps:
 // fn(e, row, other, h, thr) once per edge.
 template <int KIND, int MODE, class F>
 __device__ __forceinline__ void for_each_edge(const GraphDev& g, F&& fn) {
-    const int lane = (int)lane_id();
     const int32_t* rp = MODE == kPush ? g.rp_in : g.rp_out;
-    const int64_t m = g.m;
-    const int32_t n = g.n;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t s0 = warp * kLcmEdgesPerWarp; s0 < m; s0 += nwarps * kLcmEdgesPerWarp) {
-        const int64_t s1 = min(m, s0 + kLcmEdgesPerWarp);
-        int32_t r0 = row_of_warp(rp, 0, n, s0);
-        for (int64_t f0 = s0; f0 < s1; f0 += 32) {
-            const int64_t e = f0 + lane;
-            // starts of rows r0 .. r0+31 (rows past n start after every edge)
-            const int64_t r = (int64_t)r0 + lane;
-            const int32_t beg = r <= n ? __ldg(rp + r) : 0x7FFFFFFF;
-            int i = 0;
-#pragma unroll
-            for (int s = 16; s >= 1; s >>= 1) {
-                const int32_t b = __shfl_sync(0xFFFFFFFFu, beg, (i + s) & 31);
-                if (i + s <= 31 && (int64_t)b <= e) i += s;
-            }
-            int32_t v = r0 + i;
-            // past the 32 rows (a run of empty rows): own search
-            if (e < s1 && i == 31 && r0 + 32 <= n && (int64_t)__ldg(rp + r0 + 32) <= e)
-                v = row_of_thread(rp, r0 + 31, n, e);
-            // the next batch starts in the row of this batch's last edge
-            r0 = __shfl_sync(0xFFFFFFFFu, v, 31);
-            if (e >= s1) continue;
-            uint32_t h, thr;
-            int32_t other;
-            if constexpr (MODE == kPush) {
-                other = __ldg(g.src_in + e);
-                h = __ldg(g.h_in + e);
-                const uint32_t aux = KIND == kWC ? __ldg(g.thr_v + v) : 0u;
-                thr = edge_threshold<KIND, true>(g, (uint32_t)other, (uint32_t)v, e, aux);
-            } else {
-                other = __ldg(g.col_out + e);
-                h = __ldg(g.h_out + e);
-                thr = edge_threshold<KIND, false>(g, (uint32_t)v, (uint32_t)other, e, 0u);
-            }
-            fn(e, v, other, h, thr);
+    walk_rows(rp, g.n, g.m, [&](int64_t e, int32_t v) {
+        uint32_t h, thr;
+        int32_t other;
+        if constexpr (MODE == kPush) {
+            other = __ldg(g.src_in + e);
+            h = __ldg(g.h_in + e);
+            const uint32_t aux = KIND == kWC ? __ldg(g.thr_v + v) : 0u;
+            thr = edge_threshold<KIND, true>(g, (uint32_t)other, (uint32_t)v, e, aux);
+        } else {
+            other = __ldg(g.col_out + e);
+            h = __ldg(g.h_out + e);
+            thr = edge_threshold<KIND, false>(g, (uint32_t)v, (uint32_t)other, e, 0u);
         }
-    }
+        fn(e, v, other, h, thr);
+    });
 }
 
 __device__ __forceinline__ void load_sims(const uint32_t* X, const uint16_t* tab, int J, uint32_t* sX,
@@ -1654,6 +1730,368 @@ cudaError_t launch_init_queues(int kind, const GraphDev& g, const LevelArgs& a, 
         case kWC: k_init_queues<kWC><<<grid, kFBlock, 0, st>>>(g, a); break;
         case kTrivalency: k_init_queues<kTrivalency><<<grid, kFBlock, 0, st>>>(g, a); break;
         default: k_init_queues<kExplicit><<<grid, kFBlock, 0, st>>>(g, a); break;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Incremental rebuild (Alg. 4's rebuild computed exactly on the registers it
+// can change).  After covers since the last build, a non-visited register
+// (u, j) changes at the rebuild only if u reaches, along live edges of
+// simulation j through non-visited vertices, a vertex visited since the last
+// build: otherwise u's reach set avoiding the visited vertices is the same as
+// at the last build (whatever a visited vertex reaches is visited).  The
+// affected registers are found by a search from the newly visited ones along
+// in-edges (kAffect levels), reset to the vertex's own rank, raised by a pull
+// over their out-edges (whose other registers hold final values), and the
+// propagation then runs from the affected registers only.
+// ---------------------------------------------------------------------------
+
+// Level-0 bucket entries (block-collective; lanes with valid false add
+// none): for each chunk c of vertex v whose 16 bits in `bits` are nonzero and
+// whose bucket (of a's orientation) is nonempty, the bucket goes to the queue
+// (q, ctr, overflow word) and, with chg, the bits to that change mask.  The
+// block reserves its entries with one global atomic (warps first reserve
+// theirs in shared memory), so queue order and edge offsets agree.
+__device__ __forceinline__ void bucket_level0(const LevelArgs& a, bool valid, int32_t v,
+                                              const uint32_t* __restrict__ bits, uint32_t* chg, QEntry* q,
+                                              unsigned long long* ctr, unsigned long long* overflow) {
+    __shared__ unsigned long long s_ctr, s_base;
+    const int lane = (int)lane_id();
+    uint32_t cm_lo = 0u, cm_hi = 0u;
+    if (valid)
+        for (int w = 0; w < a.words; ++w) {
+            const uint32_t hb = halves_nonzero(__ldcg(bits + (size_t)v * a.words + w));
+            if (w < 16) cm_lo |= hb << (2 * w);
+            else cm_hi |= hb << (2 * (w - 16));
+        }
+    const uint32_t ul = __reduce_or_sync(0xFFFFFFFFu, cm_lo), uh = __reduce_or_sync(0xFFFFFFFFu, cm_hi);
+    // the buckets this lane queues (chunk bits) and their entries
+    uint32_t q_lo = 0u, q_hi = 0u, my_len = 0u;
+    {
+        uint32_t wl = ul, wh = uh;
+        while (wl | wh) {
+            int c;
+            if (wl) { c = __ffs(wl) - 1; wl &= wl - 1; }
+            else { c = 32 + __ffs(wh) - 1; wh &= wh - 1; }
+            if (!(((c < 32 ? cm_lo >> c : cm_hi >> (c - 32)) & 1u))) continue;
+            const int64_t b = (int64_t)v * a.chunks + c;
+            const uint32_t st = bucket_start(a.bk_end, b), en = __ldcg(a.bk_end + b);
+            if (en <= st) continue;
+            if (c < 32) q_lo |= 1u << c; else q_hi |= 1u << (c - 32);
+            my_len += en - st;
+        }
+    }
+    const uint32_t my_cnt = (uint32_t)(__popc(q_lo) + __popc(q_hi));
+    const uint32_t w_cnt = __reduce_add_sync(0xFFFFFFFFu, my_cnt);
+    const uint32_t w_len = __reduce_add_sync(0xFFFFFFFFu, my_len);
+    if (threadIdx.x == 0) s_ctr = 0ull;
+    __syncthreads();
+    unsigned long long wbase = 0ull;
+    if (lane == 0 && w_cnt)
+        wbase = atomicAdd(&s_ctr, ((unsigned long long)w_cnt << kCountShift) | (unsigned long long)w_len);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long tot = s_ctr;
+        unsigned long long base = ~0ull;
+        if (tot) {
+            if (a.bq_guard && (int32_t)(__ldcg(ctr) >> kCountShift) >= a.bq_cap) atomicOr(overflow, 1ull);
+            else base = atomicAdd(ctr, tot);
+        }
+        s_base = base;
+    }
+    __syncthreads();
+    const unsigned long long gb = s_base;
+    if (w_cnt == 0) return;
+    // a block refused by a full queue still sets its change bits (the level
+    // then walks every bucket)
+    const bool queued = gb != ~0ull;
+    // this warp's range, then each lane's entries in lane order
+    wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
+    uint32_t ex_cnt = my_cnt, ex_len = my_len;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        const uint32_t yc = __shfl_up_sync(0xFFFFFFFFu, ex_cnt, s), yl = __shfl_up_sync(0xFFFFFFFFu, ex_len, s);
+        if (lane >= s) { ex_cnt += yc; ex_len += yl; }
+    }
+    ex_cnt -= my_cnt;
+    ex_len -= my_len;
+    int32_t slot = (int32_t)((gb >> kCountShift) + (wbase >> kCountShift)) + (int32_t)ex_cnt;
+    uint32_t off = (uint32_t)((gb & kEdgeMask) + (wbase & kEdgeMask)) + ex_len;
+    const uint16_t* b16 = reinterpret_cast<const uint16_t*>(bits);
+    uint16_t* h16 = reinterpret_cast<uint16_t*>(chg);
+    while (q_lo | q_hi) {
+        int c;
+        if (q_lo) { c = __ffs(q_lo) - 1; q_lo &= q_lo - 1; }
+        else { c = 32 + __ffs(q_hi) - 1; q_hi &= q_hi - 1; }
+        const int64_t b = (int64_t)v * a.chunks + c;
+        const uint32_t st = bucket_start(a.bk_end, b), en = __ldcg(a.bk_end + b);
+        if (h16) h16[(size_t)v * a.words * 2 + c] = __ldcg(b16 + (size_t)v * a.words * 2 + c);
+        if (!queued) continue;
+        if (slot < a.bq_cap) {
+            QEntry e;
+            e.v = (int32_t)b; e.rp = (int32_t)st; e.off = (int32_t)off; e.aux = en - st;
+            q[slot] = e;
+        } else {
+            atomicOr(overflow, 1ull);
+        }
+        ++slot;
+        off += en - st;
+    }
+}
+
+// Level-0 vertex entry of v whose change bits are `bits` (one thread): the
+// bits go to the change mask; want tells whether v has in-edges and a bit.
+template <int KIND>
+__device__ __forceinline__ void vertex_level0(const GraphDev& g, const LevelArgs& a, int32_t v,
+                                              const uint32_t* __restrict__ bits, bool& want, int32_t& rp,
+                                              int32_t& deg, uint32_t& aux, bool& heavy, bool push) {
+    want = false;
+    heavy = false;
+    rp = g.rp_in[v];
+    deg = g.rp_in[v + 1] - rp;
+    aux = 0u;
+    if constexpr (KIND == kWC) aux = g.thr_v[v];
+    if (deg <= 0) return;
+    uint32_t any = 0u;
+    for (int w = 0; w < a.words; ++w) any |= __ldcg(bits + (size_t)v * a.words + w);
+    if (!any) return;
+    for (int w = 0; w < a.words; ++w) a.chg_next[(size_t)v * a.words + w] = __ldcg(bits + (size_t)v * a.words + w);
+    if (push) heavy = is_heavy<KIND>(deg, KIND == kWC ? aux : g.thr_uniform, a.heavy_indeg);
+    want = true;
+}
+
+// Level 0 of the affected-set search: the newly visited registers (nv).
+template <int KIND>
+__global__ void __launch_bounds__(kFBlock) k_affect_init(GraphDev g, LevelArgs a, const uint32_t* __restrict__ nv,
+                                                         int buckets) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x; v0 < g.n; v0 += stride) {
+        const int64_t v = v0 + threadIdx.x;
+        if (buckets) {
+            bucket_level0(a, v < g.n, (int32_t)v, nv, a.chg_next, a.ql_out, a.cl_out, a.ch_out);
+            continue;
+        }
+        bool want = false, heavy = false;
+        int32_t rp = 0, deg = 0;
+        uint32_t aux = 0u;
+        if (v < g.n) vertex_level0<KIND>(g, a, (int32_t)v, nv, want, rp, deg, aux, heavy, false);
+        append(want, (int32_t)v, rp, deg, aux, a.ql_out, a.cl_out, g.n, a.err);
+    }
+}
+
+// Affected registers back to the vertex's own rank (Alg. 1); every vertex with
+// one goes to `list` with its out-degree and the chunks of its affected bits,
+// and, with out-bucket lists (o.bk_end), its affected chunks' out-buckets to
+// the pull queue (pq, pctr[0] packed counter, pctr[1] overflow word).
+__global__ void __launch_bounds__(kFBlock) k_reset_affected(uint8_t* __restrict__ M, int32_t n, int J, int words,
+                                                            const uint32_t* __restrict__ salt,
+                                                            const int32_t* __restrict__ hkey,
+                                                            const uint32_t* __restrict__ aff, const int32_t* __restrict__ rp_out,
+                                                            int32_t* __restrict__ list, int32_t* __restrict__ ldeg,
+                                                            uint2* __restrict__ lmask, unsigned int* __restrict__ list_count,
+                                                            LevelArgs o, QEntry* pq, unsigned long long* pctr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x; v0 < n; v0 += stride) {
+        const int64_t v = v0 + threadIdx.x;
+        bool listed = false;
+        uint2 lm = make_uint2(0u, 0u);
+        if (v < n) {
+            uint32_t am_lo = 0u, am_hi = 0u;
+            const uint32_t ku = mm3_k(hkey ? (uint32_t)hkey[v] : (uint32_t)v);
+            for (int w = 0; w < words; ++w) {
+                uint32_t b = __ldcg(aff + (size_t)v * words + w);
+                const uint32_t hb = halves_nonzero(b);
+                if (w < 16) am_lo |= hb << (2 * w);
+                else am_hi |= hb << (2 * (w - 16));
+                while (b) {
+                    const int j = 32 * w + __ffs(b) - 1;
+                    b &= b - 1;
+                    M[(size_t)v * J + j] = (uint8_t)rank_of(ku, __ldg(salt + j));
+                }
+            }
+            listed = (am_lo | am_hi) != 0u;
+            lm = make_uint2(am_lo, am_hi);
+        }
+        // one list reservation per warp
+        const unsigned wm = __ballot_sync(0xFFFFFFFFu, listed);
+        if (wm) {
+            const int lane = (int)lane_id();
+            unsigned int base = 0u;
+            if (lane == 0) base = atomicAdd(list_count, (unsigned)__popc(wm));
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            if (listed) {
+                const unsigned int i = base + __popc(wm & ((1u << lane) - 1u));
+                list[i] = (int32_t)v;
+                ldeg[i] = rp_out[v + 1] - rp_out[v];
+                lmask[i] = lm;
+            }
+        }
+        if (o.bk_end) bucket_level0(o, v < n, (int32_t)v, aff, nullptr, pq, pctr, pctr + 1);
+    }
+}
+
+// Pull of the affected registers of the listed vertices over their
+// out-edges, edge-balanced (a hub's out-edges spread over many warps):
+// M[u][j] = max(M[u][j], M[w][j]) for every live (u -> w) in an affected
+// simulation j with w not visited, merged by CAS.
+template <int KIND>
+__global__ void __launch_bounds__(kFBlock) k_pull_affected(GraphDev g, LevelArgs a, const int32_t* __restrict__ list,
+                                                           const int32_t* __restrict__ loff,
+                                                           const uint2* __restrict__ lmask, int32_t count) {
+    const int64_t total = __ldcg(loff + count);
+    __shared__ __align__(16) uint32_t sX[kMaxJ];
+    __shared__ uint16_t sTab[kTabSize];
+    load_sims(a.X, a.tab, a.J, sX, sTab);
+    const int J = a.J, words = a.words;
+    unsigned long long n_cas = 0;
+    walk_rows(loff, count, total, [&](int64_t f, int32_t row) {
+        const int32_t u = __ldg(list + row);
+        const int64_t e = (int64_t)__ldg(g.rp_out + u) + (f - __ldg(loff + row));
+        const uint2 am = __ldg(lmask + row);
+        uint32_t m_lo = __ldg(a.lcm_lo + e) & am.x;
+        uint32_t m_hi = a.lcm_hi ? (__ldg(a.lcm_hi + e) & am.y) : 0u;
+        if (!(m_lo | m_hi)) return;
+        const int32_t w = __ldg(g.col_out + e);
+        const uint32_t h = __ldg(g.h_out + e);
+        const uint32_t thr = edge_threshold<KIND, false>(g, (uint32_t)u, (uint32_t)w, e, 0u);
+        const uint32_t* au = a.aff + (size_t)u * words;
+        while (m_lo | m_hi) {
+            int c;
+            if (m_lo) { c = __ffs(m_lo) - 1; m_lo &= m_lo - 1; }
+            else { c = 32 + __ffs(m_hi) - 1; m_hi &= m_hi - 1; }
+            const uint32_t a16 = (__ldcg(au + (c >> 1)) >> ((c & 1) * 16)) & 0xFFFFu;
+            const uint4* xs = reinterpret_cast<const uint4*>(sX + c * 16);
+            const uint4 pw = ld_cg16(a.M + (size_t)w * J + c * 16);
+            const uint32_t pv[4] = {pw.x, pw.y, pw.z, pw.w};
+            uint32_t cand[4];
+            uint32_t any = 0u;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t L = live4(xs[q], h, thr) & bits_to_bytes((a16 >> (4 * q)) & 0xFu);
+                cand[q] = pv[q] & L & ~visited_bytes(pv[q]);
+                any |= cand[q];
+            }
+            if (!any) continue;
+            uint8_t* urow = a.M + (size_t)u * J + c * 16;
+            merge_chunk(urow, cand, ld_cg16(urow), n_cas, a.err);
+        }
+    });
+}
+
+// The same pull over the out-bucket lists (a: out orientation): the queue
+// holds the affected chunks' buckets; positions of one bucket (one register
+// piece M[u][16c..16c+16)) are max-combined across the warp first, so one lane
+// per bucket and batch merges.
+__global__ void __launch_bounds__(kFBlock) k_pull_buckets(LevelArgs a, const QEntry* __restrict__ q,
+                                                          const unsigned long long* __restrict__ pctr) {
+    const unsigned long long cv = __ldcg(pctr);
+    const int32_t nq = (int32_t)(cv >> kCountShift);
+    const int64_t total = (int64_t)(cv & kEdgeMask);
+    const int J = a.J, words = a.words;
+    const uint32_t C = (uint32_t)a.chunks;
+    const int lane = (int)lane_id();
+    unsigned long long n_cas = 0;
+    walk_rows_all([&](int32_t r) -> int64_t { return r < nq ? (int64_t)__ldg(&q[r].off) : total; }, nq, total,
+                  [&](int64_t f, int32_t r, bool valid) {
+        uint32_t cand[4] = {0u, 0u, 0u, 0u};
+        uint32_t b = 0xFFFFFFFFu;
+        if (valid) {
+            const int4 raw = __ldg(reinterpret_cast<const int4*>(q) + r);
+            b = (uint32_t)raw.x;
+            const uint32_t u = b / C, c = b % C;
+            const int64_t e = (int64_t)(uint32_t)raw.y + (f - raw.z);
+            const int32_t w = __ldg(a.bk_other + e);
+            const uint32_t a16 = (__ldcg(a.aff + (size_t)u * words + (c >> 1)) >> ((c & 1u) * 16u)) & 0xFFFFu;
+            const uint32_t m16 = __ldg(a.bk_mask + e) & a16;
+            if (m16) {
+                const uint4 pw = ld_cg16(a.M + (size_t)w * J + c * 16);
+                const uint32_t pv[4] = {pw.x, pw.y, pw.z, pw.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    cand[k] = pv[k] & bits_to_bytes((m16 >> (4 * k)) & 0xFu) & ~visited_bytes(pv[k]);
+            }
+        }
+        // segmented max over runs of lanes with the same bucket
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            const uint32_t bo = __shfl_down_sync(0xFFFFFFFFu, b, s);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t x = __shfl_down_sync(0xFFFFFFFFu, cand[k], s);
+                if (lane + s < 32 && bo == b) cand[k] = byte_max(cand[k], x);
+            }
+        }
+        const uint32_t bp = __shfl_up_sync(0xFFFFFFFFu, b, 1);
+        if (!valid || (lane > 0 && bp == b)) return;
+        if (!(cand[0] | cand[1] | cand[2] | cand[3])) return;
+        uint8_t* urow = a.M + (size_t)(b / C) * J + (b % C) * 16;
+        merge_chunk(urow, cand, ld_cg16(urow), n_cas, a.err);
+    });
+}
+
+// Level 0 of the propagation after the pull: the listed vertices, their
+// affected bits as the change mask (bucket entries in bucket mode).
+template <int KIND>
+__global__ void __launch_bounds__(kFBlock) k_push_init_list(GraphDev g, LevelArgs a, const int32_t* __restrict__ list,
+                                                            const unsigned int* __restrict__ list_count, int buckets) {
+    const int64_t cnt = (int64_t)__ldcg(list_count);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < cnt; i0 += stride) {
+        const int64_t i = i0 + threadIdx.x;
+        const int32_t v = i < cnt ? __ldcg(list + i) : 0;
+        if (buckets) {
+            bucket_level0(a, i < cnt, v, a.aff, a.chg_next, a.ql_out, a.cl_out, a.ch_out);
+            continue;
+        }
+        bool want = false, heavy = false;
+        int32_t rp = 0, deg = 0;
+        uint32_t aux = 0u;
+        if (i < cnt) vertex_level0<KIND>(g, a, v, a.aff, want, rp, deg, aux, heavy, true);
+        append(want && !heavy, v, rp, deg, aux, a.ql_out, a.cl_out, g.n, a.err);
+        append(want && heavy, v, rp, deg, aux, a.qh_out, a.ch_out, g.n, a.err);
+    }
+}
+
+cudaError_t launch_incremental(int step, int kind, const GraphDev& g, const LevelArgs& a, const IncrArgs& x,
+                               cudaStream_t st) {
+    const int grid = 152 * 8;
+    switch (step) {
+        case 0:
+            switch (kind) {
+                case kUniform: k_affect_init<kUniform><<<grid, kFBlock, 0, st>>>(g, a, x.nv, x.buckets); break;
+                case kWC: k_affect_init<kWC><<<grid, kFBlock, 0, st>>>(g, a, x.nv, x.buckets); break;
+                case kTrivalency: k_affect_init<kTrivalency><<<grid, kFBlock, 0, st>>>(g, a, x.nv, x.buckets); break;
+                default: k_affect_init<kExplicit><<<grid, kFBlock, 0, st>>>(g, a, x.nv, x.buckets); break;
+            }
+            break;
+        case 1:
+            k_reset_affected<<<grid, kFBlock, 0, st>>>(a.M, g.n, a.J, a.words, x.salt, x.hkey, a.aff, g.rp_out,
+                                                       x.list, x.ldeg, x.lmask, x.list_count, a, x.pq, x.pctr);
+            break;
+        case 2: {
+            if (x.count == 0) break;
+            const int pg = grid;
+            if (x.pull_buckets) {
+                k_pull_buckets<<<pg, kFBlock, 0, st>>>(a, x.pq, x.pctr);
+                break;
+            }
+            switch (kind) {
+                case kUniform: k_pull_affected<kUniform><<<pg, kFBlock, 0, st>>>(g, a, x.list, x.loff, x.lmask, x.count); break;
+                case kWC: k_pull_affected<kWC><<<pg, kFBlock, 0, st>>>(g, a, x.list, x.loff, x.lmask, x.count); break;
+                case kTrivalency: k_pull_affected<kTrivalency><<<pg, kFBlock, 0, st>>>(g, a, x.list, x.loff, x.lmask, x.count); break;
+                default: k_pull_affected<kExplicit><<<pg, kFBlock, 0, st>>>(g, a, x.list, x.loff, x.lmask, x.count); break;
+            }
+            break;
+        }
+        default:
+            switch (kind) {
+                case kUniform: k_push_init_list<kUniform><<<grid, kFBlock, 0, st>>>(g, a, x.list, x.list_count, x.buckets); break;
+                case kWC: k_push_init_list<kWC><<<grid, kFBlock, 0, st>>>(g, a, x.list, x.list_count, x.buckets); break;
+                case kTrivalency: k_push_init_list<kTrivalency><<<grid, kFBlock, 0, st>>>(g, a, x.list, x.list_count, x.buckets); break;
+                default: k_push_init_list<kExplicit><<<grid, kFBlock, 0, st>>>(g, a, x.list, x.list_count, x.buckets); break;
+            }
+            break;
     }
     return cudaGetLastError();
 }

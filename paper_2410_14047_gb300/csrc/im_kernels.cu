@@ -240,7 +240,7 @@ __device__ void cover_seed_buckets(int32_t s, uint32_t* chg_row, int C, const ui
 // Marks row s visited and queues s as level 0 of a cover (one block).
 __device__ void cover_seed_block(uint8_t* M, int J, int32_t s, const int32_t* rp_out, QEntry* q,
                                  unsigned long long* ctr, uint32_t* chg0, unsigned long long* count,
-                                 const uint32_t* bk_end = nullptr, int C = 0) {
+                                 const uint32_t* bk_end = nullptr, int C = 0, uint32_t* nv = nullptr) {
     __shared__ unsigned int newly_sh;
     if (threadIdx.x == 0) newly_sh = 0;
     __syncthreads();
@@ -253,7 +253,11 @@ __device__ void cover_seed_block(uint8_t* M, int J, int32_t s, const int32_t* rp
         if (fresh) { row[j] = (uint8_t)kVisited; ++newly; }
         // change mask of the seed at cover level 0: its newly visited simulations
         const unsigned bits = __ballot_sync(0xFFFFFFFFu, fresh);
-        if ((j & 31) == 0) chg0[(size_t)s * words + (j >> 5)] = bits;
+        if ((j & 31) == 0) {
+            chg0[(size_t)s * words + (j >> 5)] = bits;
+            // registers newly visited since the last build (incremental rebuilds)
+            if (nv && bits) atomicOr(nv + (size_t)s * words + (j >> 5), bits);
+        }
     }
     newly = (unsigned)warp_sum(newly);
     if (lane_id() == 0 && newly) atomicAdd(&newly_sh, newly);
@@ -357,7 +361,7 @@ __device__ void pick_finish(const PickArgs& a, Top2 t) {
     }
     __syncthreads();
     if (fS == ~0ull || !a.mark) return;
-    cover_seed_block(a.M, a.J, fU, a.rp_out, a.q_cover, a.ctr_cover, a.chg0, a.count, a.bk_end_out, a.chunks);
+    cover_seed_block(a.M, a.J, fU, a.rp_out, a.q_cover, a.ctr_cover, a.chg0, a.count, a.bk_end_out, a.chunks, a.nv);
 }
 
 __device__ __forceinline__ bool is_picked(const uint32_t* seed_bits, int64_t v) {

@@ -29,10 +29,13 @@ enum StatIndex : int {
     kStSweepLiveEdges,  // examined in-edges live in a changed chunk (their ids and hashes are read)
     kStSweepBuckets,        // queued buckets walked by propagation levels
     kStSweepBucketEntries,  // bucket list entries processed (source chunk changed)
+    kStAffected,            // registers recomputed by incremental rebuilds
     kStCount
 };
 
-enum FrontierMode : int { kPush = 0, kCover = 1 };
+// kAffect: the affected-set search of an incremental rebuild (in-edges, like
+// propagation; marks bits instead of merging registers).
+enum FrontierMode : int { kPush = 0, kCover = 1, kAffect = 2 };
 
 
 // One frontier level (propagation sweep or cover level).  Queue t of a phase
@@ -101,6 +104,8 @@ struct LevelArgs {
     int32_t bucket_div;                  // output in bucket format when input work * bucket_div < m
     int32_t bq_guard;                    // check the bucket queue's fill before each append (huge graphs)
     int32_t vq_cap;                      // vertex queue capacity (n)
+    uint32_t* aff;                       // incremental rebuild: affected (vertex, simulation) bits
+    uint32_t* nv;                        // covers: registers newly visited since the last build (may be NULL)
 };
 
 // All levels of a phase in one cooperative launch (grid barrier between levels).
@@ -131,6 +136,33 @@ cudaError_t launch_phase(int kind, int mode, const GraphDev& g, const PhaseArgs&
 cudaError_t launch_level(int kind, int mode, const GraphDev& g, const LevelArgs& a, int grid,
                          cudaStream_t st);
 cudaError_t launch_init_queues(int kind, const GraphDev& g, const LevelArgs& a, cudaStream_t st);
+// Incremental rebuild steps: 0 level-0 queue of the affected-set search from
+// the newly visited registers nv; 1 reset of the affected registers and the
+// list of their vertices (out-degree, chunks of affected bits), in bucket mode
+// also the pull queue of their affected chunks' out-buckets; 2 pull over the
+// pull queue, or over the listed vertices' out-edges (loff: exclusive scan of
+// their out-degrees, count + 1 entries, loff[count] the edges of the pull);
+// 3 level-0 queue of the propagation from the list.  buckets: level-0 queues
+// of (vertex, chunk) buckets.
+struct IncrArgs {
+    const uint32_t* nv;
+    const uint32_t* salt;
+    const int32_t* hkey;
+    int32_t* list;
+    int32_t* ldeg;
+    const int32_t* loff;
+    uint2* lmask;
+    unsigned int* list_count;
+    int32_t count;
+    int buckets;
+    // pull queue over the out-bucket lists (bucket mode): entries, packed
+    // counter and overflow word; pull_buckets selects it for step 2
+    QEntry* pq;
+    unsigned long long* pctr;
+    int pull_buckets;
+};
+cudaError_t launch_incremental(int step, int kind, const GraphDev& g, const LevelArgs& a, const IncrArgs& x,
+                               cudaStream_t st);
 
 struct PickArgs {
     uint8_t* M;
@@ -162,6 +194,7 @@ struct PickArgs {
     // (chunks with newly visited simulations and live out-edges)
     const uint32_t* bk_end_out;
     int32_t chunks;
+    uint32_t* nv;                 // registers newly visited since the last build (may be NULL)
 };
 
 int pick_grid(int32_t n, int J);

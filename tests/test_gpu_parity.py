@@ -298,7 +298,9 @@ def test_errors(im, ctx):
                                     {"persistent": 0, "light_batches": 2},
                                     {"dense_div": 0}, {"dense_div": 1000000, "heavy_indeg": 16},
                                     {"lazy_pick": 0}, {"buckets": 0}, {"buckets": 0, "persistent": 0},
-                                    {"buckets": 1024}, {"buckets": 1024, "persistent": 0, "light_batches": 1}])
+                                    {"buckets": 1024}, {"buckets": 1024, "persistent": 0, "light_batches": 1},
+                                    {"incremental": 0}, {"incremental": 2, "buckets": 0, "persistent": 0},
+                                    {"incremental": 1, "buckets": 1024, "persistent": 0}])
 @pytest.mark.parametrize("gname,mname,J", [("rmat12", "wc", 256), ("cl5k", "p01", 64),
                                            ("er2k", "wc", 1024), ("rmat12", "tri", 32)])
 def test_tuning_does_not_change_results(im, ctx, tuning, gname, mname, J):
@@ -338,3 +340,36 @@ def test_lazy_pick_equals_full_pick(im, gname, mname, J, K, eps):
     assert np.array_equal(out[0]["est"], out[1]["est"])
     ref = O.select_seeds(g, O.thresholds(g, model), J, K, 8, eps, "reverse")
     assert out[0]["seeds"].tolist() == ref["seeds"].tolist()
+
+
+# --- incremental rebuilds: the registers a full rebuild produces, bit for bit ---------------
+
+@pytest.mark.parametrize("gname,mname,J,K,eps", [("rmat12", "wc", 256, 40, 0.01), ("er2k", "wc", 64, 60, 0.0),
+                                                 ("cl5k", "p01", 128, 30, 0.0), ("rmat12", "tri", 64, 30, 0.0),
+                                                 ("er2k", "p30", 32, 25, 0.0)])
+@pytest.mark.parametrize("buckets", [0, 2])
+def test_incremental_rebuild_equals_full_rebuild(im, gname, mname, J, K, eps, buckets):
+    g = GRAPHS[gname]
+    model = MODELS[mname]
+    out = []
+    # over edge scans (buckets 0) only incremental = 2 rebuilds incrementally
+    for incr in (2 if buckets == 0 else 1, 0):
+        c2 = im.im_ctx_create(0)
+        im.im_ctx_set_tuning(c2, {"incremental": incr, "buckets": buckets})
+        G = im.im_graph_load(c2, g.rowptr, g.col, model)
+        r = im.im_select_seeds(G, K, J, seed=21, rebuild_eps=eps, return_sketch=True)
+        r["M"] = r["sketch"].registers()
+        r["builds"] = im.im_last_stats(c2)["builds"]
+        r["affected"] = im.im_last_stats(c2)["affected"]
+        out.append(r)
+    assert out[0]["builds"] == out[1]["builds"] and out[0]["builds"] > 1  # rebuilds happened
+    assert out[1]["affected"] == 0
+    if mname in ("wc", "p01"):  # small cascades: covers leave affected registers
+        assert out[0]["affected"] > 0
+    assert out[0]["seeds"].tolist() == out[1]["seeds"].tolist()
+    assert np.array_equal(out[0]["score"], out[1]["score"])
+    assert np.array_equal(out[0]["est"], out[1]["est"])
+    assert np.array_equal(out[0]["M"], out[1]["M"])
+    ref = O.select_seeds(g, O.thresholds(g, model), J, K, 21, eps, "reverse")
+    assert out[0]["seeds"].tolist() == ref["seeds"].tolist()
+    assert np.array_equal(out[0]["M"], ref["M"])
