@@ -970,8 +970,29 @@ __device__ __forceinline__ void clear_unit(const LevelArgs& a, const ClearPlan& 
     }
 }
 
-// Work of one level: heavy vertices first, then slices of light batches, all
-// claimed from the level's counter.
+// Units of a level: each warp first takes a fixed unit, spread over the
+// blocks (the k-th warps of all blocks before any (k+1)-th warp, so a small
+// level runs on many SMs), then, when the level has more units than warps,
+// claims further ones from the level's counter.  A warp without a unit makes
+// no atomic: a small level costs no contended claims.
+struct UnitCursor {
+    int64_t unit, total, nwarps;
+    __device__ __forceinline__ UnitCursor(int64_t total_units) {
+        nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        unit = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+        total = total_units;
+    }
+    __device__ __forceinline__ bool valid() const { return unit < total; }
+    __device__ __forceinline__ void next(unsigned int* claim) {
+        if (total <= nwarps) { unit = total; return; }
+        unsigned int c = 0;
+        if (lane_id() == 0) c = atomicAdd(claim, 1u);
+        unit = nwarps + (int64_t)__shfl_sync(0xFFFFFFFFu, c, 0);
+    }
+};
+
+// Work of one level: heavy vertices first, then slices of light batches, taken through
+// a UnitCursor.
 template <int KIND, int MODE>
 __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a, const uint32_t* sX,
                                            const uint16_t* sTab, int64_t warp, LevelStats& ls,
@@ -1005,16 +1026,13 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
             if (MODE == kCover) atomicAdd(a.stats + kStCoverEdges, (unsigned long long)E);
             atomicAdd(a.stats + (MODE == kPush ? kStSweepLevels : kStCoverLevels), 1ull);
         }
-        for (;;) {
-            unsigned int unit = 0;
-            if (lane == 0) unit = atomicAdd(a.claim, 1u);
-            unit = __shfl_sync(0xFFFFFFFFu, unit, 0);
-            if ((int64_t)unit >= units + cp.units) break;
-            if ((int64_t)unit >= units) {
-                clear_unit(a, cp, (int64_t)unit - units);
+        for (UnitCursor uc(units + cp.units); uc.valid(); uc.next(a.claim)) {
+            const int64_t unit = uc.unit;
+            if (unit >= units) {
+                clear_unit(a, cp, unit - units);
                 continue;
             }
-            const int64_t b0 = (int64_t)unit * lb;
+            const int64_t b0 = unit * lb;
             const int64_t b1 = min(nbl, b0 + lb);
             bucket_slice<KIND, MODE>(g, a, a.ql_in, b0, b1, nq, E, dense, ls.chunks, ls.cas, ls.fresh,
                                      ls.batches, ls.bentries, out_b);
@@ -1060,14 +1078,11 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
         atomicAdd(a.stats + (MODE == kPush ? kStSweepLevels : kStCoverLevels), 1ull);
         if (MODE == kPush) atomicAdd(a.stats + kStSweepHeavy, (unsigned long long)nhv);
     }
-    for (;;) {
-        unsigned int unit = 0;
-        if (lane == 0) unit = atomicAdd(a.claim, 1u);
-        unit = __shfl_sync(0xFFFFFFFFu, unit, 0);
-        if ((int64_t)unit >= total + cp.units) break;
-        if ((int64_t)unit >= total) {
-            clear_unit(a, cp, (int64_t)unit - total);
-        } else if ((int64_t)unit < nhv) {
+    for (UnitCursor uc(total + cp.units); uc.valid(); uc.next(a.claim)) {
+        const int64_t unit = uc.unit;
+        if (unit >= total) {
+            clear_unit(a, cp, unit - total);
+        } else if (unit < nhv) {
             if constexpr (MODE == kPush && (KIND == kWC || KIND == kUniform)) {
                 const int4 raw = __ldcg(reinterpret_cast<const int4*>(a.qh_in) + unit);
                 QEntry ent;
@@ -1747,16 +1762,16 @@ cudaError_t launch_init_queues(int kind, const GraphDev& g, const LevelArgs& a, 
 // propagation then runs from the affected registers only.
 // ---------------------------------------------------------------------------
 
-// Level-0 bucket entries (block-collective; lanes with valid false add
+// Level-0 bucket entries (warp-collective; lanes with valid false add
 // none): for each chunk c of vertex v whose 16 bits in `bits` are nonzero and
 // whose bucket (of a's orientation) is nonempty, the bucket goes to the queue
 // (q, ctr, overflow word) and, with chg, the bits to that change mask.  The
-// block reserves its entries with one global atomic (warps first reserve
-// theirs in shared memory), so queue order and edge offsets agree.
+// warp's (vertex, chunk) items are dealt one per lane (their bucket bounds
+// load in parallel); one reservation per warp keeps queue order and edge
+// offsets in step.
 __device__ __forceinline__ void bucket_level0(const LevelArgs& a, bool valid, int32_t v,
                                               const uint32_t* __restrict__ bits, uint32_t* chg, QEntry* q,
                                               unsigned long long* ctr, unsigned long long* overflow) {
-    __shared__ unsigned long long s_ctr, s_base;
     const int lane = (int)lane_id();
     uint32_t cm_lo = 0u, cm_hi = 0u;
     if (valid)
@@ -1765,78 +1780,85 @@ __device__ __forceinline__ void bucket_level0(const LevelArgs& a, bool valid, in
             if (w < 16) cm_lo |= hb << (2 * w);
             else cm_hi |= hb << (2 * (w - 16));
         }
-    const uint32_t ul = __reduce_or_sync(0xFFFFFFFFu, cm_lo), uh = __reduce_or_sync(0xFFFFFFFFu, cm_hi);
-    // the buckets this lane queues (chunk bits) and their entries
-    uint32_t q_lo = 0u, q_hi = 0u, my_len = 0u;
-    {
-        uint32_t wl = ul, wh = uh;
-        while (wl | wh) {
-            int c;
-            if (wl) { c = __ffs(wl) - 1; wl &= wl - 1; }
-            else { c = 32 + __ffs(wh) - 1; wh &= wh - 1; }
-            if (!(((c < 32 ? cm_lo >> c : cm_hi >> (c - 32)) & 1u))) continue;
-            const int64_t b = (int64_t)v * a.chunks + c;
-            const uint32_t st = bucket_start(a.bk_end, b), en = __ldcg(a.bk_end + b);
-            if (en <= st) continue;
-            if (c < 32) q_lo |= 1u << c; else q_hi |= 1u << (c - 32);
-            my_len += en - st;
-        }
-    }
-    const uint32_t my_cnt = (uint32_t)(__popc(q_lo) + __popc(q_hi));
-    const uint32_t w_cnt = __reduce_add_sync(0xFFFFFFFFu, my_cnt);
-    const uint32_t w_len = __reduce_add_sync(0xFFFFFFFFu, my_len);
-    if (threadIdx.x == 0) s_ctr = 0ull;
-    __syncthreads();
-    unsigned long long wbase = 0ull;
-    if (lane == 0 && w_cnt)
-        wbase = atomicAdd(&s_ctr, ((unsigned long long)w_cnt << kCountShift) | (unsigned long long)w_len);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned long long tot = s_ctr;
-        unsigned long long base = ~0ull;
-        if (tot) {
-            if (a.bq_guard && (int32_t)(__ldcg(ctr) >> kCountShift) >= a.bq_cap) atomicOr(overflow, 1ull);
-            else base = atomicAdd(ctr, tot);
-        }
-        s_base = base;
-    }
-    __syncthreads();
-    const unsigned long long gb = s_base;
-    if (w_cnt == 0) return;
-    // a block refused by a full queue still sets its change bits (the level
-    // then walks every bucket)
-    const bool queued = gb != ~0ull;
-    // this warp's range, then each lane's entries in lane order
-    wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
-    uint32_t ex_cnt = my_cnt, ex_len = my_len;
+    const int nch = __popc(cm_lo) + __popc(cm_hi);
+    int incl = nch;
 #pragma unroll
     for (int s = 1; s < 32; s <<= 1) {
-        const uint32_t yc = __shfl_up_sync(0xFFFFFFFFu, ex_cnt, s), yl = __shfl_up_sync(0xFFFFFFFFu, ex_len, s);
-        if (lane >= s) { ex_cnt += yc; ex_len += yl; }
+        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, s);
+        if (lane >= s) incl += y;
     }
-    ex_cnt -= my_cnt;
-    ex_len -= my_len;
-    int32_t slot = (int32_t)((gb >> kCountShift) + (wbase >> kCountShift)) + (int32_t)ex_cnt;
-    uint32_t off = (uint32_t)((gb & kEdgeMask) + (wbase & kEdgeMask)) + ex_len;
+    const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    if (total == 0) return;
+    const int excl = incl - nch;
+    // the item of lane `lane` in the round starting at `base`: its bucket and bounds
+    auto item = [&](int base, int64_t& b, uint32_t& st, uint32_t& en) -> bool {
+        const int k = base + lane;
+        int i = 0;
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) {
+            const int ic = __shfl_sync(0xFFFFFFFFu, incl, i + s - 1);
+            if (ic <= k) i += s;
+        }
+        if (i > 31) i = 31;
+        const int ex_i = __shfl_sync(0xFFFFFFFFu, excl, i);
+        const uint32_t lo_i = __shfl_sync(0xFFFFFFFFu, cm_lo, i), hi_i = __shfl_sync(0xFFFFFFFFu, cm_hi, i);
+        const int32_t v_i = __shfl_sync(0xFFFFFFFFu, v, i);
+        if (k >= total) return false;
+        const int c = nth_chunk(lo_i, hi_i, k - ex_i);
+        b = (int64_t)v_i * a.chunks + c;
+        st = bucket_start(a.bk_end, b);
+        en = __ldcg(a.bk_end + b);
+        return en > st;
+    };
+    // pass 1: the warp's nonempty buckets and their entries
+    uint32_t w_cnt = 0u, w_len = 0u;
+    for (int base = 0; base < total; base += 32) {
+        int64_t b = 0;
+        uint32_t st = 0u, en = 0u;
+        const bool ne = item(base, b, st, en);
+        w_cnt += (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, ne));
+        w_len += __reduce_add_sync(0xFFFFFFFFu, ne ? en - st : 0u);
+    }
+    unsigned long long gb = ~0ull;
+    if (lane == 0 && w_cnt) {
+        if (a.bq_guard && (int32_t)(__ldcg(ctr) >> kCountShift) >= a.bq_cap) atomicOr(overflow, 1ull);
+        else gb = atomicAdd(ctr, ((unsigned long long)w_cnt << kCountShift) | (unsigned long long)w_len);
+    }
+    gb = __shfl_sync(0xFFFFFFFFu, gb, 0);
+    // pass 2: the entries (a warp refused by a full queue still sets its
+    // change bits: the level then walks every bucket)
+    int32_t slot = gb == ~0ull ? 0 : (int32_t)(gb >> kCountShift);
+    uint32_t off = gb == ~0ull ? 0u : (uint32_t)(gb & kEdgeMask);
     const uint16_t* b16 = reinterpret_cast<const uint16_t*>(bits);
     uint16_t* h16 = reinterpret_cast<uint16_t*>(chg);
-    while (q_lo | q_hi) {
-        int c;
-        if (q_lo) { c = __ffs(q_lo) - 1; q_lo &= q_lo - 1; }
-        else { c = 32 + __ffs(q_hi) - 1; q_hi &= q_hi - 1; }
-        const int64_t b = (int64_t)v * a.chunks + c;
-        const uint32_t st = bucket_start(a.bk_end, b), en = __ldcg(a.bk_end + b);
-        if (h16) h16[(size_t)v * a.words * 2 + c] = __ldcg(b16 + (size_t)v * a.words * 2 + c);
-        if (!queued) continue;
-        if (slot < a.bq_cap) {
-            QEntry e;
-            e.v = (int32_t)b; e.rp = (int32_t)st; e.off = (int32_t)off; e.aux = en - st;
-            q[slot] = e;
-        } else {
-            atomicOr(overflow, 1ull);
+    for (int base = 0; base < total; base += 32) {
+        int64_t b = 0;
+        uint32_t st = 0u, en = 0u;
+        const bool ne = item(base, b, st, en);
+        const uint32_t len = ne ? en - st : 0u;
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, ne);
+        uint32_t lincl = len;
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, lincl, s);
+            if (lane >= s) lincl += y;
         }
-        ++slot;
-        off += en - st;
+        if (ne) {
+            const uint32_t u = (uint32_t)(b / a.chunks), c = (uint32_t)(b % a.chunks);
+            if (h16) h16[(size_t)u * a.words * 2 + c] = __ldcg(b16 + (size_t)u * a.words * 2 + c);
+            const int32_t my = slot + __popc(m & ((1u << lane) - 1u));
+            if (gb != ~0ull) {
+                if (my < a.bq_cap) {
+                    QEntry e;
+                    e.v = (int32_t)b; e.rp = (int32_t)st; e.off = (int32_t)(off + lincl - len); e.aux = len;
+                    q[my] = e;
+                } else {
+                    atomicOr(overflow, 1ull);
+                }
+            }
+        }
+        slot += __popc(m);
+        off += __shfl_sync(0xFFFFFFFFu, lincl, 31);
     }
 }
 
@@ -2012,6 +2034,7 @@ __global__ void __launch_bounds__(kFBlock) k_pull_buckets(LevelArgs a, const QEn
                     cand[k] = pv[k] & bits_to_bytes((m16 >> (4 * k)) & 0xFu) & ~visited_bytes(pv[k]);
             }
         }
+        if (!__any_sync(0xFFFFFFFFu, (cand[0] | cand[1] | cand[2] | cand[3]) != 0u)) return;
         // segmented max over runs of lanes with the same bucket
 #pragma unroll
         for (int s = 1; s < 32; s <<= 1) {

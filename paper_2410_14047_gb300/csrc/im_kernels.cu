@@ -368,25 +368,52 @@ __device__ __forceinline__ bool is_picked(const uint32_t* seed_bits, int64_t v) 
     return (__ldcg(seed_bits + (v >> 5)) >> (v & 31)) & 1u;
 }
 
-// Full pick: S_u of every row (stored in lb when lazy picks follow).
+// Full pick: S_u of every row (stored in lb when lazy picks follow).  Each
+// lane sums up to 4 consecutive 16-byte pieces of a row (LPR lanes a row,
+// 32 / LPR rows a warp step) and a warp issues the loads of kPickSteps steps
+// before summing any, so every warp keeps several KB of the stream in flight.
+constexpr int kPickSteps = 2;
+constexpr int kLazySteps = 4;
+__device__ __forceinline__ void pick_layout(int J, int& cpl, int& lpr, int& rpw) {
+    const int cpr = J >> 4;
+    cpl = cpr < 4 ? cpr : 4;
+    lpr = cpr / cpl;
+    rpw = 32 / lpr;
+}
+
 __global__ void __launch_bounds__(kBlock) k_pick(PickArgs a) {
     const int J = a.J;
-    const int cpr = J >> 4;
-    const int lpr = cpr < 32 ? cpr : 32;
-    const int cpl = cpr / lpr;
-    const int rpw = 32 / lpr;
+    int cpl, lpr, rpw;
+    pick_layout(J, cpl, lpr, rpw);
     const int lane = (int)lane_id();
     const int seg = lane / lpr, seg_lane = lane % lpr;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t step_rows = (int64_t)rpw * kPickSteps;
     Top2 t;
-    for (int64_t r0 = warp * rpw; r0 < a.n; r0 += nwarps * rpw) {
-        const int64_t row = r0 + seg;
-        const bool ok = row < a.n;
-        const unsigned long long s = row_sum(a.M, J, ok ? (int32_t)row : 0, lpr, cpl, seg_lane);
-        if (ok && seg_lane == 0) {
-            if (a.lb) a.lb[row] = s;
-            if (!is_picked(a.seed_bits, row)) t.insert(s, (int32_t)row);
+    for (int64_t r0 = warp * step_rows; r0 < a.n; r0 += nwarps * step_rows) {
+        uint4 q[kPickSteps][4];
+#pragma unroll
+        for (int u = 0; u < kPickSteps; ++u) {
+            const int64_t row = r0 + (int64_t)u * rpw + seg;
+            const uint4* p = reinterpret_cast<const uint4*>(a.M + (size_t)(row < a.n ? row : 0) * J) +
+                             seg_lane * cpl;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                q[u][c] = (c < cpl && row < a.n) ? __ldcs(p + c) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < kPickSteps; ++u) {
+            const int64_t row = r0 + (int64_t)u * rpw + seg;
+            unsigned long long sum = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (c < cpl) sum += row_terms16(q[u][c]);
+            for (int off = lpr >> 1; off >= 1; off >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, off);
+            if (row < a.n && seg_lane == 0) {
+                if (a.lb) a.lb[row] = sum;
+                if (!is_picked(a.seed_bits, row)) t.insert(sum, (int32_t)row);
+            }
         }
     }
     pick_finish(a, t);
@@ -419,32 +446,44 @@ __global__ void __launch_bounds__(kBlock) k_pick_lazy(PickArgs a) {
     }
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr int U = kLazySteps;
     Top2 t;
-    for (int64_t base = warp * 32; base < a.n; base += nwarps * 32) {
-        const int64_t v = base + lane;
-        const bool ok = v < a.n && !is_picked(a.seed_bits, v);
-        unsigned long long lv = ok ? __ldcg(a.lb + v) : ~0ull;
-        const bool stale = ok && (lv < Sc || (lv == Sc && (int32_t)v < uc));
-        unsigned int m = __ballot_sync(0xFFFFFFFFu, stale);
-        while (m) {
-            const int b = __ffs(m) - 1;
-            m &= m - 1;
-            const unsigned long long s = warp_row_sum(a.M, J, (int32_t)(base + b));
-            if (lane == b) {
-                lv = s;
-                a.lb[v] = s;
-            }
+    // U * 32 vertices a warp step: the stored sums and picked words load first
+    for (int64_t base = warp * 32 * U; base < a.n; base += nwarps * 32 * U) {
+        unsigned long long lv[U];
+        uint32_t pw[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t v = base + u * 32 + lane;
+            lv[u] = v < a.n ? __ldcg(a.lb + v) : ~0ull;
+            pw[u] = base + u * 32 < a.n ? __ldcg(a.seed_bits + ((base + u * 32) >> 5)) : 0xFFFFFFFFu;
         }
-        if (ok) t.insert(lv, (int32_t)v);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t v = base + u * 32 + lane;
+            const bool ok = v < a.n && !((pw[u] >> lane) & 1u);
+            const bool stale = ok && (lv[u] < Sc || (lv[u] == Sc && (int32_t)v < uc));
+            unsigned int m = __ballot_sync(0xFFFFFFFFu, stale);
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                const unsigned long long s = warp_row_sum(a.M, J, (int32_t)(base + u * 32 + b));
+                if (lane == b) {
+                    lv[u] = s;
+                    a.lb[v] = s;
+                }
+            }
+            if (ok) t.insert(lv[u], (int32_t)v);
+        }
     }
     pick_finish(a, t);
 }
 
 int pick_grid(int32_t n, int J) {
     const int cpr = J / 16;
-    const int lpr = cpr < 32 ? cpr : 32;
-    const int rpw = 32 / lpr;
-    const int64_t rows_per_block = (int64_t)rpw * kWarpsPerBlock;
+    const int cpl = cpr < 4 ? cpr : 4;
+    const int rpw = 32 / (cpr / cpl);
+    const int64_t rows_per_block = (int64_t)rpw * kPickSteps * kWarpsPerBlock;
     int64_t grid = (n + rows_per_block - 1) / rows_per_block;
     if (grid > 152 * 8) grid = 152 * 8;
     if (grid < 1) grid = 1;
@@ -457,7 +496,7 @@ cudaError_t launch_pick(const PickArgs& a, cudaStream_t st) {
 }
 
 int pick_lazy_grid(int32_t n) {
-    const int64_t per_block = (int64_t)kWarpsPerBlock * 32 * 4;
+    const int64_t per_block = (int64_t)kWarpsPerBlock * 32 * kLazySteps;
     int64_t grid = (n + per_block - 1) / per_block;
     if (grid > 152 * 8) grid = 152 * 8;
     if (grid < 1) grid = 1;
