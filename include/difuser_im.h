@@ -145,7 +145,11 @@ typedef struct {
  * with live chunk masks throughout; incremental: 1 = im_select_seeds rebuilds
  * only the registers a rebuild can change (those of vertices that reach a
  * register visited since the last build) when the sketch has the bucketed
- * lists, 2 = also over edge scans, 0 = full rebuilds. */
+ * lists, 2 = also over edge scans, 0 = full rebuilds; chain: on a bucket
+ * level of a propagation or affected-set search with at most one batch per
+ * warp, a warp that raises a small bucket (<= 32 entries) queues it, then
+ * also processes it at once, up to `chain` such continuations per warp and
+ * level (0 = off): chains of small buckets advance several hops a level. */
 typedef struct {
     int32_t heavy_indeg;
     int32_t light_batches;
@@ -156,6 +160,7 @@ typedef struct {
     int32_t lazy_pick;
     int32_t buckets;
     int32_t incremental;
+    int32_t chain;
 } im_tuning;
 
 /* One frontier launch of the last selection / build (tracing on). */
@@ -188,7 +193,7 @@ IM_API im_status im_last_stats(const im_ctx* ctx, im_stats* out);
  * stream and report per-kind kernel time in im_stats (adds two event records
  * per launch).  Off by default. */
 IM_API im_status im_ctx_set_timing(im_ctx* ctx, int enable);
-/* Sets (NULL = defaults {256, 4, 0, 2, 1, 0, 1, 2, 1}) or reads the schedule knobs. */
+/* Sets (NULL = defaults {256, 4, 0, 2, 1, 0, 1, 2, 1, 4}) or reads the schedule knobs. */
 IM_API im_status im_ctx_set_tuning(im_ctx* ctx, const im_tuning* tuning);
 IM_API im_status im_ctx_get_tuning(const im_ctx* ctx, im_tuning* tuning);
 /* enable != 0: also keep one im_trace_rec per frontier level (implies timing):

@@ -44,7 +44,7 @@ struct im_ctx {
     bool trace = false;
     std::vector<float> launch_ms;    // kernel time per launch sequence number (tracing)
     std::vector<im_trace_rec> recs;  // frontier launches of the last call
-    im_tuning tuning{256, 4, 0, 2, 1, 0, 1, 2, 1};
+    im_tuning tuning{256, 4, 0, 2, 1, 0, 1, 2, 1, 4};
 };
 
 namespace {
@@ -310,12 +310,13 @@ extern "C" im_status im_ctx_set_timing(im_ctx* c, int enable) {
 extern "C" im_status im_ctx_set_tuning(im_ctx* c, const im_tuning* t) {
     if (!c) return IM_E_INVAL;
     if (!t) {
-        c->tuning = im_tuning{256, 4, 0, 2, 1, 0, 1, 2, 1};
+        c->tuning = im_tuning{256, 4, 0, 2, 1, 0, 1, 2, 1, 4};
         return IM_OK;
     }
     if (t->heavy_indeg < 0 || t->light_batches < 1 || t->light_batches > 4096 || t->grid_blocks < 0 ||
         t->check_every < 1 || t->check_every > 64 || t->persistent < 0 || t->persistent > 1 ||
-        t->dense_div < 0 || t->lazy_pick < 0 || t->lazy_pick > 1 || t->buckets < 0 || t->buckets > 1024 || t->incremental < 0 || t->incremental > 2)
+        t->dense_div < 0 || t->lazy_pick < 0 || t->lazy_pick > 1 || t->buckets < 0 || t->buckets > 1024 || t->incremental < 0 || t->incremental > 2 ||
+        t->chain < 0 || t->chain > 64)
         return fail(c, IM_E_INVAL, "tuning out of range");
     c->tuning = *t;
     return IM_OK;
@@ -579,7 +580,7 @@ static void sketch_plan(im_sketch* sk, int32_t n, int64_t m_edges, int32_t J, Bu
     A(sk->ticket, 4);
     A(sk->stats, (size_t)kStCount * 8);
     A(sk->err, 4);
-    A(sk->bar, 512);  // barrier words (16 B) + 64 group counters from byte 256
+    A(sk->bar, 256);  // barrier words: arrivals, abort, levels; generation from byte 128
     A(sk->level_ns, (size_t)(kMaxLevels + 2) * 8);
     A(sk->fmt, (size_t)(kMaxLevels + 2));
     // incremental rebuilds: newly visited and affected register bits, the
@@ -754,6 +755,7 @@ static void set_lcm(LevelArgs& a, const im_sketch* sk, int mode) {
     // below 2^26 - 2^22 edges the packed counter's count field cannot overflow
     a.bq_guard = sk->g->m >= (int64_t)((1 << 26) - (1 << 22)) ? 1 : 0;
     a.bucket_div = sk->buckets ? sk->ctx->tuning.buckets : 0;
+    a.chain = sk->ctx->tuning.chain;
     if (sk->buckets) {
         const int o = in ? 0 : 1;
         a.bk_end = sk->bk_end[o].as<uint32_t>();
@@ -819,11 +821,12 @@ static im_status run_phase_persistent(im_sketch* sk, int mode, bool all_first, i
     p.max_levels = kMaxLevels - 2;
     p.gen_base = sk->gen_counter + 1;
     unsigned int* bar = sk->bar.as<unsigned int>();
+    // the generation word (polled by the waiting blocks) on its own 128-byte
+    // line, away from the arrival counter
     p.bar_arrive = bar;
-    p.bar_groups = bar + 64;
-    p.bar_gen = bar + 1;
     p.abort_flag = bar + 2;
     p.levels_out = reinterpret_cast<int*>(bar + 3);
+    p.bar_gen = bar + 32;
     p.limit_ns = 20ull * 1000 * 1000 * 1000;
     p.level_ns = c->trace ? sk->level_ns.as<unsigned long long>() : nullptr;
     p.fmt = sk->fmt.as<uint8_t>();

@@ -721,17 +721,160 @@ __device__ __forceinline__ void bucket_append(bool want, uint32_t b, uint32_t st
     }
 }
 
+// A speculative continuation of a level (the chains of small levels): the
+// bucket (o, c) a lane just raised, processed again at once by the same warp
+// with the raised bits.  The bucket is also queued for the next level as
+// usual, so the continuation only adds propagation of values the registers
+// already hold (max-merges of valid values are safe in any order and number):
+// a chain of small buckets then advances several hops per level.
+struct InlineCand {
+    bool ok = false;
+    uint32_t b = 0u, start = 0u, len = 0u, bits = 0u;
+};
+constexpr int kChainCap = 32;        // continuation stack entries per warp
+constexpr uint32_t kChainMaxLen = 32;  // bucket entries a continuation may take (one batch)
+
+// One position of a bucket walk: bucket bkt (vertex u, chunk c), list entry
+// e, change bits chb of the chunk (valid false: a lane past the walk's end,
+// which still joins the warp-wide enqueue).  ic: the raised target bucket,
+// when its first change this level queued it and it is small enough to
+// continue at once.
+template <int KIND, int MODE>
+__device__ __forceinline__ void bucket_pos(const GraphDev& g, const LevelArgs& a, bool valid, uint32_t bkt,
+                                           int64_t e, uint32_t chb, unsigned long long& st_chunks,
+                                           unsigned long long& st_cas, unsigned long long& st_new,
+                                           unsigned long long& st_dealt, bool out_b, InlineCand& ic) {
+    const int J = a.J;
+    const uint32_t C = (uint32_t)a.chunks;
+    const uint32_t u = bkt / C, c = bkt % C;
+    uint32_t nbits = 0u;
+    int32_t o = 0;
+    // the entry and the source piece are fetched with the change bits
+    uint32_t m16 = 0u;
+    uint4 src = make_uint4(0u, 0u, 0u, 0u);
+    if (valid) {
+        o = __ldg(a.bk_other + e);
+        m16 = __ldg(a.bk_mask + e);
+        src = ld_cg16(a.M + (size_t)u * J + c * 16);
+    }
+    uint32_t imp = 0u;
+    uint4 tg = make_uint4(0u, 0u, 0u, 0u);
+    uint32_t cand[4] = {0u, 0u, 0u, 0u};
+    uint32_t any = 0u;
+    uint8_t* trow = a.M + (size_t)o * J + c * 16;
+    if (valid && chb) {
+        ++st_dealt;
+        m16 &= chb;
+        tg = ld_cg16(trow);
+        const uint32_t sw[4] = {src.x, src.y, src.z, src.w};
+        const uint32_t tw[4] = {tg.x, tg.y, tg.z, tg.w};
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const uint32_t L = bits_to_bytes((m16 >> (4 * w)) & 0xFu);
+            if constexpr (MODE == kPush) cand[w] = sw[w] & L & ~visited_bytes(sw[w]);
+            else if constexpr (MODE == kCover) cand[w] = L & visited_bytes(sw[w]) & ~visited_bytes(tw[w]);
+            else cand[w] = L & ~visited_bytes(tw[w]);
+            any |= cand[w];
+            // registers this item raises, as the loaded target piece shows
+            if constexpr (MODE == kPush) imp |= bytes_to_bits(byte_max(tw[w], cand[w]) ^ tw[w]) << (4 * w);
+            else if constexpr (MODE == kCover) imp |= bytes_to_bits(cand[w]) << (4 * w);
+        }
+        if constexpr (MODE == kAffect) imp = mark_affected(a, cand, o, c, st_new);
+    }
+    // the enqueue's loads and atomics go out before the register update
+    const EnqueueState eq = out_b ? bucket_enqueue_issue(a, o, c, imp)
+                                  : vertex_enqueue_issue<KIND, MODE>(g, a, o, c, imp);
+    if (MODE != kAffect) {
+        if (any) {
+            ++st_chunks;
+            if constexpr (MODE == kPush) {
+                nbits = merge_chunk(trow, cand, tg, st_cas, a.err);
+            } else {
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    if (cand[w] == 0u) continue;
+                    const uint32_t prev = atomicOr(reinterpret_cast<unsigned int*>(trow + 4 * w), cand[w]);
+                    const uint32_t really = cand[w] & ~visited_bytes(prev);
+                    if (really) {
+                        nbits |= bytes_to_bits(really) << (4 * w);
+                        st_new += (unsigned)(__popc(really) >> 3);
+                        if (a.gcount)
+                            atomicAdd(a.gcount + __ldg(a.gid + o), (unsigned long long)(__popc(really) >> 3));
+                    }
+                }
+                note_newly_visited(a, o, c, nbits);
+            }
+        }
+    }
+    (void)nbits;
+    // enqueue what changed: the target's bucket of this chunk, or the
+    // target vertex
+    if (out_b) {
+        bucket_enqueue_finish(a, imp != 0u, o, c, eq);
+        const uint32_t sh = (c & 1u) * 16u;
+        if (imp != 0u && ((eq.old >> sh) & 0xFFFFu) == 0u && eq.oe > eq.os && eq.oe - eq.os <= kChainMaxLen) {
+            ic.ok = true;
+            ic.b = (uint32_t)o * C + c;
+            ic.start = eq.os;
+            ic.len = eq.oe - eq.os;
+            ic.bits = imp;
+        }
+    } else {
+        vertex_enqueue_finish<KIND, MODE>(g, a, imp != 0u, o, eq);
+    }
+}
+
+// Pushes the warp's continuation candidates (depth d) on its stack; the ones
+// that find it full are left to the next level.
+__device__ __forceinline__ void chain_push(int4* stk, int& sp, const InlineCand& ic, int d) {
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, ic.ok);
+    if (!m) return;
+    const int lane = (int)lane_id();
+    const int pos = sp + __popc(m & ((1u << lane) - 1u));
+    if (ic.ok && pos < kChainCap)
+        stk[pos] = make_int4((int)ic.b, (int)ic.start, (int)ic.len, (int)(ic.bits | ((uint32_t)d << 16)));
+    sp = min(kChainCap, sp + __popc(m));
+    __syncwarp();
+}
+
+// Runs the warp's continuations (last pushed first) while its budget of
+// `chain` continuations this level lasts; a continuation pushes its own
+// raised buckets.  What is left on the stack is dropped (the next level has
+// it queued).
+template <int KIND, int MODE>
+__device__ __forceinline__ void chain_drain(const GraphDev& g, const LevelArgs& a, int4* stk, int& sp, int chain,
+                                            int& used, unsigned long long& st_chunks, unsigned long long& st_cas,
+                                            unsigned long long& st_new, unsigned long long& st_batches,
+                                            unsigned long long& st_dealt, bool out_b) {
+    const int lane = (int)lane_id();
+    for (; sp > 0 && used < chain; ++used) {
+        --sp;
+        const int4 it = stk[sp];
+        __syncwarp();
+        const uint32_t len = (uint32_t)it.z, bits = (uint32_t)it.w & 0xFFFFu;
+        const int d = (int)((uint32_t)it.w >> 16);
+        if (lane == 0) ++st_batches;
+        InlineCand ic;
+        bucket_pos<KIND, MODE>(g, a, (uint32_t)lane < len, (uint32_t)it.x, (int64_t)(uint32_t)it.y + lane, bits,
+                               st_chunks, st_cas, st_new, st_dealt, out_b, ic);
+        chain_push(stk, sp, ic, d + 1);
+    }
+    sp = 0;
+}
+
 // One bucket-mode unit: flat positions [b0*32, b1*32) of the level's walk.
 template <int KIND, int MODE>
 __device__ __forceinline__ void bucket_slice(const GraphDev& g, const LevelArgs& a, const QEntry* __restrict__ qlin,
                                              int64_t b0, int64_t b1, int32_t nq, int64_t E, bool dense,
                                              unsigned long long& st_chunks, unsigned long long& st_cas,
                                              unsigned long long& st_new, unsigned long long& st_batches,
-                                             unsigned long long& st_dealt, bool out_b) {
+                                             unsigned long long& st_dealt, bool out_b, int chain) {
     const int lane = (int)lane_id();
-    const int J = a.J, words = a.words;
+    const int words = a.words;
     const uint32_t C = (uint32_t)a.chunks;
     const int64_t nb = a.nbuckets;
+    __shared__ int4 sChain[kFBlock / 32][kChainCap];
+    int sp = 0, chain_used = 0;
     const uint16_t* chg16 = reinterpret_cast<const uint16_t*>(a.chg_cur);
     const int64_t fend = min(E, b1 << 5);
     int64_t f0 = b0 << 5;
@@ -815,71 +958,13 @@ __device__ __forceinline__ void bucket_slice(const GraphDev& g, const LevelArgs&
             }
         }
         if (lane == 0) ++st_batches;
-        const uint32_t u = bkt / C, c = bkt % C;
-        uint32_t nbits = 0u;
-        int32_t o = 0;
-        // the entry and the source piece are fetched with the change bits
-        uint32_t m16 = 0u;
-        uint4 src = make_uint4(0u, 0u, 0u, 0u);
-        if (f < fend) {
-            o = __ldg(a.bk_other + e);
-            m16 = __ldg(a.bk_mask + e);
-            src = ld_cg16(a.M + (size_t)u * J + c * 16);
+        InlineCand ic;
+        bucket_pos<KIND, MODE>(g, a, f < fend, bkt, e, chb, st_chunks, st_cas, st_new, st_dealt, out_b, ic);
+        if (chain > 0) {
+            chain_push(sChain[threadIdx.x >> 5], sp, ic, 1);
+            chain_drain<KIND, MODE>(g, a, sChain[threadIdx.x >> 5], sp, chain, chain_used, st_chunks, st_cas,
+                                    st_new, st_batches, st_dealt, out_b);
         }
-        uint32_t imp = 0u;
-        uint4 tg = make_uint4(0u, 0u, 0u, 0u);
-        uint32_t cand[4] = {0u, 0u, 0u, 0u};
-        uint32_t any = 0u;
-        uint8_t* trow = a.M + (size_t)o * J + c * 16;
-        if (f < fend && chb) {
-            ++st_dealt;
-            m16 &= chb;
-            tg = ld_cg16(trow);
-            const uint32_t sw[4] = {src.x, src.y, src.z, src.w};
-            const uint32_t tw[4] = {tg.x, tg.y, tg.z, tg.w};
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                const uint32_t L = bits_to_bytes((m16 >> (4 * w)) & 0xFu);
-                if constexpr (MODE == kPush) cand[w] = sw[w] & L & ~visited_bytes(sw[w]);
-                else if constexpr (MODE == kCover) cand[w] = L & visited_bytes(sw[w]) & ~visited_bytes(tw[w]);
-                else cand[w] = L & ~visited_bytes(tw[w]);
-                any |= cand[w];
-                // registers this item raises, as the loaded target piece shows
-                if constexpr (MODE == kPush) imp |= bytes_to_bits(byte_max(tw[w], cand[w]) ^ tw[w]) << (4 * w);
-                else if constexpr (MODE == kCover) imp |= bytes_to_bits(cand[w]) << (4 * w);
-            }
-            if constexpr (MODE == kAffect) imp = mark_affected(a, cand, o, c, st_new);
-        }
-        // the enqueue's loads and atomics go out before the register update
-        const EnqueueState eq = out_b ? bucket_enqueue_issue(a, o, c, imp)
-                                      : vertex_enqueue_issue<KIND, MODE>(g, a, o, c, imp);
-        if (MODE != kAffect) {
-            if (any) {
-                ++st_chunks;
-                if constexpr (MODE == kPush) {
-                    nbits = merge_chunk(trow, cand, tg, st_cas, a.err);
-                } else {
-#pragma unroll
-                    for (int w = 0; w < 4; ++w) {
-                        if (cand[w] == 0u) continue;
-                        const uint32_t prev = atomicOr(reinterpret_cast<unsigned int*>(trow + 4 * w), cand[w]);
-                        const uint32_t really = cand[w] & ~visited_bytes(prev);
-                        if (really) {
-                            nbits |= bytes_to_bits(really) << (4 * w);
-                            st_new += (unsigned)(__popc(really) >> 3);
-                            if (a.gcount)
-                                atomicAdd(a.gcount + __ldg(a.gid + o), (unsigned long long)(__popc(really) >> 3));
-                        }
-                    }
-                    note_newly_visited(a, o, c, nbits);
-                }
-            }
-        }
-        (void)nbits;
-        // enqueue what changed: the target's bucket of this chunk, or the
-        // target vertex
-        if (out_b) bucket_enqueue_finish(a, imp != 0u, o, c, eq);
-        else vertex_enqueue_finish<KIND, MODE>(g, a, imp != 0u, o, eq);
     }
 }
 
@@ -1021,6 +1106,9 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
         const int64_t lb = max((int64_t)1, min((int64_t)a.light_batches, nbl / nwarps));
         const int64_t units = (nbl + lb - 1) / lb;
         if (units + cp.units == 0) return;
+        // continuations on levels of at most one batch a warp (not in covers,
+        // whose small levels fan out rather than chain)
+        const int chain = (MODE != kCover && a.chain > 0 && out_b && !dense && nbl <= nwarps) ? a.chain : 0;
         if (warp == 0 && lane == 0) {
             atomicAdd(a.stats + (MODE == kPush ? kStSweepBuckets : kStCoverVertices), (unsigned long long)nq);
             if (MODE == kCover) atomicAdd(a.stats + kStCoverEdges, (unsigned long long)E);
@@ -1035,7 +1123,7 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
             const int64_t b0 = unit * lb;
             const int64_t b1 = min(nbl, b0 + lb);
             bucket_slice<KIND, MODE>(g, a, a.ql_in, b0, b1, nq, E, dense, ls.chunks, ls.cas, ls.fresh,
-                                     ls.batches, ls.bentries, out_b);
+                                     ls.batches, ls.bentries, out_b, chain);
         }
         return;
     }
@@ -1178,12 +1266,11 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-__device__ bool grid_barrier(unsigned int* groups, unsigned int* arrive, volatile unsigned int* gen,
-                             volatile unsigned int* abort_flag, uint32_t* err, unsigned long long limit_ns,
-                             unsigned int g0) {
-    // two-level arrival (groups of 32 blocks, then the groups) keeps the
-    // atomics on any one word to 32 at most; the waits poll only the
-    // generation word, with the abort word and the clock every 32 polls
+__device__ bool grid_barrier(unsigned int* arrive, volatile unsigned int* gen, volatile unsigned int* abort_flag,
+                             uint32_t* err, unsigned long long limit_ns, unsigned int g0) {
+    // one arrival counter (the last block to arrive resets it and advances
+    // the generation); the waits poll only the generation word, with the
+    // abort word and the clock every 32 polls
     __syncthreads();
     __shared__ bool ok;
     if (threadIdx.x == 0) {
@@ -1191,19 +1278,12 @@ __device__ bool grid_barrier(unsigned int* groups, unsigned int* arrive, volatil
         // g0: the generation word's value before this barrier (it counts the
         // barriers passed, so the caller knows it without a read)
         __threadfence();
-        const unsigned int grp = blockIdx.x >> 5;
-        const unsigned int gsize = min(32u, gridDim.x - grp * 32u);
-        const unsigned int ngroups = (gridDim.x + 31u) >> 5;
         bool last = false;
-        if (atomicAdd(groups + grp, 1u) == gsize - 1u) {
-            groups[grp] = 0u;
+        if (atomicAdd(arrive, 1u) == gridDim.x - 1u) {
+            *arrive = 0u;
             __threadfence();
-            if (atomicAdd(arrive, 1u) == ngroups - 1u) {
-                *arrive = 0u;
-                __threadfence();
-                atomicAdd((unsigned int*)gen, 1u);
-                last = true;
-            }
+            atomicAdd((unsigned int*)gen, 1u);
+            last = true;
         }
         if (!last) {
             const unsigned long long t0 = global_ns();
@@ -1284,7 +1364,7 @@ __global__ void __launch_bounds__(kFBlock, kPhaseMinBlocks) k_phase(GraphDev g, 
         prev_l = pre_l;
         prev_h = pre_h;
         prev_b = pre_b;
-        if (!grid_barrier(p.bar_groups, p.bar_arrive, p.bar_gen, p.abort_flag, a.err, p.limit_ns, (unsigned int)t))
+        if (!grid_barrier(p.bar_arrive, p.bar_gen, p.abort_flag, a.err, p.limit_ns, (unsigned int)t))
             break;
         if (p.level_ns && blockIdx.x == 0 && threadIdx.x == 0) p.level_ns[t + 1] = global_ns();
         pre_l = __ldcg(&p.ctr[t + 1].x);

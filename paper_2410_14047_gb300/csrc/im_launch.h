@@ -106,6 +106,7 @@ struct LevelArgs {
     int32_t vq_cap;                      // vertex queue capacity (n)
     uint32_t* aff;                       // incremental rebuild: affected (vertex, simulation) bits
     uint32_t* nv;                        // covers: registers newly visited since the last build (may be NULL)
+    int32_t chain;                       // continuation depth on small bucket levels (0 = none)
 };
 
 // All levels of a phase in one cooperative launch (grid barrier between levels).
@@ -119,7 +120,6 @@ struct PhaseArgs {
     int all_first;
     int max_levels;
     int32_t gen_base;                    // enqueue stamp of level t = gen_base + t
-    unsigned int* bar_groups;            // per group of 32 blocks: arrivals at the current barrier
     unsigned int* bar_arrive;            // groups arrived
     unsigned int* bar_gen;
     unsigned int* abort_flag;
