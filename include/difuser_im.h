@@ -90,9 +90,11 @@ typedef struct {
     double ms_rebuild;        /* all rebuilds, host wall clock */
     double ms_pick;           /* all pick + cover + score read-back steps, host wall clock */
     double ms_propagate;      /* CUDA-event time of all propagation sweep kernels (timing on) */
-    double ms_cover_kernels;  /* CUDA-event time of all cover level kernels (timing on) */
+    double ms_cover_kernels;  /* CUDA-event time of all cover level kernels and affected-set
+                                 searches of incremental rebuilds (timing on) */
     double ms_pick_kernels;   /* CUDA-event time of all estimate + argmax kernels (timing on) */
-    double ms_fill_kernels;   /* CUDA-event time of all fill kernels (timing on) */
+    double ms_fill_kernels;   /* CUDA-event time of all fill kernels, with the reset and pull of
+                                 incremental rebuilds (timing on) */
     int64_t launches;         /* kernels launched by the call */
     int64_t sweep_launches;   /* propagation sweep kernels launched (with or without work) */
     int64_t builds;           /* 1 + number of rebuilds */
@@ -165,7 +167,8 @@ typedef struct {
 
 /* One frontier launch of the last selection / build (tracing on). */
 typedef struct {
-    int32_t kind;    /* 0 = propagation sweep (Alg. 2), 1 = cover level (Alg. 3) */
+    int32_t kind;    /* 0 = propagation sweep (Alg. 2), 1 = cover level (Alg. 3),
+                        2 = affected-set search level (incremental rebuild) */
     int32_t level;   /* level index within its phase */
     int64_t count;   /* queued vertices the launch processed */
     int64_t edges;   /* edges of those vertices (in-edges for sweeps, out-edges for covers) */

@@ -1033,7 +1033,8 @@ static im_status incremental_rebuild(im_sketch* sk) {
         c->stats.pull_entries += c->pinned[1] & kEdgeMask;
     }
     if (x.count > 0) {
-        CK(c, timed(c, kTPush, [&] {
+        // timed with the reset (both rebuild registers from their own ranks)
+        CK(c, timed(c, kTFill, [&] {
             if (!x.pull_buckets) {
                 cudaError_t e = launch_exclusive_scan(x.ldeg, x.count, sk->aloff.as<int32_t>(), sk->ascan.p, st);
                 if (e != cudaSuccess) return e;

@@ -1542,6 +1542,33 @@ __device__ __forceinline__ void edge_chunk_masks(uint32_t h, uint32_t thr, int J
     }
 }
 
+// Chunks of one edge with at least one live simulation: bits c of lo (c <
+// 32) and hi (c >= 32).  A chunk's scan stops at its first live simulation
+// (sorted X puts an edge's candidates in a few consecutive chunks).
+__device__ __forceinline__ void edge_live_chunks(uint32_t h, uint32_t thr, int J, const uint32_t* sX,
+                                                 const uint16_t* sTab, uint32_t& lo_mask, uint32_t& hi_mask) {
+    lo_mask = 0u;
+    hi_mask = 0u;
+    if (thr >= 0x80000000u) {
+        const int C = J >> 4;
+        lo_mask = C >= 32 ? 0xFFFFFFFFu : ((1u << C) - 1u);
+        hi_mask = C > 32 ? (C >= 64 ? 0xFFFFFFFFu : ((1u << (C - 32)) - 1u)) : 0u;
+        return;
+    }
+    if (thr == 0u) return;
+    int lo, hi;
+    candidate_range(h, thr, J, sX, sTab, lo, hi);
+    for (int c = lo >> 4; hi > lo && c <= ((hi - 1) >> 4); ++c) {
+        const int j1 = min(hi, 16 * c + 16);
+        for (int j = max(lo, 16 * c); j < j1; ++j)
+            if ((sX[j] ^ h) < thr) {
+                if (c < 32) lo_mask |= 1u << c;
+                else hi_mask |= 1u << (c - 32);
+                break;
+            }
+    }
+}
+
 // Edge-balanced walk of a flat space [0, m) split into rows by the
 // non-decreasing starts start(0..nrows) (start(0) = 0, start(nrows) = m), a
 // warp taking kLcmEdgesPerWarp consecutive positions; ALL: every lane calls
@@ -1636,11 +1663,8 @@ __global__ void __launch_bounds__(kFBlock) k_live_chunks(GraphDev g, const uint3
     __shared__ uint16_t sTab[kTabSize];
     load_sims(X, tab, J, sX, sTab);
     for_each_edge<KIND, MODE>(g, [&](int64_t e, int32_t, int32_t, uint32_t h, uint32_t thr) {
-        uint32_t mlo = 0u, mhi = 0u;
-        edge_chunk_masks(h, thr, J, sX, sTab, [&](int c, uint32_t) {
-            if (c < 32) mlo |= 1u << c;
-            else mhi |= 1u << (c - 32);
-        });
+        uint32_t mlo, mhi;
+        edge_live_chunks(h, thr, J, sX, sTab, mlo, mhi);
         lo_out[e] = mlo;
         if (hi_out) hi_out[e] = mhi;
     });
