@@ -868,7 +868,8 @@ __device__ __forceinline__ void bucket_slice(const GraphDev& g, const LevelArgs&
                                              int64_t b0, int64_t b1, int32_t nq, int64_t E, bool dense,
                                              unsigned long long& st_chunks, unsigned long long& st_cas,
                                              unsigned long long& st_new, unsigned long long& st_batches,
-                                             unsigned long long& st_dealt, bool out_b, int chain) {
+                                             unsigned long long& st_dealt, bool out_b, int chain,
+                                             bool all_bits) {
     const int lane = (int)lane_id();
     const int words = a.words;
     const uint32_t C = (uint32_t)a.chunks;
@@ -901,10 +902,11 @@ __device__ __forceinline__ void bucket_slice(const GraphDev& g, const LevelArgs&
                 __reduce_or_sync(0xFFFFFFFFu, (wvalid && rel >= 1 && rel <= 31) ? (1u << rel) : 0u);
             const int myw = c0 - 1 + __popc(starts & ((2u << lane) - 1u));
             // change bits of each window entry's chunk
+            // (all_bits: every simulation of the chunk, skipping the load)
             uint32_t cwl = 0u;
             if (wvalid && rel <= 31 && lane >= c0 - 1) {
                 const uint32_t bw = (uint32_t)raw.x;
-                cwl = chg16[(size_t)(bw / C) * words * 2 + (bw % C)];
+                cwl = all_bits ? 0xFFFFu : chg16[(size_t)(bw / C) * words * 2 + (bw % C)];
             }
             bkt = (uint32_t)__shfl_sync(0xFFFFFFFFu, raw.x, myw);
             const int32_t qrp = __shfl_sync(0xFFFFFFFFu, raw.y, myw);
@@ -1109,6 +1111,12 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
         // continuations on levels of at most one batch a warp (not in covers,
         // whose small levels fan out rather than chain)
         const int chain = (MODE != kCover && a.chain > 0 && out_b && !dense && nbl <= nwarps) ? a.chain : 0;
+        // on such small levels a propagation or cover takes every simulation of
+        // a queued chunk, not only the changed ones (one dependent load less
+        // per hop): a simulation that did not change was pushed along every
+        // live edge when it last did, so its targets already hold at least its
+        // value (a visited one's targets are visited), and it raises nothing
+        const bool all_bits = MODE != kAffect && !dense && nbl <= nwarps && a.gflag == nullptr;
         if (warp == 0 && lane == 0) {
             atomicAdd(a.stats + (MODE == kPush ? kStSweepBuckets : kStCoverVertices), (unsigned long long)nq);
             if (MODE == kCover) atomicAdd(a.stats + kStCoverEdges, (unsigned long long)E);
@@ -1123,7 +1131,7 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
             const int64_t b0 = unit * lb;
             const int64_t b1 = min(nbl, b0 + lb);
             bucket_slice<KIND, MODE>(g, a, a.ql_in, b0, b1, nq, E, dense, ls.chunks, ls.cas, ls.fresh,
-                                     ls.batches, ls.bentries, out_b, chain);
+                                     ls.batches, ls.bentries, out_b, chain, all_bits);
         }
         return;
     }
@@ -1686,7 +1694,7 @@ __global__ void __launch_bounds__(kFBlock) k_buckets(GraphDev g, const uint32_t*
         edge_chunk_masks(h, thr, J, sX, sTab, [&](int c, uint32_t m16) {
             const int64_t b = (int64_t)v * C + c;
             if constexpr (PASS == 0) {
-                if (atomicAdd(cnt_or_end + b, 1u) == 0u) atomicAdd(nonempty, 1ull);
+                atomicAdd(cnt_or_end + b, 1u);
             } else {
                 const uint32_t pos = atomicAdd(cnt_or_end + b, 1u);
                 other_out[pos] = other;
@@ -1799,16 +1807,48 @@ static int edge_walk_grid(const GraphDev& g) {
     return (int)max((int64_t)1, min(want, (int64_t)level_grid()));
 }
 
+// Nonzero entries of cnt[0..n) added to *out (one atomic per block).
+__global__ void __launch_bounds__(kFBlock) k_count_nonzero(const uint32_t* __restrict__ cnt, int64_t n,
+                                                           unsigned long long* out) {
+    __shared__ unsigned long long part[kFBlock / 32];
+    unsigned long long c = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i < n; i += stride) {
+        if (i + 4 <= n && ((n & 3) == 0)) {
+            const uint4 q = __ldcs(reinterpret_cast<const uint4*>(cnt + i));
+            c += (q.x != 0u) + (q.y != 0u) + (q.z != 0u) + (q.w != 0u);
+        } else {
+            for (int64_t k = i; k < min(n, i + 4); ++k) c += __ldcs(cnt + k) != 0u;
+        }
+    }
+    c = wsum(c);
+    if (lane_id() == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kFBlock / 32; ++w) t += part[w];
+        if (t) atomicAdd(out, t);
+    }
+}
+
 cudaError_t launch_buckets(int pass, int kind, int mode, const GraphDev& g, const uint32_t* X,
                            const uint16_t* tab, int J, uint32_t* cnt_or_end, unsigned long long* nonempty,
                            int32_t* other, uint16_t* mask, cudaStream_t st) {
     if (g.m == 0) return cudaSuccess;
     const int grid = edge_walk_grid(g);
+    cudaError_t e;
     if (mode == kPush)
-        return pass == 0 ? buckets_mode<kPush, 0>(kind, g, X, tab, J, cnt_or_end, nonempty, other, mask, grid, st)
-                         : buckets_mode<kPush, 1>(kind, g, X, tab, J, cnt_or_end, nonempty, other, mask, grid, st);
-    return pass == 0 ? buckets_mode<kCover, 0>(kind, g, X, tab, J, cnt_or_end, nonempty, other, mask, grid, st)
-                     : buckets_mode<kCover, 1>(kind, g, X, tab, J, cnt_or_end, nonempty, other, mask, grid, st);
+        e = pass == 0 ? buckets_mode<kPush, 0>(kind, g, X, tab, J, cnt_or_end, nonempty, other, mask, grid, st)
+                      : buckets_mode<kPush, 1>(kind, g, X, tab, J, cnt_or_end, nonempty, other, mask, grid, st);
+    else
+        e = pass == 0 ? buckets_mode<kCover, 0>(kind, g, X, tab, J, cnt_or_end, nonempty, other, mask, grid, st)
+                      : buckets_mode<kCover, 1>(kind, g, X, tab, J, cnt_or_end, nonempty, other, mask, grid, st);
+    if (e != cudaSuccess || pass != 0) return e;
+    // the nonempty buckets, counted after the pass (not by a contended
+    // counter in it)
+    const int64_t nb = (int64_t)g.n * (J >> 4);
+    k_count_nonzero<<<152 * 4, kFBlock, 0, st>>>(cnt_or_end, nb, nonempty);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_live_chunks(int kind, int mode, const GraphDev& g, const uint32_t* X, const uint16_t* tab,
