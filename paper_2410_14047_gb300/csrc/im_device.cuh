@@ -48,7 +48,9 @@ struct GraphDev {
 
 // Work-queue entry: a vertex, the start of its edge row in the CSR the phase
 // walks, its offset in the phase's flat edge space, and a model word (the
-// weighted-cascade threshold of its in-edges for propagation sweeps).
+// weighted-cascade threshold of its in-edges for propagation sweeps).  A
+// bucket entry holds the bucket, its list start, its offset and a free word
+// (the length, or the chunk's 16 bits in queues built at level 0).
 struct __align__(16) QEntry {
     int32_t v;
     int32_t rp;

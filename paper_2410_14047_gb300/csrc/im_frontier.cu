@@ -1679,28 +1679,58 @@ __global__ void __launch_bounds__(kFBlock) k_live_chunks(GraphDev g, const uint3
 }
 
 // Bucketed live lists: pass 0 counts, pass 1 places (see launch_buckets).
+// Edges are walked in row order and a row's edges are sorted by hash, so the
+// lanes of a warp often share a bucket (same row, nearby simulations): the
+// count pass makes one atomic per bucket and chunk for those lanes together;
+// the place pass takes positions one entry at a time (its stores follow).
 template <int KIND, int MODE, int PASS>
 __global__ void __launch_bounds__(kFBlock) k_buckets(GraphDev g, const uint32_t* __restrict__ X,
                                                      const uint16_t* __restrict__ tab, int J,
                                                      uint32_t* __restrict__ cnt_or_end,
-                                                     unsigned long long* __restrict__ nonempty,
                                                      int32_t* __restrict__ other_out,
                                                      uint16_t* __restrict__ mask_out) {
     __shared__ __align__(16) uint32_t sX[kMaxJ];
     __shared__ uint16_t sTab[kTabSize];
     load_sims(X, tab, J, sX, sTab);
     const int C = J >> 4;
-    for_each_edge<KIND, MODE>(g, [&](int64_t, int32_t v, int32_t other, uint32_t h, uint32_t thr) {
-        edge_chunk_masks(h, thr, J, sX, sTab, [&](int c, uint32_t m16) {
-            const int64_t b = (int64_t)v * C + c;
-            if constexpr (PASS == 0) {
-                atomicAdd(cnt_or_end + b, 1u);
-            } else {
-                const uint32_t pos = atomicAdd(cnt_or_end + b, 1u);
+    if constexpr (PASS == 1) {
+        for_each_edge<KIND, MODE>(g, [&](int64_t, int32_t v, int32_t other, uint32_t h, uint32_t thr) {
+            edge_chunk_masks(h, thr, J, sX, sTab, [&](int c, uint32_t m16) {
+                const uint32_t pos = atomicAdd(cnt_or_end + (int64_t)v * C + c, 1u);
                 other_out[pos] = other;
                 mask_out[pos] = (uint16_t)m16;
-            }
+            });
         });
+        return;
+    }
+    const int32_t* rp = MODE == kPush ? g.rp_in : g.rp_out;
+    walk_rows_all([rp](int32_t r) -> int64_t { return (int64_t)__ldg(rp + r); }, g.n, g.m,
+                  [&](int64_t e, int32_t v, bool valid) {
+        uint32_t lo = 0u, hi = 0u;
+        if (valid) {
+            uint32_t h, thr;
+            if constexpr (MODE == kPush) {
+                const int32_t other = __ldg(g.src_in + e);
+                h = __ldg(g.h_in + e);
+                const uint32_t aux = KIND == kWC ? __ldg(g.thr_v + v) : 0u;
+                thr = edge_threshold<KIND, true>(g, (uint32_t)other, (uint32_t)v, e, aux);
+            } else {
+                const int32_t other = __ldg(g.col_out + e);
+                h = __ldg(g.h_out + e);
+                thr = edge_threshold<KIND, false>(g, (uint32_t)v, (uint32_t)other, e, 0u);
+            }
+            edge_live_chunks(h, thr, J, sX, sTab, lo, hi);
+        }
+        uint32_t ul = __reduce_or_sync(0xFFFFFFFFu, lo), uh = __reduce_or_sync(0xFFFFFFFFu, hi);
+        while (ul | uh) {
+            int c;
+            if (ul) { c = __ffs(ul) - 1; ul &= ul - 1; }
+            else { c = 32 + __ffs(uh) - 1; uh &= uh - 1; }
+            const bool mine = ((c < 32 ? lo >> c : hi >> (c - 32)) & 1u) != 0u;
+            const long long key = mine ? (long long)v * C + c : -1ll;
+            const unsigned grp = __match_any_sync(0xFFFFFFFFu, key);
+            if (mine && (int)lane_id() == __ffs(grp) - 1) atomicAdd(cnt_or_end + key, (unsigned)__popc(grp));
+        }
     });
 }
 
@@ -1790,13 +1820,12 @@ static cudaError_t live_chunks_mode(int kind, const GraphDev& g, const uint32_t*
 
 template <int MODE, int PASS>
 static cudaError_t buckets_mode(int kind, const GraphDev& g, const uint32_t* X, const uint16_t* tab, int J,
-                                uint32_t* ce, unsigned long long* ne, int32_t* other, uint16_t* mask, int grid,
-                                cudaStream_t st) {
+                                uint32_t* ce, int32_t* other, uint16_t* mask, int grid, cudaStream_t st) {
     switch (kind) {
-        case kUniform: k_buckets<kUniform, MODE, PASS><<<grid, kFBlock, 0, st>>>(g, X, tab, J, ce, ne, other, mask); break;
-        case kWC: k_buckets<kWC, MODE, PASS><<<grid, kFBlock, 0, st>>>(g, X, tab, J, ce, ne, other, mask); break;
-        case kTrivalency: k_buckets<kTrivalency, MODE, PASS><<<grid, kFBlock, 0, st>>>(g, X, tab, J, ce, ne, other, mask); break;
-        default: k_buckets<kExplicit, MODE, PASS><<<grid, kFBlock, 0, st>>>(g, X, tab, J, ce, ne, other, mask); break;
+        case kUniform: k_buckets<kUniform, MODE, PASS><<<grid, kFBlock, 0, st>>>(g, X, tab, J, ce, other, mask); break;
+        case kWC: k_buckets<kWC, MODE, PASS><<<grid, kFBlock, 0, st>>>(g, X, tab, J, ce, other, mask); break;
+        case kTrivalency: k_buckets<kTrivalency, MODE, PASS><<<grid, kFBlock, 0, st>>>(g, X, tab, J, ce, other, mask); break;
+        default: k_buckets<kExplicit, MODE, PASS><<<grid, kFBlock, 0, st>>>(g, X, tab, J, ce, other, mask); break;
     }
     return cudaGetLastError();
 }
@@ -1838,11 +1867,11 @@ cudaError_t launch_buckets(int pass, int kind, int mode, const GraphDev& g, cons
     const int grid = edge_walk_grid(g);
     cudaError_t e;
     if (mode == kPush)
-        e = pass == 0 ? buckets_mode<kPush, 0>(kind, g, X, tab, J, cnt_or_end, nonempty, other, mask, grid, st)
-                      : buckets_mode<kPush, 1>(kind, g, X, tab, J, cnt_or_end, nonempty, other, mask, grid, st);
+        e = pass == 0 ? buckets_mode<kPush, 0>(kind, g, X, tab, J, cnt_or_end, other, mask, grid, st)
+                      : buckets_mode<kPush, 1>(kind, g, X, tab, J, cnt_or_end, other, mask, grid, st);
     else
-        e = pass == 0 ? buckets_mode<kCover, 0>(kind, g, X, tab, J, cnt_or_end, nonempty, other, mask, grid, st)
-                      : buckets_mode<kCover, 1>(kind, g, X, tab, J, cnt_or_end, nonempty, other, mask, grid, st);
+        e = pass == 0 ? buckets_mode<kCover, 0>(kind, g, X, tab, J, cnt_or_end, other, mask, grid, st)
+                      : buckets_mode<kCover, 1>(kind, g, X, tab, J, cnt_or_end, other, mask, grid, st);
     if (e != cudaSuccess || pass != 0) return e;
     // the nonempty buckets, counted after the pass (not by a contended
     // counter in it)
@@ -1989,12 +2018,15 @@ __device__ __forceinline__ void bucket_level0(const LevelArgs& a, bool valid, in
         }
         if (ne) {
             const uint32_t u = (uint32_t)(b / a.chunks), c = (uint32_t)(b % a.chunks);
-            if (h16) h16[(size_t)u * a.words * 2 + c] = __ldcg(b16 + (size_t)u * a.words * 2 + c);
+            const uint16_t bits16 = __ldcg(b16 + (size_t)u * a.words * 2 + c);
+            if (h16) h16[(size_t)u * a.words * 2 + c] = bits16;
             const int32_t my = slot + __popc(m & ((1u << lane) - 1u));
             if (gb != ~0ull) {
                 if (my < a.bq_cap) {
+                    // (a bucket entry's last word: the chunk's bits here, unused by the
+                    // level walks, read by the pull)
                     QEntry e;
-                    e.v = (int32_t)b; e.rp = (int32_t)st; e.off = (int32_t)(off + lincl - len); e.aux = len;
+                    e.v = (int32_t)b; e.rp = (int32_t)st; e.off = (int32_t)(off + lincl - len); e.aux = bits16;
                     q[my] = e;
                 } else {
                     atomicOr(overflow, 1ull);
@@ -2154,7 +2186,7 @@ __global__ void __launch_bounds__(kFBlock) k_pull_buckets(LevelArgs a, const QEn
     const unsigned long long cv = __ldcg(pctr);
     const int32_t nq = (int32_t)(cv >> kCountShift);
     const int64_t total = (int64_t)(cv & kEdgeMask);
-    const int J = a.J, words = a.words;
+    const int J = a.J;
     const uint32_t C = (uint32_t)a.chunks;
     const int lane = (int)lane_id();
     unsigned long long n_cas = 0;
@@ -2165,10 +2197,10 @@ __global__ void __launch_bounds__(kFBlock) k_pull_buckets(LevelArgs a, const QEn
         if (valid) {
             const int4 raw = __ldg(reinterpret_cast<const int4*>(q) + r);
             b = (uint32_t)raw.x;
-            const uint32_t u = b / C, c = b % C;
+            const uint32_t c = b % C;
             const int64_t e = (int64_t)(uint32_t)raw.y + (f - raw.z);
             const int32_t w = __ldg(a.bk_other + e);
-            const uint32_t a16 = (__ldcg(a.aff + (size_t)u * words + (c >> 1)) >> ((c & 1u) * 16u)) & 0xFFFFu;
+            const uint32_t a16 = (uint32_t)raw.w;  // the chunk's affected bits, from the queue entry
             const uint32_t m16 = __ldg(a.bk_mask + e) & a16;
             if (m16) {
                 const uint4 pw = ld_cg16(a.M + (size_t)w * J + c * 16);
