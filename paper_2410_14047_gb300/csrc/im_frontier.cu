@@ -2092,29 +2092,59 @@ __global__ void __launch_bounds__(kFBlock) k_reset_affected(uint8_t* __restrict_
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x; v0 < n; v0 += stride) {
         const int64_t v = v0 + threadIdx.x;
+        const int lane = (int)lane_id();
         bool listed = false;
         uint2 lm = make_uint2(0u, 0u);
+        uint32_t nzw = 0u;  // words of v with an affected bit (words <= 32)
         if (v < n) {
             uint32_t am_lo = 0u, am_hi = 0u;
-            const uint32_t ku = mm3_k(hkey ? (uint32_t)hkey[v] : (uint32_t)v);
             for (int w = 0; w < words; ++w) {
-                uint32_t b = __ldcg(aff + (size_t)v * words + w);
+                const uint32_t b = __ldcg(aff + (size_t)v * words + w);
                 const uint32_t hb = halves_nonzero(b);
                 if (w < 16) am_lo |= hb << (2 * w);
                 else am_hi |= hb << (2 * (w - 16));
-                while (b) {
-                    const int j = 32 * w + __ffs(b) - 1;
-                    b &= b - 1;
-                    M[(size_t)v * J + j] = (uint8_t)rank_of(ku, __ldg(salt + j));
-                }
+                if (b) nzw |= 1u << w;
             }
             listed = (am_lo | am_hi) != 0u;
             lm = make_uint2(am_lo, am_hi);
         }
+        // the resets, dealt one (vertex, word) a lane: a vertex affected in
+        // many simulations spreads over many lanes
+        const int nz = __popc(nzw);
+        int incl = nz;
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, incl, s);
+            if (lane >= s) incl += y;
+        }
+        const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        const int excl = incl - nz;
+        for (int base = 0; base < total; base += 32) {
+            const int k = base + lane;
+            int i = 0;
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                const int ic = __shfl_sync(0xFFFFFFFFu, incl, i + s - 1);
+                if (ic <= k) i += s;
+            }
+            if (i > 31) i = 31;
+            const int ex_i = __shfl_sync(0xFFFFFFFFu, excl, i);
+            const uint32_t nzw_i = __shfl_sync(0xFFFFFFFFu, nzw, i);
+            const int64_t v_i = v - lane + i;  // the owner lane's vertex
+            if (k < total) {
+                const int w = (int)__fns(nzw_i, 0u, k - ex_i + 1);
+                const uint32_t ku = mm3_k(hkey ? (uint32_t)hkey[v_i] : (uint32_t)v_i);
+                uint32_t b = __ldcg(aff + (size_t)v_i * words + w);
+                while (b) {
+                    const int j = 32 * w + __ffs(b) - 1;
+                    b &= b - 1;
+                    M[(size_t)v_i * J + j] = (uint8_t)rank_of(ku, __ldg(salt + j));
+                }
+            }
+        }
         // one list reservation per warp
         const unsigned wm = __ballot_sync(0xFFFFFFFFu, listed);
         if (wm) {
-            const int lane = (int)lane_id();
             unsigned int base = 0u;
             if (lane == 0) base = atomicAdd(list_count, (unsigned)__popc(wm));
             base = __shfl_sync(0xFFFFFFFFu, base, 0);
