@@ -853,11 +853,14 @@ __device__ __forceinline__ void chain_drain(const GraphDev& g, const LevelArgs& 
         __syncwarp();
         const uint32_t len = (uint32_t)it.z, bits = (uint32_t)it.w & 0xFFFFu;
         const int d = (int)((uint32_t)it.w >> 16);
-        if (lane == 0) ++st_batches;
-        InlineCand ic;
-        bucket_pos<KIND, MODE>(g, a, (uint32_t)lane < len, (uint32_t)it.x, (int64_t)(uint32_t)it.y + lane, bits,
-                               st_chunks, st_cas, st_new, st_dealt, out_b, ic);
-        chain_push(stk, sp, ic, d + 1);
+        for (uint32_t off = 0; off < len; off += 32) {
+            if (lane == 0) ++st_batches;
+            InlineCand ic;
+            bucket_pos<KIND, MODE>(g, a, off + (uint32_t)lane < len, (uint32_t)it.x,
+                                   (int64_t)(uint32_t)it.y + off + lane, bits, st_chunks, st_cas, st_new, st_dealt,
+                                   out_b, ic);
+            chain_push(stk, sp, ic, d + 1);
+        }
     }
     sp = 0;
 }
