@@ -19,8 +19,8 @@ from . import im_ctx_get_tuning, im_ctx_set_tuning
 
 DEFAULT_SPACE = {
     "heavy_indeg": [64, 256],
-    "light_batches": [4, 16],
-    "dense_div": [0, 4],
+    "light_batches": [4, 16, 32],
+    "dense_div": [0, 2],
     "buckets": [0, 2],
 }
 
