@@ -215,7 +215,7 @@ struct im_graph {
     int64_t m = 0;
     int kind = kUniform;       // kernel family (a per-target model runs as kWC)
     int load_kind = kUniform;  // model kind given at load
-    DBuf rp_out, col_out, rp_in, src_in, h_in, h_out, thrw_out, thr_v, thr_out, thr_in, cls_split, q_dense,
+    DBuf rp_out, col_out, rp_in, src_in, h_in, h_out, thrw_out, thr_v, thr_out, thr_in, q_dense,
         hkey;
     int32_t n_dense = 0;
     GraphDev dev{};
@@ -384,7 +384,7 @@ static im_status check_model(im_ctx* c, const im_model* mdl, int64_t m) {
 static void graph_release(im_graph* g) {
     im_ctx* c = g->ctx;
     for (DBuf* b : {&g->rp_out, &g->col_out, &g->rp_in, &g->src_in, &g->h_in, &g->h_out,
-                    &g->thrw_out, &g->thr_v, &g->thr_out, &g->thr_in, &g->cls_split, &g->q_dense,
+                    &g->thrw_out, &g->thr_v, &g->thr_out, &g->thr_in, &g->q_dense,
                     &g->hkey})
         dfree(c, *b);
 }
@@ -466,7 +466,6 @@ static im_status graph_load_impl(im_ctx* c, int32_t n, int64_t m, const int32_t*
     if ((s = dalloc(c, e_bytes, g->thrw_out)) != IM_OK) return bail(s);
     if ((s = dalloc(c, (size_t)n * 4, g->thr_v)) != IM_OK) return bail(s);
     if ((s = dalloc(c, (size_t)n * sizeof(QEntry), g->q_dense)) != IM_OK) return bail(s);
-    if (model->kind == kTrivalency && (s = dalloc(c, (size_t)n * 8, g->cls_split)) != IM_OK) return bail(s);
     DBuf cnt, tmp;
     if ((s = dalloc(c, ((size_t)n + 1) * 4, cnt)) != IM_OK) return bail(s);
     const size_t tmp_bytes = std::max(scan_tmp_bytes(n), build_in_csr_tmp_bytes(m));
@@ -506,9 +505,7 @@ static im_status graph_load_impl(im_ctx* c, int32_t n, int64_t m, const int32_t*
     // in-CSR sorted by (target, class, edge hash): rows of equal-threshold in-edges in hash order
     e = launch_build_in_csr(g->rp_out.as<int32_t>(), g->col_out.as<int32_t>(), n, m, g->kind,
                             g->dev.tri_seed, g->hkey.as<int32_t>(), g->thr_out.as<uint32_t>(),
-                            g->rp_in.as<int32_t>(),
-                            g->src_in.as<int32_t>(), g->h_in.as<uint32_t>(), g->thr_in.as<uint32_t>(),
-                            g->cls_split.as<int2>(), tmp.p, st);
+                            g->src_in.as<int32_t>(), g->h_in.as<uint32_t>(), g->thr_in.as<uint32_t>(), tmp.p, st);
     // static vertex-ordered queue for dense levels (cnt and tmp reused as scratch)
     DBuf pos;
     if (e == cudaSuccess && (s = dalloc(c, ((size_t)n + 1) * 4, pos)) != IM_OK) { release_tmp(); return bail(s); }
@@ -1584,7 +1581,7 @@ uint64_t query_bytes(const im_graph* g, int32_t J, int32_t K) {
 uint64_t graph_bytes(const im_graph* g) {
     uint64_t total = 0;
     for (const DBuf* b : {&g->rp_out, &g->col_out, &g->rp_in, &g->src_in, &g->h_in, &g->h_out,
-                          &g->thrw_out, &g->thr_v, &g->thr_out, &g->thr_in, &g->cls_split,
+                          &g->thrw_out, &g->thr_v, &g->thr_out, &g->thr_in,
                           &g->q_dense, &g->hkey})
         total += b->bytes;
     return total;

@@ -1083,32 +1083,10 @@ __global__ void k_in_gather(const unsigned long long* __restrict__ keys, const i
     }
 }
 
-// For trivalency: first in-edge of class >= 1 and of class >= 2 in each in-row.
-__global__ void k_cls_split(const int32_t* __restrict__ rp_in, const unsigned long long* __restrict__ keys,
-                            int32_t n, int2* __restrict__ split) {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n) return;
-    const int32_t b = rp_in[v], e = rp_in[v + 1];
-    int2 r;
-    int32_t lo = b, hi = e;  // first index with class >= 1
-    while (lo < hi) {
-        const int32_t mid = (lo + hi) >> 1;
-        if (((keys[mid] >> 31) & 3ull) >= 1ull) hi = mid; else lo = mid + 1;
-    }
-    r.x = lo;
-    hi = e;
-    while (lo < hi) {
-        const int32_t mid = (lo + hi) >> 1;
-        if (((keys[mid] >> 31) & 3ull) >= 2ull) hi = mid; else lo = mid + 1;
-    }
-    r.y = lo;
-    split[v] = r;
-}
-
 cudaError_t launch_build_in_csr(const int32_t* rp_out, const int32_t* col_out, int32_t n, int64_t m,
                                 int kind, uint32_t tri_seed, const int32_t* hkey, const uint32_t* thr_out,
-                                const int32_t* rp_in, int32_t* src_in, uint32_t* h_in,
-                                uint32_t* thr_in, int2* cls_split, void* tmp, cudaStream_t st) {
+                                int32_t* src_in, uint32_t* h_in,
+                                uint32_t* thr_in, void* tmp, cudaStream_t st) {
     if (m == 0) return cudaSuccess;
     char* p = static_cast<char*>(tmp);
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(p);
@@ -1123,7 +1101,6 @@ cudaError_t launch_build_in_csr(const int32_t* rp_out, const int32_t* col_out, i
     cudaError_t e = launch_radix_sort(keys, perm, m, bits, p, st);
     if (e != cudaSuccess) return e;
     k_in_gather<<<152 * 8, kBlock, 0, st>>>(keys, perm, m, src_out, thr_out, src_in, h_in, thr_in);
-    if (cls_split) k_cls_split<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(rp_in, keys, n, cls_split);
     return cudaGetLastError();
 }
 

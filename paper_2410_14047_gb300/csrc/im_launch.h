@@ -271,15 +271,14 @@ size_t scan_tmp_bytes(int32_t n);
 cudaError_t launch_exclusive_scan(const int32_t* cnt, int32_t n, int32_t* out, void* tmp,
                                   cudaStream_t st);
 // In-CSR sorted by (target, trivalency class, edge hash): src_in, h_in (edge
-// hashes), thr_in (explicit models, may be NULL), cls_split (trivalency, may
-// be NULL).  rp_in must already hold the in-CSR row pointers.  hkey (may be
-// NULL = the vertex id itself) is the id each vertex hashes with (batches:
-// its id inside its own graph).
+// hashes), thr_in (explicit models, may be NULL), in the order of the in-CSR
+// row pointers built beforehand.  hkey (may be NULL = the vertex id itself) is
+// the id each vertex hashes with (batches: its id inside its own graph).
 size_t build_in_csr_tmp_bytes(int64_t m);
 cudaError_t launch_build_in_csr(const int32_t* rp_out, const int32_t* col_out, int32_t n, int64_t m,
                                 int kind, uint32_t tri_seed, const int32_t* hkey, const uint32_t* thr_out,
-                                const int32_t* rp_in, int32_t* src_in, uint32_t* h_in,
-                                uint32_t* thr_in, int2* cls_split, void* tmp, cudaStream_t st);
+                                int32_t* src_in, uint32_t* h_in,
+                                uint32_t* thr_in, void* tmp, cudaStream_t st);
 cudaError_t launch_out_edge_words(const int32_t* rp_out, const int32_t* col_out, int32_t n, int64_t m,
                                   const uint32_t* thr_v, const int32_t* hkey, uint32_t* h_out,
                                   uint32_t* thrw_out, cudaStream_t st);
