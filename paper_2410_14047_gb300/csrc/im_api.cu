@@ -868,7 +868,7 @@ static im_status run_levels(im_sketch* sk, int mode, bool all_first) {
     im_ctx* c = sk->ctx;
     auto st = c->stream;
     if (c->tuning.persistent) {
-        // the grid barrier counts arrivals in 64 groups of 32 blocks
+        // one cooperative grid of every resident block (at most 2048)
         const int pgrid = std::min(phase_grid(), 64 * 32);
         if (pgrid > 0) return run_phase_persistent(sk, mode, all_first, pgrid);
     }

@@ -3,9 +3,10 @@
 //
 // Work of a level = a "light" queue, walked as a flat edge space (sum of the
 // queued vertices' degrees), plus, for propagation, a "heavy" queue of
-// in-degree hubs.  Warps claim units dynamically from one counter: first the
-// heavy vertices (longest first), then slices of `light_batches` 32-edge
-// batches.  Each queued vertex carries a change mask (one bit per
+// in-degree hubs.  The units (the heavy vertices first, then slices of
+// `light_batches` 32-edge batches) go one to each warp, and, when a level has
+// more units than warps, the rest are claimed from one counter.  Each queued
+// vertex carries a change mask (one bit per
 // simulation): only simulations that changed at the previous level are pushed
 // (propagation) or expanded (cover).
 //
