@@ -241,6 +241,10 @@ struct im_sketch {
     bool lazy = false;      // picks after the first refresh stored sums only (im_select_seeds)
     bool chg_dirty = true;  // change masks may hold bits (new sketch, or a phase that failed)
     bool lb_ready = false;  // lb holds the sums of the last full pick or later refreshes
+    // a selection in flight: phases and rebuilds queue without host reads;
+    // their error word is read once at the end
+    bool defer = false;
+    bool pull_safe = false;  // the pull queue holds every out-bucket (it cannot overflow)
     DBuf out_seed, out_S, out_est;
     int32_t out_cap = 0;
     int32_t gen_counter = 0;
@@ -774,6 +778,7 @@ static im_status check_err(im_sketch* sk) {
     if (err & kErrQueue) return fail(c, IM_E_STATE, "frontier queue overflow");
     if (err & kErrCasLimit) return fail(c, IM_E_TIMEOUT, "register CAS retry limit exceeded");
     if (err & kErrBarrier) return fail(c, IM_E_TIMEOUT, "grid barrier wait exceeded its time limit");
+    if (err & kErrLevels) return fail(c, IM_E_TIMEOUT, "frontier did not empty within %d levels", kMaxLevels - 2);
     return IM_OK;
 }
 
@@ -829,11 +834,20 @@ static im_status run_phase_persistent(im_sketch* sk, int mode, bool all_first, i
     p.fmt = sk->fmt.as<uint8_t>();
     CK(c, timed(c, mode == kPush ? kTPush : kTCover,
                 [&] { return launch_phase(sk->kind, mode, sk->dev, p, grid, st); }));
+    // stamps gen_base .. gen_base + max_levels are this phase's
+    sk->gen_counter += kMaxLevels;
+    if (sk->gen_counter > (1 << 30)) {
+        CK(c, cudaMemsetAsync(sk->gen.p, 0, sk->gen.bytes, st));
+        sk->gen_counter = 0;
+    }
+    if (sk->defer && !c->trace) {
+        sk->chg_dirty = false;  // a failed phase fails the whole selection
+        return IM_OK;
+    }
     CK(c, cudaMemcpyAsync(c->pinned, bar, 16, cudaMemcpyDeviceToHost, st));
     CK(c, sync_collect(c));
     const unsigned int* hb = reinterpret_cast<const unsigned int*>(c->pinned);
     const int levels = (int)hb[3];
-    sk->gen_counter += levels + 1;
     sk->chg_dirty = true;
     if (c->trace && levels > 0 && levels < p.max_levels) {
         // per-level records from the in-kernel clock (one launch for all levels)
@@ -1019,17 +1033,18 @@ static im_status incremental_rebuild(im_sketch* sk) {
     CK(c, cudaMemsetAsync(x.list_count, 0, 4, st));
     CK(c, cudaMemsetAsync(x.pctr, 0, 16, st));
     CK(c, timed(c, kTFill, [&] { return launch_incremental(1, sk->kind, sk->dev, b, x, st); }));
-    CK(c, cudaMemcpyAsync(c->pinned, x.list_count, 4, cudaMemcpyDeviceToHost, st));
-    CK(c, cudaMemcpyAsync(c->pinned + 1, x.pctr, 16, cudaMemcpyDeviceToHost, st));
-    CK(c, sync_collect(c));
-    x.count = (int32_t)(uint32_t)c->pinned[0];
-    const int64_t npull = (int64_t)(c->pinned[1] >> kCountShift);
-    x.pull_buckets = sk->buckets && c->pinned[2] == 0 && npull <= sk->bq_cap ? 1 : 0;
-    if (x.pull_buckets) {
-        c->stats.pull_buckets += (uint64_t)npull;
-        c->stats.pull_entries += c->pinned[1] & kEdgeMask;
+    if (sk->buckets && sk->pull_safe) {
+        // the pull reads its queue's counters on the device
+        x.pull_buckets = 1;
+    } else {
+        CK(c, cudaMemcpyAsync(c->pinned, x.list_count, 4, cudaMemcpyDeviceToHost, st));
+        CK(c, cudaMemcpyAsync(c->pinned + 1, x.pctr, 16, cudaMemcpyDeviceToHost, st));
+        CK(c, sync_collect(c));
+        x.count = (int32_t)(uint32_t)c->pinned[0];
+        const int64_t npull = (int64_t)(c->pinned[1] >> kCountShift);
+        x.pull_buckets = sk->buckets && c->pinned[2] == 0 && npull <= sk->bq_cap ? 1 : 0;
     }
-    if (x.count > 0) {
+    if (x.pull_buckets || x.count > 0) {
         // timed with the reset (both rebuild registers from their own ranks)
         CK(c, timed(c, kTFill, [&] {
             if (!x.pull_buckets) {
@@ -1099,6 +1114,8 @@ static im_status stats_collect(im_sketch* sk) {
     s.sweep_buckets = h[kStSweepBuckets];
     s.sweep_bucket_entries = h[kStSweepBucketEntries];
     s.affected = h[kStAffected];
+    s.pull_buckets = h[kStPullBuckets];
+    s.pull_entries = h[kStPullEntries];
     // algorithmic bytes of the sweeps: queue entry (16 B) + the queued vertex's
     // register row (J B) per queued vertex; live chunk mask (4 B, 8 B when
     // J = 1024) per in-edge; source id + edge hash (8 B, + 4 B threshold for
@@ -1217,6 +1234,7 @@ static im_status build_buckets(im_sketch* sk) {
         }
     sk->chg_dirty = true;  // the new buffers start zeroed by the next phase
     sk->bq_cap = (int32_t)cap;
+    sk->pull_safe = cap >= (int64_t)nonempty[1];
     sk->buckets = true;
     return IM_OK;
 }
@@ -1435,6 +1453,7 @@ static im_status select_seeds_impl(im_ctx* c, im_graph* g, int32_t K, int32_t J,
     im_sketch* sk = nullptr;
     CKS(sketch_start(c, g, J, seed, model, &sk));
     sk->lazy = c->tuning.lazy_pick != 0;
+    sk->defer = true;
     // incremental rebuilds pay off with bucketed lists (sparse affected-set
     // searches); over edge scans a full rebuild is faster unless asked for (2)
     sk->incr = c->tuning.incremental == 2 || (c->tuning.incremental == 1 && sk->buckets);
@@ -1470,6 +1489,9 @@ static im_status select_seeds_impl(im_ctx* c, im_graph* g, int32_t K, int32_t J,
         }
     }
     sk->picks = K;
+    // the error word of every deferred phase and rebuild
+    if ((s = check_err(sk)) != IM_OK) return bail(s);
+    sk->defer = false;  // step-level calls on a returned sketch check each phase
     std::vector<int32_t> seeds(K);
     std::vector<double> est(K);
     cudaError_t e = cudaMemcpyAsync(seeds.data(), sk->out_seed.p, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream);

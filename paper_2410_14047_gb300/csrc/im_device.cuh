@@ -25,7 +25,7 @@ enum ModelKind : int { kUniform = 0, kWC = 1, kTrivalency = 2, kExplicit = 3,
                        kTargetModel = 4 /* per-target-vertex probability; runs as kWC */ };
 
 // Error bits a kernel may raise (host turns them into IM_E_* codes).
-enum : uint32_t { kErrCasLimit = 1u, kErrQueue = 2u, kErrBarrier = 4u };
+enum : uint32_t { kErrCasLimit = 1u, kErrQueue = 2u, kErrBarrier = 4u, kErrLevels = 8u };
 
 // Device view of a loaded graph.
 struct GraphDev {

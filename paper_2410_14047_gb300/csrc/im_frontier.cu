@@ -1397,7 +1397,12 @@ __global__ void __launch_bounds__(kFBlock, kPhaseMinBlocks) k_phase(GraphDev g, 
         a.fmt_prev = p.fmt ? p.fmt + t - 1 : nullptr;
         clear_prev_bits(a, warp, nwarps);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *p.levels_out = t;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *p.levels_out = t;
+        // a frontier that did not empty within the level limit is an error the
+        // host reads with the others (it may read it only after later launches)
+        if (t >= p.max_levels) atomicOr(a.err, kErrLevels);
+    }
 }
 
 int phase_grid() {
@@ -2220,6 +2225,10 @@ __global__ void __launch_bounds__(kFBlock) k_pull_buckets(LevelArgs a, const QEn
     const unsigned long long cv = __ldcg(pctr);
     const int32_t nq = (int32_t)(cv >> kCountShift);
     const int64_t total = (int64_t)(cv & kEdgeMask);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        atomicAdd(a.stats + kStPullBuckets, (unsigned long long)nq);
+        atomicAdd(a.stats + kStPullEntries, (unsigned long long)total);
+    }
     const int J = a.J;
     const uint32_t C = (uint32_t)a.chunks;
     const int lane = (int)lane_id();
@@ -2303,7 +2312,7 @@ cudaError_t launch_incremental(int step, int kind, const GraphDev& g, const Leve
                                                        x.list, x.ldeg, x.lmask, x.list_count, a, x.pq, x.pctr);
             break;
         case 2: {
-            if (x.count == 0) break;
+            if (!x.pull_buckets && x.count == 0) break;
             const int pg = grid;
             if (x.pull_buckets) {
                 k_pull_buckets<<<pg, kFBlock, 0, st>>>(a, x.pq, x.pctr);

@@ -30,6 +30,8 @@ enum StatIndex : int {
     kStSweepBuckets,        // queued buckets walked by propagation levels
     kStSweepBucketEntries,  // bucket list entries processed (source chunk changed)
     kStAffected,            // registers recomputed by incremental rebuilds
+    kStPullBuckets,         // out-buckets queued by the pulls of incremental rebuilds
+    kStPullEntries,         // out-bucket entries walked by those pulls
     kStCount
 };
 
