@@ -805,7 +805,10 @@ static im_status phase_begin(im_sketch* sk, int mode, int fmt0 = -1) {
     return IM_OK;
 }
 
-// All levels of a phase in one cooperative launch; one host synchronisation.
+// All levels of a phase in one cooperative launch.  Inside a selection
+// (sk->defer) nothing is read back: the host queues the next work at once and
+// reads the error word at the end; otherwise (step-level calls, tracing) the
+// host reads the level count and the error word after the launch.
 static im_status run_phase_persistent(im_sketch* sk, int mode, bool all_first, int grid) {
     im_ctx* c = sk->ctx;
     auto st = c->stream;
