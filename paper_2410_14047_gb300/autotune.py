@@ -21,7 +21,7 @@ DEFAULT_SPACE = {
     "heavy_indeg": [64, 256],
     "light_batches": [4, 16, 32],
     "dense_div": [0, 2],
-    "buckets": [0, 2],
+    "buckets": [0, 1, 2],
 }
 
 
