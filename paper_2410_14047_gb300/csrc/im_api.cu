@@ -227,7 +227,8 @@ struct im_sketch {
     int32_t J = 0;
     DBuf M, X, salt, tab, ql[3], qh[3], ctr, claim, chg[3], gen, seed_bits, count, part_S, part_u,
         ticket, stats, err, bar, lb, cand, part_S2, part_u2, lcm_in_lo, lcm_in_hi, lcm_out_lo, lcm_out_hi,
-        level_ns, fmt, nv, aff, alist, acount, aldeg, aloff, almask, ascan, apctr;
+        level_ns, fmt, nv, aff, alist, acount, aldeg, aloff, almask, ascan, apctr, awl,
+        awlc;
     bool incr = false;      // covers record newly visited registers; rebuilds are incremental
     // bucket mode: bucketed live lists per orientation (0: in-edges, 1:
     // out-edges); the light queues then hold buckets, bq_cap entries each
@@ -595,6 +596,8 @@ static void sketch_plan(im_sketch* sk, int32_t n, int64_t m_edges, int32_t J, Bu
     A(sk->ascan, scan_tmp_bytes(n));
     A(sk->acount, 4);
     A(sk->apctr, 16);
+    A(sk->awl, (size_t)n * ((J + 31) / 32) * 4);
+    A(sk->awlc, 4);
     A(sk->lb, (size_t)n * 8);
     A(sk->cand, 4);
     A(sk->part_S2, (size_t)pg * 8);
@@ -745,6 +748,10 @@ static DBuf& chg_buf(im_sketch* sk, int mode, int i) {
 static void set_lcm(LevelArgs& a, const im_sketch* sk, int mode) {
     const bool in = mode != kCover;
     a.aff = sk->aff.as<uint32_t>();
+    // the affected-set search lists the words it makes nonzero (bucket mode)
+    const bool words = mode == kAffect && sk->buckets && sk->pull_safe;
+    a.awl = words ? sk->awl.as<uint32_t>() : nullptr;
+    a.awl_count = words ? sk->awlc.as<unsigned int>() : nullptr;
     a.nv = (mode == kCover && sk->incr) ? sk->nv.as<uint32_t>() : nullptr;
     a.lcm_lo = (in ? sk->lcm_in_lo : sk->lcm_out_lo).as<uint32_t>();
     a.lcm_hi = sk->J > 512 ? (in ? sk->lcm_in_hi : sk->lcm_out_hi).as<uint32_t>() : nullptr;
@@ -1017,6 +1024,10 @@ static im_status incremental_rebuild(im_sketch* sk) {
     // the pull queue: the third light queue, free between phases
     x.pq = sk->ql[2].as<QEntry>();
     x.pctr = sk->apctr.as<unsigned long long>();
+    x.words_list = sk->buckets && sk->pull_safe ? 1 : 0;
+    x.awl = sk->awl.as<uint32_t>();
+    x.awl_count = sk->awlc.as<unsigned int>();
+    if (x.words_list) CK(c, cudaMemsetAsync(sk->awlc.p, 0, 4, st));
     // 1. the affected registers (level 0 in bucket format where the sketch
     // has bucketed lists)
     CKS(phase_begin(sk, kAffect, x.buckets));

@@ -23,6 +23,8 @@
 // (the edge hash must agree with X_j above the threshold's top bit).  Each
 // changed simulation costs two binary searches in v's row plus the live
 // candidates, instead of a scan of all in-edges.
+#include <cooperative_groups.h>
+
 #include "im_launch.h"
 
 namespace im {
@@ -283,6 +285,14 @@ __device__ __forceinline__ uint32_t mark_affected(const LevelArgs& a, const uint
     const uint32_t old = atomicOr(a.aff + (size_t)o * a.words + (c >> 1), b16 << sh);
     const uint32_t fresh = b16 & ~(old >> sh) & 0xFFFFu;
     st_new += (unsigned)__popc(fresh);
+    if (old == 0u && a.awl) {
+        // the word's first bit: list it (one append for the lanes here together)
+        cooperative_groups::coalesced_group grp = cooperative_groups::coalesced_threads();
+        unsigned int base = 0u;
+        if (grp.thread_rank() == 0) base = atomicAdd(a.awl_count, grp.size());
+        base = grp.shfl(base, 0);
+        a.awl[base + grp.thread_rank()] = (uint32_t)o * (uint32_t)a.words + (c >> 1);
+    }
     return fresh;
 }
 
@@ -2295,6 +2305,98 @@ __global__ void __launch_bounds__(kFBlock) k_push_init_list(GraphDev g, LevelArg
     }
 }
 
+// Bucket entries for listed words (warp-collective): word item it = v * words
+// + w (valid lanes) gives chunks 2w, 2w+1; each chunk whose 16 bits in `bits`
+// are nonzero and whose bucket (a's orientation) is nonempty is queued (its
+// bits in the entry's last word), and, with chg, its bits go to that change
+// mask.
+__device__ __forceinline__ void bucket_words(const LevelArgs& a, bool valid, uint32_t it,
+                                             const uint32_t* __restrict__ bits, uint32_t* chg, QEntry* q,
+                                             unsigned long long* ctr, unsigned long long* overflow) {
+    const int lane = (int)lane_id();
+    const uint32_t v = valid ? it / (uint32_t)a.words : 0u, w = valid ? it % (uint32_t)a.words : 0u;
+    const uint32_t word = valid ? __ldcg(bits + it) : 0u;
+    uint16_t* h16 = reinterpret_cast<uint16_t*>(chg);
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const uint32_t b16 = (word >> (16 * half)) & 0xFFFFu;
+        const int64_t b = (int64_t)v * a.chunks + 2 * w + half;
+        uint32_t st = 0u, en = 0u;
+        if (b16) {
+            st = bucket_start(a.bk_end, b);
+            en = __ldcg(a.bk_end + b);
+        }
+        const bool ne = b16 != 0u && en > st;
+        if (ne && h16) h16[(size_t)it * 2 + half] = (uint16_t)b16;
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, ne);
+        if (!m) continue;
+        const uint32_t len = ne ? en - st : 0u;
+        uint32_t incl = len;
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, s);
+            if (lane >= s) incl += y;
+        }
+        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        unsigned long long gb = ~0ull;
+        if (lane == 0) {
+            if (a.bq_guard && (int32_t)(__ldcg(ctr) >> kCountShift) >= a.bq_cap) atomicOr(overflow, 1ull);
+            else gb = atomicAdd(ctr, ((unsigned long long)__popc(m) << kCountShift) | (unsigned long long)tot);
+        }
+        gb = __shfl_sync(0xFFFFFFFFu, gb, 0);
+        if (!ne || gb == ~0ull) continue;
+        const int32_t slot = (int32_t)(gb >> kCountShift) + __popc(m & ((1u << lane) - 1u));
+        if (slot < a.bq_cap) {
+            QEntry e;
+            e.v = (int32_t)b; e.rp = (int32_t)st; e.off = (int32_t)((gb & kEdgeMask) + incl - len); e.aux = b16;
+            q[slot] = e;
+        } else {
+            atomicOr(overflow, 1ull);
+        }
+    }
+}
+
+// Reset of the listed affected words to their vertices' own ranks (Alg. 1),
+// and the pull queue of their chunks' out-buckets (o: out orientation).
+__global__ void __launch_bounds__(kFBlock) k_reset_words(uint8_t* __restrict__ M, int J, const uint32_t* __restrict__ salt,
+                                                         const int32_t* __restrict__ hkey, const uint32_t* __restrict__ aff,
+                                                         const uint32_t* __restrict__ awl,
+                                                         const unsigned int* __restrict__ awl_count, LevelArgs o,
+                                                         QEntry* pq, unsigned long long* pctr) {
+    const int64_t cnt = (int64_t)__ldcg(awl_count);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < cnt; i0 += stride) {
+        const int64_t i = i0 + threadIdx.x;
+        const bool valid = i < cnt;
+        const uint32_t it = valid ? __ldcg(awl + i) : 0u;
+        if (valid) {
+            const uint32_t v = it / (uint32_t)o.words, w = it % (uint32_t)o.words;
+            const uint32_t ku = mm3_k(hkey ? (uint32_t)hkey[v] : v);
+            uint32_t b = __ldcg(aff + it);
+            while (b) {
+                const int j = 32 * (int)w + __ffs(b) - 1;
+                b &= b - 1;
+                M[(size_t)v * J + j] = (uint8_t)rank_of(ku, __ldg(salt + j));
+            }
+        }
+        bucket_words(o, valid, it, aff, nullptr, pq, pctr, pctr + 1);
+    }
+}
+
+// Level 0 of the propagation after the pull from the listed words: their
+// chunks' in-buckets, the affected bits as the change mask.
+__global__ void __launch_bounds__(kFBlock) k_push_init_words(LevelArgs a, const uint32_t* __restrict__ awl,
+                                                             const unsigned int* __restrict__ awl_count) {
+    const int64_t cnt = (int64_t)__ldcg(awl_count);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < cnt; i0 += stride) {
+        const int64_t i = i0 + threadIdx.x;
+        const bool valid = i < cnt;
+        const uint32_t it = valid ? __ldcg(awl + i) : 0u;
+        bucket_words(a, valid, it, a.aff, a.chg_next, a.ql_out, a.cl_out, a.ch_out);
+    }
+}
+
 cudaError_t launch_incremental(int step, int kind, const GraphDev& g, const LevelArgs& a, const IncrArgs& x,
                                cudaStream_t st) {
     const int grid = 152 * 8;
@@ -2308,6 +2410,11 @@ cudaError_t launch_incremental(int step, int kind, const GraphDev& g, const Leve
             }
             break;
         case 1:
+            if (x.words_list) {
+                k_reset_words<<<grid, kFBlock, 0, st>>>(a.M, a.J, x.salt, x.hkey, a.aff, x.awl, x.awl_count, a, x.pq,
+                                                        x.pctr);
+                break;
+            }
             k_reset_affected<<<grid, kFBlock, 0, st>>>(a.M, g.n, a.J, a.words, x.salt, x.hkey, a.aff, g.rp_out,
                                                        x.list, x.ldeg, x.lmask, x.list_count, a, x.pq, x.pctr);
             break;
@@ -2327,6 +2434,10 @@ cudaError_t launch_incremental(int step, int kind, const GraphDev& g, const Leve
             break;
         }
         default:
+            if (x.words_list) {
+                k_push_init_words<<<grid, kFBlock, 0, st>>>(a, x.awl, x.awl_count);
+                break;
+            }
             switch (kind) {
                 case kUniform: k_push_init_list<kUniform><<<grid, kFBlock, 0, st>>>(g, a, x.list, x.list_count, x.buckets); break;
                 case kWC: k_push_init_list<kWC><<<grid, kFBlock, 0, st>>>(g, a, x.list, x.list_count, x.buckets); break;

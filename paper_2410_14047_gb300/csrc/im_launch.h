@@ -107,6 +107,8 @@ struct LevelArgs {
     int32_t bq_guard;                    // check the bucket queue's fill before each append (huge graphs)
     int32_t vq_cap;                      // vertex queue capacity (n)
     uint32_t* aff;                       // incremental rebuild: affected (vertex, simulation) bits
+    uint32_t* awl;                       // affected-set search: words of aff that became nonzero
+    unsigned int* awl_count;             //   (v * words + w each), their count (NULL: no list)
     uint32_t* nv;                        // covers: registers newly visited since the last build (may be NULL)
     int32_t chain;                       // continuation depth on small bucket levels (0 = none)
 };
@@ -162,6 +164,11 @@ struct IncrArgs {
     QEntry* pq;
     unsigned long long* pctr;
     int pull_buckets;
+    // the affected words listed by the search (bucket mode): steps 1 and 3
+    // then walk only them (words_list)
+    const uint32_t* awl;
+    const unsigned int* awl_count;
+    int words_list;
 };
 cudaError_t launch_incremental(int step, int kind, const GraphDev& g, const LevelArgs& a, const IncrArgs& x,
                                cudaStream_t st);
