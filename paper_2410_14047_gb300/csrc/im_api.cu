@@ -745,11 +745,18 @@ static DBuf& chg_buf(im_sketch* sk, int mode, int i) {
 }
 
 // Live chunk masks of the phase's edge orientation.
+// Incremental rebuilds walk the affected words the search lists (instead of
+// every vertex) when the pull queue cannot overflow and word ids fit 32 bits.
+static bool words_list_ok(const im_sketch* sk) {
+    return sk->buckets && sk->pull_safe && (uint64_t)sk->g->n * (uint64_t)((sk->J + 31) / 32) < (1ull << 32);
+}
+
 static void set_lcm(LevelArgs& a, const im_sketch* sk, int mode) {
     const bool in = mode != kCover;
     a.aff = sk->aff.as<uint32_t>();
-    // the affected-set search lists the words it makes nonzero (bucket mode)
-    const bool words = mode == kAffect && sk->buckets && sk->pull_safe;
+    // the affected-set search lists the words it makes nonzero (bucket mode;
+    // a word is listed as v * words + w in 32 bits)
+    const bool words = mode == kAffect && words_list_ok(sk);
     a.awl = words ? sk->awl.as<uint32_t>() : nullptr;
     a.awl_count = words ? sk->awlc.as<unsigned int>() : nullptr;
     a.nv = (mode == kCover && sk->incr) ? sk->nv.as<uint32_t>() : nullptr;
@@ -1024,7 +1031,7 @@ static im_status incremental_rebuild(im_sketch* sk) {
     // the pull queue: the third light queue, free between phases
     x.pq = sk->ql[2].as<QEntry>();
     x.pctr = sk->apctr.as<unsigned long long>();
-    x.words_list = sk->buckets && sk->pull_safe ? 1 : 0;
+    x.words_list = words_list_ok(sk) ? 1 : 0;
     x.awl = sk->awl.as<uint32_t>();
     x.awl_count = sk->awlc.as<unsigned int>();
     if (x.words_list) CK(c, cudaMemsetAsync(sk->awlc.p, 0, 4, st));
