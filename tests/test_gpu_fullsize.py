@@ -1,7 +1,8 @@
 """Parity at the full mid-size workload (R-MAT scale 20, WC, J=256, K=50) in
-the configuration bench.py times: seeds, scores and estimates against the
-oracle's stored run (tests/golden/make_golden.py), plus sampled registers
-(one oracle BFS each) and whole visited columns (oracle reach sets)."""
+the default schedule and in the one the autotuner picks (as bench.py does
+before timing): seeds, scores and estimates against the oracle's stored run
+(tests/golden/make_golden.py), plus sampled registers (one oracle BFS each)
+and whole visited columns (oracle reach sets)."""
 import hashlib
 import json
 import os
@@ -48,6 +49,25 @@ def test_mid_workload_selection_matches_oracle(setup):
     thr = O.thresholds(g, wl.model)
     for j in (0, 77, 255):
         assert np.array_equal(M[:, j] == 0xFF, O.reach_mark(g, thr, X[j], gold["seeds"]))
+
+
+def test_mid_workload_selection_in_the_autotuned_configuration(setup):
+    # the benchmark first lets the autotuner pick the schedule on this very
+    # workload; the selection it then times equals the oracle's as well
+    im, ctx, G, g, wl, gold = setup
+    from paper_2410_14047_gb300 import autotune
+    c2 = im.im_ctx_create(0)
+    G2 = im.im_graph_load(c2, g.rowptr, g.col, wl.model)
+
+    def step():
+        return im.im_select_seeds(G2, wl.K, wl.J, seed=wl.seed, rebuild_eps=wl.rebuild_eps)
+
+    rep = autotune.tune(c2, step, repeats=1)
+    assert im.im_ctx_get_tuning(c2) == rep["tuning"]
+    r = step()
+    assert r["seeds"].tolist() == gold["seeds"]
+    assert r["score"].tolist() == gold["score"]
+    np.testing.assert_allclose(r["est"], [float.fromhex(x) for x in gold["est"]], rtol=1e-12, atol=0)
 
 
 def test_mid_workload_build_sampled_registers(setup):
