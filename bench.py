@@ -465,7 +465,7 @@ def run_gpu(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     agg = {"alg_bytes_sweep": 0, "ms_propagate": 0.0, "sweep_launches": 0, "launches": 0,
            "builds": 0, "sweeps": 0, "ms_pick_kernels": 0.0, "ms_cover_kernels": 0.0,
-           "ms_fill_kernels": 0.0, "cover_levels": 0, "sweep_edges": 0}
+           "ms_fill_kernels": 0.0, "cover_levels": 0, "sweep_edges": 0, "sweep_bucket_entries": 0}
     deterministic = True
     ev0.record(stream)
     for _ in range(args.steps):
@@ -518,8 +518,11 @@ def run_gpu(args):
             "data": "synthetic (seeded R-MAT standing in for the paper's SNAP graphs)",
             "config": workload_config(wl, g, world),
             "time_to_k_seeds_s": tmax / args.steps,
-            "register_gteps": agg["sweep_edges"] * wl.J / (agg["ms_propagate"] / 1e3) / 1e9
-            if agg["ms_propagate"] else None,
+            # (edge, simulation) pairs the propagation covered: every simulation
+            # of an examined in-edge on vertex levels, the 16 of a chunk per list
+            # entry on bucket levels
+            "register_gteps": (agg["sweep_edges"] * wl.J + agg["sweep_bucket_entries"] * 16)
+            / (agg["ms_propagate"] / 1e3) / 1e9 if agg["ms_propagate"] else None,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": tr,
                          "kernel": "k_phase<%s,kPush> (persistent propagation phase, one launch per build)"
