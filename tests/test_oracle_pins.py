@@ -431,3 +431,87 @@ def test_score_equals_hash_sampled_spread():
     for k in range(K):
         s, _ = O.spread_hash(g, thr, r["seeds"][: k + 1], J, seed=77)
         assert s == round(r["score"][k] * J)
+
+
+# --- single-register and single-simulation checkers -----------------------------
+# orc_register_entry and orc_reach_mark check full-size GPU runs one register or
+# one simulation at a time; here they are pinned to networkx reachability on the
+# live subgraph of each simulation (Eq. hash_prob), not to the oracle's builds.
+
+def _pin_models(g):
+    rng = np.random.default_rng(g.n)
+    return [{"kind": "uniform", "p": 0.35}, {"kind": "wc"}, {"kind": "trivalency", "seed": 5},
+            {"kind": "explicit", "w": rng.uniform(0, 0.6, g.m).astype(np.float32)},
+            {"kind": "target", "w": rng.uniform(0, 0.6, g.n).astype(np.float32)}]
+
+
+@pytest.mark.parametrize("gi", [0, 1, 2])
+def test_register_entry_equals_reach_max_of_live_subgraph(gi):
+    # Sec. 2.3 / Alg. 2 fixpoint: M[u][j] = max rank over the vertices reachable
+    # from u along edges live in simulation j, avoiding visited vertices; a
+    # visited u reads 0xFF (Sec. 3.1)
+    g = _small_graphs()[gi]
+    rng = np.random.default_rng(40 + gi)
+    J = 16
+    X, salt = O.draw_sims(90 + gi, J)
+    R = _ranks(g.n, salt)
+    for model in _pin_models(g):
+        thr = O.thresholds(g, model)
+        vis = np.where(rng.random((g.n, J)) < 0.15, 0xFF, 0).astype(np.uint8)
+        for j in range(J):
+            D = _live_digraph(g, thr, X[j])
+            keep = [v for v in range(g.n) if vis[v, j] == 0]
+            sub = D.subgraph(keep)
+            for u in range(g.n):
+                if vis[u, j]:
+                    want = 0xFF
+                else:
+                    want = max(int(R[w, j]) for w in nx.descendants(sub, u) | {u})
+                got = O.register_entry(g, thr, X[j], salt[j], u, vis[:, j])
+                assert got == want, (model["kind"], j, u)
+            # without visited marks: reach over the whole live subgraph
+            for u in range(0, g.n, 7):
+                want = max(int(R[w, j]) for w in nx.descendants(D, u) | {u})
+                assert O.register_entry(g, thr, X[j], salt[j], u) == want
+
+
+@pytest.mark.parametrize("gi", [0, 1, 2])
+def test_reach_mark_equals_networkx_descendants(gi):
+    # Alg. 3 cascade: the vertices reachable from the seed set along edges live
+    # in simulation j, the seeds included
+    g = _small_graphs()[gi]
+    rng = np.random.default_rng(70 + gi)
+    J = 16
+    X, _ = O.draw_sims(5 + gi, J)
+    for model in _pin_models(g):
+        thr = O.thresholds(g, model)
+        for j in range(J):
+            D = _live_digraph(g, thr, X[j])
+            k = int(rng.integers(1, 4))
+            seeds = rng.integers(0, g.n, size=k).tolist() + [int(rng.integers(0, g.n))] * 2  # repeats
+            reach = set(seeds)
+            for s in seeds:
+                reach |= nx.descendants(D, s)
+            mark = O.reach_mark(g, thr, X[j], seeds)
+            assert set(np.nonzero(mark)[0].tolist()) == reach, (model["kind"], j)
+    assert not O.reach_mark(g, O.thresholds(g, {"kind": "wc"}), X[0], []).any()
+
+
+def test_thresholds_per_target_hand_worked():
+    # per-target model: every edge into v fires with w[v] (Sec. 2.1 with a
+    # per-vertex probability); fixed point floor(fp32(w) * 2^31)
+    g = W.from_edges(7, [(6, 0), (5, 0), (6, 1), (6, 2), (0, 3), (1, 3), (6, 4), (6, 5), (3, 5)])
+    w = np.array([0.01, 0.1, 0.5, 1.0, 0.0, 1.0 / 3.0, 0.9], np.float32)
+    thr = O.thresholds(g, {"kind": "target", "w": w})
+    by_target = {}
+    for e, v in enumerate(g.col.tolist()):
+        by_target.setdefault(v, set()).add(int(thr[e]))
+    # fp32(0.01) -> 21474836, fp32(0.1) -> 214748368, 0.5 -> 2^30, 1 -> 2^31,
+    # 0 -> 0, fp32(1/3) = 0.3333333432674408 -> 715827904
+    assert by_target == {0: {21474836}, 1: {214748368}, 2: {2**30}, 3: {2**31}, 4: {0},
+                         5: {715827904}}
+    # weighted cascade is the per-target case w[v] = fp32(1 / indeg(v))
+    h = W.rmat(9, 8, seed=4)
+    indeg = np.bincount(h.col, minlength=h.n)
+    wv = np.array([1.0 / d if d else 0.0 for d in indeg], np.float32)
+    assert (O.thresholds(h, {"kind": "target", "w": wv}) == O.thresholds(h, {"kind": "wc"})).all()
