@@ -1,17 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the sketch-based IM hot path (one K-seed selection per step).
 
-A step is one call of im_select_seeds on the mid-size workload: R-MAT scale
-20 (edge factor 16, a/b/c = 0.57/0.19/0.19, duplicates and self-loops
-removed), weighted-cascade IC, J = 256 simulations, K = 50 seeds, rebuild
-threshold e = 0.01 (the paper's Table 3 workload shape at Pokec /
-LiveJournal scale; synthetic because the SNAP graphs are not available).
-Covers every step of the method: draws, fill, propagation to the fixpoint,
-estimate + argmax, cover, count, rebuilds.
+A step is one call of im_select_seeds on the large workload: R-MAT scale 24
+(16.7M vertices, edge factor 16, a/b/c = 0.57/0.19/0.19, duplicates and
+self-loops removed, 263M edges), trivalency IC (p in {0.1, 0.01, 0.001} per
+edge by hash), J = 512 simulations (8.6 GB of registers), K = 50 seeds,
+rebuild threshold e = 0.01 (the paper's Table 3 setting at Sinaweibo scale;
+synthetic because the SNAP graphs are not available).  --workload rmat20 or
+er10k selects the mid-size or tiny workload.  Covers every step of the
+method: draws, fill, propagation to the fixpoint, estimate + argmax, cover,
+count, rebuilds.
 
 Metric: K-seed selections per second (the inverse of time-to-K-seeds),
 whole job: with --gpus N every rank runs an independent replica (the path
-does not shard on one GPU), value = N * steps / max-over-ranks time.
+does not shard on one GPU), value = N * steps / max-over-ranks time.  On one
+GPU the line also carries the batched and served forms (nested "forms" key;
+--no-forms leaves them out) and the oracle on the host cores (cpu_baseline).
 
 --impl reference times the CPU oracle on the host cores instead.
 """
@@ -33,6 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "time-to-K-seeds (K-seed selections/s)"
 UNIT = "selections/s"
 CPU_SAMPLE_J = 16
+ORACLE_CALIBRATION = os.path.join(ROOT, "profiles", "oracle_calibration.json")
 
 
 def parse():
@@ -41,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="rmat20")
+    ap.add_argument("--workload", default="rmat24")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--mode", default="select", choices=["select", "build", "fillrate"],
@@ -58,7 +63,14 @@ def parse():
     ap.add_argument("--slots", type=int, default=8,
                     help="concurrent queries of the server (--workload served)")
     ap.add_argument("--quick", action="store_true",
-                    help="profiling runs: no clock sampling, end-to-end pass or CPU baseline")
+                    help="profiling runs: no clock sampling, end-to-end pass, CPU baseline or forms")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="leave the batched and served forms out of the plain benchmark line")
+    ap.add_argument("--served-carried-rate", type=float, default=10.0,
+                    help="arrival rate of the served run below capacity, queries/s")
+    ap.add_argument("--calibrate-oracle", action="store_true",
+                    help="time one full oracle selection and the oracle sample on this host "
+                         "(the factor that scales the sample to a selection)")
     return ap.parse_args()
 
 
@@ -85,10 +97,33 @@ def replicas_value(steps: int, world: int, tmax: float) -> float:
     return world * steps / tmax
 
 
+def alg_bytes_terms(st: dict, J: int, model_kind: str) -> dict:
+    """Algorithmic bytes of the propagation launches from their device counts,
+    by the per-unit figures of the propagation sweep's byte count: per
+    frontier vertex 8 (row bounds) + J (its register row), per examined in-edge
+    4 (endpoint) + t (a stored per-edge threshold: explicit weights only; the
+    other models' thresholds are per target or recomputed), per changed vertex
+    J (its row written), per (edge, 32-simulation chunk) with a live,
+    non-visited simulation 32 (the neighbour's 32 register bytes).  Levels on
+    (vertex, 16-simulation chunk) buckets count the same at 16-simulation
+    granularity: per queued bucket 8 + 16, per list entry 4 + t + 16, per
+    changed bucket 16.  Hubs pushed by per-simulation hash search are not
+    counted (their edges are searched, not read)."""
+    t = 4 if model_kind == "explicit" else 0
+    per_unit = {"frontier_vertices": 8 + J, "in_edges": 4 + t, "changed_vertices": J, "live_32sim_chunks": 32,
+                "frontier_buckets": 8 + 16, "bucket_entries": 4 + t + 16, "changed_buckets": 16}
+    units = {"frontier_vertices": st["sweep_vertices"], "in_edges": st["sweep_edges"],
+             "changed_vertices": st["sweep_changed"], "live_32sim_chunks": st["sweep_live32"],
+             "frontier_buckets": st["sweep_buckets"], "bucket_entries": st["sweep_bucket_entries"],
+             "changed_buckets": st["sweep_changed_buckets"]}
+    return {"bytes": sum(units[k] * per_unit[k] for k in units), "units": units, "per_unit": per_unit}
+
+
 def workload_config(wl, g, world):
     return {"workload": wl.name, "n": g.n, "m": g.m, "J": wl.J, "K": wl.K,
             "model": wl.model["kind"], "rebuild_eps": wl.rebuild_eps, "seed": wl.seed,
-            "l2": "inputs larger than L2 (n*J register bytes > 129 MB)",
+            "l2": ("inputs larger than L2 (n*J register bytes > 129 MB), no flush" if g.n * wl.J > 129e6
+                   else "register matrix fits in L2 (tiny workload), no flush"),
             "replicas": world, "parallelism": f"replicas x{world}"}
 
 
@@ -170,19 +205,80 @@ def ncu_traffic(workload):
         return None
 
 
-def cpu_baseline(wl, g):
-    """The oracle, as it stands, on a bounded sample: J=16 of the workload's J
-    simulations (all K seeds, same graph and model); time scaled by J/16."""
+def oracle_sample(wl, g, thr) -> float:
+    """The bounded oracle sample, in seconds: the oracle's first sketch build
+    (Alg. 1 fill + Alg. 2 fixpoint by reverse search, its graph set-up
+    included) of CPU_SAMPLE_J of the workload's J simulations."""
+    import oracle as O
+    X, salt = O.draw_sims(wl.seed, CPU_SAMPLE_J)
+    t = time.perf_counter()
+    O.build_reverse(g, thr, CPU_SAMPLE_J, X, salt)
+    return time.perf_counter() - t
+
+
+def host_key() -> str:
+    import platform
+    return f"{platform.machine()}-{os.cpu_count()}cpu"
+
+
+def oracle_factor(workload: str):
+    """Seconds of one full oracle selection per second of the sample, measured
+    on this kind of host by --calibrate-oracle; (factor, source)."""
+    try:
+        cal = json.load(open(ORACLE_CALIBRATION))
+        e = cal[workload][host_key()]
+        return e["full_s"] / e["sample_s"], (f"one full oracle selection measured {e['full_s']:.1f} s against "
+                                              f"{e['sample_s']:.1f} s for the sample on {host_key()} "
+                                              f"({e.get('when', '?')})")
+    except Exception:
+        return None, "no calibration for this host: value not scaled (the sample's own rate)"
+
+
+def oracle_rate(wl, args_workload, t_sample: float):
+    """Selections/s of the oracle from a sample time: the sample scaled by the
+    calibrated factor, or (no calibration) the sample's own rate, a bound the
+    full selection cannot beat."""
+    f, src = oracle_factor(args_workload)
+    if f is None:
+        return 1.0 / t_sample, None, src
+    return 1.0 / (t_sample * f), t_sample * f, src
+
+
+def cpu_baseline(wl, g, args_workload):
+    """The oracle, as it stands, on the bounded sample, scaled to selections/s
+    of the whole workload by the calibrated factor."""
     import oracle as O
     thr = O.thresholds(g, wl.model)
+    dt = oracle_sample(wl, g, thr)
+    value, full_s, src = oracle_rate(wl, args_workload, dt)
+    return {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": (f"oracle sketch build (fill + fixpoint, graph set-up included) of {CPU_SAMPLE_J} of the "
+                       f"{wl.J} simulations on the same graph and model, measured {dt:.2f} s"),
+            "extrapolated": full_s is not None,
+            "seconds_per_selection": full_s, "scale_source": src}
+
+
+def run_calibration(args):
+    """One full oracle selection and the sample on this host (minutes to
+    hours on the large workload): the factor oracle_factor uses."""
+    import oracle as O
+    import workloads as W
+    wl = W.workload(args.workload)
+    g = wl.graph()
+    thr = O.thresholds(g, wl.model)
+    t_s = oracle_sample(wl, g, thr)
     t = time.perf_counter()
-    O.select_seeds(g, thr, CPU_SAMPLE_J, wl.K, wl.seed, wl.rebuild_eps, "reverse")
-    dt = time.perf_counter() - t
-    scaled = dt * wl.J / CPU_SAMPLE_J
-    return {"value": 1.0 / scaled, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": (f"oracle select_seeds on the same graph with J={CPU_SAMPLE_J} of {wl.J} "
-                       f"simulations, K={wl.K}; measured {dt:.2f} s, scaled x{wl.J // CPU_SAMPLE_J} "
-                       f"to {scaled:.1f} s per selection")}
+    r = O.select_seeds(g, thr, wl.J, wl.K, wl.seed, wl.rebuild_eps, "reverse")
+    t_full = time.perf_counter() - t
+    golden = None
+    gp = os.path.join(ROOT, "tests", "golden", f"select_{args.workload}.json")
+    if os.path.exists(gp):
+        golden = json.load(open(gp))["seeds"] == r["seeds"].tolist()
+    print(json.dumps({"mode": "calibrate-oracle", "workload": args.workload, "host": host_key(),
+                      "threads": O.num_threads(), "sample_s": t_s, "full_s": t_full,
+                      "rebuilds": int(r.get("rebuilds", -1)), "seeds_match_golden": golden,
+                      "when": time.strftime("%Y-%m-%d")}), flush=True)
+    return 0
 
 
 def run_reference(args):
@@ -195,31 +291,29 @@ def run_reference(args):
     g = wl.graph()
     thr = O.thresholds(g, wl.model)
     for _ in range(args.warmup):
-        O.select_seeds(g, thr, CPU_SAMPLE_J, wl.K, wl.seed, wl.rebuild_eps, "reverse")
-    times = []
-    for _ in range(args.steps):
-        t = time.perf_counter()
-        O.select_seeds(g, thr, CPU_SAMPLE_J, wl.K, wl.seed, wl.rebuild_eps, "reverse")
-        times.append((time.perf_counter() - t) * wl.J / CPU_SAMPLE_J)
+        oracle_sample(wl, g, thr)
+    times = [oracle_sample(wl, g, thr) for _ in range(args.steps)]
     per = sum(times) / len(times)
-    value = 1.0 / per
-    sample = (f"oracle select_seeds with J={CPU_SAMPLE_J} of {wl.J} simulations per step, "
-              f"K={wl.K}; step times scaled x{wl.J // CPU_SAMPLE_J}")
+    value, full_s, src = oracle_rate(wl, args.workload, per)
+    sample = (f"each step: the oracle's sketch build (fill + fixpoint, graph set-up included) of "
+              f"{CPU_SAMPLE_J} of the {wl.J} simulations on the same graph and model")
     out = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
            "data": "synthetic", "config": workload_config(wl, g, 1),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-                            "sample": sample},
+                            "sample": sample, "extrapolated": full_s is not None,
+                            "seconds_per_selection": full_s, "scale_source": src},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
 
 
-def run_batched(args):
+def batched_form(args):
     """Batched form: many uneven Chung-Lu graphs selected in one batched run
     (rounds fused across graphs, schedule from the autotuner) against the
-    plain path (one im_select_seeds per graph, sequentially)."""
+    plain path (one im_select_seeds per graph, sequentially, on resident
+    graphs).  Returns the result dict."""
     import numpy as np
     import torch
 
@@ -243,16 +337,17 @@ def run_batched(args):
     tune = autotune.tune(ctx, lambda: im.im_batch_select_seeds(B, J, K, seed=2410),
                          space={"buckets": [0, 2], "light_batches": [4, 16]}, repeats=1)
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    steps = max(args.steps, 1)
+    for _ in range(max(args.warmup, 1)):
         res = im.im_batch_select_seeds(B, J, K, seed=2410)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         res = im.im_batch_select_seeds(B, J, K, seed=2410)
     ev1.record(stream)
     ev1.synchronize()
-    batched_s = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    batched_s = ev0.elapsed_time(ev1) / 1e3 / steps
     bstats = im.im_last_stats(ctx)
     B.free()
     # plain path: one query at a time on resident graphs
@@ -266,64 +361,86 @@ def run_batched(args):
         finish.append(time.perf_counter() - t0)
         identical &= r["seeds"].tolist() == res[i]["seeds"].tolist()
     plain_s = time.perf_counter() - t0
+    for Gs in solo:
+        Gs.free()
     lat = np.array(finish)
-    out = {"metric": "batched K-seed selections/s", "value": G / batched_s, "unit": "selections/s",
-           "impl": "gb300-batched", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": batched_s * 1e3, "higher_is_better": True, "dtype": "u8",
-           "data": "synthetic (seeded Chung-Lu graphs)",
-           "config": {"workload": f"batched: {G} Chung-Lu graphs gamma 2.1, n U[1k,200k], avg deg U[8,32], "
-                                  f"K U[5,50], J {{64,128}}, p U[0.005,0.05]",
-                      "graphs": G, "sum_n": int(sum(g.n for g in graphs)), "sum_m": int(sum(g.m for g in graphs)),
-                      "sum_K": int(sum(K))},
-           "plain": {"value": G / plain_s, "unit": "selections/s", "total_s": plain_s,
-                     "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99))},
-           "batched_latency": {"p50_s": batched_s, "p99_s": batched_s,
-                               "note": "every graph of a batch completes with the batch"},
-           "speedup_vs_plain": plain_s / batched_s,
-           "identical_to_plain": bool(identical),
-           "autotune": {"tuning": tune["tuning"], "trials": len(tune["trials"])},
-           "batched_kernel_ms": {k: bstats[k] for k in ("ms_propagate", "ms_cover_kernels", "ms_pick_kernels",
-                                                         "ms_fill_kernels")},
-           "generation_s": gen_s, "batch_load_s": load_s}
+    return {"metric": "batched K-seed selections/s", "value": G / batched_s, "unit": "selections/s",
+            "impl": "gb300-batched", "n_gpus": 1, "steps": steps, "ms_per_step": batched_s * 1e3,
+            "higher_is_better": True, "dtype": "u8", "data": "synthetic (seeded Chung-Lu graphs)",
+            "config": {"workload": f"batched: {G} Chung-Lu graphs gamma 2.1, n U[1k,200k], avg deg U[8,32], "
+                                   f"K U[5,50], J {{64,128}}, p U[0.005,0.05]",
+                       "graphs": G, "sum_n": int(sum(g.n for g in graphs)), "sum_m": int(sum(g.m for g in graphs)),
+                       "sum_K": int(sum(K))},
+            "plain": {"value": G / plain_s, "unit": "selections/s", "total_s": plain_s,
+                      "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99))},
+            "batched_latency": {"p50_s": batched_s, "p99_s": batched_s,
+                                "note": "every graph of a batch completes with the batch, so p50 = p99 = "
+                                        "the batch time; the plain path's latencies count from the start "
+                                        "of the sequence"},
+            "speedup_vs_plain": plain_s / batched_s,
+            "identical_to_plain": bool(identical),
+            "autotune": {"tuning": tune["tuning"], "trials": len(tune["trials"])},
+            "batched_kernel_ms": {k: bstats[k] for k in ("ms_propagate", "ms_cover_kernels", "ms_pick_kernels",
+                                                          "ms_fill_kernels")},
+            "generation_s": gen_s, "batch_load_s": load_s}
+
+
+def run_batched(args):
+    out = batched_form(args)
+    out["warmup"] = args.warmup
     print(json.dumps(out), flush=True)
     return 0
 
 
-def run_served(args):
-    """Served form: Poisson arrivals of queries against 16 resident R-MAT
-    graphs, run by the query server (concurrent slots, HBM-budget admission)
-    and, on the same arrival sequence, by the plain path one query at a time.
-    Latency = completion - arrival; queries/s = queries / (last completion -
-    first arrival)."""
+class ServedSetup:
+    """16 resident R-MAT graphs (scales 14-22) loaded once for served runs."""
+
+    def __init__(self, local: int):
+        import torch
+
+        import paper_2410_14047_gb300 as im
+        import workloads as W
+        self.local = local
+        t0 = time.perf_counter()
+        self.graphs = W.served_graphs(seed=2410)
+        self.gen_s = time.perf_counter() - t0
+        self.ctx = im.im_ctx_create(local)
+        self.loaded = [im.im_graph_load(self.ctx, g.rowptr, g.col, {"kind": "wc"}) for g in self.graphs]
+        torch.cuda.synchronize()
+        self.warm = False
+
+
+def served_run(st: ServedSetup, queries: int, rate: float, slots: int, warmup: int, quick: bool):
+    """Poisson arrivals of queries against the resident graphs, run by the
+    query server (concurrent slots, HBM-budget admission) and, on the same
+    arrival sequence, by the plain path one query at a time.  Latency =
+    completion - arrival; queries/s = queries / (last completion - first
+    arrival).  Returns the result dict."""
     import numpy as np
     import torch
 
     import paper_2410_14047_gb300 as im
     import workloads as W
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    t0 = time.perf_counter()
-    graphs = W.served_graphs(seed=2410)
-    gen_s = time.perf_counter() - t0
-    ctx = im.im_ctx_create(local)
-    loaded = [im.im_graph_load(ctx, g.rowptr, g.col, {"kind": "wc"}) for g in graphs]
-    torch.cuda.synchronize()
-    qs = W.served_queries(args.queries, rate=args.rate, n_graphs=len(graphs), seed=2410)
+    graphs, loaded, local = st.graphs, st.loaded, st.local
+    qs = W.served_queries(queries, rate=rate, n_graphs=len(graphs), seed=2410)
     budget = 150 * 10**9
-    srv = im.Server(local, slots=args.slots, hbm_budget_bytes=budget, max_bypass=2 * args.slots)
+    srv = im.Server(local, slots=slots, hbm_budget_bytes=budget, max_bypass=2 * slots)
     for G in loaded:
         srv.add_graph(G)
-    warm = W.served_queries(max(args.warmup, 1) * 4, rate=1e6, n_graphs=len(graphs), seed=99)
-    for q in warm:  # module load, pool growth, first launches of each path
-        srv.wait(srv.submit(**{k: q[k] for k in ("graph", "K", "J", "model", "seed", "rebuild_eps")}))
-        im.im_select_seeds(loaded[q["graph"]], q["K"], q["J"], model=q["model"], seed=q["seed"])
-    torch.cuda.synchronize()
 
     def args_of(q):
         return {k: q[k] for k in ("graph", "K", "J", "model", "seed", "rebuild_eps")}
 
-    clocks = None if args.quick else ClockSampler(local)
+    if not st.warm:
+        warm = W.served_queries(max(warmup, 1) * 4, rate=1e6, n_graphs=len(graphs), seed=99)
+        for q in warm:  # module load, pool growth, first launches of each path
+            srv.wait(srv.submit(**args_of(q)))
+            im.im_select_seeds(loaded[q["graph"]], q["K"], q["J"], model=q["model"], seed=q["seed"])
+        torch.cuda.synchronize()
+        st.warm = True
+
+    clocks = None if quick else ClockSampler(local)
     if clocks:
         clocks.start()
     # served: submit at the arrival times, collect completions
@@ -340,8 +457,10 @@ def run_served(args):
     served = [srv.wait(t) for t in tickets]
     sstats = srv.stats()
     s_done = np.array([r["t_done_ms"] for r in served])
+    s_start = np.array([r["t_start_ms"] for r in served])
     s_arr = np.array([t_base + q["arrival_s"] * 1e3 for q in qs])
     s_lat = (s_done - s_arr) / 1e3
+    s_wait = (s_start - s_arr) / 1e3
     served_s = (s_done.max() - s_arr.min()) / 1e3
     srv.close()
     # plain: one query at a time in arrival order on the same resident graphs
@@ -352,18 +471,15 @@ def run_served(args):
         due = t_base + q["arrival_s"] * 1e3
         while srv.clock_ms() < due:
             time.sleep(0.001)
+        p_start.append(max(due, srv.clock_ms()))
         plain_res.append(im.im_select_seeds(loaded[q["graph"]], q["K"], q["J"], model=q["model"],
                                             seed=q["seed"], rebuild_eps=q["rebuild_eps"]))
         p_done.append(srv.clock_ms())
-        p_start.append(max(due, p_done[-2] if len(p_done) > 1 else due))
     p_done = np.array(p_done)
     p_service = p_done - np.array(p_start)
-    by_class = {}
-    for q, ms in zip(qs, p_service):
-        key = f"scale{graphs[q['graph']].n.bit_length() - 1}_J{q['J']}_{q['model']['kind']}"
-        by_class.setdefault(key, []).append(float(ms))
     p_arr = np.array([t_base + q["arrival_s"] * 1e3 for q in qs])
     p_lat = (p_done - p_arr) / 1e3
+    p_wait = (np.array(p_start) - p_arr) / 1e3
     plain_s = (p_done.max() - p_arr.min()) / 1e3
     clk = clocks.stop() if clocks else None
     identical = all(r["status"] == 0 and r["seeds"].tolist() == pr["seeds"].tolist()
@@ -373,24 +489,50 @@ def run_served(args):
            "unit": "queries/s", "impl": "gb300-served", "n_gpus": 1, "higher_is_better": True,
            "dtype": "u8", "data": "synthetic (seeded R-MAT graphs, Poisson arrivals)",
            "config": {"workload": f"served: 16 resident R-MAT graphs scales 14-22 ef 16, {N} queries, "
-                                  f"Poisson {args.rate:g}/s, K {{10,25,50}}, J {{64,256,1024}}, "
+                                  f"Poisson {rate:g}/s, K {{10,25,50}}, J {{64,256,1024}}, "
                                   "model p=0.01 or WC, 150 GB budget",
-                      "queries": N, "rate": args.rate, "slots": args.slots, "budget_bytes": budget,
+                      "queries": N, "rate": rate, "slots": slots, "budget_bytes": budget,
                       "sum_n": int(sum(g.n for g in graphs)), "sum_m": int(sum(g.m for g in graphs))},
            "served": {"value": N / served_s, "total_s": served_s,
                       "p50_s": float(np.percentile(s_lat, 50)), "p99_s": float(np.percentile(s_lat, 99)),
+                      "queue_wait_p50_s": float(np.percentile(s_wait, 50)),
                       "running_peak": sstats["running_peak"], "reserved_peak_bytes": sstats["reserved_peak"],
                       "graph_bytes": sstats["graph_bytes"], "bypassed": sstats["bypassed"]},
            "plain": {"value": N / plain_s, "unit": "queries/s", "total_s": plain_s,
-                     "p50_s": float(np.percentile(p_lat, 50)), "p99_s": float(np.percentile(p_lat, 99))},
+                     "p50_s": float(np.percentile(p_lat, 50)), "p99_s": float(np.percentile(p_lat, 99)),
+                     "queue_wait_p50_s": float(np.percentile(p_wait, 50)),
+                     "service_p50_ms": float(np.percentile(p_service, 50))},
            "speedup_vs_plain": plain_s / served_s,
+           "p99_vs_plain": float(np.percentile(p_lat, 99)) / float(np.percentile(s_lat, 99)),
            "identical_to_plain": bool(identical),
-           "plain_service_ms": {k: [len(v), round(float(np.mean(v)), 2)] for k, v in sorted(by_class.items())},
-           "generation_s": gen_s}
+           "generation_s": st.gen_s}
     if clk:
         out["clocks"] = clk
-    print(json.dumps(out), flush=True)
+    return out
+
+
+def run_served(args):
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    st = ServedSetup(local)
+    print(json.dumps(served_run(st, args.queries, args.rate, args.slots, args.warmup, args.quick)), flush=True)
     return 0
+
+
+def forms(args):
+    """The batched and served forms for the plain benchmark line: the batch
+    against plain selections, and the server at an arrival rate both paths can
+    carry (latency = service time and overlap) and at the overload rate of the
+    served configuration (latency = queueing)."""
+    import torch
+    out = {"batched": batched_form(args)}
+    torch.cuda.empty_cache()
+    st = ServedSetup(dist_env()[2])
+    out["served_carried"] = served_run(st, max(args.queries // 2, 50), args.served_carried_rate, args.slots,
+                                       args.warmup, True)
+    out["served_overload"] = served_run(st, args.queries, args.rate, args.slots, args.warmup, True)
+    return out
 
 
 def run_gpu(args):
@@ -465,7 +607,9 @@ def run_gpu(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     agg = {"alg_bytes_sweep": 0, "ms_propagate": 0.0, "sweep_launches": 0, "launches": 0,
            "builds": 0, "sweeps": 0, "ms_pick_kernels": 0.0, "ms_cover_kernels": 0.0,
-           "ms_fill_kernels": 0.0, "cover_levels": 0, "sweep_edges": 0, "sweep_bucket_entries": 0}
+           "ms_fill_kernels": 0.0, "cover_levels": 0, "sweep_edges": 0, "sweep_bucket_entries": 0,
+           "sweep_vertices": 0, "sweep_changed": 0, "sweep_live32": 0, "sweep_buckets": 0,
+           "sweep_changed_buckets": 0, "sweep_heavy": 0, "sweep_heavy_sims": 0}
     deterministic = True
     ev0.record(stream)
     for _ in range(args.steps):
@@ -508,8 +652,9 @@ def run_gpu(args):
             golden = json.load(open(gp))["seeds"] == ref_seeds
         peaks = measured_peaks()
         peak = peaks["hbm_gbs"] if peaks else 6800.0
-        achieved = (agg["alg_bytes_sweep"] / 1e9) / (agg["ms_propagate"] / 1e3) if agg["ms_propagate"] else 0.0
-        per_launch_bytes = agg["alg_bytes_sweep"] / max(agg["sweep_launches"], 1)
+        launches = max(agg["sweep_launches"], 1)
+        terms = alg_bytes_terms(agg, wl.J, wl.model["kind"])
+        achieved = (terms["bytes"] / 1e9) / (agg["ms_propagate"] / 1e3) if agg["ms_propagate"] else 0.0
         tr = ncu_traffic(args.workload)
         out = {
             "metric": METRIC, "value": replicas_value(args.steps, world, tmax), "unit": UNIT, "n_gpus": world,
@@ -528,9 +673,14 @@ def run_gpu(args):
                          "kernel": "k_phase<%s,kPush> (persistent propagation phase, one launch per build)"
                                    % {"wc": "kWC", "uniform": "kUniform", "trivalency": "kTrivalency",
                                       "explicit": "kExplicit"}[wl.model["kind"]],
-                         "alg_bytes_per_launch": per_launch_bytes,
-                         "avg_launch_ms": agg["ms_propagate"] / max(agg["sweep_launches"], 1),
-                         "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
+                         "alg_bytes_per_launch": terms["bytes"] / launches,
+                         "avg_launch_ms": agg["ms_propagate"] / launches,
+                         "launches_per_step": agg["sweep_launches"] / args.steps,
+                         # the counts behind alg_bytes_per_launch (per launch)
+                         "units_per_launch": {k: v / launches for k, v in terms["units"].items()},
+                         "bytes_per_unit": terms["per_unit"],
+                         "alg_bytes_model_per_launch": agg["alg_bytes_sweep"] / launches,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback"},
             "phase_ms_per_step": {k: agg[k] / args.steps for k in
                                   ("ms_propagate", "ms_pick_kernels", "ms_cover_kernels", "ms_fill_kernels")},
             "counts_per_step": {k: agg[k] / args.steps for k in
@@ -547,7 +697,12 @@ def run_gpu(args):
                        ("--tuning" if args.tuning else "defaults")},
         }
         if world == 1 and not args.no_cpu_baseline and not args.quick:
-            out["cpu_baseline"] = cpu_baseline(wl, g)
+            out["cpu_baseline"] = cpu_baseline(wl, g, args.workload)
+        if world == 1 and not args.no_forms and not args.quick:
+            del G, ctx
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+            out["forms"] = forms(args)
         print(json.dumps(out), flush=True)
     if dist:
         dist.barrier()
@@ -557,6 +712,8 @@ def run_gpu(args):
 
 def main():
     args = parse()
+    if args.calibrate_oracle:
+        return run_calibration(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":

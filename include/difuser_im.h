@@ -104,7 +104,8 @@ typedef struct {
     uint64_t sweep_edges;     /* in-edges examined by all sweeps */
     uint64_t sweep_chunks;    /* 16-simulation chunks with >= 1 live, non-visited source register */
     uint64_t sweep_cas;       /* 4-register words written by atomic CAS (improvements) */
-    uint64_t sweep_changed;   /* vertices enqueued as changed */
+    uint64_t sweep_changed;   /* vertices whose registers a propagation level changed (vertex-format
+                                 levels: the queued vertices of every level after the first) */
     uint64_t cover_edges;     /* out-edges examined by cover levels */
     uint64_t cover_chunks;    /* 16-simulation chunks examined by cover levels */
     uint64_t visited;         /* registers visited at the end (Count(M,-1)) */
@@ -122,6 +123,11 @@ typedef struct {
     uint64_t affected;        /* registers recomputed by incremental rebuilds */
     uint64_t pull_buckets;    /* out-buckets queued by the pulls of incremental rebuilds */
     uint64_t pull_entries;    /* out-bucket entries walked by those pulls */
+    uint64_t sweep_changed_buckets; /* (vertex, 16-simulation chunk) buckets whose registers a
+                                 propagation level changed (bucket-format levels) */
+    uint64_t sweep_live32;    /* (in-edge, 32-simulation chunk) pairs of vertex-format propagation
+                                 levels with a simulation where the edge is live, the source
+                                 changed and its register is not visited */
 } im_stats;
 
 /* Schedule knobs of the frontier kernels (chosen by the autotuner; results
@@ -199,6 +205,21 @@ IM_API im_status im_ctx_set_timing(im_ctx* ctx, int enable);
 /* Sets (NULL = defaults {256, 4, 0, 2, 1, 0, 1, 2, 1, 8}) or reads the schedule knobs. */
 IM_API im_status im_ctx_set_tuning(im_ctx* ctx, const im_tuning* tuning);
 IM_API im_status im_ctx_get_tuning(const im_ctx* ctx, im_tuning* tuning);
+/* Bounds of the waits inside the device code, so that a loop that should end
+ * but does not returns IM_E_TIMEOUT instead of holding the GPU:
+ * barrier_wait_ns bounds every wait of a block at the grid barrier between
+ * two levels of a phase (all levels of a build or a cover run in one
+ * cooperative launch); a block that waits longer raises an abort word, every
+ * block leaves the launch at its next barrier, and the call returns
+ * IM_E_TIMEOUT (0: a block that has to wait at all gives up at once).
+ * max_levels bounds the levels of one phase (propagation to the fixpoint,
+ * one cover, one affected-set search): a frontier still non-empty after
+ * max_levels levels ends the phase with IM_E_TIMEOUT.  Defaults: 2 s and
+ * 16382 levels (the most a phase can record).  After IM_E_TIMEOUT the
+ * context stays usable; the sketch of the failed call is released (or, for
+ * step-level calls, must be rebuilt).  Errors: IM_E_INVAL (max_levels outside
+ * [1, 16382]). */
+IM_API im_status im_ctx_set_limits(im_ctx* ctx, uint64_t barrier_wait_ns, int32_t max_levels);
 /* enable != 0: also keep one im_trace_rec per frontier level (implies timing):
  * its duration comes from CUDA events around the level's launch, or, when a
  * phase runs all its levels in one launch, from the device's global timer
@@ -220,7 +241,8 @@ IM_API int64_t im_last_trace(const im_ctx* ctx, im_trace_rec* out, int64_t cap);
 IM_API im_status im_graph_load(im_ctx* ctx, int32_t n, int64_t m, const int32_t* rowptr,
                         const int32_t* col, const im_model* model, im_graph** out);
 IM_API void im_graph_free(im_graph* g);
-/* Device pointers of the loaded out-CSR (for callers that gather on device). */
+/* Size of a loaded graph: *n vertices, *m edges (either pointer may be NULL).
+ * Errors: IM_E_INVAL (g NULL). */
 IM_API im_status im_graph_info(const im_graph* g, int32_t* n, int64_t* m);
 
 /* ---- sketches (the step-level interface of Alg. 4) ---------------------- */
@@ -302,10 +324,14 @@ IM_API im_status im_batch_select_seeds(im_batch* b, const int32_t* J, const int3
  * stall the device).  Same result as im_sketch_pick on the same registers:
  * the vertex s not marked in `picked` with the smallest S_s (largest
  * estimate), lowest id on ties; its bit in `picked` is set.
- *   M       device, n*J register bytes (row-major, as im_sketch_registers)
- *   picked  device, ceil(n/32) uint32 words: bit v set = v excluded; in/out
- *   s_out   device int32: the pick, -1 if every vertex is excluded
- *   S_out   device uint64: S_s;  est_out: device double, J*2^32/(phi*S_s)
+ *   M       device, n*J register bytes (row-major, as im_sketch_registers),
+ *           16-byte aligned
+ *   picked  device, ceil(n/32) uint32 words (4-byte aligned): bit v set =
+ *           v excluded; in/out
+ *   s_out   device int32 (4-byte aligned): the pick, -1 if every vertex is
+ *           excluded
+ *   S_out   device uint64 (8-byte aligned): S_s;  est_out: device double
+ *           (8-byte aligned), J*2^32/(phi*S_s)
  * Work runs on `cuda_stream` (NULL = legacy default stream); results are
  * ready when the stream reaches them.  Scratch lives in one static device
  * array (at most 1216 blocks of partials, about 15 KB, held by every GPU that
@@ -313,8 +339,9 @@ IM_API im_status im_batch_select_seeds(im_batch* b, const int32_t* J, const int3
  * the GPU race and must be serialised by the caller.  The first call on each
  * device looks up the array's address (cudaGetSymbolAddress); make that first
  * call before any stream capture.  Calls no cudaMalloc/cudaFree.
- * Errors: IM_E_INVAL (NULL pointer, unsupported J), IM_E_RANGE (n outside
- * [1, 2^26)), IM_E_CUDA. */
+ * Errors (all found on the host, before any launch): IM_E_INVAL (NULL
+ * pointer, a buffer below its alignment, unsupported J), IM_E_RANGE (n
+ * outside [1, 2^26)), IM_E_CUDA. */
 IM_API im_status im_argmax_noalloc(const uint8_t* M, int32_t n, int32_t J, uint32_t* picked,
                                    void* cuda_stream, int32_t* s_out, uint64_t* S_out,
                                    double* est_out);

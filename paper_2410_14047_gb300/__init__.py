@@ -17,6 +17,8 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_libdifuser_im.so")
+# the bounds-checked test variant of the same sources (see _build.py)
+BOUNDS_LIB_PATH = os.path.join(HERE, "_libdifuser_im_bounds.so")
 
 MODEL_KINDS = {"uniform": 0, "wc": 1, "trivalency": 2, "explicit": 3, "target": 4}
 STATUS = {0: "IM_OK", -1: "IM_E_INVAL", -2: "IM_E_RANGE", -3: "IM_E_NOMEM", -4: "IM_E_CUDA",
@@ -26,6 +28,7 @@ STATUS = {0: "IM_OK", -1: "IM_E_INVAL", -2: "IM_E_RANGE", -3: "IM_E_NOMEM", -4: 
 EXPORTS = ["im_ctx_create", "im_ctx_destroy", "im_ctx_bytes_in_use", "im_ctx_bytes_peak",
            "im_last_error", "im_status_str", "im_last_stats", "im_ctx_set_timing",
            "im_ctx_set_trace", "im_last_trace", "im_ctx_set_tuning", "im_ctx_get_tuning",
+           "im_ctx_set_limits",
            "im_graph_load", "im_graph_free",
            "im_graph_info", "im_sketch_build", "im_sketch_free", "im_sketch_registers",
            "im_sketch_set_registers", "im_sketch_sims", "im_sketch_sums", "im_sketch_pick",
@@ -67,7 +70,8 @@ class im_stats(ctypes.Structure):
                                                "sweep_heavy", "sweep_heavy_sims", "sweep_batches",
                                                "sweep_dealt", "sweep_edges_live", "sweep_buckets",
                                                "sweep_bucket_entries", "affected",
-                                               "pull_buckets", "pull_entries")]
+                                               "pull_buckets", "pull_entries",
+                                               "sweep_changed_buckets", "sweep_live32")]
 
 
 class im_tuning(ctypes.Structure):
@@ -106,14 +110,14 @@ class im_server_stats(ctypes.Structure):
                [(k, ctypes.c_uint64) for k in ("budget", "graph_bytes", "reserved", "reserved_peak")]
 
 
-_lib = None
+_libs = {}
 
 
 def load_library(path: str = LIB_PATH):
     """Load the compiled library and declare the C signatures."""
-    global _lib
-    if _lib is not None:
-        return _lib
+    path = os.path.abspath(path)
+    if path in _libs:
+        return _libs[path]
     if not os.path.exists(path):
         raise IMError(-4, f"CUDA library not built ({path}); run paper_2410_14047_gb300._build.build()")
     L = ctypes.CDLL(path)
@@ -132,6 +136,7 @@ def load_library(path: str = LIB_PATH):
         "im_last_trace": (i64, [vp, P(im_trace_rec), i64]),
         "im_ctx_set_tuning": (ctypes.c_int, [vp, P(im_tuning)]),
         "im_ctx_get_tuning": (ctypes.c_int, [vp, P(im_tuning)]),
+        "im_ctx_set_limits": (ctypes.c_int, [vp, u64, i32]),
         "im_graph_load": (ctypes.c_int, [vp, i32, i64, P(i32), P(i32), P(im_model), P(vp)]),
         "im_graph_free": (None, [vp]),
         "im_graph_info": (ctypes.c_int, [vp, P(i32), P(i64)]),
@@ -166,7 +171,7 @@ def load_library(path: str = LIB_PATH):
         f = getattr(L, name)
         f.restype = res
         f.argtypes = args
-    _lib = L
+    _libs[path] = L
     return L
 
 
@@ -314,8 +319,8 @@ class Sketch:
 # ---------------------------------------------------------------------------
 
 def im_ctx_create(device: int = 0, stream=None, hbm_budget_bytes: int = 0,
-                  torch_allocator: bool = True) -> Context:
-    L = load_library()
+                  torch_allocator: bool = True, lib_path: str = LIB_PATH) -> Context:
+    L = load_library(lib_path)
     allocator = None
     if stream is None or torch_allocator:
         import torch
@@ -467,6 +472,16 @@ def im_ctx_set_tuning(ctx: Context, tuning: dict | None = None):
     for k, _ in im_tuning._fields_:
         setattr(t, k, int(cur[k]))
     ctx.check(ctx.lib.im_ctx_set_tuning(ctx.handle, ctypes.byref(t)))
+
+
+DEFAULT_BARRIER_WAIT_NS = 2_000_000_000
+DEFAULT_MAX_LEVELS = 16382
+
+
+def im_ctx_set_limits(ctx: Context, barrier_wait_ns: int = DEFAULT_BARRIER_WAIT_NS,
+                      max_levels: int = DEFAULT_MAX_LEVELS):
+    """Bounds of the device-side waits (grid barrier wait, levels per phase)."""
+    ctx.check(ctx.lib.im_ctx_set_limits(ctx.handle, _u64(barrier_wait_ns), int(max_levels)))
 
 
 def im_ctx_get_tuning(ctx: Context) -> dict:

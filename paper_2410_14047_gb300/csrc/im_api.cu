@@ -21,6 +21,8 @@
 
 using namespace im;
 
+constexpr uint64_t kDefaultBarrierLimitNs = 2000000000ull;  // 2 s
+
 struct im_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -45,6 +47,9 @@ struct im_ctx {
     std::vector<float> launch_ms;    // kernel time per launch sequence number (tracing)
     std::vector<im_trace_rec> recs;  // frontier launches of the last call
     im_tuning tuning{256, 4, 0, 2, 1, 0, 1, 2, 1, 8};
+    // bounds of the device-side waits (im_ctx_set_limits)
+    uint64_t barrier_limit_ns = kDefaultBarrierLimitNs;
+    int32_t max_levels = kMaxLevels - 2;
 };
 
 namespace {
@@ -324,6 +329,15 @@ extern "C" im_status im_ctx_set_tuning(im_ctx* c, const im_tuning* t) {
         t->chain < 0 || t->chain > 64)
         return fail(c, IM_E_INVAL, "tuning out of range");
     c->tuning = *t;
+    return IM_OK;
+}
+
+extern "C" im_status im_ctx_set_limits(im_ctx* c, uint64_t barrier_wait_ns, int32_t max_levels) {
+    if (!c) return IM_E_INVAL;
+    if (max_levels < 1 || max_levels > kMaxLevels - 2)
+        return fail(c, IM_E_INVAL, "max_levels must be in [1, %d]", kMaxLevels - 2);
+    c->barrier_limit_ns = barrier_wait_ns;
+    c->max_levels = max_levels;
     return IM_OK;
 }
 
@@ -792,7 +806,8 @@ static im_status check_err(im_sketch* sk) {
     if (err & kErrQueue) return fail(c, IM_E_STATE, "frontier queue overflow");
     if (err & kErrCasLimit) return fail(c, IM_E_TIMEOUT, "register CAS retry limit exceeded");
     if (err & kErrBarrier) return fail(c, IM_E_TIMEOUT, "grid barrier wait exceeded its time limit");
-    if (err & kErrLevels) return fail(c, IM_E_TIMEOUT, "frontier did not empty within %d levels", kMaxLevels - 2);
+    if (err & kErrLevels) return fail(c, IM_E_TIMEOUT, "frontier did not empty within %d levels", c->max_levels);
+    if (err & kErrBounds) return fail(c, IM_E_STATE, "device index out of bounds (bounds-checked build)");
     return IM_OK;
 }
 
@@ -837,7 +852,7 @@ static im_status run_phase_persistent(im_sketch* sk, int mode, bool all_first, i
     p.ctr = sk->ctr.as<ulonglong2>();
     p.claim = sk->claim.as<unsigned int>();
     p.all_first = all_first ? 1 : 0;
-    p.max_levels = kMaxLevels - 2;
+    p.max_levels = c->max_levels;
     p.gen_base = sk->gen_counter + 1;
     unsigned int* bar = sk->bar.as<unsigned int>();
     // the generation word (polled by the waiting blocks) on its own 128-byte
@@ -846,7 +861,7 @@ static im_status run_phase_persistent(im_sketch* sk, int mode, bool all_first, i
     p.abort_flag = bar + 2;
     p.levels_out = reinterpret_cast<int*>(bar + 3);
     p.bar_gen = bar + 32;
-    p.limit_ns = 20ull * 1000 * 1000 * 1000;
+    p.limit_ns = c->barrier_limit_ns;
     p.level_ns = c->trace ? sk->level_ns.as<unsigned long long>() : nullptr;
     p.fmt = sk->fmt.as<uint8_t>();
     CK(c, timed(c, mode == kPush ? kTPush : kTCover,
@@ -946,9 +961,9 @@ static im_status run_levels(im_sketch* sk, int mode, bool all_first) {
             CK(c, cudaMemcpyAsync(c->pinned, &ctr[t], 16, cudaMemcpyDeviceToHost, st));
             CK(c, sync_collect(c));
             if ((c->pinned[0] >> kCountShift) == 0 && (c->pinned[1] >> kCountShift) == 0) break;
-            if (t + 16 >= kMaxLevels) {
+            if (t >= c->max_levels || t + 16 >= kMaxLevels) {
                 sk->chg_dirty = true;
-                return fail(c, IM_E_TIMEOUT, "frontier did not empty within %d levels", kMaxLevels);
+                return fail(c, IM_E_TIMEOUT, "frontier did not empty within %d levels", (int)t);
             }
             if (check < 8) check *= 2;
         }
@@ -1137,6 +1152,8 @@ static im_status stats_collect(im_sketch* sk) {
     s.affected = h[kStAffected];
     s.pull_buckets = h[kStPullBuckets];
     s.pull_entries = h[kStPullEntries];
+    s.sweep_changed_buckets = h[kStSweepChangedBuckets];
+    s.sweep_live32 = h[kStSweepLive32];
     // algorithmic bytes of the sweeps: queue entry (16 B) + the queued vertex's
     // register row (J B) per queued vertex; live chunk mask (4 B, 8 B when
     // J = 1024) per in-edge; source id + edge hash (8 B, + 4 B threshold for

@@ -25,7 +25,28 @@ enum ModelKind : int { kUniform = 0, kWC = 1, kTrivalency = 2, kExplicit = 3,
                        kTargetModel = 4 /* per-target-vertex probability; runs as kWC */ };
 
 // Error bits a kernel may raise (host turns them into IM_E_* codes).
-enum : uint32_t { kErrCasLimit = 1u, kErrQueue = 2u, kErrBarrier = 4u, kErrLevels = 8u };
+enum : uint32_t { kErrCasLimit = 1u, kErrQueue = 2u, kErrBarrier = 4u, kErrLevels = 8u, kErrBounds = 16u };
+
+// Index checks of the bounds-checked build (compiled with IM_BOUNDS_CHECK, a
+// debug variant of the library): an index outside [0, hi) raises kErrBounds
+// and is replaced by 0, an index every checked access may use, so the bad
+// access is recorded and redirected instead of faulting; the host turns the
+// bit into IM_E_STATE.  In the normal build a check is the index itself.
+#ifdef IM_BOUNDS_CHECK
+template <class T>
+__device__ __forceinline__ T chk(T i, int64_t hi, uint32_t* err) {
+    if ((int64_t)i < 0 || (int64_t)i >= hi) {
+        if (err) atomicOr(err, kErrBounds);
+        return (T)0;
+    }
+    return i;
+}
+#else
+template <class T>
+__device__ __forceinline__ T chk(T i, int64_t, uint32_t*) {
+    return i;
+}
+#endif
 
 // Device view of a loaded graph.
 struct GraphDev {

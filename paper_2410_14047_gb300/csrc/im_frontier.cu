@@ -357,8 +357,8 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                                             int64_t El, unsigned long long& st_chunks,
                                             unsigned long long& st_cas, unsigned long long& st_new,
                                             unsigned long long& st_batches, unsigned long long& st_dealt,
-                                            unsigned long long& st_live, bool skip_heavy,
-                                            uint32_t (*sKeep)[kKeepWords], bool out_b) {
+                                            unsigned long long& st_live, unsigned long long& st_live32,
+                                            bool skip_heavy, uint32_t (*sKeep)[kKeepWords], bool out_b) {
     const int lane = (int)lane_id();
     const int J = a.J, words = a.words;
     const int64_t fend = min(El, b1 << 5);
@@ -375,7 +375,7 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
         const unsigned starts =
             __reduce_or_sync(0xFFFFFFFFu, (wvalid && rel >= 1 && rel <= 31) ? (1u << rel) : 0u);
         const int myw = c0 - 1 + __popc(starts & ((2u << lane) - 1u));
-        const int32_t qv = __shfl_sync(0xFFFFFFFFu, raw.x, myw);
+        const int32_t qv = chk(__shfl_sync(0xFFFFFFFFu, raw.x, myw), g.n, a.err);
         const int32_t qrp = __shfl_sync(0xFFFFFFFFu, raw.y, myw);
         const int32_t qoff = __shfl_sync(0xFFFFFFFFu, raw.z, myw);
         const uint32_t qaux = (uint32_t)__shfl_sync(0xFFFFFFFFu, raw.w, myw);
@@ -390,19 +390,20 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
         // this lane's edge: live chunk mask, source and hash are fetched at
         // once (one round trip with the change words below)
         const int64_t f = f0 + lane;
-        const int64_t e = (int64_t)qrp + (f - qoff);
+        int64_t e = (int64_t)qrp + (f - qoff);
         int32_t o = 0;
         uint32_t h = 0, thr = 0;
         uint32_t m_lo = 0u, m_hi = 0u;
         if (f < fend) {
+            e = chk(e, g.m, a.err);
             m_lo = __ldg(a.lcm_lo + e);
             if (a.lcm_hi) m_hi = __ldg(a.lcm_hi + e);
             if constexpr (MODE != kCover) {
-                o = __ldg(g.src_in + e);
+                o = chk(__ldg(g.src_in + e), g.n, a.err);
                 h = __ldg(g.h_in + e);
                 if constexpr (KIND == kExplicit) thr = __ldg(g.thr_in + e);
             } else {
-                o = __ldg(g.col_out + e);
+                o = chk(__ldg(g.col_out + e), g.n, a.err);
                 h = __ldg(g.h_out + e);
                 if constexpr (KIND == kExplicit || KIND == kWC) thr = edge_threshold<KIND, false>(g, 0u, 0u, e, 0u);
             }
@@ -411,7 +412,8 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
         uint32_t cm_lo = 0xFFFFFFFFu, cm_hi = 0xFFFFFFFFu;
         const bool used = wvalid && rel <= 31 && lane >= c0 - 1;
         __syncwarp();
-        if (!a.all_changed && used) chunk_change_mask(a.chg_cur, raw.x, words, cm_lo, cm_hi, sKeep[lane]);
+        if (!a.all_changed && used)
+            chunk_change_mask(a.chg_cur, chk(raw.x, g.n, a.err), words, cm_lo, cm_hi, sKeep[lane]);
         if constexpr (MODE == kPush) {
             // dense walk: the heavy queue pushes the hubs
             if (skip_heavy && used) {
@@ -444,6 +446,10 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
         const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
         const int excl = incl - nch;
         if (lane == 0) { ++st_batches; st_dealt += (unsigned)total; }
+        // the previous item (edge, chunk, raised anything) for the count of
+        // 32-simulation chunks: an odd chunk whose even partner of the same
+        // edge came just before and was counted is not counted again
+        uint32_t carry = 0xFFFFFFFFu;
         for (int base = 0; base < total; base += 32) {
             const int k = base + lane;
             int i = 0;
@@ -461,11 +467,11 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
             const int32_t q_i = __shfl_sync(0xFFFFFFFFu, qv, i);
             const uint32_t h_i = __shfl_sync(0xFFFFFFFFu, h, i);
             const uint32_t t_i = __shfl_sync(0xFFFFFFFFu, thr, i);
-            uint32_t nbits = 0u, imp = 0u;
+            uint32_t nbits = 0u, imp = 0u, any = 0u;
             int chunk = 0;
             EnqueueState eq;
             if (k < total) {
-                chunk = nth_chunk(ml_i, mh_i, k - ex_i);
+                chunk = chk(nth_chunk(ml_i, mh_i, k - ex_i), a.chunks, a.err);
                 uint32_t chb = 0xFFFFu;
                 if (!a.all_changed) {
                     const uint32_t cw = words <= kKeepWords ? sKeep[w_i][chunk >> 1]
@@ -481,7 +487,6 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                     const uint32_t sw[4] = {src.x, src.y, src.z, src.w};
                     const uint32_t tw[4] = {tg.x, tg.y, tg.z, tg.w};
                     uint32_t cand[4];
-                    uint32_t any = 0u;
 #pragma unroll
                     for (int w = 0; w < 4; ++w) {
                         const uint32_t L = live4(xs[w], h_i, t_i) & bits_to_bytes((chb >> (4 * w)) & 0xFu);
@@ -521,6 +526,15 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                 }
             }
             (void)nbits;
+            if constexpr (MODE == kPush) {
+                const uint32_t tag = k < total ? ((uint32_t)i << 7 | (uint32_t)chunk << 1 | (any ? 1u : 0u))
+                                               : 0xFFFFFFFFu;
+                uint32_t ptag = __shfl_up_sync(0xFFFFFFFFu, tag, 1);
+                if (lane == 0) ptag = carry;
+                carry = __shfl_sync(0xFFFFFFFFu, tag, 31);
+                const bool partner = (chunk & 1) && ptag == (((uint32_t)i << 7) | ((uint32_t)(chunk - 1) << 1) | 1u);
+                if (k < total && any && !partner) ++st_live32;
+            }
             // enqueue what changed: the vertex, or its chunk's bucket
             if (out_b) bucket_enqueue_finish(a, imp != 0u, o_i, (uint32_t)chunk, eq);
             else vertex_enqueue_finish<KIND, MODE>(g, a, imp != 0u, o_i, eq);
@@ -562,7 +576,7 @@ __device__ __forceinline__ void heavy_vertex(const GraphDev& g, const LevelArgs&
                                              unsigned long long& st_cas, bool out_b) {
     const int lane = (int)lane_id();
     const int J = a.J, words = a.words;
-    const int32_t v = ent.v;
+    const int32_t v = chk(ent.v, g.n, a.err);
     const int32_t rb = ent.rp;
     const int32_t re = __ldg(g.rp_in + v + 1);
     const uint32_t thr = KIND == kWC ? ent.aux : g.thr_uniform;
@@ -628,10 +642,10 @@ __device__ __forceinline__ void heavy_vertex(const GraphDev& g, const LevelArgs&
             bool changed = false;
             int32_t u = 0;
             if (c < ncand) {
-                const int32_t e = a0 + c;
+                const int32_t e = chk(a0 + c, g.m, a.err);
                 const uint32_t h = __ldg(g.h_in + e);
                 if ((Xj ^ h) < thr) {
-                    u = __ldg(g.src_in + e);
+                    u = chk(__ldg(g.src_in + e), g.n, a.err);
                     unsigned int* addr = reinterpret_cast<unsigned int*>(a.M + (((size_t)u * J + j) & ~(size_t)3));
                     const uint32_t b = val << (8 * (j & 3));
                     uint32_t cur = __ldcg(addr);
@@ -757,6 +771,7 @@ __device__ __forceinline__ void bucket_pos(const GraphDev& g, const LevelArgs& a
                                            unsigned long long& st_dealt, bool out_b, InlineCand& ic) {
     const int J = a.J;
     const uint32_t C = (uint32_t)a.chunks;
+    if (valid) bkt = chk(bkt, a.nbuckets, a.err);
     const uint32_t u = bkt / C, c = bkt % C;
     uint32_t nbits = 0u;
     int32_t o = 0;
@@ -764,7 +779,10 @@ __device__ __forceinline__ void bucket_pos(const GraphDev& g, const LevelArgs& a
     uint32_t m16 = 0u;
     uint4 src = make_uint4(0u, 0u, 0u, 0u);
     if (valid) {
-        o = __ldg(a.bk_other + e);
+#ifdef IM_BOUNDS_CHECK
+        e = chk(e, (int64_t)__ldcg(a.bk_end + a.nbuckets - 1), a.err);
+#endif
+        o = chk(__ldg(a.bk_other + e), g.n, a.err);
         m16 = __ldg(a.bk_mask + e);
         src = ld_cg16(a.M + (size_t)u * J + c * 16);
     }
@@ -986,7 +1004,7 @@ __device__ __forceinline__ void bucket_slice(const GraphDev& g, const LevelArgs&
 
 struct LevelStats {
     unsigned long long chunks = 0, cas = 0, fresh = 0, hsims = 0, batches = 0, dealt = 0, live = 0,
-        bentries = 0;
+        bentries = 0, live32 = 0;
 };
 
 // Clears the change bits read by the level before the previous one.
@@ -1005,7 +1023,7 @@ __device__ __forceinline__ void clear_prev_bits(const LevelArgs& a, int64_t warp
         }
         uint16_t* h16 = reinterpret_cast<uint16_t*>(a.chg_prev);
         for (int64_t i = warp * 32 + lane; i < nlp; i += nwarps * 32) {
-            const uint32_t b = (uint32_t)__ldcg(&a.ql_prev[i].v);
+            const uint32_t b = chk((uint32_t)__ldcg(&a.ql_prev[i].v), a.nbuckets, a.err);
             const uint32_t u = b / (uint32_t)a.chunks, c = b % (uint32_t)a.chunks;
             h16[(size_t)u * a.words * 2 + c] = 0;
         }
@@ -1013,7 +1031,7 @@ __device__ __forceinline__ void clear_prev_bits(const LevelArgs& a, int64_t warp
     }
     const int32_t nhp = a.ch_prev ? (int32_t)(__ldcg(a.ch_prev) >> kCountShift) : 0;
     for (int64_t i = warp; i < (int64_t)nlp + nhp; i += nwarps) {
-        const int32_t v = i < nlp ? __ldcg(&a.ql_prev[i].v) : __ldcg(&a.qh_prev[i - nlp].v);
+        const int32_t v = chk(i < nlp ? __ldcg(&a.ql_prev[i].v) : __ldcg(&a.qh_prev[i - nlp].v), a.vq_cap, a.err);
         if (lane < a.words) a.chg_prev[(size_t)v * a.words + lane] = 0u;
     }
 }
@@ -1058,14 +1076,14 @@ __device__ __forceinline__ void clear_unit(const LevelArgs& a, const ClearPlan& 
     } else if (c.mode == 2) {
         const int64_t i = (u << 5) + lane;
         if (i < c.n) {
-            const uint32_t b = (uint32_t)__ldcg(&a.ql_prev[i].v);
+            const uint32_t b = chk((uint32_t)__ldcg(&a.ql_prev[i].v), a.nbuckets, a.err);
             const uint32_t v = b / (uint32_t)a.chunks, ch = b % (uint32_t)a.chunks;
             reinterpret_cast<uint16_t*>(a.chg_prev)[(size_t)v * a.words * 2 + ch] = 0;
         }
     } else if (c.mode == 1) {
         const int64_t i = (u << 5) + lane;
         if (i < c.n) {
-            const int32_t v = i < c.nl ? __ldcg(&a.ql_prev[i].v) : __ldcg(&a.qh_prev[i - c.nl].v);
+            const int32_t v = chk(i < c.nl ? __ldcg(&a.ql_prev[i].v) : __ldcg(&a.qh_prev[i - c.nl].v), a.vq_cap, a.err);
             for (int w = 0; w < a.words; ++w) a.chg_prev[(size_t)v * a.words + w] = 0u;
         }
     }
@@ -1133,6 +1151,8 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
         const bool all_bits = MODE != kAffect && !dense && nbl <= nwarps && a.gflag == nullptr;
         if (warp == 0 && lane == 0) {
             atomicAdd(a.stats + (MODE == kPush ? kStSweepBuckets : kStCoverVertices), (unsigned long long)nq);
+            // the input of a level after the first: what the previous level changed
+            if (MODE == kPush && a.cl_prev) atomicAdd(a.stats + kStSweepChangedBuckets, (unsigned long long)nq);
             if (MODE == kCover) atomicAdd(a.stats + kStCoverEdges, (unsigned long long)E);
             atomicAdd(a.stats + (MODE == kPush ? kStSweepLevels : kStCoverLevels), 1ull);
         }
@@ -1184,6 +1204,10 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
     if (warp == 0 && lane == 0) {
         atomicAdd(a.stats + (MODE == kPush ? kStSweepVertices : kStCoverVertices),
                   (unsigned long long)(nl + nh));
+        // the input of a level after the first: the vertices the previous
+        // level changed (the queues' own counts, also on a dense walk)
+        if (MODE == kPush && a.cl_prev)
+            atomicAdd(a.stats + kStSweepChanged, (cl >> kCountShift) + (ch >> kCountShift));
         atomicAdd(a.stats + (MODE == kPush ? kStSweepEdges : kStCoverEdges), (unsigned long long)(El + (hscan ? Eh : 0)));
         atomicAdd(a.stats + (MODE == kPush ? kStSweepLevels : kStCoverLevels), 1ull);
         if (MODE == kPush) atomicAdd(a.stats + kStSweepHeavy, (unsigned long long)nhv);
@@ -1204,13 +1228,13 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
             const int64_t b0 = lu * lb;
             const int64_t b1 = min(nbl, b0 + lb);
             light_slice<KIND, MODE>(g, a, ql, sX, sTab, b0, b1, nl, El, ls.chunks, ls.cas, ls.fresh,
-                                    ls.batches, ls.dealt, ls.live, dense && nh > 0, sKeep, out_b);
+                                    ls.batches, ls.dealt, ls.live, ls.live32, dense && nh > 0, sKeep, out_b);
         } else {
             const int64_t hu = (int64_t)unit - nhv - lunits;
             const int64_t b0 = hu * lb;
             const int64_t b1 = min(nbh, b0 + lb);
             light_slice<KIND, MODE>(g, a, a.qh_in, sX, sTab, b0, b1, nh, Eh, ls.chunks, ls.cas, ls.fresh,
-                                    ls.batches, ls.dealt, ls.live, false, sKeep, out_b);
+                                    ls.batches, ls.dealt, ls.live, ls.live32, false, sKeep, out_b);
         }
     }
 }
@@ -1225,8 +1249,10 @@ __device__ __forceinline__ void flush_stats(const LevelArgs& a, LevelStats& ls) 
     ls.dealt = wsum(ls.dealt);
     ls.live = wsum(ls.live);
     ls.bentries = wsum(ls.bentries);
+    ls.live32 = wsum(ls.live32);
     if (lane_id() == 0) {
         if constexpr (MODE == kPush) {
+            if (ls.live32) atomicAdd(a.stats + kStSweepLive32, ls.live32);
             if (ls.bentries) atomicAdd(a.stats + kStSweepBucketEntries, ls.bentries);
             if (ls.live) atomicAdd(a.stats + kStSweepLiveEdges, ls.live);
             if (ls.batches) atomicAdd(a.stats + kStSweepBatches, ls.batches);
@@ -1279,9 +1305,10 @@ __global__ void __launch_bounds__(kFBlock, kLevelMinBlocks) k_level(GraphDev g, 
 }
 
 // Grid-wide barrier of a cooperative launch: arrival counter + generation
-// word.  Every wait is bounded by `limit_ns` of global time; a block that
-// gives up raises kErrBarrier and the abort word, and all blocks leave the
-// phase at their next barrier.
+// word.  Every wait is bounded by `limit_ns` of global time (0: a block that
+// has to wait gives up at its first poll); a block that gives up raises
+// kErrBarrier and the abort word, and all blocks leave the phase at their
+// next barrier.
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -1292,7 +1319,7 @@ __device__ bool grid_barrier(unsigned int* arrive, volatile unsigned int* gen, v
                              uint32_t* err, unsigned long long limit_ns, unsigned int g0) {
     // one arrival counter (the last block to arrive resets it and advances
     // the generation); the waits poll only the generation word, with the
-    // abort word and the clock every 32 polls
+    // abort word and the clock at the first poll and every 32nd
     __syncthreads();
     __shared__ bool ok;
     if (threadIdx.x == 0) {
@@ -1311,9 +1338,9 @@ __device__ bool grid_barrier(unsigned int* arrive, volatile unsigned int* gen, v
             const unsigned long long t0 = global_ns();
             unsigned int it = 0;
             while (*gen == g0) {
-                if ((++it & 31u) == 0u) {
+                if ((it++ & 31u) == 0u) {
                     if (*abort_flag) { ok = false; break; }
-                    if (global_ns() - t0 > limit_ns) {
+                    if (global_ns() - t0 >= limit_ns) {
                         atomicOr(err, kErrBarrier);
                         *abort_flag = 1u;
                         ok = false;
@@ -2193,13 +2220,13 @@ __global__ void __launch_bounds__(kFBlock) k_pull_affected(GraphDev g, LevelArgs
     const int J = a.J, words = a.words;
     unsigned long long n_cas = 0;
     walk_rows(loff, count, total, [&](int64_t f, int32_t row) {
-        const int32_t u = __ldg(list + row);
-        const int64_t e = (int64_t)__ldg(g.rp_out + u) + (f - __ldg(loff + row));
+        const int32_t u = chk(__ldg(list + row), g.n, a.err);
+        const int64_t e = chk((int64_t)__ldg(g.rp_out + u) + (f - __ldg(loff + row)), g.m, a.err);
         const uint2 am = __ldg(lmask + row);
         uint32_t m_lo = __ldg(a.lcm_lo + e) & am.x;
         uint32_t m_hi = a.lcm_hi ? (__ldg(a.lcm_hi + e) & am.y) : 0u;
         if (!(m_lo | m_hi)) return;
-        const int32_t w = __ldg(g.col_out + e);
+        const int32_t w = chk(__ldg(g.col_out + e), g.n, a.err);
         const uint32_t h = __ldg(g.h_out + e);
         const uint32_t thr = edge_threshold<KIND, false>(g, (uint32_t)u, (uint32_t)w, e, 0u);
         const uint32_t* au = a.aff + (size_t)u * words;
@@ -2249,10 +2276,13 @@ __global__ void __launch_bounds__(kFBlock) k_pull_buckets(LevelArgs a, const QEn
         uint32_t b = 0xFFFFFFFFu;
         if (valid) {
             const int4 raw = __ldg(reinterpret_cast<const int4*>(q) + r);
-            b = (uint32_t)raw.x;
+            b = chk((uint32_t)raw.x, a.nbuckets, a.err);
             const uint32_t c = b % C;
-            const int64_t e = (int64_t)(uint32_t)raw.y + (f - raw.z);
-            const int32_t w = __ldg(a.bk_other + e);
+            int64_t e = (int64_t)(uint32_t)raw.y + (f - raw.z);
+#ifdef IM_BOUNDS_CHECK
+            e = chk(e, (int64_t)__ldcg(a.bk_end + a.nbuckets - 1), a.err);
+#endif
+            const int32_t w = chk(__ldg(a.bk_other + e), a.vq_cap, a.err);
             const uint32_t a16 = (uint32_t)raw.w;  // the chunk's affected bits, from the queue entry
             const uint32_t m16 = __ldg(a.bk_mask + e) & a16;
             if (m16) {
@@ -2291,7 +2321,7 @@ __global__ void __launch_bounds__(kFBlock) k_push_init_list(GraphDev g, LevelArg
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < cnt; i0 += stride) {
         const int64_t i = i0 + threadIdx.x;
-        const int32_t v = i < cnt ? __ldcg(list + i) : 0;
+        const int32_t v = i < cnt ? chk(__ldcg(list + i), g.n, a.err) : 0;
         if (buckets) {
             bucket_level0(a, i < cnt, v, a.aff, a.chg_next, a.ql_out, a.cl_out, a.ch_out);
             continue;
@@ -2368,7 +2398,7 @@ __global__ void __launch_bounds__(kFBlock) k_reset_words(uint8_t* __restrict__ M
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < cnt; i0 += stride) {
         const int64_t i = i0 + threadIdx.x;
         const bool valid = i < cnt;
-        const uint32_t it = valid ? __ldcg(awl + i) : 0u;
+        const uint32_t it = valid ? chk(__ldcg(awl + i), (int64_t)o.vq_cap * o.words, o.err) : 0u;
         if (valid) {
             const uint32_t v = it / (uint32_t)o.words, w = it % (uint32_t)o.words;
             const uint32_t ku = mm3_k(hkey ? (uint32_t)hkey[v] : v);

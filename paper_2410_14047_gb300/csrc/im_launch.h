@@ -32,6 +32,8 @@ enum StatIndex : int {
     kStAffected,            // registers recomputed by incremental rebuilds
     kStPullBuckets,         // out-buckets queued by the pulls of incremental rebuilds
     kStPullEntries,         // out-bucket entries walked by those pulls
+    kStSweepChangedBuckets, // (vertex, chunk) buckets whose registers changed (bucket-format levels)
+    kStSweepLive32,         // (edge, 32-simulation chunk) pairs with a live, changed, non-visited source
     kStCount
 };
 

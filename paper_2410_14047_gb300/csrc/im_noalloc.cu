@@ -7,6 +7,7 @@
 // that loads the library holds the array (about 15 KB) until the process
 // exits.  Host code may not use the array's name as a device address; the
 // address is looked up with cudaGetSymbolAddress once per device.
+#include <cstdint>
 #include <mutex>
 
 #include "../../include/difuser_im.h"
@@ -48,6 +49,13 @@ extern "C" im_status im_argmax_noalloc(const uint8_t* M, int32_t n, int32_t J, u
                                        void* cuda_stream, int32_t* s_out, uint64_t* S_out,
                                        double* est_out) {
     if (!M || !picked || !s_out || !S_out || !est_out) return IM_E_INVAL;
+    // the kernel reads register rows as 16-byte vectors and the outputs as
+    // naturally aligned words: a misaligned buffer (say, a slice of a larger
+    // tensor at an odd offset) is refused here, before anything reaches the GPU
+    if ((reinterpret_cast<uintptr_t>(M) & 15u) || (reinterpret_cast<uintptr_t>(picked) & 3u) ||
+        (reinterpret_cast<uintptr_t>(s_out) & 3u) || (reinterpret_cast<uintptr_t>(S_out) & 7u) ||
+        (reinterpret_cast<uintptr_t>(est_out) & 7u))
+        return IM_E_INVAL;
     if (n < 1 || n >= (1 << 26)) return IM_E_RANGE;
     if (J < 16 || J > im::kMaxJ || (J & (J - 1)) != 0) return IM_E_INVAL;
     if (im::pick_grid(n, J) > kNoAllocMaxBlocks) return IM_E_RANGE;

@@ -34,6 +34,14 @@ def test_library_builds_and_exports_every_declared_symbol():
     im.load_library(path)
 
 
+def test_bounds_checked_variant_builds_and_exports_every_declared_symbol():
+    from paper_2410_14047_gb300 import _build
+
+    L = ctypes.CDLL(_build.build_bounds())
+    missing = [n for n in _declared() if not hasattr(L, n)]
+    assert not missing, missing
+
+
 def test_status_strings_without_gpu():
     import paper_2410_14047_gb300 as im
 
@@ -58,10 +66,6 @@ def test_ctx_create_without_gpu_fails_cleanly():
 def test_missing_library_fails_loudly(tmp_path):
     import paper_2410_14047_gb300 as im
 
-    saved = im._lib
-    try:
-        im._lib = None
-        with pytest.raises(im.IMError):
-            im.load_library(str(tmp_path / "nope.so"))
-    finally:
-        im._lib = saved
+    with pytest.raises(im.IMError):
+        im.load_library(str(tmp_path / "nope.so"))
+    assert str(tmp_path / "nope.so") not in im._libs
