@@ -49,9 +49,10 @@ def parse():
     ap.add_argument("--workload", default="rmat24")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--mode", default="select", choices=["select", "build", "fillrate"],
+    ap.add_argument("--mode", default="select", choices=["select", "build", "fillrate", "trace"],
                     help="select: the benchmark; build: time im_sketch_build only (profiling); "
-                         "fillrate: warp fill rate of the live tests, draw order vs sorted X (Table 6 analogue)")
+                         "fillrate: warp fill rate of the live tests, draw order vs sorted X (Table 6 analogue); "
+                         "trace: per-level records of one selection (frontier sizes, edges, duration)")
     ap.add_argument("--batch-graphs", type=int, default=512,
                     help="graphs of the batched workload (--workload batched)")
     ap.add_argument("--tuning", default="",
@@ -584,6 +585,38 @@ def run_gpu(args):
 
     def step():
         return im.im_select_seeds(G, wl.K, wl.J, seed=wl.seed, rebuild_eps=wl.rebuild_eps)
+
+    if args.mode == "trace":
+        # one warm selection, then one traced: every level of every phase
+        step()
+        im.im_ctx_set_trace(ctx, True)
+        r = step()
+        tr = im.im_last_trace(ctx)
+        st = im.im_last_stats(ctx)
+        im.im_ctx_set_trace(ctx, False)
+        phases, cur = [], None
+        for rec in tr:
+            if rec["level"] == 0 or cur is None or rec["kind"] != cur["kind"]:
+                cur = {"kind": ["propagate", "cover", "affect"][int(rec["kind"])], "levels": []}
+                phases.append(cur)
+            cur["levels"].append([int(rec["count"]), int(rec["edges"]), round(float(rec["ms"]), 4)])
+        summary = {}
+        for ph in phases:
+            d = summary.setdefault(ph["kind"], {"phases": 0, "levels": 0, "ms": 0.0})
+            d["phases"] += 1
+            d["levels"] += len(ph["levels"])
+            d["ms"] += sum(x[2] for x in ph["levels"])
+        if rank == 0:
+            print(json.dumps({"mode": "trace", "workload": wl.name, "seeds": r["seeds"].tolist()[:8],
+                              "summary": summary,
+                              "propagation_phases": [p["levels"] for p in phases if p["kind"] == "propagate"],
+                              "largest_covers": sorted(([sum(x[2] for x in p["levels"]), len(p["levels"])]
+                                                        for p in phases if p["kind"] == "cover"),
+                                                       reverse=True)[:10],
+                              "stats": {k: st[k] for k in ("ms_propagate", "ms_cover_kernels", "ms_pick_kernels",
+                                                           "ms_fill_kernels", "builds", "sweeps",
+                                                           "cover_levels")}}), flush=True)
+        return 0
 
     # the schedule knobs for this workload: the project's autotuner, untimed
     tuned = None

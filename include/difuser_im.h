@@ -157,7 +157,10 @@ typedef struct {
  * level of a propagation or affected-set search with at most one batch per
  * warp, a warp that raises a small bucket (<= 32 entries) queues it, then
  * also processes it at once, up to `chain` such continuations per warp and
- * level (0 = off): chains of small buckets advance several hops a level. */
+ * level (0 = off): chains of small buckets advance several hops a level;
+ * pick_tile: the J-tile width of a full estimate + argmax pass, the 16-byte
+ * register pieces (16 simulations each) one lane sums per row: 1, 2 or 4
+ * (0 = 4); fewer pieces a lane means more lanes per row. */
 typedef struct {
     int32_t heavy_indeg;
     int32_t light_batches;
@@ -169,6 +172,7 @@ typedef struct {
     int32_t buckets;
     int32_t incremental;
     int32_t chain;
+    int32_t pick_tile;
 } im_tuning;
 
 /* One frontier launch of the last selection / build (tracing on). */
@@ -202,7 +206,7 @@ IM_API im_status im_last_stats(const im_ctx* ctx, im_stats* out);
  * stream and report per-kind kernel time in im_stats (adds two event records
  * per launch).  Off by default. */
 IM_API im_status im_ctx_set_timing(im_ctx* ctx, int enable);
-/* Sets (NULL = defaults {256, 4, 0, 2, 1, 0, 1, 2, 1, 8}) or reads the schedule knobs. */
+/* Sets (NULL = defaults {256, 4, 0, 2, 1, 0, 1, 2, 1, 8, 4}) or reads the schedule knobs. */
 IM_API im_status im_ctx_set_tuning(im_ctx* ctx, const im_tuning* tuning);
 IM_API im_status im_ctx_get_tuning(const im_ctx* ctx, im_tuning* tuning);
 /* Bounds of the waits inside the device code, so that a loop that should end

@@ -4,9 +4,12 @@ Chooses the im_tuning knobs (vertex-to-warp mapping: the in-degree above which
 a hub is pushed by per-simulation hash search instead of an in-edge scan;
 work granularity: 32-edge batches per claimed unit; frontier thresholds: when a
 propagation level walks every vertex in vertex order, and below which level
-size queues switch from vertices to (vertex, chunk) buckets) by timing short
-runs of the caller's workload.  The knobs change how work is split, never a
-result.
+size queues switch from vertices to (vertex, chunk) buckets; J-tile width: the
+16-simulation register pieces one lane sums per row in the estimate + argmax
+pass) by timing short runs of the caller's workload.  The frontier knobs are
+tried together (every combination), then the J-tile width with the best of
+them fixed (the estimate pass does not interact with the frontier schedule).
+The knobs change how work is split, never a result.
 """
 from __future__ import annotations
 
@@ -23,6 +26,11 @@ DEFAULT_SPACE = {
     "dense_div": [0, 2],
     "buckets": [0, 1, 2],
 }
+
+
+# stages of the default search: each stage's combinations are timed with the
+# winners of the earlier stages in place
+DEFAULT_STAGES = [DEFAULT_SPACE, {"pick_tile": [1, 2, 4]}]
 
 
 def candidates(space: dict | None = None):
@@ -43,20 +51,27 @@ def tune(ctx, run, space: dict | None = None, repeats: int = 2, cache: str | Non
             im_ctx_set_tuning(ctx, stored["tuning"])
             return dict(stored, cached=True)
     base = im_ctx_get_tuning(ctx)
+    stages = DEFAULT_STAGES if space is None else [space]
     trials = []
-    for cand in candidates(space):
-        t = dict(base, **cand)
-        im_ctx_set_tuning(ctx, t)
-        run()  # warm-up under this schedule
-        best = float("inf")
-        for _ in range(repeats):
-            t0 = time.perf_counter()
-            run()
-            best = min(best, time.perf_counter() - t0)
-        trials.append({"tuning": cand, "ms": best * 1e3})
-    winner = min(trials, key=lambda x: x["ms"])
-    im_ctx_set_tuning(ctx, dict(base, **winner["tuning"]))
-    report = {"tuning": dict(base, **winner["tuning"]), "ms": winner["ms"], "trials": trials}
+    chosen = {}
+    winner = None
+    for stage in stages:
+        stage_trials = []
+        for cand in candidates(stage):
+            pick = dict(chosen, **cand)
+            im_ctx_set_tuning(ctx, dict(base, **pick))
+            run()  # warm-up under this schedule
+            best = float("inf")
+            for _ in range(repeats):
+                t0 = time.perf_counter()
+                run()
+                best = min(best, time.perf_counter() - t0)
+            stage_trials.append({"tuning": pick, "ms": best * 1e3})
+        winner = min(stage_trials, key=lambda x: x["ms"])
+        chosen = dict(winner["tuning"])
+        trials += stage_trials
+    im_ctx_set_tuning(ctx, dict(base, **chosen))
+    report = {"tuning": dict(base, **chosen), "ms": winner["ms"], "trials": trials}
     if cache and key:
         data = json.load(open(cache)) if os.path.exists(cache) else {}
         data[key] = {"tuning": report["tuning"], "ms": report["ms"]}

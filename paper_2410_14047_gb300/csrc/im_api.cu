@@ -46,7 +46,7 @@ struct im_ctx {
     bool trace = false;
     std::vector<float> launch_ms;    // kernel time per launch sequence number (tracing)
     std::vector<im_trace_rec> recs;  // frontier launches of the last call
-    im_tuning tuning{256, 4, 0, 2, 1, 0, 1, 2, 1, 8};
+    im_tuning tuning{256, 4, 0, 2, 1, 0, 1, 2, 1, 8, 4};
     // bounds of the device-side waits (im_ctx_set_limits)
     uint64_t barrier_limit_ns = kDefaultBarrierLimitNs;
     int32_t max_levels = kMaxLevels - 2;
@@ -320,13 +320,14 @@ extern "C" im_status im_ctx_set_timing(im_ctx* c, int enable) {
 extern "C" im_status im_ctx_set_tuning(im_ctx* c, const im_tuning* t) {
     if (!c) return IM_E_INVAL;
     if (!t) {
-        c->tuning = im_tuning{256, 4, 0, 2, 1, 0, 1, 2, 1, 8};
+        c->tuning = im_tuning{256, 4, 0, 2, 1, 0, 1, 2, 1, 8, 4};
         return IM_OK;
     }
     if (t->heavy_indeg < 0 || t->light_batches < 1 || t->light_batches > 4096 || t->grid_blocks < 0 ||
         t->check_every < 1 || t->check_every > 64 || t->persistent < 0 || t->persistent > 1 ||
         t->dense_div < 0 || t->lazy_pick < 0 || t->lazy_pick > 1 || t->buckets < 0 || t->buckets > 1024 || t->incremental < 0 || t->incremental > 2 ||
-        t->chain < 0 || t->chain > 64)
+        t->chain < 0 || t->chain > 64 ||
+        !(t->pick_tile == 0 || t->pick_tile == 1 || t->pick_tile == 2 || t->pick_tile == 4))
         return fail(c, IM_E_INVAL, "tuning out of range");
     c->tuning = *t;
     return IM_OK;
@@ -579,7 +580,8 @@ extern "C" im_status im_graph_info(const im_graph* g, int32_t* n, int64_t* m) {
 // sizes; sketch_alloc allocates exactly this list and query_bytes sums it.
 using BufPlan = std::vector<std::pair<DBuf*, size_t>>;
 static void sketch_plan(im_sketch* sk, int32_t n, int64_t m_edges, int32_t J, BufPlan& plan) {
-    const int pg = std::max(pick_grid(n, J), pick_lazy_grid(n));
+    // the partials of a full pick at any J-tile width, or of a lazy pick
+    const int pg = std::max({pick_grid(n, J, 1), pick_grid(n, J, 2), pick_grid(n, J, 4), pick_lazy_grid(n)});
     auto A = [&](DBuf& b, size_t bytes) { plan.emplace_back(&b, bytes); };
     A(sk->M, (size_t)n * J);
     A(sk->X, (size_t)J * 4);
@@ -1400,6 +1402,7 @@ static PickArgs pick_args(im_sketch* sk, int k) {
     a.bk_end_out = sk->buckets ? sk->bk_end[1].as<uint32_t>() : nullptr;
     a.chunks = sk->J / 16;
     a.nv = sk->incr ? sk->nv.as<uint32_t>() : nullptr;
+    a.tile = sk->ctx->tuning.pick_tile;
     return a;
 }
 

@@ -30,6 +30,9 @@
 namespace im {
 
 constexpr int kFBlock = 256;
+// per-lane statistics counters: 32 bits (a lane's counts over one phase stay
+// far below 2^32) keep registers free in the frontier loops; warp sums are 64-bit
+using StatT = uint32_t;
 // resident blocks per SM the frontier kernels are compiled for (register cap);
 // the work is latency-bound, so more resident warps hide more of it
 #ifndef IM_PHASE_MIN_BLOCKS
@@ -125,7 +128,7 @@ __device__ __forceinline__ bool is_heavy(int32_t deg, uint32_t thr, int32_t heav
 // changed by another thread meanwhile) one word at a time.  Returns the
 // changed registers as 16 bits.
 __device__ __forceinline__ uint32_t merge_chunk(uint8_t* trow, const uint32_t cand[4], uint4 tg,
-                                               unsigned long long& n_cas, uint32_t* err) {
+                                               StatT& n_cas, uint32_t* err) {
     uint32_t cur[4] = {tg.x, tg.y, tg.z, tg.w};
     uint32_t nw[4], prev[4];
     bool pend[4];
@@ -276,7 +279,7 @@ __device__ __forceinline__ void vertex_enqueue_finish(const GraphDev& g, const L
 // reached along a live edge and its register is not visited); returns the
 // 16 bits that were not marked before.
 __device__ __forceinline__ uint32_t mark_affected(const LevelArgs& a, const uint32_t cand[4], int32_t o, uint32_t c,
-                                                  unsigned long long& st_new) {
+                                                  StatT& st_new) {
     uint32_t b16 = 0u;
 #pragma unroll
     for (int w = 0; w < 4; ++w) b16 |= bytes_to_bits(cand[w]) << (4 * w);
@@ -354,10 +357,10 @@ template <int KIND, int MODE>
 __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& a, const QEntry* __restrict__ qlin,
                                             const uint32_t* sX,
                                             const uint16_t* sTab, int64_t b0, int64_t b1, int32_t nl,
-                                            int64_t El, unsigned long long& st_chunks,
-                                            unsigned long long& st_cas, unsigned long long& st_new,
-                                            unsigned long long& st_batches, unsigned long long& st_dealt,
-                                            unsigned long long& st_live, unsigned long long& st_live32,
+                                            int64_t El, StatT& st_chunks,
+                                            StatT& st_cas, StatT& st_new,
+                                            StatT& st_batches, StatT& st_dealt,
+                                            StatT& st_live, StatT& st_live32,
                                             bool skip_heavy, uint32_t (*sKeep)[kKeepWords], bool out_b) {
     const int lane = (int)lane_id();
     const int J = a.J, words = a.words;
@@ -572,8 +575,8 @@ __device__ __forceinline__ int32_t lower_bound_h(const uint32_t* __restrict__ h,
 // ---------------------------------------------------------------------------
 template <int KIND>
 __device__ __forceinline__ void heavy_vertex(const GraphDev& g, const LevelArgs& a, const uint32_t* sX,
-                                             QEntry ent, unsigned long long& st_chunks,
-                                             unsigned long long& st_cas, bool out_b) {
+                                             QEntry ent, StatT& st_chunks,
+                                             StatT& st_cas, bool out_b) {
     const int lane = (int)lane_id();
     const int J = a.J, words = a.words;
     const int32_t v = chk(ent.v, g.n, a.err);
@@ -766,9 +769,9 @@ constexpr uint32_t kChainMaxLen = 32;  // bucket entries a continuation may take
 // continue at once.
 template <int KIND, int MODE>
 __device__ __forceinline__ void bucket_pos(const GraphDev& g, const LevelArgs& a, bool valid, uint32_t bkt,
-                                           int64_t e, uint32_t chb, unsigned long long& st_chunks,
-                                           unsigned long long& st_cas, unsigned long long& st_new,
-                                           unsigned long long& st_dealt, bool out_b, InlineCand& ic) {
+                                           int64_t e, uint32_t chb, StatT& st_chunks,
+                                           StatT& st_cas, StatT& st_new,
+                                           StatT& st_dealt, bool out_b, InlineCand& ic) {
     const int J = a.J;
     const uint32_t C = (uint32_t)a.chunks;
     if (valid) bkt = chk(bkt, a.nbuckets, a.err);
@@ -872,9 +875,9 @@ __device__ __forceinline__ void chain_push(int4* stk, int& sp, const InlineCand&
 // it queued).
 template <int KIND, int MODE>
 __device__ __forceinline__ void chain_drain(const GraphDev& g, const LevelArgs& a, int4* stk, int& sp, int chain,
-                                            int& used, unsigned long long& st_chunks, unsigned long long& st_cas,
-                                            unsigned long long& st_new, unsigned long long& st_batches,
-                                            unsigned long long& st_dealt, bool out_b) {
+                                            int& used, StatT& st_chunks, StatT& st_cas,
+                                            StatT& st_new, StatT& st_batches,
+                                            StatT& st_dealt, bool out_b) {
     const int lane = (int)lane_id();
     for (; sp > 0 && used < chain; ++used) {
         --sp;
@@ -898,9 +901,9 @@ __device__ __forceinline__ void chain_drain(const GraphDev& g, const LevelArgs& 
 template <int KIND, int MODE>
 __device__ __forceinline__ void bucket_slice(const GraphDev& g, const LevelArgs& a, const QEntry* __restrict__ qlin,
                                              int64_t b0, int64_t b1, int32_t nq, int64_t E, bool dense,
-                                             unsigned long long& st_chunks, unsigned long long& st_cas,
-                                             unsigned long long& st_new, unsigned long long& st_batches,
-                                             unsigned long long& st_dealt, bool out_b, int chain,
+                                             StatT& st_chunks, StatT& st_cas,
+                                             StatT& st_new, StatT& st_batches,
+                                             StatT& st_dealt, bool out_b, int chain,
                                              bool all_bits) {
     const int lane = (int)lane_id();
     const int words = a.words;
@@ -1003,8 +1006,7 @@ __device__ __forceinline__ void bucket_slice(const GraphDev& g, const LevelArgs&
 }
 
 struct LevelStats {
-    unsigned long long chunks = 0, cas = 0, fresh = 0, hsims = 0, batches = 0, dealt = 0, live = 0,
-        bentries = 0, live32 = 0;
+    StatT chunks = 0, cas = 0, fresh = 0, hsims = 0, batches = 0, dealt = 0, live = 0, bentries = 0, live32 = 0;
 };
 
 // Clears the change bits read by the level before the previous one.
@@ -1241,33 +1243,27 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
 
 template <int MODE>
 __device__ __forceinline__ void flush_stats(const LevelArgs& a, LevelStats& ls) {
-    ls.chunks = wsum(ls.chunks);
-    ls.cas = wsum(ls.cas);
-    ls.fresh = wsum(ls.fresh);
-    ls.hsims = wsum(ls.hsims);
-    ls.batches = wsum(ls.batches);
-    ls.dealt = wsum(ls.dealt);
-    ls.live = wsum(ls.live);
-    ls.bentries = wsum(ls.bentries);
-    ls.live32 = wsum(ls.live32);
+    const unsigned long long chunks = wsum(ls.chunks), cas = wsum(ls.cas), fresh = wsum(ls.fresh),
+                             hsims = wsum(ls.hsims), batches = wsum(ls.batches), dealt = wsum(ls.dealt),
+                             live = wsum(ls.live), bentries = wsum(ls.bentries), live32 = wsum(ls.live32);
     if (lane_id() == 0) {
         if constexpr (MODE == kPush) {
-            if (ls.live32) atomicAdd(a.stats + kStSweepLive32, ls.live32);
-            if (ls.bentries) atomicAdd(a.stats + kStSweepBucketEntries, ls.bentries);
-            if (ls.live) atomicAdd(a.stats + kStSweepLiveEdges, ls.live);
-            if (ls.batches) atomicAdd(a.stats + kStSweepBatches, ls.batches);
-            if (ls.dealt) atomicAdd(a.stats + kStSweepDealt, ls.dealt);
-            if (ls.chunks) atomicAdd(a.stats + kStSweepChunks, ls.chunks);
-            if (ls.cas) atomicAdd(a.stats + kStSweepCas, ls.cas);
-            if (ls.hsims) atomicAdd(a.stats + kStSweepHeavySims, ls.hsims);
+            if (live32) atomicAdd(a.stats + kStSweepLive32, live32);
+            if (bentries) atomicAdd(a.stats + kStSweepBucketEntries, bentries);
+            if (live) atomicAdd(a.stats + kStSweepLiveEdges, live);
+            if (batches) atomicAdd(a.stats + kStSweepBatches, batches);
+            if (dealt) atomicAdd(a.stats + kStSweepDealt, dealt);
+            if (chunks) atomicAdd(a.stats + kStSweepChunks, chunks);
+            if (cas) atomicAdd(a.stats + kStSweepCas, cas);
+            if (hsims) atomicAdd(a.stats + kStSweepHeavySims, hsims);
         } else if constexpr (MODE == kCover) {
-            if (ls.chunks) atomicAdd(a.stats + kStCoverChunks, ls.chunks);
-            if (ls.fresh) {
-                atomicAdd(a.stats + kStCoverNew, ls.fresh);
-                atomicAdd(a.count, ls.fresh);
+            if (chunks) atomicAdd(a.stats + kStCoverChunks, chunks);
+            if (fresh) {
+                atomicAdd(a.stats + kStCoverNew, fresh);
+                atomicAdd(a.count, fresh);
             }
         } else {
-            if (ls.fresh) atomicAdd(a.stats + kStAffected, ls.fresh);
+            if (fresh) atomicAdd(a.stats + kStAffected, fresh);
         }
     }
     ls = LevelStats();
@@ -2218,7 +2214,7 @@ __global__ void __launch_bounds__(kFBlock) k_pull_affected(GraphDev g, LevelArgs
     __shared__ uint16_t sTab[kTabSize];
     load_sims(a.X, a.tab, a.J, sX, sTab);
     const int J = a.J, words = a.words;
-    unsigned long long n_cas = 0;
+    StatT n_cas = 0;
     walk_rows(loff, count, total, [&](int64_t f, int32_t row) {
         const int32_t u = chk(__ldg(list + row), g.n, a.err);
         const int64_t e = chk((int64_t)__ldg(g.rp_out + u) + (f - __ldg(loff + row)), g.m, a.err);
@@ -2269,7 +2265,7 @@ __global__ void __launch_bounds__(kFBlock) k_pull_buckets(LevelArgs a, const QEn
     const int J = a.J;
     const uint32_t C = (uint32_t)a.chunks;
     const int lane = (int)lane_id();
-    unsigned long long n_cas = 0;
+    StatT n_cas = 0;
     walk_rows_all([&](int32_t r) -> int64_t { return r < nq ? (int64_t)__ldg(&q[r].off) : total; }, nq, total,
                   [&](int64_t f, int32_t r, bool valid) {
         uint32_t cand[4] = {0u, 0u, 0u, 0u};

@@ -369,14 +369,16 @@ __device__ __forceinline__ bool is_picked(const uint32_t* seed_bits, int64_t v) 
 }
 
 // Full pick: S_u of every row (stored in lb when lazy picks follow).  Each
-// lane sums up to 4 consecutive 16-byte pieces of a row (LPR lanes a row,
-// 32 / LPR rows a warp step) and a warp issues the loads of kPickSteps steps
-// before summing any, so every warp keeps several KB of the stream in flight.
+// lane sums up to `tile` (1, 2 or 4: the J-tile width, a schedule knob)
+// consecutive 16-byte pieces of a row (LPR lanes a row, 32 / LPR rows a warp
+// step) and a warp issues the loads of kPickSteps steps before summing any,
+// so every warp keeps several KB of the stream in flight.
 constexpr int kPickSteps = 2;
 constexpr int kLazySteps = 4;
-__device__ __forceinline__ void pick_layout(int J, int& cpl, int& lpr, int& rpw) {
+__host__ __device__ __forceinline__ void pick_layout(int J, int tile, int& cpl, int& lpr, int& rpw) {
     const int cpr = J >> 4;
-    cpl = cpr < 4 ? cpr : 4;
+    const int tl = tile == 1 || tile == 2 ? tile : 4;
+    cpl = cpr < tl ? cpr : tl;
     lpr = cpr / cpl;
     rpw = 32 / lpr;
 }
@@ -384,7 +386,7 @@ __device__ __forceinline__ void pick_layout(int J, int& cpl, int& lpr, int& rpw)
 __global__ void __launch_bounds__(kBlock) k_pick(PickArgs a) {
     const int J = a.J;
     int cpl, lpr, rpw;
-    pick_layout(J, cpl, lpr, rpw);
+    pick_layout(J, a.tile, cpl, lpr, rpw);
     const int lane = (int)lane_id();
     const int seg = lane / lpr, seg_lane = lane % lpr;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -479,10 +481,9 @@ __global__ void __launch_bounds__(kBlock) k_pick_lazy(PickArgs a) {
     pick_finish(a, t);
 }
 
-int pick_grid(int32_t n, int J) {
-    const int cpr = J / 16;
-    const int cpl = cpr < 4 ? cpr : 4;
-    const int rpw = 32 / (cpr / cpl);
+int pick_grid(int32_t n, int J, int tile) {
+    int cpl, lpr, rpw;
+    pick_layout(J, tile, cpl, lpr, rpw);
     const int64_t rows_per_block = (int64_t)rpw * kPickSteps * kWarpsPerBlock;
     int64_t grid = (n + rows_per_block - 1) / rows_per_block;
     if (grid > 152 * 8) grid = 152 * 8;
@@ -491,7 +492,7 @@ int pick_grid(int32_t n, int J) {
 }
 
 cudaError_t launch_pick(const PickArgs& a, cudaStream_t st) {
-    k_pick<<<pick_grid(a.n, a.J), kBlock, 0, st>>>(a);
+    k_pick<<<pick_grid(a.n, a.J, a.tile), kBlock, 0, st>>>(a);
     return cudaGetLastError();
 }
 

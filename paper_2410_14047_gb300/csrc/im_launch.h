@@ -206,9 +206,12 @@ struct PickArgs {
     const uint32_t* bk_end_out;
     int32_t chunks;
     uint32_t* nv;                 // registers newly visited since the last build (may be NULL)
+    int tile;                     // J-tile width of a full pick: 16-byte pieces a lane sums (1, 2, 4)
 };
 
-int pick_grid(int32_t n, int J);
+// Blocks of a full pick: one row group per warp step, at most 152 * 8; tile
+// = 16-byte pieces of a row a lane sums (1, 2 or 4; other values: 4).
+int pick_grid(int32_t n, int J, int tile = 4);
 int pick_lazy_grid(int32_t n);
 
 cudaError_t launch_sims(uint64_t seed, int J, uint32_t* X, uint32_t* salt, uint16_t* tab,

@@ -79,6 +79,7 @@ extern "C" im_status im_argmax_noalloc(const uint8_t* M, int32_t n, int32_t J, u
     a.out_est = est_out;
     a.k = 0;
     a.mark = 0;
+    a.tile = 4;  // the grid pick_grid(n, J) sized above
     if (im::launch_pick(a, st) != cudaSuccess) return IM_E_CUDA;
     return IM_OK;
 }

@@ -302,7 +302,8 @@ def test_errors(im, ctx):
                                     {"incremental": 0}, {"incremental": 2, "buckets": 0, "persistent": 0},
                                     {"incremental": 1, "buckets": 1024, "persistent": 0},
                                     {"chain": 0}, {"chain": 64, "buckets": 1024},
-                                    {"chain": 1, "buckets": 1024, "persistent": 0, "light_batches": 1}])
+                                    {"chain": 1, "buckets": 1024, "persistent": 0, "light_batches": 1},
+                                    {"pick_tile": 1, "lazy_pick": 0}, {"pick_tile": 2}])
 @pytest.mark.parametrize("gname,mname,J", [("rmat12", "wc", 256), ("cl5k", "p01", 64),
                                            ("er2k", "wc", 1024), ("rmat12", "tri", 32)])
 def test_tuning_does_not_change_results(im, ctx, tuning, gname, mname, J):

@@ -170,7 +170,9 @@ class Workload:
 
 
 def workload(name: str) -> Workload:
-    """The plain-method workloads: er10k (tiny), rmat20 (mid), rmat24 (large)."""
+    """The plain-method workloads: er10k (tiny), rmat20 (mid), rmat24 (large);
+    rmat22 is the large workload's shape at a quarter of its size (profiling
+    captures that must stay within a few GB of device memory)."""
     if name == "er10k":
         return Workload("er10k: ER n=10000 m=100000, IC p=0.01, J=64, K=10",
                         lambda: erdos_renyi(10_000, 100_000, seed=2410),
@@ -181,6 +183,10 @@ def workload(name: str) -> Workload:
     if name == "rmat24":
         return Workload("rmat24: R-MAT scale 24 ef 16 (0.57/0.19/0.19), trivalency, J=512, K=50",
                         lambda: rmat(24, 16, seed=2410), {"kind": "trivalency", "seed": 2410},
+                        J=512, K=50)
+    if name == "rmat22":
+        return Workload("rmat22: R-MAT scale 22 ef 16 (0.57/0.19/0.19), trivalency, J=512, K=50",
+                        lambda: rmat(22, 16, seed=2410), {"kind": "trivalency", "seed": 2410},
                         J=512, K=50)
     raise KeyError(name)
 
