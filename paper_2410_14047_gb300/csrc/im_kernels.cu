@@ -377,7 +377,10 @@ constexpr int kPickSteps = 2;
 constexpr int kLazySteps = 4;
 __host__ __device__ __forceinline__ void pick_layout(int J, int tile, int& cpl, int& lpr, int& rpw) {
     const int cpr = J >> 4;
-    const int tl = tile == 1 || tile == 2 ? tile : 4;
+    // at most 32 lanes a row: a row of 64 pieces (J = 1024) takes 2 a lane at least
+    const int least = (cpr + 31) >> 5;
+    int tl = tile == 1 || tile == 2 ? tile : 4;
+    if (tl < least) tl = least;
     cpl = cpr < tl ? cpr : tl;
     lpr = cpr / cpl;
     rpw = 32 / lpr;
