@@ -104,17 +104,21 @@ def alg_bytes_terms(st: dict, J: int, model_kind: str) -> dict:
     frontier vertex 8 (row bounds) + J (its register row), per examined in-edge
     4 (endpoint) + t (a stored per-edge threshold: explicit weights only; the
     other models' thresholds are per target or recomputed), per changed vertex
-    J (its row written), per (edge, 32-simulation chunk) with a live,
-    non-visited simulation 32 (the neighbour's 32 register bytes).  Levels on
-    (vertex, 16-simulation chunk) buckets count the same at 16-simulation
-    granularity: per queued bucket 8 + 16, per list entry 4 + t + 16, per
-    changed bucket 16.  Hubs pushed by per-simulation hash search are not
-    counted (their edges are searched, not read)."""
+    J (its row written), per live chunk 1 byte per simulation of the chunk
+    (the neighbour's register bytes: 32 per 32-simulation chunk), counted at
+    the 16-simulation granularity the kernels work in: 16 per (edge,
+    16-simulation chunk) with a simulation where the edge is live, the source
+    changed and its register is not visited (a 32-simulation chunk with one
+    such half counts 16, not 32).  Levels on (vertex, 16-simulation chunk)
+    buckets count the same at 16-simulation granularity: per queued bucket
+    8 + 16, per list entry 4 + t + 16, per changed bucket 16.  Hubs pushed by
+    per-simulation hash search are not counted (their edges are searched, not
+    read)."""
     t = 4 if model_kind == "explicit" else 0
-    per_unit = {"frontier_vertices": 8 + J, "in_edges": 4 + t, "changed_vertices": J, "live_32sim_chunks": 32,
+    per_unit = {"frontier_vertices": 8 + J, "in_edges": 4 + t, "changed_vertices": J, "live_16sim_chunks": 16,
                 "frontier_buckets": 8 + 16, "bucket_entries": 4 + t + 16, "changed_buckets": 16}
     units = {"frontier_vertices": st["sweep_vertices"], "in_edges": st["sweep_edges"],
-             "changed_vertices": st["sweep_changed"], "live_32sim_chunks": st["sweep_live32"],
+             "changed_vertices": st["sweep_changed"], "live_16sim_chunks": st["sweep_chunks"],
              "frontier_buckets": st["sweep_buckets"], "bucket_entries": st["sweep_bucket_entries"],
              "changed_buckets": st["sweep_changed_buckets"]}
     return {"bytes": sum(units[k] * per_unit[k] for k in units), "units": units, "per_unit": per_unit}
@@ -596,8 +600,9 @@ def run_gpu(args):
         im.im_ctx_set_trace(ctx, False)
         phases, cur = [], None
         for rec in tr:
-            if rec["level"] == 0 or cur is None or rec["kind"] != cur["kind"]:
-                cur = {"kind": ["propagate", "cover", "affect"][int(rec["kind"])], "levels": []}
+            kind = ["propagate", "cover", "affect"][int(rec["kind"])]
+            if rec["level"] == 0 or cur is None or kind != cur["kind"]:
+                cur = {"kind": kind, "levels": []}
                 phases.append(cur)
             cur["levels"].append([int(rec["count"]), int(rec["edges"]), round(float(rec["ms"]), 4)])
         summary = {}
@@ -610,9 +615,9 @@ def run_gpu(args):
             print(json.dumps({"mode": "trace", "workload": wl.name, "seeds": r["seeds"].tolist()[:8],
                               "summary": summary,
                               "propagation_phases": [p["levels"] for p in phases if p["kind"] == "propagate"],
-                              "largest_covers": sorted(([sum(x[2] for x in p["levels"]), len(p["levels"])]
+                              "largest_covers": sorted(([round(sum(x[2] for x in p["levels"]), 4), p["levels"]]
                                                         for p in phases if p["kind"] == "cover"),
-                                                       reverse=True)[:10],
+                                                       key=lambda x: -x[0])[:3],
                               "stats": {k: st[k] for k in ("ms_propagate", "ms_cover_kernels", "ms_pick_kernels",
                                                            "ms_fill_kernels", "builds", "sweeps",
                                                            "cover_levels")}}), flush=True)
@@ -641,7 +646,7 @@ def run_gpu(args):
     agg = {"alg_bytes_sweep": 0, "ms_propagate": 0.0, "sweep_launches": 0, "launches": 0,
            "builds": 0, "sweeps": 0, "ms_pick_kernels": 0.0, "ms_cover_kernels": 0.0,
            "ms_fill_kernels": 0.0, "cover_levels": 0, "sweep_edges": 0, "sweep_bucket_entries": 0,
-           "sweep_vertices": 0, "sweep_changed": 0, "sweep_live32": 0, "sweep_buckets": 0,
+           "sweep_vertices": 0, "sweep_changed": 0, "sweep_chunks": 0, "sweep_buckets": 0,
            "sweep_changed_buckets": 0, "sweep_heavy": 0, "sweep_heavy_sims": 0}
     deterministic = True
     ev0.record(stream)

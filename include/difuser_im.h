@@ -102,7 +102,9 @@ typedef struct {
     int64_t cover_levels;     /* cover level launches that had work */
     uint64_t sweep_vertices;  /* queue entries processed by all sweeps */
     uint64_t sweep_edges;     /* in-edges examined by all sweeps */
-    uint64_t sweep_chunks;    /* 16-simulation chunks with >= 1 live, non-visited source register */
+    uint64_t sweep_chunks;    /* (in-edge, 16-simulation chunk) pairs of vertex-format propagation
+                                 levels with a simulation where the edge is live, the source
+                                 changed and its register is not visited */
     uint64_t sweep_cas;       /* 4-register words written by atomic CAS (improvements) */
     uint64_t sweep_changed;   /* vertices whose registers a propagation level changed (vertex-format
                                  levels: the queued vertices of every level after the first) */
@@ -125,9 +127,6 @@ typedef struct {
     uint64_t pull_entries;    /* out-bucket entries walked by those pulls */
     uint64_t sweep_changed_buckets; /* (vertex, 16-simulation chunk) buckets whose registers a
                                  propagation level changed (bucket-format levels) */
-    uint64_t sweep_live32;    /* (in-edge, 32-simulation chunk) pairs of vertex-format propagation
-                                 levels with a simulation where the edge is live, the source
-                                 changed and its register is not visited */
 } im_stats;
 
 /* Schedule knobs of the frontier kernels (chosen by the autotuner; results
@@ -160,7 +159,10 @@ typedef struct {
  * level (0 = off): chains of small buckets advance several hops a level;
  * pick_tile: the J-tile width of a full estimate + argmax pass, the 16-byte
  * register pieces (16 simulations each) one lane sums per row: 1, 2 or 4
- * (0 = 4); fewer pieces a lane means more lanes per row. */
+ * (0 = 4); fewer pieces a lane means more lanes per row; dense_out: 1 = a
+ * propagation level that walks every vertex (dense_div) records what it raises
+ * in the change bits only, without a queue, while the frontier stays large
+ * (the next level walks every vertex again), 0 = every level builds a queue. */
 typedef struct {
     int32_t heavy_indeg;
     int32_t light_batches;
@@ -173,6 +175,7 @@ typedef struct {
     int32_t incremental;
     int32_t chain;
     int32_t pick_tile;
+    int32_t dense_out;
 } im_tuning;
 
 /* One frontier launch of the last selection / build (tracing on). */
@@ -206,7 +209,7 @@ IM_API im_status im_last_stats(const im_ctx* ctx, im_stats* out);
  * stream and report per-kind kernel time in im_stats (adds two event records
  * per launch).  Off by default. */
 IM_API im_status im_ctx_set_timing(im_ctx* ctx, int enable);
-/* Sets (NULL = defaults {256, 4, 0, 2, 1, 0, 1, 2, 1, 8, 4}) or reads the schedule knobs. */
+/* Sets (NULL = defaults {256, 4, 0, 2, 1, 0, 1, 2, 1, 8, 4, 1}) or reads the schedule knobs. */
 IM_API im_status im_ctx_set_tuning(im_ctx* ctx, const im_tuning* tuning);
 IM_API im_status im_ctx_get_tuning(const im_ctx* ctx, im_tuning* tuning);
 /* Bounds of the waits inside the device code, so that a loop that should end

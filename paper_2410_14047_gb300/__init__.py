@@ -71,7 +71,7 @@ class im_stats(ctypes.Structure):
                                                "sweep_dealt", "sweep_edges_live", "sweep_buckets",
                                                "sweep_bucket_entries", "affected",
                                                "pull_buckets", "pull_entries",
-                                               "sweep_changed_buckets", "sweep_live32")]
+                                               "sweep_changed_buckets")]
 
 
 class im_tuning(ctypes.Structure):
@@ -79,7 +79,7 @@ class im_tuning(ctypes.Structure):
                 ("grid_blocks", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("persistent", ctypes.c_int32), ("dense_div", ctypes.c_int32),
                 ("lazy_pick", ctypes.c_int32), ("buckets", ctypes.c_int32), ("incremental", ctypes.c_int32),
-                ("chain", ctypes.c_int32), ("pick_tile", ctypes.c_int32)]
+                ("chain", ctypes.c_int32), ("pick_tile", ctypes.c_int32), ("dense_out", ctypes.c_int32)]
 
 
 class im_trace_rec(ctypes.Structure):

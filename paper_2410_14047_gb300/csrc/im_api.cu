@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -46,7 +47,7 @@ struct im_ctx {
     bool trace = false;
     std::vector<float> launch_ms;    // kernel time per launch sequence number (tracing)
     std::vector<im_trace_rec> recs;  // frontier launches of the last call
-    im_tuning tuning{256, 4, 0, 2, 1, 0, 1, 2, 1, 8, 4};
+    im_tuning tuning{256, 4, 0, 2, 1, 0, 1, 2, 1, 8, 4, 1};
     // bounds of the device-side waits (im_ctx_set_limits)
     uint64_t barrier_limit_ns = kDefaultBarrierLimitNs;
     int32_t max_levels = kMaxLevels - 2;
@@ -320,14 +321,15 @@ extern "C" im_status im_ctx_set_timing(im_ctx* c, int enable) {
 extern "C" im_status im_ctx_set_tuning(im_ctx* c, const im_tuning* t) {
     if (!c) return IM_E_INVAL;
     if (!t) {
-        c->tuning = im_tuning{256, 4, 0, 2, 1, 0, 1, 2, 1, 8, 4};
+        c->tuning = im_tuning{256, 4, 0, 2, 1, 0, 1, 2, 1, 8, 4, 1};
         return IM_OK;
     }
     if (t->heavy_indeg < 0 || t->light_batches < 1 || t->light_batches > 4096 || t->grid_blocks < 0 ||
         t->check_every < 1 || t->check_every > 64 || t->persistent < 0 || t->persistent > 1 ||
         t->dense_div < 0 || t->lazy_pick < 0 || t->lazy_pick > 1 || t->buckets < 0 || t->buckets > 1024 || t->incremental < 0 || t->incremental > 2 ||
         t->chain < 0 || t->chain > 64 ||
-        !(t->pick_tile == 0 || t->pick_tile == 1 || t->pick_tile == 2 || t->pick_tile == 4))
+        !(t->pick_tile == 0 || t->pick_tile == 1 || t->pick_tile == 2 || t->pick_tile == 4) ||
+        t->dense_out < 0 || t->dense_out > 1)
         return fail(c, IM_E_INVAL, "tuning out of range");
     c->tuning = *t;
     return IM_OK;
@@ -446,6 +448,64 @@ static im_status set_model(im_graph* g, const im_model* mdl) {
     return IM_OK;
 }
 
+// Validation of a host CSR: rows [r0, r1) ascending, ids in range, no
+// self-loops, rows strictly ascending.  Returns the first bad row (r1 if
+// none) and writes its error.
+static int32_t check_rows(int32_t n, const int32_t* rowptr, const int32_t* col, int32_t r0, int32_t r1,
+                          im_status* st, char* msg, size_t cap) {
+    for (int32_t u = r0; u < r1; ++u) {
+        const int32_t b = rowptr[u], e = rowptr[u + 1];
+        if (e < b) { *st = IM_E_INVAL; snprintf(msg, cap, "rowptr decreases at %d", u); return u; }
+        for (int32_t i = b; i < e; ++i) {
+            const int32_t v = col[i];
+            if (v < 0 || v >= n) { *st = IM_E_RANGE; snprintf(msg, cap, "col[%d] = %d out of range", i, v); return u; }
+            if (v == u) { *st = IM_E_INVAL; snprintf(msg, cap, "self-loop at vertex %d", u); return u; }
+            if (i > b && col[i - 1] >= v) {
+                *st = IM_E_INVAL;
+                snprintf(msg, cap, "row %d not strictly ascending (duplicate edge?)", u);
+                return u;
+            }
+        }
+    }
+    return r1;
+}
+
+// The same over all rows, split by row ranges over host threads on large
+// graphs (the lowest bad row is reported, as a single pass would).  rowptr
+// is first checked to be non-decreasing, so every range's edges are in
+// [0, m).
+static im_status check_csr(im_ctx* c, int32_t n, int64_t m, const int32_t* rowptr, const int32_t* col) {
+    for (int32_t u = 0; u < n; ++u)
+        if (rowptr[u + 1] < rowptr[u]) return fail(c, IM_E_INVAL, "rowptr decreases at %d", u);
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int T = m < (1 << 22) ? 1 : (int)std::max(1u, std::min(hw, 32u));
+    std::vector<int32_t> bad(T, n);
+    std::vector<im_status> sts(T, IM_OK);
+    std::vector<std::string> msgs(T);
+    auto run = [&](int t) {
+        // rows whose first edge falls in the t-th share of the edges
+        auto first_row = [&](int64_t edge) {
+            return (int32_t)(std::upper_bound(rowptr, rowptr + n + 1, (int32_t)edge) - rowptr - 1);
+        };
+        const int32_t r0 = t == 0 ? 0 : std::max(first_row(m * t / T) + 1, 0);
+        const int32_t r1 = t == T - 1 ? n : std::max(first_row(m * (t + 1) / T) + 1, 0);
+        if (r1 <= r0) return;
+        char buf[256];
+        const int32_t b = check_rows(n, rowptr, col, r0, std::min(r1, n), &sts[t], buf, sizeof buf);
+        if (b < std::min(r1, n)) { bad[t] = b; msgs[t] = buf; }
+    };
+    if (T == 1) {
+        run(0);
+    } else {
+        std::vector<std::thread> th;
+        for (int t = 0; t < T; ++t) th.emplace_back(run, t);
+        for (auto& x : th) x.join();
+    }
+    for (int t = 0; t < T; ++t)
+        if (bad[t] < n) return fail(c, sts[t], "%s", msgs[t].c_str());
+    return IM_OK;
+}
+
 static im_status graph_load_impl(im_ctx* c, int32_t n, int64_t m, const int32_t* rowptr,
                                  const int32_t* col, const im_model* model, const int32_t* hkey_host,
                                  im_graph** out) {
@@ -454,17 +514,7 @@ static im_status graph_load_impl(im_ctx* c, int32_t n, int64_t m, const int32_t*
     if (m < 0 || m >= (1ll << 31)) return fail(c, IM_E_RANGE, "m must be in [0, 2^31)");
     CKS(check_model(c, model, m));
     if (rowptr[0] != 0 || rowptr[n] != m) return fail(c, IM_E_INVAL, "rowptr[0] != 0 or rowptr[n] != m");
-    for (int32_t u = 0; u < n; ++u) {
-        const int32_t b = rowptr[u], e = rowptr[u + 1];
-        if (e < b) return fail(c, IM_E_INVAL, "rowptr decreases at %d", u);
-        for (int32_t i = b; i < e; ++i) {
-            const int32_t v = col[i];
-            if (v < 0 || v >= n) return fail(c, IM_E_RANGE, "col[%d] = %d out of range", i, v);
-            if (v == u) return fail(c, IM_E_INVAL, "self-loop at vertex %d", u);
-            if (i > b && col[i - 1] >= v)
-                return fail(c, IM_E_INVAL, "row %d not strictly ascending (duplicate edge?)", u);
-        }
-    }
+    CKS(check_csr(c, n, m, rowptr, col));
     CK(c, cudaSetDevice(c->device));
     im_graph* g = new im_graph();
     g->ctx = c;
@@ -749,6 +799,7 @@ static LevelArgs level_args(im_sketch* sk) {
     a.n_dense = sk->g->n_dense;
     a.e_dense = sk->g->m;
     a.dense_div = sk->gflag ? 0 : t.dense_div;  // a batch build covers only some graphs
+    a.dense_out = t.dense_out;
     a.gid = sk->gid;
     a.gcount = sk->gcount;
     a.gflag = sk->gflag;
@@ -1155,7 +1206,6 @@ static im_status stats_collect(im_sketch* sk) {
     s.pull_buckets = h[kStPullBuckets];
     s.pull_entries = h[kStPullEntries];
     s.sweep_changed_buckets = h[kStSweepChangedBuckets];
-    s.sweep_live32 = h[kStSweepLive32];
     // algorithmic bytes of the sweeps: queue entry (16 B) + the queued vertex's
     // register row (J B) per queued vertex; live chunk mask (4 B, 8 B when
     // J = 1024) per in-edge; source id + edge hash (8 B, + 4 B threshold for

@@ -350,6 +350,23 @@ __device__ __forceinline__ void bucket_enqueue_finish(const LevelArgs& a, bool c
                   a.bq_cap, a.bq_guard != 0);
 }
 
+// Dense-format output (a propagation level that walks every vertex, while the
+// frontier stays large): a raised register only sets its change bits (no
+// reply needed), and the lane counts its raised items; no queue entry, no
+// enqueue stamp, no row words.  Each warp adds its count to the next level's
+// counter once, at the end of the level (dense_count_flush).  The next level
+// walks every vertex again and reads the change bits.
+__device__ __forceinline__ void dense_enqueue_issue(const LevelArgs& a, int32_t o, uint32_t c, uint32_t imp) {
+    if (imp) atomicOr(a.chg_next + (size_t)o * a.words + (c >> 1), imp << ((c & 1u) * 16u));
+}
+
+__device__ __forceinline__ void dense_count_flush(const LevelArgs& a, StatT n) {
+    unsigned long long s = n;
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, k);
+    if (s && lane_id() == 0) atomicAdd(a.cl_out, s << kCountShift);
+}
+
 // ---------------------------------------------------------------------------
 // Light units: a slice of 32-edge batches of the flat edge space.
 // ---------------------------------------------------------------------------
@@ -360,8 +377,8 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                                             int64_t El, StatT& st_chunks,
                                             StatT& st_cas, StatT& st_new,
                                             StatT& st_batches, StatT& st_dealt,
-                                            StatT& st_live, StatT& st_live32,
-                                            bool skip_heavy, uint32_t (*sKeep)[kKeepWords], bool out_b) {
+                                            StatT& st_live, bool skip_heavy, uint32_t (*sKeep)[kKeepWords], bool out_b,
+                                            bool out_d, StatT* st_chg, StatT& st_draised) {
     const int lane = (int)lane_id();
     const int J = a.J, words = a.words;
     const int64_t fend = min(El, b1 << 5);
@@ -417,6 +434,9 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
         __syncwarp();
         if (!a.all_changed && used)
             chunk_change_mask(a.chg_cur, chk(raw.x, g.n, a.err), words, cm_lo, cm_hi, sKeep[lane]);
+        // a walk over every vertex counts the changed ones (the previous
+        // level's output had no queue): once each, where its row starts
+        if (st_chg && used && rel >= 0 && (cm_lo | cm_hi) != 0u) ++*st_chg;
         if constexpr (MODE == kPush) {
             // dense walk: the heavy queue pushes the hubs
             if (skip_heavy && used) {
@@ -449,10 +469,6 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
         const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
         const int excl = incl - nch;
         if (lane == 0) { ++st_batches; st_dealt += (unsigned)total; }
-        // the previous item (edge, chunk, raised anything) for the count of
-        // 32-simulation chunks: an odd chunk whose even partner of the same
-        // edge came just before and was counted is not counted again
-        uint32_t carry = 0xFFFFFFFFu;
         for (int base = 0; base < total; base += 32) {
             const int k = base + lane;
             int i = 0;
@@ -503,8 +519,9 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                     }
                     if constexpr (MODE == kAffect) imp = mark_affected(a, cand, o_i, (uint32_t)chunk, st_new);
                     // the enqueue's loads and atomics go out before the register update
-                    eq = out_b ? bucket_enqueue_issue(a, o_i, (uint32_t)chunk, imp)
-                               : vertex_enqueue_issue<KIND, MODE>(g, a, o_i, (uint32_t)chunk, imp);
+                    if (out_d) dense_enqueue_issue(a, o_i, (uint32_t)chunk, imp);
+                    else eq = out_b ? bucket_enqueue_issue(a, o_i, (uint32_t)chunk, imp)
+                                    : vertex_enqueue_issue<KIND, MODE>(g, a, o_i, (uint32_t)chunk, imp);
                     if (MODE != kAffect && any) {
                         ++st_chunks;
                         if constexpr (MODE == kPush) {
@@ -529,17 +546,9 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                 }
             }
             (void)nbits;
-            if constexpr (MODE == kPush) {
-                const uint32_t tag = k < total ? ((uint32_t)i << 7 | (uint32_t)chunk << 1 | (any ? 1u : 0u))
-                                               : 0xFFFFFFFFu;
-                uint32_t ptag = __shfl_up_sync(0xFFFFFFFFu, tag, 1);
-                if (lane == 0) ptag = carry;
-                carry = __shfl_sync(0xFFFFFFFFu, tag, 31);
-                const bool partner = (chunk & 1) && ptag == (((uint32_t)i << 7) | ((uint32_t)(chunk - 1) << 1) | 1u);
-                if (k < total && any && !partner) ++st_live32;
-            }
             // enqueue what changed: the vertex, or its chunk's bucket
-            if (out_b) bucket_enqueue_finish(a, imp != 0u, o_i, (uint32_t)chunk, eq);
+            if (out_d) st_draised += imp != 0u ? 1u : 0u;
+            else if (out_b) bucket_enqueue_finish(a, imp != 0u, o_i, (uint32_t)chunk, eq);
             else vertex_enqueue_finish<KIND, MODE>(g, a, imp != 0u, o_i, eq);
         }
         qi = qn;
@@ -1006,7 +1015,7 @@ __device__ __forceinline__ void bucket_slice(const GraphDev& g, const LevelArgs&
 }
 
 struct LevelStats {
-    StatT chunks = 0, cas = 0, fresh = 0, hsims = 0, batches = 0, dealt = 0, live = 0, bentries = 0, live32 = 0;
+    StatT chunks = 0, cas = 0, fresh = 0, hsims = 0, batches = 0, dealt = 0, live = 0, bentries = 0, chg = 0;
 };
 
 // Clears the change bits read by the level before the previous one.
@@ -1014,7 +1023,13 @@ __device__ __forceinline__ void clear_prev_bits(const LevelArgs& a, int64_t warp
     if (!a.chg_prev) return;
     const int lane = (int)lane_id();
     const int32_t nlp = a.cl_prev ? (int32_t)(__ldcg(a.cl_prev) >> kCountShift) : 0;
-    if (a.fmt_prev && __ldcg(a.fmt_prev) != 0) {
+    if (a.fmt_prev && __ldcg(a.fmt_prev) == kFmtDense) {
+        // a level without a queue (dense format): every change word
+        const int64_t nw = (int64_t)a.vq_cap * a.words;
+        for (int64_t i = warp * 32 + lane; i < nw; i += nwarps * 32) a.chg_prev[i] = 0u;
+        return;
+    }
+    if (a.fmt_prev && __ldcg(a.fmt_prev) == kFmtBucket) {
         // bucket queue: each entry owns the 16 change bits of its chunk; a
         // queue that overflowed (its level walked every bucket) clears all
         const bool overflow = nlp > a.bq_cap || (a.ch_prev && __ldcg(a.ch_prev) != 0ull);
@@ -1048,11 +1063,17 @@ struct ClearPlan {
 };
 
 __device__ __forceinline__ ClearPlan clear_plan(const LevelArgs& a, unsigned long long pl, unsigned long long ph,
-                                                bool pb) {
+                                                int pfmt) {
     ClearPlan c;
     if (!a.chg_prev) return c;
     const int32_t nlp = (int32_t)(pl >> kCountShift);
-    if (pb) {
+    if (pfmt == kFmtDense) {
+        c.mode = 3;
+        c.n = (int64_t)a.vq_cap * a.words;
+        c.units = (c.n + 1023) >> 10;
+        return c;
+    }
+    if (pfmt == kFmtBucket) {
         if (nlp > a.bq_cap || ph != 0ull) {
             c.mode = 3;
             c.n = (int64_t)a.nbuckets / a.chunks * a.words;
@@ -1113,12 +1134,15 @@ struct UnitCursor {
 };
 
 // Work of one level: heavy vertices first, then slices of light batches, taken through
-// a UnitCursor.
-template <int KIND, int MODE>
+// a UnitCursor.  BK: the sketch may have bucketed lists (false: edge scans
+// only, so the bucket code is compiled out and the scan loops keep more
+// registers).
+template <int KIND, int MODE, bool BK>
 __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a, const uint32_t* sX,
                                            const uint16_t* sTab, int64_t warp, LevelStats& ls,
                                            uint32_t (*sKeep)[kKeepWords], unsigned long long cl,
-                                           unsigned long long ch, bool in_b, const ClearPlan& cp) {
+                                           unsigned long long ch, int in_fmt, const ClearPlan& cp) {
+    const bool in_b = in_fmt == kFmtBucket;
     const int lane = (int)lane_id();
     // output format: bucket entries once the level's input work is small
     // against the graph (the bucketed lists then skip the edges of unchanged
@@ -1126,10 +1150,11 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
     auto out_bucket = [&](int64_t work) {
         // the affected-set search is sparse in simulations: bucket queues
         // whenever the sketch has the lists
+        if (!BK) return false;
         if (MODE == kAffect) return a.bk_end != nullptr;
         return a.bk_end != nullptr && a.bucket_div > 0 && work * a.bucket_div < g.m;
     };
-    if (in_b) {
+    if (BK && in_b) {
         // the queue's buckets, or every bucket when the queue overflowed
         // (ch = overflow word)
         const int32_t nq = (int32_t)(cl >> kCountShift);
@@ -1176,20 +1201,34 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
     int32_t nh = (int32_t)(ch >> kCountShift);
     const QEntry* ql = a.ql_in;
     // dense level: walk every vertex with in-edges in vertex order (contiguous
-    // in-CSR reads); vertices without changed simulations produce no chunks
-    bool dense = false;
+    // in-CSR reads); vertices without changed simulations produce no chunks.
+    // A dense-format input (no queue: its count is the raised items) is always
+    // walked this way.
+    const bool in_d = MODE == kPush && in_fmt == kFmtDense;
+    bool dense = in_d;
     if (MODE == kPush && a.q_dense && a.dense_div > 0 && (nl + nh) > 0 &&
-        ((int64_t)(nl + nh) * a.dense_div > (int64_t)a.n_dense || a.all_changed)) {
+        ((int64_t)(nl + nh) * a.dense_div > (int64_t)a.n_dense || a.all_changed))
+        dense = true;
+    // the output of a dense walk stays in dense format while the frontier is
+    // large: the input's vertices (or, after a dense-format level, its raised
+    // items, several per vertex) above n_dense / dense_div
+    bool out_d = false;
+    if (MODE == kPush && dense && a.dense_out)
+        out_d = in_d ? (int64_t)nl * a.dense_div > 4 * (int64_t)a.n_dense : true;
+    if (dense) {
         ql = a.q_dense;
         nl = a.n_dense;
         El = a.e_dense;
-        dense = true;
+        if (in_d) nh = 0;
     }
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     // a small level scans the hubs' in-edges as a second flat edge space
     // (split over many warps) instead of searching per changed simulation:
     // the searches' chains of dependent loads would set the level's latency
-    const int64_t Eh = (int64_t)(ch & kEdgeMask);
+    const int64_t Eh = in_d ? 0 : (int64_t)(ch & kEdgeMask);
+    // a dense-format output scans the hubs' in-edges in the walk (the hub path
+    // would enqueue them), so the heavy queue is not used then
+    if (out_d && nh > 0) nh = 0;
     const bool hscan = MODE == kPush && nh > 0 && El + Eh <= nwarps * 32 * 4;
     const int64_t nbl = (El + 31) >> 5;
     const int64_t nbh = hscan ? (Eh + 31) >> 5 : 0;
@@ -1200,20 +1239,22 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
     const int64_t hunits = (nbh + lb - 1) / lb;
     const int64_t nhv = hscan ? 0 : (int64_t)nh;  // hubs searched per changed simulation
     const int64_t total = nhv + lunits + hunits;
-    const bool out_b = out_bucket(El + Eh);
-    if (a.fmt_out && blockIdx.x == 0 && threadIdx.x == 0) *a.fmt_out = out_b ? 1 : 0;
+    const bool out_b = !out_d && out_bucket(El + Eh);
+    if (a.fmt_out && blockIdx.x == 0 && threadIdx.x == 0) *a.fmt_out = out_d ? kFmtDense : (out_b ? kFmtBucket : kFmtVertex);
     if (total + cp.units == 0) return;
     if (warp == 0 && lane == 0) {
         atomicAdd(a.stats + (MODE == kPush ? kStSweepVertices : kStCoverVertices),
                   (unsigned long long)(nl + nh));
         // the input of a level after the first: the vertices the previous
-        // level changed (the queues' own counts, also on a dense walk)
-        if (MODE == kPush && a.cl_prev)
+        // level changed (the queues' own counts, also on a dense walk; after
+        // a dense-format level the walk counts them)
+        if (MODE == kPush && a.cl_prev && !in_d)
             atomicAdd(a.stats + kStSweepChanged, (cl >> kCountShift) + (ch >> kCountShift));
         atomicAdd(a.stats + (MODE == kPush ? kStSweepEdges : kStCoverEdges), (unsigned long long)(El + (hscan ? Eh : 0)));
         atomicAdd(a.stats + (MODE == kPush ? kStSweepLevels : kStCoverLevels), 1ull);
         if (MODE == kPush) atomicAdd(a.stats + kStSweepHeavy, (unsigned long long)nhv);
     }
+    StatT draised = 0;  // raised items of a dense-format output
     for (UnitCursor uc(total + cp.units); uc.valid(); uc.next(a.claim)) {
         const int64_t unit = uc.unit;
         if (unit >= total) {
@@ -1230,25 +1271,27 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
             const int64_t b0 = lu * lb;
             const int64_t b1 = min(nbl, b0 + lb);
             light_slice<KIND, MODE>(g, a, ql, sX, sTab, b0, b1, nl, El, ls.chunks, ls.cas, ls.fresh,
-                                    ls.batches, ls.dealt, ls.live, ls.live32, dense && nh > 0, sKeep, out_b);
+                                    ls.batches, ls.dealt, ls.live, dense && nh > 0, sKeep, out_b, out_d,
+                                    in_d ? &ls.chg : nullptr, draised);
         } else {
             const int64_t hu = (int64_t)unit - nhv - lunits;
             const int64_t b0 = hu * lb;
             const int64_t b1 = min(nbh, b0 + lb);
             light_slice<KIND, MODE>(g, a, a.qh_in, sX, sTab, b0, b1, nh, Eh, ls.chunks, ls.cas, ls.fresh,
-                                    ls.batches, ls.dealt, ls.live, ls.live32, false, sKeep, out_b);
+                                    ls.batches, ls.dealt, ls.live, false, sKeep, out_b, false, nullptr, draised);
         }
     }
+    if (out_d) dense_count_flush(a, draised);
 }
 
 template <int MODE>
 __device__ __forceinline__ void flush_stats(const LevelArgs& a, LevelStats& ls) {
     const unsigned long long chunks = wsum(ls.chunks), cas = wsum(ls.cas), fresh = wsum(ls.fresh),
                              hsims = wsum(ls.hsims), batches = wsum(ls.batches), dealt = wsum(ls.dealt),
-                             live = wsum(ls.live), bentries = wsum(ls.bentries), live32 = wsum(ls.live32);
+                             live = wsum(ls.live), bentries = wsum(ls.bentries), chg = wsum(ls.chg);
     if (lane_id() == 0) {
         if constexpr (MODE == kPush) {
-            if (live32) atomicAdd(a.stats + kStSweepLive32, live32);
+            if (chg) atomicAdd(a.stats + kStSweepChanged, chg);
             if (bentries) atomicAdd(a.stats + kStSweepBucketEntries, bentries);
             if (live) atomicAdd(a.stats + kStSweepLiveEdges, live);
             if (batches) atomicAdd(a.stats + kStSweepBatches, batches);
@@ -1285,7 +1328,7 @@ __global__ void __launch_bounds__(kFBlock, kLevelMinBlocks) k_level(GraphDev g, 
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const unsigned long long cl = __ldcg(a.cl_in);
     const unsigned long long ch = a.ch_in ? __ldcg(a.ch_in) : 0ull;
-    const bool in_b = a.fmt_in != nullptr && __ldcg(a.fmt_in) != 0;
+    const int in_fmt = a.fmt_in != nullptr ? (int)__ldcg(a.fmt_in) : kFmtVertex;
     if ((cl >> kCountShift) == 0 && (ch >> kCountShift) == 0 && !a.all_changed) {
         clear_prev_bits(a, warp, nwarps);
         return;
@@ -1295,8 +1338,8 @@ __global__ void __launch_bounds__(kFBlock, kLevelMinBlocks) k_level(GraphDev g, 
     // the previous level's change bits (read by no one any more) are cleared
     // by the warps that find no work
     const ClearPlan cp = clear_plan(a, a.cl_prev ? __ldcg(a.cl_prev) : 0ull, a.ch_prev ? __ldcg(a.ch_prev) : 0ull,
-                                    a.fmt_prev != nullptr && __ldcg(a.fmt_prev) != 0);
-    level_work<KIND, MODE>(g, a, sX, sTab, warp, ls, sKeep[threadIdx.x >> 5], cl, ch, in_b, cp);
+                                    a.fmt_prev != nullptr ? (int)__ldcg(a.fmt_prev) : kFmtVertex);
+    level_work<KIND, MODE, true>(g, a, sX, sTab, warp, ls, sKeep[threadIdx.x >> 5], cl, ch, in_fmt, cp);
     flush_stats<MODE>(a, ls);
 }
 
@@ -1354,8 +1397,8 @@ __device__ bool grid_barrier(unsigned int* arrive, volatile unsigned int* gen, v
 
 // All levels of one phase in one cooperative launch: level t uses queue
 // buffers t % 3 as in k_level; a grid barrier separates levels; the phase
-// ends when both queues of the next level are empty.
-template <int KIND, int MODE>
+// ends when both queues of the next level are empty.  BK as in level_work.
+template <int KIND, int MODE, bool BK>
 __global__ void __launch_bounds__(kFBlock, kPhaseMinBlocks) k_phase(GraphDev g, PhaseArgs p) {
     __shared__ __align__(16) uint32_t sX[kMaxJ];
     __shared__ uint16_t sTab[kTabSize];
@@ -1370,10 +1413,10 @@ __global__ void __launch_bounds__(kFBlock, kPhaseMinBlocks) k_phase(GraphDev g, 
     // counters and format of the level's input queue, read once after the
     // barrier that precedes it
     unsigned long long pre_l = __ldcg(&p.ctr[0].x), pre_h = __ldcg(&p.ctr[0].y);
-    bool pre_b = p.fmt != nullptr && __ldcg(p.fmt) != 0;
+    int pre_f = p.fmt != nullptr ? (int)__ldcg(p.fmt) : kFmtVertex;
     // the previous level's input counters and format (its bits are cleared now)
     unsigned long long prev_l = 0ull, prev_h = 0ull;
-    bool prev_b = false;
+    int prev_f = kFmtVertex;
     for (; t < p.max_levels; ++t) {
         const int bi = t % 3, bo = (t + 1) % 3, bp = (t + 2) % 3;
         a.ql_in = p.ql[bi];
@@ -1404,17 +1447,17 @@ __global__ void __launch_bounds__(kFBlock, kPhaseMinBlocks) k_phase(GraphDev g, 
         a.fmt_prev = (p.fmt && t >= 1) ? p.fmt + t - 1 : nullptr;
         // the previous level's change bits are cleared by the warps that find
         // no work this level
-        const ClearPlan cp = clear_plan(a, prev_l, prev_h, prev_b);
-        level_work<KIND, MODE>(g, a, sX, sTab, warp, ls, sKeep[threadIdx.x >> 5], pre_l, pre_h, pre_b, cp);
+        const ClearPlan cp = clear_plan(a, prev_l, prev_h, prev_f);
+        level_work<KIND, MODE, BK>(g, a, sX, sTab, warp, ls, sKeep[threadIdx.x >> 5], pre_l, pre_h, pre_f, cp);
         prev_l = pre_l;
         prev_h = pre_h;
-        prev_b = pre_b;
+        prev_f = pre_f;
         if (!grid_barrier(p.bar_arrive, p.bar_gen, p.abort_flag, a.err, p.limit_ns, (unsigned int)t))
             break;
         if (p.level_ns && blockIdx.x == 0 && threadIdx.x == 0) p.level_ns[t + 1] = global_ns();
         pre_l = __ldcg(&p.ctr[t + 1].x);
         pre_h = __ldcg(&p.ctr[t + 1].y);
-        pre_b = p.fmt != nullptr && __ldcg(p.fmt + t + 1) != 0;
+        pre_f = p.fmt != nullptr ? (int)__ldcg(p.fmt + t + 1) : kFmtVertex;
         if ((pre_l >> kCountShift) == 0 && (pre_h >> kCountShift) == 0) { ++t; break; }
     }
     flush_stats<MODE>(a, ls);
@@ -1445,17 +1488,21 @@ int phase_grid() {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phase<kWC, kPush>, kFBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phase<kWC, kPush, true>, kFBlock, 0);
         int pc = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, k_phase<kWC, kCover>, kFBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, k_phase<kWC, kCover, true>, kFBlock, 0);
         if (pc < per_sm) per_sm = pc;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, k_phase<kWC, kAffect>, kFBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, k_phase<kWC, kAffect, true>, kFBlock, 0);
+        if (pc < per_sm) per_sm = pc;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, k_phase<kTrivalency, kPush, false>, kFBlock, 0);
+        if (pc < per_sm) per_sm = pc;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, k_phase<kWC, kCover, false>, kFBlock, 0);
         if (pc < per_sm) per_sm = pc;
         for (int kd : {0, 2, 3}) {
             int q = 0;
-            if (kd == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_phase<kUniform, kPush>, kFBlock, 0);
-            if (kd == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_phase<kTrivalency, kPush>, kFBlock, 0);
-            if (kd == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_phase<kExplicit, kPush>, kFBlock, 0);
+            if (kd == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_phase<kUniform, kPush, true>, kFBlock, 0);
+            if (kd == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_phase<kTrivalency, kPush, true>, kFBlock, 0);
+            if (kd == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_phase<kExplicit, kPush, true>, kFBlock, 0);
             if (q < per_sm) per_sm = q;
         }
         if (per_sm < 1 || !coop) per_sm = 0;
@@ -1467,7 +1514,10 @@ int phase_grid() {
 template <int KIND, int MODE>
 static cudaError_t coop_launch(const GraphDev& g, const PhaseArgs& p, int grid, cudaStream_t st) {
     void* args[] = {(void*)&g, (void*)&p};
-    return cudaLaunchCooperativeKernel((const void*)k_phase<KIND, MODE>, dim3(grid), dim3(kFBlock), args, 0, st);
+    // edge-scan sketches (no bucketed lists) run the variant without the bucket code
+    const void* fn = p.base.bk_end != nullptr ? (const void*)k_phase<KIND, MODE, true>
+                                              : (const void*)k_phase<KIND, MODE, false>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kFBlock), args, 0, st);
 }
 
 cudaError_t launch_phase(int kind, int mode, const GraphDev& g, const PhaseArgs& p, int grid,

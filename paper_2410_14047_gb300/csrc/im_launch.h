@@ -33,13 +33,17 @@ enum StatIndex : int {
     kStPullBuckets,         // out-buckets queued by the pulls of incremental rebuilds
     kStPullEntries,         // out-bucket entries walked by those pulls
     kStSweepChangedBuckets, // (vertex, chunk) buckets whose registers changed (bucket-format levels)
-    kStSweepLive32,         // (edge, 32-simulation chunk) pairs with a live, changed, non-visited source
     kStCount
 };
 
 // kAffect: the affected-set search of an incremental rebuild (in-edges, like
 // propagation; marks bits instead of merging registers).
 enum FrontierMode : int { kPush = 0, kCover = 1, kAffect = 2 };
+
+// Formats of a level's queue: vertex entries, (vertex, chunk) bucket entries,
+// or no queue at all (dense: the next level walks every vertex and reads the
+// change bits; the counter's count field holds the raised items).
+enum QueueFormat : int { kFmtVertex = 0, kFmtBucket = 1, kFmtDense = 2 };
 
 
 // One frontier level (propagation sweep or cover level).  Queue t of a phase
@@ -113,6 +117,7 @@ struct LevelArgs {
     unsigned int* awl_count;             //   (v * words + w each), their count (NULL: no list)
     uint32_t* nv;                        // covers: registers newly visited since the last build (may be NULL)
     int32_t chain;                       // continuation depth on small bucket levels (0 = none)
+    int32_t dense_out;                   // dense walks of a propagation may output dense format
 };
 
 // All levels of a phase in one cooperative launch (grid barrier between levels).

@@ -282,6 +282,26 @@ def test_errors(im, ctx):
     with pytest.raises(im.IMError) as e:
         im.im_graph_load(ctx, g.rowptr, bad, MODELS["p30"])
     assert e.value.status == -1
+    # a graph large enough that the host checks run over several threads:
+    # each planted error is found wherever it lies
+    big = W.rmat(18, 20, seed=4)
+    assert big.m >= 1 << 22
+    for where, kind, status in [(big.m - 2, "dup", -1), (big.m // 2, "range", -2), (37, "self", -1)]:
+        bad = big.col.copy()
+        u = int(np.searchsorted(big.rowptr, where, side="right") - 1)
+        while big.rowptr[u + 1] - big.rowptr[u] < 2:
+            u -= 1
+        i = int(big.rowptr[u]) + 1
+        if kind == "dup":
+            bad[i] = bad[i - 1]
+        elif kind == "range":
+            bad[i] = big.n
+        else:
+            bad[i - 1] = u
+            bad[int(big.rowptr[u]):int(big.rowptr[u + 1])].sort()
+        with pytest.raises(im.IMError) as e:
+            im.im_graph_load(ctx, big.rowptr, bad, MODELS["p30"])
+        assert e.value.status == status, (kind, str(e.value))
     small = im.im_ctx_create(0, hbm_budget_bytes=1 << 16)
     with pytest.raises(im.IMError) as e:
         im.im_graph_load(small, g.rowptr, g.col, MODELS["p30"])
@@ -303,7 +323,10 @@ def test_errors(im, ctx):
                                     {"incremental": 1, "buckets": 1024, "persistent": 0},
                                     {"chain": 0}, {"chain": 64, "buckets": 1024},
                                     {"chain": 1, "buckets": 1024, "persistent": 0, "light_batches": 1},
-                                    {"pick_tile": 1, "lazy_pick": 0}, {"pick_tile": 2}])
+                                    {"pick_tile": 1, "lazy_pick": 0}, {"pick_tile": 2},
+                                    {"dense_out": 1, "dense_div": 2}, {"dense_out": 1, "dense_div": 1000000},
+                                    {"dense_out": 1, "dense_div": 2, "persistent": 0},
+                                    {"dense_out": 0, "dense_div": 2, "buckets": 0}])
 @pytest.mark.parametrize("gname,mname,J", [("rmat12", "wc", 256), ("cl5k", "p01", 64),
                                            ("er2k", "wc", 1024), ("rmat12", "tri", 32)])
 def test_tuning_does_not_change_results(im, ctx, tuning, gname, mname, J):
