@@ -222,8 +222,9 @@ struct im_graph {
     int kind = kUniform;       // kernel family (a per-target model runs as kWC)
     int load_kind = kUniform;  // model kind given at load
     DBuf rp_out, col_out, rp_in, src_in, h_in, h_out, thrw_out, thr_v, thr_out, thr_in, q_dense,
-        hkey;
-    int32_t n_dense = 0;
+        hkey, q_dense_out;
+    int32_t n_dense = 0;      // vertices with in-edges (q_dense: their in-rows in vertex order)
+    int32_t n_dense_out = 0;  // vertices with out-edges (q_dense_out: their out-rows)
     GraphDev dev{};
 };
 
@@ -407,7 +408,7 @@ static void graph_release(im_graph* g) {
     im_ctx* c = g->ctx;
     for (DBuf* b : {&g->rp_out, &g->col_out, &g->rp_in, &g->src_in, &g->h_in, &g->h_out,
                     &g->thrw_out, &g->thr_v, &g->thr_out, &g->thr_in, &g->q_dense,
-                    &g->hkey})
+                    &g->hkey, &g->q_dense_out})
         dfree(c, *b);
 }
 
@@ -536,6 +537,7 @@ static im_status graph_load_impl(im_ctx* c, int32_t n, int64_t m, const int32_t*
     if ((s = dalloc(c, e_bytes, g->thrw_out)) != IM_OK) return bail(s);
     if ((s = dalloc(c, (size_t)n * 4, g->thr_v)) != IM_OK) return bail(s);
     if ((s = dalloc(c, (size_t)n * sizeof(QEntry), g->q_dense)) != IM_OK) return bail(s);
+    if ((s = dalloc(c, (size_t)n * sizeof(QEntry), g->q_dense_out)) != IM_OK) return bail(s);
     DBuf cnt, tmp;
     if ((s = dalloc(c, ((size_t)n + 1) * 4, cnt)) != IM_OK) return bail(s);
     const size_t tmp_bytes = std::max(scan_tmp_bytes(n), build_in_csr_tmp_bytes(m));
@@ -582,13 +584,20 @@ static im_status graph_load_impl(im_ctx* c, int32_t n, int64_t m, const int32_t*
     if (e == cudaSuccess)
         e = launch_dense_queue(g->rp_in.as<int32_t>(), n, g->thr_v.as<uint32_t>(), cnt.as<int32_t>(),
                                pos.as<int32_t>(), tmp.p, g->q_dense.as<QEntry>(), st);
-    int32_t nd = 0;
+    int32_t nd = 0, ndo = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&nd, pos.as<int32_t>() + n, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    // the same over the out-rows (dense cover levels)
+    if (e == cudaSuccess)
+        e = launch_dense_queue(g->rp_out.as<int32_t>(), n, nullptr, cnt.as<int32_t>(), pos.as<int32_t>(), tmp.p,
+                               g->q_dense_out.as<QEntry>(), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ndo, pos.as<int32_t>() + n, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     dfree(c, pos);
     release_tmp();
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "graph load"));
     g->n_dense = nd;
+    g->n_dense_out = ndo;
     g->dev.n = n;
     g->dev.m = m;
     g->dev.rp_out = g->rp_out.as<int32_t>();
@@ -828,6 +837,12 @@ static void set_lcm(LevelArgs& a, const im_sketch* sk, int mode) {
     a.awl_count = words ? sk->awlc.as<unsigned int>() : nullptr;
     a.nv = (mode == kCover && sk->incr) ? sk->nv.as<uint32_t>() : nullptr;
     a.lcm_lo = (in ? sk->lcm_in_lo : sk->lcm_out_lo).as<uint32_t>();
+    if (mode == kCover) {
+        // dense cover levels walk every vertex's out-row
+        a.q_dense = sk->g->q_dense_out.as<QEntry>();
+        a.n_dense = sk->g->n_dense_out;
+        a.e_dense = sk->g->m;
+    }
     a.lcm_hi = sk->J > 512 ? (in ? sk->lcm_in_hi : sk->lcm_out_hi).as<uint32_t>() : nullptr;
     a.chunks = sk->J / 16;
     a.nbuckets = (int64_t)sk->g->n * (sk->J / 16);

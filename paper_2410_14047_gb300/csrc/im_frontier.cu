@@ -1200,20 +1200,25 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
     int64_t El = (int64_t)(cl & kEdgeMask);
     int32_t nh = (int32_t)(ch >> kCountShift);
     const QEntry* ql = a.ql_in;
-    // dense level: walk every vertex with in-edges in vertex order (contiguous
-    // in-CSR reads); vertices without changed simulations produce no chunks.
-    // A dense-format input (no queue: its count is the raised items) is always
-    // walked this way.
-    const bool in_d = MODE == kPush && in_fmt == kFmtDense;
+    // dense level: walk every vertex with in-edges (propagation) or out-edges
+    // (cover) in vertex order (contiguous CSR reads); vertices without changed
+    // simulations produce no chunks.  A propagation level goes dense when its
+    // frontier holds more than n_dense / dense_div vertices, a cover level when
+    // its frontier's out-edges exceed m / dense_div (a cascade's frontier is
+    // few hubs with most edges).  A dense-format input (no queue: its count is
+    // the raised items) is always walked this way.
+    constexpr bool kDenseMode = MODE == kPush || MODE == kCover;
+    const bool in_d = kDenseMode && in_fmt == kFmtDense;
     bool dense = in_d;
-    if (MODE == kPush && a.q_dense && a.dense_div > 0 && (nl + nh) > 0 &&
-        ((int64_t)(nl + nh) * a.dense_div > (int64_t)a.n_dense || a.all_changed))
-        dense = true;
+    if (kDenseMode && a.q_dense && a.dense_div > 0 && (nl + nh) > 0) {
+        if (MODE == kPush && ((int64_t)(nl + nh) * a.dense_div > (int64_t)a.n_dense || a.all_changed)) dense = true;
+        if (MODE == kCover && El * a.dense_div > g.m) dense = true;
+    }
     // the output of a dense walk stays in dense format while the frontier is
     // large: the input's vertices (or, after a dense-format level, its raised
     // items, several per vertex) above n_dense / dense_div
     bool out_d = false;
-    if (MODE == kPush && dense && a.dense_out)
+    if (kDenseMode && dense && a.dense_out)
         out_d = in_d ? (int64_t)nl * a.dense_div > 4 * (int64_t)a.n_dense : true;
     if (dense) {
         ql = a.q_dense;
@@ -1272,7 +1277,7 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
             const int64_t b1 = min(nbl, b0 + lb);
             light_slice<KIND, MODE>(g, a, ql, sX, sTab, b0, b1, nl, El, ls.chunks, ls.cas, ls.fresh,
                                     ls.batches, ls.dealt, ls.live, dense && nh > 0, sKeep, out_b, out_d,
-                                    in_d ? &ls.chg : nullptr, draised);
+                                    MODE == kPush && in_d ? &ls.chg : nullptr, draised);
         } else {
             const int64_t hu = (int64_t)unit - nhv - lunits;
             const int64_t b0 = hu * lb;

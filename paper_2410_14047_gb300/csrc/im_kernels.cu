@@ -673,8 +673,9 @@ cudaError_t launch_exclusive_scan(const int32_t* cnt, int32_t n, int32_t* out, v
     return cudaGetLastError();
 }
 
-// Static queue of every vertex with in-edges, in vertex order (dense levels):
-// entry k is the k-th such vertex, its flat-space offset is its in-row start.
+// Static queue of every vertex with in-edges (rp = the in-CSR) or out-edges
+// (rp = the out-CSR), in vertex order (dense levels): entry k is the k-th such
+// vertex, its flat-space offset is its row start; aux = thr_v (may be NULL).
 __global__ void k_flag_in(const int32_t* __restrict__ rp_in, int32_t n, int32_t* flag) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v < n) flag[v] = rp_in[v + 1] > rp_in[v] ? 1 : 0;
@@ -687,7 +688,7 @@ __global__ void k_dense_queue(const int32_t* __restrict__ rp_in, int32_t n, cons
     const int32_t b = rp_in[v], e = rp_in[v + 1];
     if (e > b) {
         QEntry x;
-        x.v = (int32_t)v; x.rp = b; x.off = b; x.aux = thr_v[v];
+        x.v = (int32_t)v; x.rp = b; x.off = b; x.aux = thr_v ? thr_v[v] : 0u;
         q[pos[v]] = x;
     }
 }

@@ -45,6 +45,7 @@ SCHEDULES = {
     "scans": {"buckets": 0, "incremental": 2, "heavy_indeg": 8},
     "levels": {"persistent": 0, "dense_div": 2},
     "full_rebuilds": {"incremental": 0, "chain": 0, "lazy_pick": 0},
+    "dense_walks": {"buckets": 0, "dense_div": 1000000, "dense_out": 1, "incremental": 0},
 }
 
 

@@ -326,7 +326,8 @@ def test_errors(im, ctx):
                                     {"pick_tile": 1, "lazy_pick": 0}, {"pick_tile": 2},
                                     {"dense_out": 1, "dense_div": 2}, {"dense_out": 1, "dense_div": 1000000},
                                     {"dense_out": 1, "dense_div": 2, "persistent": 0},
-                                    {"dense_out": 0, "dense_div": 2, "buckets": 0}])
+                                    {"dense_out": 0, "dense_div": 2, "buckets": 0},
+                                    {"dense_out": 1, "dense_div": 1000000, "buckets": 0, "persistent": 0}])
 @pytest.mark.parametrize("gname,mname,J", [("rmat12", "wc", 256), ("cl5k", "p01", 64),
                                            ("er2k", "wc", 1024), ("rmat12", "tri", 32)])
 def test_tuning_does_not_change_results(im, ctx, tuning, gname, mname, J):
