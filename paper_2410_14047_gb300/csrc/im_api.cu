@@ -222,7 +222,7 @@ struct im_graph {
     int kind = kUniform;       // kernel family (a per-target model runs as kWC)
     int load_kind = kUniform;  // model kind given at load
     DBuf rp_out, col_out, rp_in, src_in, h_in, h_out, thrw_out, thr_v, thr_out, thr_in, q_dense,
-        hkey, q_dense_out;
+        hkey, q_dense_out, out_to_in;
     int32_t n_dense = 0;      // vertices with in-edges (q_dense: their in-rows in vertex order)
     int32_t n_dense_out = 0;  // vertices with out-edges (q_dense_out: their out-rows)
     GraphDev dev{};
@@ -408,7 +408,7 @@ static void graph_release(im_graph* g) {
     im_ctx* c = g->ctx;
     for (DBuf* b : {&g->rp_out, &g->col_out, &g->rp_in, &g->src_in, &g->h_in, &g->h_out,
                     &g->thrw_out, &g->thr_v, &g->thr_out, &g->thr_in, &g->q_dense,
-                    &g->hkey, &g->q_dense_out})
+                    &g->hkey, &g->q_dense_out, &g->out_to_in})
         dfree(c, *b);
 }
 
@@ -535,6 +535,7 @@ static im_status graph_load_impl(im_ctx* c, int32_t n, int64_t m, const int32_t*
     if ((s = dalloc(c, e_bytes, g->h_in)) != IM_OK) return bail(s);
     if ((s = dalloc(c, e_bytes, g->h_out)) != IM_OK) return bail(s);
     if ((s = dalloc(c, e_bytes, g->thrw_out)) != IM_OK) return bail(s);
+    if ((s = dalloc(c, e_bytes, g->out_to_in)) != IM_OK) return bail(s);
     if ((s = dalloc(c, (size_t)n * 4, g->thr_v)) != IM_OK) return bail(s);
     if ((s = dalloc(c, (size_t)n * sizeof(QEntry), g->q_dense)) != IM_OK) return bail(s);
     if ((s = dalloc(c, (size_t)n * sizeof(QEntry), g->q_dense_out)) != IM_OK) return bail(s);
@@ -577,7 +578,8 @@ static im_status graph_load_impl(im_ctx* c, int32_t n, int64_t m, const int32_t*
     // in-CSR sorted by (target, class, edge hash): rows of equal-threshold in-edges in hash order
     e = launch_build_in_csr(g->rp_out.as<int32_t>(), g->col_out.as<int32_t>(), n, m, g->kind,
                             g->dev.tri_seed, g->hkey.as<int32_t>(), g->thr_out.as<uint32_t>(),
-                            g->src_in.as<int32_t>(), g->h_in.as<uint32_t>(), g->thr_in.as<uint32_t>(), tmp.p, st);
+                            g->src_in.as<int32_t>(), g->h_in.as<uint32_t>(), g->thr_in.as<uint32_t>(),
+                            g->out_to_in.as<int32_t>(), tmp.p, st);
     // static vertex-ordered queue for dense levels (cnt and tmp reused as scratch)
     DBuf pos;
     if (e == cudaSuccess && (s = dalloc(c, ((size_t)n + 1) * 4, pos)) != IM_OK) { release_tmp(); return bail(s); }
@@ -1245,15 +1247,22 @@ static im_status build_scan_mode(im_sketch* sk) {
     BufPlan plan;
     scan_plan(sk, sk->g->n, sk->g->m, J, plan);
     for (auto& [b, bytes] : plan) CKS(dalloc(c, bytes, *b));
-    for (int mode : {kPush, kCover}) {
-        const bool in = mode == kPush;
-        CK(c, timed(c, kTOther, [&] {
-            return launch_live_chunks(sk->kind, mode, sk->dev, sk->X.as<uint32_t>(), sk->tab.as<uint16_t>(), J,
-                                      (in ? sk->lcm_in_lo : sk->lcm_out_lo).as<uint32_t>(),
-                                      J > 512 ? (in ? sk->lcm_in_hi : sk->lcm_out_hi).as<uint32_t>() : nullptr,
-                                      c->stream);
-        }));
-    }
+    // an edge's live chunks are the same in both orientations: computed over
+    // the in-edges (rows sorted by edge hash, so a warp's candidate ranges
+    // agree), then gathered into out-CSR order
+    CK(c, timed(c, kTOther, [&] {
+        return launch_live_chunks(sk->kind, kPush, sk->dev, sk->X.as<uint32_t>(), sk->tab.as<uint16_t>(), J,
+                                  sk->lcm_in_lo.as<uint32_t>(), J > 512 ? sk->lcm_in_hi.as<uint32_t>() : nullptr,
+                                  c->stream);
+    }));
+    const int32_t* o2i = sk->g->out_to_in.as<int32_t>();
+    CK(c, timed(c, kTOther, [&] {
+        cudaError_t e = launch_gather_u32(sk->lcm_in_lo.as<uint32_t>(), o2i, sk->g->m, sk->lcm_out_lo.as<uint32_t>(),
+                                          c->stream);
+        if (e == cudaSuccess && J > 512)
+            e = launch_gather_u32(sk->lcm_in_hi.as<uint32_t>(), o2i, sk->g->m, sk->lcm_out_hi.as<uint32_t>(), c->stream);
+        return e;
+    }));
     return IM_OK;
 }
 
@@ -1710,7 +1719,7 @@ uint64_t graph_bytes(const im_graph* g) {
     uint64_t total = 0;
     for (const DBuf* b : {&g->rp_out, &g->col_out, &g->rp_in, &g->src_in, &g->h_in, &g->h_out,
                           &g->thrw_out, &g->thr_v, &g->thr_out, &g->thr_in,
-                          &g->q_dense, &g->hkey})
+                          &g->q_dense, &g->hkey, &g->q_dense_out, &g->out_to_in})
         total += b->bytes;
     return total;
 }

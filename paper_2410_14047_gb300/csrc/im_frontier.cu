@@ -252,7 +252,11 @@ __device__ __forceinline__ EnqueueState vertex_enqueue_issue(const GraphDev& g, 
                                                              uint32_t c, uint32_t imp) {
     EnqueueState q;
     if (imp) {
-        atomicOr(a.chg_next + (size_t)o * a.words + (c >> 1), imp << ((c & 1u) * 16u));
+        // a cover reads the word's previous bits (newly_visited counts from them)
+        if constexpr (MODE == kCover)
+            q.old = atomicOr(a.chg_next + (size_t)o * a.words + (c >> 1), imp << ((c & 1u) * 16u));
+        else
+            atomicOr(a.chg_next + (size_t)o * a.words + (c >> 1), imp << ((c & 1u) * 16u));
         const int32_t* rpp = MODE != kCover ? g.rp_in : g.rp_out;
         q.rp = __ldg(rpp + o);
         q.deg = __ldg(rpp + o + 1);
@@ -356,8 +360,26 @@ __device__ __forceinline__ void bucket_enqueue_finish(const LevelArgs& a, bool c
 // enqueue stamp, no row words.  Each warp adds its count to the next level's
 // counter once, at the end of the level (dense_count_flush).  The next level
 // walks every vertex again and reads the change bits.
-__device__ __forceinline__ void dense_enqueue_issue(const LevelArgs& a, int32_t o, uint32_t c, uint32_t imp) {
-    if (imp) atomicOr(a.chg_next + (size_t)o * a.words + (c >> 1), imp << ((c & 1u) * 16u));
+template <int MODE>
+__device__ __forceinline__ uint32_t dense_enqueue_issue(const LevelArgs& a, int32_t o, uint32_t c, uint32_t imp) {
+    if (!imp) return 0u;
+    uint32_t* w = a.chg_next + (size_t)o * a.words + (c >> 1);
+    if constexpr (MODE == kCover) return atomicOr(w, imp << ((c & 1u) * 16u));
+    atomicOr(w, imp << ((c & 1u) * 16u));
+    return 0u;
+}
+
+// The registers a cover item visits first: a register becomes visited at
+// exactly one level (a later level's target load sees the mark), every item
+// that visits it at that level sets its change bit, and the one whose
+// atomicOr found the bit clear counts it (old: the change word before).
+__device__ __forceinline__ void newly_visited(const LevelArgs& a, int32_t o, uint32_t c, uint32_t imp, uint32_t old,
+                                              StatT& st_new) {
+    const uint32_t fresh = imp & ~(old >> ((c & 1u) * 16u)) & 0xFFFFu;
+    if (!fresh) return;
+    const unsigned k = (unsigned)__popc(fresh);
+    st_new += k;
+    if (a.gcount) atomicAdd(a.gcount + __ldg(a.gid + o), (unsigned long long)k);
 }
 
 __device__ __forceinline__ void dense_count_flush(const LevelArgs& a, StatT n) {
@@ -519,7 +541,7 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                     }
                     if constexpr (MODE == kAffect) imp = mark_affected(a, cand, o_i, (uint32_t)chunk, st_new);
                     // the enqueue's loads and atomics go out before the register update
-                    if (out_d) dense_enqueue_issue(a, o_i, (uint32_t)chunk, imp);
+                    if (out_d) eq.old = dense_enqueue_issue<MODE>(a, o_i, (uint32_t)chunk, imp);
                     else eq = out_b ? bucket_enqueue_issue(a, o_i, (uint32_t)chunk, imp)
                                     : vertex_enqueue_issue<KIND, MODE>(g, a, o_i, (uint32_t)chunk, imp);
                     if (MODE != kAffect && any) {
@@ -527,20 +549,13 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                         if constexpr (MODE == kPush) {
                             nbits = merge_chunk(trow, cand, tg, st_cas, a.err);
                         } else {
+                            // the visited marks go out without a reply; the
+                            // change word's previous bits count the new ones
 #pragma unroll
-                            for (int w = 0; w < 4; ++w) {
-                                if (cand[w] == 0u) continue;
-                                const uint32_t prev = atomicOr(reinterpret_cast<unsigned int*>(trow + 4 * w), cand[w]);
-                                const uint32_t really = cand[w] & ~visited_bytes(prev);
-                                if (really) {
-                                    nbits |= bytes_to_bits(really) << (4 * w);
-                                    st_new += (unsigned)(__popc(really) >> 3);
-                                    if (a.gcount)
-                                        atomicAdd(a.gcount + __ldg(a.gid + o_i),
-                                                  (unsigned long long)(__popc(really) >> 3));
-                                }
-                            }
-                            note_newly_visited(a, o_i, (uint32_t)chunk, nbits);
+                            for (int w = 0; w < 4; ++w)
+                                if (cand[w]) atomicOr(reinterpret_cast<unsigned int*>(trow + 4 * w), cand[w]);
+                            newly_visited(a, o_i, (uint32_t)chunk, imp, eq.old, st_new);
+                            note_newly_visited(a, o_i, (uint32_t)chunk, imp);
                         }
                     }
                 }
@@ -832,18 +847,10 @@ __device__ __forceinline__ void bucket_pos(const GraphDev& g, const LevelArgs& a
                 nbits = merge_chunk(trow, cand, tg, st_cas, a.err);
             } else {
 #pragma unroll
-                for (int w = 0; w < 4; ++w) {
-                    if (cand[w] == 0u) continue;
-                    const uint32_t prev = atomicOr(reinterpret_cast<unsigned int*>(trow + 4 * w), cand[w]);
-                    const uint32_t really = cand[w] & ~visited_bytes(prev);
-                    if (really) {
-                        nbits |= bytes_to_bits(really) << (4 * w);
-                        st_new += (unsigned)(__popc(really) >> 3);
-                        if (a.gcount)
-                            atomicAdd(a.gcount + __ldg(a.gid + o), (unsigned long long)(__popc(really) >> 3));
-                    }
-                }
-                note_newly_visited(a, o, c, nbits);
+                for (int w = 0; w < 4; ++w)
+                    if (cand[w]) atomicOr(reinterpret_cast<unsigned int*>(trow + 4 * w), cand[w]);
+                newly_visited(a, o, c, imp, eq.old, st_new);
+                note_newly_visited(a, o, c, imp);
             }
         }
     }
@@ -1023,10 +1030,12 @@ __device__ __forceinline__ void clear_prev_bits(const LevelArgs& a, int64_t warp
     if (!a.chg_prev) return;
     const int lane = (int)lane_id();
     const int32_t nlp = a.cl_prev ? (int32_t)(__ldcg(a.cl_prev) >> kCountShift) : 0;
+    auto clear_all = [&](int64_t nw) {
+        for (int64_t i = warp * 32 + lane; i < nw; i += nwarps * 32) a.chg_prev[i] = 0u;
+    };
     if (a.fmt_prev && __ldcg(a.fmt_prev) == kFmtDense) {
         // a level without a queue (dense format): every change word
-        const int64_t nw = (int64_t)a.vq_cap * a.words;
-        for (int64_t i = warp * 32 + lane; i < nw; i += nwarps * 32) a.chg_prev[i] = 0u;
+        clear_all((int64_t)a.vq_cap * a.words);
         return;
     }
     if (a.fmt_prev && __ldcg(a.fmt_prev) == kFmtBucket) {
@@ -1034,8 +1043,7 @@ __device__ __forceinline__ void clear_prev_bits(const LevelArgs& a, int64_t warp
         // queue that overflowed (its level walked every bucket) clears all
         const bool overflow = nlp > a.bq_cap || (a.ch_prev && __ldcg(a.ch_prev) != 0ull);
         if (overflow) {
-            const int64_t nw = (int64_t)a.nbuckets / a.chunks * a.words;
-            for (int64_t i = warp * 32 + lane; i < nw; i += nwarps * 32) a.chg_prev[i] = 0u;
+            clear_all((int64_t)a.nbuckets / a.chunks * a.words);
             return;
         }
         uint16_t* h16 = reinterpret_cast<uint16_t*>(a.chg_prev);
@@ -1465,7 +1473,6 @@ __global__ void __launch_bounds__(kFBlock, kPhaseMinBlocks) k_phase(GraphDev g, 
         pre_f = p.fmt != nullptr ? (int)__ldcg(p.fmt + t + 1) : kFmtVertex;
         if ((pre_l >> kCountShift) == 0 && (pre_h >> kCountShift) == 0) { ++t; break; }
     }
-    flush_stats<MODE>(a, ls);
     // the last queue read (t - 1) still has its change bits; clearing them
     // leaves every change mask zero for the next phase
     if (t >= 1 && t < p.max_levels && !*(volatile unsigned int*)p.abort_flag) {
@@ -1478,6 +1485,7 @@ __global__ void __launch_bounds__(kFBlock, kPhaseMinBlocks) k_phase(GraphDev g, 
         a.fmt_prev = p.fmt ? p.fmt + t - 1 : nullptr;
         clear_prev_bits(a, warp, nwarps);
     }
+    flush_stats<MODE>(a, ls);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *p.levels_out = t;
         // a frontier that did not empty within the level limit is an error the

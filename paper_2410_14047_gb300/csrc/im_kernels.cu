@@ -1078,20 +1078,36 @@ cudaError_t launch_out_edge_words(const int32_t* rp_out, const int32_t* col_out,
 __global__ void k_in_gather(const unsigned long long* __restrict__ keys, const int32_t* __restrict__ perm,
                             int64_t m, const int32_t* __restrict__ src_out,
                             const uint32_t* __restrict__ thr_out, int32_t* __restrict__ src_in,
-                            uint32_t* __restrict__ h_in, uint32_t* __restrict__ thr_in) {
+                            uint32_t* __restrict__ h_in, uint32_t* __restrict__ thr_in,
+                            int32_t* __restrict__ out_to_in) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t e = perm[i];
         src_in[i] = src_out[e];
         h_in[i] = (uint32_t)keys[i] & 0x7FFFFFFFu;
         if (thr_in) thr_in[i] = thr_out[e];
+        if (out_to_in) out_to_in[e] = (int32_t)i;
     }
+}
+
+// dst[i] = src[idx[i]] (per-edge words from one CSR orientation to the other)
+__global__ void k_gather_u32(const uint32_t* __restrict__ src, const int32_t* __restrict__ idx, int64_t m,
+                             uint32_t* __restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __ldg(src + __ldg(idx + i));
+}
+
+cudaError_t launch_gather_u32(const uint32_t* src, const int32_t* idx, int64_t m, uint32_t* dst, cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    k_gather_u32<<<152 * 8, kBlock, 0, st>>>(src, idx, m, dst);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_build_in_csr(const int32_t* rp_out, const int32_t* col_out, int32_t n, int64_t m,
                                 int kind, uint32_t tri_seed, const int32_t* hkey, const uint32_t* thr_out,
                                 int32_t* src_in, uint32_t* h_in,
-                                uint32_t* thr_in, void* tmp, cudaStream_t st) {
+                                uint32_t* thr_in, int32_t* out_to_in, void* tmp, cudaStream_t st) {
     if (m == 0) return cudaSuccess;
     char* p = static_cast<char*>(tmp);
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(p);
@@ -1105,7 +1121,7 @@ cudaError_t launch_build_in_csr(const int32_t* rp_out, const int32_t* col_out, i
     while ((1ll << (bits - 33)) < n) ++bits;
     cudaError_t e = launch_radix_sort(keys, perm, m, bits, p, st);
     if (e != cudaSuccess) return e;
-    k_in_gather<<<152 * 8, kBlock, 0, st>>>(keys, perm, m, src_out, thr_out, src_in, h_in, thr_in);
+    k_in_gather<<<152 * 8, kBlock, 0, st>>>(keys, perm, m, src_out, thr_out, src_in, h_in, thr_in, out_to_in);
     return cudaGetLastError();
 }
 

@@ -64,3 +64,36 @@ def test_batch_against_oracle(im):
         ref = O.select_seeds(g, O.thresholds(g, {"kind": "uniform", "p": p[i]}), J[i], K[i], 5, 0.01, "reverse")
         assert res[i]["seeds"].tolist() == ref["seeds"].tolist()
         assert np.array_equal(res[i]["score"], ref["score"])
+
+
+def test_per_target_model_against_oracle(im):
+    # the per-target model the batched form runs on (every edge into v fires
+    # with w[v]), loaded on its own with uneven w, against the oracle's
+    # per-target thresholds
+    ctx = im.im_ctx_create(0)
+    rng = np.random.default_rng(23)
+    for g in (W.chung_lu(3000, 10.0, 2.1, seed=41), W.rmat(11, 12, seed=42)):
+        w = rng.uniform(0.0, 0.4, g.n).astype(np.float32)
+        model = {"kind": "target", "w": w}
+        G = im.im_graph_load(ctx, g.rowptr, g.col, model)
+        for J, K in ((64, 6), (128, 4)):
+            r = im.im_select_seeds(G, K, J, seed=31, return_sketch=True)
+            ref = O.select_seeds(g, O.thresholds(g, model), J, K, 31, 0.01, "reverse")
+            assert r["seeds"].tolist() == ref["seeds"].tolist()
+            assert np.array_equal(r["score"], ref["score"])
+            assert np.array_equal(r["sketch"].registers(), ref["M"])
+
+
+def test_every_batched_graph_against_oracle_per_target_thresholds(im):
+    # the whole batch (every graph, not a sample) against the oracle run with
+    # the per-target thresholds the batch uses: w[v] = p of v's graph
+    graphs, p, J, K = _mix(17)
+    ctx = im.im_ctx_create(0)
+    B = im.im_batch_load(ctx, graphs, p)
+    res = im.im_batch_select_seeds(B, J, K, seed=8)
+    for i, g in enumerate(graphs):
+        thr = O.thresholds(g, {"kind": "target", "w": np.full(g.n, p[i], np.float32)})
+        ref = O.select_seeds(g, thr, J[i], K[i], 8, 0.01, "reverse")
+        assert res[i]["seeds"].tolist() == ref["seeds"].tolist(), i
+        assert np.array_equal(res[i]["score"], ref["score"]), i
+        np.testing.assert_allclose(res[i]["est"], ref["est"], rtol=1e-12, atol=0)
