@@ -582,9 +582,12 @@ def run_gpu(args):
         torch.cuda.synchronize()
         if rank == 0:
             st = im.im_last_stats(ctx)
+            terms = alg_bytes_terms(st, wl.J, wl.model["kind"])
             print(json.dumps({"mode": "build", "workload": wl.name, "steps": args.steps,
                               "ms_per_build": (time.perf_counter() - t0) / max(args.steps, 1) * 1e3,
-                              "sweeps": st["sweeps"], "ms_propagate": st["ms_propagate"]}), flush=True)
+                              "sweeps": st["sweeps"], "ms_propagate": st["ms_propagate"],
+                              "alg_bytes_last_build": terms["bytes"], "units_last_build": terms["units"]}),
+                  flush=True)
         return 0
 
     def step():
