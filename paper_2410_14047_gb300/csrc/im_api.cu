@@ -222,7 +222,7 @@ struct im_graph {
     int kind = kUniform;       // kernel family (a per-target model runs as kWC)
     int load_kind = kUniform;  // model kind given at load
     DBuf rp_out, col_out, rp_in, src_in, h_in, h_out, thrw_out, thr_v, thr_out, thr_in, q_dense,
-        hkey, q_dense_out, out_to_in;
+        hkey, q_dense_out, out_to_in, tri_b;
     int32_t n_dense = 0;      // vertices with in-edges (q_dense: their in-rows in vertex order)
     int32_t n_dense_out = 0;  // vertices with out-edges (q_dense_out: their out-rows)
     GraphDev dev{};
@@ -408,7 +408,7 @@ static void graph_release(im_graph* g) {
     im_ctx* c = g->ctx;
     for (DBuf* b : {&g->rp_out, &g->col_out, &g->rp_in, &g->src_in, &g->h_in, &g->h_out,
                     &g->thrw_out, &g->thr_v, &g->thr_out, &g->thr_in, &g->q_dense,
-                    &g->hkey, &g->q_dense_out, &g->out_to_in})
+                    &g->hkey, &g->q_dense_out, &g->out_to_in, &g->tri_b})
         dfree(c, *b);
 }
 
@@ -421,6 +421,12 @@ static void model_words(GraphDev& dev, int& kind, const im_model* mdl) {
     dev.tri_thr[0] = prob_threshold_host(0.1f);
     dev.tri_thr[1] = prob_threshold_host(0.01f);
     dev.tri_thr[2] = prob_threshold_host(0.001f);
+}
+
+// The in-rows' trivalency class bounds hold for a device view only when its
+// model is the trivalency model the rows were sorted under.
+static void keep_class_bounds(GraphDev& dev, int kind, const im_graph* g) {
+    if (kind != kTrivalency || g->kind != kTrivalency || dev.tri_seed != g->dev.tri_seed) dev.tri_b = nullptr;
 }
 
 // Sets the model part of the device view; allocates per-vertex / per-edge
@@ -575,11 +581,14 @@ static im_status graph_load_impl(im_ctx* c, int32_t n, int64_t m, const int32_t*
     if (g->kind == kExplicit && m > 0) {
         if ((s = dalloc(c, (size_t)m * 4, g->thr_in)) != IM_OK) { release_tmp(); return bail(s); }
     }
+    if (g->kind == kTrivalency) {
+        if ((s = dalloc(c, (size_t)n * sizeof(int2), g->tri_b)) != IM_OK) { release_tmp(); return bail(s); }
+    }
     // in-CSR sorted by (target, class, edge hash): rows of equal-threshold in-edges in hash order
     e = launch_build_in_csr(g->rp_out.as<int32_t>(), g->col_out.as<int32_t>(), n, m, g->kind,
                             g->dev.tri_seed, g->hkey.as<int32_t>(), g->thr_out.as<uint32_t>(),
                             g->src_in.as<int32_t>(), g->h_in.as<uint32_t>(), g->thr_in.as<uint32_t>(),
-                            g->out_to_in.as<int32_t>(), tmp.p, st);
+                            g->out_to_in.as<int32_t>(), g->rp_in.as<int32_t>(), g->tri_b.as<int2>(), tmp.p, st);
     // static vertex-ordered queue for dense levels (cnt and tmp reused as scratch)
     DBuf pos;
     if (e == cudaSuccess && (s = dalloc(c, ((size_t)n + 1) * 4, pos)) != IM_OK) { release_tmp(); return bail(s); }
@@ -612,6 +621,7 @@ static im_status graph_load_impl(im_ctx* c, int32_t n, int64_t m, const int32_t*
     g->dev.thr_v = g->thr_v.as<uint32_t>();
     g->dev.thr_out = g->thr_out.as<uint32_t>();
     g->dev.thr_in = g->thr_in.as<uint32_t>();
+    g->dev.tri_b = g->tri_b.as<int2>();
     *out = g;
     return IM_OK;
 }
@@ -1363,6 +1373,7 @@ static im_status sketch_start(im_ctx* c, im_graph* g, int32_t J, uint64_t seed, 
     sk->dev = g->dev;
     sk->kind = g->kind;
     if (model) model_words(sk->dev, sk->kind, model);  // this call's model, on the sketch's copy
+    keep_class_bounds(sk->dev, sk->kind, g);
     cudaError_t e = timed(c, kTOther, [&] {
         return launch_sims(seed, J, sk->X.as<uint32_t>(), sk->salt.as<uint32_t>(),
                            sk->tab.as<uint16_t>(), c->stream);
@@ -1653,6 +1664,7 @@ extern "C" im_status im_fill_rate(im_graph* g, int32_t J, uint64_t seed, const i
     GraphDev dev = g->dev;
     int kind = g->kind;
     if (model) model_words(dev, kind, model);
+    keep_class_bounds(dev, kind, g);
     DBuf X, salt, tab, cnt;
     im_status s = dalloc(c, (size_t)J * 4, X);
     if (s == IM_OK) s = dalloc(c, (size_t)J * 4, salt);
@@ -1719,7 +1731,7 @@ uint64_t graph_bytes(const im_graph* g) {
     uint64_t total = 0;
     for (const DBuf* b : {&g->rp_out, &g->col_out, &g->rp_in, &g->src_in, &g->h_in, &g->h_out,
                           &g->thrw_out, &g->thr_v, &g->thr_out, &g->thr_in,
-                          &g->q_dense, &g->hkey, &g->q_dense_out, &g->out_to_in})
+                          &g->q_dense, &g->hkey, &g->q_dense_out, &g->out_to_in, &g->tri_b})
         total += b->bytes;
     return total;
 }

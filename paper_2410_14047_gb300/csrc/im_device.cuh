@@ -65,6 +65,13 @@ struct GraphDev {
     uint32_t thr_uniform;    // kUniform
     uint32_t tri_seed;       // kTrivalency class-hash seed
     uint32_t tri_thr[3];     // kTrivalency thresholds of the three classes
+    // kTrivalency: in-rows are sorted by (class, hash), so the class of in-edge
+    // e of row v is (e >= tri_b[v].x) + (e >= tri_b[v].y) (the first in-edges
+    // of classes 1 and 2; the row end when a class is absent); used by the
+    // once-per-sketch walk over every in-edge (the frontier levels hash: one
+    // more load per row cost them more than the hash).  NULL when the rows were
+    // sorted under another model than the sketch's.
+    const int2* tri_b;
 };
 
 // Work-queue entry: a vertex, the start of its edge row in the CSR the phase
@@ -211,5 +218,14 @@ __device__ __forceinline__ uint4 ld_cg16(const uint8_t* p) {
 }
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// Reductions whose result is not needed (change bits, visited marks, counters):
+// sent as reductions, so nothing waits for a reply.
+__device__ __forceinline__ void red_or(uint32_t* p, uint32_t v) {
+    asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(p), "r"(v));
+}
+__device__ __forceinline__ void red_add(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v));
+}
 
 }  // namespace im

@@ -256,7 +256,7 @@ __device__ __forceinline__ EnqueueState vertex_enqueue_issue(const GraphDev& g, 
         if constexpr (MODE == kCover)
             q.old = atomicOr(a.chg_next + (size_t)o * a.words + (c >> 1), imp << ((c & 1u) * 16u));
         else
-            atomicOr(a.chg_next + (size_t)o * a.words + (c >> 1), imp << ((c & 1u) * 16u));
+            red_or(a.chg_next + (size_t)o * a.words + (c >> 1), imp << ((c & 1u) * 16u));
         const int32_t* rpp = MODE != kCover ? g.rp_in : g.rp_out;
         q.rp = __ldg(rpp + o);
         q.deg = __ldg(rpp + o + 1);
@@ -306,7 +306,7 @@ __device__ __forceinline__ uint32_t mark_affected(const LevelArgs& a, const uint
 // Cover: registers newly visited since the last build (the next incremental
 // rebuild starts from them).
 __device__ __forceinline__ void note_newly_visited(const LevelArgs& a, int32_t o, uint32_t c, uint32_t nbits) {
-    if (a.nv && nbits) atomicOr(a.nv + (size_t)o * a.words + (c >> 1), nbits << ((c & 1u) * 16u));
+    if (a.nv && nbits) red_or(a.nv + (size_t)o * a.words + (c >> 1), nbits << ((c & 1u) * 16u));
 }
 
 // Forward declarations (bucket mode, below).
@@ -365,7 +365,7 @@ __device__ __forceinline__ uint32_t dense_enqueue_issue(const LevelArgs& a, int3
     if (!imp) return 0u;
     uint32_t* w = a.chg_next + (size_t)o * a.words + (c >> 1);
     if constexpr (MODE == kCover) return atomicOr(w, imp << ((c & 1u) * 16u));
-    atomicOr(w, imp << ((c & 1u) * 16u));
+    red_or(w, imp << ((c & 1u) * 16u));
     return 0u;
 }
 
@@ -379,7 +379,7 @@ __device__ __forceinline__ void newly_visited(const LevelArgs& a, int32_t o, uin
     if (!fresh) return;
     const unsigned k = (unsigned)__popc(fresh);
     st_new += k;
-    if (a.gcount) atomicAdd(a.gcount + __ldg(a.gid + o), (unsigned long long)k);
+    if (a.gcount) red_add(a.gcount + __ldg(a.gid + o), (unsigned long long)k);
 }
 
 __device__ __forceinline__ void dense_count_flush(const LevelArgs& a, StatT n) {
@@ -453,6 +453,7 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
         // chunks with a changed simulation of each queue entry this batch uses
         uint32_t cm_lo = 0xFFFFFFFFu, cm_hi = 0xFFFFFFFFu;
         const bool used = wvalid && rel <= 31 && lane >= c0 - 1;
+
         __syncwarp();
         if (!a.all_changed && used)
             chunk_change_mask(a.chg_cur, chk(raw.x, g.n, a.err), words, cm_lo, cm_hi, sKeep[lane]);
@@ -553,7 +554,7 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                             // change word's previous bits count the new ones
 #pragma unroll
                             for (int w = 0; w < 4; ++w)
-                                if (cand[w]) atomicOr(reinterpret_cast<unsigned int*>(trow + 4 * w), cand[w]);
+                                if (cand[w]) red_or(reinterpret_cast<uint32_t*>(trow + 4 * w), cand[w]);
                             newly_visited(a, o_i, (uint32_t)chunk, imp, eq.old, st_new);
                             note_newly_visited(a, o_i, (uint32_t)chunk, imp);
                         }
@@ -685,7 +686,7 @@ __device__ __forceinline__ void heavy_vertex(const GraphDev& g, const LevelArgs&
                         nw = byte_max(cur, b);
                         if (++tries > kCasRetryLimit) { atomicOr(a.err, kErrCasLimit); break; }
                     }
-                    if (changed && !out_b) atomicOr(a.chg_next + (size_t)u * words + (j >> 5), 1u << (j & 31));
+                    if (changed && !out_b) red_or(a.chg_next + (size_t)u * words + (j >> 5), 1u << (j & 31));
                 }
             }
             if (out_b) bucket_enqueue(a, changed, u, (uint32_t)(j >> 4), 1u << (j & 15));
@@ -848,7 +849,7 @@ __device__ __forceinline__ void bucket_pos(const GraphDev& g, const LevelArgs& a
             } else {
 #pragma unroll
                 for (int w = 0; w < 4; ++w)
-                    if (cand[w]) atomicOr(reinterpret_cast<unsigned int*>(trow + 4 * w), cand[w]);
+                    if (cand[w]) red_or(reinterpret_cast<uint32_t*>(trow + 4 * w), cand[w]);
                 newly_visited(a, o, c, imp, eq.old, st_new);
                 note_newly_visited(a, o, c, imp);
             }
@@ -1750,7 +1751,13 @@ __device__ __forceinline__ void for_each_edge(const GraphDev& g, F&& fn) {
             other = __ldg(g.src_in + e);
             h = __ldg(g.h_in + e);
             const uint32_t aux = KIND == kWC ? __ldg(g.thr_v + v) : 0u;
-            thr = edge_threshold<KIND, true>(g, (uint32_t)other, (uint32_t)v, e, aux);
+            if (KIND == kTrivalency && g.tri_b) {
+                const int2 tb = __ldg(g.tri_b + v);
+                const int cls = (e >= tb.x ? 1 : 0) + (e >= tb.y ? 1 : 0);
+                thr = cls == 0 ? g.tri_thr[0] : (cls == 1 ? g.tri_thr[1] : g.tri_thr[2]);
+            } else {
+                thr = edge_threshold<KIND, true>(g, (uint32_t)other, (uint32_t)v, e, aux);
+            }
         } else {
             other = __ldg(g.col_out + e);
             h = __ldg(g.h_out + e);

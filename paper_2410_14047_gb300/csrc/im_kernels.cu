@@ -1104,10 +1104,35 @@ cudaError_t launch_gather_u32(const uint32_t* src, const int32_t* idx, int64_t m
     return cudaGetLastError();
 }
 
+// Trivalency class bounds of every in-row from the sorted keys: tri_b[v] =
+// (first in-edge of class >= 1, first of class 2), the row end when absent.
+__global__ void k_tri_init(const int32_t* __restrict__ rp_in, int32_t n, int2* __restrict__ tri_b) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) tri_b[v] = make_int2(rp_in[v + 1], rp_in[v + 1]);
+}
+
+__global__ void k_tri_bounds(const unsigned long long* __restrict__ keys, int64_t m, int2* __restrict__ tri_b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long k = keys[i];
+        const int32_t v = (int32_t)(k >> 33);
+        const int c = (int)((k >> 31) & 3u);
+        int pc = -1;  // class of the previous edge of the row (none: row start)
+        if (i > 0) {
+            const unsigned long long kp = keys[i - 1];
+            if ((int32_t)(kp >> 33) == v) pc = (int)((kp >> 31) & 3u);
+        }
+        // each class boundary of a row is crossed by exactly one edge
+        if (pc < 1 && c >= 1) tri_b[v].x = (int32_t)i;
+        if (pc < 2 && c >= 2) tri_b[v].y = (int32_t)i;
+    }
+}
+
 cudaError_t launch_build_in_csr(const int32_t* rp_out, const int32_t* col_out, int32_t n, int64_t m,
                                 int kind, uint32_t tri_seed, const int32_t* hkey, const uint32_t* thr_out,
                                 int32_t* src_in, uint32_t* h_in,
-                                uint32_t* thr_in, int32_t* out_to_in, void* tmp, cudaStream_t st) {
+                                uint32_t* thr_in, int32_t* out_to_in, const int32_t* rp_in, int2* tri_b,
+                                void* tmp, cudaStream_t st) {
     if (m == 0) return cudaSuccess;
     char* p = static_cast<char*>(tmp);
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(p);
@@ -1122,6 +1147,10 @@ cudaError_t launch_build_in_csr(const int32_t* rp_out, const int32_t* col_out, i
     cudaError_t e = launch_radix_sort(keys, perm, m, bits, p, st);
     if (e != cudaSuccess) return e;
     k_in_gather<<<152 * 8, kBlock, 0, st>>>(keys, perm, m, src_out, thr_out, src_in, h_in, thr_in, out_to_in);
+    if (kind == kTrivalency && tri_b) {
+        k_tri_init<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(rp_in, n, tri_b);
+        k_tri_bounds<<<152 * 8, kBlock, 0, st>>>(keys, m, tri_b);
+    }
     return cudaGetLastError();
 }
 

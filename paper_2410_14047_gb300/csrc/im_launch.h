@@ -294,11 +294,13 @@ cudaError_t launch_exclusive_scan(const int32_t* cnt, int32_t n, int32_t* out, v
 // row pointers built beforehand.  hkey (may be NULL = the vertex id itself) is
 // the id each vertex hashes with (batches: its id inside its own graph).
 size_t build_in_csr_tmp_bytes(int64_t m);
-// out_to_in (may be NULL): in-CSR position of every out-edge.
+// out_to_in (may be NULL): in-CSR position of every out-edge; tri_b (trivalency,
+// may be NULL): class bounds of every in-row (rp_in: the in-CSR row starts).
 cudaError_t launch_build_in_csr(const int32_t* rp_out, const int32_t* col_out, int32_t n, int64_t m,
                                 int kind, uint32_t tri_seed, const int32_t* hkey, const uint32_t* thr_out,
                                 int32_t* src_in, uint32_t* h_in,
-                                uint32_t* thr_in, int32_t* out_to_in, void* tmp, cudaStream_t st);
+                                uint32_t* thr_in, int32_t* out_to_in, const int32_t* rp_in, int2* tri_b,
+                                void* tmp, cudaStream_t st);
 // dst[i] = src[idx[i]], i < m.
 cudaError_t launch_gather_u32(const uint32_t* src, const int32_t* idx, int64_t m, uint32_t* dst, cudaStream_t st);
 cudaError_t launch_out_edge_words(const int32_t* rp_out, const int32_t* col_out, int32_t n, int64_t m,
