@@ -178,17 +178,22 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
 // the cover.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long row_terms16(uint4 q) {
-    unsigned long long s = 0;
+    // ranks 1..32 give 2^(32-r) = 0x80000000 >> (r - 1), at most 2^31: summed
+    // in 64 bits; rank 0 and visited (0xFF) give 2^32: counted (r - 1 > 31)
+    unsigned long long lo = 0;
+    uint32_t big = 0;
     const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            const uint32_t r = (w[i] >> (8 * b)) & 0xFFu;
-            s += (r == kVisited) ? (1ull << 32) : (1ull << (32 - r));
+            const uint32_t sh = ((w[i] >> (8 * b)) & 0xFFu) - 1u;
+            const bool is_big = sh > 31u;
+            big += is_big ? 1u : 0u;
+            lo += is_big ? 0u : (0x80000000u >> sh);
         }
     }
-    return s;
+    return ((unsigned long long)big << 32) + lo;
 }
 
 // Sum of the row owned by this lane's segment; valid in every lane of the segment.
