@@ -162,7 +162,10 @@ typedef struct {
  * (0 = 4); fewer pieces a lane means more lanes per row; dense_out: 1 = a
  * propagation level that walks every vertex (dense_div) records what it raises
  * in the change bits only, without a queue, while the frontier stays large
- * (the next level walks every vertex again), 0 = every level builds a queue. */
+ * (the next level walks every vertex again), 0 = every level builds a queue;
+ * dense_all: 1 = such a walk pushes every live simulation of every vertex,
+ * changed or not, so what a vertex raised earlier in the same walk moves on
+ * at once (0 = only the simulations that changed at the previous level). */
 typedef struct {
     int32_t heavy_indeg;
     int32_t light_batches;
@@ -176,6 +179,7 @@ typedef struct {
     int32_t chain;
     int32_t pick_tile;
     int32_t dense_out;
+    int32_t dense_all;
 } im_tuning;
 
 /* One frontier launch of the last selection / build (tracing on). */
@@ -209,7 +213,7 @@ IM_API im_status im_last_stats(const im_ctx* ctx, im_stats* out);
  * stream and report per-kind kernel time in im_stats (adds two event records
  * per launch).  Off by default. */
 IM_API im_status im_ctx_set_timing(im_ctx* ctx, int enable);
-/* Sets (NULL = defaults {256, 4, 0, 2, 1, 0, 1, 2, 1, 8, 4, 1}) or reads the schedule knobs. */
+/* Sets (NULL = defaults {256, 4, 0, 2, 1, 0, 1, 2, 1, 8, 4, 1, 0}) or reads the schedule knobs. */
 IM_API im_status im_ctx_set_tuning(im_ctx* ctx, const im_tuning* tuning);
 IM_API im_status im_ctx_get_tuning(const im_ctx* ctx, im_tuning* tuning);
 /* Bounds of the waits inside the device code, so that a loop that should end

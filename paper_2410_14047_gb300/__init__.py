@@ -79,7 +79,8 @@ class im_tuning(ctypes.Structure):
                 ("grid_blocks", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("persistent", ctypes.c_int32), ("dense_div", ctypes.c_int32),
                 ("lazy_pick", ctypes.c_int32), ("buckets", ctypes.c_int32), ("incremental", ctypes.c_int32),
-                ("chain", ctypes.c_int32), ("pick_tile", ctypes.c_int32), ("dense_out", ctypes.c_int32)]
+                ("chain", ctypes.c_int32), ("pick_tile", ctypes.c_int32), ("dense_out", ctypes.c_int32),
+                ("dense_all", ctypes.c_int32)]
 
 
 class im_trace_rec(ctypes.Structure):

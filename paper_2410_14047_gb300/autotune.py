@@ -4,8 +4,8 @@ Chooses the im_tuning knobs (vertex-to-warp mapping: the in-degree above which
 a hub is pushed by per-simulation hash search instead of an in-edge scan;
 work granularity: 32-edge batches per claimed unit; frontier thresholds: when a
 propagation level walks every vertex in vertex order, and below which level
-size queues switch from vertices to (vertex, chunk) buckets, and whether dense
-walks skip building queues; J-tile width: the 16-simulation register pieces
+size queues switch from vertices to (vertex, chunk) buckets, whether dense
+walks skip building queues and push every live simulation; J-tile width: the 16-simulation register pieces
 one lane sums per row in the estimate + argmax pass) by timing short runs of
 the caller's workload.  The frontier knobs are tried together (every
 combination), then the dense-walk output with them fixed, then the J-tile
@@ -31,7 +31,7 @@ DEFAULT_SPACE = {
 
 # stages of the default search: each stage's combinations are timed with the
 # winners of the earlier stages in place
-DEFAULT_STAGES = [DEFAULT_SPACE, {"dense_out": [0, 1]}, {"pick_tile": [1, 2, 4]}]
+DEFAULT_STAGES = [DEFAULT_SPACE, {"dense_out": [0, 1], "dense_all": [0, 1]}, {"pick_tile": [1, 2, 4]}]
 
 
 def candidates(space: dict | None = None):

@@ -47,7 +47,7 @@ struct im_ctx {
     bool trace = false;
     std::vector<float> launch_ms;    // kernel time per launch sequence number (tracing)
     std::vector<im_trace_rec> recs;  // frontier launches of the last call
-    im_tuning tuning{256, 4, 0, 2, 1, 0, 1, 2, 1, 8, 4, 1};
+    im_tuning tuning{256, 4, 0, 2, 1, 0, 1, 2, 1, 8, 4, 1, 0};
     // bounds of the device-side waits (im_ctx_set_limits)
     uint64_t barrier_limit_ns = kDefaultBarrierLimitNs;
     int32_t max_levels = kMaxLevels - 2;
@@ -322,7 +322,7 @@ extern "C" im_status im_ctx_set_timing(im_ctx* c, int enable) {
 extern "C" im_status im_ctx_set_tuning(im_ctx* c, const im_tuning* t) {
     if (!c) return IM_E_INVAL;
     if (!t) {
-        c->tuning = im_tuning{256, 4, 0, 2, 1, 0, 1, 2, 1, 8, 4, 1};
+        c->tuning = im_tuning{256, 4, 0, 2, 1, 0, 1, 2, 1, 8, 4, 1, 0};
         return IM_OK;
     }
     if (t->heavy_indeg < 0 || t->light_batches < 1 || t->light_batches > 4096 || t->grid_blocks < 0 ||
@@ -330,7 +330,7 @@ extern "C" im_status im_ctx_set_tuning(im_ctx* c, const im_tuning* t) {
         t->dense_div < 0 || t->lazy_pick < 0 || t->lazy_pick > 1 || t->buckets < 0 || t->buckets > 1024 || t->incremental < 0 || t->incremental > 2 ||
         t->chain < 0 || t->chain > 64 ||
         !(t->pick_tile == 0 || t->pick_tile == 1 || t->pick_tile == 2 || t->pick_tile == 4) ||
-        t->dense_out < 0 || t->dense_out > 1)
+        t->dense_out < 0 || t->dense_out > 1 || t->dense_all < 0 || t->dense_all > 1)
         return fail(c, IM_E_INVAL, "tuning out of range");
     c->tuning = *t;
     return IM_OK;
@@ -821,6 +821,7 @@ static LevelArgs level_args(im_sketch* sk) {
     a.e_dense = sk->g->m;
     a.dense_div = sk->gflag ? 0 : t.dense_div;  // a batch build covers only some graphs
     a.dense_out = t.dense_out;
+    a.dense_all = t.dense_all;
     a.gid = sk->gid;
     a.gcount = sk->gcount;
     a.gflag = sk->gflag;

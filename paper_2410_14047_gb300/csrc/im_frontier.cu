@@ -400,7 +400,7 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                                             StatT& st_cas, StatT& st_new,
                                             StatT& st_batches, StatT& st_dealt,
                                             StatT& st_live, bool skip_heavy, uint32_t (*sKeep)[kKeepWords], bool out_b,
-                                            bool out_d, StatT* st_chg, StatT& st_draised) {
+                                            bool out_d, StatT* st_chg, StatT& st_draised, bool all_sims) {
     const int lane = (int)lane_id();
     const int J = a.J, words = a.words;
     const int64_t fend = min(El, b1 << 5);
@@ -455,11 +455,15 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
         const bool used = wvalid && rel <= 31 && lane >= c0 - 1;
 
         __syncwarp();
-        if (!a.all_changed && used)
+        if (!a.all_changed && used && (!all_sims || st_chg))
             chunk_change_mask(a.chg_cur, chk(raw.x, g.n, a.err), words, cm_lo, cm_hi, sKeep[lane]);
         // a walk over every vertex counts the changed ones (the previous
         // level's output had no queue): once each, where its row starts
         if (st_chg && used && rel >= 0 && (cm_lo | cm_hi) != 0u) ++*st_chg;
+        // all_sims: the walk pushes every live simulation of every vertex,
+        // changed or not (what a source raised earlier in this same walk then
+        // moves on at once)
+        if (all_sims) { cm_lo = 0xFFFFFFFFu; cm_hi = 0xFFFFFFFFu; }
         if constexpr (MODE == kPush) {
             // dense walk: the heavy queue pushes the hubs
             if (skip_heavy && used) {
@@ -515,7 +519,7 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
             if (k < total) {
                 chunk = chk(nth_chunk(ml_i, mh_i, k - ex_i), a.chunks, a.err);
                 uint32_t chb = 0xFFFFu;
-                if (!a.all_changed) {
+                if (!a.all_changed && !all_sims) {
                     const uint32_t cw = words <= kKeepWords ? sKeep[w_i][chunk >> 1]
                                                             : __ldcg(a.chg_cur + (size_t)q_i * words + (chunk >> 1));
                     chb = (cw >> ((chunk & 1) * 16)) & 0xFFFFu;
@@ -1206,6 +1210,7 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
         return;
     }
     int32_t nl = (int32_t)(cl >> kCountShift);
+    const int32_t nl_in = nl;  // the input's count (raised items after a dense-format level)
     int64_t El = (int64_t)(cl & kEdgeMask);
     int32_t nh = (int32_t)(ch >> kCountShift);
     const QEntry* ql = a.ql_in;
@@ -1269,6 +1274,13 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
         if (MODE == kPush) atomicAdd(a.stats + kStSweepHeavy, (unsigned long long)nhv);
     }
     StatT draised = 0;  // raised items of a dense-format output
+    // dense_all: a dense walk pushes every live simulation while the frontier
+    // is large (a vertex queue that went dense, or a dense-format input with
+    // more than two raised items per vertex): what a vertex raised earlier in
+    // the walk then moves on in the same level; a small dense-format input (a
+    // rebuild's second level) pushes only what changed
+    const bool all_sims = MODE == kPush && dense && a.dense_all != 0 &&
+                          (!in_d || (int64_t)nl_in > 2 * (int64_t)a.n_dense);
     for (UnitCursor uc(total + cp.units); uc.valid(); uc.next(a.claim)) {
         const int64_t unit = uc.unit;
         if (unit >= total) {
@@ -1286,13 +1298,13 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
             const int64_t b1 = min(nbl, b0 + lb);
             light_slice<KIND, MODE>(g, a, ql, sX, sTab, b0, b1, nl, El, ls.chunks, ls.cas, ls.fresh,
                                     ls.batches, ls.dealt, ls.live, dense && nh > 0, sKeep, out_b, out_d,
-                                    MODE == kPush && in_d ? &ls.chg : nullptr, draised);
+                                    MODE == kPush && in_d ? &ls.chg : nullptr, draised, all_sims);
         } else {
             const int64_t hu = (int64_t)unit - nhv - lunits;
             const int64_t b0 = hu * lb;
             const int64_t b1 = min(nbh, b0 + lb);
             light_slice<KIND, MODE>(g, a, a.qh_in, sX, sTab, b0, b1, nh, Eh, ls.chunks, ls.cas, ls.fresh,
-                                    ls.batches, ls.dealt, ls.live, false, sKeep, out_b, false, nullptr, draised);
+                                    ls.batches, ls.dealt, ls.live, false, sKeep, out_b, false, nullptr, draised, false);
         }
     }
     if (out_d) dense_count_flush(a, draised);

@@ -118,6 +118,7 @@ struct LevelArgs {
     uint32_t* nv;                        // covers: registers newly visited since the last build (may be NULL)
     int32_t chain;                       // continuation depth on small bucket levels (0 = none)
     int32_t dense_out;                   // dense walks of a propagation may output dense format
+    int32_t dense_all;                   // dense walks of a propagation push every live simulation
 };
 
 // All levels of a phase in one cooperative launch (grid barrier between levels).
