@@ -208,7 +208,11 @@ __device__ __forceinline__ void chunk_change_mask(const uint32_t* __restrict__ c
 // Position of the r-th (0-based) set bit of the 64-bit mask (lo, hi).
 __device__ __forceinline__ int nth_chunk(uint32_t lo, uint32_t hi, int r) {
     const int cl = __popc(lo);
-    return r < cl ? (int)__fns(lo, 0u, r + 1) : 32 + (int)__fns(hi, 0u, r - cl + 1);
+    uint32_t m = r < cl ? lo : hi;
+    // an edge is live in a few consecutive chunks: clearing the r lowest set
+    // bits takes a handful of steps
+    for (int t = r < cl ? r : r - cl; t > 0; --t) m &= m - 1u;
+    return (r < cl ? 0 : 32) + __ffs((int)m) - 1;
 }
 
 // Vertex-format enqueue (warp-collective): vertex o, whose registers changed
