@@ -127,18 +127,16 @@ __device__ __forceinline__ bool is_heavy(int32_t deg, uint32_t thr, int32_t heav
 // 4-byte words: the four first attempts are issued together, retries (a word
 // changed by another thread meanwhile) one word at a time.  Returns the
 // changed registers as 16 bits.
-__device__ __forceinline__ uint32_t merge_chunk(uint8_t* trow, const uint32_t cand[4], uint4 tg,
-                                               StatT& n_cas, uint32_t* err) {
+// The same with the merged words nw (byte_max of tg and cand) already known.
+__device__ __forceinline__ uint32_t merge_chunk_nw(uint8_t* trow, const uint32_t cand[4], uint4 tg,
+                                                  const uint32_t nw[4], StatT& n_cas, uint32_t* err) {
     uint32_t cur[4] = {tg.x, tg.y, tg.z, tg.w};
-    uint32_t nw[4], prev[4];
+    uint32_t prev[4];
     bool pend[4];
     uint32_t bits = 0u;
     unsigned int* addr = reinterpret_cast<unsigned int*>(trow);
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
-        nw[w] = byte_max(cur[w], cand[w]);
-        pend[w] = cand[w] != 0u && nw[w] != cur[w];
-    }
+    for (int w = 0; w < 4; ++w) pend[w] = nw[w] != cur[w];
 #pragma unroll
     for (int w = 0; w < 4; ++w)
         if (pend[w]) prev[w] = atomicCAS(addr + w, cur[w], nw[w]);
@@ -169,6 +167,20 @@ __device__ __forceinline__ uint32_t merge_chunk(uint8_t* trow, const uint32_t ca
         }
     }
     return bits;
+}
+
+__device__ __forceinline__ uint32_t merge_chunk(uint8_t* trow, const uint32_t cand[4], uint4 tg,
+                                               StatT& n_cas, uint32_t* err) {
+    const uint32_t nw[4] = {byte_max(tg.x, cand[0]), byte_max(tg.y, cand[1]), byte_max(tg.z, cand[2]),
+                            byte_max(tg.w, cand[3])};
+    return merge_chunk_nw(trow, cand, tg, nw, n_cas, err);
+}
+
+// Registers of cand (ranks, no visited bytes) above those of t: 0x80 in each
+// such byte.  (t | 0x80) - c never borrows across bytes because every byte of
+// c is below 0x80.
+__device__ __forceinline__ uint32_t raise_hi(uint32_t t, uint32_t c) {
+    return ~((t | 0x80808080u) - c) & 0x80808080u;
 }
 
 // Two bits per change word: bit 0 = a simulation of its low 16 changed, bit 1
@@ -536,7 +548,7 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                     const uint4 tg = ld_cg16(trow);
                     const uint32_t sw[4] = {src.x, src.y, src.z, src.w};
                     const uint32_t tw[4] = {tg.x, tg.y, tg.z, tg.w};
-                    uint32_t cand[4];
+                    uint32_t cand[4], nwv[4];
 #pragma unroll
                     for (int w = 0; w < 4; ++w) {
                         const uint32_t L = live4(xs[w], h_i, t_i) & bits_to_bytes((chb >> (4 * w)) & 0xFu);
@@ -545,8 +557,14 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                         else cand[w] = L & ~visited_bytes(tw[w]);
                         any |= cand[w];
                         // registers this item raises, as the loaded target piece shows
-                        if constexpr (MODE == kPush) imp |= bytes_to_bits(byte_max(tw[w], cand[w]) ^ tw[w]) << (4 * w);
-                        else if constexpr (MODE == kCover) imp |= bytes_to_bits(cand[w]) << (4 * w);
+                        if constexpr (MODE == kPush) {
+                            const uint32_t gt = raise_hi(tw[w], cand[w]) >> 7;
+                            imp |= ((gt * 0x10204080u) >> 28) << (4 * w);
+                            const uint32_t m = gt * 0xFFu;
+                            nwv[w] = (tw[w] & ~m) | (cand[w] & m);
+                        } else if constexpr (MODE == kCover) {
+                            imp |= bytes_to_bits(cand[w]) << (4 * w);
+                        }
                     }
                     if constexpr (MODE == kAffect) imp = mark_affected(a, cand, o_i, (uint32_t)chunk, st_new);
                     // the enqueue's loads and atomics go out before the register update
@@ -556,7 +574,7 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                     if (MODE != kAffect && any) {
                         ++st_chunks;
                         if constexpr (MODE == kPush) {
-                            nbits = merge_chunk(trow, cand, tg, st_cas, a.err);
+                            nbits = merge_chunk_nw(trow, cand, tg, nwv, st_cas, a.err);
                         } else {
                             // the visited marks go out without a reply; the
                             // change word's previous bits count the new ones
