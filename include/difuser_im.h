@@ -127,6 +127,7 @@ typedef struct {
     uint64_t pull_entries;    /* out-bucket entries walked by those pulls */
     uint64_t sweep_changed_buckets; /* (vertex, 16-simulation chunk) buckets whose registers a
                                  propagation level changed (bucket-format levels) */
+    uint64_t pick_refreshed;  /* rows whose stored S_u lazy picks recomputed */
 } im_stats;
 
 /* Schedule knobs of the frontier kernels (chosen by the autotuner; results
@@ -163,9 +164,11 @@ typedef struct {
  * propagation level that walks every vertex (dense_div) records what it raises
  * in the change bits only, without a queue, while the frontier stays large
  * (the next level walks every vertex again), 0 = every level builds a queue;
- * dense_all: 1 = such a walk pushes every live simulation of every vertex,
+ * dense_all: bit 0 = such a walk pushes every live simulation of every vertex,
  * changed or not, so what a vertex raised earlier in the same walk moves on
- * at once (0 = only the simulations that changed at the previous level). */
+ * at once (clear: only the simulations that changed at the previous level);
+ * bit 1 = a cover level that walks every vertex pushes every visited
+ * simulation, not only those visited at the previous level (values 0..3). */
 typedef struct {
     int32_t heavy_indeg;
     int32_t light_batches;

@@ -71,7 +71,7 @@ class im_stats(ctypes.Structure):
                                                "sweep_dealt", "sweep_edges_live", "sweep_buckets",
                                                "sweep_bucket_entries", "affected",
                                                "pull_buckets", "pull_entries",
-                                               "sweep_changed_buckets")]
+                                               "sweep_changed_buckets", "pick_refreshed")]
 
 
 class im_tuning(ctypes.Structure):

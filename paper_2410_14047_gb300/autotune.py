@@ -31,7 +31,9 @@ DEFAULT_SPACE = {
 
 # stages of the default search: each stage's combinations are timed with the
 # winners of the earlier stages in place
-DEFAULT_STAGES = [DEFAULT_SPACE, {"dense_out": [0, 1], "dense_all": [0, 1]}, {"pick_tile": [1, 2, 4]}]
+# (dense_all: bit 0 = propagation walks, bit 1 = cover walks push every
+# live / visited simulation)
+DEFAULT_STAGES = [DEFAULT_SPACE, {"dense_out": [0, 1], "dense_all": [0, 1, 2, 3]}, {"pick_tile": [1, 2, 4]}]
 
 
 def candidates(space: dict | None = None):

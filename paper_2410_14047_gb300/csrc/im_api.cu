@@ -248,6 +248,9 @@ struct im_sketch {
     int32_t bq_cap = 0;
     bool lazy = false;      // picks after the first refresh stored sums only (im_select_seeds)
     bool chg_dirty = true;  // change masks may hold bits (new sketch, or a phase that failed)
+    // the registers were never written (a new sketch): the first fill writes
+    // every register without reading it, so no zeroing pass precedes it
+    bool fresh = true;
     bool lb_ready = false;  // lb holds the sums of the last full pick or later refreshes
     // a selection in flight: phases and rebuilds queue without host reads;
     // their error word is read once at the end
@@ -330,7 +333,7 @@ extern "C" im_status im_ctx_set_tuning(im_ctx* c, const im_tuning* t) {
         t->dense_div < 0 || t->lazy_pick < 0 || t->lazy_pick > 1 || t->buckets < 0 || t->buckets > 1024 || t->incremental < 0 || t->incremental > 2 ||
         t->chain < 0 || t->chain > 64 ||
         !(t->pick_tile == 0 || t->pick_tile == 1 || t->pick_tile == 2 || t->pick_tile == 4) ||
-        t->dense_out < 0 || t->dense_out > 1 || t->dense_all < 0 || t->dense_all > 1)
+        t->dense_out < 0 || t->dense_out > 1 || t->dense_all < 0 || t->dense_all > 3)
         return fail(c, IM_E_INVAL, "tuning out of range");
     c->tuning = *t;
     return IM_OK;
@@ -770,7 +773,6 @@ static im_status sketch_alloc(im_ctx* c, im_graph* g, int32_t J, im_sketch** out
     if (e == cudaSuccess) e = cudaMemsetAsync(sk->ticket.p, 0, 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(sk->stats.p, 0, sk->stats.bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(sk->err.p, 0, 4, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(sk->M.p, 0, sk->M.bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(sk->nv.p, 0, sk->nv.bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(sk->aff.p, 0, sk->aff.bytes, st);
     if (e != cudaSuccess) {
@@ -1192,8 +1194,12 @@ static im_status incremental_rebuild(im_sketch* sk) {
 static im_status build_registers(im_sketch* sk) {
     im_ctx* c = sk->ctx;
     CK(c, timed(c, kTFill, [&] {
-        return launch_fill(sk->M.as<uint8_t>(), sk->g->n, sk->J, sk->salt.as<uint32_t>(), c->stream);
+        return launch_fill(sk->M.as<uint8_t>(), sk->g->n, sk->J, sk->salt.as<uint32_t>(), sk->fresh, c->stream);
     }));
+    sk->fresh = false;
+    // every stored S_u stays a lower bound, but after a full build every row
+    // is stale for a lazy pick: the next pick reads every row in one pass
+    sk->lb_ready = false;
     return propagate(sk);
 }
 
@@ -1234,6 +1240,7 @@ static im_status stats_collect(im_sketch* sk) {
     s.pull_buckets = h[kStPullBuckets];
     s.pull_entries = h[kStPullEntries];
     s.sweep_changed_buckets = h[kStSweepChangedBuckets];
+    s.pick_refreshed = h[kStPickRefreshed];
     // algorithmic bytes of the sweeps: queue entry (16 B) + the queued vertex's
     // register row (J B) per queued vertex; live chunk mask (4 B, 8 B when
     // J = 1024) per in-edge; source id + edge hash (8 B, + 4 B threshold for
@@ -1489,6 +1496,7 @@ static PickArgs pick_args(im_sketch* sk, int k) {
     a.chunks = sk->J / 16;
     a.nv = sk->incr ? sk->nv.as<uint32_t>() : nullptr;
     a.tile = sk->ctx->tuning.pick_tile;
+    a.stats = sk->stats.as<unsigned long long>();
     return a;
 }
 
@@ -1951,6 +1959,9 @@ extern "C" void im_batch_free(im_batch* b) {
 // Fill of the flagged graphs' rows, then propagation from their vertices.
 static im_status batch_build(im_sketch* sk) {
     im_ctx* c = sk->ctx;
+    // the flagged fill keeps visited registers: a new sketch's are zeroed first
+    if (sk->fresh) CK(c, cudaMemsetAsync(sk->M.p, 0, sk->M.bytes, c->stream));
+    sk->fresh = false;
     CK(c, timed(c, kTFill, [&] {
         return launch_fill_flagged(sk->M.as<uint8_t>(), sk->g->n, sk->J, sk->salt.as<uint32_t>(),
                                    sk->gid, sk->gflag, sk->g->hkey.as<int32_t>(), c->stream);

@@ -1301,8 +1301,14 @@ __device__ __forceinline__ void level_work(const GraphDev& g, const LevelArgs& a
     // more than two raised items per vertex): what a vertex raised earlier in
     // the walk then moves on in the same level; a small dense-format input (a
     // rebuild's second level) pushes only what changed
-    const bool all_sims = MODE == kPush && dense && a.dense_all != 0 &&
-                          (!in_d || (int64_t)nl_in > 2 * (int64_t)a.n_dense);
+    // A dense cover walk (dense_all bit 1) pushes every visited simulation of
+    // every vertex: a register visited at an earlier level, or by an earlier
+    // cover, has every live successor visited already (a cover's visited set
+    // is closed under live edges once it ends), so it marks nothing, and what
+    // a vertex visited earlier in the walk moves on in the same level
+    const bool all_sims = (MODE == kPush && dense && (a.dense_all & 1) != 0 &&
+                           (!in_d || (int64_t)nl_in > 2 * (int64_t)a.n_dense)) ||
+                          (MODE == kCover && dense && (a.dense_all & 2) != 0);
     for (UnitCursor uc(total + cp.units); uc.valid(); uc.next(a.claim)) {
         const int64_t unit = uc.unit;
         if (unit >= total) {

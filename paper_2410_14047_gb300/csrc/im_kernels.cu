@@ -67,6 +67,9 @@ cudaError_t launch_sims(uint64_t seed, int J, uint32_t* X, uint32_t* salt, uint1
 // a3: Fill-Sketches (Alg. 1).  Thread per 16-byte chunk of a register row;
 // non-visited bytes get the vertex's rank, visited bytes are kept.
 // ---------------------------------------------------------------------------
+// FRESH: the registers were never written (a new sketch), none is visited:
+// every register is written without reading the row first.
+template <bool FRESH>
 __global__ void __launch_bounds__(kBlock) k_fill(uint8_t* __restrict__ M, int32_t n, int J,
                                                  const uint32_t* __restrict__ salt) {
     const int cpr_log = __ffs(J >> 4) - 1;  // chunks per row = J/16, a power of two
@@ -76,7 +79,7 @@ __global__ void __launch_bounds__(kBlock) k_fill(uint8_t* __restrict__ M, int32_
         const uint32_t u = (uint32_t)(c >> cpr_log);
         const int ch = (int)(c & ((1 << cpr_log) - 1));
         uint4* p = reinterpret_cast<uint4*>(M + (size_t)u * J + ch * 16);
-        const uint4 cur = *p;
+        const uint4 cur = FRESH ? make_uint4(0u, 0u, 0u, 0u) : *p;
         const uint32_t ku = mm3_k(u);
         const uint4* sl = reinterpret_cast<const uint4*>(salt + ch * 16);
         uint32_t w[4] = {cur.x, cur.y, cur.z, cur.w};
@@ -131,12 +134,13 @@ cudaError_t launch_fill_flagged(uint8_t* M, int32_t n, int J, const uint32_t* sa
     return cudaGetLastError();
 }
 
-cudaError_t launch_fill(uint8_t* M, int32_t n, int J, const uint32_t* salt, cudaStream_t st) {
+cudaError_t launch_fill(uint8_t* M, int32_t n, int J, const uint32_t* salt, bool fresh, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     const int64_t total = (int64_t)n * (J / 16);
     int64_t grid = (total + kBlock - 1) / kBlock;
     if (grid > 152 * 16) grid = 152 * 16;
-    k_fill<<<(int)grid, kBlock, 0, st>>>(M, n, J, salt);
+    if (fresh) k_fill<true><<<(int)grid, kBlock, 0, st>>>(M, n, J, salt);
+    else k_fill<false><<<(int)grid, kBlock, 0, st>>>(M, n, J, salt);
     return cudaGetLastError();
 }
 
@@ -177,21 +181,27 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
 // and its estimate J*2^32/(phi*S), marks its row visited and queues it for
 // the cover.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t shr_clamped(uint32_t x, uint32_t s) {
+    // PTX shr.u32 clamps shift amounts above 32 to 32 (result 0)
+    uint32_t r;
+    asm("shr.u32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(s));
+    return r;
+}
+
 __device__ __forceinline__ unsigned long long row_terms16(uint4 q) {
     // ranks 1..32 give 2^(32-r) = 0x80000000 >> (r - 1), at most 2^31: summed
-    // in 64 bits; rank 0 and visited (0xFF) give 2^32: counted (r - 1 > 31)
+    // in 64 bits; rank 0 and visited (0xFF) give 2^32: counted per word from
+    // its zero and visited bytes (r - 1 wraps above 31 there, and the
+    // clamped shift adds 0)
     unsigned long long lo = 0;
     uint32_t big = 0;
     const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
+        const uint32_t nz = (((w[i] & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w[i]) & 0x80808080u;
+        big += (uint32_t)__popc((~nz & 0x80808080u) | (w[i] & 0x80808080u));
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const uint32_t sh = ((w[i] >> (8 * b)) & 0xFFu) - 1u;
-            const bool is_big = sh > 31u;
-            big += is_big ? 1u : 0u;
-            lo += is_big ? 0u : (0x80000000u >> sh);
-        }
+        for (int b = 0; b < 4; ++b) lo += shr_clamped(0x80000000u, __byte_perm(w[i], 0u, 0x4440u | b) - 1u);
     }
     return ((unsigned long long)big << 32) + lo;
 }
@@ -380,6 +390,7 @@ __device__ __forceinline__ bool is_picked(const uint32_t* seed_bits, int64_t v) 
 // so every warp keeps several KB of the stream in flight.
 constexpr int kPickSteps = 2;
 constexpr int kLazySteps = 4;
+constexpr int kLazyRows = 4;  // stale rows a lazy-pick warp refreshes at once
 __host__ __device__ __forceinline__ void pick_layout(int J, int tile, int& cpl, int& lpr, int& rpw) {
     const int cpr = J >> 4;
     // at most 32 lanes a row: a row of 64 pieces (J = 1024) takes 2 a lane at least
@@ -457,6 +468,8 @@ __global__ void __launch_bounds__(kBlock) k_pick_lazy(PickArgs a) {
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     constexpr int U = kLazySteps;
+    const int cpr = J >> 4;
+    unsigned refreshed = 0;  // rows refreshed by this warp
     Top2 t;
     // U * 32 vertices a warp step: the stored sums and picked words load first
     for (int64_t base = warp * 32 * U; base < a.n; base += nwarps * 32 * U) {
@@ -474,18 +487,47 @@ __global__ void __launch_bounds__(kBlock) k_pick_lazy(PickArgs a) {
             const bool ok = v < a.n && !((pw[u] >> lane) & 1u);
             const bool stale = ok && (lv[u] < Sc || (lv[u] == Sc && (int32_t)v < uc));
             unsigned int m = __ballot_sync(0xFFFFFFFFu, stale);
+            refreshed += (unsigned)__popc(m);
+            // stale rows cluster (influential vertices sit together): the
+            // warp refreshes kLazyRows of them at once, their loads in flight
+            // together
             while (m) {
-                const int b = __ffs(m) - 1;
-                m &= m - 1;
-                const unsigned long long s = warp_row_sum(a.M, J, (int32_t)(base + u * 32 + b));
-                if (lane == b) {
-                    lv[u] = s;
-                    a.lb[v] = s;
+                int b[kLazyRows];
+#pragma unroll
+                for (int r = 0; r < kLazyRows; ++r) {
+                    b[r] = m ? __ffs(m) - 1 : -1;
+                    m &= m - 1;
+                }
+                unsigned long long s[kLazyRows];
+#pragma unroll
+                for (int r = 0; r < kLazyRows; ++r) s[r] = 0ull;
+                // a row has at most 64 pieces: piece lane, then lane + 32
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = lane + 32 * h;
+                    if (c >= cpr) break;  // lanes past the row's pieces (J < 512) sum nothing
+                    uint4 q[kLazyRows];
+#pragma unroll
+                    for (int r = 0; r < kLazyRows; ++r)
+                        q[r] = b[r] >= 0 ? __ldcg(reinterpret_cast<const uint4*>(a.M + (size_t)(base + u * 32 + b[r]) * J) + c)
+                                         : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                    for (int r = 0; r < kLazyRows; ++r) s[r] += row_terms16(q[r]);
+                }
+#pragma unroll
+                for (int r = 0; r < kLazyRows; ++r) {
+                    if (b[r] < 0) continue;  // warp-uniform
+                    const unsigned long long sr = warp_sum(s[r]);
+                    if (lane == b[r]) {
+                        lv[u] = sr;
+                        a.lb[v] = sr;
+                    }
                 }
             }
             if (ok) t.insert(lv[u], (int32_t)v);
         }
     }
+    if (a.stats && lane == 0 && refreshed) atomicAdd(a.stats + kStPickRefreshed, (unsigned long long)refreshed);
     pick_finish(a, t);
 }
 

@@ -33,6 +33,7 @@ enum StatIndex : int {
     kStPullBuckets,         // out-buckets queued by the pulls of incremental rebuilds
     kStPullEntries,         // out-bucket entries walked by those pulls
     kStSweepChangedBuckets, // (vertex, chunk) buckets whose registers changed (bucket-format levels)
+    kStPickRefreshed,       // rows whose stored S_u a lazy pick recomputed
     kStCount
 };
 
@@ -213,6 +214,7 @@ struct PickArgs {
     int32_t chunks;
     uint32_t* nv;                 // registers newly visited since the last build (may be NULL)
     int tile;                     // J-tile width of a full pick: 16-byte pieces a lane sums (1, 2, 4)
+    unsigned long long* stats;    // statistics block (rows refreshed by lazy picks; may be NULL)
 };
 
 // Blocks of a full pick: one row group per warp step, at most 152 * 8; tile
@@ -222,7 +224,7 @@ int pick_lazy_grid(int32_t n);
 
 cudaError_t launch_sims(uint64_t seed, int J, uint32_t* X, uint32_t* salt, uint16_t* tab,
                         cudaStream_t st);
-cudaError_t launch_fill(uint8_t* M, int32_t n, int J, const uint32_t* salt, cudaStream_t st);
+cudaError_t launch_fill(uint8_t* M, int32_t n, int J, const uint32_t* salt, bool fresh, cudaStream_t st);
 // Fill of the rows whose graph has gflag[gid[u]] != 0 (batches).
 cudaError_t launch_fill_flagged(uint8_t* M, int32_t n, int J, const uint32_t* salt, const int32_t* gid,
                                 const uint8_t* gflag, const int32_t* hkey, cudaStream_t st);

@@ -40,7 +40,7 @@ def cost(t):
     # a schedule-dependent run time with one best point in the default space
     return (1.0 + 0.1 * abs(t["light_batches"] - 16) + 0.2 * (t["dense_div"] != 2)
             + 0.05 * (t["heavy_indeg"] == 256) + 0.3 * (t["buckets"] == 0) + 0.01 * (t["pick_tile"] != 2)
-            + 0.02 * (t["dense_out"] != 0) + 0.03 * (t["dense_all"] != 1))
+            + 0.02 * (t["dense_out"] != 0) + 0.03 * (t["dense_all"] != 3))
 
 
 def test_every_candidate_is_tried_and_the_fastest_kept(fake):
@@ -55,7 +55,7 @@ def test_every_candidate_is_tried_and_the_fastest_kept(fake):
     for v in space.values():
         n *= len(v)
     # the frontier knobs together, then the dense output, then the J-tile width
-    assert len(rep["trials"]) == n + 4 + len(A.DEFAULT_STAGES[2]["pick_tile"])
+    assert len(rep["trials"]) == n + 8 + len(A.DEFAULT_STAGES[2]["pick_tile"])
     tried = [tuple(sorted(tr["tuning"].items())) for tr in rep["trials"][:n]]
     assert len(set(tried)) == n
     best = min(candidates_with_cost(space), key=lambda x: x[1])[0]
@@ -63,14 +63,14 @@ def test_every_candidate_is_tried_and_the_fastest_kept(fake):
         assert ctx.tuning[k] == v and rep["tuning"][k] == v
     for tr in rep["trials"][n:]:
         assert {k: tr["tuning"][k] for k in best} == best
-    for tr in rep["trials"][n + 4:]:
-        assert tr["tuning"]["dense_out"] == 0 and tr["tuning"]["dense_all"] == 1
+    for tr in rep["trials"][n + 8:]:
+        assert tr["tuning"]["dense_out"] == 0 and tr["tuning"]["dense_all"] == 3
     assert ctx.tuning["pick_tile"] == 2 and rep["tuning"]["pick_tile"] == 2
-    assert ctx.tuning["dense_out"] == 0 and ctx.tuning["dense_all"] == 1
+    assert ctx.tuning["dense_out"] == 0 and ctx.tuning["dense_all"] == 3
     # knobs outside the space keep the context's values
     for k in ("grid_blocks", "check_every", "persistent", "lazy_pick", "incremental", "chain"):
         assert ctx.tuning[k] == BASE[k]
-    assert rep["ms"] == pytest.approx(cost(dict(BASE, **best, pick_tile=2, dense_out=0, dense_all=1)) * 1e3)
+    assert rep["ms"] == pytest.approx(cost(dict(BASE, **best, pick_tile=2, dense_out=0, dense_all=3)) * 1e3)
 
 
 def candidates_with_cost(space):

@@ -46,6 +46,7 @@ SCHEDULES = {
     "levels": {"persistent": 0, "dense_div": 2},
     "full_rebuilds": {"incremental": 0, "chain": 0, "lazy_pick": 0},
     "dense_walks": {"buckets": 0, "dense_div": 1000000, "dense_out": 1, "incremental": 0},
+    "dense_all_sims": {"buckets": 0, "dense_div": 1000000, "dense_out": 1, "dense_all": 3, "incremental": 2},
 }
 
 

@@ -329,7 +329,12 @@ def test_errors(im, ctx):
                                     {"dense_out": 0, "dense_div": 2, "buckets": 0},
                                     {"dense_out": 1, "dense_div": 1000000, "buckets": 0, "persistent": 0},
                                     {"dense_all": 1, "dense_div": 2, "buckets": 0},
-                                    {"dense_all": 1, "dense_out": 0, "dense_div": 1000000}])
+                                    {"dense_all": 1, "dense_out": 0, "dense_div": 1000000},
+                                    {"dense_all": 3, "dense_div": 2, "buckets": 0},
+                                    {"dense_all": 2, "dense_div": 1000000, "buckets": 0, "persistent": 0},
+                                    {"dense_all": 3, "dense_out": 0, "dense_div": 1000000, "incremental": 2,
+                                     "buckets": 0},
+                                    {"dense_all": 2, "dense_div": 2, "buckets": 1024}])
 @pytest.mark.parametrize("gname,mname,J", [("rmat12", "wc", 256), ("cl5k", "p01", 64),
                                            ("er2k", "wc", 1024), ("rmat12", "tri", 32)])
 def test_tuning_does_not_change_results(im, ctx, tuning, gname, mname, J):
