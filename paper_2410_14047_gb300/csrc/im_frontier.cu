@@ -1646,34 +1646,7 @@ cudaError_t launch_level(int kind, int mode, const GraphDev& g, const LevelArgs&
 // next 32 rows and every lane picks its row among them (a lane whose edge
 // lies past those rows, after a run of empty rows, searches on its own).
 // ---------------------------------------------------------------------------
-constexpr int kLcmEdgesPerWarp = 512;
-
-// Last row r in [lo, hi) with start(r) <= e (starts non-decreasing, start(lo) <= e), warp-wide.
-template <class S>
-__device__ __forceinline__ int32_t row_of_warp(S&& start, int32_t lo, int32_t hi, int64_t e) {
-    const int lane = (int)lane_id();
-    while (hi - lo > 1) {
-        const int32_t step = (hi - lo + 31) >> 5;
-        const int64_t idx = (int64_t)lo + (int64_t)step * (lane + 1);
-        const bool le = idx < hi && start((int32_t)idx) <= e;
-        const int c = __popc(__ballot_sync(0xFFFFFFFFu, le));
-        const int32_t nlo = lo + step * c;
-        const int32_t nhi = (c < 32) ? (int32_t)min((int64_t)hi, (int64_t)lo + (int64_t)step * (c + 1)) : hi;
-        lo = nlo;
-        hi = nhi;
-    }
-    return lo;
-}
-
-// Same search by one thread (binary).
-template <class S>
-__device__ __forceinline__ int32_t row_of_thread(S&& start, int32_t lo, int32_t hi, int64_t e) {
-    while (hi - lo > 1) {
-        const int32_t mid = lo + ((hi - lo) >> 1);
-        if (start(mid) <= e) lo = mid; else hi = mid;
-    }
-    return lo;
-}
+// (kLcmEdgesPerWarp, row_of_warp and the row walks are in im_device.cuh.)
 
 // Live masks of one edge over every chunk that holds a candidate simulation:
 // fn(c, m16) for each chunk c with m16 != 0 (bit i: simulation 16c + i live).
@@ -1721,61 +1694,6 @@ __device__ __forceinline__ void edge_live_chunks(uint32_t h, uint32_t thr, int J
                 break;
             }
     }
-}
-
-// Edge-balanced walk of a flat space [0, m) split into rows by the
-// non-decreasing starts start(0..nrows) (start(0) = 0, start(nrows) = m), a
-// warp taking kLcmEdgesPerWarp consecutive positions; ALL: every lane calls
-// fn(f, row, valid) together, else fn(f, row) once per position.
-template <bool ALL, class S, class F>
-__device__ __forceinline__ void walk_rows_by(S&& start, int32_t nrows, int64_t m, F&& fn) {
-    const int lane = (int)lane_id();
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t s0 = warp * kLcmEdgesPerWarp; s0 < m; s0 += nwarps * kLcmEdgesPerWarp) {
-        const int64_t s1 = min(m, s0 + kLcmEdgesPerWarp);
-        int32_t r0 = row_of_warp(start, 0, nrows, s0);
-        for (int64_t f0 = s0; f0 < s1; f0 += 32) {
-            const int64_t e = f0 + lane;
-            // starts of rows r0 .. r0+31 (rows past nrows start after every position)
-            const int64_t r = (int64_t)r0 + lane;
-            const int64_t beg = r <= nrows ? start((int32_t)r) : INT64_MAX;
-            int i = 0;
-#pragma unroll
-            for (int s = 16; s >= 1; s >>= 1) {
-                const int64_t b = __shfl_sync(0xFFFFFFFFu, beg, (i + s) & 31);
-                if (i + s <= 31 && b <= e) i += s;
-            }
-            int32_t v = r0 + i;
-            // past the 32 rows (a run of empty rows): own search
-            if (e < s1 && i == 31 && r0 + 32 <= nrows && start(r0 + 32) <= e)
-                v = row_of_thread(start, r0 + 31, nrows, e);
-            // the next batch starts in the row of this batch's last position
-            r0 = __shfl_sync(0xFFFFFFFFu, v, 31);
-            if constexpr (ALL) {
-                fn(e, v, e < s1);
-            } else {
-                if (e >= s1) continue;
-                fn(e, v);
-            }
-        }
-    }
-}
-
-// Edge-balanced walk of a flat space [0, m) split into rows by the
-// non-decreasing starts rp[0..nrows] (rp[0] = 0, rp[nrows] = m): fn(f, row)
-// once per position, a warp taking kLcmEdgesPerWarp consecutive positions.
-template <class F>
-__device__ __forceinline__ void walk_rows(const int32_t* __restrict__ rp, int32_t nrows, int64_t m, F&& fn) {
-    walk_rows_by<false>([rp](int32_t r) -> int64_t { return (int64_t)__ldg(rp + r); }, nrows, m, fn);
-}
-
-// The same walk with the row starts given by start(r) (start(nrows) = m),
-// fn(f, row, valid) called by every lane of the warp together (valid false
-// past the end), so fn may use warp-wide operations.
-template <class S, class F>
-__device__ __forceinline__ void walk_rows_all(S&& start, int32_t nrows, int64_t m, F&& fn) {
-    walk_rows_by<true>(start, nrows, m, fn);
 }
 
 // Every edge of one CSR orientation with its row (the owner vertex), the

@@ -1005,8 +1005,8 @@ namespace im {
 // 32-bit payload.  Used once per graph to build the in-CSR sorted by
 // (target, class, edge hash).
 // ---------------------------------------------------------------------------
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kBlock * kSortItems;  // 4096 keys per block
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kBlock * kSortItems;  // 2048 keys per block (24 KB of them in shared memory)
 
 __global__ void __launch_bounds__(kBlock) k_sort_hist(const unsigned long long* __restrict__ keys,
                                                       int64_t n, int shift, int nblocks,
@@ -1023,14 +1023,37 @@ __global__ void __launch_bounds__(kBlock) k_sort_hist(const unsigned long long* 
     hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = (int32_t)h[threadIdx.x];
 }
 
+// Scatter of one pass: the tile's keys are first ranked stably by digit
+// (rounds of 256 keys in index order; inside a round, warps in order, lanes of
+// a digit by __match_any_sync) and placed in shared memory in digit order,
+// then written out from there: consecutive threads write a digit's keys to
+// consecutive global positions (runs of about kSortTile / 256 keys instead of
+// one key per store).
 __global__ void __launch_bounds__(kBlock) k_sort_scatter(
     const unsigned long long* __restrict__ keys, const int32_t* __restrict__ vals, int64_t n, int shift,
-    int nblocks, const int32_t* __restrict__ offs, unsigned long long* __restrict__ keys_out,
-    int32_t* __restrict__ vals_out) {
+    int nblocks, const int32_t* __restrict__ hist, const int32_t* __restrict__ offs,
+    unsigned long long* __restrict__ keys_out, int32_t* __restrict__ vals_out) {
+    __shared__ unsigned long long sk[kSortTile];
+    __shared__ int32_t sv[kSortTile];
     __shared__ unsigned int wcount[kWarpsPerBlock][256];
-    __shared__ unsigned int run[256];
+    __shared__ unsigned int run[256];    // keys of the digit placed so far (tile order)
+    __shared__ unsigned int start[256];  // first tile position of the digit
+    __shared__ unsigned int gbase[256];  // global position of the tile's first key of the digit
     const int lane = (int)lane_id(), w = threadIdx.x >> 5;
-    run[threadIdx.x] = (unsigned)offs[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+    const int d0 = threadIdx.x;
+    const unsigned cnt_d = (unsigned)hist[(int64_t)d0 * nblocks + blockIdx.x];
+    gbase[d0] = (unsigned)offs[(int64_t)d0 * nblocks + blockIdx.x];
+    run[d0] = 0u;
+    // exclusive scan of the tile's digit counts (one digit a thread)
+    start[d0] = cnt_d;
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {
+        const unsigned x = d0 >= o ? start[d0 - o] : 0u;
+        __syncthreads();
+        start[d0] += x;
+        __syncthreads();
+    }
+    start[d0] -= cnt_d;
     const int64_t base = (int64_t)blockIdx.x * kSortTile;
     for (int r = 0; r < kSortItems; ++r) {
         for (int d = lane; d < 256; d += 32) wcount[w][d] = 0u;
@@ -1052,9 +1075,9 @@ __global__ void __launch_bounds__(kBlock) k_sort_scatter(
         if (ok) {
             unsigned before = 0;
             for (int ww = 0; ww < w; ++ww) before += wcount[ww][d];
-            const unsigned pos = run[d] + before + rank_w;
-            keys_out[pos] = k;
-            vals_out[pos] = v;
+            const unsigned pos = start[d] + run[d] + before + rank_w;
+            sk[pos] = k;
+            sv[pos] = v;
         }
         __syncthreads();
         {
@@ -1063,6 +1086,14 @@ __global__ void __launch_bounds__(kBlock) k_sort_scatter(
             run[threadIdx.x] += tot;
         }
         __syncthreads();
+    }
+    const int tile_n = (int)min((int64_t)kSortTile, n - base);
+    for (int j = threadIdx.x; j < tile_n; j += kBlock) {
+        const unsigned long long k = sk[j];
+        const unsigned d = (unsigned)(k >> shift) & 0xFFu;
+        const unsigned pos = gbase[d] + (unsigned)j - start[d];
+        keys_out[pos] = k;
+        vals_out[pos] = sv[j];
     }
 }
 
@@ -1075,50 +1106,50 @@ size_t sort_tmp_bytes(int64_t n) {
 
 // Sort keys of the in-CSR: (target << 33) | (class << 31) | hE(source, target),
 // payload = out-edge index.  class = trivalency class (0 for other models).
+// Edge-balanced over the out-CSR (a hub's row spreads over many warps, a run
+// of small rows shares one warp).
 __global__ void k_in_keys(const int32_t* __restrict__ rp_out, const int32_t* __restrict__ col_out,
-                          int32_t n, int kind, uint32_t tri_seed, const int32_t* __restrict__ hkey,
+                          int32_t n, int64_t m, int kind, uint32_t tri_seed, const int32_t* __restrict__ hkey,
                           unsigned long long* __restrict__ keys, int32_t* __restrict__ perm,
                           int32_t* __restrict__ src_out) {
-    const int lane = (int)lane_id();
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = warp; u < n; u += nwarps) {
-        const int32_t b = rp_out[u], e = rp_out[u + 1];
-        for (int32_t i = b + lane; i < e; i += 32) {
-            const uint32_t v = (uint32_t)col_out[i];
-            // hash keys: the vertex ids of the graph the edge belongs to
-            const uint32_t ku = hkey ? (uint32_t)hkey[u] : (uint32_t)u;
-            const uint32_t kv = hkey ? (uint32_t)hkey[v] : v;
-            const uint32_t cls = kind == kTrivalency ? hash_pair(ku, kv, tri_seed) % 3u : 0u;
-            keys[i] = ((unsigned long long)v << 33) | ((unsigned long long)cls << 31) | edge_hash(ku, kv);
-            perm[i] = i;
-            src_out[i] = (int32_t)u;
-        }
-    }
+    walk_rows(rp_out, n, m, [&](int64_t i, int32_t u) {
+        const uint32_t v = (uint32_t)col_out[i];
+        // hash keys: the vertex ids of the graph the edge belongs to
+        const uint32_t ku = hkey ? (uint32_t)hkey[u] : (uint32_t)u;
+        const uint32_t kv = hkey ? (uint32_t)hkey[v] : v;
+        const uint32_t cls = kind == kTrivalency ? hash_pair(ku, kv, tri_seed) % 3u : 0u;
+        keys[i] = ((unsigned long long)v << 33) | ((unsigned long long)cls << 31) | edge_hash(ku, kv);
+        perm[i] = (int32_t)i;
+        src_out[i] = u;
+    });
 }
 
-// Out-edge hash and weighted-cascade threshold of every out-edge (out-CSR order).
+// Out-edge hash and weighted-cascade threshold of every out-edge (out-CSR
+// order), edge-balanced.
 __global__ void k_out_edge_words(const int32_t* __restrict__ rp_out, const int32_t* __restrict__ col_out,
-                                 int32_t n, const uint32_t* __restrict__ thr_v, const int32_t* __restrict__ hkey,
-                                 uint32_t* __restrict__ h_out, uint32_t* __restrict__ thrw_out) {
-    const int lane = (int)lane_id();
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = warp; u < n; u += nwarps) {
-        const int32_t b = rp_out[u], e = rp_out[u + 1];
-        for (int32_t i = b + lane; i < e; i += 32) {
-            const uint32_t v = (uint32_t)col_out[i];
-            h_out[i] = hkey ? edge_hash((uint32_t)hkey[u], (uint32_t)hkey[v]) : edge_hash((uint32_t)u, v);
-            thrw_out[i] = thr_v[v];
-        }
-    }
+                                 int32_t n, int64_t m, const uint32_t* __restrict__ thr_v,
+                                 const int32_t* __restrict__ hkey, uint32_t* __restrict__ h_out,
+                                 uint32_t* __restrict__ thrw_out) {
+    walk_rows(rp_out, n, m, [&](int64_t i, int32_t u) {
+        const uint32_t v = (uint32_t)col_out[i];
+        h_out[i] = hkey ? edge_hash((uint32_t)hkey[u], (uint32_t)hkey[v]) : edge_hash((uint32_t)u, v);
+        thrw_out[i] = thr_v[v];
+    });
+}
+
+// Blocks of an edge-balanced walk over m positions (kLcmEdgesPerWarp a warp).
+static int walk_grid(int64_t m) {
+    const int64_t warps = (m + kLcmEdgesPerWarp - 1) / kLcmEdgesPerWarp;
+    int64_t grid = (warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (grid > 152 * 16) grid = 152 * 16;
+    return (int)(grid < 1 ? 1 : grid);
 }
 
 cudaError_t launch_out_edge_words(const int32_t* rp_out, const int32_t* col_out, int32_t n, int64_t m,
                                   const uint32_t* thr_v, const int32_t* hkey, uint32_t* h_out,
                                   uint32_t* thrw_out, cudaStream_t st) {
     if (m == 0) return cudaSuccess;
-    k_out_edge_words<<<152 * 8, kBlock, 0, st>>>(rp_out, col_out, n, thr_v, hkey, h_out, thrw_out);
+    k_out_edge_words<<<walk_grid(m), kBlock, 0, st>>>(rp_out, col_out, n, m, thr_v, hkey, h_out, thrw_out);
     return cudaGetLastError();
 }
 
@@ -1127,8 +1158,25 @@ __global__ void k_in_gather(const unsigned long long* __restrict__ keys, const i
                             const uint32_t* __restrict__ thr_out, int32_t* __restrict__ src_in,
                             uint32_t* __restrict__ h_in, uint32_t* __restrict__ thr_in,
                             int32_t* __restrict__ out_to_in) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    // four positions a thread per step, their random reads in flight together
+    const int64_t st = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; i + 3 * st < m; i += 4 * st) {
+        int32_t e[4], s4[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) e[k] = perm[i + k * st];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s4[k] = src_out[e[k]];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t ik = i + k * st;
+            src_in[ik] = s4[k];
+            h_in[ik] = (uint32_t)keys[ik] & 0x7FFFFFFFu;
+            if (thr_in) thr_in[ik] = thr_out[e[k]];
+            if (out_to_in) out_to_in[e[k]] = (int32_t)ik;
+        }
+    }
+    for (; i < m; i += st) {
         const int32_t e = perm[i];
         src_in[i] = src_out[e];
         h_in[i] = (uint32_t)keys[i] & 0x7FFFFFFFu;
@@ -1140,9 +1188,20 @@ __global__ void k_in_gather(const unsigned long long* __restrict__ keys, const i
 // dst[i] = src[idx[i]] (per-edge words from one CSR orientation to the other)
 __global__ void k_gather_u32(const uint32_t* __restrict__ src, const int32_t* __restrict__ idx, int64_t m,
                              uint32_t* __restrict__ dst) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = __ldg(src + __ldg(idx + i));
+    // four positions a thread per step, their random reads in flight together
+    const int64_t st = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; i + 3 * st < m; i += 4 * st) {
+        int32_t k4[4];
+        uint32_t v4[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) k4[k] = __ldg(idx + i + k * st);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v4[k] = __ldg(src + k4[k]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dst[i + k * st] = v4[k];
+    }
+    for (; i < m; i += st) dst[i] = __ldg(src + __ldg(idx + i));
 }
 
 cudaError_t launch_gather_u32(const uint32_t* src, const int32_t* idx, int64_t m, uint32_t* dst, cudaStream_t st) {
@@ -1188,7 +1247,7 @@ cudaError_t launch_build_in_csr(const int32_t* rp_out, const int32_t* col_out, i
     p += ((size_t)m * 4 + 255) & ~(size_t)255;
     int32_t* src_out = reinterpret_cast<int32_t*>(p);
     p += ((size_t)m * 4 + 255) & ~(size_t)255;
-    k_in_keys<<<152 * 8, kBlock, 0, st>>>(rp_out, col_out, n, kind, tri_seed, hkey, keys, perm, src_out);
+    k_in_keys<<<walk_grid(m), kBlock, 0, st>>>(rp_out, col_out, n, m, kind, tri_seed, hkey, keys, perm, src_out);
     int bits = 33;
     while ((1ll << (bits - 33)) < n) ++bits;
     cudaError_t e = launch_radix_sort(keys, perm, m, bits, p, st);
@@ -1230,7 +1289,7 @@ cudaError_t launch_radix_sort(unsigned long long* keys, int32_t* vals, int64_t n
         k_sort_hist<<<nb, kBlock, 0, st>>>(ka, n, shift, nb, hist);
         cudaError_t e = launch_exclusive_scan(hist, cnt, offs, scan_tmp, st);
         if (e != cudaSuccess) return e;
-        k_sort_scatter<<<nb, kBlock, 0, st>>>(ka, va, n, shift, nb, offs, kb, vb);
+        k_sort_scatter<<<nb, kBlock, 0, st>>>(ka, va, n, shift, nb, hist, offs, kb, vb);
         unsigned long long* tk = ka; ka = kb; kb = tk;
         int32_t* tv = va; va = vb; vb = tv;
     }
