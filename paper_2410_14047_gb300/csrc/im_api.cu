@@ -460,7 +460,8 @@ static im_status set_model(im_graph* g, const im_model* mdl) {
 
 // Validation of a host CSR: rows [r0, r1) ascending, ids in range, no
 // self-loops, rows strictly ascending.  Returns the first bad row (r1 if
-// none) and writes its error.
+// none) and writes its error.  (The graph load validates on the device and
+// runs this on the one row it reports, for the message.)
 static int32_t check_rows(int32_t n, const int32_t* rowptr, const int32_t* col, int32_t r0, int32_t r1,
                           im_status* st, char* msg, size_t cap) {
     for (int32_t u = r0; u < r1; ++u) {
@@ -480,42 +481,6 @@ static int32_t check_rows(int32_t n, const int32_t* rowptr, const int32_t* col, 
     return r1;
 }
 
-// The same over all rows, split by row ranges over host threads on large
-// graphs (the lowest bad row is reported, as a single pass would).  rowptr
-// is first checked to be non-decreasing, so every range's edges are in
-// [0, m).
-static im_status check_csr(im_ctx* c, int32_t n, int64_t m, const int32_t* rowptr, const int32_t* col) {
-    for (int32_t u = 0; u < n; ++u)
-        if (rowptr[u + 1] < rowptr[u]) return fail(c, IM_E_INVAL, "rowptr decreases at %d", u);
-    const unsigned hw = std::thread::hardware_concurrency();
-    const int T = m < (1 << 22) ? 1 : (int)std::max(1u, std::min(hw, 32u));
-    std::vector<int32_t> bad(T, n);
-    std::vector<im_status> sts(T, IM_OK);
-    std::vector<std::string> msgs(T);
-    auto run = [&](int t) {
-        // rows whose first edge falls in the t-th share of the edges
-        auto first_row = [&](int64_t edge) {
-            return (int32_t)(std::upper_bound(rowptr, rowptr + n + 1, (int32_t)edge) - rowptr - 1);
-        };
-        const int32_t r0 = t == 0 ? 0 : std::max(first_row(m * t / T) + 1, 0);
-        const int32_t r1 = t == T - 1 ? n : std::max(first_row(m * (t + 1) / T) + 1, 0);
-        if (r1 <= r0) return;
-        char buf[256];
-        const int32_t b = check_rows(n, rowptr, col, r0, std::min(r1, n), &sts[t], buf, sizeof buf);
-        if (b < std::min(r1, n)) { bad[t] = b; msgs[t] = buf; }
-    };
-    if (T == 1) {
-        run(0);
-    } else {
-        std::vector<std::thread> th;
-        for (int t = 0; t < T; ++t) th.emplace_back(run, t);
-        for (auto& x : th) x.join();
-    }
-    for (int t = 0; t < T; ++t)
-        if (bad[t] < n) return fail(c, sts[t], "%s", msgs[t].c_str());
-    return IM_OK;
-}
-
 static im_status graph_load_impl(im_ctx* c, int32_t n, int64_t m, const int32_t* rowptr,
                                  const int32_t* col, const im_model* model, const int32_t* hkey_host,
                                  im_graph** out) {
@@ -524,7 +489,6 @@ static im_status graph_load_impl(im_ctx* c, int32_t n, int64_t m, const int32_t*
     if (m < 0 || m >= (1ll << 31)) return fail(c, IM_E_RANGE, "m must be in [0, 2^31)");
     CKS(check_model(c, model, m));
     if (rowptr[0] != 0 || rowptr[n] != m) return fail(c, IM_E_INVAL, "rowptr[0] != 0 or rowptr[n] != m");
-    CKS(check_csr(c, n, m, rowptr, col));
     CK(c, cudaSetDevice(c->device));
     im_graph* g = new im_graph();
     g->ctx = c;
@@ -557,6 +521,24 @@ static im_status graph_load_impl(im_ctx* c, int32_t n, int64_t m, const int32_t*
     cudaError_t e = cudaMemcpyAsync(g->rp_out.p, rowptr, rp_bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && m > 0)
         e = cudaMemcpyAsync(g->col_out.p, col, (size_t)m * 4, cudaMemcpyHostToDevice, st);
+    // the CSR is validated on the device before any kernel indexes by its ids;
+    // the message of a bad row comes from the host check of that row alone
+    {
+        int32_t bad[2] = {0, 0};
+        if (e == cudaSuccess) e = launch_check_csr(g->rp_out.as<int32_t>(), g->col_out.as<int32_t>(), n, m,
+                                                   cnt.as<int32_t>(), st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(bad, cnt.p, 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess && (bad[0] < n || bad[1] < n)) {
+            release_tmp();
+            if (bad[0] < n) return bail(fail(c, IM_E_INVAL, "rowptr decreases at %d", bad[0]));
+            im_status rs = IM_E_INVAL;
+            char buf[256];
+            snprintf(buf, sizeof buf, "invalid row %d", bad[1]);
+            check_rows(n, rowptr, col, bad[1], bad[1] + 1, &rs, buf, sizeof buf);
+            return bail(fail(c, rs, "%s", buf));
+        }
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt.p, 0, ((size_t)n + 1) * 4, st);
     if (e == cudaSuccess) e = launch_indegree(g->col_out.as<int32_t>(), m, cnt.as<int32_t>(), st);
     if (e == cudaSuccess) e = launch_exclusive_scan(cnt.as<int32_t>(), n, g->rp_in.as<int32_t>(), tmp.p, st);

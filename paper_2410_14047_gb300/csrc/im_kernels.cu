@@ -1137,12 +1137,45 @@ __global__ void k_out_edge_words(const int32_t* __restrict__ rp_out, const int32
     });
 }
 
+// CSR validation on the device (graph load), before any kernel indexes by
+// the ids: bad[0] = the lowest u with rowptr[u + 1] < rowptr[u]; bad[1] = the
+// lowest row holding an id out of [0, n), a self-loop, or an id not above the
+// previous one of its row.  Both start at kCsrOk (above any row: n < 2^26).
+// The row walk needs a non-decreasing rowptr, so the second kernel returns at
+// once after a bad one.
+constexpr int32_t kCsrOk = 0x7F7F7F7F;  // the byte 0x7F in every byte (set by a memset)
+
+__global__ void k_check_rowptr(const int32_t* __restrict__ rp, int32_t n, int32_t* __restrict__ bad) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+        if (rp[u + 1] < rp[u]) atomicMin(bad, (int32_t)u);
+}
+
+__global__ void k_check_rows(const int32_t* __restrict__ rp, const int32_t* __restrict__ col, int32_t n, int64_t m,
+                             int32_t* __restrict__ bad) {
+    if (*(volatile int32_t*)bad != kCsrOk) return;
+    walk_rows(rp, n, m, [&](int64_t i, int32_t u) {
+        const int32_t v = col[i];
+        bool b = v < 0 || v >= n || v == u;
+        if (!b && i > (int64_t)__ldg(rp + u)) b = col[i - 1] >= v;
+        if (b) atomicMin(bad + 1, u);
+    });
+}
+
 // Blocks of an edge-balanced walk over m positions (kLcmEdgesPerWarp a warp).
 static int walk_grid(int64_t m) {
     const int64_t warps = (m + kLcmEdgesPerWarp - 1) / kLcmEdgesPerWarp;
     int64_t grid = (warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (grid > 152 * 16) grid = 152 * 16;
     return (int)(grid < 1 ? 1 : grid);
+}
+
+cudaError_t launch_check_csr(const int32_t* rp, const int32_t* col, int32_t n, int64_t m, int32_t* bad,
+                             cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(bad, 0x7F, 8, st);  // both words kCsrOk
+    if (e != cudaSuccess) return e;
+    k_check_rowptr<<<152 * 8, kBlock, 0, st>>>(rp, n, bad);
+    if (m > 0) k_check_rows<<<walk_grid(m), kBlock, 0, st>>>(rp, col, n, m, bad);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_out_edge_words(const int32_t* rp_out, const int32_t* col_out, int32_t n, int64_t m,

@@ -306,6 +306,11 @@ cudaError_t launch_build_in_csr(const int32_t* rp_out, const int32_t* col_out, i
                                 void* tmp, cudaStream_t st);
 // dst[i] = src[idx[i]], i < m.
 cudaError_t launch_gather_u32(const uint32_t* src, const int32_t* idx, int64_t m, uint32_t* dst, cudaStream_t st);
+// CSR validation of an uploaded graph: bad[0] = the lowest u whose rowptr
+// decreases, bad[1] = the lowest row with an id out of range, a self-loop or
+// ids not strictly ascending; each >= n when there is none.
+cudaError_t launch_check_csr(const int32_t* rp, const int32_t* col, int32_t n, int64_t m, int32_t* bad,
+                             cudaStream_t st);
 cudaError_t launch_out_edge_words(const int32_t* rp_out, const int32_t* col_out, int32_t n, int64_t m,
                                   const uint32_t* thr_v, const int32_t* hkey, uint32_t* h_out,
                                   uint32_t* thrw_out, cudaStream_t st);

@@ -302,6 +302,31 @@ def test_errors(im, ctx):
         with pytest.raises(im.IMError) as e:
             im.im_graph_load(ctx, big.rowptr, bad, MODELS["p30"])
         assert e.value.status == status, (kind, str(e.value))
+    # a decreasing rowptr is reported at its lowest vertex
+    rp = big.rowptr.copy()
+    k = int(np.argmax(np.diff(big.rowptr) > 0)) + 1000
+    while big.rowptr[k + 1] == big.rowptr[k]:
+        k += 1
+    rp[k] = rp[k + 1] + 1
+    with pytest.raises(im.IMError) as e:
+        im.im_graph_load(ctx, rp, big.col, MODELS["p30"])
+    assert e.value.status == -1 and f"rowptr decreases at {k}" in str(e.value)
+    # two bad rows: the lower one is reported, with its first bad edge
+    bad = big.col.copy()
+    hi_row = int(np.searchsorted(big.rowptr, big.m - 10, side="right") - 1)
+    lo_row = int(np.searchsorted(big.rowptr, big.m // 3, side="right") - 1)
+    while big.rowptr[hi_row + 1] - big.rowptr[hi_row] < 2:
+        hi_row -= 1
+    while big.rowptr[lo_row + 1] == big.rowptr[lo_row]:
+        lo_row += 1
+    assert lo_row < hi_row
+    i_hi = int(big.rowptr[hi_row]) + 1
+    bad[i_hi] = bad[i_hi - 1]
+    i_lo = int(big.rowptr[lo_row])
+    bad[i_lo] = -5
+    with pytest.raises(im.IMError) as e:
+        im.im_graph_load(ctx, big.rowptr, bad, MODELS["p30"])
+    assert e.value.status == -2 and f"col[{i_lo}] = -5" in str(e.value)
     small = im.im_ctx_create(0, hbm_budget_bytes=1 << 16)
     with pytest.raises(im.IMError) as e:
         im.im_graph_load(small, g.rowptr, g.col, MODELS["p30"])
