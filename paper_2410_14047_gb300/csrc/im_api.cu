@@ -257,6 +257,7 @@ struct im_sketch {
     bool defer = false;
     bool pull_safe = false;  // the pull queue holds every out-bucket (it cannot overflow)
     DBuf out_seed, out_S, out_est;
+    DBuf gsum;  // lazy-pick group records
     int32_t out_cap = 0;
     int32_t gen_counter = 0;
     int32_t picks = 0;
@@ -671,6 +672,7 @@ static void sketch_plan(im_sketch* sk, int32_t n, int64_t m_edges, int32_t J, Bu
     A(sk->awl, (size_t)n * ((J + 31) / 32) * 4);
     A(sk->awlc, 4);
     A(sk->lb, (size_t)n * 8);
+    A(sk->gsum, (size_t)pick_groups(n) * 32);
     A(sk->cand, 4);
     A(sk->part_S2, (size_t)pg * 8);
     A(sk->part_u2, (size_t)pg * 4);
@@ -1494,9 +1496,20 @@ static im_status pick_and_cover(im_sketch* sk, int k) {
         a.cand = sk->cand.as<int32_t>();
         a.part_S2 = sk->part_S2.as<unsigned long long>();
         a.part_u2 = sk->part_u2.as<int32_t>();
+        a.gsum = sk->gsum.as<unsigned long long>();
+        a.ngroups = pick_groups(sk->g->n);
     }
     const bool lazy_now = sk->lazy && sk->lb_ready;
-    CK(c, timed(c, kTPick, [&] { return lazy_now ? launch_pick_lazy(a, c->stream) : launch_pick(a, c->stream); }));
+    CK(c, timed(c, kTPick, [&] {
+        if (lazy_now) return launch_pick_lazy(a, c->stream);
+        // a full pick stores every S_u; the group records follow (the seed's
+        // bit is set by then)
+        PickArgs f = a;
+        f.gsum = nullptr;
+        cudaError_t e = launch_pick(f, c->stream);
+        if (e == cudaSuccess && sk->lazy) e = launch_group_summaries(a, c->stream);
+        return e;
+    }));
     if (sk->lazy) sk->lb_ready = true;
     return run_levels(sk, kCover, false);
 }

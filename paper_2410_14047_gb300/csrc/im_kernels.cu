@@ -322,6 +322,32 @@ struct Top2 {
     }
 };
 
+constexpr int kGroupRows = 1024;  // rows of a lazy-pick group record
+
+__device__ __forceinline__ bool is_picked(const uint32_t* seed_bits, int64_t v) {
+    return (__ldcg(seed_bits + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+// The two least stored (S, u) of the unpicked rows of group g (warp-wide;
+// every lane gets them), and their record in gsum (S1, S2, u1 | u2 << 32).
+__device__ __forceinline__ Top2 group_top2(const PickArgs& a, int64_t g) {
+    const int lane = (int)lane_id();
+    const int64_t r0 = g * kGroupRows;
+    Top2 t;
+    for (int k = 0; k < kGroupRows / 32; ++k) {
+        const int64_t v = r0 + k * 32 + lane;
+        if (v < a.n && !is_picked(a.seed_bits, v)) t.insert(__ldcg(a.lb + v), (int32_t)v);
+    }
+    t.warp_reduce();
+    if (lane == 0) {
+        a.gsum[4 * g] = t.s1;
+        a.gsum[4 * g + 1] = t.s2;
+        a.gsum[4 * g + 2] = (unsigned long long)(uint32_t)t.u1 | ((unsigned long long)(uint32_t)t.u2 << 32);
+    }
+    return t;
+}
+
+
 // Block + grid reduction of the per-thread Top2 (last block by ticket), then
 // the seed record: out_seed / out_S / out_est[k], the seed bit, the next
 // lazy candidate, and (mark) the seed row visited + queued for the cover.
@@ -375,13 +401,12 @@ __device__ void pick_finish(const PickArgs& a, Top2 t) {
         }
     }
     __syncthreads();
+    // lazy picks: the picked vertex's group is recorded again without it
+    if (a.gsum && fS != ~0ull && threadIdx.x < 32) group_top2(a, (int64_t)fU / kGroupRows);
     if (fS == ~0ull || !a.mark) return;
     cover_seed_block(a.M, a.J, fU, a.rp_out, a.q_cover, a.ctr_cover, a.chg0, a.count, a.bk_end_out, a.chunks, a.nv);
 }
 
-__device__ __forceinline__ bool is_picked(const uint32_t* seed_bits, int64_t v) {
-    return (__ldcg(seed_bits + (v >> 5)) >> (v & 31)) & 1u;
-}
 
 // Full pick: S_u of every row (stored in lb when lazy picks follow).  Each
 // lane sums up to `tile` (1, 2 or 4: the J-tile width, a schedule knob)
@@ -455,76 +480,112 @@ __device__ __forceinline__ unsigned long long warp_row_sum(const uint8_t* __rest
 // unvisited), so lb[v] <= S_v.  With S_c fresh for the candidate c, every
 // unpicked v with (lb[v], v) < (S_c, c) is refreshed; then the least stored
 // pair is the least current pair, the same vertex a full pick chooses.
+// Refreshes the stale rows of rows r0 .. r0 + 31 (lv: this lane's stored sum,
+// m: the stale lanes), kLazyRows of them at once with their loads in flight
+// together (stale rows cluster: influential vertices sit together).
+__device__ __forceinline__ void refresh_rows(const PickArgs& a, int64_t r0, unsigned int m) {
+    const int lane = (int)lane_id();
+    const int J = a.J, cpr = J >> 4;
+    while (m) {
+        int b[kLazyRows];
+#pragma unroll
+        for (int r = 0; r < kLazyRows; ++r) {
+            b[r] = m ? __ffs(m) - 1 : -1;
+            m &= m - 1;
+        }
+        unsigned long long s[kLazyRows];
+#pragma unroll
+        for (int r = 0; r < kLazyRows; ++r) s[r] = 0ull;
+        // a row has at most 64 pieces: piece lane, then lane + 32
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            if (c >= cpr) break;  // lanes past the row's pieces (J < 512) sum nothing
+            uint4 q[kLazyRows];
+#pragma unroll
+            for (int r = 0; r < kLazyRows; ++r)
+                q[r] = b[r] >= 0 ? __ldcg(reinterpret_cast<const uint4*>(a.M + (size_t)(r0 + b[r]) * J) + c)
+                                 : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int r = 0; r < kLazyRows; ++r) s[r] += row_terms16(q[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < kLazyRows; ++r) {
+            if (b[r] < 0) continue;  // warp-uniform
+            const unsigned long long sr = warp_sum(s[r]);
+            if (lane == b[r]) a.lb[r0 + b[r]] = sr;
+        }
+    }
+}
+
+// Group records after a full pick (its stored sums and seed bit in place).
+__global__ void __launch_bounds__(kBlock) k_group_summaries(PickArgs a) {
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t g = warp; g < a.ngroups; g += nwarps) group_top2(a, g);
+}
+
+// Lazy pick (CELF-style, exact): S_u only grows during a selection (covers
+// turn registers into visited = 2^32, rebuilds lower the ranks of what stays
+// unvisited), so lb[v] <= S_v.  With S_c fresh for the candidate c, every
+// unpicked v with (lb[v], v) < (S_c, c) is refreshed; then the least stored
+// pair is the least current pair, the same vertex a full pick chooses.  The
+// rows are read through their groups' records: a group whose least stored
+// pair is not below (S_c, c) holds no stale row and gives its two least pairs
+// as they are; the few others are refreshed and re-recorded.  The picked
+// vertex's group is re-recorded by the last block (pick_finish).
 __global__ void __launch_bounds__(kBlock) k_pick_lazy(PickArgs a) {
-    const int J = a.J;
     const int lane = (int)lane_id();
     const int32_t c = __ldcg(a.cand);
     unsigned long long Sc = 0;
     int32_t uc = -1;  // no candidate: nothing is refreshed
     if (c >= 0) {
-        Sc = warp_row_sum(a.M, J, c);
+        Sc = warp_row_sum(a.M, a.J, c);
         uc = c;
     }
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    constexpr int U = kLazySteps;
-    const int cpr = J >> 4;
     unsigned refreshed = 0;  // rows refreshed by this warp
     Top2 t;
-    // U * 32 vertices a warp step: the stored sums and picked words load first
-    for (int64_t base = warp * 32 * U; base < a.n; base += nwarps * 32 * U) {
-        unsigned long long lv[U];
-        uint32_t pw[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t v = base + u * 32 + lane;
-            lv[u] = v < a.n ? __ldcg(a.lb + v) : ~0ull;
-            pw[u] = base + u * 32 < a.n ? __ldcg(a.seed_bits + ((base + u * 32) >> 5)) : 0xFFFFFFFFu;
+    // one group a lane, 32 a warp step
+    for (int64_t g0 = warp * 32; g0 < a.ngroups; g0 += nwarps * 32) {
+        const int64_t g = g0 + lane;
+        unsigned long long s1 = ~0ull, s2 = ~0ull;
+        int32_t u1 = 0x7FFFFFFF, u2 = 0x7FFFFFFF;
+        if (g < a.ngroups) {
+            s1 = __ldcg(a.gsum + 4 * g);
+            s2 = __ldcg(a.gsum + 4 * g + 1);
+            const unsigned long long pk = __ldcg(a.gsum + 4 * g + 2);
+            u1 = (int32_t)(uint32_t)pk;
+            u2 = (int32_t)(uint32_t)(pk >> 32);
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t v = base + u * 32 + lane;
-            const bool ok = v < a.n && !((pw[u] >> lane) & 1u);
-            const bool stale = ok && (lv[u] < Sc || (lv[u] == Sc && (int32_t)v < uc));
-            unsigned int m = __ballot_sync(0xFFFFFFFFu, stale);
-            refreshed += (unsigned)__popc(m);
-            // stale rows cluster (influential vertices sit together): the
-            // warp refreshes kLazyRows of them at once, their loads in flight
-            // together
-            while (m) {
-                int b[kLazyRows];
-#pragma unroll
-                for (int r = 0; r < kLazyRows; ++r) {
-                    b[r] = m ? __ffs(m) - 1 : -1;
-                    m &= m - 1;
+        const bool stale = g < a.ngroups && (s1 < Sc || (s1 == Sc && u1 < uc));
+        if (!stale) {
+            t.insert(s1, u1);
+            t.insert(s2, u2);
+        }
+        unsigned int m = __ballot_sync(0xFFFFFFFFu, stale);
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            const int64_t gg = g0 + b;
+            for (int k = 0; k < kGroupRows / 32; ++k) {
+                const int64_t r0 = gg * kGroupRows + k * 32;
+                const int64_t v = r0 + lane;
+                bool st = false;
+                if (v < a.n && !is_picked(a.seed_bits, v)) {
+                    const unsigned long long lv = __ldcg(a.lb + v);
+                    st = lv < Sc || (lv == Sc && (int32_t)v < uc);
                 }
-                unsigned long long s[kLazyRows];
-#pragma unroll
-                for (int r = 0; r < kLazyRows; ++r) s[r] = 0ull;
-                // a row has at most 64 pieces: piece lane, then lane + 32
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int c = lane + 32 * h;
-                    if (c >= cpr) break;  // lanes past the row's pieces (J < 512) sum nothing
-                    uint4 q[kLazyRows];
-#pragma unroll
-                    for (int r = 0; r < kLazyRows; ++r)
-                        q[r] = b[r] >= 0 ? __ldcg(reinterpret_cast<const uint4*>(a.M + (size_t)(base + u * 32 + b[r]) * J) + c)
-                                         : make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-                    for (int r = 0; r < kLazyRows; ++r) s[r] += row_terms16(q[r]);
-                }
-#pragma unroll
-                for (int r = 0; r < kLazyRows; ++r) {
-                    if (b[r] < 0) continue;  // warp-uniform
-                    const unsigned long long sr = warp_sum(s[r]);
-                    if (lane == b[r]) {
-                        lv[u] = sr;
-                        a.lb[v] = sr;
-                    }
-                }
+                const unsigned int sm = __ballot_sync(0xFFFFFFFFu, st);
+                refreshed += (unsigned)__popc(sm);
+                refresh_rows(a, r0, sm);
             }
-            if (ok) t.insert(lv[u], (int32_t)v);
+            const Top2 gt = group_top2(a, gg);
+            if (lane == b) {
+                t.insert(gt.s1, gt.u1);
+                t.insert(gt.s2, gt.u2);
+            }
         }
     }
     if (a.stats && lane == 0 && refreshed) atomicAdd(a.stats + kStPickRefreshed, (unsigned long long)refreshed);
@@ -547,11 +608,21 @@ cudaError_t launch_pick(const PickArgs& a, cudaStream_t st) {
 }
 
 int pick_lazy_grid(int32_t n) {
-    const int64_t per_block = (int64_t)kWarpsPerBlock * 32 * kLazySteps;
-    int64_t grid = (n + per_block - 1) / per_block;
+    // one group a lane
+    const int64_t groups = ((int64_t)n + kGroupRows - 1) / kGroupRows;
+    int64_t grid = (groups + 32 * kWarpsPerBlock - 1) / (32 * kWarpsPerBlock);
     if (grid > 152 * 8) grid = 152 * 8;
     if (grid < 1) grid = 1;
     return (int)grid;
+}
+
+int pick_groups(int32_t n) { return (int)(((int64_t)n + kGroupRows - 1) / kGroupRows); }
+
+cudaError_t launch_group_summaries(const PickArgs& a, cudaStream_t st) {
+    int64_t grid = ((int64_t)a.ngroups + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (grid > 152 * 8) grid = 152 * 8;
+    k_group_summaries<<<(int)(grid < 1 ? 1 : grid), kBlock, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pick_lazy(const PickArgs& a, cudaStream_t st) {

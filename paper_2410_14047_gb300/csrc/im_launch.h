@@ -215,12 +215,20 @@ struct PickArgs {
     uint32_t* nv;                 // registers newly visited since the last build (may be NULL)
     int tile;                     // J-tile width of a full pick: 16-byte pieces a lane sums (1, 2, 4)
     unsigned long long* stats;    // statistics block (rows refreshed by lazy picks; may be NULL)
+    // lazy picks: per group of 1024 rows the two least stored (S, u) of its
+    // unpicked rows (4 words a group: S1, S2, u1 | u2 << 32, unused); NULL
+    // for full picks that keep no records
+    unsigned long long* gsum;
+    int32_t ngroups;
 };
 
 // Blocks of a full pick: one row group per warp step, at most 152 * 8; tile
 // = 16-byte pieces of a row a lane sums (1, 2 or 4; other values: 4).
 int pick_grid(int32_t n, int J, int tile = 4);
 int pick_lazy_grid(int32_t n);
+int pick_groups(int32_t n);  // lazy-pick group records of n rows
+// Group records of every group (after a full pick that stored every S_u).
+cudaError_t launch_group_summaries(const PickArgs& a, cudaStream_t st);
 
 cudaError_t launch_sims(uint64_t seed, int J, uint32_t* X, uint32_t* salt, uint16_t* tab,
                         cudaStream_t st);

@@ -401,6 +401,23 @@ def test_lazy_pick_equals_full_pick(im, gname, mname, J, K, eps):
     assert out[0]["seeds"].tolist() == ref["seeds"].tolist()
 
 
+@pytest.mark.parametrize("eps", [0.01, -1.0])
+def test_lazy_pick_over_many_groups(im, eps):
+    # 65,536 rows = 64 lazy-pick groups of 1024 (the picks read group records;
+    # eps -1: a full rebuild after every pick, then a full pick; eps 0.01:
+    # lazy picks whose stale groups are refreshed and recorded again)
+    g = W.rmat(16, 8, seed=21)
+    model = {"kind": "wc"}
+    out = []
+    for lazy in (1, 0):
+        c2 = im.im_ctx_create(0)
+        im.im_ctx_set_tuning(c2, {"lazy_pick": lazy})
+        G = im.im_graph_load(c2, g.rowptr, g.col, model)
+        out.append(im.im_select_seeds(G, 60, 64, seed=9, rebuild_eps=eps))
+    assert out[0]["seeds"].tolist() == out[1]["seeds"].tolist()
+    assert np.array_equal(out[0]["score"], out[1]["score"])
+
+
 # --- incremental rebuilds: the registers a full rebuild produces, bit for bit ---------------
 
 @pytest.mark.parametrize("gname,mname,J,K,eps", [("rmat12", "wc", 256, 40, 0.01), ("er2k", "wc", 64, 60, 0.0),
