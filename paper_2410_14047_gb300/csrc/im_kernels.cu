@@ -322,7 +322,7 @@ struct Top2 {
     }
 };
 
-constexpr int kGroupRows = 1024;  // rows of a lazy-pick group record
+constexpr int kGroupRows = 128;  // rows of a lazy-pick group record
 
 __device__ __forceinline__ bool is_picked(const uint32_t* seed_bits, int64_t v) {
     return (__ldcg(seed_bits + (v >> 5)) >> (v & 31)) & 1u;
@@ -547,9 +547,11 @@ __global__ void __launch_bounds__(kBlock) k_pick_lazy(PickArgs a) {
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned refreshed = 0;  // rows refreshed by this warp
     Top2 t;
-    // one group a lane, 32 a warp step
-    for (int64_t g0 = warp * 32; g0 < a.ngroups; g0 += nwarps * 32) {
-        const int64_t g = g0 + lane;
+    // one group a lane; lane l of warp w takes group w + l * nwarps, so the
+    // stale groups, which cluster after a rebuild (influential vertices sit
+    // together), go to different warps
+    for (int64_t base = warp; base < a.ngroups; base += nwarps * 32) {
+        const int64_t g = base + (int64_t)lane * nwarps;
         unsigned long long s1 = ~0ull, s2 = ~0ull;
         int32_t u1 = 0x7FFFFFFF, u2 = 0x7FFFFFFF;
         if (g < a.ngroups) {
@@ -561,6 +563,7 @@ __global__ void __launch_bounds__(kBlock) k_pick_lazy(PickArgs a) {
         }
         const bool stale = g < a.ngroups && (s1 < Sc || (s1 == Sc && u1 < uc));
         if (!stale) {
+            // no stale row: its two least pairs as recorded
             t.insert(s1, u1);
             t.insert(s2, u2);
         }
@@ -568,9 +571,9 @@ __global__ void __launch_bounds__(kBlock) k_pick_lazy(PickArgs a) {
         while (m) {
             const int b = __ffs(m) - 1;
             m &= m - 1;
-            const int64_t gg = g0 + b;
-            for (int k = 0; k < kGroupRows / 32; ++k) {
-                const int64_t r0 = gg * kGroupRows + k * 32;
+            const int64_t gg = base + (int64_t)b * nwarps;
+            for (int q = 0; q < kGroupRows / 32; ++q) {
+                const int64_t r0 = gg * kGroupRows + q * 32;
                 const int64_t v = r0 + lane;
                 bool st = false;
                 if (v < a.n && !is_picked(a.seed_bits, v)) {
@@ -608,11 +611,14 @@ cudaError_t launch_pick(const PickArgs& a, cudaStream_t st) {
 }
 
 int pick_lazy_grid(int32_t n) {
-    // one group a lane
+    // one group a lane, and at least 2048 warps: the stale groups of a pick
+    // (spread over the warps by the group-to-lane mapping) are refreshed by as
+    // many warps as there are
     const int64_t groups = ((int64_t)n + kGroupRows - 1) / kGroupRows;
-    int64_t grid = (groups + 32 * kWarpsPerBlock - 1) / (32 * kWarpsPerBlock);
+    int64_t warps = (groups + 31) / 32;
+    if (warps < 2048) warps = 2048;
+    int64_t grid = (warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (grid > 152 * 8) grid = 152 * 8;
-    if (grid < 1) grid = 1;
     return (int)grid;
 }
 

@@ -215,7 +215,7 @@ struct PickArgs {
     uint32_t* nv;                 // registers newly visited since the last build (may be NULL)
     int tile;                     // J-tile width of a full pick: 16-byte pieces a lane sums (1, 2, 4)
     unsigned long long* stats;    // statistics block (rows refreshed by lazy picks; may be NULL)
-    // lazy picks: per group of 1024 rows the two least stored (S, u) of its
+    // lazy picks: per group of 128 rows the two least stored (S, u) of its
     // unpicked rows (4 words a group: S1, S2, u1 | u2 << 32, unused); NULL
     // for full picks that keep no records
     unsigned long long* gsum;

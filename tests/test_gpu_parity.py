@@ -403,7 +403,7 @@ def test_lazy_pick_equals_full_pick(im, gname, mname, J, K, eps):
 
 @pytest.mark.parametrize("eps", [0.01, -1.0])
 def test_lazy_pick_over_many_groups(im, eps):
-    # 65,536 rows = 64 lazy-pick groups of 1024 (the picks read group records;
+    # 65,536 rows = 512 lazy-pick groups of 128 (the picks read group records;
     # eps -1: a full rebuild after every pick, then a full pick; eps 0.01:
     # lazy picks whose stale groups are refreshed and recorded again)
     g = W.rmat(16, 8, seed=21)
