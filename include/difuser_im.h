@@ -250,8 +250,11 @@ IM_API int64_t im_last_trace(const im_ctx* ctx, im_trace_rec* out, int64_t cap);
  * edges must be merged beforehand, Sec. 2.1) and a diffusion model to the
  * device, builds the reverse CSR (in-edges) and the edge thresholds
  * (Sec. 2.1 models, Eq. hash_prob fixed point).  The caller keeps ownership of
- * every input.  Errors: IM_E_INVAL (malformed CSR or model), IM_E_RANGE
- * (n or m out of range), IM_E_NOMEM, IM_E_CUDA. */
+ * every input.  The CSR is checked on the device right after the upload,
+ * before any kernel uses its ids; an error names the lowest bad row (its first
+ * bad edge).  Errors: IM_E_INVAL (malformed CSR or model: rowptr decreasing
+ * or not from 0 to m, a self-loop, a row not strictly ascending), IM_E_RANGE
+ * (n or m out of range, an id out of [0, n)), IM_E_NOMEM, IM_E_CUDA. */
 IM_API im_status im_graph_load(im_ctx* ctx, int32_t n, int64_t m, const int32_t* rowptr,
                         const int32_t* col, const im_model* model, im_graph** out);
 IM_API void im_graph_free(im_graph* g);
