@@ -105,7 +105,7 @@ typedef struct {
     uint64_t sweep_chunks;    /* (in-edge, 16-simulation chunk) pairs of vertex-format propagation
                                  levels with a simulation where the edge is live, the source
                                  changed and its register is not visited */
-    uint64_t sweep_cas;       /* 4-register words written by atomic CAS (improvements) */
+    uint64_t sweep_cas;       /* 16-register pieces written by 16-byte CAS (improvements) */
     uint64_t sweep_changed;   /* vertices whose registers a propagation level changed (vertex-format
                                  levels: the queued vertices of every level after the first) */
     uint64_t cover_edges;     /* out-edges examined by cover levels */

@@ -123,50 +123,50 @@ __device__ __forceinline__ bool is_heavy(int32_t deg, uint32_t thr, int32_t heav
         return false;
 }
 
-// Byte-wise max of cand into the 16 register bytes at trow through CAS on
-// 4-byte words: the four first attempts are issued together, retries (a word
-// changed by another thread meanwhile) one word at a time.  Returns the
-// changed registers as 16 bits.
-// The same with the merged words nw (byte_max of tg and cand) already known.
+// 16-byte compare-and-swap (PTX atom.cas.b128, sm_90 and later): returns the
+// piece found at p; it was replaced by nw when it equalled cmp.
+__device__ __forceinline__ uint4 cas16(uint8_t* p, uint4 cmp, uint4 nw) {
+    const unsigned long long c_lo = (unsigned long long)cmp.x | ((unsigned long long)cmp.y << 32);
+    const unsigned long long c_hi = (unsigned long long)cmp.z | ((unsigned long long)cmp.w << 32);
+    const unsigned long long n_lo = (unsigned long long)nw.x | ((unsigned long long)nw.y << 32);
+    const unsigned long long n_hi = (unsigned long long)nw.z | ((unsigned long long)nw.w << 32);
+    unsigned long long o_lo, o_hi;
+    asm volatile(
+        "{\n\t.reg .b128 d, b, c;\n\t"
+        "mov.b128 b, {%2, %3};\n\t"
+        "mov.b128 c, {%4, %5};\n\t"
+        "atom.global.cas.b128 d, [%6], b, c;\n\t"
+        "mov.b128 {%0, %1}, d;\n\t}"
+        : "=l"(o_lo), "=l"(o_hi)
+        : "l"(c_lo), "l"(c_hi), "l"(n_lo), "l"(n_hi), "l"(p)
+        : "memory");
+    return make_uint4((uint32_t)o_lo, (uint32_t)(o_lo >> 32), (uint32_t)o_hi, (uint32_t)(o_hi >> 32));
+}
+
+// Byte-wise max of cand into the 16 register bytes at trow (16-byte aligned)
+// through 16-byte CAS, the merged words nw (byte_max of tg and cand) already
+// known; a retry (the piece changed meanwhile) merges into what it found.
+// Returns the changed registers as 16 bits.
 __device__ __forceinline__ uint32_t merge_chunk_nw(uint8_t* trow, const uint32_t cand[4], uint4 tg,
                                                   const uint32_t nw[4], StatT& n_cas, uint32_t* err) {
-    uint32_t cur[4] = {tg.x, tg.y, tg.z, tg.w};
-    uint32_t prev[4];
-    bool pend[4];
-    uint32_t bits = 0u;
-    unsigned int* addr = reinterpret_cast<unsigned int*>(trow);
-#pragma unroll
-    for (int w = 0; w < 4; ++w) pend[w] = nw[w] != cur[w];
-#pragma unroll
-    for (int w = 0; w < 4; ++w)
-        if (pend[w]) prev[w] = atomicCAS(addr + w, cur[w], nw[w]);
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-        if (!pend[w]) continue;
-        if (prev[w] == cur[w]) {
-            bits |= bytes_to_bits(nw[w] ^ cur[w]) << (4 * w);
+    uint4 cur = tg;
+    uint4 nv = make_uint4(nw[0], nw[1], nw[2], nw[3]);
+    for (int tries = 0;; ++tries) {
+        if (nv.x == cur.x && nv.y == cur.y && nv.z == cur.z && nv.w == cur.w) return 0u;
+        const uint4 prev = cas16(trow, cur, nv);
+        if (prev.x == cur.x && prev.y == cur.y && prev.z == cur.z && prev.w == cur.w) {
             ++n_cas;
-            continue;
+            return bytes_to_bits(nv.x ^ cur.x) | (bytes_to_bits(nv.y ^ cur.y) << 4) |
+                   (bytes_to_bits(nv.z ^ cur.z) << 8) | (bytes_to_bits(nv.w ^ cur.w) << 12);
         }
-        uint32_t c = prev[w];
-        uint32_t n = byte_max(c, cand[w]);
-        int tries = 0;
-        while (n != c) {
-            const uint32_t pv = atomicCAS(addr + w, c, n);
-            if (pv == c) {
-                bits |= bytes_to_bits(n ^ c) << (4 * w);
-                ++n_cas;
-                break;
-            }
-            c = pv;
-            n = byte_max(c, cand[w]);
-            if (++tries > kCasRetryLimit) {
-                atomicOr(err, kErrCasLimit);
-                break;
-            }
+        if (tries >= kCasRetryLimit) {
+            atomicOr(err, kErrCasLimit);
+            return 0u;
         }
+        cur = prev;
+        nv = make_uint4(byte_max(cur.x, cand[0]), byte_max(cur.y, cand[1]), byte_max(cur.z, cand[2]),
+                        byte_max(cur.w, cand[3]));
     }
-    return bits;
 }
 
 __device__ __forceinline__ uint32_t merge_chunk(uint8_t* trow, const uint32_t cand[4], uint4 tg,
