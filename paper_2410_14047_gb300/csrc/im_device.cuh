@@ -224,6 +224,17 @@ __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 __device__ __forceinline__ void red_or(uint32_t* p, uint32_t v) {
     asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(p), "r"(v));
 }
+__device__ __forceinline__ void red_or64(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.or.b64 [%0], %1;" ::"l"(p), "l"(v));
+}
+// The visited marks of a 16-byte register piece (8-byte aligned halves): two
+// reductions at most, none for a half without marks.
+__device__ __forceinline__ void red_or_piece(uint8_t* p, const uint32_t m[4]) {
+    const unsigned long long lo = (unsigned long long)m[0] | ((unsigned long long)m[1] << 32);
+    const unsigned long long hi = (unsigned long long)m[2] | ((unsigned long long)m[3] << 32);
+    if (lo) red_or64(reinterpret_cast<unsigned long long*>(p), lo);
+    if (hi) red_or64(reinterpret_cast<unsigned long long*>(p + 8), hi);
+}
 __device__ __forceinline__ void red_add(unsigned long long* p, unsigned long long v) {
     asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v));
 }

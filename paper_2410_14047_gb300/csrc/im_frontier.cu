@@ -578,9 +578,7 @@ __device__ __forceinline__ void light_slice(const GraphDev& g, const LevelArgs& 
                         } else {
                             // the visited marks go out without a reply; the
                             // change word's previous bits count the new ones
-#pragma unroll
-                            for (int w = 0; w < 4; ++w)
-                                if (cand[w]) red_or(reinterpret_cast<uint32_t*>(trow + 4 * w), cand[w]);
+                            red_or_piece(trow, cand);
                             newly_visited(a, o_i, (uint32_t)chunk, imp, eq.old, st_new);
                             note_newly_visited(a, o_i, (uint32_t)chunk, imp);
                         }
@@ -873,9 +871,7 @@ __device__ __forceinline__ void bucket_pos(const GraphDev& g, const LevelArgs& a
             if constexpr (MODE == kPush) {
                 nbits = merge_chunk(trow, cand, tg, st_cas, a.err);
             } else {
-#pragma unroll
-                for (int w = 0; w < 4; ++w)
-                    if (cand[w]) red_or(reinterpret_cast<uint32_t*>(trow + 4 * w), cand[w]);
+                red_or_piece(trow, cand);
                 newly_visited(a, o, c, imp, eq.old, st_new);
                 note_newly_visited(a, o, c, imp);
             }
