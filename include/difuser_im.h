@@ -94,7 +94,9 @@ typedef struct {
                                  searches of incremental rebuilds (timing on) */
     double ms_pick_kernels;   /* CUDA-event time of all estimate + argmax kernels (timing on) */
     double ms_fill_kernels;   /* CUDA-event time of all fill kernels, with the reset and pull of
-                                 incremental rebuilds (timing on) */
+                                 incremental rebuilds (timing on); a new sketch's first fill
+                                 runs on a second stream next to the live chunk masks, so its
+                                 time includes that overlap */
     int64_t launches;         /* kernels launched by the call */
     int64_t sweep_launches;   /* propagation sweep kernels launched (with or without work) */
     int64_t builds;           /* 1 + number of rebuilds */

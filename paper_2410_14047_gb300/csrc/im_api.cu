@@ -51,6 +51,11 @@ struct im_ctx {
     // bounds of the device-side waits (im_ctx_set_limits)
     uint64_t barrier_limit_ns = kDefaultBarrierLimitNs;
     int32_t max_levels = kMaxLevels - 2;
+    // a second stream for work independent of the main stream's (the first
+    // fill of a sketch next to its live chunk masks), forked and joined with
+    // events; created on first use
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -189,7 +194,9 @@ cudaError_t timed(im_ctx* c, int kind, F&& launch) {
     int slot = -1;
     if (c->timing) {
         if (c->ev_used * 2 + 2 > (int)c->ev.size()) {
+            // (a pair recorded on the side stream must be complete as well)
             cudaError_t e = cudaStreamSynchronize(c->stream);
+            if (e == cudaSuccess && c->side) e = cudaStreamSynchronize(c->side);
             if (e != cudaSuccess) return e;
             timing_collect(c);
         }
@@ -206,9 +213,42 @@ cudaError_t timed(im_ctx* c, int kind, F&& launch) {
     return e;
 }
 
+// The same bracket on another stream of the context.
+template <class F>
+cudaError_t timed_on(im_ctx* c, cudaStream_t st, int kind, F&& launch) {
+    int slot = -1;
+    if (c->timing) {
+        if (c->ev_used * 2 + 2 > (int)c->ev.size()) {
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) return e;
+            timing_collect(c);
+        }
+        slot = c->ev_used++;
+        c->ev_kind[slot] = kind;
+        c->ev_seq[slot] = c->seq;
+        cudaEventRecord(c->ev[2 * slot], st);
+    }
+    cudaError_t e = launch();
+    if (slot >= 0) cudaEventRecord(c->ev[2 * slot + 1], st);
+    c->stats.launches++;
+    c->seq++;
+    return e;
+}
+
+// The context's second stream and its fork / join events (created once).
+cudaError_t ensure_side(im_ctx* c) {
+    if (c->side) return cudaSuccess;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    return e;
+}
+
 // Stream synchronize followed by the collection of finished timings.
 cudaError_t sync_collect(im_ctx* c) {
     cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess && c->side) e = cudaStreamSynchronize(c->side);
     if (e == cudaSuccess && c->timing) timing_collect(c);
     return e;
 }
@@ -251,6 +291,9 @@ struct im_sketch {
     // the registers were never written (a new sketch): the first fill writes
     // every register without reading it, so no zeroing pass precedes it
     bool fresh = true;
+    // that first fill runs on the context's side stream next to the live
+    // chunk masks; the main stream waits for it (ev_join) before its first use
+    bool fill_pending = false;
     bool lb_ready = false;  // lb holds the sums of the last full pick or later refreshes
     // a selection in flight: phases and rebuilds queue without host reads;
     // their error word is read once at the end
@@ -304,6 +347,12 @@ extern "C" im_status im_ctx_create(int device, void* cuda_stream, uint64_t hbm_b
 extern "C" void im_ctx_destroy(im_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+        cudaEventDestroy(c->ev_fork);
+        cudaEventDestroy(c->ev_join);
+    }
     if (c->pinned) cudaFreeHost(c->pinned);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     delete c;
@@ -721,6 +770,10 @@ static uint64_t bucket_reserve_bytes(int32_t n, int64_t m, int32_t J) {
 // (null ones are skipped).
 static void sketch_release(im_sketch* sk) {
     im_ctx* c = sk->ctx;
+    if (sk->fill_pending) {
+        cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+        sk->fill_pending = false;
+    }
     BufPlan plan;
     sketch_plan(sk, sk->g->n, sk->g->m, sk->J, plan);
     scan_plan(sk, sk->g->n, sk->g->m, sk->J, plan);
@@ -1177,9 +1230,15 @@ static im_status incremental_rebuild(im_sketch* sk) {
 // Fill (Alg. 1) of the non-visited registers, then Simulate to the fixpoint.
 static im_status build_registers(im_sketch* sk) {
     im_ctx* c = sk->ctx;
-    CK(c, timed(c, kTFill, [&] {
-        return launch_fill(sk->M.as<uint8_t>(), sk->g->n, sk->J, sk->salt.as<uint32_t>(), sk->fresh, c->stream);
-    }));
+    if (sk->fill_pending) {
+        // the first fill ran on the side stream (sketch_start)
+        CK(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+        sk->fill_pending = false;
+    } else {
+        CK(c, timed(c, kTFill, [&] {
+            return launch_fill(sk->M.as<uint8_t>(), sk->g->n, sk->J, sk->salt.as<uint32_t>(), sk->fresh, c->stream);
+        }));
+    }
     sk->fresh = false;
     // every stored S_u stays a lower bound, but after a full build every row
     // is stale for a lazy pick: the next pick reads every row in one pass
@@ -1357,8 +1416,12 @@ static im_status build_buckets(im_sketch* sk) {
 
 // New sketch: buffers, the J simulations, the model words (the graph's, or
 // `model` for this call) and the live chunk masks of every edge.
+// prefill: the caller builds the registers next (im_sketch_build, a
+// selection): the first fill is issued on the side stream right after the
+// simulations are drawn, next to the live chunk masks, which do not read the
+// registers.
 static im_status sketch_start(im_ctx* c, im_graph* g, int32_t J, uint64_t seed, const im_model* model,
-                              im_sketch** out) {
+                              bool prefill, im_sketch** out) {
     CK(c, cudaSetDevice(c->device));
     im_sketch* sk = nullptr;
     CKS(sketch_alloc(c, g, J, &sk));
@@ -1370,6 +1433,17 @@ static im_status sketch_start(im_ctx* c, im_graph* g, int32_t J, uint64_t seed, 
         return launch_sims(seed, J, sk->X.as<uint32_t>(), sk->salt.as<uint32_t>(),
                            sk->tab.as<uint16_t>(), c->stream);
     });
+    if (e == cudaSuccess && prefill && sk->fresh) {
+        e = ensure_side(c);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_fork, c->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+        if (e == cudaSuccess)
+            e = timed_on(c, c->side, kTFill, [&] {
+                return launch_fill(sk->M.as<uint8_t>(), g->n, J, sk->salt.as<uint32_t>(), true, c->side);
+            });
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
+        if (e == cudaSuccess) sk->fill_pending = true;
+    }
     if (e != cudaSuccess) {
         sketch_release(sk);
         delete sk;
@@ -1392,7 +1466,7 @@ extern "C" im_status im_sketch_build(im_graph* g, int32_t J, uint64_t seed, im_s
     stats_begin(c);
     const double t0 = now_ms();
     im_sketch* sk = nullptr;
-    CKS(sketch_start(c, g, J, seed, nullptr, &sk));
+    CKS(sketch_start(c, g, J, seed, nullptr, true, &sk));
     im_status s = build_registers(sk);
     if (s == IM_OK) s = stats_collect(sk);
     if (s != IM_OK) {
@@ -1581,7 +1655,7 @@ static im_status select_seeds_impl(im_ctx* c, im_graph* g, int32_t K, int32_t J,
     stats_begin(c);
     const double t0 = now_ms();
     im_sketch* sk = nullptr;
-    CKS(sketch_start(c, g, J, seed, model, &sk));
+    CKS(sketch_start(c, g, J, seed, model, true, &sk));
     sk->lazy = c->tuning.lazy_pick != 0;
     sk->defer = true;
     // incremental rebuilds pay off with bucketed lists (sparse affected-set
@@ -1999,7 +2073,7 @@ extern "C" im_status im_batch_select_seeds(im_batch* b, const int32_t* J, const 
             te[g] = (int32_t)tiles.size();
         }
         im_sketch* sk = nullptr;
-        CKS(sketch_start(c, b->g, Jg, seed, nullptr, &sk));
+        CKS(sketch_start(c, b->g, Jg, seed, nullptr, false, &sk));
         DBuf tiles_d, tb_d, te_d, active_d, flag_d, gcount_d, pS, pU, oseed, oS, oest;
         std::vector<DBuf*> tmp = {&tiles_d, &tb_d, &te_d, &active_d, &flag_d, &gcount_d, &pS, &pU, &oseed, &oS, &oest};
         auto cleanup = [&]() {

@@ -1316,7 +1316,8 @@ __global__ void k_gather_u32(const uint32_t* __restrict__ src, const int32_t* __
 
 cudaError_t launch_gather_u32(const uint32_t* src, const int32_t* idx, int64_t m, uint32_t* dst, cudaStream_t st) {
     if (m == 0) return cudaSuccess;
-    k_gather_u32<<<152 * 8, kBlock, 0, st>>>(src, idx, m, dst);
+    // half the resident threads: the first fill runs next to it on the side stream
+    k_gather_u32<<<152 * 4, kBlock, 0, st>>>(src, idx, m, dst);
     return cudaGetLastError();
 }
 
